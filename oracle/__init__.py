@@ -1,0 +1,191 @@
+"""Plain CPU FP64 oracle for the covariance factor / sampling path.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product package never imports
+it.  The arithmetic lives in ``emu_oracle.c`` (plain loops, FP64); this module
+compiles it with gcc on first use and exposes numpy-friendly wrappers.
+
+Every matrix is a Fortran-ordered (column-major) float64 numpy array.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "emu_oracle.c")
+_HDR = os.path.join(_HERE, "emu_oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Unit roundoff of each precision class, most precise first:
+# FP64, FP32 (computed on tensor cores as split TF32), TF32, BF16, FP8-E4M3.
+CLASS_NAMES = ("fp64", "fp32", "tf32", "bf16", "e4m3")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if fresh and not force:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+           "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    i, lg, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+    L.orc_lm_of_index.argtypes = [lg, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.orc_cov_build.argtypes = [i, d, d, d, dp, lg]
+    L.orc_tile_norms.argtypes = [i, dp, lg, i, dp]
+    L.orc_frob_from_tiles.argtypes = [i, dp]
+    L.orc_frob_from_tiles.restype = d
+    L.orc_precision_map.argtypes = [i, dp, d, dp, i, ctypes.c_uint, i, u8p]
+    L.orc_potrf_unblocked.argtypes = [i, dp, lg]
+    L.orc_potrf_unblocked.restype = i
+    L.orc_potrf_blocked.argtypes = [i, i, dp, lg, i]
+    L.orc_potrf_blocked.restype = i
+    L.orc_trmm_lower.argtypes = [i, i, dp, lg, dp, lg, dp, lg]
+    L.orc_potrs.argtypes = [i, i, dp, lg, dp, lg, dp, lg]
+    L.orc_logdet_chol.argtypes = [i, dp, lg]
+    L.orc_logdet_chol.restype = d
+    L.orc_backward_error.argtypes = [i, dp, lg, dp, lg]
+    L.orc_backward_error.restype = d
+    L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.orc_normal_matrix.argtypes = [ctypes.c_uint64, ctypes.c_uint32, i, i, dp, lg]
+    L.orc_uniform_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint32, lg, i, dp, dp]
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    a = np.asarray(a, dtype=np.float64)
+    return np.asfortranarray(a)
+
+
+def lm_of_index(k: int):
+    l, m = ctypes.c_int(), ctypes.c_int()
+    lib().orc_lm_of_index(k, ctypes.byref(l), ctypes.byref(m))
+    return l.value, m.value
+
+
+def cov_build(L: int, beta: float, sigma_exp: float = 1.5, nugget_rel: float = 1e-8):
+    n = L * L
+    S = np.zeros((n, n), dtype=np.float64, order="F")
+    lib().orc_cov_build(L, beta, sigma_exp, nugget_rel, _dp(S), n)
+    return S
+
+
+def tile_norms(S, nb: int):
+    S = _f64(S)
+    n = S.shape[0]
+    NT = (n + nb - 1) // nb
+    t = np.zeros((NT, NT), dtype=np.float64, order="F")
+    lib().orc_tile_norms(n, _dp(S), S.shape[0], nb, _dp(t))
+    return t
+
+
+def frob_from_tiles(t):
+    t = _f64(t)
+    return lib().orc_frob_from_tiles(t.shape[0], _dp(t))
+
+
+def precision_map(t, eps: float, u, mask: int, diag_fp64: bool = False):
+    t = _f64(t)
+    NT = t.shape[0]
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    cls = np.zeros((NT, NT), dtype=np.uint8, order="F")
+    lib().orc_precision_map(NT, _dp(t), eps, _dp(u), len(u), mask, int(diag_fp64),
+                            cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return cls
+
+
+def potrf_unblocked(A):
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    info = lib().orc_potrf_unblocked(A.shape[0], _dp(A), A.shape[0])
+    return np.tril(A), info
+
+
+def potrf_blocked(A, nb: int, kmax: int = -1, inplace: bool = False):
+    if inplace:
+        assert A.dtype == np.float64 and A.flags.f_contiguous
+    else:
+        A = np.array(A, dtype=np.float64, order="F", copy=True)
+    info = lib().orc_potrf_blocked(A.shape[0], nb, _dp(A), A.shape[0], kmax)
+    if inplace:
+        return A, info
+    return np.tril(A), info
+
+
+def trmm_lower(Lf, Z):
+    Lf = _f64(Lf)
+    Z = _f64(Z)
+    n, s = Z.shape
+    Y = np.zeros((n, s), dtype=np.float64, order="F")
+    lib().orc_trmm_lower(n, s, _dp(Lf), Lf.shape[0], _dp(Z), n, _dp(Y), n)
+    return Y
+
+
+def potrs(Lf, B):
+    Lf = _f64(Lf)
+    B = _f64(B)
+    n, r = B.shape
+    X = np.zeros((n, r), dtype=np.float64, order="F")
+    lib().orc_potrs(n, r, _dp(Lf), Lf.shape[0], _dp(B), n, _dp(X), n)
+    return X
+
+
+def logdet_chol(Lf):
+    Lf = _f64(Lf)
+    return lib().orc_logdet_chol(Lf.shape[0], _dp(Lf), Lf.shape[0])
+
+
+def backward_error(A, Lf):
+    A = _f64(A)
+    Lf = _f64(Lf)
+    return lib().orc_backward_error(A.shape[0], _dp(A), A.shape[0], _dp(Lf), Lf.shape[0])
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def uniform_pair(seed: int, stream: int, p: int, c: int):
+    u1, u2 = ctypes.c_double(), ctypes.c_double()
+    lib().orc_uniform_pair(seed, stream, p, c, ctypes.byref(u1), ctypes.byref(u2))
+    return u1.value, u2.value
+
+
+def normal_matrix(seed: int, stream: int, n: int, s: int):
+    Z = np.zeros((n, s), dtype=np.float64, order="F")
+    lib().orc_normal_matrix(seed, stream, n, s, _dp(Z), n)
+    return Z

@@ -1,0 +1,293 @@
+/*
+ * emu_oracle.c -- plain CPU FP64 oracle (TEST INFRASTRUCTURE ONLY; see
+ * emu_oracle.h).  Slow on purpose: straight loops in the order the
+ * definitions are written, no blocking beyond the tile algorithm itself,
+ * OpenMP only across independent columns.  Shares nothing with the CUDA
+ * library.
+ */
+#include "emu_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+/* ---------------------------------------------------------------- indexing */
+void orc_lm_of_index(long k, int *l, int *m) {
+  /* k = l^2 + l + m with |m| <= l, so l = floor(sqrt(k)). */
+  long ll = 0;
+  while ((ll + 1) * (ll + 1) <= k) ll++;
+  *l = (int)ll;
+  *m = (int)(k - ll * ll - ll);
+}
+
+/* -------------------------------------------------------------- covariance */
+void orc_cov_build(int L, double beta, double sigma_exp, double nugget_rel,
+                   double *S, long ld) {
+  long n = (long)L * L;
+  for (long j = 0; j < n; j++) {
+    int lj, mj;
+    orc_lm_of_index(j, &lj, &mj);
+    double sj = pow(1.0 + lj, -sigma_exp);
+    for (long i = 0; i < n; i++) {
+      int li, mi;
+      orc_lm_of_index(i, &li, &mi);
+      double si = pow(1.0 + li, -sigma_exp);
+      double dl = (double)(li - lj), dm = (double)(mi - mj);
+      double d = sqrt(dl * dl + dm * dm);
+      S[IDX(i, j, ld)] = si * sj * exp(-d / beta);
+    }
+  }
+  double dmax = 0.0;
+  for (long k = 0; k < n; k++)
+    if (S[IDX(k, k, ld)] > dmax) dmax = S[IDX(k, k, ld)];
+  for (long k = 0; k < n; k++) S[IDX(k, k, ld)] += nugget_rel * dmax;
+}
+
+/* ------------------------------------------------------ norms and the map */
+void orc_tile_norms(int n, const double *S, long ld, int nb, double *t) {
+  int NT = (n + nb - 1) / nb;
+  for (int j = 0; j < NT; j++) {
+    for (int i = 0; i < NT; i++) {
+      if (i < j) {
+        t[i + (size_t)j * NT] = 0.0;
+        continue;
+      }
+      double ss = 0.0;
+      int r1 = (i + 1) * nb < n ? (i + 1) * nb : n;
+      int c1 = (j + 1) * nb < n ? (j + 1) * nb : n;
+      for (int c = j * nb; c < c1; c++) {
+        for (int r = i * nb; r < r1; r++) {
+          if (i == j && r < c) continue; /* lower triangle only */
+          double v = S[IDX(r, c, ld)];
+          double w = (i == j && r != c) ? 2.0 : 1.0; /* mirrored entry */
+          ss += w * v * v;
+        }
+      }
+      t[i + (size_t)j * NT] = sqrt(ss);
+    }
+  }
+}
+
+double orc_frob_from_tiles(int NT, const double *t) {
+  double ss = 0.0;
+  for (int j = 0; j < NT; j++)
+    for (int i = j; i < NT; i++) {
+      double v = t[i + (size_t)j * NT];
+      ss += (i == j ? 1.0 : 2.0) * v * v;
+    }
+  return sqrt(ss);
+}
+
+void orc_precision_map(int NT, const double *t, double eps, const double *u,
+                       int nclass, unsigned mask, int diag_fp64,
+                       unsigned char *cls) {
+  double thr = eps * orc_frob_from_tiles(NT, t) / (double)NT;
+  for (int j = 0; j < NT; j++)
+    for (int i = 0; i < NT; i++) {
+      if (i < j) {
+        cls[i + (size_t)j * NT] = 255;
+        continue;
+      }
+      int c = 0;
+      if (!(diag_fp64 && i == j)) {
+        for (int cc = nclass - 1; cc >= 1; cc--) {
+          if (((mask >> cc) & 1u) && t[i + (size_t)j * NT] * u[cc] <= thr) {
+            c = cc;
+            break;
+          }
+        }
+      }
+      cls[i + (size_t)j * NT] = (unsigned char)c;
+    }
+}
+
+/* -------------------------------------------------------------- Cholesky */
+int orc_potrf_unblocked(int n, double *A, long ld) {
+  /* Cholesky-Banachiewicz: row i of L from rows 0..i-1. */
+  for (int i = 0; i < n; i++) {
+    for (int j = 0; j <= i; j++) {
+      double s = A[IDX(i, j, ld)];
+      for (int p = 0; p < j; p++) s -= A[IDX(i, p, ld)] * A[IDX(j, p, ld)];
+      if (i == j) {
+        if (!(s > 0.0)) return i + 1;
+        A[IDX(i, i, ld)] = sqrt(s);
+      } else {
+        A[IDX(i, j, ld)] = s / A[IDX(j, j, ld)];
+      }
+    }
+  }
+  return 0;
+}
+
+/* Diagonal-block factor used inside the blocked algorithm: column-by-column
+ * (Cholesky-Crout), a different loop order from the unblocked routine above
+ * so that the two cross-check each other. */
+static int potrf_block(int kb, double *A, long ld) {
+  for (int j = 0; j < kb; j++) {
+    double d = A[IDX(j, j, ld)];
+    for (int p = 0; p < j; p++) d -= A[IDX(j, p, ld)] * A[IDX(j, p, ld)];
+    if (!(d > 0.0)) return j + 1;
+    d = sqrt(d);
+    A[IDX(j, j, ld)] = d;
+    for (int i = j + 1; i < kb; i++) {
+      double s = A[IDX(i, j, ld)];
+      for (int p = 0; p < j; p++) s -= A[IDX(i, p, ld)] * A[IDX(j, p, ld)];
+      A[IDX(i, j, ld)] = s / d;
+    }
+  }
+  return 0;
+}
+
+int orc_potrf_blocked(int n, int nb, double *A, long ld, int kmax) {
+  int NT = (n + nb - 1) / nb;
+  if (kmax < 0 || kmax > NT) kmax = NT;
+  for (int k = 0; k < kmax; k++) {
+    int k0 = k * nb;
+    int kb = (k0 + nb <= n) ? nb : n - k0;
+    /* POTRF(k,k) */
+    int info = potrf_block(kb, &A[IDX(k0, k0, ld)], ld);
+    if (info) return k0 + info;
+    int r0 = k0 + kb;
+    if (r0 >= n) break;
+    /* TRSM: A(r0:n, k0:k0+kb) <- A(r0:n, k0:k0+kb) * L_kk^{-T}, i.e. each row
+     * x solves L_kk x^T = a^T by forward substitution over the columns. */
+    for (int c = 0; c < kb; c++) {
+      double *xc = &A[IDX(r0, k0 + c, ld)];
+      for (int p = 0; p < c; p++) {
+        double l = A[IDX(k0 + c, k0 + p, ld)];
+        const double *xp = &A[IDX(r0, k0 + p, ld)];
+        for (int i = 0; i < n - r0; i++) xc[i] -= xp[i] * l;
+      }
+      double d = A[IDX(k0 + c, k0 + c, ld)];
+      for (int i = 0; i < n - r0; i++) xc[i] /= d;
+    }
+    /* SYRK/GEMM: A(j:n, j) -= A(j:n, panel) * A(j, panel)^T for j >= r0. */
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int j = r0; j < n; j++) {
+      double *cj = &A[IDX(j, j, ld)];
+      for (int p = 0; p < kb; p++) {
+        double ajp = A[IDX(j, k0 + p, ld)];
+        const double *ap = &A[IDX(j, k0 + p, ld)];
+        for (int i = 0; i < n - j; i++) cj[i] -= ap[i] * ajp;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ----------------------------------------------------- sampling and solve */
+void orc_trmm_lower(int n, int s, const double *Lf, long ldl, const double *Z,
+                    long ldz, double *Y, long ldy) {
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < s; c++) {
+    double *y = &Y[IDX(0, c, ldy)];
+    for (int i = 0; i < n; i++) y[i] = 0.0;
+    for (int p = 0; p < n; p++) {
+      double z = Z[IDX(p, c, ldz)];
+      const double *lp = &Lf[IDX(0, p, ldl)];
+      for (int i = p; i < n; i++) y[i] += lp[i] * z;
+    }
+  }
+}
+
+void orc_potrs(int n, int nrhs, const double *Lf, long ldl, const double *B,
+               long ldb, double *X, long ldx) {
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < nrhs; c++) {
+    double *x = &X[IDX(0, c, ldx)];
+    for (int i = 0; i < n; i++) x[i] = B[IDX(i, c, ldb)];
+    /* L y = b */
+    for (int p = 0; p < n; p++) {
+      x[p] /= Lf[IDX(p, p, ldl)];
+      const double *lp = &Lf[IDX(0, p, ldl)];
+      for (int i = p + 1; i < n; i++) x[i] -= lp[i] * x[p];
+    }
+    /* L^T x = y */
+    for (int p = n - 1; p >= 0; p--) {
+      const double *lp = &Lf[IDX(0, p, ldl)];
+      double s = x[p];
+      for (int i = p + 1; i < n; i++) s -= lp[i] * x[i];
+      x[p] = s / Lf[IDX(p, p, ldl)];
+    }
+  }
+}
+
+double orc_logdet_chol(int n, const double *Lf, long ldl) {
+  double s = 0.0;
+  for (int k = 0; k < n; k++) s += log(Lf[IDX(k, k, ldl)]);
+  return 2.0 * s;
+}
+
+double orc_backward_error(int n, const double *A, long lda, const double *Lf,
+                          long ldl) {
+  double num = 0.0, den = 0.0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : num, den)
+  for (int j = 0; j < n; j++) {
+    for (int i = j; i < n; i++) {
+      double m = 0.0;
+      for (int p = 0; p <= j; p++) m += Lf[IDX(i, p, ldl)] * Lf[IDX(j, p, ldl)];
+      double a = A[IDX(i, j, lda)];
+      double w = (i == j) ? 1.0 : 2.0;
+      num += w * (m - a) * (m - a);
+      den += w * a * a;
+    }
+  }
+  return sqrt(num) / sqrt(den);
+}
+
+/* ------------------------------------------------------------------- RNG */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u; /* Weyl sequence key schedule */
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+void orc_uniform_pair(uint64_t seed, uint32_t stream, long p, int c,
+                      double *u1, double *u2) {
+  uint32_t ctr[4] = {(uint32_t)((uint64_t)p & 0xffffffffu),
+                     (uint32_t)((uint64_t)p >> 32), (uint32_t)c, stream};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  orc_philox4x32_10(ctr, key, w);
+  uint64_t a = ((uint64_t)w[0] << 21) | (uint64_t)(w[1] >> 11); /* 53 bits */
+  uint64_t b = ((uint64_t)w[2] << 21) | (uint64_t)(w[3] >> 11);
+  *u1 = ((double)a + 1.0) * 0x1.0p-53; /* (0, 1] */
+  *u2 = (double)b * 0x1.0p-53;         /* [0, 1) */
+}
+
+void orc_normal_matrix(uint64_t seed, uint32_t stream, int n, int s, double *Z,
+                       long ldz) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int c = 0; c < s; c++) {
+    for (int r = 0; r < n; r += 2) {
+      double u1, u2;
+      orc_uniform_pair(seed, stream, r / 2, c, &u1, &u2);
+      double rad = sqrt(-2.0 * log(u1));
+      double th = two_pi * u2;
+      Z[IDX(r, c, ldz)] = rad * cos(th);
+      if (r + 1 < n) Z[IDX(r + 1, c, ldz)] = rad * sin(th);
+    }
+  }
+}

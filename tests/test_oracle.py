@@ -1,0 +1,281 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle itself:
+exact recovery of a known integer factor, two different Cholesky loop orders,
+eigenvalue log-determinants, backward error, closed-form covariance values,
+published Philox known-answer vectors, hand-derived precision maps and the
+distribution of the Box-Muller normals.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U = np.array([2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4])
+
+
+def _spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.logspace(0, -math.log10(cond), n)
+    return np.asfortranarray((Q * ev) @ Q.T)
+
+
+def _int_factor(n, seed):
+    """Lower-triangular integer L0, entries in [-3, 3], diagonal 2^k, k in {1,2,3}."""
+    rng = np.random.default_rng(seed)
+    L0 = np.tril(rng.integers(-3, 4, size=(n, n)).astype(np.float64), -1)
+    L0[np.diag_indices(n)] = 2.0 ** rng.integers(1, 4, size=n)
+    return L0
+
+
+# ------------------------------------------------------------------ factor
+@pytest.mark.parametrize("n,nb", [(1, 1), (7, 3), (32, 8), (64, 16), (64, 64), (50, 16)])
+def test_exact_recovery_of_integer_factor(n, nb):
+    # Sigma = L0 L0^T is exact in FP64 (small integers); every division is by a
+    # power of two and every square root is of a perfect square, so both
+    # algorithms must return L0 bit for bit.
+    L0 = _int_factor(n, seed=n * 131 + nb)
+    S = np.asfortranarray(L0 @ L0.T)
+    Lu, iu = O.potrf_unblocked(S)
+    Lb, ib = O.potrf_blocked(S, nb)
+    assert iu == 0 and ib == 0
+    assert np.array_equal(Lu, L0)
+    assert np.array_equal(Lb, L0)
+
+
+@pytest.mark.parametrize("n,nb", [(256, 64), (200, 64), (130, 17), (96, 128)])
+def test_blocked_matches_unblocked(n, nb):
+    S = _spd(n, seed=n + nb)
+    Lu, _ = O.potrf_unblocked(S)
+    Lb, _ = O.potrf_blocked(S, nb)
+    assert np.linalg.norm(Lb - Lu) / np.linalg.norm(Lu) < 1e-14
+    assert np.all(np.diag(Lb) > 0)
+    assert np.all(np.triu(Lb, 1) == 0)
+
+
+@pytest.mark.parametrize("n", [16, 100, 512])
+def test_logdet_equals_eigenvalue_sum(n):
+    S = _spd(n, seed=7 * n, cond=1e4)
+    Lb, _ = O.potrf_blocked(S, 32)
+    ld = O.logdet_chol(Lb)
+    ref = float(np.sum(np.log(np.linalg.eigvalsh(S))))
+    assert abs(ld - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("L,nb,beta", [(8, 16, 4.0), (16, 64, 4.0), (32, 128, 4.0)])
+def test_backward_error_on_covariance(L, nb, beta):
+    S = O.cov_build(L, beta)
+    Lb, info = O.potrf_blocked(S, nb)
+    assert info == 0
+    assert np.all(np.diag(Lb) > 0)
+    rel = np.linalg.norm(Lb @ Lb.T - S) / np.linalg.norm(S)
+    assert rel <= 1e-13
+    # the oracle's own backward-error routine agrees with numpy's product
+    assert abs(O.backward_error(S, Lb) - rel) <= 1e-15 + 1e-3 * rel
+
+
+def test_partial_factor_steps():
+    # kmax panel steps leave the first kmax*nb columns final and the trailing
+    # block equal to its Schur complement.
+    S = _spd(96, seed=3)
+    A, info = O.potrf_blocked(S, 32, kmax=1, inplace=False)
+    assert info == 0
+    Lfull, _ = O.potrf_blocked(S, 32)
+    assert np.allclose(A[:, :32], Lfull[:, :32], rtol=0, atol=1e-13)
+    L11 = Lfull[:32, :32]
+    L21 = Lfull[32:, :32]
+    schur = S[32:, 32:] - L21 @ L21.T
+    assert np.allclose(np.tril(A[32:, 32:]), np.tril(schur), atol=1e-13)
+    assert np.allclose(L11 @ L11.T, S[:32, :32], atol=1e-13)
+
+
+@pytest.mark.parametrize("blocked", [False, True])
+def test_not_positive_definite_reports_pivot(blocked):
+    n = 40
+    S = np.asfortranarray(np.eye(n))
+    S[22, 22] = -1.0  # first failing pivot: column 23 (1-based)
+    if blocked:
+        _, info = O.potrf_blocked(S, 16)
+    else:
+        _, info = O.potrf_unblocked(S)
+    assert info == 23
+
+
+# -------------------------------------------------------------- covariance
+def test_index_order_by_degree_then_order():
+    k = 0
+    for l in range(12):
+        for m in range(-l, l + 1):
+            assert O.lm_of_index(k) == (l, m)
+            k += 1
+
+
+def test_covariance_closed_form_values():
+    L, beta = 8, 4.0
+    S = O.cov_build(L, beta)
+    n = L * L
+    assert S.shape == (n, n)
+    assert np.array_equal(S, S.T)
+    # sigma_0 = 1 is the largest diagonal entry, so the nugget is 1e-8 exactly
+    assert S[0, 0] == 1.0 + 1e-8
+    # diagonal: (1+l)^-3 + 1e-8; for l = 1, 3, 7 this is 1/8, 1/64, 1/512
+    for l, v in [(1, 1 / 8), (3, 1 / 64), (7, 1 / 512)]:
+        k = l * l + l
+        assert abs(S[k, k] - (v + 1e-8)) <= 4e-16 * v
+    # correlation depends on the distance between (l,m) pairs only and is
+    # exp(-d/beta): collinear steps multiply, rho(d1 + d2) = rho(d1) rho(d2)
+    D = np.sqrt(np.diag(S) - 1e-8)
+    R = S / np.outer(D, D)
+
+    def rho(a, b):
+        return R[a[0] ** 2 + a[0] + a[1], b[0] ** 2 + b[0] + b[1]]
+
+    assert abs(rho((2, 0), (4, 0)) - rho((2, 0), (3, 0)) * rho((3, 0), (4, 0))) < 1e-15
+    assert abs(rho((3, -2), (3, 2)) - rho((3, -2), (3, 0)) ** 2) < 1e-15
+    # translation invariance in (l, m)
+    assert abs(rho((2, 1), (5, 3)) - rho((3, 1), (6, 3))) < 1e-15
+    # unit distance: rho = e^{-1/beta}; distance 5 via the 3-4-5 triangle
+    assert abs(rho((4, 0), (5, 0)) - math.exp(-0.25)) < 1e-15
+    assert abs(rho((1, 0), (4, 4)) - math.exp(-5 / 4)) < 1e-15
+
+
+def test_covariance_limits_and_definiteness():
+    # beta -> 0 removes all correlation: S = diag((1+l)^-3) + nugget
+    S0 = O.cov_build(5, 1e-4)
+    off = S0 - np.diag(np.diag(S0))
+    assert np.max(np.abs(off)) == 0.0
+    # the exponential kernel is positive definite, so lambda_min >= nugget
+    S = O.cov_build(8, 4.0)
+    lam = np.linalg.eigvalsh(S)
+    assert lam.min() >= 1e-8 * (1 - 1e-6)
+
+
+def test_tile_norms_against_numpy():
+    S = O.cov_build(10, 3.0)  # n = 100, ragged with nb = 32
+    nb = 32
+    t = O.tile_norms(S, nb)
+    NT = 4
+    for i in range(NT):
+        for j in range(NT):
+            blk = S[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb]
+            ref = np.linalg.norm(blk) if i >= j else 0.0
+            assert abs(t[i, j] - ref) <= 1e-14 * max(ref, 1e-300)
+    assert abs(O.frob_from_tiles(t) - np.linalg.norm(S)) <= 1e-14 * np.linalg.norm(S)
+
+
+# ------------------------------------------------------------ precision map
+def _hand_cases():
+    rows = []
+    with open(os.path.join(GOLDEN, "precision_map_hand.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            lhs, rhs = line.split(":")
+            eps, mask, dg = lhs.split()
+            rows.append((float(eps), int(mask), int(dg), [int(x) for x in rhs.split()]))
+    return rows
+
+
+@pytest.mark.parametrize("eps,mask,dg,expect", _hand_cases())
+def test_precision_map_hand_derived(eps, mask, dg, expect):
+    t = np.array([[2.0, 0.0], [1e-6, 1.0]], order="F")
+    c = O.precision_map(t, eps, U, mask, bool(dg))
+    assert [c[0, 0], c[1, 0], c[1, 1]] == expect
+    assert c[0, 1] == 255
+
+
+def test_precision_map_properties():
+    S = O.cov_build(16, 6.0)
+    t = O.tile_norms(S, 32)
+    NT = t.shape[0]
+    for eps in [1e-12, 1e-8, 1e-6, 1e-3]:
+        c = O.precision_map(t, eps, U, 0b11111, False)
+        thr = eps * np.linalg.norm(S) / NT
+        err2 = 0.0
+        for i in range(NT):
+            for j in range(i + 1):
+                cc = c[i, j]
+                assert cc == 0 or t[i, j] * U[cc] <= thr
+                for lower in range(cc + 1, 5):  # every less precise class fails
+                    assert t[i, j] * U[lower] > thr
+                err2 += (1 if i == j else 2) * (t[i, j] * U[cc]) ** 2
+        # the rule's purpose: summed tile-level rounding stays below eps*||S||
+        assert math.sqrt(err2) <= eps * np.linalg.norm(S) * (1 + 1e-12) or np.all(
+            c[np.tril_indices(NT)] == 0)
+    # eps tiny -> all fp64; eps huge -> everything in the least precise class
+    assert np.all(O.precision_map(t, 1e-300, U, 31)[np.tril_indices(NT)] == 0)
+    assert np.all(O.precision_map(t, 1e6, U, 31)[np.tril_indices(NT)] == 4)
+    assert np.all(O.precision_map(t, 1e6, U, 0b01011)[np.tril_indices(NT)] == 3)
+
+
+# -------------------------------------------------------------------- RNG
+def _kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            lhs, rhs = line.split(":")
+            w = [int(x, 16) for x in lhs.split()]
+            rows.append((w[:4], w[4:], [int(x, 16) for x in rhs.split()]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,out", _kat())
+def test_philox_known_answers(ctr, key, out):
+    assert O.philox4x32_10(ctr, key) == out
+
+
+def test_uniform_ranges_and_counter_independence():
+    u1, u2 = O.uniform_pair(0, 0, 0, 0)
+    assert 0.0 < u1 <= 1.0 and 0.0 <= u2 < 1.0
+    assert O.uniform_pair(0, 0, 0, 0) != O.uniform_pair(1, 0, 0, 0)  # seed
+    assert O.uniform_pair(0, 0, 0, 0) != O.uniform_pair(0, 1, 0, 0)  # stream
+    assert O.uniform_pair(0, 0, 1, 0) != O.uniform_pair(0, 0, 0, 1)  # row pair vs column
+
+
+def test_box_muller_distribution():
+    from scipy import stats
+
+    Z = O.normal_matrix(seed=12345, stream=0, n=1000, s=400)
+    z = Z.ravel()
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # the two members of a Box-Muller pair are uncorrelated, and their squared
+    # radius is -2 ln u1
+    a, b = Z[0::2, :].ravel(), Z[1::2, :].ravel()
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / math.sqrt(a.size)
+    u1, _ = O.uniform_pair(12345, 0, 3, 7)
+    assert abs(Z[6, 7] ** 2 + Z[7, 7] ** 2 + 2 * math.log(u1)) < 1e-12
+    # odd n: the last row takes the cosine member
+    Zo = O.normal_matrix(seed=12345, stream=0, n=7, s=3)
+    assert np.array_equal(Zo, Z[:7, :3])
+
+
+# ----------------------------------------------------------- sample, solve
+def test_trmm_matches_numpy_and_reproduces_covariance():
+    S = O.cov_build(4, 2.0)  # n = 16
+    Lb, _ = O.potrf_blocked(S, 8)
+    Z = O.normal_matrix(seed=5, stream=0, n=16, s=64)
+    Y = O.trmm_lower(Lb, Z)
+    assert np.allclose(Y, Lb @ Z, rtol=0, atol=1e-14)
+    # second moment: E[Y Y^T] = L L^T = S
+    Zb = O.normal_matrix(seed=6, stream=0, n=16, s=200000)
+    Yb = O.trmm_lower(Lb, Zb)
+    C = Yb @ Yb.T / Yb.shape[1]
+    d = np.sqrt(np.diag(S))
+    assert np.max(np.abs(C - S) / np.outer(d, d)) < 6 / math.sqrt(Yb.shape[1])
+
+
+def test_potrs_solves():
+    S = O.cov_build(6, 3.0)
+    Lb, _ = O.potrf_blocked(S, 16)
+    rng = np.random.default_rng(0)
+    B = np.asfortranarray(rng.standard_normal((36, 5)))
+    X = O.potrs(Lb, B)
+    ref = np.linalg.solve(S, B)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-11
