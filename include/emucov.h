@@ -1,0 +1,205 @@
+/*
+ * emucov.h -- C ABI of the GB300 (sm_103a) covariance-factorisation library
+ * for spherical-harmonic climate emulators (arXiv 2408.04440).
+ *
+ * What the library computes (paper sections):
+ *   - "Modeling the Temporal Dependence and Constructing a Covariance Matrix":
+ *     the L^2 x L^2 covariance U-hat of the spherical-harmonic coefficients,
+ *     made positive definite by a small diagonal perturbation, and its
+ *     Cholesky factor U-hat = V V^T (the O(L^6) step).
+ *   - "Advancements in Dense Linear Algebra" and "Mixed-Precision Computation
+ *     Innovations": the factor is a tile algorithm (POTRF on diagonal tiles,
+ *     TRSM on the panel, SYRK/GEMM on the trailing tiles) in which each tile
+ *     runs in its own precision.
+ *   - "Performance of Mixed-Precision Cholesky on Summit": a panel tile is
+ *     converted once, by its producer, into the precision of its consumers.
+ *   - "Generating Emulations": draws xi = V z with z ~ N(0, I).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are indexed from 0.  Dense arrays passed in or out are FP64,
+ *     column-major, with a leading dimension `ld` >= number of rows, and live
+ *     in DEVICE memory unless a parameter says "host".
+ *   - The library owns `emu_ctx` and `emu_mat` objects; they are released only
+ *     by emu_destroy / emu_mat_free.  Caller pointers are borrowed for the
+ *     duration of the call and of the stream work it enqueues.
+ *   - All device work is enqueued on the context's stream (the one given to
+ *     emu_create; NULL = the legacy default stream).  Calls that fill an
+ *     `info` struct, or that return a status decided on the device
+ *     (EMU_ENOTPD, EMU_ETIMEOUT, EMU_ENOCONV), synchronise that stream.
+ *   - Every call returns an emu_status.  No exception or signal crosses the
+ *     ABI.  On EMU_ECUDA the CUDA error string is kept in the context
+ *     (emu_last_error).  Arguments are validated on the host before any launch.
+ *   - The library runs on one GPU, the device given to emu_create, which must
+ *     be an sm_103 (GB300) device.
+ */
+#ifndef EMUCOV_H
+#define EMUCOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EMU_OK = 0,
+  EMU_EINVAL = 1,   /* bad argument (checked on the host)                    */
+  EMU_ENOMEM = 2,   /* device allocation failed or a size limit was exceeded */
+  EMU_ENOTPD = 3,   /* factor met a non-positive pivot; see info->pivot      */
+  EMU_ENOCONV = 4,  /* refinement did not reach tol within maxit             */
+  EMU_ETIMEOUT = 5, /* a bounded device wait expired                         */
+  EMU_ECUDA = 6,    /* CUDA runtime/driver error; see emu_last_error         */
+  EMU_ESTATE = 7    /* matrix in the wrong state for this call               */
+} emu_status;
+
+/* Precision classes of a tile, most precise first.  The unit roundoff u that
+ * the precision rule uses for each class is in emu_mp_opts.u (defaults:
+ * 2^-53, 2^-24, 2^-11, 2^-8, 2^-4).  "fp32" is computed on the tensor cores
+ * as a three-way BF16 split of each operand (six partial products, FP32
+ * accumulation); "e4m3" carries a power-of-two scale per tile. */
+enum {
+  EMU_CLASS_FP64 = 0,
+  EMU_CLASS_FP32 = 1,
+  EMU_CLASS_TF32 = 2,
+  EMU_CLASS_BF16 = 3,
+  EMU_CLASS_E4M3 = 4,
+  EMU_NCLASS = 5
+};
+
+typedef struct emu_ctx emu_ctx;
+typedef struct emu_mat emu_mat;
+
+/* Synthetic covariance of the spherical-harmonic coefficients, a stand-in for
+ * the empirical U-hat ("Modeling the Temporal Dependence ...", equation for
+ * U-hat, and the diagonal perturbation that follows it).  Row k holds the
+ * coefficient (l, m), k = l^2 + l + m, 0 <= l < L, |m| <= l, n = L^2:
+ *   S[i,j] = s(l_i) s(l_j) exp(-sqrt((l_i-l_j)^2 + (m_i-m_j)^2) / beta),
+ *   s(l) = (1 + l)^(-sigma_exp),   S[k,k] += nugget_rel * max_k S[k,k]. */
+typedef struct {
+  int L;
+  double beta;
+  double sigma_exp;
+  double nugget_rel;
+} emu_cov_params;
+
+/* Options of the factorisation ("Mixed-Precision Computation Innovations").
+ * eps <= 0 selects the plain FP64 tile Cholesky.  eps > 0 selects the adaptive
+ * per-tile precision: tile (i,j) runs in the least precise class c allowed by
+ * prec_mask for which ||S_ij||_F * u[c] <= eps * ||S||_F / NT (NT = number of
+ * tile rows, ||S||_F over the full symmetric matrix); FP64 when none passes.
+ * The diagonal POTRF is always FP64.  diag_fp64 != 0 also pins the diagonal
+ * tiles' storage and updates to FP64.  u[c] <= 0 takes the default. */
+typedef struct {
+  double eps;
+  unsigned prec_mask; /* bit c enables class c; bit 0 (FP64) is implied */
+  int diag_fp64;
+  double u[EMU_NCLASS];
+} emu_mp_opts;
+
+typedef struct {
+  int n, nb, nt;
+  int pivot;                  /* EMU_ENOTPD: 1-based global column, else 0  */
+  int tiles[EMU_NCLASS];      /* lower tiles per class                      */
+  double update_flops[EMU_NCLASS]; /* SYRK/GEMM/TRSM flops per class        */
+  double frob;                /* ||S||_F of the input (0 for plain FP64)    */
+  double ms;                  /* device time of the factor, CUDA events     */
+} emu_factor_info;
+
+typedef struct {
+  int iters;        /* refinement corrections applied                       */
+  double rel_resid; /* at exit, max over columns of the normwise backward
+                       error ||b - S x||_2 / (||S||_F ||x||_2 + ||b||_2)     */
+  double ms;
+} emu_refine_info;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on `device` that enqueues on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  Fails with EMU_EINVAL when the device is
+ * not sm_103. */
+emu_status emu_create(emu_ctx **ctx, int device, void *stream);
+emu_status emu_destroy(emu_ctx *ctx);
+emu_status emu_set_stream(emu_ctx *ctx, void *stream);
+const char *emu_status_str(emu_status s);
+const char *emu_last_error(const emu_ctx *ctx);
+/* Number of this library's kernels launched through `ctx` so far. */
+uint64_t emu_launch_count(const emu_ctx *ctx);
+
+/* ---------------------------------------------------------------- matrices */
+/* Build the synthetic covariance on the device as an n x n tiled matrix with
+ * tile size nb (n = L^2).  The lower tiles are stored packed, each tile
+ * nb x nb column-major in FP64; a ragged last tile row is padded with zeros
+ * and a unit diagonal, which the factor carries through as an identity block.
+ * The per-tile Frobenius norms are computed in the same pass. */
+emu_status emu_cov_build(emu_ctx *ctx, const emu_cov_params *p, int nb,
+                         emu_mat **out);
+/* Import a user covariance: dA is n x n FP64 column-major on the device, only
+ * its lower triangle is read. */
+emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda,
+                          int nb, emu_mat **out);
+/* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
+emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);
+/* Write the matrix as a dense FP64 lower triangle (upper set to 0) into dOut
+ * (n x n, column-major, device).  For a mixed factor each tile is widened
+ * from its stored precision. */
+emu_status emu_mat_export(emu_ctx *ctx, const emu_mat *A, double *dOut,
+                          long ld);
+/* Copy the per-tile precision classes (NT x NT column-major bytes, upper =
+ * 255) and tile norms (NT x NT doubles, upper = 0) to HOST arrays; either
+ * pointer may be NULL. */
+emu_status emu_mat_tile_info(emu_ctx *ctx, const emu_mat *A,
+                             unsigned char *h_cls, double *h_norms);
+/* n, nb, NT and state (0 = covariance, 1 = FP64 factor, 2 = mixed factor). */
+emu_status emu_mat_shape(const emu_mat *A, int *n, int *nb, int *nt,
+                         int *state);
+emu_status emu_mat_free(emu_mat *A);
+
+/* ------------------------------------------------------------------ factor */
+/* Factor A = L L^T in place (A must hold a covariance, state 0).  Plain FP64
+ * when o == NULL or o->eps <= 0, otherwise the adaptive mixed-precision tile
+ * factor described at emu_mp_opts.  On a non-positive pivot returns
+ * EMU_ENOTPD with info->pivot set and leaves A in an unspecified state. */
+emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o,
+                        emu_factor_info *info);
+
+/* ---------------------------------------------------------------- sampling */
+/* Draw `nsamples` emulations Y = L Z ("Generating Emulations", xi = V z) with
+ * Z ~ N(0, I) generated on the device: entry (r, c) of Z comes from
+ * Philox4x32-10 (Salmon et al., SC'11) at counter {r/2 mod 2^32, r/2 >> 32,
+ * c, stream_id} and key {seed mod 2^32, seed >> 32}, turned into two 53-bit
+ * uniforms and a Box-Muller pair for rows (2p, 2p+1), so Y is bit-identical
+ * for the same (seed, factor) whatever the launch shape.  dY: n x nsamples
+ * FP64, column-major, ldy >= n.  If dZ != NULL the normals are also written
+ * there (n x nsamples, ld ldy). */
+emu_status emu_sample(emu_ctx *ctx, const emu_mat *L, int nsamples,
+                      uint64_t seed, uint32_t stream_id, double *dY, long ldy,
+                      double *dZ);
+
+/* Same, with Y and (optionally) Z in HOST memory: the device work and both
+ * copies are enqueued on the context stream and the call returns after the
+ * copies complete. */
+emu_status emu_sample_host(emu_ctx *ctx, const emu_mat *L, int nsamples,
+                           uint64_t seed, uint32_t stream_id, double *hY,
+                           long ldy);
+
+/* ------------------------------------------------------------------ solves */
+/* X = (L L^T)^{-1} B with the factor L (two triangular solves in the stored
+ * tile precisions).  dB, dX: n x nrhs, column-major; dX may equal dB. */
+emu_status emu_potrs(emu_ctx *ctx, const emu_mat *L, const double *dB,
+                     long ldb, double *dX, long ldx, int nrhs);
+
+/* Solve S X = B by iterative refinement: X0 = (L L^T)^{-1} B, then FP64
+ * residual R = B - S X against the FP64 covariance S (state 0, same n and
+ * nb as L), correction D = (L L^T)^{-1} R in the factor's precisions, FP64
+ * update X += D, until every column's normwise backward error
+ * ||r||_2 / (||S||_F ||x||_2 + ||b||_2) is <= tol.  Returns EMU_ENOCONV when
+ * maxit corrections do not reach tol (X then holds the last iterate). */
+emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu_mat *S,
+                            const double *dB, long ldb, double *dX, long ldx,
+                            int nrhs, double tol, int maxit,
+                            emu_refine_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMUCOV_H */

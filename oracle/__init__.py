@@ -60,6 +60,7 @@ def _declare(L):
     i, lg, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
     L.orc_lm_of_index.argtypes = [lg, ctypes.POINTER(i), ctypes.POINTER(i)]
     L.orc_cov_build.argtypes = [i, d, d, d, dp, lg]
+    L.orc_cov_rows.argtypes = [i, d, d, d, ctypes.POINTER(lg), i, dp]
     L.orc_tile_norms.argtypes = [i, dp, lg, i, dp]
     L.orc_frob_from_tiles.argtypes = [i, dp]
     L.orc_frob_from_tiles.restype = d
@@ -99,6 +100,15 @@ def cov_build(L: int, beta: float, sigma_exp: float = 1.5, nugget_rel: float = 1
     S = np.zeros((n, n), dtype=np.float64, order="F")
     lib().orc_cov_build(L, beta, sigma_exp, nugget_rel, _dp(S), n)
     return S
+
+
+def cov_rows(L: int, beta: float, rows, sigma_exp: float = 1.5, nugget_rel: float = 1e-8):
+    """Rows `rows` of the covariance (len(rows) x L^2), without the full matrix."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), L * L), dtype=np.float64, order="F")
+    lib().orc_cov_rows(L, beta, sigma_exp, nugget_rel, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                       len(rows), _dp(out))
+    return out
 
 
 def tile_norms(S, nb: int):

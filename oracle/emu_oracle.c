@@ -45,6 +45,32 @@ void orc_cov_build(int L, double beta, double sigma_exp, double nugget_rel,
   for (long k = 0; k < n; k++) S[IDX(k, k, ld)] += nugget_rel * dmax;
 }
 
+void orc_cov_rows(int L, double beta, double sigma_exp, double nugget_rel,
+                  const long *rows, int nrows, double *out) {
+  long n = (long)L * L;
+  /* max diagonal entry: the diagonal of the correlation part is exp(0) = 1 */
+  double dmax = 0.0;
+  for (int l = 0; l < L; l++) {
+    double s = pow(1.0 + l, -sigma_exp);
+    if (s * s > dmax) dmax = s * s;
+  }
+  for (int q = 0; q < nrows; q++) {
+    long i = rows[q];
+    int li, mi;
+    orc_lm_of_index(i, &li, &mi);
+    double si = pow(1.0 + li, -sigma_exp);
+    for (long j = 0; j < n; j++) {
+      int lj, mj;
+      orc_lm_of_index(j, &lj, &mj);
+      double sj = pow(1.0 + lj, -sigma_exp);
+      double dl = (double)(li - lj), dm = (double)(mi - mj);
+      double v = si * sj * exp(-sqrt(dl * dl + dm * dm) / beta);
+      if (j == i) v += nugget_rel * dmax;
+      out[q + j * (long)nrows] = v;
+    }
+  }
+}
+
 /* ------------------------------------------------------ norms and the map */
 void orc_tile_norms(int n, const double *S, long ld, int nb, double *t) {
   int NT = (n + nb - 1) / nb;

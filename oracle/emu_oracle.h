@@ -40,6 +40,11 @@ void orc_lm_of_index(long k, int *l, int *m);
 void orc_cov_build(int L, double beta, double sigma_exp, double nugget_rel,
                    double *S, long ld);
 
+/* Selected rows of the same covariance: out[q + c*nrows] = S[rows[q], c]
+ * for c < n (nrows x n, column-major), without forming the full matrix. */
+void orc_cov_rows(int L, double beta, double sigma_exp, double nugget_rel,
+                  const long *rows, int nrows, double *out);
+
 /* Frobenius norm of every lower tile (i >= j) of the tiling with tile size nb
  * (the last tile row/column is ragged when nb does not divide n).
  * t[i + j*NT] = ||S_ij||_F, NT = ceil(n/nb); upper entries set to 0. */

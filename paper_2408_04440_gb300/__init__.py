@@ -1,0 +1,318 @@
+"""GB300-native mixed-precision covariance factorisation for spherical-harmonic
+climate emulators (arXiv 2408.04440): Python binding of ``libemucov``.
+
+This module only marshals arguments into the C ABI declared in
+``include/emucov.h`` (same function names); every step of the computation runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.
+Importing works without a GPU; calling anything that needs the library fails
+loudly if ``libemucov.so`` has not been built (``build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libemucov.so")
+
+EMU_OK, EMU_EINVAL, EMU_ENOMEM, EMU_ENOTPD, EMU_ENOCONV, EMU_ETIMEOUT, EMU_ECUDA, EMU_ESTATE = range(8)
+STATUS_NAMES = {0: "EMU_OK", 1: "EMU_EINVAL", 2: "EMU_ENOMEM", 3: "EMU_ENOTPD", 4: "EMU_ENOCONV",
+                5: "EMU_ETIMEOUT", 6: "EMU_ECUDA", 7: "EMU_ESTATE"}
+CLASS_FP64, CLASS_FP32, CLASS_TF32, CLASS_BF16, CLASS_E4M3 = range(5)
+NCLASS = 5
+CLASS_NAMES = ("fp64", "fp32", "tf32", "bf16", "e4m3")
+DEFAULT_U = (2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4)
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTED = (
+    "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
+    "emu_launch_count", "emu_cov_build", "emu_mat_import", "emu_mat_clone", "emu_mat_export",
+    "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free", "emu_potrf_mp", "emu_sample",
+    "emu_sample_host", "emu_potrs", "emu_solve_refine",
+)
+
+
+class EmuError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class emu_cov_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("beta", ctypes.c_double), ("sigma_exp", ctypes.c_double),
+                ("nugget_rel", ctypes.c_double)]
+
+
+class emu_mp_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("prec_mask", ctypes.c_uint), ("diag_fp64", ctypes.c_int),
+                ("u", ctypes.c_double * NCLASS)]
+
+
+class emu_factor_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nb", ctypes.c_int), ("nt", ctypes.c_int), ("pivot", ctypes.c_int),
+                ("tiles", ctypes.c_int * NCLASS), ("update_flops", ctypes.c_double * NCLASS),
+                ("frob", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class emu_refine_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libemucov.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2408_04440_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, lg, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    st = ctypes.c_int
+    L.emu_create.argtypes = [ctypes.POINTER(vp), i, vp]
+    L.emu_destroy.argtypes = [vp]
+    L.emu_set_stream.argtypes = [vp, vp]
+    L.emu_status_str.argtypes = [st]
+    L.emu_status_str.restype = ctypes.c_char_p
+    L.emu_last_error.argtypes = [vp]
+    L.emu_last_error.restype = ctypes.c_char_p
+    L.emu_launch_count.argtypes = [vp]
+    L.emu_launch_count.restype = ctypes.c_uint64
+    L.emu_cov_build.argtypes = [vp, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(vp)]
+    L.emu_mat_import.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
+    L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
+    L.emu_mat_export.argtypes = [vp, vp, vp, lg]
+    L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
+    L.emu_mat_shape.argtypes = [vp] + [ctypes.POINTER(i)] * 4
+    L.emu_mat_free.argtypes = [vp]
+    L.emu_potrf_mp.argtypes = [vp, vp, ctypes.POINTER(emu_mp_opts), ctypes.POINTER(emu_factor_info)]
+    L.emu_sample.argtypes = [vp, vp, i, ctypes.c_uint64, ctypes.c_uint32, vp, lg, vp]
+    L.emu_sample_host.argtypes = [vp, vp, i, ctypes.c_uint64, ctypes.c_uint32, vp, lg]
+    L.emu_potrs.argtypes = [vp, vp, vp, lg, vp, lg, i]
+    L.emu_solve_refine.argtypes = [vp, vp, vp, vp, lg, vp, lg, i, d, i, ctypes.POINTER(emu_refine_info)]
+    for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_cov_build", "emu_mat_import",
+                 "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
+                 "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine"):
+        getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _colmajor_empty(rows: int, cols: int, device):
+    """(rows x cols) FP64 tensor whose storage is column-major with ld = rows."""
+    import torch
+
+    return torch.empty((cols, rows), dtype=torch.float64, device=device).t()
+
+
+class Context:
+    """A library context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        self._check(self.lib.emu_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)),
+                    "emu_create", with_ctx=False)
+        self.h = h
+
+    def _check(self, status: int, where: str, with_ctx: bool = True):
+        if status != EMU_OK:
+            detail = ""
+            if with_ctx and getattr(self, "h", None):
+                detail = (self.lib.emu_last_error(self.h) or b"").decode()
+            raise EmuError(status, where, detail)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.emu_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.emu_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Mat:
+    """A tiled matrix owned by the library (covariance or factor)."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p):
+        self.ctx = ctx
+        self.h = handle
+
+    def shape_info(self):
+        n, nb, nt, st = (ctypes.c_int() for _ in range(4))
+        self.ctx._check(self.ctx.lib.emu_mat_shape(self.h, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(nt),
+                                                   ctypes.byref(st)), "emu_mat_shape")
+        return n.value, nb.value, nt.value, st.value
+
+    @property
+    def n(self):
+        return self.shape_info()[0]
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.emu_mat_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def emu_cov_build(ctx: Context, L: int, beta: float, nb: int, sigma_exp: float = 1.5,
+                  nugget_rel: float = 1e-8) -> Mat:
+    p = emu_cov_params(L, beta, sigma_exp, nugget_rel)
+    h = ctypes.c_void_p()
+    ctx._check(ctx.lib.emu_cov_build(ctx.h, ctypes.byref(p), nb, ctypes.byref(h)), "emu_cov_build")
+    return Mat(ctx, h)
+
+
+def emu_mat_import(ctx: Context, A, nb: int) -> Mat:
+    """A: (n x n) float64 CUDA tensor; its lower triangle is read."""
+    n = A.shape[0]
+    if A.stride() != (1, n):
+        A = A.t().contiguous().t()  # column-major storage
+    h = ctypes.c_void_p()
+    ctx._check(ctx.lib.emu_mat_import(ctx.h, ctypes.c_void_p(_ptr(A)), n, n, nb, ctypes.byref(h)),
+               "emu_mat_import")
+    m = Mat(ctx, h)
+    m._keep = A
+    return m
+
+
+def emu_mat_clone(ctx: Context, A: Mat) -> Mat:
+    h = ctypes.c_void_p()
+    ctx._check(ctx.lib.emu_mat_clone(ctx.h, A.h, ctypes.byref(h)), "emu_mat_clone")
+    return Mat(ctx, h)
+
+
+def emu_mat_export(ctx: Context, A: Mat, out=None):
+    n = A.n
+    if out is None:
+        out = _colmajor_empty(n, n, ctx.device)
+    ctx._check(ctx.lib.emu_mat_export(ctx.h, A.h, ctypes.c_void_p(_ptr(out)), out.stride(1)), "emu_mat_export")
+    return out
+
+
+def emu_mat_tile_info(ctx: Context, A: Mat):
+    nt = A.shape_info()[2]
+    cls = np.zeros((nt, nt), dtype=np.uint8, order="F")
+    tn = np.zeros((nt, nt), dtype=np.float64, order="F")
+    ctx._check(ctx.lib.emu_mat_tile_info(ctx.h, A.h, ctypes.c_void_p(cls.ctypes.data),
+                                         ctypes.c_void_p(tn.ctypes.data)), "emu_mat_tile_info")
+    return cls, tn
+
+
+@dataclass
+class FactorInfo:
+    status: int
+    n: int
+    nb: int
+    nt: int
+    pivot: int
+    tiles: list = field(default_factory=list)
+    update_flops: list = field(default_factory=list)
+    frob: float = 0.0
+    ms: float = 0.0
+
+
+def mp_opts(eps: float = 0.0, prec_mask: int = 0b01011, diag_fp64: bool = False, u=None) -> emu_mp_opts:
+    uu = (ctypes.c_double * NCLASS)(*(u if u is not None else DEFAULT_U))
+    return emu_mp_opts(eps, prec_mask, int(diag_fp64), uu)
+
+
+def emu_potrf_mp(ctx: Context, A: Mat, eps: float = 0.0, prec_mask: int = 0b01011, diag_fp64: bool = False,
+                 u=None, raise_on_error: bool = True) -> FactorInfo:
+    o = mp_opts(eps, prec_mask, diag_fp64, u)
+    info = emu_factor_info()
+    s = ctx.lib.emu_potrf_mp(ctx.h, A.h, ctypes.byref(o), ctypes.byref(info))
+    fi = FactorInfo(s, info.n, info.nb, info.nt, info.pivot, list(info.tiles), list(info.update_flops),
+                    info.frob, info.ms)
+    if raise_on_error and s != EMU_OK:
+        ctx._check(s, "emu_potrf_mp")
+    return fi
+
+
+def emu_sample(ctx: Context, L: Mat, nsamples: int, seed: int, stream_id: int = 0, out=None,
+               return_z: bool = False):
+    n = L.n
+    if out is None:
+        out = _colmajor_empty(n, nsamples, ctx.device)
+    Z = _colmajor_empty(n, nsamples, ctx.device) if return_z else None
+    ld = out.stride(1)
+    if Z is not None and Z.stride(1) != ld:
+        raise ValueError("Y and Z must share a leading dimension")
+    ctx._check(ctx.lib.emu_sample(ctx.h, L.h, nsamples, seed, stream_id, ctypes.c_void_p(_ptr(out)), ld,
+                                  ctypes.c_void_p(_ptr(Z))), "emu_sample")
+    return (out, Z) if return_z else out
+
+
+def emu_sample_host(ctx: Context, L: Mat, nsamples: int, seed: int, stream_id: int = 0, out=None):
+    """Samples into a (pinned) host buffer; out: numpy float64 (n x s), Fortran order."""
+    n = L.n
+    if out is None:
+        out = np.empty((n, nsamples), dtype=np.float64, order="F")
+    ctx._check(ctx.lib.emu_sample_host(ctx.h, L.h, nsamples, seed, stream_id,
+                                       ctypes.c_void_p(out.ctypes.data), n), "emu_sample_host")
+    return out
+
+
+def emu_potrs(ctx: Context, L: Mat, B, out=None):
+    n, r = B.shape
+    if B.stride() != (1, n):
+        B = B.t().contiguous().t()
+    if out is None:
+        out = _colmajor_empty(n, r, ctx.device)
+    ctx._check(ctx.lib.emu_potrs(ctx.h, L.h, ctypes.c_void_p(_ptr(B)), n, ctypes.c_void_p(_ptr(out)),
+                                 out.stride(1), r), "emu_potrs")
+    return out
+
+
+@dataclass
+class RefineInfo:
+    status: int
+    iters: int
+    rel_resid: float
+    ms: float
+
+
+def emu_solve_refine(ctx: Context, L: Mat, S: Mat, B, tol: float = 1e-14, maxit: int = 50, out=None,
+                     raise_on_error: bool = True):
+    n, r = B.shape
+    if B.stride() != (1, n):
+        B = B.t().contiguous().t()
+    if out is None:
+        out = _colmajor_empty(n, r, ctx.device)
+    info = emu_refine_info()
+    s = ctx.lib.emu_solve_refine(ctx.h, L.h, S.h, ctypes.c_void_p(_ptr(B)), n, ctypes.c_void_p(_ptr(out)),
+                                 out.stride(1), r, tol, maxit, ctypes.byref(info))
+    ri = RefineInfo(s, info.iters, info.rel_resid, info.ms)
+    if raise_on_error and s != EMU_OK:
+        ctx._check(s, "emu_solve_refine")
+    return out, ri

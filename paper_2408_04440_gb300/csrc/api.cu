@@ -1,0 +1,417 @@
+// api.cu -- the C ABI of libemucov: context and matrix lifetime, argument
+// checks, and the host-side order of kernel launches (the tile-DAG schedule
+// of the factor, sampling, solves).  See include/emucov.h for the contract.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "emu_internal.h"
+#include "mixed.h"
+
+emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what) {
+  if (ctx) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    ctx->last_error = buf;
+  }
+  return EMU_ECUDA;
+}
+
+static emu_status fail_msg(emu_ctx *ctx, emu_status s, const char *msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+extern "C" {
+
+const char *emu_status_str(emu_status s) {
+  switch (s) {
+    case EMU_OK: return "ok";
+    case EMU_EINVAL: return "invalid argument";
+    case EMU_ENOMEM: return "out of device memory or size limit exceeded";
+    case EMU_ENOTPD: return "matrix not positive definite";
+    case EMU_ENOCONV: return "refinement did not converge";
+    case EMU_ETIMEOUT: return "device wait timed out";
+    case EMU_ECUDA: return "CUDA error";
+    case EMU_ESTATE: return "matrix in wrong state";
+  }
+  return "unknown status";
+}
+
+const char *emu_last_error(const emu_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+uint64_t emu_launch_count(const emu_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+emu_status emu_create(emu_ctx **out, int device, void *stream) {
+  if (!out) return EMU_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return EMU_EINVAL;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return EMU_ECUDA;
+  if (p.major != 10 || p.minor != 3) return EMU_EINVAL;  // sm_103 only
+  emu_ctx *ctx = new (std::nothrow) emu_ctx();
+  if (!ctx) return EMU_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->sm_count = p.multiProcessorCount;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, ST_WORDS * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, ST_WORDS * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, ST_WORDS * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e != cudaSuccess) {
+    emu_destroy(ctx);
+    return EMU_ECUDA;
+  }
+  *out = ctx;
+  return EMU_OK;
+}
+
+emu_status emu_destroy(emu_ctx *ctx) {
+  if (!ctx) return EMU_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  mixed_ctx_release(ctx);
+  delete ctx;
+  return EMU_OK;
+}
+
+emu_status emu_set_stream(emu_ctx *ctx, void *stream) {
+  if (!ctx) return EMU_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return EMU_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- matrices
+static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out) {
+  if (!ctx || !out || n <= 0 || nb < 64 || nb > 2048 || (nb % 64) != 0)
+    return fail_msg(ctx, EMU_EINVAL, "need n > 0 and nb a multiple of 64 in [64, 2048]");
+  *out = nullptr;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  emu_mat *A = new (std::nothrow) emu_mat();
+  if (!A) return EMU_ENOMEM;
+  A->ctx = ctx;
+  A->n = n;
+  A->nb = nb;
+  A->nt = (n + nb - 1) / nb;
+  A->ntiles = tile_count(A->nt);
+  A->tile_elems = (size_t)nb * nb;
+  A->nchunk = nb / 32;
+  size_t bytes64 = (size_t)A->ntiles * A->tile_elems * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  if (bytes64 + (64u << 20) > free_b) {
+    delete A;
+    return fail_msg(ctx, EMU_ENOMEM, "FP64 tile arena does not fit in free device memory");
+  }
+  cudaError_t e = cudaMalloc(&A->t64, bytes64);
+  if (e == cudaSuccess) e = cudaMalloc(&A->d_partial, (size_t)A->ntiles * A->nchunk * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&A->d_tnorm, (size_t)A->ntiles * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&A->d_frob, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&A->d_cls, (size_t)A->ntiles);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->d_cls, 0, (size_t)A->ntiles, ctx->stream);
+  if (e != cudaSuccess) {
+    emu_mat_free(A);
+    return e == cudaErrorMemoryAllocation ? EMU_ENOMEM : emu_cuda_fail(ctx, e, "mat_alloc");
+  }
+  A->h_cls = new (std::nothrow) unsigned char[A->ntiles];
+  if (!A->h_cls) {
+    emu_mat_free(A);
+    return EMU_ENOMEM;
+  }
+  memset(A->h_cls, 0, A->ntiles);
+  *out = A;
+  return EMU_OK;
+}
+
+extern "C" {
+
+emu_status emu_mat_free(emu_mat *A) {
+  if (!A) return EMU_EINVAL;
+  if (A->ctx) cudaSetDevice(A->ctx->device);
+  cudaFree(A->t64);
+  cudaFree(A->t32);
+  cudaFree(A->d_partial);
+  cudaFree(A->d_tnorm);
+  cudaFree(A->d_frob);
+  cudaFree(A->d_cls);
+  cudaFree(A->op_bf16);
+  delete[] A->h_cls;
+  delete A;
+  return EMU_OK;
+}
+
+emu_status emu_cov_build(emu_ctx *ctx, const emu_cov_params *p, int nb, emu_mat **out) {
+  if (!ctx || !p || !out) return EMU_EINVAL;
+  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel >= 0.0))
+    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, nugget_rel >= 0");
+  emu_mat *A = nullptr;
+  emu_status s = mat_alloc(ctx, p->L * p->L, nb, &A);
+  if (s != EMU_OK) return s;
+  s = launch_cov_build(ctx, A, p);
+  if (s != EMU_OK) {
+    emu_mat_free(A);
+    return s;
+  }
+  *out = A;
+  return EMU_OK;
+}
+
+emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda, int nb,
+                          emu_mat **out) {
+  if (!ctx || !dA || !out || lda < n) return EMU_EINVAL;
+  emu_mat *A = nullptr;
+  emu_status s = mat_alloc(ctx, n, nb, &A);
+  if (s != EMU_OK) return s;
+  s = launch_import(ctx, A, dA, lda);
+  if (s != EMU_OK) {
+    emu_mat_free(A);
+    return s;
+  }
+  *out = A;
+  return EMU_OK;
+}
+
+emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out) {
+  if (!ctx || !A || !out) return EMU_EINVAL;
+  if (A->state != MAT_COV) return fail_msg(ctx, EMU_ESTATE, "clone supports covariance matrices");
+  emu_mat *B = nullptr;
+  emu_status s = mat_alloc(ctx, A->n, A->nb, &B);
+  if (s != EMU_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(B->t64, A->t64, (size_t)A->ntiles * A->tile_elems * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_partial, A->d_partial, (size_t)A->ntiles * A->nchunk * sizeof(double),
+                        cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_tnorm, A->d_tnorm, (size_t)A->ntiles * sizeof(double),
+                        cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_frob, A->d_frob, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    emu_mat_free(B);
+    return emu_cuda_fail(ctx, e, "clone");
+  }
+  *out = B;
+  return EMU_OK;
+}
+
+emu_status emu_mat_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld) {
+  if (!ctx || !A || !dOut || ld < A->n) return EMU_EINVAL;
+  return launch_export(ctx, A, dOut, ld);
+}
+
+emu_status emu_mat_tile_info(emu_ctx *ctx, const emu_mat *A, unsigned char *h_cls,
+                             double *h_norms) {
+  if (!ctx || !A) return EMU_EINVAL;
+  int NT = A->nt;
+  unsigned char *cls = new (std::nothrow) unsigned char[A->ntiles];
+  double *tn = new (std::nothrow) double[A->ntiles];
+  if (!cls || !tn) {
+    delete[] cls;
+    delete[] tn;
+    return EMU_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(cls, A->d_cls, A->ntiles, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tn, A->d_tnorm, A->ntiles * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    delete[] cls;
+    delete[] tn;
+    return emu_cuda_fail(ctx, e, "tile_info");
+  }
+  for (int j = 0; j < NT; j++)
+    for (int i = 0; i < NT; i++) {
+      size_t o = (size_t)i + (size_t)j * NT;
+      if (i < j) {
+        if (h_cls) h_cls[o] = 255;
+        if (h_norms) h_norms[o] = 0.0;
+      } else {
+        long t = tile_index(i, j, NT);
+        if (h_cls) h_cls[o] = cls[t];
+        if (h_norms) h_norms[o] = tn[t];
+      }
+    }
+  delete[] cls;
+  delete[] tn;
+  return EMU_OK;
+}
+
+emu_status emu_mat_shape(const emu_mat *A, int *n, int *nb, int *nt, int *state) {
+  if (!A) return EMU_EINVAL;
+  if (n) *n = A->n;
+  if (nb) *nb = A->nb;
+  if (nt) *nt = A->nt;
+  if (state) *state = A->state;
+  return EMU_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ factor
+// Reads the device status word after the stream drains.
+static emu_status collect_status(emu_ctx *ctx, int *pivot) {
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(int),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (pivot) *pivot = ctx->h_status[ST_PIVOT];
+  if (ctx->h_status[ST_CODE] == DEV_NOTPD) return EMU_ENOTPD;
+  if (ctx->h_status[ST_CODE] == DEV_TIMEOUT) return fail_msg(ctx, EMU_ETIMEOUT, "device wait timed out");
+  return EMU_OK;
+}
+
+// Plain FP64 right-looking tile Cholesky: POTRF(k), TRSM(:,k), SYRK/GEMM of
+// the trailing tiles, k = 0 .. NT-1.
+static emu_status factor64(emu_ctx *ctx, emu_mat *A) {
+  for (int k = 0; k < A->nt; k++) {
+    emu_status s = launch_potrf64_tile(ctx, A, k);
+    if (s == EMU_OK) s = launch_trsm64_panel(ctx, A, k);
+    if (s == EMU_OK) s = launch_update64(ctx, A, k);
+    if (s != EMU_OK) return s;
+  }
+  return launch_tril_diag(ctx, A);
+}
+
+extern "C" emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o,
+                                   emu_factor_info *info) {
+  if (!ctx || !A) return EMU_EINVAL;
+  if (A->state != MAT_COV) return fail_msg(ctx, EMU_ESTATE, "matrix is already factored");
+  bool mixed = o && o->eps > 0.0;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+  emu_status s;
+  if (mixed) {
+    s = factor_mixed(ctx, A, o);
+  } else {
+    s = factor64(ctx, A);
+  }
+  if (s != EMU_OK) return s;
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+  int pivot = 0;
+  s = collect_status(ctx, &pivot);
+  A->state = mixed ? MAT_FACTOR_MIXED : MAT_FACTOR64;
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->n = A->n;
+    info->nb = A->nb;
+    info->nt = A->nt;
+    info->pivot = (s == EMU_ENOTPD) ? pivot : 0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    info->ms = ms;
+    double nb3 = (double)A->nb * A->nb * A->nb;
+    if (mixed) {
+      mixed_fill_info(A, info);
+    } else {
+      info->tiles[EMU_CLASS_FP64] = (int)A->ntiles;
+      int NT = A->nt;
+      double f = 0.0;
+      for (int j = 0; j < NT; j++) f += (double)(NT - j - 1) * nb3 + (double)(NT - j - 1) * (NT - j) * nb3;
+      info->update_flops[EMU_CLASS_FP64] = f;
+    }
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- sampling
+extern "C" emu_status emu_sample(emu_ctx *ctx, const emu_mat *L, int nsamples, uint64_t seed,
+                                 uint32_t stream_id, double *dY, long ldy, double *dZ) {
+  if (!ctx || !L || !dY || nsamples < 0 || ldy < L->n) return EMU_EINVAL;
+  if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
+    return fail_msg(ctx, EMU_ESTATE, "sampling needs a factored matrix");
+  if (nsamples == 0) return EMU_OK;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  long npad = (long)L->nt * L->nb;
+  double *Z = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&Z, (size_t)npad * nsamples * sizeof(double), ctx->stream));
+  emu_status s = launch_normals(ctx, seed, stream_id, (int)npad, nsamples, Z, npad);
+  if (s == EMU_OK) {
+    if (L->state == MAT_FACTOR64)
+      s = launch_trmm64(ctx, L, Z, npad, nsamples, dY, ldy);
+    else
+      s = mixed_sample(ctx, L, Z, npad, nsamples, dY, ldy);
+  }
+  if (s == EMU_OK && dZ) {
+    cudaError_t e = cudaMemcpy2DAsync(dZ, ldy * sizeof(double), Z, npad * sizeof(double),
+                                      (size_t)L->n * sizeof(double), nsamples,
+                                      cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "copy Z");
+  }
+  cudaFreeAsync(Z, ctx->stream);
+  return s;
+}
+
+extern "C" emu_status emu_sample_host(emu_ctx *ctx, const emu_mat *L, int nsamples, uint64_t seed,
+                                      uint32_t stream_id, double *hY, long ldy) {
+  if (!ctx || !L || !hY || nsamples < 0 || ldy < L->n) return EMU_EINVAL;
+  if (nsamples == 0) return EMU_OK;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  double *Y = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&Y, (size_t)L->n * nsamples * sizeof(double), ctx->stream));
+  emu_status s = emu_sample(ctx, L, nsamples, seed, stream_id, Y, L->n, nullptr);
+  if (s == EMU_OK) {
+    cudaError_t e = cudaMemcpy2DAsync(hY, ldy * sizeof(double), Y, (size_t)L->n * sizeof(double),
+                                      (size_t)L->n * sizeof(double), nsamples,
+                                      cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "copy Y to host");
+  }
+  cudaFreeAsync(Y, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return s;
+}
+
+// ------------------------------------------------------------------ solves
+// Copies B (n rows) into a zero-padded npad-row buffer, solves there.
+static emu_status potrs_padded(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs) {
+  if (L->state == MAT_FACTOR64) return launch_potrs64(ctx, L, X, ldx, nrhs);
+  return mixed_potrs(ctx, L, X, ldx, nrhs);
+}
+
+extern "C" emu_status emu_potrs(emu_ctx *ctx, const emu_mat *L, const double *dB, long ldb,
+                                double *dX, long ldx, int nrhs) {
+  if (!ctx || !L || !dB || !dX || nrhs < 0 || ldb < L->n || ldx < L->n) return EMU_EINVAL;
+  if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
+    return fail_msg(ctx, EMU_ESTATE, "solve needs a factored matrix");
+  if (nrhs == 0) return EMU_OK;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  long npad = (long)L->nt * L->nb;
+  double *W = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&W, (size_t)npad * nrhs * sizeof(double), ctx->stream));
+  cudaError_t e = cudaMemsetAsync(W, 0, (size_t)npad * nrhs * sizeof(double), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(W, npad * sizeof(double), dB, ldb * sizeof(double),
+                          (size_t)L->n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, ctx->stream);
+  emu_status s = (e == cudaSuccess) ? potrs_padded(ctx, L, W, npad, nrhs) : emu_cuda_fail(ctx, e, "potrs copy-in");
+  if (s == EMU_OK) {
+    e = cudaMemcpy2DAsync(dX, ldx * sizeof(double), W, npad * sizeof(double),
+                          (size_t)L->n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "potrs copy-out");
+  }
+  cudaFreeAsync(W, ctx->stream);
+  return s;
+}
+
+extern "C" emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu_mat *S,
+                                       const double *dB, long ldb, double *dX, long ldx, int nrhs,
+                                       double tol, int maxit, emu_refine_info *info) {
+  if (!ctx || !L || !S || !dB || !dX || nrhs < 0 || ldb < L->n || ldx < L->n || maxit < 0 ||
+      !(tol > 0.0))
+    return EMU_EINVAL;
+  if (S->state != MAT_COV || S->n != L->n || S->nb != L->nb)
+    return fail_msg(ctx, EMU_ESTATE, "S must be the unfactored covariance with the factor's tiling");
+  if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
+    return fail_msg(ctx, EMU_ESTATE, "refinement needs a factored matrix");
+  return refine_solve(ctx, L, S, dB, ldb, dX, ldx, nrhs, tol, maxit, info);
+}

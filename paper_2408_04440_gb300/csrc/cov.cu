@@ -1,0 +1,269 @@
+// cov.cu -- covariance build / import into packed FP64 tiles, the fused
+// per-tile Frobenius-norm pass, the precision map, and export to dense.
+//
+// Covariance: synthetic stand-in for U-hat ("Modeling the Temporal Dependence
+// and Constructing a Covariance Matrix", equation for U-hat and the diagonal
+// perturbation that keeps it positive definite).  The correlation exp(-d/beta)
+// depends only on (l_i - l_j, m_i - m_j), so it is evaluated once per offset
+// into a table; every entry is then s(l_i) * s(l_j) * rho(dl, dm) -- the same
+// operations, in the same order, as evaluating the formula entry by entry.
+#include "emu_internal.h"
+
+namespace {
+
+constexpr int kChunk = 32;     // columns of a tile handled by one CTA
+constexpr int kThreads = 256;
+
+// Degree l of coefficient row k (k = l^2 + l + m): floor(sqrt(k)), from a
+// single-precision estimate corrected in integer arithmetic.
+__device__ inline int degree_of(long k) {
+  int l = (int)sqrtf((float)k);
+  while ((long)l * l > k) l--;
+  while ((long)(l + 1) * (l + 1) <= k) l++;
+  return l;
+}
+
+// sigma[l] = (1 + l)^(-sexp); rho[(dl + L - 1) * W + (dm + 2L - 2)] =
+// exp(-sqrt(dl^2 + dm^2) / beta), W = 4L - 3; out[0] = nugget added to
+// the diagonal = nugget_rel * max_l sigma[l]^2.
+__global__ void k_cov_tables(int L, double beta, double sexp, double nugget_rel,
+                             double *sigma, double *rho, double *nugget) {
+  int W = 4 * L - 3;
+  long total = (long)(2 * L - 1) * W;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x) {
+    int a = (int)(t / W), b = (int)(t % W);
+    double dl = (double)(a - (L - 1)), dm = (double)(b - (2 * L - 2));
+    double d = sqrt(dl * dl + dm * dm);
+    rho[t] = exp(-d / beta);
+  }
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L;
+       l += gridDim.x * blockDim.x)
+    sigma[l] = pow(1.0 + l, -sexp);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double dmax = 0.0;
+    for (int l = 0; l < L; l++) {
+      double s = pow(1.0 + l, -sexp);
+      double v = s * s * 1.0;  // rho(0, 0) = exp(0) = 1
+      if (v > dmax) dmax = v;
+    }
+    *nugget = nugget_rel * dmax;
+  }
+}
+
+// Deterministic block reduction of one double per thread (fixed tree).
+__device__ inline double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) r += sh[i];
+  }
+  __syncthreads();
+  return r;
+}
+
+// One CTA per (tile, 32-column chunk): blockIdx.x = tile, blockIdx.y = chunk.  Writes the tile's chunk (padded
+// entries: unit diagonal, zeros elsewhere) and the chunk's sum of squares
+// over the real (unpadded) entries of the full symmetric tile.
+__global__ void __launch_bounds__(kThreads)
+    k_cov_build(int L, int n, int nb, int NT, const double *__restrict__ sigma,
+                const double *__restrict__ rho, const double *__restrict__ nugget,
+                double *__restrict__ t64, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  int W = 4 * L - 3;
+  double nug = *nugget;
+  double *tile = t64 + (size_t)t * nb * nb;
+  double ss = 0.0;
+  for (int cc = 0; cc < kChunk; cc++) {
+    int c = blockIdx.y * kChunk + cc;
+    long gj = (long)tj * nb + c;
+    int lj = 0, mj = 0;
+    if (gj < n) {
+      lj = degree_of(gj);
+      mj = (int)(gj - (long)lj * lj - lj);
+    }
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      long gi = (long)ti * nb + r;
+      double v;
+      if (gi < n && gj < n) {
+        int li = degree_of(gi);
+        int mi = (int)(gi - (long)li * li - li);
+        double e = rho[(long)(li - lj + L - 1) * W + (mi - mj + 2 * L - 2)];
+        v = __dmul_rn(__dmul_rn(sigma[li], sigma[lj]), e);  // no FMA contraction
+        if (gi == gj) v = __dadd_rn(v, nug);
+        ss += v * v;
+      } else {
+        v = (gi == gj) ? 1.0 : 0.0;
+      }
+      tile[r + (size_t)c * nb] = v;
+    }
+  }
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
+// Same layout from a dense, column-major, lower-triangle user matrix.
+__global__ void __launch_bounds__(kThreads)
+    k_import(int n, int nb, int NT, const double *__restrict__ A, long lda,
+             double *__restrict__ t64, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  double *tile = t64 + (size_t)t * nb * nb;
+  double ss = 0.0;
+  for (int cc = 0; cc < kChunk; cc++) {
+    int c = blockIdx.y * kChunk + cc;
+    long gj = (long)tj * nb + c;
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      long gi = (long)ti * nb + r;
+      double v;
+      if (gi < n && gj < n) {
+        v = (gi >= gj) ? A[gi + gj * lda] : A[gj + gi * lda];
+        ss += v * v;
+      } else {
+        v = (gi == gj) ? 1.0 : 0.0;
+      }
+      tile[r + (size_t)c * nb] = v;
+    }
+  }
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
+// Single CTA: tile norms from the partial sums (fixed order), ||S||_F, and
+// the class of each tile under the rule t_ij * u[c] <= eps * ||S||_F / NT.
+__global__ void __launch_bounds__(1024)
+    k_precision_map(int NT, long ntiles, int nchunk,
+                    const double *__restrict__ partial, double *__restrict__ tnorm,
+                    double *__restrict__ frob, unsigned char *__restrict__ cls,
+                    double eps, double u1, double u2, double u3, double u4,
+                    unsigned mask, int diag_fp64) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunk; c++) s += partial[t * nchunk + c];
+    double tn = sqrt(s);
+    tnorm[t] = tn;
+    int i, j;
+    tile_coords(t, NT, &i, &j);
+    acc += (i == j ? 1.0 : 2.0) * tn * tn;
+  }
+  double tot = block_sum(acc, sh);
+  __shared__ double s_frob;
+  if (threadIdx.x == 0) {
+    s_frob = sqrt(tot);
+    *frob = s_frob;
+  }
+  __syncthreads();
+  if (cls == nullptr) return;
+  double thr = eps * s_frob / (double)NT;
+  const double uu[EMU_NCLASS] = {0.0, u1, u2, u3, u4};
+  for (long t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    int i, j;
+    tile_coords(t, NT, &i, &j);
+    int c = 0;
+    if (!(diag_fp64 && i == j)) {
+      double tn = tnorm[t];
+      for (int cc = EMU_NCLASS - 1; cc >= 1; cc--) {
+        if (((mask >> cc) & 1u) && tn * uu[cc] <= thr) {
+          c = cc;
+          break;
+        }
+      }
+    }
+    cls[t] = (unsigned char)c;
+  }
+}
+
+// Dense FP64 lower triangle from the tiles.  grid.x enumerates all NT*NT tile
+// pairs; upper tiles and the strict upper part of diagonal tiles become 0.
+// Low-precision off-diagonal tiles of a mixed factor come from the FP32
+// master arena.
+__global__ void __launch_bounds__(kThreads)
+    k_export(int n, int nb, int NT, const double *__restrict__ t64,
+             const float *__restrict__ t32, const unsigned char *__restrict__ cls,
+             double *__restrict__ out, long ld) {
+  int ti = blockIdx.x % NT, tj = blockIdx.x / NT;
+  const double *tile = nullptr;
+  const float *tile32 = nullptr;
+  if (ti >= tj) {
+    long t = tile_index(ti, tj, NT);
+    if (t32 != nullptr && cls != nullptr && ti != tj && cls[t] != EMU_CLASS_FP64)
+      tile32 = t32 + (size_t)t * nb * nb;
+    else
+      tile = t64 + (size_t)t * nb * nb;
+  }
+  for (int cc = 0; cc < kChunk; cc++) {
+    int c = blockIdx.y * kChunk + cc;
+    long gj = (long)tj * nb + c;
+    if (gj >= n) break;
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      long gi = (long)ti * nb + r;
+      if (gi >= n) break;
+      double v = 0.0;
+      if (gi >= gj) {
+        if (tile32) v = (double)tile32[r + (size_t)c * nb];
+        else if (tile) v = tile[r + (size_t)c * nb];
+      }
+      out[gi + gj * ld] = v;
+    }
+  }
+}
+
+}  // namespace
+
+emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p) {
+  int L = p->L;
+  size_t ntab = (size_t)(2 * L - 1) * (4 * L - 3);
+  double *buf = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&buf, (ntab + L + 1) * sizeof(double), ctx->stream));
+  double *rho = buf, *sigma = buf + ntab, *nug = buf + ntab + L;
+  int blocks = (int)((ntab + 255) / 256);
+  if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
+  k_cov_tables<<<blocks, 256, 0, ctx->stream>>>(L, p->beta, p->sigma_exp, p->nugget_rel,
+                                               sigma, rho, nug);
+  EMU_LAUNCHED(ctx);
+  dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+  k_cov_build<<<grid, kThreads, 0, ctx->stream>>>(L, A->n, A->nb, A->nt, sigma, rho, nug,
+                                                 A->t64, A->d_partial);
+  EMU_LAUNCHED(ctx);
+  EMU_CUDA_TRY(ctx, cudaFreeAsync(buf, ctx->stream));
+  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+}
+
+emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {
+  dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+  k_import<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, dA, lda, A->t64,
+                                              A->d_partial);
+  EMU_LAUNCHED(ctx);
+  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+}
+
+// With u == nullptr only the norms and ||S||_F are (re)computed.
+emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
+                                const double *u, unsigned mask, int diag_fp64) {
+  k_precision_map<<<1, 1024, 0, ctx->stream>>>(
+      A->nt, A->ntiles, A->nchunk, A->d_partial, A->d_tnorm, A->d_frob,
+      u ? A->d_cls : nullptr, eps, u ? u[1] : 0.0, u ? u[2] : 0.0,
+      u ? u[3] : 0.0, u ? u[4] : 0.0, mask, diag_fp64);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld) {
+  dim3 grid((unsigned)(A->nt * A->nt), A->nb / kChunk);
+  bool mixed = A->state == MAT_FACTOR_MIXED;
+  k_export<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, A->t64,
+                                              mixed ? A->t32 : nullptr,
+                                              mixed ? A->d_cls : nullptr, dOut, ld);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}

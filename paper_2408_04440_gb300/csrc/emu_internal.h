@@ -1,0 +1,102 @@
+// emu_internal.h -- internal types shared by the CUDA translation units of
+// libemucov (context, tiled matrix, tile indexing, launch bookkeeping).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/emucov.h"
+
+// ----------------------------------------------------------------- tiling
+// Lower tiles (i >= j) of an NT x NT tiling are packed column by column:
+// tile (i, j) has index j*NT - j*(j-1)/2 + (i - j).  Each tile is nb x nb,
+// column-major (element (r, c) at r + c*nb).
+__host__ __device__ inline long tile_index(int i, int j, int NT) {
+  return (long)j * NT - (long)j * (j - 1) / 2 + (i - j);
+}
+__host__ __device__ inline void tile_coords(long t, int NT, int *i, int *j) {
+  int jj = 0;
+  long base = 0;
+  while (base + (NT - jj) <= t) {
+    base += NT - jj;
+    jj++;
+  }
+  *j = jj;
+  *i = jj + (int)(t - base);
+}
+inline long tile_count(int NT) { return (long)NT * (NT + 1) / 2; }
+
+// Device status word written by kernels and read back at sync points.
+enum { ST_CODE = 0, ST_PIVOT = 1, ST_AUX = 2, ST_WORDS = 4 };
+enum { DEV_OK = 0, DEV_NOTPD = 1, DEV_TIMEOUT = 2 };
+
+// Matrix states.
+enum { MAT_COV = 0, MAT_FACTOR64 = 1, MAT_FACTOR_MIXED = 2 };
+
+struct emu_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int *d_status = nullptr;    // ST_WORDS ints
+  int *h_status = nullptr;    // pinned mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint64_t launches = 0;
+  std::string last_error;
+};
+
+struct emu_mat {
+  emu_ctx *ctx = nullptr;
+  int n = 0, nb = 0, nt = 0;
+  int state = MAT_COV;
+  long ntiles = 0;
+  size_t tile_elems = 0;       // nb*nb
+  double *t64 = nullptr;       // FP64 arena: ntiles tiles
+  float *t32 = nullptr;        // FP32 master arena (mixed factor), ntiles tiles
+  // norm pass: per-tile partial sums of squares, tile norms, classes
+  int nchunk = 0;              // column chunks per tile (nb / 32)
+  double *d_partial = nullptr; // ntiles * nchunk
+  double *d_tnorm = nullptr;   // ntiles
+  double *d_frob = nullptr;    // 1
+  unsigned char *d_cls = nullptr; // ntiles
+  unsigned char *h_cls = nullptr; // ntiles (host copy, valid for mixed)
+  double frob = 0.0;
+  // mixed factor operand copies (three BF16 pieces per tile, row-major)
+  uint16_t *op_bf16 = nullptr; // ntiles * 3 * nb*nb
+};
+
+// ------------------------------------------------------------- bookkeeping
+emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what);
+#define EMU_CUDA_TRY(ctx, expr)                                   \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return emu_cuda_fail((ctx), _e, #expr); \
+  } while (0)
+// After a launch: count it and surface launch-configuration errors.
+#define EMU_LAUNCHED(ctx)                                                   \
+  do {                                                                      \
+    (ctx)->launches++;                                                      \
+    cudaError_t _e = cudaGetLastError();                                    \
+    if (_e != cudaSuccess) return emu_cuda_fail((ctx), _e, "kernel launch"); \
+  } while (0)
+
+// Kernel launch wrappers (defined in the .cu files that own the kernels).
+// cov.cu
+emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
+emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda);
+emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
+                                const double *u, unsigned mask, int diag_fp64);
+emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
+// fp64.cu
+emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
+emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k);
+emu_status launch_update64(emu_ctx *ctx, emu_mat *A, int k);
+emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A);
+emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z,
+                         long ldz, int s, double *Y, long ldy);
+emu_status launch_potrs64(emu_ctx *ctx, const emu_mat *L, double *X, long ldx,
+                          int nrhs);
+// rng.cu
+emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id,
+                          int nrows, int s, double *Z, long ldz);

@@ -1,0 +1,65 @@
+// rng.cu -- standard normals z ~ N(0, I) for drawing emulations
+// ("Generating Emulations": xi = V z).  Counter-based, so every entry depends
+// only on (seed, stream id, row, column) and never on the launch shape:
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) at counter
+// {p mod 2^32, p >> 32, column, stream id}, key {seed mod 2^32, seed >> 32},
+// p = row / 2; two 53-bit uniforms u1 in (0,1], u2 in [0,1); Box-Muller gives
+// rows 2p (cosine) and 2p+1 (sine).
+#include "emu_internal.h"
+
+namespace {
+
+__device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+__global__ void k_normals(uint64_t seed, uint32_t stream_id, int nrows, int s,
+                          double *__restrict__ Z, long ldz) {
+  long npairs = (nrows + 1) / 2;
+  long total = npairs * s;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+       q += (long)gridDim.x * blockDim.x) {
+    long p = q % npairs;
+    int col = (int)(q / npairs);
+    uint32_t c[4] = {(uint32_t)((uint64_t)p & 0xffffffffu), (uint32_t)((uint64_t)p >> 32),
+                     (uint32_t)col, stream_id};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    uint64_t a = ((uint64_t)c[0] << 21) | (uint64_t)(c[1] >> 11);
+    uint64_t b = ((uint64_t)c[2] << 21) | (uint64_t)(c[3] >> 11);
+    double u1 = ((double)a + 1.0) * 0x1.0p-53;
+    double u2 = (double)b * 0x1.0p-53;
+    double rad = sqrt(-2.0 * log(u1));
+    double th = two_pi * u2;
+    double *z = Z + (size_t)col * ldz + 2 * p;
+    z[0] = rad * cos(th);
+    if (2 * p + 1 < nrows) z[1] = rad * sin(th);
+  }
+}
+
+}  // namespace
+
+emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id, int nrows,
+                          int s, double *Z, long ldz) {
+  long total = (long)((nrows + 1) / 2) * s;
+  long blocks = (total + 255) / 256;
+  if (blocks > 8L * ctx->sm_count) blocks = 8L * ctx->sm_count;
+  if (blocks < 1) blocks = 1;
+  k_normals<<<(unsigned)blocks, 256, 0, ctx->stream>>>(seed, stream_id, nrows, s, Z, ldz);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}

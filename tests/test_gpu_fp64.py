@@ -1,0 +1,159 @@
+"""Parity of the plain FP64 GPU path with the CPU oracle, through the C ABI:
+covariance build, tile norms, FP64 tile Cholesky (<= 1e-12 relative), the
+sampler (Y = L Z) and the solves.  Sizes span several tiles and a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import paper_2408_04440_gb300 as E
+    from paper_2408_04440_gb300 import build
+
+    build.build()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(E):
+    c = E.Context(0)
+    yield c
+    c.close()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("L,nb,beta", [(8, 64, 4.0), (12, 64, 3.0), (20, 128, 4.0), (32, 128, 4.0)])
+def test_cov_build_and_norms(E, ctx, L, nb, beta):
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    S = O.cov_build(L, beta)
+    G = _np(E.emu_mat_export(ctx, A))
+    ref = np.tril(S)
+    assert np.max(np.abs(G - ref)) <= 4e-16 * np.max(np.abs(ref))
+    cls, tn = E.emu_mat_tile_info(ctx, A)
+    t_ref = O.tile_norms(S, nb)
+    assert np.allclose(tn, t_ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("L,nb,beta", [(8, 64, 4.0), (12, 64, 3.0), (20, 128, 4.0), (32, 128, 4.0)])
+def test_fp64_factor_matches_oracle(E, ctx, L, nb, beta):
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A)
+    assert info.status == E.EMU_OK and info.pivot == 0
+    G = _np(E.emu_mat_export(ctx, A))
+    Lo, oinfo = O.potrf_blocked(O.cov_build(L, beta), nb)
+    assert oinfo == 0
+    rel = np.linalg.norm(G - Lo) / np.linalg.norm(Lo)
+    assert rel <= 1e-12, rel
+    assert np.all(np.triu(G, 1) == 0)
+
+
+def test_fp64_factor_of_imported_matrix(E, ctx):
+    import torch
+
+    rng = np.random.default_rng(11)
+    n = 200  # ragged with nb = 64
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    S = (Q * np.logspace(0, -6, n)) @ Q.T
+    S = 0.5 * (S + S.T)
+    A = E.emu_mat_import(ctx, torch.from_numpy(S).cuda(), 64)
+    E.emu_potrf_mp(ctx, A)
+    G = _np(E.emu_mat_export(ctx, A))
+    Lo, _ = O.potrf_blocked(S, 64)
+    assert np.linalg.norm(G - Lo) / np.linalg.norm(Lo) <= 1e-12
+
+
+@pytest.mark.parametrize("bad", [1, 70, 199])
+def test_not_positive_definite_reports_pivot(E, ctx, bad):
+    import torch
+
+    n = 200
+    S = np.eye(n)
+    S[bad - 1, bad - 1] = -1.0
+    A = E.emu_mat_import(ctx, torch.from_numpy(S).cuda(), 64)
+    info = E.emu_potrf_mp(ctx, A, raise_on_error=False)
+    assert info.status == E.EMU_ENOTPD
+    assert info.pivot == bad
+    # the context stays usable after the failure
+    B = E.emu_cov_build(ctx, 6, 2.0, 64)
+    assert E.emu_potrf_mp(ctx, B).status == E.EMU_OK
+
+
+@pytest.mark.parametrize("L,nb,s", [(12, 64, 5), (32, 128, 64)])
+def test_fp64_sampling(E, ctx, L, nb, s):
+    A = E.emu_cov_build(ctx, L, 4.0, nb)
+    E.emu_potrf_mp(ctx, A)
+    Y, Z = E.emu_sample(ctx, A, s, seed=0, return_z=True)
+    Zo = O.normal_matrix(0, 0, L * L, s)
+    Zg = _np(Z)
+    assert np.max(np.abs(Zg - Zo)) <= 1e-14 * np.max(np.abs(Zo))
+    Lo, _ = O.potrf_blocked(O.cov_build(L, 4.0), nb)
+    Yo = O.trmm_lower(Lo, Zo)
+    Yg = _np(Y)
+    assert np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo) <= 1e-12
+    # bit-identical on rerun
+    Y2 = _np(E.emu_sample(ctx, A, s, seed=0))
+    assert np.array_equal(Y2, Yg)
+    # a different seed or stream id gives different draws
+    assert not np.array_equal(_np(E.emu_sample(ctx, A, s, seed=1)), Yg)
+    assert not np.array_equal(_np(E.emu_sample(ctx, A, s, seed=0, stream_id=1)), Yg)
+
+
+def test_fp64_sampling_host_buffers(E, ctx):
+    A = E.emu_cov_build(ctx, 10, 3.0, 64)
+    E.emu_potrf_mp(ctx, A)
+    Yh = E.emu_sample_host(ctx, A, 7, seed=3)
+    Yd = _np(E.emu_sample(ctx, A, 7, seed=3))
+    assert np.array_equal(Yh, Yd)
+
+
+def test_fp64_solves(E, ctx):
+    import torch
+
+    L, nb = 16, 64
+    A = E.emu_cov_build(ctx, L, 4.0, nb)
+    S = E.emu_mat_clone(ctx, A)
+    E.emu_potrf_mp(ctx, A)
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((L * L, 3))
+    X = _np(E.emu_potrs(ctx, A, torch.from_numpy(B).cuda()))
+    So = O.cov_build(L, 4.0)
+    Lo, _ = O.potrf_blocked(So, nb)
+    Xo = O.potrs(Lo, B)
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-9
+    Xr, ri = E.emu_solve_refine(ctx, A, S, torch.from_numpy(B).cuda(), tol=1e-15, maxit=10)
+    assert ri.status == E.EMU_OK
+    Xr = _np(Xr)
+    eta = np.linalg.norm(B - So @ Xr, axis=0) / (np.linalg.norm(So) * np.linalg.norm(Xr, axis=0)
+                                                 + np.linalg.norm(B, axis=0))
+    assert eta.max() <= 1e-15
+
+
+def test_bad_arguments(E, ctx):
+    import ctypes
+
+    h = ctypes.c_void_p()
+    p = E.emu_cov_params(0, 1.0, 1.5, 1e-8)
+    assert ctx.lib.emu_cov_build(ctx.h, ctypes.byref(p), 64, ctypes.byref(h)) == E.EMU_EINVAL
+    p = E.emu_cov_params(8, 1.0, 1.5, 1e-8)
+    assert ctx.lib.emu_cov_build(ctx.h, ctypes.byref(p), 100, ctypes.byref(h)) == E.EMU_EINVAL
+    A = E.emu_cov_build(ctx, 8, 2.0, 64)
+    with pytest.raises(E.EmuError):
+        E.emu_sample(ctx, A, 4, seed=0)  # not factored yet: EMU_ESTATE
+    E.emu_potrf_mp(ctx, A)
+    with pytest.raises(E.EmuError):
+        E.emu_potrf_mp(ctx, A)  # already factored
+
+
+def test_launch_count_increases(E, ctx):
+    before = ctx.launch_count
+    A = E.emu_cov_build(ctx, 8, 2.0, 64)
+    E.emu_potrf_mp(ctx, A)
+    assert ctx.launch_count > before
