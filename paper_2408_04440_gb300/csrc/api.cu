@@ -145,6 +145,7 @@ emu_status emu_mat_free(emu_mat *A) {
   cudaFree(A->d_frob);
   cudaFree(A->d_cls);
   cudaFree(A->op_bf16);
+  mixed_mat_release(A);
   delete[] A->h_cls;
   delete A;
   return EMU_OK;

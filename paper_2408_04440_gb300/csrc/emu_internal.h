@@ -64,6 +64,7 @@ struct emu_mat {
   double frob = 0.0;
   // mixed factor operand copies (three BF16 pieces per tile, row-major)
   uint16_t *op_bf16 = nullptr; // ntiles * 3 * nb*nb
+  void *plan = nullptr;        // mixed-factor schedule (mixed.cu)
 };
 
 // ------------------------------------------------------------- bookkeeping
@@ -90,11 +91,15 @@ emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
-emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k);
+// d_rows: device list of the tile rows i > k to solve (nullptr: all of them)
+emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows = nullptr,
+                               int nrows = 0);
 emu_status launch_update64(emu_ctx *ctx, emu_mat *A, int k);
 emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A);
+// cls != nullptr: only the FP64-class tiles contribute (mixed factors)
 emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z,
-                         long ldz, int s, double *Y, long ldy);
+                         long ldz, int s, double *Y, long ldy,
+                         const unsigned char *cls = nullptr);
 emu_status launch_potrs64(emu_ctx *ctx, const emu_mat *L, double *X, long ldx,
                           int nrhs);
 // rng.cu

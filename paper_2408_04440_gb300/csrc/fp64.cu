@@ -113,12 +113,13 @@ __global__ void __launch_bounds__(256)
 // column blocks cb left to right: subtract the already-solved blocks
 // (GEMM part), then solve against the 32x32 diagonal block of L_kk.
 __global__ void __launch_bounds__(256)
-    k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *st) {
+    k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
+                   const int *st) {
   if (failed(st)) return;
   __shared__ double xp[B][B + 1];
   __shared__ double lc[B][B + 1];
   __shared__ double sx[B][B + 1];
-  int i = k + 1 + blockIdx.y;
+  int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
   int r0 = blockIdx.x * B;
   const double *Lkk = t64 + (size_t)tile_index(k, k, NT) * nb * nb;
   double *X = t64 + (size_t)tile_index(i, k, NT) * nb * nb + r0;  // row block
@@ -245,7 +246,7 @@ __global__ void k_tril_diag(double *__restrict__ t64, int nb, int NT) {
 __global__ void __launch_bounds__(256)
     k_trmm64(const double *__restrict__ t64, int n, int nb, int NT,
              const double *__restrict__ Z, long ldz, int s, double *__restrict__ Y,
-             long ldy) {
+             long ldy, const unsigned char *__restrict__ cls) {
   int nsub = nb / GM;
   int i = blockIdx.x / nsub, bi = blockIdx.x % nsub;
   int c0 = blockIdx.y * GM;
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(256)
   int zc = t / 4, zp = (t % 4) * 4;      // Z loader: sample zc, rows zp..zp+3
   double acc[4][4] = {};
   for (int k = 0; k <= i; k++) {
+    if (cls && cls[tile_index(i, k, NT)] != EMU_CLASS_FP64) continue;
     const double *Ai = t64 + (size_t)tile_index(i, k, NT) * nb * nb + bi * GM;
     for (int p0 = 0; p0 < nb; p0 += GK) {
 #pragma unroll
@@ -378,10 +380,10 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   return EMU_OK;
 }
 
-emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k) {
-  int m = A->nt - k - 1;
+emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows, int nrows) {
+  int m = d_rows ? nrows : A->nt - k - 1;
   if (m <= 0) return EMU_OK;
-  k_trsm64_panel<<<dim3(A->nb / B, m), 256, 0, ctx->stream>>>(A->t64, A->nb, A->nt, k,
+  k_trsm64_panel<<<dim3(A->nb / B, m), 256, 0, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
                                                              ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
@@ -405,9 +407,9 @@ emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A) {
 }
 
 emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z, long ldz,
-                         int s, double *Y, long ldy) {
+                         int s, double *Y, long ldy, const unsigned char *cls) {
   dim3 grid(L->nt * (L->nb / GM), (s + GM - 1) / GM);
-  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy);
+  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -1,0 +1,47 @@
+// gemm_tc.h -- host interface of the tcgen05 tile GEMM (gemm_tc.cu).
+//
+// One launch processes a list of output blocks ("items") of BM x BN.  Each
+// item accumulates, in a TMEM FP32 accumulator, the sum over its segments of
+// A_seg * B_seg^T, where A_seg (BM x nb) and B_seg (BN x nb) are K-major BF16
+// operand blocks fetched by TMA (three split pieces per operand for the FP32
+// class, one for BF16), then applies the epilogue:
+//   mode TC_SUB_F32: out32[off + r + c*ldo] -= acc   (trailing tile update)
+//   mode TC_ADD_F64: out64[off + r + c*ldo] += acc   (sampling, r/c bounded)
+#pragma once
+#include <cuda.h>
+
+#include "emu_internal.h"
+
+namespace gemm_tc {
+
+constexpr int BM = 128;   // rows of an output block (TMEM lanes)
+constexpr int BN = 256;   // columns of an output block (TMEM columns)
+constexpr int BK = 32;    // K per pipeline stage (BF16: 64 bytes, 64B swizzle)
+constexpr int STAGES = 3;
+constexpr int NPIECE = 3; // split pieces of an FP32-class operand
+
+enum { TC_SUB_F32 = 0, TC_ADD_F64 = 1 };
+
+struct Seg {
+  int ax, ay, ay_step;  // TMA coordinates of A piece 0 (x = K offset) and piece stride in rows
+  int bx, by, by_step;  // same for B
+  int cls;              // EMU_CLASS_FP32 (6 products) or EMU_CLASS_BF16 (1 product)
+  int pad;
+};
+
+struct Item {
+  int seg_begin, seg_end;
+  long out_off;
+  int rows_valid, cols_valid;  // TC_ADD_F64 only
+};
+
+// 2-D BF16 tensor map over a row-major [rows x inner] array, box
+// [box_rows x BK], 64-byte swizzle.
+emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
+                         uint64_t rows, uint32_t box_rows);
+
+emu_status launch(emu_ctx *ctx, const CUtensorMap &mapA, const CUtensorMap &mapB, const Item *d_items,
+                  int nitems, const Seg *d_segs, int ksteps, int mode, float *out32, double *out64,
+                  int ldo, int max_ctas);
+
+}  // namespace gemm_tc

@@ -1,0 +1,138 @@
+"""Adaptive per-tile precision path on the GPU, through the C ABI, against the
+oracle: the precision map equals the oracle's rule evaluation, the mixed
+factor meets ||L L^T - S||_F / ||S||_F <= eps against the oracle's S, the
+sampler reproduces L Z, and refinement recovers FP64-accurate solves.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U = np.array([2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4])
+MASK_FP64_FP32_BF16 = 0b01011
+
+
+@pytest.fixture(scope="module")
+def E():
+    import paper_2408_04440_gb300 as E
+    from paper_2408_04440_gb300 import build
+
+    build.build()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(E):
+    c = E.Context(0)
+    yield c
+    c.close()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _backward_error(Lf, S):
+    return np.linalg.norm(Lf @ Lf.T - S) / np.linalg.norm(S)
+
+
+def _map_matches(cls_gpu, t, eps, mask, diag_fp64=False):
+    """Classes equal the oracle's, except where a tile sits within 1e-12 of a
+    class threshold (both sides round their norms differently)."""
+    cls_o = O.precision_map(t, eps, U, mask, diag_fp64)
+    NT = t.shape[0]
+    thr = eps * O.frob_from_tiles(t) / NT
+    for i in range(NT):
+        for j in range(i + 1):
+            if cls_gpu[i, j] == cls_o[i, j]:
+                continue
+            margins = [abs(t[i, j] * U[c] - thr) / thr for c in range(1, 5)]
+            assert min(margins) < 1e-12, (i, j, cls_gpu[i, j], cls_o[i, j])
+
+
+@pytest.mark.parametrize("L,nb,beta,eps", [(20, 256, 3.0, 1e-8), (32, 256, 4.0, 1e-8), (32, 256, 4.0, 1e-6),
+                                           (48, 512, 6.0, 1e-8), (48, 256, 6.0, 1e-6)])
+def test_mixed_factor_meets_eps(E, ctx, L, nb, beta, eps):
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=MASK_FP64_FP32_BF16)
+    assert info.status == E.EMU_OK
+    S = O.cov_build(L, beta)
+    cls, _ = E.emu_mat_tile_info(ctx, A)
+    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_FP64_FP32_BF16)
+    assert sum(info.tiles) == (info.nt * (info.nt + 1)) // 2
+    G = _np(E.emu_mat_export(ctx, A))
+    be = _backward_error(G, S)
+    assert be <= eps, be
+    Lo, _ = O.potrf_blocked(S, nb)
+    # the forward error is stated, not bounded by eps (it carries kappa)
+    print(f"L={L} nb={nb} eps={eps:g}: backward {be:.2e}, forward vs oracle "
+          f"{np.linalg.norm(G - Lo) / np.linalg.norm(Lo):.2e}, tiles {info.tiles}")
+
+
+@pytest.mark.parametrize("mask,eps,tol", [(0b00011, 1e-6, 1e-6),   # FP64 diagonal region + FP32 tensor-core GEMMs
+                                          (0b01001, 1e-2, 1e-2)])  # everything that can drops to BF16
+def test_forced_tensor_core_classes(E, ctx, mask, eps, tol):
+    L, nb, beta = 40, 256, 5.0  # n = 1600: 7 tile rows, ragged last
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=mask)
+    low = info.tiles[1] + info.tiles[3]
+    assert low >= info.nt * (info.nt - 1) // 2  # all off-diagonal tiles on the tensor cores
+    S = O.cov_build(L, beta)
+    G = _np(E.emu_mat_export(ctx, A))
+    assert _backward_error(G, S) <= tol
+
+
+def test_fp32_class_accuracy_against_oracle(E, ctx):
+    # eps small enough that every tile uses the FP32 class (diagonal too):
+    # the factor then tracks the FP64 oracle to FP32-level relative accuracy
+    L, nb, beta = 24, 256, 2.0
+    S = O.cov_build(L, beta)
+    t = O.tile_norms(S, nb)
+    NT = t.shape[0]
+    eps = 1.01 * t.max() * U[1] * NT / O.frob_from_tiles(t)
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=0b00011)
+    assert info.tiles[1] == NT * (NT + 1) // 2
+    G = _np(E.emu_mat_export(ctx, A))
+    be = _backward_error(G, S)
+    assert be <= 4 * 2.0**-24, be
+
+
+def test_mixed_sampling(E, ctx):
+    L, nb, beta, s = 32, 256, 4.0, 300  # s not a multiple of the 256-sample block
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=1e-8, prec_mask=MASK_FP64_FP32_BF16)
+    G = _np(E.emu_mat_export(ctx, A))
+    Y, Z = E.emu_sample(ctx, A, s, seed=1, return_z=True)
+    Y, Z = _np(Y), _np(Z)
+    Zo = O.normal_matrix(1, 0, L * L, s)
+    assert np.max(np.abs(Z - Zo)) <= 1e-14 * np.max(np.abs(Zo))
+    ref = G @ Zo
+    rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-6, rel
+    Y2 = _np(E.emu_sample(ctx, A, s, seed=1))
+    assert np.array_equal(Y, Y2)  # bit-reproducible per seed
+
+
+def test_mixed_refinement(E, ctx):
+    import torch
+
+    L, nb, beta = 32, 256, 4.0
+    S_mat = E.emu_cov_build(ctx, L, beta, nb)
+    A = E.emu_mat_clone(ctx, S_mat)
+    E.emu_potrf_mp(ctx, A, eps=1e-6, prec_mask=MASK_FP64_FP32_BF16)
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((L * L, 16))
+    X, ri = E.emu_solve_refine(ctx, A, S_mat, torch.from_numpy(B).cuda(), tol=1e-15, maxit=60)
+    assert ri.status == E.EMU_OK
+    X = _np(X)
+    S = O.cov_build(L, beta)
+    eta = np.linalg.norm(B - S @ X, axis=0) / (np.linalg.norm(S) * np.linalg.norm(X, axis=0)
+                                               + np.linalg.norm(B, axis=0))
+    assert eta.max() <= 2e-15
+    Lo, _ = O.potrf_blocked(S, nb)
+    Xo = O.potrs(Lo, B)
+    print(f"refine: {ri.iters} iterations, forward error vs oracle "
+          f"{np.linalg.norm(X - Xo) / np.linalg.norm(Xo):.2e}")
