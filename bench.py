@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the emulator's hot path on GB300: covariance build -> adaptive
+mixed-precision tile Cholesky -> emulations L z.
+
+Workload (default): bandlimit L=128 (n = L^2 = 16384), tile nb=512, beta=8,
+sigma_l = (1+l)^-1.5, nugget 1e-8; adaptive FP64/FP32/BF16 tiles at
+eps = 1e-8; 256 samples, seed 1.  One "step" is the whole path on one
+synthetic covariance, inputs already in HBM.  The metric is Cholesky TFLOP/s
+counted as n^3/3 per step over the step time; the plain FP64 tile Cholesky of
+the same matrix on the same GPU is timed beside it for the speedup.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank factors its own covariance (independent
+problems, weak scaling, no collective on the data path); rank 0 prints the
+JSON line with the max time over ranks.  --impl reference times the CPU
+oracle (test infrastructure) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Cholesky TFLOP/s (n³/3) & speedup vs FP64 on 1 GB300 at ‖LLᵀ−Σ‖/‖Σ‖≤ε"
+MASK_FP64_FP32_BF16 = 0b01011
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=128)
+    ap.add_argument("--nb", type=int, default=512)
+    ap.add_argument("--beta", type=float, default=8.0)
+    ap.add_argument("--eps", type=float, default=1e-8)
+    ap.add_argument("--samples", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"L={a.L} n={a.L * a.L} nb={a.nb} beta={a.beta:g}: adaptive FP64/FP32/BF16 tile Cholesky at "
+            f"eps={a.eps:g}, FP32 accumulate, + {a.samples} samples seed {a.seed}")
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        smax = float(parts[2])
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, parts[5:9]):
+                        if v.lower().startswith("active"):
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2408_04440_gb300 as E
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2408_04440_gb300 import build as _b
+
+    if rank == 0 or world == 1:
+        _b.build()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    ctx = E.Context(local, stream=stream)
+    n, s = a.L * a.L, a.samples
+    flops = n ** 3 / 3.0
+    Y = E._colmajor_empty(n, s, ctx.device)
+    seed = a.seed + 1000 * rank
+
+    factor_ms = []
+
+    def step():
+        A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+        info = E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+        factor_ms.append(info.ms)
+        E.emu_sample(ctx, A, s, seed=seed, out=Y)
+        A.free()
+        return info
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(a.warmup, 0)):
+            info = step()
+        factor_ms.clear()
+        clocks = ClockSampler(local)
+        barrier()
+        launches0 = ctx.launch_count
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            info = step()
+        e1.record(stream)
+        stream.synchronize()
+        barrier()
+        clk = clocks.stop()
+        gpu_launches = ctx.launch_count - launches0
+        ms_total = e0.elapsed_time(e1)
+        t = torch.tensor([ms_total], device=ctx.device)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item()) / a.steps
+        value = world * flops / (ms_per_step * 1e-3) / 1e12
+
+        if rank != 0:
+            ctx.close()
+            if dist is not None:
+                dist.barrier()
+                dist.destroy_process_group()
+            return
+
+        mixed_factor_ms = statistics.median(factor_ms)
+        extra = {"factor_ms": round(mixed_factor_ms, 4),
+                 "factor_tflops": round(flops / (mixed_factor_ms * 1e-3) / 1e12, 3),
+                 "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)),
+                 "update_flop_share": {c: round(f / max(sum(info.update_flops), 1.0), 4)
+                                       for c, f in zip(E.CLASS_NAMES, info.update_flops)}}
+
+        # per-kernel-group device time of one profiled step (events on the launch stream)
+        ctx.prof_enable(True)
+        step()
+        prof = ctx.prof_read()
+        ctx.prof_enable(False)
+        step_ms = sum(v["ms"] for v in prof.values())
+        extra["kernel_groups"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                      "share": round(v["ms"] / step_ms, 4)} for k, v in prof.items() if v["launches"]}
+        peaks = load_peaks()
+        roof = roofline(prof, peaks)
+
+        # accuracy: backward error on 64 sampled rows against the GPU-built covariance
+        extra["backward_error_rows64"] = backward_error_rows(E, ctx, a, rows=64)
+
+        if not a.no_fp64:
+            A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+            E.emu_potrf_mp(ctx, A)  # warm-up of the FP64 path
+            A.free()
+            A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+            i64 = E.emu_potrf_mp(ctx, A)
+            A.free()
+            extra["fp64_factor_ms"] = round(i64.ms, 3)
+            extra["fp64_tflops"] = round(flops / (i64.ms * 1e-3) / 1e12, 4)
+            extra["speedup_vs_fp64"] = round(i64.ms / mixed_factor_ms, 2)
+
+        e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
+
+    cpu = None if (a.no_cpu or world > 1) else cpu_baseline(a)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed:f64+f32(3xbf16 split)+bf16", "data": "synthetic",
+        "config": {"workload": workload_name(a), "L": a.L, "n": n, "nb": a.nb, "beta": a.beta, "eps": a.eps,
+                   "samples": s, "seed": a.seed, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2: each step rebuilds the 1.1 GB FP64 tile arena"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(prof: dict, peaks: dict) -> dict:
+    """Roofline of the kernel group with the largest device time in the step."""
+    group = max(prof, key=lambda k: prof[k]["ms"])
+    g = prof[group]
+    per_launch_ms = g["ms"] / max(g["launches"], 1)
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
+    if g["mma_flops"] > 0:
+        # tensor cores: algorithmic flops against the precision-weighted peak of
+        # this launch's class mix (FP32 class = six BF16 products)
+        achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
+        peak = bf16 * g["flops"] / g["mma_flops"]
+        return {"kernel": group, "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
+                "peak_note": f"bf16 sustained {bf16} TF/s {src}, weighted by the class mix"}
+    if group in ("potrf", "trsm64", "update64", "trmm64", "solve"):
+        fp64 = 1.19  # DFMA loop measured on this GPU model
+        achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
+        return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": fp64, "unit": "TFLOP/s",
+                "frac": round(achieved / fp64, 4), "traffic": None, "per_launch_ms": round(per_launch_ms, 4),
+                "launches": g["launches"], "peak_note": "FP64 DFMA peak measured with a DFMA loop"}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    achieved = g["bytes"] / (g["ms"] * 1e-3) / 1e9
+    return {"kernel": group, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "per_launch_ms": round(per_launch_ms, 4),
+            "launches": g["launches"]}
+
+
+def backward_error_rows(E, ctx, a, rows: int) -> float:
+    import torch
+
+    n = a.L * a.L
+    S = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+    Sd = E.emu_mat_export(ctx, S)  # lower triangle
+    S.free()
+    Sd = Sd + Sd.t() - torch.diag(torch.diag(Sd))
+    A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+    Ld = E.emu_mat_export(ctx, A)
+    A.free()
+    g = torch.Generator().manual_seed(7)
+    idx = torch.randperm(n, generator=g)[:rows].to(Ld.device)
+    R = Ld[idx, :] @ Ld.t() - Sd[idx, :]
+    be = float(torch.linalg.norm(R) / torch.linalg.norm(Sd[idx, :]))
+    del Sd, Ld, R
+    torch.cuda.empty_cache()
+    return be
+
+
+def run_e2e(E, ctx, a, flops) -> dict:
+    """Same step through the C ABI with HOST buffers: the covariance comes from
+    pinned host memory (lower triangle copied tile column by tile column) and
+    the samples go back to pinned host memory, copies inside the timed region."""
+    import torch
+
+    n, s, nb = a.L * a.L, a.samples, a.nb
+    A = E.emu_cov_build(ctx, a.L, a.beta, nb)
+    Sd = E.emu_mat_export(ctx, A)
+    A.free()
+    hS = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()  # column-major host
+    hS.copy_(Sd)
+    del Sd
+    torch.cuda.empty_cache()
+    hY = torch.empty((s, n), dtype=torch.float64, pin_memory=True).t()
+    NT = (n + nb - 1) // nb
+    h2d = sum((n - j * nb) * min(nb, n - j * nb) * 8 for j in range(NT))
+    d2h = n * s * 8
+
+    def step():
+        M = E.emu_mat_import_host(ctx, hS, nb)
+        E.emu_potrf_mp(ctx, M, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+        E.emu_sample_host(ctx, M, s, seed=a.seed, out=hY)
+        M.free()
+
+    for _ in range(2):
+        step()
+    k = max(3, min(a.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    return {"value": round(flops / dt / 1e12, 4), "unit": "TFLOP/s", "ms_per_step": round(dt * 1e3, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
+            "path": "emu_mat_import_host -> emu_potrf_mp -> emu_sample_host"}
+
+
+# ------------------------------------------------------------- CPU oracle
+def _panel_flops(n: int, nb: int, k: int) -> float:
+    m = max(n - (k + 1) * nb, 0)
+    kb = min(nb, n - k * nb)
+    return kb ** 3 / 3.0 + m * kb * kb + m * m * kb
+
+
+def cpu_baseline(a, budget_s: float = 15.0) -> dict:
+    """The oracle, as it stands, on this host's cores: the first panel steps of
+    the same n=16384 blocked factor (as many as fit in about budget_s)."""
+    import oracle as O
+
+    n, nb = a.L * a.L, a.nb
+    S = O.cov_build(a.L, a.beta)
+    NT = (n + nb - 1) // nb
+    fl, dt, k = 0.0, 0.0, 0
+    while k < NT and dt < budget_s:
+        t0 = time.perf_counter()
+        O.lib().orc_potrf_blocked_steps(n, nb, O._dp(S), n, k, k + 1)
+        dt += time.perf_counter() - t0
+        fl += _panel_flops(n, nb, k)
+        k += 1
+    return {"value": round(fl / dt / 1e12, 5), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {k} of {NT} panel steps of the n={n}, nb={nb} FP64 blocked Cholesky "
+                      f"({fl:.3e} flop in {dt:.1f} s)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    n, nb = a.L * a.L, a.nb
+    NT = (n + nb - 1) // nb
+    S = O.cov_build(a.L, a.beta)
+    state = {"k": 0}
+
+    def step():
+        if state["k"] >= NT:
+            S[:, :] = O.cov_build(a.L, a.beta)
+            state["k"] = 0
+        k = state["k"]
+        O.lib().orc_potrf_blocked_steps(n, nb, O._dp(S), n, k, k + 1)
+        state["k"] += 1
+        return _panel_flops(n, nb, k)
+
+    for _ in range(a.warmup):
+        step()
+    fl = 0.0
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        fl += step()
+    dt = time.perf_counter() - t0
+    value = fl / dt / 1e12
+    cpu = {"value": round(value, 5), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{a.steps} panel steps of the n={n}, nb={nb} FP64 blocked Cholesky per timed region"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / max(a.steps, 1) * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "L": a.L, "n": n, "nb": nb},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

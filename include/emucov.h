@@ -125,6 +125,22 @@ const char *emu_last_error(const emu_ctx *ctx);
 /* Number of this library's kernels launched through `ctx` so far. */
 uint64_t emu_launch_count(const emu_ctx *ctx);
 
+/* Optional per-kernel-group timing, for roofline accounting.  When enabled,
+ * every group of launches is bracketed by CUDA events on the context stream
+ * (which adds a small gap between launches).  emu_prof_enable resets the
+ * counters; emu_prof_read synchronises the stream and returns, for `group`
+ * (EMU_PROF_*), the launches, their total device time, their algorithmic
+ * flops and bytes, and the tensor-core flops they executed (split products
+ * included). */
+enum {
+  EMU_PROF_COV = 0, EMU_PROF_MAP, EMU_PROF_POTRF, EMU_PROF_TRSM64, EMU_PROF_TRSM32,
+  EMU_PROF_UPDATE64, EMU_PROF_TC_FACTOR, EMU_PROF_TC_SAMPLE, EMU_PROF_TRMM64,
+  EMU_PROF_RNG, EMU_PROF_SPLIT, EMU_PROF_SOLVE, EMU_PROF_NGROUPS
+};
+emu_status emu_prof_enable(emu_ctx *ctx, int on);
+emu_status emu_prof_read(emu_ctx *ctx, int group, int *launches, double *total_ms,
+                         double *flops, double *bytes, double *mma_flops);
+
 /* ---------------------------------------------------------------- matrices */
 /* Build the synthetic covariance on the device as an n x n tiled matrix with
  * tile size nb (n = L^2).  The lower tiles are stored packed, each tile
@@ -137,6 +153,12 @@ emu_status emu_cov_build(emu_ctx *ctx, const emu_cov_params *p, int nb,
  * its lower triangle is read. */
 emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda,
                           int nb, emu_mat **out);
+/* Same from HOST memory hA (pinned memory gives full copy bandwidth): only
+ * the lower triangle is copied, one tile column at a time, through a device
+ * staging buffer of n x nb doubles.  The call synchronises the stream before
+ * returning, so hA may be reused at once. */
+emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda,
+                               int nb, emu_mat **out);
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);
 /* Write the matrix as a dense FP64 lower triangle (upper set to 0) into dOut

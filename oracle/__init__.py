@@ -69,6 +69,8 @@ def _declare(L):
     L.orc_potrf_unblocked.restype = i
     L.orc_potrf_blocked.argtypes = [i, i, dp, lg, i]
     L.orc_potrf_blocked.restype = i
+    L.orc_potrf_blocked_steps.argtypes = [i, i, dp, lg, i, i]
+    L.orc_potrf_blocked_steps.restype = i
     L.orc_trmm_lower.argtypes = [i, i, dp, lg, dp, lg, dp, lg]
     L.orc_potrs.argtypes = [i, i, dp, lg, dp, lg, dp, lg]
     L.orc_logdet_chol.argtypes = [i, dp, lg]

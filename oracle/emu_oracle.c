@@ -26,6 +26,7 @@ void orc_lm_of_index(long k, int *l, int *m) {
 void orc_cov_build(int L, double beta, double sigma_exp, double nugget_rel,
                    double *S, long ld) {
   long n = (long)L * L;
+#pragma omp parallel for schedule(static)
   for (long j = 0; j < n; j++) {
     int lj, mj;
     orc_lm_of_index(j, &lj, &mj);
@@ -166,27 +167,27 @@ static int potrf_block(int kb, double *A, long ld) {
   return 0;
 }
 
-int orc_potrf_blocked(int n, int nb, double *A, long ld, int kmax) {
+int orc_potrf_blocked_steps(int n, int nb, double *A, long ld, int k0, int k1) {
   int NT = (n + nb - 1) / nb;
-  if (kmax < 0 || kmax > NT) kmax = NT;
-  for (int k = 0; k < kmax; k++) {
-    int k0 = k * nb;
-    int kb = (k0 + nb <= n) ? nb : n - k0;
+  if (k1 > NT) k1 = NT;
+  for (int k = k0; k < k1; k++) {
+    int c0 = k * nb;
+    int kb = (c0 + nb <= n) ? nb : n - c0;
     /* POTRF(k,k) */
-    int info = potrf_block(kb, &A[IDX(k0, k0, ld)], ld);
-    if (info) return k0 + info;
-    int r0 = k0 + kb;
+    int info = potrf_block(kb, &A[IDX(c0, c0, ld)], ld);
+    if (info) return c0 + info;
+    int r0 = c0 + kb;
     if (r0 >= n) break;
-    /* TRSM: A(r0:n, k0:k0+kb) <- A(r0:n, k0:k0+kb) * L_kk^{-T}, i.e. each row
+    /* TRSM: A(r0:n, c0:c0+kb) <- A(r0:n, c0:c0+kb) * L_kk^{-T}, i.e. each row
      * x solves L_kk x^T = a^T by forward substitution over the columns. */
     for (int c = 0; c < kb; c++) {
-      double *xc = &A[IDX(r0, k0 + c, ld)];
+      double *xc = &A[IDX(r0, c0 + c, ld)];
       for (int p = 0; p < c; p++) {
-        double l = A[IDX(k0 + c, k0 + p, ld)];
-        const double *xp = &A[IDX(r0, k0 + p, ld)];
+        double l = A[IDX(c0 + c, c0 + p, ld)];
+        const double *xp = &A[IDX(r0, c0 + p, ld)];
         for (int i = 0; i < n - r0; i++) xc[i] -= xp[i] * l;
       }
-      double d = A[IDX(k0 + c, k0 + c, ld)];
+      double d = A[IDX(c0 + c, c0 + c, ld)];
       for (int i = 0; i < n - r0; i++) xc[i] /= d;
     }
     /* SYRK/GEMM: A(j:n, j) -= A(j:n, panel) * A(j, panel)^T for j >= r0. */
@@ -194,13 +195,19 @@ int orc_potrf_blocked(int n, int nb, double *A, long ld, int kmax) {
     for (int j = r0; j < n; j++) {
       double *cj = &A[IDX(j, j, ld)];
       for (int p = 0; p < kb; p++) {
-        double ajp = A[IDX(j, k0 + p, ld)];
-        const double *ap = &A[IDX(j, k0 + p, ld)];
+        double ajp = A[IDX(j, c0 + p, ld)];
+        const double *ap = &A[IDX(j, c0 + p, ld)];
         for (int i = 0; i < n - j; i++) cj[i] -= ap[i] * ajp;
       }
     }
   }
   return 0;
+}
+
+int orc_potrf_blocked(int n, int nb, double *A, long ld, int kmax) {
+  int NT = (n + nb - 1) / nb;
+  if (kmax < 0 || kmax > NT) kmax = NT;
+  return orc_potrf_blocked_steps(n, nb, A, ld, 0, kmax);
 }
 
 /* ----------------------------------------------------- sampling and solve */

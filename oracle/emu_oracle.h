@@ -74,6 +74,9 @@ int orc_potrf_unblocked(int n, double *A, long ld);
  * on the trailing tiles).  Runs panel steps k = 0 .. kmax-1 (kmax < 0: all).
  * Returns 0, or the 1-based global column of the first non-positive pivot. */
 int orc_potrf_blocked(int n, int nb, double *A, long ld, int kmax);
+/* Panel steps k0 .. k1-1 of the same algorithm on a matrix whose steps
+ * 0 .. k0-1 are already done. */
+int orc_potrf_blocked_steps(int n, int nb, double *A, long ld, int k0, int k1);
 
 /* Y = L Z for lower-triangular L (n x n) and Z (n x s): drawing emulations
  * xi = V z (Section "Generating Emulations"). */

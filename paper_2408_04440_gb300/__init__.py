@@ -29,10 +29,12 @@ DEFAULT_U = (2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4)
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_cov_build", "emu_mat_import", "emu_mat_clone", "emu_mat_export",
-    "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free", "emu_potrf_mp", "emu_sample",
-    "emu_sample_host", "emu_potrs", "emu_solve_refine",
+    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_cov_build", "emu_mat_import",
+    "emu_mat_import_host", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
 )
+PROF_GROUPS = ("cov", "map", "potrf", "trsm64", "trsm32", "update64", "tc_factor", "tc_sample", "trmm64",
+               "rng", "split", "solve")
 
 
 class EmuError(RuntimeError):
@@ -86,7 +88,11 @@ def load() -> ctypes.CDLL:
     L.emu_last_error.restype = ctypes.c_char_p
     L.emu_launch_count.argtypes = [vp]
     L.emu_launch_count.restype = ctypes.c_uint64
+    dpp = ctypes.POINTER(ctypes.c_double)
+    L.emu_prof_enable.argtypes = [vp, i]
+    L.emu_prof_read.argtypes = [vp, i, ctypes.POINTER(i), dpp, dpp, dpp, dpp]
     L.emu_cov_build.argtypes = [vp, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(vp)]
+    L.emu_mat_import_host.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
     L.emu_mat_import.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
@@ -98,7 +104,8 @@ def load() -> ctypes.CDLL:
     L.emu_sample_host.argtypes = [vp, vp, i, ctypes.c_uint64, ctypes.c_uint32, vp, lg]
     L.emu_potrs.argtypes = [vp, vp, vp, lg, vp, lg, i]
     L.emu_solve_refine.argtypes = [vp, vp, vp, vp, lg, vp, lg, i, d, i, ctypes.POINTER(emu_refine_info)]
-    for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_cov_build", "emu_mat_import",
+    for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
+                 "emu_mat_import_host", "emu_cov_build", "emu_mat_import",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
                  "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine"):
         getattr(L, name).restype = st
@@ -143,6 +150,21 @@ class Context:
     @property
     def launch_count(self) -> int:
         return int(self.lib.emu_launch_count(self.h))
+
+    def prof_enable(self, on: bool = True):
+        self._check(self.lib.emu_prof_enable(self.h, int(on)), "emu_prof_enable")
+
+    def prof_read(self) -> dict:
+        """Per kernel group: launches, total ms, algorithmic flops/bytes, tensor-core flops."""
+        out = {}
+        for g, name in enumerate(PROF_GROUPS):
+            n = ctypes.c_int()
+            ms, fl, by, mm = (ctypes.c_double() for _ in range(4))
+            self._check(self.lib.emu_prof_read(self.h, g, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                               ctypes.byref(by), ctypes.byref(mm)), "emu_prof_read")
+            out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value,
+                         "mma_flops": mm.value}
+        return out
 
     def close(self):
         if getattr(self, "h", None):
@@ -204,6 +226,27 @@ def emu_mat_import(ctx: Context, A, nb: int) -> Mat:
     m = Mat(ctx, h)
     m._keep = A
     return m
+
+
+def emu_mat_import_host(ctx: Context, A, nb: int) -> Mat:
+    """A: (n x n) float64 host array (numpy or CPU tensor, ideally pinned), Fortran
+    (column-major) storage; its lower triangle is copied and read."""
+    import torch
+
+    if isinstance(A, torch.Tensor):
+        n = A.shape[0]
+        if A.stride() != (1, n):
+            raise ValueError("host matrix must be column-major (stride (1, n))")
+        ptr = A.data_ptr()
+    else:
+        if not A.flags.f_contiguous:
+            raise ValueError("host matrix must be Fortran-ordered")
+        n = A.shape[0]
+        ptr = A.ctypes.data
+    h = ctypes.c_void_p()
+    ctx._check(ctx.lib.emu_mat_import_host(ctx.h, ctypes.c_void_p(ptr), n, n, nb, ctypes.byref(h)),
+               "emu_mat_import_host")
+    return Mat(ctx, h)
 
 
 def emu_mat_clone(ctx: Context, A: Mat) -> Mat:
@@ -274,12 +317,14 @@ def emu_sample(ctx: Context, L: Mat, nsamples: int, seed: int, stream_id: int = 
 
 
 def emu_sample_host(ctx: Context, L: Mat, nsamples: int, seed: int, stream_id: int = 0, out=None):
-    """Samples into a (pinned) host buffer; out: numpy float64 (n x s), Fortran order."""
+    """Samples into a host buffer: out is a float64 (n x s) column-major numpy array
+    or CPU tensor (pinned memory gives full copy bandwidth)."""
     n = L.n
     if out is None:
         out = np.empty((n, nsamples), dtype=np.float64, order="F")
-    ctx._check(ctx.lib.emu_sample_host(ctx.h, L.h, nsamples, seed, stream_id,
-                                       ctypes.c_void_p(out.ctypes.data), n), "emu_sample_host")
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    ctx._check(ctx.lib.emu_sample_host(ctx.h, L.h, nsamples, seed, stream_id, ctypes.c_void_p(ptr), n),
+               "emu_sample_host")
     return out
 
 

@@ -23,6 +23,55 @@ static emu_status fail_msg(emu_ctx *ctx, emu_status s, const char *msg) {
   return s;
 }
 
+// ------------------------------------------------------------- profiling
+ProfScope::ProfScope(emu_ctx *c, int group, double flops, double bytes, double mma_flops)
+    : ctx(c), on(c && c->prof) {
+  if (!on) return;
+  for (int q = 0; q < 2; q++) {
+    cudaEvent_t e;
+    if (ctx->ev_pool.empty()) {
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        return;
+      }
+    } else {
+      e = ctx->ev_pool.back();
+      ctx->ev_pool.pop_back();
+    }
+    (q == 0 ? rec.a : rec.b) = e;
+  }
+  rec.group = group;
+  rec.flops = flops;
+  rec.bytes = bytes;
+  rec.mma_flops = mma_flops;
+  rec.launches0 = ctx->launches;
+  cudaEventRecord(rec.a, ctx->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!on) return;
+  cudaEventRecord(rec.b, ctx->stream);
+  rec.launches0 = ctx->launches - rec.launches0;  // launches inside the scope
+  ctx->prof_open.push_back(rec);
+}
+
+static void prof_collect(emu_ctx *ctx) {
+  if (ctx->prof_open.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (const ProfRec &r : ctx->prof_open) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    ctx->prof_ms[r.group] += ms;
+    ctx->prof_launches[r.group] += (int)r.launches0;
+    ctx->prof_flops[r.group] += r.flops;
+    ctx->prof_bytes[r.group] += r.bytes;
+    ctx->prof_mma[r.group] += r.mma_flops;
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->prof_open.clear();
+}
+
 extern "C" {
 
 const char *emu_status_str(emu_status s) {
@@ -63,6 +112,14 @@ emu_status emu_create(emu_ctx **out, int device, void *stream) {
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, ST_WORDS * sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e == cudaSuccess) {
+    // matrices are allocated stream-ordered from the device's default pool;
+    // keep released blocks cached so that rebuilding a matrix is cheap
+    cudaMemPool_t pool;
+    e = cudaDeviceGetDefaultMemPool(&pool, device);
+    uint64_t keep = UINT64_MAX;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (e != cudaSuccess) {
     emu_destroy(ctx);
     return EMU_ECUDA;
@@ -78,6 +135,8 @@ emu_status emu_destroy(emu_ctx *ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   mixed_ctx_release(ctx);
   delete ctx;
   return EMU_OK;
@@ -86,6 +145,29 @@ emu_status emu_destroy(emu_ctx *ctx) {
 emu_status emu_set_stream(emu_ctx *ctx, void *stream) {
   if (!ctx) return EMU_EINVAL;
   ctx->stream = (cudaStream_t)stream;
+  return EMU_OK;
+}
+
+emu_status emu_prof_enable(emu_ctx *ctx, int on) {
+  if (!ctx) return EMU_EINVAL;
+  prof_collect(ctx);
+  for (int g = 0; g < PROF_NGROUPS; g++) {
+    ctx->prof_launches[g] = 0;
+    ctx->prof_ms[g] = ctx->prof_flops[g] = ctx->prof_bytes[g] = ctx->prof_mma[g] = 0.0;
+  }
+  ctx->prof = on != 0;
+  return EMU_OK;
+}
+
+emu_status emu_prof_read(emu_ctx *ctx, int group, int *launches, double *total_ms, double *flops,
+                         double *bytes, double *mma_flops) {
+  if (!ctx || group < 0 || group >= PROF_NGROUPS) return EMU_EINVAL;
+  prof_collect(ctx);
+  if (launches) *launches = ctx->prof_launches[group];
+  if (total_ms) *total_ms = ctx->prof_ms[group];
+  if (flops) *flops = ctx->prof_flops[group];
+  if (bytes) *bytes = ctx->prof_bytes[group];
+  if (mma_flops) *mma_flops = ctx->prof_mma[group];
   return EMU_OK;
 }
 
@@ -113,11 +195,12 @@ static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out) {
     delete A;
     return fail_msg(ctx, EMU_ENOMEM, "FP64 tile arena does not fit in free device memory");
   }
-  cudaError_t e = cudaMalloc(&A->t64, bytes64);
-  if (e == cudaSuccess) e = cudaMalloc(&A->d_partial, (size_t)A->ntiles * A->nchunk * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&A->d_tnorm, (size_t)A->ntiles * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&A->d_frob, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&A->d_cls, (size_t)A->ntiles);
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMallocAsync(&A->t64, bytes64, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&A->d_partial, (size_t)A->ntiles * A->nchunk * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&A->d_tnorm, (size_t)A->ntiles * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&A->d_frob, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&A->d_cls, (size_t)A->ntiles, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(A->d_cls, 0, (size_t)A->ntiles, ctx->stream);
   if (e != cudaSuccess) {
     emu_mat_free(A);
@@ -137,14 +220,11 @@ extern "C" {
 
 emu_status emu_mat_free(emu_mat *A) {
   if (!A) return EMU_EINVAL;
+  cudaStream_t s = A->ctx ? A->ctx->stream : nullptr;
   if (A->ctx) cudaSetDevice(A->ctx->device);
-  cudaFree(A->t64);
-  cudaFree(A->t32);
-  cudaFree(A->d_partial);
-  cudaFree(A->d_tnorm);
-  cudaFree(A->d_frob);
-  cudaFree(A->d_cls);
-  cudaFree(A->op_bf16);
+  void *bufs[] = {A->t64, A->t32, A->d_partial, A->d_tnorm, A->d_frob, A->d_cls, A->op_bf16};
+  for (void *b : bufs)
+    if (b) cudaFreeAsync(b, s);
   mixed_mat_release(A);
   delete[] A->h_cls;
   delete A;
@@ -174,6 +254,34 @@ emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda, int n
   emu_status s = mat_alloc(ctx, n, nb, &A);
   if (s != EMU_OK) return s;
   s = launch_import(ctx, A, dA, lda);
+  if (s != EMU_OK) {
+    emu_mat_free(A);
+    return s;
+  }
+  *out = A;
+  return EMU_OK;
+}
+
+emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda, int nb,
+                               emu_mat **out) {
+  if (!ctx || !hA || !out || lda < n) return EMU_EINVAL;
+  emu_mat *A = nullptr;
+  emu_status s = mat_alloc(ctx, n, nb, &A);
+  if (s != EMU_OK) return s;
+  double *stage = nullptr;
+  cudaError_t e = cudaMallocAsync(&stage, (size_t)n * nb * sizeof(double), ctx->stream);
+  for (int j = 0; j < A->nt && e == cudaSuccess && s == EMU_OK; j++) {
+    long r0 = (long)j * nb;
+    long cols = (r0 + nb <= n) ? nb : n - r0;
+    // rows r0 .. n-1 of columns r0 .. r0+cols-1: the lower part of tile column j
+    e = cudaMemcpy2DAsync(stage, (size_t)(n - r0) * sizeof(double), hA + r0 + r0 * lda, lda * sizeof(double),
+                          (size_t)(n - r0) * sizeof(double), cols, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) s = launch_import_col(ctx, A, j, stage, n - r0);
+  }
+  if (stage) cudaFreeAsync(stage, ctx->stream);
+  if (e == cudaSuccess && s == EMU_OK) s = launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+  if (e == cudaSuccess && s == EMU_OK) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "import_host");
   if (s != EMU_OK) {
     emu_mat_free(A);
     return s;

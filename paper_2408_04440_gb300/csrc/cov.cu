@@ -137,6 +137,36 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
 }
 
+// One tile column j from a staging block holding rows j*nb .. n-1 of
+// columns j*nb .. j*nb+nb-1 (column-major, leading dimension ld).
+__global__ void __launch_bounds__(kThreads)
+    k_import_col(int n, int nb, int NT, int tj, const double *__restrict__ S, long ld,
+                 double *__restrict__ t64, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  int ti = tj + blockIdx.x;
+  long t = tile_index(ti, tj, NT);
+  double *tile = t64 + (size_t)t * nb * nb;
+  long base = (long)tj * nb;
+  double ss = 0.0;
+  for (int cc = 0; cc < kChunk; cc++) {
+    int c = blockIdx.y * kChunk + cc;
+    long gj = base + c;
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      long gi = (long)ti * nb + r;
+      double v;
+      if (gi < n && gj < n) {
+        v = (gi >= gj) ? S[(gi - base) + (gj - base) * ld] : S[(gj - base) + (gi - base) * ld];
+        ss += v * v;
+      } else {
+        v = (gi == gj) ? 1.0 : 0.0;
+      }
+      tile[r + (size_t)c * nb] = v;
+    }
+  }
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
 // Single CTA: tile norms from the partial sums (fixed order), ||S||_F, and
 // the class of each tile under the rule t_ij * u[c] <= eps * ||S||_F / NT.
 __global__ void __launch_bounds__(1024)
@@ -232,6 +262,7 @@ emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p) {
                                                sigma, rho, nug);
   EMU_LAUNCHED(ctx);
   dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+  ProfScope ps(ctx, PROF_COV, 3.0 * A->ntiles * A->tile_elems, 8.0 * A->ntiles * A->tile_elems);
   k_cov_build<<<grid, kThreads, 0, ctx->stream>>>(L, A->n, A->nb, A->nt, sigma, rho, nug,
                                                  A->t64, A->d_partial);
   EMU_LAUNCHED(ctx);
@@ -247,9 +278,17 @@ emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {
   return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
 }
 
+emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS, long ld) {
+  dim3 grid(A->nt - tj, A->nb / kChunk);
+  k_import_col<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, tj, dS, ld, A->t64, A->d_partial);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
 // With u == nullptr only the norms and ||S||_F are (re)computed.
 emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
                                 const double *u, unsigned mask, int diag_fp64) {
+  ProfScope ps(ctx, PROF_MAP, 0.0, 8.0 * A->ntiles * (A->nchunk + 1));
   k_precision_map<<<1, 1024, 0, ctx->stream>>>(
       A->nt, A->ntiles, A->nchunk, A->d_partial, A->d_tnorm, A->d_frob,
       u ? A->d_cls : nullptr, eps, u ? u[1] : 0.0, u ? u[2] : 0.0,

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/emucov.h"
 
@@ -35,6 +36,20 @@ enum { DEV_OK = 0, DEV_NOTPD = 1, DEV_TIMEOUT = 2 };
 // Matrix states.
 enum { MAT_COV = 0, MAT_FACTOR64 = 1, MAT_FACTOR_MIXED = 2 };
 
+// Kernel groups timed by the optional per-launch profiler (emu_prof_*).
+enum {
+  PROF_COV = 0, PROF_MAP, PROF_POTRF, PROF_TRSM64, PROF_TRSM32, PROF_UPDATE64,
+  PROF_TC_FACTOR, PROF_TC_SAMPLE, PROF_TRMM64, PROF_RNG, PROF_SPLIT, PROF_SOLVE,
+  PROF_NGROUPS
+};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int group;
+  uint64_t launches0;
+  double flops, bytes, mma_flops;
+};
+
 struct emu_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -44,6 +59,24 @@ struct emu_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   uint64_t launches = 0;
   std::string last_error;
+  bool prof = false;
+  std::vector<ProfRec> prof_open;   // recorded, not yet collected
+  std::vector<cudaEvent_t> ev_pool;  // reusable events
+  int prof_launches[PROF_NGROUPS] = {};
+  double prof_ms[PROF_NGROUPS] = {}, prof_flops[PROF_NGROUPS] = {}, prof_bytes[PROF_NGROUPS] = {};
+  double prof_mma[PROF_NGROUPS] = {};
+};
+
+// Brackets the launches issued during its lifetime with CUDA events on the
+// context stream when profiling is on; `flops` / `bytes` are the algorithmic
+// work of those launches, `mma_flops` the tensor-core multiply-adds they
+// execute (x2), split products included.
+struct ProfScope {
+  emu_ctx *ctx;
+  ProfRec rec;
+  bool on;
+  ProfScope(emu_ctx *c, int group, double flops = 0.0, double bytes = 0.0, double mma_flops = 0.0);
+  ~ProfScope();
 };
 
 struct emu_mat {
@@ -86,6 +119,7 @@ emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what);
 // cov.cu
 emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda);
+emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS, long ld);
 emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
                                 const double *u, unsigned mask, int diag_fp64);
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);

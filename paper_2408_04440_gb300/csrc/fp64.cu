@@ -367,6 +367,7 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   int nb = A->nb, NT = A->nt;
   double *D = A->t64 + (size_t)tile_index(k, k, NT) * nb * nb;
   int nbb = nb / B;
+  ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
   for (int s = 0; s < nbb; s++) {
     k_potrf_leaf<<<1, 32, 0, ctx->stream>>>(D, nb, s, k * nb, ctx->d_status);
     EMU_LAUNCHED(ctx);
@@ -383,6 +384,8 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
 emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows, int nrows) {
   int m = d_rows ? nrows : A->nt - k - 1;
   if (m <= 0) return EMU_OK;
+  double nb3 = (double)A->nb * A->nb * A->nb;
+  ProfScope ps(ctx, PROF_TRSM64, m * nb3, 16.0 * m * A->nb * A->nb);
   k_trsm64_panel<<<dim3(A->nb / B, m), 256, 0, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
                                                              ctx->d_status);
   EMU_LAUNCHED(ctx);
@@ -394,6 +397,8 @@ emu_status launch_update64(emu_ctx *ctx, emu_mat *A, int k) {
   if (m <= 0) return EMU_OK;
   long pairs = (long)m * (m + 1) / 2;
   int nsub = A->nb / GM;
+  double nb3 = (double)A->nb * A->nb * A->nb;
+  ProfScope ps(ctx, PROF_UPDATE64, (double)m * m * nb3, 8.0 * A->nb * A->nb * (2.0 * pairs + 2.0 * m));
   k_update64<<<dim3((unsigned)pairs, nsub * nsub), 256, 0, ctx->stream>>>(
       A->t64, A->nb, A->nt, k, ctx->d_status);
   EMU_LAUNCHED(ctx);
@@ -409,6 +414,7 @@ emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A) {
 emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z, long ldz,
                          int s, double *Y, long ldy, const unsigned char *cls) {
   dim3 grid(L->nt * (L->nb / GM), (s + GM - 1) / GM);
+  ProfScope ps(ctx, PROF_TRMM64, (double)L->n * L->n * s, 8.0 * tile_count(L->nt) * L->nb * L->nb);
   k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
@@ -418,6 +424,7 @@ emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z, long l
 emu_status launch_potrs64(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs) {
   int nb = L->nb, NT = L->nt;
   int thr = 256;
+  ProfScope ps(ctx, PROF_SOLVE, 2.0 * L->n * L->n * nrhs, 16.0 * tile_count(NT) * nb * nb);
   for (int k = 0; k < NT; k++) {
     if (k > 0) {
       k_solve_update<<<dim3((nb + thr - 1) / thr, nrhs), thr, 0, ctx->stream>>>(

@@ -314,6 +314,7 @@ struct MixedPlan {
   // per step k: offsets into the concatenated device lists
   std::vector<int> off_t64rows, off_t32rows, off_pairs, off_items;
   std::vector<int> diag_low;       // class(k,k) != FP64
+  std::vector<double> step_flops, step_mma;  // tensor-core work of each step
   int *d_rows64 = nullptr, *d_rows32 = nullptr;
   int2 *d_pairs = nullptr;
   gemm_tc::Item *d_items = nullptr;
@@ -374,6 +375,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     P->off_t32rows.push_back((int)rows32.size());
     P->off_pairs.push_back((int)pairs.size());
     P->off_items.push_back((int)items.size());
+    double sf = 0.0, sm = 0.0;
     for (int i = k + 1; i < NT; i++) {
       if (C(i, k) == EMU_CLASS_FP64) {
         rows64.push_back(i);
@@ -411,8 +413,13 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
             it.rows_valid = gemm_tc::BM;
             it.cols_valid = gemm_tc::BN;
             items.push_back(it);
+            double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
+            sf += f;
+            sm += f * (cc == EMU_CLASS_FP32 ? 6.0 : 1.0);
           }
       }
+    P->step_flops.push_back(sf);
+    P->step_mma.push_back(sm);
   }
   P->off_t64rows.push_back((int)rows64.size());
   P->off_t32rows.push_back((int)rows32.size());
@@ -449,19 +456,25 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(&A->frob, A->d_frob, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   size_t te = A->tile_elems;
-  if (!A->t32) EMU_CUDA_TRY(ctx, cudaMalloc(&A->t32, (size_t)A->ntiles * te * sizeof(float)));
-  if (!A->op_bf16) EMU_CUDA_TRY(ctx, cudaMalloc(&A->op_bf16, (size_t)A->ntiles * 3 * te * sizeof(uint16_t)));
+  if (!A->t32) EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->t32, (size_t)A->ntiles * te * sizeof(float), ctx->stream));
+  if (!A->op_bf16)
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->op_bf16, (size_t)A->ntiles * 3 * te * sizeof(uint16_t), ctx->stream));
   mixed_mat_release(A);
   MixedPlan *P = new MixedPlan();
   A->plan = P;
   if ((s = build_plan(ctx, A, P)) != EMU_OK) return s;
 
   int *st = ctx->d_status;
-  k_to_f32<<<dim3(64, (unsigned)A->ntiles), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, te);
-  EMU_LAUNCHED(ctx);
+  double nb3 = (double)nb * nb * nb;
+  {
+    ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * A->ntiles * te);
+    k_to_f32<<<dim3(64, (unsigned)A->ntiles), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, te);
+    EMU_LAUNCHED(ctx);
+  }
   for (int k = 0; k < NT; k++) {
     long tkk = tile_index(k, k, NT);
     if (P->diag_low[k]) {
+      ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * te);
       k_tile_to_f64<<<64, 256, 0, ctx->stream>>>(A->t32 + tkk * te, A->t64 + tkk * te, te, st);
       EMU_LAUNCHED(ctx);
     }
@@ -470,23 +483,27 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     int n32 = P->off_t32rows[k + 1] - P->off_t32rows[k];
     if (n64 > 0) {
       if ((s = launch_trsm64_panel(ctx, A, k, P->d_rows64 + P->off_t64rows[k], n64)) != EMU_OK) return s;
+      ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
       k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(
           A->t64, A->op_bf16, P->d_tiles_fp64_panel + P->off_t64rows[k], nb, 0, st);
       EMU_LAUNCHED(ctx);
     }
     if (n32 > 0) {
+      ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
       k_trsm32_panel<<<dim3(nb / B, n32), 256, 0, ctx->stream>>>(A->t64, A->t32, A->op_bf16, nb, NT, k,
                                                                 P->d_rows32 + P->off_t32rows[k], st);
       EMU_LAUNCHED(ctx);
     }
     int np = P->off_pairs[k + 1] - P->off_pairs[k];
     if (np > 0) {
+      ProfScope ps(ctx, PROF_UPDATE64, 2.0 * np * nb3, 24.0 * np * te);
       k_update64_list<<<dim3(np, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
           A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + P->off_pairs[k], st);
       EMU_LAUNCHED(ctx);
     }
     int ni = P->off_items[k + 1] - P->off_items[k];
     if (ni > 0) {
+      ProfScope ps(ctx, PROF_TC_FACTOR, P->step_flops[k], 0.0, P->step_mma[k]);
       s = gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + P->off_items[k], ni, P->d_segs, nb / gemm_tc::BK,
                           gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctx->sm_count);
       if (s != EMU_OK) return s;
@@ -494,6 +511,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   }
   if ((s = launch_tril_diag(ctx, A)) != EMU_OK) return s;
   // pieces of the (lower-triangular) diagonal factor tiles, for the sampler
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * NT * te);
   k_split_tiles<double><<<dim3((nb / B) * (nb / B), NT), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
                                                                                P->d_diag_tiles, nb, 1, st);
   EMU_LAUNCHED(ctx);
@@ -562,10 +580,21 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
   EMU_CUDA_TRY(ctx, cudaMallocAsync(&d_segs, sbytes, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), ibytes, cudaMemcpyHostToDevice, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_segs, segs.data(), sbytes, cudaMemcpyHostToDevice, ctx->stream));
-  k_split_z<<<8 * ctx->sm_count, 256, 0, ctx->stream>>>(Z, ldz, npad, s, s_pad, zp);
-  EMU_LAUNCHED(ctx);
+  {
+    ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * npad * s_pad);
+    k_split_z<<<8 * ctx->sm_count, 256, 0, ctx->stream>>>(Z, ldz, npad, s, s_pad, zp);
+    EMU_LAUNCHED(ctx);
+  }
+  double tf = 0.0, tm = 0.0;
+  for (const gemm_tc::Item &it : items)
+    for (int q = it.seg_begin; q < it.seg_end; q++) {
+      double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
+      tf += f;
+      tm += f * (segs[q].cls == EMU_CLASS_FP32 ? 6.0 : 1.0);
+    }
   CUtensorMap mapB;
   st = gemm_tc::make_map_bf16(ctx, &mapB, zp, npad, (uint64_t)3 * s_pad, gemm_tc::BN);
+  ProfScope ps(ctx, PROF_TC_SAMPLE, tf, 0.0, tm);
   if (st == EMU_OK)
     st = gemm_tc::launch(ctx, P->mapA, mapB, d_items, (int)items.size(), d_segs, nb / gemm_tc::BK,
                          gemm_tc::TC_ADD_F64, nullptr, Y, (int)ldy, ctx->sm_count);
@@ -580,6 +609,7 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
 emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs) {
   int nb = L->nb, NT = L->nt;
   int thr = 256;
+  ProfScope ps(ctx, PROF_SOLVE, 2.0 * L->n * L->n * nrhs, 0.0);
   for (int k = 0; k < NT; k++) {
     if (k > 0) {
       k_solve32_update<<<dim3((nb + thr - 1) / thr, nrhs), thr, 0, ctx->stream>>>(L->t64, L->t32, L->d_cls, nb, NT,

@@ -59,6 +59,7 @@ emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id, int n
   long blocks = (total + 255) / 256;
   if (blocks > 8L * ctx->sm_count) blocks = 8L * ctx->sm_count;
   if (blocks < 1) blocks = 1;
+  ProfScope ps(ctx, PROF_RNG, 0.0, 8.0 * nrows * (double)s);
   k_normals<<<(unsigned)blocks, 256, 0, ctx->stream>>>(seed, stream_id, nrows, s, Z, ldz);
   EMU_LAUNCHED(ctx);
   return EMU_OK;

@@ -157,3 +157,27 @@ def test_launch_count_increases(E, ctx):
     A = E.emu_cov_build(ctx, 8, 2.0, 64)
     E.emu_potrf_mp(ctx, A)
     assert ctx.launch_count > before
+
+
+def test_import_from_host_buffer(E, ctx):
+    L, nb, beta = 14, 64, 3.0  # n = 196: ragged last tile column
+    S = O.cov_build(L, beta)
+    A = E.emu_mat_import_host(ctx, np.asfortranarray(S), nb)
+    G = _np(E.emu_mat_export(ctx, A))
+    assert np.array_equal(G, np.tril(S))
+    _, tn = E.emu_mat_tile_info(ctx, A)
+    assert np.allclose(tn, O.tile_norms(S, nb), rtol=1e-13, atol=0)
+    E.emu_potrf_mp(ctx, A)
+    Lo, _ = O.potrf_blocked(S, nb)
+    G = _np(E.emu_mat_export(ctx, A))
+    assert np.linalg.norm(G - Lo) / np.linalg.norm(Lo) <= 1e-12
+
+
+def test_profiler_counts_launches(E, ctx):
+    ctx.prof_enable(True)
+    A = E.emu_cov_build(ctx, 12, 3.0, 64)
+    E.emu_potrf_mp(ctx, A)
+    prof = ctx.prof_read()
+    ctx.prof_enable(False)
+    assert prof["cov"]["launches"] >= 1 and prof["potrf"]["launches"] >= 3
+    assert prof["update64"]["flops"] > 0 and prof["potrf"]["ms"] > 0

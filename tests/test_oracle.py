@@ -279,3 +279,12 @@ def test_potrs_solves():
     X = O.potrs(Lb, B)
     ref = np.linalg.solve(S, B)
     assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def test_blocked_steps_compose():
+    S = _spd(200, seed=9)
+    A1, _ = O.potrf_blocked(S, 64)
+    A2 = np.array(S, order="F", copy=True)
+    for k in range(4):
+        assert O.lib().orc_potrf_blocked_steps(200, 64, O._dp(A2), 200, k, k + 1) == 0
+    assert np.array_equal(np.tril(A2), A1)
