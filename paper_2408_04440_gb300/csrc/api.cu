@@ -137,6 +137,9 @@ emu_status emu_destroy(emu_ctx *ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  cudaFree(ctx->dag_tasks);
+  cudaFree(ctx->dag_ws);
+  cudaFree(ctx->trace_buf);
   mixed_ctx_release(ctx);
   delete ctx;
   return EMU_OK;
@@ -156,6 +159,24 @@ emu_status emu_prof_enable(emu_ctx *ctx, int on) {
     ctx->prof_ms[g] = ctx->prof_flops[g] = ctx->prof_bytes[g] = ctx->prof_mma[g] = 0.0;
   }
   ctx->prof = on != 0;
+  return EMU_OK;
+}
+
+emu_status emu_trace_enable(emu_ctx *ctx, int on) {
+  if (!ctx) return EMU_EINVAL;
+  ctx->trace_on = on != 0;
+  ctx->trace_records = 0;
+  return EMU_OK;
+}
+
+emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records, size_t *n_records) {
+  if (!ctx || !n_records) return EMU_EINVAL;
+  *n_records = ctx->trace_records;
+  if (!h_records || ctx->trace_records == 0) return EMU_OK;
+  size_t n = ctx->trace_records < max_records ? ctx->trace_records : max_records;
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(h_records, ctx->trace_buf, n * 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return EMU_OK;
 }
 

@@ -65,6 +65,20 @@ struct emu_ctx {
   int prof_launches[PROF_NGROUPS] = {};
   double prof_ms[PROF_NGROUPS] = {}, prof_flops[PROF_NGROUPS] = {}, prof_bytes[PROF_NGROUPS] = {};
   double prof_mma[PROF_NGROUPS] = {};
+  // mixed factor schedule: high-priority stream for the critical path
+  // (POTRF, TRSM, next-column update), low-priority stream for the bulk
+  // trailing update, and events ordering them
+  cudaStream_t crit = nullptr, bulk = nullptr;
+  std::vector<cudaEvent_t> sched_ev;
+  // dataflow POTRF of a diagonal tile: task list and workspace (per nb)
+  void *dag_tasks = nullptr;
+  int *dag_ws = nullptr;
+  size_t dag_ws_bytes = 0;
+  int dag_ntasks = 0, dag_nbb = 0;
+  // optional device-side task trace of the dataflow POTRF
+  bool trace_on = false;
+  unsigned long long *trace_buf = nullptr;
+  size_t trace_cap = 0, trace_records = 0;
 };
 
 // Brackets the launches issued during its lifetime with CUDA events on the

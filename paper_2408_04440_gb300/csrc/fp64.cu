@@ -6,6 +6,8 @@
 // GB300 runs FP64 on the SIMT pipe at about 2 DFMA per clock per SM (the FP64
 // MMA path measured slower), so these kernels are FP64-issue bound: the
 // register/shared-memory blocking below only has to keep that pipe busy.
+#include <vector>
+
 #include "emu_internal.h"
 
 namespace {
@@ -17,95 +19,215 @@ __device__ inline bool failed(const int *st) {
 }
 
 // ------------------------------------------------------------ POTRF (tile)
-// The diagonal tile D (nb x nb, column-major) is factored right-looking in
-// 32-wide steps s: leaf POTRF of block (s,s), TRSM of the blocks below it,
-// SYRK/GEMM of the trailing lower blocks.
+// FP64 Cholesky of one diagonal tile D (nb x nb, column-major) as a
+// persistent dataflow kernel over 16 x 16 blocks.  Tasks:
+//   LEAF(s)       apply panel s-1 to block (s,s), then factor it
+//   TRSM(r,s)     apply panel s-1 to block (r,s), then X_rs = D_rs L_ss^{-T}
+//   UPD(r,c,s)    D_rc -= X_rs X_cs^T for s + 2 <= c <= r
+// (a block's last update is fused into its LEAF / TRSM so the critical
+// chain LEAF(s) -> TRSM(s+1,s) -> LEAF(s+1) has two hops per step).  Tasks
+// are listed in a topological, lookahead-first order and fetched by the CTAs
+// through an atomic counter.  state[r*nbb + c] counts completed operations on
+// block (r,c): UPD by panels 0..c-2 take it to c-1, its LEAF/TRSM to c+1
+// (final).  Because tasks are fetched in topological order the earliest
+// unfinished task always has its inputs ready, so the kernel makes progress
+// whatever number of CTAs is resident.  Every wait is bounded (status
+// DEV_TIMEOUT) and every CTA leaves as soon as the status word reports a
+// failure.  Data written by other CTAs is read through L2 (ld.cg).
+// GB300 executes a dependent FP64 FMA in ~64 cycles and an FP64 rsqrt in
+// ~430, so the leaf keeps its block in registers (one lane per row) and
+// broadcasts the pivot column by shuffles.
+constexpr int PB = 16;
+enum { T_LEAF = 0, T_TRSM = 1, T_UPD = 2 };
+constexpr uint64_t kDagWaitNs = 2000000000ull;
 
-// Leaf: one warp factors the 32x32 block (s,s) in shared memory.
-__global__ void __launch_bounds__(32)
-    k_potrf_leaf(double *__restrict__ D, int nb, int s, int gcol0, int *st) {
-  if (failed(st)) return;
-  __shared__ double a[B][B + 1];
-  int lane = threadIdx.x;
-  double *blk = D + (size_t)s * B + (size_t)s * B * nb;
-  for (int c = 0; c < B; c++) a[lane][c] = (lane >= c) ? blk[lane + (size_t)c * nb] : 0.0;
-  __syncwarp();
-  for (int j = 0; j < B; j++) {
-    double d = a[j][j];
-    if (!(d > 0.0)) {  // also catches NaN
-      if (lane == 0) {
-        st[ST_PIVOT] = gcol0 + s * B + j + 1;
-        __threadfence();
-        atomicExch(&st[ST_CODE], DEV_NOTPD);
+__device__ inline uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 waits until state[idx] >= v (or failure / timeout).
+__device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
+  volatile const int *p = state + idx;
+  if (*p >= v) return true;
+  uint64_t t0 = gtimer();
+  while (true) {
+    if (*p >= v) return true;
+    if (*((volatile const int *)st) != DEV_OK) return false;
+    if (gtimer() - t0 > kDagWaitNs) {
+      if (atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 2;
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+__global__ void __launch_bounds__(PB * PB)
+    k_potrf_dag(double *__restrict__ D, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
+                int *__restrict__ ws, int *st, unsigned long long *__restrict__ trace) {
+  __shared__ double a[PB][PB + 1];   // the block being factored / solved against
+  __shared__ double xr[PB][PB + 1];  // panel rows of block r
+  __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
+  __shared__ double rinv[PB];
+  __shared__ int s_task, s_ok, bad;
+  int *counter = ws;
+  int *state = ws + 1;
+  const int nbb = nb / PB;
+  double *rinv_g = reinterpret_cast<double *>(ws + 2 + nbb * nbb + ((nbb * nbb) & 1));
+  const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
+  const size_t ld = nb;
+  while (true) {
+    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    int t = s_task;
+    if (t >= ntasks) return;
+    short4 tk = tasks[t];
+    int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LEAF: (s,s,s); TRSM: (r,s,s); UPD: (r,c,s)
+    unsigned long long t_fetch = 0;
+    if (trace && threadIdx.x == 0) t_fetch = gtimer();
+    if (threadIdx.x == 0) {
+      bool ok;
+      if (kind == T_LEAF)
+        ok = (s == 0 || dag_wait(state, s * nbb + (s - 1), s, st)) && dag_wait(state, s * nbb + s, s - 1, st);
+      else if (kind == T_TRSM)
+        ok = dag_wait(state, s * nbb + s, s + 1, st) && (s == 0 || dag_wait(state, r * nbb + (s - 1), s, st)) &&
+             dag_wait(state, r * nbb + s, s - 1, st);
+      else
+        ok = dag_wait(state, r * nbb + s, s + 1, st) && dag_wait(state, c * nbb + s, s + 1, st) &&
+             dag_wait(state, r * nbb + c, s, st);
+      __threadfence();
+      s_ok = ok;
+      bad = 0;
+      if (trace) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        unsigned long long *rec = trace + (size_t)t * 5;
+        rec[0] = (unsigned long long)kind | ((unsigned long long)r << 8) | ((unsigned long long)c << 24) |
+                 ((unsigned long long)s << 40);
+        rec[1] = smid;
+        rec[2] = t_fetch;
+        rec[3] = gtimer();
       }
-      return;
     }
-    d = sqrt(d);
-    __syncwarp();
-    if (lane == j) a[j][j] = d;
-    if (lane > j) a[lane][j] /= d;
-    __syncwarp();
-    if (lane > j) {
-      double lj = a[lane][j];
-      for (int c = j + 1; c <= lane; c++) a[lane][c] -= lj * a[c][j];
+    __syncthreads();
+    if (!s_ok) return;
+    if (kind == T_UPD) {
+      xr[ty][tx] = __ldcg(D + (size_t)(r * PB + ty) + (size_t)(s * PB + tx) * ld);
+      xc[ty][tx] = __ldcg(D + (size_t)(c * PB + ty) + (size_t)(s * PB + tx) * ld);
+      double *cp = D + (size_t)(r * PB + ty) + (size_t)(c * PB + tx) * ld;
+      double v = __ldcg(cp);
+      __syncthreads();
+      double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+      for (int p = 0; p < PB; p += 2) {
+        acc0 += xr[ty][p] * xc[tx][p];
+        acc1 += xr[ty][p + 1] * xc[tx][p + 1];
+      }
+      __stcg(cp, v - (acc0 + acc1));
+    } else {
+      // LEAF (r == s) and TRSM both first apply panel s-1 to their block
+      double *bp = D + (size_t)(r * PB + ty) + (size_t)(s * PB + tx) * ld;
+      double v = __ldcg(bp);
+      if (kind == T_TRSM) {
+        a[ty][tx] = __ldcg(D + (size_t)(s * PB + ty) + (size_t)(s * PB + tx) * ld);
+        if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + s * PB + threadIdx.x);
+      }
+      if (s > 0) {
+        xr[ty][tx] = __ldcg(D + (size_t)(r * PB + ty) + (size_t)((s - 1) * PB + tx) * ld);
+        xc[ty][tx] = __ldcg(D + (size_t)(s * PB + ty) + (size_t)((s - 1) * PB + tx) * ld);
+      }
+      __syncthreads();
+      if (s > 0) {
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int p = 0; p < PB; p += 2) {
+          acc0 += xr[ty][p] * xc[tx][p];
+          acc1 += xr[ty][p + 1] * xc[tx][p + 1];
+        }
+        v -= acc0 + acc1;
+      }
+      if (kind == T_LEAF) {
+        a[ty][tx] = v;
+        __syncthreads();
+        // warp 0, lane l < 16 holds row l of the block in registers
+        if (threadIdx.x < 32) {
+          int lane = threadIdx.x;
+          int row = lane & (PB - 1);
+          double x[PB];
+#pragma unroll
+          for (int q = 0; q < PB; q++) x[q] = a[row][q];
+          int fail = 0;
+#pragma unroll
+          for (int j = 0; j < PB; j++) {
+            double d = __shfl_sync(0xffffffffu, x[j], j);  // pivot from lane j
+            if (!(d > 0.0) && !fail) fail = j + 1;  // also catches NaN; same in every lane
+            if (fail) d = 1.0;  // keep going without branching; the result is discarded
+            double rs = rsqrt(d);
+            double l = (row == j) ? d * rs : x[j] * rs;  // L[row][j]
+            x[j] = (row >= j) ? l : x[j];
+            if (lane == 0) rinv[j] = rs;
+            double lm = (row > j) ? l : 0.0;
+            // branch-free rank-1 update keeps x[] in registers
+#pragma unroll
+            for (int q = j + 1; q < PB; q++) {
+              double lq = __shfl_sync(0xffffffffu, l, q);  // L[q][j]
+              x[q] = fma(-((row >= q) ? lm : 0.0), lq, x[q]);
+            }
+          }
+          if (fail) {
+            if (lane == 0) bad = fail;
+          } else if (lane < PB) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) a[row][q] = x[q];
+          }
+        }
+        __syncthreads();
+        if (bad) {
+          if (threadIdx.x == 0) {
+            st[ST_PIVOT] = gcol0 + s * PB + bad;
+            __threadfence();
+            atomicExch(&st[ST_CODE], DEV_NOTPD);
+          }
+          return;
+        }
+        if (ty >= tx) __stcg(bp, a[ty][tx]);
+        if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
+      } else {
+        // solve row ty of block (r,s) against L_ss; the 16 lanes of a row
+        // exchange solved entries by shuffle
+#pragma unroll
+        for (int j = 0; j < PB; j++) {
+          double xj = __shfl_sync(0xffffffffu, v, j, PB) * rinv[j];
+          if (tx == j) v = xj;
+          if (tx > j) v -= xj * a[tx][j];
+        }
+        __stcg(bp, v);
+      }
     }
-    __syncwarp();
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(&state[r * nbb + c], s + 1);
+      if (trace) trace[(size_t)t * 5 + 4] = gtimer();
+    }
   }
-  for (int c = 0; c <= lane; c++) blk[lane + (size_t)c * nb] = a[lane][c];
 }
 
-// Rows below block s inside the tile: X = D[rows, s] * L_ss^{-T}.  One warp
-// per 32-row block; lane r solves row r by forward substitution.
-__global__ void __launch_bounds__(32)
-    k_potrf_inner_trsm(double *__restrict__ D, int nb, int s, const int *st) {
-  if (failed(st)) return;
-  __shared__ double l[B][B + 1];
-  __shared__ double x[B][B + 1];
-  int lane = threadIdx.x;
-  int r0 = (s + 1 + blockIdx.x) * B;
-  const double *ls = D + (size_t)s * B + (size_t)s * B * nb;
-  double *xs = D + r0 + (size_t)s * B * nb;
-  for (int c = 0; c < B; c++) {
-    l[lane][c] = ls[lane + (size_t)c * nb];
-    x[lane][c] = xs[lane + (size_t)c * nb];
+// Task list of the dataflow POTRF for nbb blocks per side (see k_potrf_dag).
+static void dag_tasks(int nbb, std::vector<short4> &out) {
+  out.clear();
+  auto push = [&](int kind, int r, int c, int s) {
+    out.push_back(make_short4((short)kind, (short)r, (short)c, (short)s));
+  };
+  push(T_LEAF, 0, 0, 0);
+  for (int r = 1; r < nbb; r++) push(T_TRSM, r, 0, 0);
+  for (int s = 0; s + 1 < nbb; s++) {
+    push(T_LEAF, s + 1, s + 1, s + 1);
+    for (int r = s + 2; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
+    for (int c = s + 2; c < nbb; c++)
+      for (int r = c; r < nbb; r++) push(T_UPD, r, c, s);
   }
-  __syncwarp();
-  for (int c = 0; c < B; c++) {
-    double v = x[lane][c];
-    for (int p = 0; p < c; p++) v -= x[lane][p] * l[c][p];
-    x[lane][c] = v / l[c][c];
-  }
-  __syncwarp();
-  for (int c = 0; c < B; c++) xs[lane + (size_t)c * nb] = x[lane][c];
-}
-
-// Trailing lower blocks (bi >= bj) inside the tile:
-// D[bi, bj] -= X_bi X_bj^T, X_b = D[block b rows, s-block columns].
-__global__ void __launch_bounds__(256)
-    k_potrf_inner_syrk(double *__restrict__ D, int nb, int s, const int *st) {
-  int bi = s + 1 + blockIdx.x, bj = s + 1 + blockIdx.y;
-  if (bi < bj || failed(st)) return;
-  __shared__ double xi[B][B + 1];
-  __shared__ double xj[B][B + 1];
-  int t = threadIdx.x;
-  int c = t % B, rr = t / B;  // rr in 0..7
-  const double *pi = D + (size_t)bi * B + (size_t)s * B * nb;
-  const double *pj = D + (size_t)bj * B + (size_t)s * B * nb;
-  for (int q = 0; q < 4; q++) {
-    int p = rr + 8 * q;  // column of the panel
-    xi[c][p] = pi[c + (size_t)p * nb];
-    xj[c][p] = pj[c + (size_t)p * nb];
-  }
-  __syncthreads();
-  double acc[4] = {0, 0, 0, 0};
-  for (int p = 0; p < B; p++) {
-    double bjv = xj[c][p];
-#pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] += xi[rr + 8 * q][p] * bjv;
-  }
-  double *cb = D + (size_t)bi * B + (size_t)bj * B * nb;
-#pragma unroll
-  for (int q = 0; q < 4; q++) cb[(rr + 8 * q) + (size_t)c * nb] -= acc[q];
 }
 
 // ------------------------------------------------------------ panel TRSM
@@ -365,19 +487,52 @@ __global__ void k_solve_diag(const double *__restrict__ t64, int nb, int NT, int
 
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   int nb = A->nb, NT = A->nt;
-  double *D = A->t64 + (size_t)tile_index(k, k, NT) * nb * nb;
-  int nbb = nb / B;
-  ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
-  for (int s = 0; s < nbb; s++) {
-    k_potrf_leaf<<<1, 32, 0, ctx->stream>>>(D, nb, s, k * nb, ctx->d_status);
-    EMU_LAUNCHED(ctx);
-    int m = nbb - s - 1;
-    if (m == 0) break;
-    k_potrf_inner_trsm<<<m, 32, 0, ctx->stream>>>(D, nb, s, ctx->d_status);
-    EMU_LAUNCHED(ctx);
-    k_potrf_inner_syrk<<<dim3(m, m), 256, 0, ctx->stream>>>(D, nb, s, ctx->d_status);
-    EMU_LAUNCHED(ctx);
+  int nbb = nb / PB;
+  if (ctx->dag_nbb != nbb) {
+    std::vector<short4> tasks;
+    dag_tasks(nbb, tasks);
+    cudaFree(ctx->dag_tasks);
+    cudaFree(ctx->dag_ws);
+    ctx->dag_tasks = nullptr;
+    ctx->dag_ws = nullptr;
+    ctx->dag_nbb = 0;
+    EMU_CUDA_TRY(ctx, cudaMalloc(&ctx->dag_tasks, tasks.size() * sizeof(short4)));
+    EMU_CUDA_TRY(ctx, cudaMemcpy(ctx->dag_tasks, tasks.data(), tasks.size() * sizeof(short4),
+                                 cudaMemcpyHostToDevice));
+    // counter, state[nbb*nbb], alignment pad, rinv[nb] doubles
+    ctx->dag_ws_bytes = (size_t)(2 + nbb * nbb + 1) * sizeof(int) + (size_t)nb * sizeof(double);
+    EMU_CUDA_TRY(ctx, cudaMalloc(&ctx->dag_ws, ctx->dag_ws_bytes));
+    ctx->dag_ntasks = (int)tasks.size();
+    ctx->dag_nbb = nbb;
   }
+  double *D = A->t64 + (size_t)tile_index(k, k, NT) * nb * nb;
+  ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
+  size_t state_bytes = (size_t)(1 + nbb * nbb) * sizeof(int);
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dag_ws, 0, state_bytes, ctx->stream));
+  int grid = ctx->sm_count < ctx->dag_ntasks ? ctx->sm_count : ctx->dag_ntasks;
+  unsigned long long *trace = nullptr;
+  if (ctx->trace_on) {
+    size_t need = (size_t)(k + 1) * ctx->dag_ntasks * 5;
+    if (need > ctx->trace_cap) {
+      // grow: keep earlier tiles' records of this factor
+      unsigned long long *nt = nullptr;
+      size_t cap = need * 2;
+      EMU_CUDA_TRY(ctx, cudaMallocAsync((void **)&nt, cap * sizeof(unsigned long long), ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), ctx->stream));
+      if (ctx->trace_buf) {
+        EMU_CUDA_TRY(ctx, cudaMemcpyAsync(nt, ctx->trace_buf, ctx->trace_cap * sizeof(unsigned long long),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+        cudaFreeAsync(ctx->trace_buf, ctx->stream);
+      }
+      ctx->trace_buf = nt;
+      ctx->trace_cap = cap;
+    }
+    trace = ctx->trace_buf + (size_t)k * ctx->dag_ntasks * 5;
+    ctx->trace_records = (size_t)(k + 1) * ctx->dag_ntasks;
+  }
+  k_potrf_dag<<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks, ctx->dag_ntasks,
+                                                ctx->dag_ws, ctx->d_status, trace);
+  EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
 

@@ -205,16 +205,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + ch * 32, r);
         tc::tmem_ld_wait();
+        // all 32 loads of the chunk are issued before any store, so their
+        // latencies overlap (each warp-wide access is one 128-byte column piece)
         if (mode == TC_SUB_F32) {
           float *o = out32 + item.out_off + row + (long)(ch * 32) * ldo;
+          float c[32];
 #pragma unroll
-          for (int x = 0; x < 32; x++) o[(long)x * ldo] -= __uint_as_float(r[x]);
+          for (int x = 0; x < 32; x++) c[x] = __ldcg(o + (long)x * ldo);
+#pragma unroll
+          for (int x = 0; x < 32; x++) __stcg(o + (long)x * ldo, c[x] - __uint_as_float(r[x]));
         } else {
           if (row < item.rows_valid) {
             double *o = out64 + item.out_off + row + (long)(ch * 32) * ldo;
+            int nval = item.cols_valid - ch * 32;
+            double c[32];
+#pragma unroll
+            for (int x = 0; x < 32; x++) c[x] = (x < nval) ? __ldcg(o + (long)x * ldo) : 0.0;
 #pragma unroll
             for (int x = 0; x < 32; x++)
-              if (ch * 32 + x < item.cols_valid) o[(long)x * ldo] += (double)__uint_as_float(r[x]);
+              if (x < nval) __stcg(o + (long)x * ldo, c[x] + (double)__uint_as_float(r[x]));
           }
         }
       }

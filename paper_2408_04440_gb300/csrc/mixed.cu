@@ -67,6 +67,16 @@ __global__ void k_tile_to_f64(const float *__restrict__ s, double *__restrict__ 
     d[e] = (double)s[e];
 }
 
+// FP32 copy of the FP64 diagonal factor tile L_kk for the FP32 panel TRSM
+// (converted once here instead of by every TRSM CTA).
+__global__ void k_diag_to_f32(const double *__restrict__ s, float *__restrict__ d, size_t tile_elems,
+                              const int *st) {
+  if (failed(st)) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tile_elems;
+       e += (size_t)gridDim.x * blockDim.x)
+    d[e] = (float)s[e];
+}
+
 // Three BF16 pieces, row-major, of whole tiles from their FP64 (or FP32)
 // masters.  One CTA per (32x32 block, listed tile); lower_only zeroes the
 // strict upper triangle (diagonal tiles).
@@ -100,74 +110,92 @@ __global__ void k_split_tiles(const T *__restrict__ src, uint16_t *__restrict__ 
 // FP32 panel TRSM for the low-precision tiles of column k:
 // L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and the FP64 L_kk (read as
 // FP32), written back to the master and, split, to the operand arena.
+// One CTA per (32-row block, tile): the 32 rows stay in shared memory; for
+// each 32-column block cb the already-solved columns are subtracted (a small
+// GEMM against L_kk blocks staged in shared memory), then warp w solves rows
+// 4w..4w+3 against the 32x32 diagonal block by forward substitution, one
+// lane per column, with shuffles (no block-wide barrier inside the solve).
+constexpr int TS_LD_PAD = 4;
+constexpr int TS_STRIP = 512;  // columns of L_kk staged at once
 __global__ void __launch_bounds__(256)
-    k_trsm32_panel(const double *__restrict__ t64, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
+    k_trsm32_panel(const float *__restrict__ Lkk, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
                    int NT, int k, const int *__restrict__ rows, const int *st) {
   if (failed(st)) return;
-  __shared__ float xp[B][B + 1];
-  __shared__ float lc[B][B + 1];
-  __shared__ float sx[B][B + 1];
+  extern __shared__ float sm[];
+  const int ldx = nb + TS_LD_PAD;
+  const int lds = TS_STRIP + 1;
+  float *X = sm;              // [32][ldx]: the CTA's rows of A_ik, solved in place
+  float *S = X + 32 * ldx;    // [32][lds]: strip of L_kk rows cb*32 + lane, up to TS_STRIP columns
   int i = rows[blockIdx.y];
   int r0 = blockIdx.x * B;
   long ti = tile_index(i, k, NT);
-  const double *Lkk = t64 + (size_t)tile_index(k, k, NT) * nb * nb;
-  float *X = t32 + (size_t)ti * nb * nb + r0;
-  size_t plane = (size_t)nb * nb;
-  uint16_t *P = op + (size_t)ti * 3 * plane;
-  int t = threadIdx.x;
-  int c = t % B, rr = t / B;
+  float *A = t32 + (size_t)ti * nb * nb + r0;
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < 32 * nb; e += 256) {
+    int r = e & 31, c = e >> 5;
+    X[r * ldx + c] = A[r + (size_t)c * nb];
+  }
   int nbb = nb / B;
   for (int cb = 0; cb < nbb; cb++) {
-    float acc[4];
+    const float *Lrow = Lkk + cb * B + lane;  // row cb*32 + lane of L_kk
+    float ld[B];
 #pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] = X[(rr + 8 * q) + (size_t)(cb * B + c) * nb];
-    for (int pb = 0; pb < cb; pb++) {
+    for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.f;
+    float acc[4];
+    __syncthreads();  // X of the previous column blocks is complete
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[q] = X[(4 * w + q) * ldx + cb * B + lane];
+    for (int p0 = 0; p0 < cb * B; p0 += TS_STRIP) {
+      int pw = min(TS_STRIP, cb * B - p0);
+      // the strip chunk: all loads issued together
+      for (int p = w; p < pw; p += 8) S[lane * lds + p] = Lrow[(size_t)(p0 + p) * nb];
       __syncthreads();
+#pragma unroll 4
+      for (int p = 0; p < pw; p++) {
+        float l = S[lane * lds + p];
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[q] -= X[(4 * w + q) * ldx + p0 + p] * l;
+      }
+      __syncthreads();
+    }
+    float mydiag = ld[0];
+#pragma unroll
+    for (int p = 1; p < B; p++)
+      if (p == lane) mydiag = ld[p];
+    float myrinv = 1.0f / mydiag;
+#pragma unroll
+    for (int j = 0; j < B; j++) {
+      float rj = __shfl_sync(0xffffffffu, myrinv, j);
 #pragma unroll
       for (int q = 0; q < 4; q++) {
-        int p = rr + 8 * q;
-        xp[c][p] = X[c + (size_t)(pb * B + p) * nb];
-        lc[c][p] = (float)Lkk[(cb * B + c) + (size_t)(pb * B + p) * nb];
-      }
-      __syncthreads();
-      for (int p = 0; p < B; p++) {
-        float lv = lc[c][p];
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[q] -= xp[rr + 8 * q][p] * lv;
+        float xj = __shfl_sync(0xffffffffu, acc[q], j) * rj;
+        if (lane == j) acc[q] = xj;
+        if (lane > j) acc[q] -= xj * ld[j];
       }
     }
-    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      sx[rr + 8 * q][c] = acc[q];
-      int p = rr + 8 * q;
-      lc[c][p] = (float)Lkk[(cb * B + c) + (size_t)(cb * B + p) * nb];
-    }
-    __syncthreads();
-    if (t < B) {
-      for (int cc = 0; cc < B; cc++) {
-        float v = sx[t][cc];
-        for (int p = 0; p < cc; p++) v -= sx[t][p] * lc[cc][p];
-        sx[t][cc] = v / lc[cc][cc];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; q++) X[(rr + 8 * q) + (size_t)(cb * B + c) * nb] = sx[rr + 8 * q][c];
-    // sender-side conversion: row-major pieces of row (r0 + rr + 8q), column c
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int r = rr + 8 * q;
-      uint16_t p0, p1, p2;
-      split3(sx[r][c], p0, p1, p2);
-      size_t off = (size_t)(r0 + r) * nb + cb * B + c;
-      P[off] = p0;
-      P[plane + off] = p1;
-      P[2 * plane + off] = p2;
-    }
-    __syncthreads();
+    for (int q = 0; q < 4; q++) X[(4 * w + q) * ldx + cb * B + lane] = acc[q];
+  }
+  __syncthreads();
+  // FP32 master (column-major) and the sender-side BF16 pieces (row-major)
+  for (int e = tid; e < 32 * nb; e += 256) {
+    int r = e & 31, c = e >> 5;
+    A[r + (size_t)c * nb] = X[r * ldx + c];
+  }
+  size_t plane = (size_t)nb * nb;
+  uint16_t *P = op + (size_t)ti * 3 * plane + (size_t)r0 * nb;
+  for (int e = tid; e < 32 * nb; e += 256) {
+    int r = e / nb, c = e % nb;
+    uint16_t p0, p1, p2;
+    split3(X[r * ldx + c], p0, p1, p2);
+    size_t off = (size_t)r * nb + c;
+    P[off] = p0;
+    P[plane + off] = p1;
+    P[2 * plane + off] = p2;
   }
 }
+
+static size_t trsm32_smem(int nb) { return (size_t)(32 * (nb + TS_LD_PAD) + 32 * (TS_STRIP + 1)) * sizeof(float); }
 
 // FP64-class trailing tiles: C_ij -= L_ik L_jk^T in FP64; each operand comes
 // from the FP64 master or (widened) from the FP32 master, by its class.
@@ -313,6 +341,7 @@ struct MixedPlan {
   std::vector<unsigned char> cls;  // packed by tile index
   // per step k: offsets into the concatenated device lists
   std::vector<int> off_t64rows, off_t32rows, off_pairs, off_items;
+  std::vector<int> g1_pairs, g1_items;  // leading entries of a step that update column k+1
   std::vector<int> diag_low;       // class(k,k) != FP64
   std::vector<double> step_flops, step_mma;  // tensor-core work of each step
   int *d_rows64 = nullptr, *d_rows32 = nullptr;
@@ -321,6 +350,7 @@ struct MixedPlan {
   gemm_tc::Seg *d_segs = nullptr;
   int *d_tiles_fp64_panel = nullptr;  // FP64-class off-diagonal tiles (split after their TRSM)
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
+  float *d_lkk32 = nullptr;           // FP32 copy of the current L_kk
   CUtensorMap mapA, mapB;
   double update_flops[EMU_NCLASS] = {};
   int tiles[EMU_NCLASS] = {};
@@ -335,6 +365,7 @@ static void plan_free(MixedPlan *p) {
   cudaFree(p->d_segs);
   cudaFree(p->d_tiles_fp64_panel);
   cudaFree(p->d_diag_tiles);
+  cudaFree(p->d_lkk32);
   delete p;
 }
 
@@ -376,6 +407,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     P->off_pairs.push_back((int)pairs.size());
     P->off_items.push_back((int)items.size());
     double sf = 0.0, sm = 0.0;
+    int g1p = 0, g1i = 0;
     for (int i = k + 1; i < NT; i++) {
       if (C(i, k) == EMU_CLASS_FP64) {
         rows64.push_back(i);
@@ -390,6 +422,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         int c = C(i, j);
         if (c == EMU_CLASS_FP64) {
           pairs.push_back(make_int2(i, j));
+          if (j == k + 1) g1p++;
           continue;
         }
         int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;  // TF32/E4M3 fall back
@@ -416,8 +449,11 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
             double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
             sf += f;
             sm += f * (cc == EMU_CLASS_FP32 ? 6.0 : 1.0);
+            if (j == k + 1) g1i++;
           }
       }
+    P->g1_pairs.push_back(g1p);
+    P->g1_items.push_back(g1i);
     P->step_flops.push_back(sf);
     P->step_mma.push_back(sm);
   }
@@ -433,9 +469,27 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   if ((s = upload(ctx, &P->d_segs, segs)) != EMU_OK) return s;
   if ((s = upload(ctx, &P->d_tiles_fp64_panel, fp64panel)) != EMU_OK) return s;
   if ((s = upload(ctx, &P->d_diag_tiles, diag)) != EMU_OK) return s;
+  EMU_CUDA_TRY(ctx, cudaMalloc(&P->d_lkk32, (size_t)nb * nb * sizeof(float)));
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapA, A->op_bf16, nb, rows, gemm_tc::BM)) != EMU_OK) return s;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapB, A->op_bf16, nb, rows, gemm_tc::BN)) != EMU_OK) return s;
+  return EMU_OK;
+}
+
+// Internal streams of the mixed schedule (created once per context) and at
+// least `nev` ordering events.
+static emu_status sched_streams(emu_ctx *ctx, int nev) {
+  if (!ctx->crit) {
+    int least = 0, greatest = 0;
+    EMU_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    EMU_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->crit, cudaStreamNonBlocking, greatest));
+    EMU_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->bulk, cudaStreamNonBlocking, least));
+  }
+  while ((int)ctx->sched_ev.size() < nev) {
+    cudaEvent_t e;
+    EMU_CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->sched_ev.push_back(e);
+  }
   return EMU_OK;
 }
 
@@ -471,18 +525,30 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     k_to_f32<<<dim3(64, (unsigned)A->ntiles), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, te);
     EMU_LAUNCHED(ctx);
   }
+  // Lookahead-1 schedule.  Critical stream: POTRF(k), TRSM(:,k), then the
+  // update of column k+1 by panel k (G1), which feeds POTRF(k+1).  Bulk
+  // stream: the update of columns >= k+2 by panel k (G2), overlapping the
+  // next panel.  G1(k) must not overlap G2(k-1) (both write column k+1).
+  cudaStream_t user = ctx->stream;
+  if ((s = sched_streams(ctx, 2 * NT + 2)) != EMU_OK) return s;
+  cudaEvent_t ev_start = ctx->sched_ev[2 * NT], ev_bulk_end = ctx->sched_ev[2 * NT + 1];
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_start, user));
+  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev_start, 0));
+  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev_start, 0));
   for (int k = 0; k < NT; k++) {
+    cudaEvent_t ev_trsm = ctx->sched_ev[2 * k], ev_g2 = ctx->sched_ev[2 * k + 1];
     long tkk = tile_index(k, k, NT);
+    ctx->stream = ctx->crit;
     if (P->diag_low[k]) {
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * te);
       k_tile_to_f64<<<64, 256, 0, ctx->stream>>>(A->t32 + tkk * te, A->t64 + tkk * te, te, st);
       EMU_LAUNCHED(ctx);
     }
-    if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) return s;
+    if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) break;
     int n64 = P->off_t64rows[k + 1] - P->off_t64rows[k];
     int n32 = P->off_t32rows[k + 1] - P->off_t32rows[k];
     if (n64 > 0) {
-      if ((s = launch_trsm64_panel(ctx, A, k, P->d_rows64 + P->off_t64rows[k], n64)) != EMU_OK) return s;
+      if ((s = launch_trsm64_panel(ctx, A, k, P->d_rows64 + P->off_t64rows[k], n64)) != EMU_OK) break;
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
       k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(
           A->t64, A->op_bf16, P->d_tiles_fp64_panel + P->off_t64rows[k], nb, 0, st);
@@ -490,25 +556,49 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     }
     if (n32 > 0) {
       ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
-      k_trsm32_panel<<<dim3(nb / B, n32), 256, 0, ctx->stream>>>(A->t64, A->t32, A->op_bf16, nb, NT, k,
-                                                                P->d_rows32 + P->off_t32rows[k], st);
+      k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te, P->d_lkk32, te, st);
+      EMU_LAUNCHED(ctx);
+      size_t sm = trsm32_smem(nb);
+      EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_trsm32_panel<<<dim3(nb / B, n32), 256, sm, ctx->stream>>>(P->d_lkk32, A->t32, A->op_bf16, nb, NT, k,
+                                                                  P->d_rows32 + P->off_t32rows[k], st);
       EMU_LAUNCHED(ctx);
     }
-    int np = P->off_pairs[k + 1] - P->off_pairs[k];
-    if (np > 0) {
-      ProfScope ps(ctx, PROF_UPDATE64, 2.0 * np * nb3, 24.0 * np * te);
-      k_update64_list<<<dim3(np, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
-          A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + P->off_pairs[k], st);
-      EMU_LAUNCHED(ctx);
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev_trsm, ctx->crit));
+    if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ctx->sched_ev[2 * (k - 1) + 1], 0));
+    int p0 = P->off_pairs[k], np = P->off_pairs[k + 1] - p0, np1 = P->g1_pairs[k];
+    int i0 = P->off_items[k], ni = P->off_items[k + 1] - i0, ni1 = P->g1_items[k];
+    // G1 on the critical stream, G2 on the bulk stream
+    for (int part = 0; part < 2 && s == EMU_OK; part++) {
+      ctx->stream = part == 0 ? ctx->crit : ctx->bulk;
+      if (part == 1) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev_trsm, 0));
+      int pb = part == 0 ? p0 : p0 + np1, pn = part == 0 ? np1 : np - np1;
+      int ib = part == 0 ? i0 : i0 + ni1, in = part == 0 ? ni1 : ni - ni1;
+      if (pn > 0) {
+        ProfScope ps(ctx, PROF_UPDATE64, 2.0 * pn * nb3, 24.0 * pn * te);
+        k_update64_list<<<dim3(pn, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, nb, NT,
+                                                                                 k, P->d_pairs + pb, st);
+        EMU_LAUNCHED(ctx);
+      }
+      if (in > 0) {
+        double fr = (double)in / ni;
+        ProfScope ps(ctx, PROF_TC_FACTOR, P->step_flops[k] * fr, 0.0, P->step_mma[k] * fr);
+        // short-lived CTAs on the bulk stream (at most 4 items each) let the
+        // critical stream's CTAs take SMs as they free up
+        int ctas = part == 0 ? ctx->sm_count : std::max(1, (in + 3) / 4);
+        s = gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + ib, in, P->d_segs, nb / gemm_tc::BK,
+                            gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctas);
+      }
     }
-    int ni = P->off_items[k + 1] - P->off_items[k];
-    if (ni > 0) {
-      ProfScope ps(ctx, PROF_TC_FACTOR, P->step_flops[k], 0.0, P->step_mma[k]);
-      s = gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + P->off_items[k], ni, P->d_segs, nb / gemm_tc::BK,
-                          gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctx->sm_count);
-      if (s != EMU_OK) return s;
-    }
+    if (s != EMU_OK) break;
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev_g2, ctx->bulk));
   }
+  ctx->stream = user;
+  if (s != EMU_OK) return s;
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_bulk_end, ctx->bulk));
+  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev_bulk_end, 0));
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_bulk_end, ctx->crit));
+  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ev_bulk_end, 0));
   if ((s = launch_tril_diag(ctx, A)) != EMU_OK) return s;
   // pieces of the (lower-triangular) diagonal factor tiles, for the sampler
   ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * NT * te);
@@ -631,4 +721,10 @@ emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int 
   return EMU_OK;
 }
 
-void mixed_ctx_release(emu_ctx *) {}
+void mixed_ctx_release(emu_ctx *ctx) {
+  for (cudaEvent_t e : ctx->sched_ev) cudaEventDestroy(e);
+  ctx->sched_ev.clear();
+  if (ctx->crit) cudaStreamDestroy(ctx->crit);
+  if (ctx->bulk) cudaStreamDestroy(ctx->bulk);
+  ctx->crit = ctx->bulk = nullptr;
+}
