@@ -141,7 +141,8 @@ emu_status emu_prof_enable(emu_ctx *ctx, int on);
 /* Device-side task trace of the dataflow FP64 POTRF of the diagonal tiles
  * (off by default).  While enabled, each factor records, for every task of
  * every diagonal tile (tile k's records follow tile k-1's), five 64-bit words:
- * kind | r << 8 | c << 24 | s << 40 (kind 0 = leaf, 1 = TRSM, 2 = update of
+ * kind | r << 8 | c << 24 | s << 40 (kind 0 = leaf with its sub-diagonal
+ * solve, 1 = TRSM, 2 = update of
  * 16x16 block (r,c) by panel s), the SM id, and %globaltimer nanoseconds when
  * the task was fetched, when its inputs were ready, and when it completed.
  * emu_trace_read copies up to max_records records to host memory and reports

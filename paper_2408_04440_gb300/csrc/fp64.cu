@@ -21,24 +21,26 @@ __device__ inline bool failed(const int *st) {
 // ------------------------------------------------------------ POTRF (tile)
 // FP64 Cholesky of one diagonal tile D (nb x nb, column-major) as a
 // persistent dataflow kernel over 16 x 16 blocks.  Tasks:
-//   LEAF(s)       apply panel s-1 to block (s,s), then factor it
-//   TRSM(r,s)     apply panel s-1 to block (r,s), then X_rs = D_rs L_ss^{-T}
-//   UPD(r,c,s)    D_rc -= X_rs X_cs^T for s + 2 <= c <= r
-// (a block's last update is fused into its LEAF / TRSM so the critical
-// chain LEAF(s) -> TRSM(s+1,s) -> LEAF(s+1) has two hops per step).  Tasks
+//   LT(s)      solve the sub-diagonal block X_{s,s-1} = D_{s,s-1} L_{s-1,s-1}^{-T}
+//              (after applying panel s-2 to it), apply it to the diagonal
+//              block (s,s), and factor that block (the leaf);
+//   TRSM(r,s)  r >= s+2: apply panel s-1 to block (r,s), then solve it;
+//   UPD(r,c,s) c >= s+2: D_rc -= X_rs X_cs^T.
+// A block's last update is fused into the task that finalises it, so the
+// critical chain is LT(s) -> LT(s+1): one task per 16-column step.  Tasks
 // are listed in a topological, lookahead-first order and fetched by the CTAs
 // through an atomic counter.  state[r*nbb + c] counts completed operations on
-// block (r,c): UPD by panels 0..c-2 take it to c-1, its LEAF/TRSM to c+1
-// (final).  Because tasks are fetched in topological order the earliest
-// unfinished task always has its inputs ready, so the kernel makes progress
-// whatever number of CTAs is resident.  Every wait is bounded (status
-// DEV_TIMEOUT) and every CTA leaves as soon as the status word reports a
-// failure.  Data written by other CTAs is read through L2 (ld.cg).
+// block (r,c) (final value c+1).  Because tasks are fetched in topological
+// order the earliest unfinished task always has its inputs ready, so the
+// kernel makes progress whatever number of CTAs is resident.  Every wait is
+// bounded (status DEV_TIMEOUT) and every CTA leaves as soon as the status
+// word reports a failure.  Data written by other CTAs is read through L2.
 // GB300 executes a dependent FP64 FMA in ~64 cycles and an FP64 rsqrt in
-// ~430, so the leaf keeps its block in registers (one lane per row) and
-// broadcasts the pivot column by shuffles.
+// ~430, so the leaf keeps its block in registers (one lane per row), the
+// pivot column is broadcast by shuffles, and solves use L scaled by the
+// pivot reciprocals (one dependent FMA per substitution step).
 constexpr int PB = 16;
-enum { T_LEAF = 0, T_TRSM = 1, T_UPD = 2 };
+enum { T_LT = 0, T_TRSM = 1, T_UPD = 2 };
 constexpr uint64_t kDagWaitNs = 2000000000ull;
 
 __device__ inline uint64_t gtimer() {
@@ -63,10 +65,22 @@ __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
   }
 }
 
+// 16x16 products of panel rows: sum_p A[ty][p] B[tx][p], two chains.
+__device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)[PB + 1], int ty, int tx) {
+  double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+  for (int p = 0; p < PB; p += 2) {
+    acc0 += A[ty][p] * Bm[tx][p];
+    acc1 += A[ty][p + 1] * Bm[tx][p + 1];
+  }
+  return acc0 + acc1;
+}
+
 __global__ void __launch_bounds__(PB * PB)
     k_potrf_dag(double *__restrict__ D, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
                 int *__restrict__ ws, int *st, unsigned long long *__restrict__ trace) {
-  __shared__ double a[PB][PB + 1];   // the block being factored / solved against
+  __shared__ double a[PB][PB + 1];   // L of the block solved against, then the block factored
+  __shared__ double m[PB][PB + 1];   // L scaled by the pivot reciprocals (solves)
   __shared__ double xr[PB][PB + 1];  // panel rows of block r
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
@@ -77,19 +91,22 @@ __global__ void __launch_bounds__(PB * PB)
   double *rinv_g = reinterpret_cast<double *>(ws + 2 + nbb * nbb + ((nbb * nbb) & 1));
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
+  auto blk = [&](int br, int bc) { return D + (size_t)(br * PB + ty) + (size_t)(bc * PB + tx) * ld; };
   while (true) {
     if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
     int t = s_task;
     if (t >= ntasks) return;
     short4 tk = tasks[t];
-    int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LEAF: (s,s,s); TRSM: (r,s,s); UPD: (r,c,s)
+    int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LT: (s, s-1, s); TRSM: (r, s, s); UPD: (r, c, s)
     unsigned long long t_fetch = 0;
     if (trace && threadIdx.x == 0) t_fetch = gtimer();
     if (threadIdx.x == 0) {
       bool ok;
-      if (kind == T_LEAF)
-        ok = (s == 0 || dag_wait(state, s * nbb + (s - 1), s, st)) && dag_wait(state, s * nbb + s, s - 1, st);
+      if (kind == T_LT)
+        ok = (s == 0) || (dag_wait(state, (s - 1) * nbb + (s - 1), s, st) &&
+                          (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
+                          dag_wait(state, s * nbb + (s - 1), s - 2, st));
       else if (kind == T_TRSM)
         ok = dag_wait(state, s * nbb + s, s + 1, st) && (s == 0 || dag_wait(state, r * nbb + (s - 1), s, st)) &&
              dag_wait(state, r * nbb + s, s - 1, st);
@@ -113,73 +130,86 @@ __global__ void __launch_bounds__(PB * PB)
     __syncthreads();
     if (!s_ok) return;
     if (kind == T_UPD) {
-      xr[ty][tx] = __ldcg(D + (size_t)(r * PB + ty) + (size_t)(s * PB + tx) * ld);
-      xc[ty][tx] = __ldcg(D + (size_t)(c * PB + ty) + (size_t)(s * PB + tx) * ld);
-      double *cp = D + (size_t)(r * PB + ty) + (size_t)(c * PB + tx) * ld;
+      xr[ty][tx] = __ldcg(blk(r, s));
+      xc[ty][tx] = __ldcg(blk(c, s));
+      double *cp = blk(r, c);
       double v = __ldcg(cp);
       __syncthreads();
-      double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll
-      for (int p = 0; p < PB; p += 2) {
-        acc0 += xr[ty][p] * xc[tx][p];
-        acc1 += xr[ty][p + 1] * xc[tx][p + 1];
-      }
-      __stcg(cp, v - (acc0 + acc1));
+      __stcg(cp, v - panel_dot(xr, xc, ty, tx));
     } else {
-      // LEAF (r == s) and TRSM both first apply panel s-1 to their block
-      double *bp = D + (size_t)(r * PB + ty) + (size_t)(s * PB + tx) * ld;
-      double v = __ldcg(bp);
-      if (kind == T_TRSM) {
-        a[ty][tx] = __ldcg(D + (size_t)(s * PB + ty) + (size_t)(s * PB + tx) * ld);
-        if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + s * PB + threadIdx.x);
-      }
-      if (s > 0) {
-        xr[ty][tx] = __ldcg(D + (size_t)(r * PB + ty) + (size_t)((s - 1) * PB + tx) * ld);
-        xc[ty][tx] = __ldcg(D + (size_t)(s * PB + ty) + (size_t)((s - 1) * PB + tx) * ld);
-      }
-      __syncthreads();
-      if (s > 0) {
-        double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll
-        for (int p = 0; p < PB; p += 2) {
-          acc0 += xr[ty][p] * xc[tx][p];
-          acc1 += xr[ty][p + 1] * xc[tx][p + 1];
+      // Solve a block against L_{q,q} (q = s-1 for LT, s for TRSM) after its
+      // fused update by panel q-1: row ty's 16 lanes exchange entries by shuffle.
+      int q = (kind == T_LT) ? s - 1 : s;  // panel solved against
+      int br = (kind == T_LT) ? s : r;     // block row solved
+      double x = 0.0;
+      if (q >= 0) {
+        a[ty][tx] = __ldcg(blk(q, q));
+        if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + q * PB + threadIdx.x);
+        double *bp = blk(br, q);
+        double v = __ldcg(bp);
+        if (q >= 1) {
+          xr[ty][tx] = __ldcg(blk(br, q - 1));
+          xc[ty][tx] = __ldcg(blk(q, q - 1));
         }
-        v -= acc0 + acc1;
-      }
-      if (kind == T_LEAF) {
-        a[ty][tx] = v;
         __syncthreads();
-        // warp 0, lane l < 16 holds row l of the block in registers
+        m[ty][tx] = a[ty][tx] * rinv[tx];
+        if (q >= 1) v -= panel_dot(xr, xc, ty, tx);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PB; j++) {
+          double vj = __shfl_sync(0xffffffffu, v, j, PB);
+          if (tx > j) v = fma(-vj, m[tx][j], v);
+        }
+        x = v * rinv[tx];
+        __stcg(bp, x);
+      }
+      if (kind == T_LT) {
+        // apply the freshly solved panel row to the diagonal block, then factor it
+        if (q >= 0) {
+          __syncthreads();
+          xr[ty][tx] = x;
+          if (threadIdx.x == 0) {
+            __threadfence();
+            s_ok = dag_wait(state, s * nbb + s, s - 1, st);
+            __threadfence();
+          }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        double v2 = __ldcg(blk(s, s));
+        if (q >= 0) v2 -= panel_dot(xr, xr, ty, tx);
+        a[ty][tx] = v2;
+        __syncthreads();
+        // warp 0, lane l holds row (l mod 16) of the block in registers
         if (threadIdx.x < 32) {
           int lane = threadIdx.x;
           int row = lane & (PB - 1);
-          double x[PB];
+          double xx[PB];
 #pragma unroll
-          for (int q = 0; q < PB; q++) x[q] = a[row][q];
+          for (int k2 = 0; k2 < PB; k2++) xx[k2] = a[row][k2];
           int fail = 0;
 #pragma unroll
           for (int j = 0; j < PB; j++) {
-            double d = __shfl_sync(0xffffffffu, x[j], j);  // pivot from lane j
-            if (!(d > 0.0) && !fail) fail = j + 1;  // also catches NaN; same in every lane
+            double d = __shfl_sync(0xffffffffu, xx[j], j);  // pivot from lane j
+            if (!(d > 0.0) && !fail) fail = j + 1;        // also catches NaN; same in every lane
             if (fail) d = 1.0;  // keep going without branching; the result is discarded
             double rs = rsqrt(d);
-            double l = (row == j) ? d * rs : x[j] * rs;  // L[row][j]
-            x[j] = (row >= j) ? l : x[j];
+            double l = (row == j) ? d * rs : xx[j] * rs;  // L[row][j]
+            xx[j] = (row >= j) ? l : xx[j];
             if (lane == 0) rinv[j] = rs;
             double lm = (row > j) ? l : 0.0;
-            // branch-free rank-1 update keeps x[] in registers
+            // branch-free rank-1 update keeps xx[] in registers
 #pragma unroll
-            for (int q = j + 1; q < PB; q++) {
-              double lq = __shfl_sync(0xffffffffu, l, q);  // L[q][j]
-              x[q] = fma(-((row >= q) ? lm : 0.0), lq, x[q]);
+            for (int k2 = j + 1; k2 < PB; k2++) {
+              double lq = __shfl_sync(0xffffffffu, l, k2);  // L[k2][j]
+              xx[k2] = fma(-((row >= k2) ? lm : 0.0), lq, xx[k2]);
             }
           }
           if (fail) {
             if (lane == 0) bad = fail;
           } else if (lane < PB) {
 #pragma unroll
-            for (int q = 0; q < PB; q++) a[row][q] = x[q];
+            for (int k2 = 0; k2 < PB; k2++) a[row][k2] = xx[k2];
           }
         }
         __syncthreads();
@@ -191,24 +221,19 @@ __global__ void __launch_bounds__(PB * PB)
           }
           return;
         }
-        if (ty >= tx) __stcg(bp, a[ty][tx]);
+        if (ty >= tx) __stcg(blk(s, s), a[ty][tx]);
         if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
-      } else {
-        // solve row ty of block (r,s) against L_ss; the 16 lanes of a row
-        // exchange solved entries by shuffle
-#pragma unroll
-        for (int j = 0; j < PB; j++) {
-          double xj = __shfl_sync(0xffffffffu, v, j, PB) * rinv[j];
-          if (tx == j) v = xj;
-          if (tx > j) v -= xj * a[tx][j];
-        }
-        __stcg(bp, v);
       }
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      atomicExch(&state[r * nbb + c], s + 1);
+      if (kind == T_LT) {
+        if (s >= 1) atomicExch(&state[s * nbb + (s - 1)], s);
+        atomicExch(&state[s * nbb + s], s + 1);
+      } else {
+        atomicExch(&state[r * nbb + c], s + 1);
+      }
       if (trace) trace[(size_t)t * 5 + 4] = gtimer();
     }
   }
@@ -220,11 +245,11 @@ static void dag_tasks(int nbb, std::vector<short4> &out) {
   auto push = [&](int kind, int r, int c, int s) {
     out.push_back(make_short4((short)kind, (short)r, (short)c, (short)s));
   };
-  push(T_LEAF, 0, 0, 0);
-  for (int r = 1; r < nbb; r++) push(T_TRSM, r, 0, 0);
+  push(T_LT, 0, 0, 0);
+  for (int r = 2; r < nbb; r++) push(T_TRSM, r, 0, 0);
   for (int s = 0; s + 1 < nbb; s++) {
-    push(T_LEAF, s + 1, s + 1, s + 1);
-    for (int r = s + 2; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
+    push(T_LT, s + 1, s, s + 1);
+    for (int r = s + 3; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
     for (int c = s + 2; c < nbb; c++)
       for (int r = c; r < nbb; r++) push(T_UPD, r, c, s);
   }
