@@ -138,6 +138,12 @@ enum {
   EMU_PROF_RNG, EMU_PROF_SPLIT, EMU_PROF_SOLVE, EMU_PROF_NGROUPS
 };
 emu_status emu_prof_enable(emu_ctx *ctx, int on);
+/* Timeline of the profiled kernel groups since emu_prof_enable: four doubles
+ * per record (group, stream: 0 = context stream, 1 = critical, 2 = panel,
+ * 3 = bulk stream of the mixed factor, start ms, end ms, both relative to the
+ * enable call).  Reports the number of records in *n_records. */
+emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
+                             size_t *n_records);
 /* Device-side task trace of the dataflow FP64 POTRF of the diagonal tiles
  * (off by default).  While enabled, each factor records, for every task of
  * every diagonal tile (tile k's records follow tile k-1's), five 64-bit words:

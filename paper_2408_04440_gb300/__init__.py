@@ -29,7 +29,7 @@ DEFAULT_U = (2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4)
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
+    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
 )
@@ -91,6 +91,7 @@ def load() -> ctypes.CDLL:
     dpp = ctypes.POINTER(ctypes.c_double)
     L.emu_prof_enable.argtypes = [vp, i]
     L.emu_trace_enable.argtypes = [vp, i]
+    L.emu_prof_timeline.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_trace_read.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_prof_read.argtypes = [vp, i, ctypes.POINTER(i), dpp, dpp, dpp, dpp]
     L.emu_cov_build.argtypes = [vp, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(vp)]
@@ -107,7 +108,7 @@ def load() -> ctypes.CDLL:
     L.emu_potrs.argtypes = [vp, vp, vp, lg, vp, lg, i]
     L.emu_solve_refine.argtypes = [vp, vp, vp, vp, lg, vp, lg, i, d, i, ctypes.POINTER(emu_refine_info)]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
-                 "emu_trace_enable", "emu_trace_read",
+                 "emu_trace_enable", "emu_trace_read", "emu_prof_timeline",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
                  "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine"):
@@ -167,6 +168,16 @@ class Context:
                                                ctypes.byref(by), ctypes.byref(mm)), "emu_prof_read")
             out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value,
                          "mma_flops": mm.value}
+        return out
+
+    def prof_timeline(self):
+        """(N, 4) array: group index, stream (0 ctx, 1 critical, 2 panel, 3 bulk), start ms, end ms."""
+        n = ctypes.c_size_t()
+        self._check(self.lib.emu_prof_timeline(self.h, None, 0, ctypes.byref(n)), "emu_prof_timeline")
+        out = np.zeros((n.value, 4), dtype=np.float64)
+        if n.value:
+            self._check(self.lib.emu_prof_timeline(self.h, ctypes.c_void_p(out.ctypes.data), n.value,
+                                                   ctypes.byref(n)), "emu_prof_timeline")
         return out
 
     def trace_enable(self, on: bool = True):

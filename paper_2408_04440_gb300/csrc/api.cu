@@ -45,6 +45,7 @@ ProfScope::ProfScope(emu_ctx *c, int group, double flops, double bytes, double m
   rec.bytes = bytes;
   rec.mma_flops = mma_flops;
   rec.launches0 = ctx->launches;
+  rec.stream = ctx->stream;
   cudaEventRecord(rec.a, ctx->stream);
 }
 
@@ -59,8 +60,10 @@ static void prof_collect(emu_ctx *ctx) {
   if (ctx->prof_open.empty()) return;
   cudaStreamSynchronize(ctx->stream);
   for (const ProfRec &r : ctx->prof_open) {
-    float ms = 0.f;
+    float ms = 0.f, t0 = 0.f;
     cudaEventElapsedTime(&ms, r.a, r.b);
+    if (ctx->prof_base && cudaEventElapsedTime(&t0, ctx->prof_base, r.a) == cudaSuccess)
+      ctx->timeline.push_back({r.group, r.stream, (double)t0, (double)t0 + ms});
     ctx->prof_ms[r.group] += ms;
     ctx->prof_launches[r.group] += (int)r.launches0;
     ctx->prof_flops[r.group] += r.flops;
@@ -137,6 +140,7 @@ emu_status emu_destroy(emu_ctx *ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->prof_base) cudaEventDestroy(ctx->prof_base);
   cudaFree(ctx->dag_tasks);
   cudaFree(ctx->dag_ws);
   cudaFree(ctx->trace_buf);
@@ -159,6 +163,28 @@ emu_status emu_prof_enable(emu_ctx *ctx, int on) {
     ctx->prof_ms[g] = ctx->prof_flops[g] = ctx->prof_bytes[g] = ctx->prof_mma[g] = 0.0;
   }
   ctx->prof = on != 0;
+  ctx->timeline.clear();
+  if (ctx->prof) {
+    if (!ctx->prof_base) EMU_CUDA_TRY(ctx, cudaEventCreate(&ctx->prof_base));
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->prof_base, ctx->stream));
+  }
+  return EMU_OK;
+}
+
+emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records, size_t *n_records) {
+  if (!ctx || !n_records) return EMU_EINVAL;
+  prof_collect(ctx);
+  *n_records = ctx->timeline.size();
+  if (!h_out) return EMU_OK;
+  size_t n = ctx->timeline.size() < max_records ? ctx->timeline.size() : max_records;
+  for (size_t i = 0; i < n; i++) {
+    const auto &r = ctx->timeline[i];
+    int sid = r.stream == ctx->crit ? 1 : r.stream == ctx->mid ? 2 : r.stream == ctx->bulk ? 3 : 0;
+    h_out[4 * i] = r.group;
+    h_out[4 * i + 1] = sid;
+    h_out[4 * i + 2] = r.t0;
+    h_out[4 * i + 3] = r.t1;
+  }
   return EMU_OK;
 }
 

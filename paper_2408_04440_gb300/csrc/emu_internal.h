@@ -45,6 +45,7 @@ enum {
 
 struct ProfRec {
   cudaEvent_t a, b;
+  cudaStream_t stream;
   int group;
   uint64_t launches0;
   double flops, bytes, mma_flops;
@@ -65,10 +66,17 @@ struct emu_ctx {
   int prof_launches[PROF_NGROUPS] = {};
   double prof_ms[PROF_NGROUPS] = {}, prof_flops[PROF_NGROUPS] = {}, prof_bytes[PROF_NGROUPS] = {};
   double prof_mma[PROF_NGROUPS] = {};
+  cudaEvent_t prof_base = nullptr;  // recorded when profiling is enabled
+  struct TimelineRec {
+    int group;
+    cudaStream_t stream;
+    double t0, t1;  // ms after prof_base
+  };
+  std::vector<TimelineRec> timeline;
   // mixed factor schedule: high-priority stream for the critical path
   // (POTRF, TRSM, next-column update), low-priority stream for the bulk
   // trailing update, and events ordering them
-  cudaStream_t crit = nullptr, bulk = nullptr;
+  cudaStream_t crit = nullptr, mid = nullptr, bulk = nullptr;
   std::vector<cudaEvent_t> sched_ev;
   // dataflow POTRF of a diagonal tile: task list and workspace (per nb)
   void *dag_tasks = nullptr;

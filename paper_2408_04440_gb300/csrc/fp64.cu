@@ -256,61 +256,87 @@ static void dag_tasks(int nbb, std::vector<short4> &out) {
 }
 
 // ------------------------------------------------------------ panel TRSM
-// L_ik = A_ik L_kk^{-T} for every i > k.  One CTA per (32-row block, tile);
-// column blocks cb left to right: subtract the already-solved blocks
-// (GEMM part), then solve against the 32x32 diagonal block of L_kk.
-__global__ void __launch_bounds__(256)
+// L_ik = A_ik L_kk^{-T} in FP64 for the listed tiles i > k.  GB300 runs FP64
+// at ~2 FMA per clock per SM, so a tile's nb^3 flops are spread over many
+// small CTAs: one CTA per (4-row block, tile), 4 warps, warp w = row w, lane =
+// column of the current 32-column block cb.  For each cb the solved columns
+// are subtracted (L_kk rows staged in shared memory, four independent partial
+// sums against the 64-cycle FMA latency), then each warp solves its row
+// against the 32x32 diagonal block by forward substitution with shuffles.
+constexpr int T64_ROWS = 4;
+constexpr int T64_STRIP = 128;
+__global__ void __launch_bounds__(128)
     k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
                    const int *st) {
   if (failed(st)) return;
-  __shared__ double xp[B][B + 1];
-  __shared__ double lc[B][B + 1];
-  __shared__ double sx[B][B + 1];
+  extern __shared__ double sm64[];
+  const int ldx = nb + 1;
+  const int lds = T64_STRIP + 1;
+  double *X = sm64;                  // [4][ldx]
+  double *S = X + T64_ROWS * ldx;    // [32][lds]
   int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
-  int r0 = blockIdx.x * B;
+  int r0 = blockIdx.x * T64_ROWS;
   const double *Lkk = t64 + (size_t)tile_index(k, k, NT) * nb * nb;
-  double *X = t64 + (size_t)tile_index(i, k, NT) * nb * nb + r0;  // row block
-  int t = threadIdx.x;
-  int c = t % B, rr = t / B;
+  double *A = t64 + (size_t)tile_index(i, k, NT) * nb * nb + r0;
+  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll 8
+  for (int e = tid; e < T64_ROWS * nb; e += 128) {
+    int r = e % T64_ROWS, c = e / T64_ROWS;
+    X[r * ldx + c] = A[r + (size_t)c * nb];
+  }
   int nbb = nb / B;
   for (int cb = 0; cb < nbb; cb++) {
-    double acc[4];
+    const double *Lrow = Lkk + cb * B + lane;  // row cb*32 + lane of L_kk
+    double ld[B];
 #pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] = X[(rr + 8 * q) + (size_t)(cb * B + c) * nb];
-    for (int pb = 0; pb < cb; pb++) {
-      __syncthreads();
+    for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.0;
+    __syncthreads();
+    double a0 = X[w * ldx + cb * B + lane], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int p0 = 0; p0 < cb * B; p0 += T64_STRIP) {
+      int pw = min(T64_STRIP, cb * B - p0);
+      {
+        double v[T64_STRIP / 4];
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        int p = rr + 8 * q;
-        xp[c][p] = X[c + (size_t)(pb * B + p) * nb];                   // X[r=c][p]
-        lc[c][p] = Lkk[(cb * B + c) + (size_t)(pb * B + p) * nb];      // L[cb row c][p]
+        for (int u = 0; u < T64_STRIP / 4; u++) {
+          int pp = w + 4 * u;
+          v[u] = (pp < pw) ? Lrow[(size_t)(p0 + pp) * nb] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < T64_STRIP / 4; u++) {
+          int pp = w + 4 * u;
+          if (pp < pw) S[lane * lds + pp] = v[u];
+        }
       }
       __syncthreads();
-      for (int p = 0; p < B; p++) {
-        double lv = lc[c][p];
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[q] -= xp[rr + 8 * q][p] * lv;
+      const double *xr = X + w * ldx + p0, *sl = S + lane * lds;
+      for (int p = 0; p < pw; p += 4) {
+        a0 -= xr[p] * sl[p];
+        a1 -= xr[p + 1] * sl[p + 1];
+        a2 -= xr[p + 2] * sl[p + 2];
+        a3 -= xr[p + 3] * sl[p + 3];
       }
+      __syncthreads();
     }
-    __syncthreads();
+    double a = (a0 + a1) + (a2 + a3);
+    double mydiag = ld[0];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      sx[rr + 8 * q][c] = acc[q];
-      int p = rr + 8 * q;
-      lc[c][p] = Lkk[(cb * B + c) + (size_t)(cb * B + p) * nb];  // diagonal block
-    }
-    __syncthreads();
-    if (t < B) {
-      for (int cc = 0; cc < B; cc++) {
-        double v = sx[t][cc];
-        for (int p = 0; p < cc; p++) v -= sx[t][p] * lc[cc][p];
-        sx[t][cc] = v / lc[cc][cc];
-      }
-    }
-    __syncthreads();
+    for (int p = 1; p < B; p++)
+      if (p == lane) mydiag = ld[p];
+    double myrinv = 1.0 / mydiag;  // off the dependency chain
 #pragma unroll
-    for (int q = 0; q < 4; q++) X[(rr + 8 * q) + (size_t)(cb * B + c) * nb] = sx[rr + 8 * q][c];
-    __syncthreads();
+    for (int j = 0; j < B; j++) {
+      double rj = __shfl_sync(0xffffffffu, myrinv, j);
+      double xj = __shfl_sync(0xffffffffu, a, j) * rj;
+      if (lane == j) a = xj;
+      if (lane > j) a -= xj * ld[j];
+    }
+    X[w * ldx + cb * B + lane] = a;
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int e = tid; e < T64_ROWS * nb; e += 128) {
+    int r = e % T64_ROWS, c = e / T64_ROWS;
+    A[r + (size_t)c * nb] = X[r * ldx + c];
   }
 }
 
@@ -566,8 +592,10 @@ emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_row
   if (m <= 0) return EMU_OK;
   double nb3 = (double)A->nb * A->nb * A->nb;
   ProfScope ps(ctx, PROF_TRSM64, m * nb3, 16.0 * m * A->nb * A->nb);
-  k_trsm64_panel<<<dim3(A->nb / B, m), 256, 0, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
-                                                             ctx->d_status);
+  size_t sm = (size_t)(T64_ROWS * (A->nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_trsm64_panel<<<dim3(A->nb / T64_ROWS, m), 128, sm, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
+                                                                     ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

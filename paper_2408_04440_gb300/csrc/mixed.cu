@@ -13,6 +13,8 @@
 // consumer reads the pieces its class needs (three for FP32, one for BF16).
 #include <cuda_bf16.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -108,31 +110,40 @@ __global__ void k_split_tiles(const T *__restrict__ src, uint16_t *__restrict__ 
 }
 
 // FP32 panel TRSM for the low-precision tiles of column k:
-// L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and the FP64 L_kk (read as
-// FP32), written back to the master and, split, to the operand arena.
-// One CTA per (32-row block, tile): the 32 rows stay in shared memory; for
-// each 32-column block cb the already-solved columns are subtracted (a small
-// GEMM against L_kk blocks staged in shared memory), then warp w solves rows
-// 4w..4w+3 against the 32x32 diagonal block by forward substitution, one
-// lane per column, with shuffles (no block-wide barrier inside the solve).
+// L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy of the
+// FP64 L_kk, written back to the master and, split, to the operand arena.
+// One CTA per (16-row block, tile), 8 warps: warp w owns rows w and w + 8, a
+// lane owns one column of the current 32-column block cb.  For each cb the
+// already-solved columns are subtracted (a small GEMM against L_kk rows staged
+// in shared memory in 128-column strips), then each warp solves its two rows
+// against the 32x32 diagonal block by forward substitution with shuffles.
+// About 50 KB of shared memory per CTA, so four CTAs share an SM and hide each
+// other's strip-load latency.
 constexpr int TS_LD_PAD = 4;
-constexpr int TS_STRIP = 512;  // columns of L_kk staged at once
-__global__ void __launch_bounds__(256)
+constexpr int TS_STRIP = 128;  // columns of L_kk staged at once
+// NW warps, RPW rows per warp: the CTA solves NW*RPW rows (warp w owns rows
+// w + NW*q).  16-row CTAs (8 warps x 2) for throughput on the panel, 4-row
+// CTAs (4 warps x 1) for the single tile on the critical path, where more
+// CTAs in parallel mean less latency.
+template <int NW, int RPW>
+__global__ void __launch_bounds__(NW * 32)
     k_trsm32_panel(const float *__restrict__ Lkk, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
                    int NT, int k, const int *__restrict__ rows, const int *st) {
+  constexpr int ROWS = NW * RPW, NTH = NW * 32;
   if (failed(st)) return;
   extern __shared__ float sm[];
   const int ldx = nb + TS_LD_PAD;
   const int lds = TS_STRIP + 1;
-  float *X = sm;              // [32][ldx]: the CTA's rows of A_ik, solved in place
-  float *S = X + 32 * ldx;    // [32][lds]: strip of L_kk rows cb*32 + lane, up to TS_STRIP columns
+  float *X = sm;                // [ROWS][ldx]: the CTA's rows of A_ik, solved in place
+  float *S = X + ROWS * ldx;    // [32][lds]: strip of L_kk rows cb*32 + lane
   int i = rows[blockIdx.y];
-  int r0 = blockIdx.x * B;
+  int r0 = blockIdx.x * ROWS;
   long ti = tile_index(i, k, NT);
   float *A = t32 + (size_t)ti * nb * nb + r0;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int e = tid; e < 32 * nb; e += 256) {
-    int r = e & 31, c = e >> 5;
+#pragma unroll 8
+  for (int e = tid; e < ROWS * nb; e += NTH) {
+    int r = e % ROWS, c = e / ROWS;
     X[r * ldx + c] = A[r + (size_t)c * nb];
   }
   int nbb = nb / B;
@@ -141,20 +152,41 @@ __global__ void __launch_bounds__(256)
     float ld[B];
 #pragma unroll
     for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.f;
-    float acc[4];
     __syncthreads();  // X of the previous column blocks is complete
+    float a[RPW], b[RPW];
 #pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] = X[(4 * w + q) * ldx + cb * B + lane];
+    for (int q = 0; q < RPW; q++) {
+      a[q] = X[(w + NW * q) * ldx + cb * B + lane];
+      b[q] = 0.f;  // second accumulators halve the FMA chains
+    }
     for (int p0 = 0; p0 < cb * B; p0 += TS_STRIP) {
       int pw = min(TS_STRIP, cb * B - p0);
-      // the strip chunk: all loads issued together
-      for (int p = w; p < pw; p += 8) S[lane * lds + p] = Lrow[(size_t)(p0 + p) * nb];
-      __syncthreads();
-#pragma unroll 4
-      for (int p = 0; p < pw; p++) {
-        float l = S[lane * lds + p];
+      // all of this thread's strip loads in flight before the first store
+      {
+        constexpr int PER = TS_STRIP / NW;
+        float v[PER];
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc[q] -= X[(4 * w + q) * ldx + p0 + p] * l;
+        for (int u = 0; u < PER; u++) {
+          int pp = w + NW * u;
+          v[u] = (pp < pw) ? Lrow[(size_t)(p0 + pp) * nb] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+          int pp = w + NW * u;
+          if (pp < pw) S[lane * lds + pp] = v[u];
+        }
+      }
+      __syncthreads();
+      const float *sl = S + lane * lds;
+#pragma unroll 4
+      for (int p = 0; p < pw; p += 2) {
+        float l0 = sl[p], l1 = sl[p + 1];
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+          const float *xq = X + (w + NW * q) * ldx + p0;
+          a[q] -= xq[p] * l0;
+          b[q] -= xq[p + 1] * l1;
+        }
       }
       __syncthreads();
     }
@@ -164,27 +196,30 @@ __global__ void __launch_bounds__(256)
       if (p == lane) mydiag = ld[p];
     float myrinv = 1.0f / mydiag;
 #pragma unroll
+    for (int q = 0; q < RPW; q++) a[q] += b[q];
+#pragma unroll
     for (int j = 0; j < B; j++) {
       float rj = __shfl_sync(0xffffffffu, myrinv, j);
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        float xj = __shfl_sync(0xffffffffu, acc[q], j) * rj;
-        if (lane == j) acc[q] = xj;
-        if (lane > j) acc[q] -= xj * ld[j];
+      for (int q = 0; q < RPW; q++) {
+        float xj = __shfl_sync(0xffffffffu, a[q], j) * rj;
+        if (lane == j) a[q] = xj;
+        if (lane > j) a[q] -= xj * ld[j];
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++) X[(4 * w + q) * ldx + cb * B + lane] = acc[q];
+    for (int q = 0; q < RPW; q++) X[(w + NW * q) * ldx + cb * B + lane] = a[q];
   }
   __syncthreads();
   // FP32 master (column-major) and the sender-side BF16 pieces (row-major)
-  for (int e = tid; e < 32 * nb; e += 256) {
-    int r = e & 31, c = e >> 5;
+#pragma unroll 8
+  for (int e = tid; e < ROWS * nb; e += NTH) {
+    int r = e % ROWS, c = e / ROWS;
     A[r + (size_t)c * nb] = X[r * ldx + c];
   }
   size_t plane = (size_t)nb * nb;
   uint16_t *P = op + (size_t)ti * 3 * plane + (size_t)r0 * nb;
-  for (int e = tid; e < 32 * nb; e += 256) {
+  for (int e = tid; e < ROWS * nb; e += NTH) {
     int r = e / nb, c = e % nb;
     uint16_t p0, p1, p2;
     split3(X[r * ldx + c], p0, p1, p2);
@@ -195,7 +230,9 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-static size_t trsm32_smem(int nb) { return (size_t)(32 * (nb + TS_LD_PAD) + 32 * (TS_STRIP + 1)) * sizeof(float); }
+static size_t trsm32_smem(int nb, int rows) {
+  return (size_t)(rows * (nb + TS_LD_PAD) + 32 * (TS_STRIP + 1)) * sizeof(float);
+}
 
 // FP64-class trailing tiles: C_ij -= L_ik L_jk^T in FP64; each operand comes
 // from the FP64 master or (widened) from the FP32 master, by its class.
@@ -336,36 +373,46 @@ __global__ void k_solve32_diag(const double *__restrict__ t64, int nb, int NT, i
 }  // namespace
 
 // ------------------------------------------------------------------ plan
+// Work of panel step k, split so that the critical chain
+// POTRF(k) -> TRSM(k+1,k) -> SYRK(k+1,k+1) -> POTRF(k+1) carries as little
+// as possible.  Groups: T1 = TRSM of row k+1, TR = TRSM of rows >= k+2,
+// S = update of tile (k+1,k+1), G1 = updates of (i, k+1), i >= k+2,
+// G2A = updates of column k+2, G2 = updates of columns >= k+3.  Each group has FP64 entries (rows / pairs
+// for the SIMT kernels) and tensor-core items.
+enum { GR_S = 0, GR_G1 = 1, GR_G2A = 2, GR_G2 = 3, GR_N = 4 };
+struct StepPlan {
+  int r64_1 = 0, n64_1 = 0, r32_1 = 0, n32_1 = 0;  // T1 (offset, count) in rows64 / rows32
+  int r64_r = 0, n64_r = 0, r32_r = 0, n32_r = 0;  // TR
+  int p_off[GR_N] = {}, p_n[GR_N] = {};            // FP64 pairs per update group
+  int i_off[GR_N] = {}, i_n[GR_N] = {};            // tensor-core items per update group
+  double flops[GR_N] = {}, mma[GR_N] = {};
+  bool diag_low = false;
+};
+
 struct MixedPlan {
   int NT = 0, nb = 0;
   std::vector<unsigned char> cls;  // packed by tile index
-  // per step k: offsets into the concatenated device lists
-  std::vector<int> off_t64rows, off_t32rows, off_pairs, off_items;
-  std::vector<int> g1_pairs, g1_items;  // leading entries of a step that update column k+1
-  std::vector<int> diag_low;       // class(k,k) != FP64
-  std::vector<double> step_flops, step_mma;  // tensor-core work of each step
+  std::vector<StepPlan> steps;
   int *d_rows64 = nullptr, *d_rows32 = nullptr;
   int2 *d_pairs = nullptr;
   gemm_tc::Item *d_items = nullptr;
   gemm_tc::Seg *d_segs = nullptr;
-  int *d_tiles_fp64_panel = nullptr;  // FP64-class off-diagonal tiles (split after their TRSM)
+  int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
-  float *d_lkk32 = nullptr;           // FP32 copy of the current L_kk
+  float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
   CUtensorMap mapA, mapB;
   double update_flops[EMU_NCLASS] = {};
   int tiles[EMU_NCLASS] = {};
+  // every device list above lives in one stream-ordered allocation, filled by
+  // one copy from `host_blob` (kept until the factor's stream work is done)
+  void *d_blob = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<char> host_blob;
 };
 
 static void plan_free(MixedPlan *p) {
   if (!p) return;
-  cudaFree(p->d_rows64);
-  cudaFree(p->d_rows32);
-  cudaFree(p->d_pairs);
-  cudaFree(p->d_items);
-  cudaFree(p->d_segs);
-  cudaFree(p->d_tiles_fp64_panel);
-  cudaFree(p->d_diag_tiles);
-  cudaFree(p->d_lkk32);
+  if (p->d_blob) cudaFreeAsync(p->d_blob, p->stream);
   delete p;
 }
 
@@ -374,21 +421,13 @@ void mixed_mat_release(emu_mat *A) {
   A->plan = nullptr;
 }
 
-template <typename T>
-static emu_status upload(emu_ctx *ctx, T **dst, const std::vector<T> &v) {
-  size_t n = v.empty() ? 1 : v.size();
-  EMU_CUDA_TRY(ctx, cudaMalloc(dst, n * sizeof(T)));
-  if (!v.empty()) EMU_CUDA_TRY(ctx, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return EMU_OK;
-}
-
 static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   int NT = A->nt, nb = A->nb;
   P->NT = NT;
   P->nb = nb;
   P->cls.assign(A->h_cls, A->h_cls + A->ntiles);
   auto C = [&](int i, int j) { return (int)P->cls[tile_index(i, j, NT)]; };
-  std::vector<int> rows64, rows32, fp64panel, diag;
+  std::vector<int> rows64, rows32, tiles64, diag;
   std::vector<int2> pairs;
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
@@ -399,82 +438,120 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
       P->tiles[c]++;
       P->update_flops[c] += (i == j ? 1.0 : 2.0) * j * nb3 + (i > j ? nb3 : 0.0);
     }
+  auto add_tile_update = [&](StepPlan &sp, int g, int k, int i, int j) {
+    int c = C(i, j);
+    if (c == EMU_CLASS_FP64) {
+      pairs.push_back(make_int2(i, j));
+      sp.p_n[g]++;
+      return;
+    }
+    int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;  // TF32/E4M3 fall back
+    for (int nbk = 0; nbk < nb / gemm_tc::BN; nbk++)
+      for (int mb = 0; mb < nb / gemm_tc::BM; mb++) {
+        if (i == j && mb * gemm_tc::BM + gemm_tc::BM - 1 < nbk * gemm_tc::BN) continue;  // above the diagonal
+        gemm_tc::Seg s;
+        s.ax = 0;
+        s.ay = (int)(tile_index(i, k, NT) * 3 * nb + mb * gemm_tc::BM);
+        s.ay_step = nb;
+        s.bx = 0;
+        s.by = (int)(tile_index(j, k, NT) * 3 * nb + nbk * gemm_tc::BN);
+        s.by_step = nb;
+        s.cls = cc;
+        s.pad = 0;
+        gemm_tc::Item it;
+        it.seg_begin = (int)segs.size();
+        segs.push_back(s);
+        it.seg_end = (int)segs.size();
+        it.out_off = tile_index(i, j, NT) * (long)nb * nb + mb * gemm_tc::BM + (long)nbk * gemm_tc::BN * nb;
+        it.rows_valid = gemm_tc::BM;
+        it.cols_valid = gemm_tc::BN;
+        items.push_back(it);
+        double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
+        sp.i_n[g]++;
+        sp.flops[g] += f;
+        sp.mma[g] += f * (cc == EMU_CLASS_FP32 ? 6.0 : 1.0);
+      }
+  };
+  auto add_row = [&](int k, int i, int &n64, int &n32) {
+    if (C(i, k) == EMU_CLASS_FP64) {
+      rows64.push_back(i);
+      tiles64.push_back((int)tile_index(i, k, NT));
+      n64++;
+    } else {
+      rows32.push_back(i);
+      n32++;
+    }
+  };
   for (int k = 0; k < NT; k++) {
+    StepPlan sp;
     diag.push_back((int)tile_index(k, k, NT));
-    P->diag_low.push_back(C(k, k) != EMU_CLASS_FP64);
-    P->off_t64rows.push_back((int)rows64.size());
-    P->off_t32rows.push_back((int)rows32.size());
-    P->off_pairs.push_back((int)pairs.size());
-    P->off_items.push_back((int)items.size());
-    double sf = 0.0, sm = 0.0;
-    int g1p = 0, g1i = 0;
-    for (int i = k + 1; i < NT; i++) {
-      if (C(i, k) == EMU_CLASS_FP64) {
-        rows64.push_back(i);
-        fp64panel.push_back((int)tile_index(i, k, NT));
+    sp.diag_low = C(k, k) != EMU_CLASS_FP64;
+    sp.r64_1 = (int)rows64.size();
+    sp.r32_1 = (int)rows32.size();
+    if (k + 1 < NT) add_row(k, k + 1, sp.n64_1, sp.n32_1);
+    sp.r64_r = (int)rows64.size();
+    sp.r32_r = (int)rows32.size();
+    for (int i = k + 2; i < NT; i++) add_row(k, i, sp.n64_r, sp.n32_r);
+    for (int g = 0; g < GR_N; g++) {
+      sp.p_off[g] = (int)pairs.size();
+      sp.i_off[g] = (int)items.size();
+      if (g == GR_S) {
+        if (k + 1 < NT) add_tile_update(sp, g, k, k + 1, k + 1);
+      } else if (g == GR_G1) {
+        for (int i = k + 2; i < NT; i++) add_tile_update(sp, g, k, i, k + 1);
+      } else if (g == GR_G2A) {
+        for (int i = k + 2; i < NT; i++) add_tile_update(sp, g, k, i, k + 2);
       } else {
-        rows32.push_back(i);
+        for (int j = k + 3; j < NT; j++)
+          for (int i = j; i < NT; i++) add_tile_update(sp, g, k, i, j);
       }
     }
-    // trailing tiles, ordered by column j then row i
-    for (int j = k + 1; j < NT; j++)
-      for (int i = j; i < NT; i++) {
-        int c = C(i, j);
-        if (c == EMU_CLASS_FP64) {
-          pairs.push_back(make_int2(i, j));
-          if (j == k + 1) g1p++;
-          continue;
-        }
-        int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;  // TF32/E4M3 fall back
-        for (int nbk = 0; nbk < nb / gemm_tc::BN; nbk++)
-          for (int mb = 0; mb < nb / gemm_tc::BM; mb++) {
-            if (i == j && mb * gemm_tc::BM + gemm_tc::BM - 1 < nbk * gemm_tc::BN) continue;  // above diagonal
-            gemm_tc::Seg s;
-            s.ax = 0;
-            s.ay = (int)(tile_index(i, k, NT) * 3 * nb + mb * gemm_tc::BM);
-            s.ay_step = nb;
-            s.bx = 0;
-            s.by = (int)(tile_index(j, k, NT) * 3 * nb + nbk * gemm_tc::BN);
-            s.by_step = nb;
-            s.cls = cc;
-            s.pad = 0;
-            gemm_tc::Item it;
-            it.seg_begin = (int)segs.size();
-            segs.push_back(s);
-            it.seg_end = (int)segs.size();
-            it.out_off = tile_index(i, j, NT) * (long)nb * nb + mb * gemm_tc::BM + (long)nbk * gemm_tc::BN * nb;
-            it.rows_valid = gemm_tc::BM;
-            it.cols_valid = gemm_tc::BN;
-            items.push_back(it);
-            double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
-            sf += f;
-            sm += f * (cc == EMU_CLASS_FP32 ? 6.0 : 1.0);
-            if (j == k + 1) g1i++;
-          }
-      }
-    P->g1_pairs.push_back(g1p);
-    P->g1_items.push_back(g1i);
-    P->step_flops.push_back(sf);
-    P->step_mma.push_back(sm);
+    P->steps.push_back(sp);
   }
-  P->off_t64rows.push_back((int)rows64.size());
-  P->off_t32rows.push_back((int)rows32.size());
-  P->off_pairs.push_back((int)pairs.size());
-  P->off_items.push_back((int)items.size());
+  // one allocation and one copy for all lists (256-byte aligned parts)
+  size_t off = 0;
+  auto part = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  auto vbytes = [](const auto &v) { return v.size() * sizeof(v[0]); };
+  size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_pairs = part(vbytes(pairs)),
+         o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
+         o_diag = part(vbytes(diag)), o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
+  size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
+  P->host_blob.assign(copy_bytes, 0);
+  auto put = [&](size_t o, const auto &v) {
+    if (!v.empty()) memcpy(P->host_blob.data() + o, v.data(), vbytes(v));
+  };
+  put(o_r64, rows64);
+  put(o_r32, rows32);
+  put(o_pairs, pairs);
+  put(o_items, items);
+  put(o_segs, segs);
+  put(o_t64, tiles64);
+  put(o_diag, diag);
+  P->stream = ctx->stream;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_blob, off, ctx->stream));
+  char *b = static_cast<char *>(P->d_blob);
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(b, P->host_blob.data(), copy_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  P->d_rows64 = reinterpret_cast<int *>(b + o_r64);
+  P->d_rows32 = reinterpret_cast<int *>(b + o_r32);
+  P->d_pairs = reinterpret_cast<int2 *>(b + o_pairs);
+  P->d_items = reinterpret_cast<gemm_tc::Item *>(b + o_items);
+  P->d_segs = reinterpret_cast<gemm_tc::Seg *>(b + o_segs);
+  P->d_tiles64 = reinterpret_cast<int *>(b + o_t64);
+  P->d_diag_tiles = reinterpret_cast<int *>(b + o_diag);
+  P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
   emu_status s;
-  if ((s = upload(ctx, &P->d_rows64, rows64)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_rows32, rows32)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_pairs, pairs)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_items, items)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_segs, segs)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_tiles_fp64_panel, fp64panel)) != EMU_OK) return s;
-  if ((s = upload(ctx, &P->d_diag_tiles, diag)) != EMU_OK) return s;
-  EMU_CUDA_TRY(ctx, cudaMalloc(&P->d_lkk32, (size_t)nb * nb * sizeof(float)));
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapA, A->op_bf16, nb, rows, gemm_tc::BM)) != EMU_OK) return s;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapB, A->op_bf16, nb, rows, gemm_tc::BN)) != EMU_OK) return s;
   return EMU_OK;
 }
+
+// SMs the bulk trailing update leaves to the critical-path kernels.
+constexpr int kReservedSMs = 16;
 
 // Internal streams of the mixed schedule (created once per context) and at
 // least `nev` ordering events.
@@ -483,6 +560,7 @@ static emu_status sched_streams(emu_ctx *ctx, int nev) {
     int least = 0, greatest = 0;
     EMU_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     EMU_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->crit, cudaStreamNonBlocking, greatest));
+    EMU_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->mid, cudaStreamNonBlocking, (greatest + least) / 2));
     EMU_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->bulk, cudaStreamNonBlocking, least));
   }
   while ((int)ctx->sched_ev.size() < nev) {
@@ -525,80 +603,118 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     k_to_f32<<<dim3(64, (unsigned)A->ntiles), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, te);
     EMU_LAUNCHED(ctx);
   }
-  // Lookahead-1 schedule.  Critical stream: POTRF(k), TRSM(:,k), then the
-  // update of column k+1 by panel k (G1), which feeds POTRF(k+1).  Bulk
-  // stream: the update of columns >= k+2 by panel k (G2), overlapping the
-  // next panel.  G1(k) must not overlap G2(k-1) (both write column k+1).
+  // Lookahead schedule on three priority streams (see StepPlan):
+  //   crit: POTRF(k) -> TRSM(k+1,k) -> S(k) = SYRK of tile (k+1,k+1)
+  //   mid : TRSM(i>=k+2, k) -> G1(k) = update of column k+1 below the diagonal
+  //   bulk: G2A(k) = update of column k+2, then G2(k) = columns >= k+3
+  // Two launches that write the same tiles never overlap: S(k) and G1(k)
+  // wait for G2A(k-1) (the last other writer of column k+1), and the bulk
+  // stream runs G2A(k-1), G2(k-1), G2A(k), G2(k) in order.  TRSM(k+1,k) waits
+  // for G1(k-1), which finished the update of its tile.
   cudaStream_t user = ctx->stream;
-  if ((s = sched_streams(ctx, 2 * NT + 2)) != EMU_OK) return s;
-  cudaEvent_t ev_start = ctx->sched_ev[2 * NT], ev_bulk_end = ctx->sched_ev[2 * NT + 1];
+  const int EV = 5;  // per step: POTRF done, TRSM(k+1) done, TRSM rest done, G1 done, G2 done
+  if ((s = sched_streams(ctx, EV * NT + 2)) != EMU_OK) return s;
+  auto ev = [&](int k, int w) { return ctx->sched_ev[EV * k + w]; };
+  enum { E_P = 0, E_T1 = 1, E_T = 2, E_G1 = 3, E_G2 = 4 };
+  cudaEvent_t ev_start = ctx->sched_ev[EV * NT], ev_end = ctx->sched_ev[EV * NT + 1];
   EMU_CUDA_TRY(ctx, cudaEventRecord(ev_start, user));
-  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev_start, 0));
-  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev_start, 0));
-  for (int k = 0; k < NT; k++) {
-    cudaEvent_t ev_trsm = ctx->sched_ev[2 * k], ev_g2 = ctx->sched_ev[2 * k + 1];
+  for (cudaStream_t q : {ctx->crit, ctx->mid, ctx->bulk}) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(q, ev_start, 0));
+  size_t tsm16 = trsm32_smem(nb, 16), tsm4 = trsm32_smem(nb, 4);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsm16));
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsm4));
+
+  // TRSM of the listed rows of panel k (FP64 rows on the FP64 pipe, then split)
+  auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
+    emu_status e = EMU_OK;
+    if (n64 > 0) {
+      if ((e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64)) != EMU_OK) return e;
+      ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
+      k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
+                                                                                    P->d_tiles64 + r64, nb, 0, st);
+      EMU_LAUNCHED(ctx);
+    }
+    if (n32 > 0) {
+      ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
+      const float *lkk = P->d_lkk32 + (size_t)(k & 1) * te;
+      if (critical)
+        k_trsm32_panel<4, 1><<<dim3(nb / 4, n32), 128, tsm4, ctx->stream>>>(lkk, A->t32, A->op_bf16, nb, NT, k,
+                                                                           P->d_rows32 + r32, st);
+      else
+        k_trsm32_panel<8, 2><<<dim3(nb / 16, n32), 256, tsm16, ctx->stream>>>(lkk, A->t32, A->op_bf16, nb, NT, k,
+                                                                             P->d_rows32 + r32, st);
+      EMU_LAUNCHED(ctx);
+    }
+    return e;
+  };
+  // updates of group g of panel k on at most `max_ctas` persistent CTAs
+  auto update_group = [&](int k, int g, int max_ctas) -> emu_status {
+    const StepPlan &sp = P->steps[k];
+    if (sp.p_n[g] > 0) {
+      ProfScope ps(ctx, PROF_UPDATE64, 2.0 * sp.p_n[g] * nb3, 24.0 * sp.p_n[g] * te);
+      k_update64_list<<<dim3(sp.p_n[g], (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
+          A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
+      EMU_LAUNCHED(ctx);
+    }
+    if (sp.i_n[g] > 0) {
+      ProfScope ps(ctx, PROF_TC_FACTOR, sp.flops[g], 0.0, sp.mma[g]);
+      int in = sp.i_n[g];
+      int ctas = std::max(1, max_ctas);
+      return gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + sp.i_off[g], in, P->d_segs, nb / gemm_tc::BK,
+                             gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctas);
+    }
+    return EMU_OK;
+  };
+
+  for (int k = 0; k < NT && s == EMU_OK; k++) {
+    const StepPlan &sp = P->steps[k];
     long tkk = tile_index(k, k, NT);
+    // ---- critical stream
     ctx->stream = ctx->crit;
-    if (P->diag_low[k]) {
+    if (sp.diag_low) {
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * te);
       k_tile_to_f64<<<64, 256, 0, ctx->stream>>>(A->t32 + tkk * te, A->t64 + tkk * te, te, st);
       EMU_LAUNCHED(ctx);
     }
     if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) break;
-    int n64 = P->off_t64rows[k + 1] - P->off_t64rows[k];
-    int n32 = P->off_t32rows[k + 1] - P->off_t32rows[k];
-    if (n64 > 0) {
-      if ((s = launch_trsm64_panel(ctx, A, k, P->d_rows64 + P->off_t64rows[k], n64)) != EMU_OK) break;
-      ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
-      k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(
-          A->t64, A->op_bf16, P->d_tiles_fp64_panel + P->off_t64rows[k], nb, 0, st);
+    if (sp.n32_1 + sp.n32_r > 0) {
+      k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te, P->d_lkk32 + (size_t)(k & 1) * te,
+                                                               te, st);
       EMU_LAUNCHED(ctx);
     }
-    if (n32 > 0) {
-      ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
-      k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te, P->d_lkk32, te, st);
-      EMU_LAUNCHED(ctx);
-      size_t sm = trsm32_smem(nb);
-      EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_trsm32_panel<<<dim3(nb / B, n32), 256, sm, ctx->stream>>>(P->d_lkk32, A->t32, A->op_bf16, nb, NT, k,
-                                                                  P->d_rows32 + P->off_t32rows[k], st);
-      EMU_LAUNCHED(ctx);
-    }
-    EMU_CUDA_TRY(ctx, cudaEventRecord(ev_trsm, ctx->crit));
-    if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ctx->sched_ev[2 * (k - 1) + 1], 0));
-    int p0 = P->off_pairs[k], np = P->off_pairs[k + 1] - p0, np1 = P->g1_pairs[k];
-    int i0 = P->off_items[k], ni = P->off_items[k + 1] - i0, ni1 = P->g1_items[k];
-    // G1 on the critical stream, G2 on the bulk stream
-    for (int part = 0; part < 2 && s == EMU_OK; part++) {
-      ctx->stream = part == 0 ? ctx->crit : ctx->bulk;
-      if (part == 1) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev_trsm, 0));
-      int pb = part == 0 ? p0 : p0 + np1, pn = part == 0 ? np1 : np - np1;
-      int ib = part == 0 ? i0 : i0 + ni1, in = part == 0 ? ni1 : ni - ni1;
-      if (pn > 0) {
-        ProfScope ps(ctx, PROF_UPDATE64, 2.0 * pn * nb3, 24.0 * pn * te);
-        k_update64_list<<<dim3(pn, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(A->t64, A->t32, A->d_cls, nb, NT,
-                                                                                 k, P->d_pairs + pb, st);
-        EMU_LAUNCHED(ctx);
-      }
-      if (in > 0) {
-        double fr = (double)in / ni;
-        ProfScope ps(ctx, PROF_TC_FACTOR, P->step_flops[k] * fr, 0.0, P->step_mma[k] * fr);
-        // short-lived CTAs on the bulk stream (at most 4 items each) let the
-        // critical stream's CTAs take SMs as they free up
-        int ctas = part == 0 ? ctx->sm_count : std::max(1, (in + 3) / 4);
-        s = gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + ib, in, P->d_segs, nb / gemm_tc::BK,
-                            gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctas);
-      }
-    }
-    if (s != EMU_OK) break;
-    EMU_CUDA_TRY(ctx, cudaEventRecord(ev_g2, ctx->bulk));
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
+    if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
+    if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T1), ctx->crit));
+    if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G2), 0));  // G2A(k-1)
+    if ((s = update_group(k, GR_S, ctx->sm_count)) != EMU_OK) break;
+    // ---- mid stream
+    ctx->stream = ctx->mid;
+    EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_P), 0));
+    if ((s = trsm_rows(k, sp.r64_r, sp.n64_r, sp.r32_r, sp.n32_r, false)) != EMU_OK) break;
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T), ctx->mid));
+    EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_T1), 0));
+    if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k - 1, E_G2), 0));
+    if ((s = update_group(k, GR_G1, ctx->sm_count)) != EMU_OK) break;
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G1), ctx->mid));
+    // ---- bulk stream: persistent on all but kReservedSMs SMs, which stay
+    // free for the critical and panel streams' kernels
+    ctx->stream = ctx->bulk;
+    EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev(k, E_T), 0));
+    int bulk_ctas = std::max(1, ctx->sm_count - kReservedSMs);
+    if ((s = update_group(k, GR_G2A, bulk_ctas)) != EMU_OK) break;
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G2), ctx->bulk));
+    if ((s = update_group(k, GR_G2, bulk_ctas)) != EMU_OK) break;
   }
   ctx->stream = user;
   if (s != EMU_OK) return s;
-  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_bulk_end, ctx->bulk));
-  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev_bulk_end, 0));
-  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_bulk_end, ctx->crit));
-  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ev_bulk_end, 0));
+  for (cudaStream_t q : {ctx->mid, ctx->bulk}) {
+    EMU_CUDA_TRY(ctx, cudaEventRecord(ev_end, q));
+    EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev_end, 0));
+  }
+  EMU_CUDA_TRY(ctx, cudaEventRecord(ev_end, ctx->crit));
+  EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ev_end, 0));
   if ((s = launch_tril_diag(ctx, A)) != EMU_OK) return s;
   // pieces of the (lower-triangular) diagonal factor tiles, for the sampler
   ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * NT * te);
@@ -725,6 +841,7 @@ void mixed_ctx_release(emu_ctx *ctx) {
   for (cudaEvent_t e : ctx->sched_ev) cudaEventDestroy(e);
   ctx->sched_ev.clear();
   if (ctx->crit) cudaStreamDestroy(ctx->crit);
+  if (ctx->mid) cudaStreamDestroy(ctx->mid);
   if (ctx->bulk) cudaStreamDestroy(ctx->bulk);
-  ctx->crit = ctx->bulk = nullptr;
+  ctx->crit = ctx->mid = ctx->bulk = nullptr;
 }
