@@ -239,6 +239,33 @@ emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu_mat *S,
                             int nrhs, double tol, int maxit,
                             emu_refine_info *info);
 
+/* ------------------------------------------------------- no-allocation build */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they call the library: code inside
+ * a framework that owns the device heap, a process that reserved all memory up
+ * front, or work issued while a CUDA graph is being built around it.  It needs
+ * no context (creating one allocates).
+ *
+ * Writes the lower triangle (rows >= columns) of the synthetic covariance of
+ * emu_cov_build, n = L^2, into dS (device, n x n FP64, column-major, ld >= n);
+ * the strict upper triangle is not touched.  The values are those emu_cov_build
+ * stores.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default)
+ * and the call returns without synchronising.
+ *
+ * Scratch: the correlation and scale tables live in a fixed 1 MiB file-scope
+ * device array instead of allocated memory, which bounds L to 128 (n <= 16384);
+ * a larger L returns EMU_ENOMEM.  Every device that loads the library holds
+ * the array until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams, no ordering between them) race and
+ * may produce wrong values.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  Returns EMU_EINVAL for bad arguments, EMU_ECUDA for a
+ * launch failure. */
+emu_status emu_cov_build_dense_noalloc(int L, double beta, double sigma_exp,
+                                       double nugget_rel, double *dS, long ld,
+                                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

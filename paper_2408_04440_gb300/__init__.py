@@ -32,6 +32,7 @@ EXPORTED = (
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
+    "emu_cov_build_dense_noalloc",
 )
 PROF_GROUPS = ("cov", "map", "potrf", "trsm64", "trsm32", "update64", "tc_factor", "tc_sample", "trmm64",
                "rng", "split", "solve")
@@ -107,11 +108,13 @@ def load() -> ctypes.CDLL:
     L.emu_sample_host.argtypes = [vp, vp, i, ctypes.c_uint64, ctypes.c_uint32, vp, lg]
     L.emu_potrs.argtypes = [vp, vp, vp, lg, vp, lg, i]
     L.emu_solve_refine.argtypes = [vp, vp, vp, vp, lg, vp, lg, i, d, i, ctypes.POINTER(emu_refine_info)]
+    L.emu_cov_build_dense_noalloc.argtypes = [i, d, d, d, vp, lg, vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
                  "emu_trace_enable", "emu_trace_read", "emu_prof_timeline",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
-                 "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine"):
+                 "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
+                 "emu_cov_build_dense_noalloc"):
         getattr(L, name).restype = st
     _lib = L
     return L
