@@ -20,8 +20,10 @@
  *     column-major, with a leading dimension `ld` >= number of rows, and live
  *     in DEVICE memory unless a parameter says "host".
  *   - The library owns `emu_ctx` and `emu_mat` objects; they are released only
- *     by emu_destroy / emu_mat_free.  Caller pointers are borrowed for the
- *     duration of the call and of the stream work it enqueues.
+ *     by emu_destroy / emu_mat_free.  A matrix keeps a pointer to the context
+ *     it was made in: free every matrix before destroying that context.
+ *     Caller pointers are borrowed for the duration of the call and of the
+ *     stream work it enqueues.
  *   - All device work is enqueued on the context's stream (the one given to
  *     emu_create; NULL = the legacy default stream).  Calls that fill an
  *     `info` struct, or that return a status decided on the device

@@ -10,6 +10,7 @@ loudly if ``libemucov.so`` has not been built (``build.build()``).
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 from dataclasses import dataclass, field
 
@@ -146,6 +147,8 @@ class Context:
         self._check(self.lib.emu_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)),
                     "emu_create", with_ctx=False)
         self.h = h
+        # matrices still alive: a matrix must be freed before its context
+        self._mats = weakref.WeakSet()
 
     def _check(self, status: int, where: str, with_ctx: bool = True):
         if status != EMU_OK:
@@ -198,6 +201,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            for m in list(self._mats):
+                m.free()
             self.lib.emu_destroy(self.h)
             self.h = None
 
@@ -214,6 +219,7 @@ class Mat:
     def __init__(self, ctx: Context, handle: ctypes.c_void_p):
         self.ctx = ctx
         self.h = handle
+        ctx._mats.add(self)
 
     def shape_info(self):
         n, nb, nt, st = (ctypes.c_int() for _ in range(4))
@@ -226,9 +232,10 @@ class Mat:
         return self.shape_info()[0]
 
     def free(self):
-        if self.h:
+        # after the context is closed its matrices are already freed
+        if self.h and getattr(self.ctx, "h", None):
             self.ctx.lib.emu_mat_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -119,6 +119,8 @@ struct emu_mat {
   double frob = 0.0;
   // mixed factor operand copies (three BF16 pieces per tile, row-major)
   uint16_t *op_bf16 = nullptr; // ntiles * 3 * nb*nb
+  uint8_t *op_e4m3 = nullptr;  // ntiles * nb*nb FP8-E4M3 copies (row-major), when E4M3 tiles exist
+  float *scale_e4m3 = nullptr; // ntiles power-of-two scales of those copies
   void *plan = nullptr;        // mixed-factor schedule (mixed.cu)
 };
 

@@ -3,8 +3,10 @@
 // ("Mixed-Precision Computation Innovations") and the low-precision part of
 // drawing emulations ("Generating Emulations", xi = V z).
 //
-// Precision classes on the tensor cores (kind::f16, BF16 x BF16 -> FP32):
-//   BF16 class: one product a0 b0 of the round-to-nearest BF16 operands.
+// Precision classes on the tensor cores (FP32 accumulation):
+//   E4M3 class: one kind::f8f6f4 product of FP8-E4M3 copies carrying a
+//     power-of-two scale per tile; the epilogue divides the scales out.
+//   BF16 class: one kind::f16 product a0 b0 of the round-to-nearest BF16 operands.
 //   FP32 class: each FP32 operand is split into three BF16 pieces
 //     x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1))
 //     and the six products with i + j <= 2 are accumulated, smallest first:
@@ -35,6 +37,9 @@ constexpr int SMEM_BYTES = RING_BYTES + BAR_BYTES + 1024;  // + alignment slack
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t IDESC = tc::idesc_f32acc(1u /*BF16*/, BM, BN);
+constexpr uint32_t IDESC8 = tc::idesc_f32acc(0u /*E4M3*/, BM, BN);
+constexpr int A8_BYTES = BM * BK;  // FP8: BK elements = BK bytes per row
+constexpr int B8_BYTES = BN * BK;
 
 struct Shared {
   uint64_t full[STAGES];
@@ -53,10 +58,9 @@ __device__ inline void raise_timeout(Shared *sh, int *status) {
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const Item *__restrict__ items, int nitems, const Seg *__restrict__ segs, int ksteps,
-              int mode, float *__restrict__ out32, double *__restrict__ out64, int ldo,
-              int *status) {
+    k_tc_gemm(const __grid_constant__ Operands ops, const Item *__restrict__ items, int nitems,
+              const Seg *__restrict__ segs, int ksteps, int mode, float *__restrict__ out32,
+              double *__restrict__ out64, int ldo, int *status) {
   extern __shared__ uint8_t smem_raw[];
   uint32_t raw_addr = tc::smem_u32(smem_raw);
   uint32_t pad = ((raw_addr + 1023u) & ~1023u) - raw_addr;
@@ -77,8 +81,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc::mbar_init(&sh->done, 1);
     sh->abort = 0;
     tc::fence_barrier_init();
-    tc::tma_prefetch_desc(&mapA);
-    tc::tma_prefetch_desc(&mapB);
+    tc::tma_prefetch_desc(&ops.a16);
+    tc::tma_prefetch_desc(&ops.b16);
   }
   if (warp == 1) {
     tc::tmem_alloc(&sh->tmem_base, TMEM_COLS);
@@ -100,8 +104,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         Item item = items[it];
         for (int sg = item.seg_begin; sg < item.seg_end && ok; sg++) {
           Seg s = segs[sg];
+          bool f8 = s.cls == EMU_CLASS_E4M3;
           int np = (s.cls == EMU_CLASS_FP32) ? NPIECE : 1;
-          uint32_t bytes = (uint32_t)np * (A_PIECE + B_PIECE);
+          uint32_t bytes = f8 ? (uint32_t)(A8_BYTES + B8_BYTES) : (uint32_t)np * (A_PIECE + B_PIECE);
           for (int kc = 0; kc < ksteps; kc++) {
             if (!tc::mbar_wait(&sh->empty[stage], phase ^ 1u, abort)) {
               raise_timeout(sh, status);
@@ -110,10 +115,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::mbar_arrive_expect_tx(&sh->full[stage], bytes);
             uint8_t *st = ring + stage * STAGE_BYTES;
-            for (int q = 0; q < np; q++) {
-              tc::tma_load_2d(st + q * A_PIECE, &mapA, &sh->full[stage], s.ax + kc * BK, s.ay + q * s.ay_step);
-              tc::tma_load_2d(st + NPIECE * A_PIECE + q * B_PIECE, &mapB, &sh->full[stage], s.bx + kc * BK,
-                              s.by + q * s.by_step);
+            if (f8) {
+              tc::tma_load_2d(st, &ops.a8, &sh->full[stage], s.ax + kc * BK, s.ay);
+              tc::tma_load_2d(st + NPIECE * A_PIECE, &ops.b8, &sh->full[stage], s.bx + kc * BK, s.by);
+            } else {
+              for (int q = 0; q < np; q++) {
+                tc::tma_load_2d(st + q * A_PIECE, &ops.a16, &sh->full[stage], s.ax + kc * BK,
+                                s.ay + q * s.ay_step);
+                tc::tma_load_2d(st + NPIECE * A_PIECE + q * B_PIECE, &ops.b16, &sh->full[stage], s.bx + kc * BK,
+                                s.by + q * s.by_step);
+              }
             }
             if (++stage == STAGES) {
               stage = 0;
@@ -160,14 +171,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::fence_after_sync();
             uint32_t st = ring_addr + stage * STAGE_BYTES;
+            if (cls == EMU_CLASS_E4M3) {
+              // one K = 32 product of the FP8 copies (rows of 32 bytes, 32-byte swizzle)
+              uint64_t ad = tc::smem_desc(st, 16, 256, tc::kSwizzle32B);
+              uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE, 16, 256, tc::kSwizzle32B);
+              tc::mma_f8(d_tmem, ad, bd, IDESC8, accumulate);
+              accumulate = 1;
+            } else {
 #pragma unroll
-            for (int ks = 0; ks < BK / 16; ks++) {
-              for (int p = p0; p < 6; p++) {
-                uint64_t ad = tc::smem_desc(st + pa[p] * A_PIECE + ks * 32, 16, 512, tc::kSwizzle64B);
-                uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE + pb[p] * B_PIECE + ks * 32, 16, 512,
-                                            tc::kSwizzle64B);
-                tc::mma_f16(d_tmem, ad, bd, IDESC, accumulate);
-                accumulate = 1;
+              for (int ks = 0; ks < BK / 16; ks++) {
+                for (int p = p0; p < 6; p++) {
+                  uint64_t ad = tc::smem_desc(st + pa[p] * A_PIECE + ks * 32, 16, 512, tc::kSwizzle64B);
+                  uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE + pb[p] * B_PIECE + ks * 32, 16, 512,
+                                              tc::kSwizzle64B);
+                  tc::mma_f16(d_tmem, ad, bd, IDESC, accumulate);
+                  accumulate = 1;
+                }
               }
             }
             tc::mma_commit(&sh->empty[stage]);  // frees the stage once these MMAs complete
@@ -212,8 +231,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           float c[32];
 #pragma unroll
           for (int x = 0; x < 32; x++) c[x] = __ldcg(o + (long)x * ldo);
+          // E4M3 items: undo the operands' power-of-two scales (exact)
+          float sc = (item.sa >= 0) ? 1.0f / (ops.scale8[item.sa] * ops.scale8[item.sb]) : 1.0f;
 #pragma unroll
-          for (int x = 0; x < 32; x++) __stcg(o + (long)x * ldo, c[x] - __uint_as_float(r[x]));
+          for (int x = 0; x < 32; x++) __stcg(o + (long)x * ldo, c[x] - __uint_as_float(r[x]) * sc);
         } else {
           if (row < item.rows_valid) {
             double *o = out64 + item.out_off + row + (long)(ch * 32) * ldo;
@@ -282,9 +303,33 @@ emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint6
   return EMU_OK;
 }
 
-emu_status launch(emu_ctx *ctx, const CUtensorMap &mapA, const CUtensorMap &mapB, const Item *d_items,
-                  int nitems, const Seg *d_segs, int ksteps, int mode, float *out32, double *out64, int ldo,
-                  int max_ctas) {
+emu_status make_map_e4m3(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows,
+                         uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    ctx->last_error = "cuTensorMapEncodeTiled unavailable";
+    return EMU_ECUDA;
+  }
+  if (((uintptr_t)base & 15u) != 0 || inner % 16 != 0 || inner % BK != 0) {
+    ctx->last_error = "TMA operand base/stride not 16-byte aligned";
+    return EMU_EINVAL;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed";
+    return EMU_ECUDA;
+  }
+  return EMU_OK;
+}
+
+emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
+                  int ksteps, int mode, float *out32, double *out64, int ldo, int max_ctas) {
   if (nitems <= 0) return EMU_OK;
   static bool attr_done = false;
   if (!attr_done) {
@@ -292,8 +337,8 @@ emu_status launch(emu_ctx *ctx, const CUtensorMap &mapA, const CUtensorMap &mapB
     attr_done = true;
   }
   int grid = nitems < max_ctas ? nitems : max_ctas;
-  k_tc_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(mapA, mapB, d_items, nitems, d_segs, ksteps, mode,
-                                                         out32, out64, ldo, ctx->d_status);
+  k_tc_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(ops, d_items, nitems, d_segs, ksteps, mode, out32,
+                                                         out64, ldo, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -2,9 +2,10 @@
 //
 // One launch processes a list of output blocks ("items") of BM x BN.  Each
 // item accumulates, in a TMEM FP32 accumulator, the sum over its segments of
-// A_seg * B_seg^T, where A_seg (BM x nb) and B_seg (BN x nb) are K-major BF16
-// operand blocks fetched by TMA (three split pieces per operand for the FP32
-// class, one for BF16), then applies the epilogue:
+// A_seg * B_seg^T, where A_seg (BM x nb) and B_seg (BN x nb) are K-major
+// operand blocks fetched by TMA (three BF16 split pieces per operand for the
+// FP32 class, one BF16 piece for BF16, one FP8-E4M3 copy for E4M3, whose
+// per-tile scales the epilogue divides out), then applies the epilogue:
 //   mode TC_SUB_F32: out32[off + r + c*ldo] -= acc   (trailing tile update)
 //   mode TC_ADD_F64: out64[off + r + c*ldo] += acc   (sampling, r/c bounded)
 #pragma once
@@ -25,7 +26,7 @@ enum { TC_SUB_F32 = 0, TC_ADD_F64 = 1 };
 struct Seg {
   int ax, ay, ay_step;  // TMA coordinates of A piece 0 (x = K offset) and piece stride in rows
   int bx, by, by_step;  // same for B
-  int cls;              // EMU_CLASS_FP32 (6 products) or EMU_CLASS_BF16 (1 product)
+  int cls;              // EMU_CLASS_FP32 (6 products), EMU_CLASS_BF16 (1), EMU_CLASS_E4M3 (1, FP8 copies)
   int pad;
 };
 
@@ -33,6 +34,15 @@ struct Item {
   int seg_begin, seg_end;
   long out_off;
   int rows_valid, cols_valid;  // TC_ADD_F64 only
+  int sa, sb;                  // E4M3 items: tiles whose scales multiply A and B (else -1)
+};
+
+// Operand sources of a launch: BF16 pieces (A box 128 x 32, B box 256 x 32,
+// 64-byte swizzle) and FP8-E4M3 copies (same boxes in bytes, 32-byte swizzle)
+// with one power-of-two scale per tile.
+struct Operands {
+  CUtensorMap a16, b16, a8, b8;
+  const float *scale8;
 };
 
 // 2-D BF16 tensor map over a row-major [rows x inner] array, box
@@ -40,8 +50,12 @@ struct Item {
 emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
                          uint64_t rows, uint32_t box_rows);
 
-emu_status launch(emu_ctx *ctx, const CUtensorMap &mapA, const CUtensorMap &mapB, const Item *d_items,
-                  int nitems, const Seg *d_segs, int ksteps, int mode, float *out32, double *out64,
-                  int ldo, int max_ctas);
+// 2-D FP8 tensor map over a row-major [rows x inner] byte array, box
+// [box_rows x 32], 32-byte swizzle.
+emu_status make_map_e4m3(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
+                         uint64_t rows, uint32_t box_rows);
+
+emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
+                  int ksteps, int mode, float *out32, double *out64, int ldo, int max_ctas);
 
 }  // namespace gemm_tc

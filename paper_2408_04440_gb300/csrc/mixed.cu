@@ -12,6 +12,7 @@
 // three BF16 pieces, row-major (K-major), in the operand arena `op`; every
 // consumer reads the pieces its class needs (three for FP32, one for BF16).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <string.h>
 
@@ -107,6 +108,43 @@ __global__ void k_split_tiles(const T *__restrict__ src, uint16_t *__restrict__ 
     o[plane + off] = p1;
     o[2 * plane + off] = p2;
   }
+}
+
+// FP8-E4M3 copies of whole panel tiles for E4M3-class consumers, from the
+// leading BF16 piece (already row-major / K-major).  One CTA per listed tile:
+// amax over the tile, power-of-two scale s = 2^floor(log2(448 / amax)) so
+// that |x s| <= 448 (the largest finite E4M3), then a saturating,
+// round-to-nearest conversion of x s.  Zero tiles get s = 1.
+__global__ void __launch_bounds__(1024)
+    k_quant_e4m3(const uint16_t *__restrict__ op, uint8_t *__restrict__ op8, float *__restrict__ scale,
+                 const int *__restrict__ tiles, int nb, const int *st) {
+  if (failed(st)) return;
+  __shared__ float red[32];
+  __shared__ float s_scale;
+  long t = tiles[blockIdx.x];
+  size_t plane = (size_t)nb * nb;
+  const uint16_t *x0 = op + (size_t)t * 3 * plane;
+  float amax = 0.f;
+  for (size_t e = threadIdx.x; e < plane; e += blockDim.x)
+    amax = fmaxf(amax, fabsf(__bfloat162float(__ushort_as_bfloat16(x0[e]))));
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
+    // 448 / m = f 2^e with f in [0.5, 1): the largest power of two not above it is 2^(e-1)
+    int e = 1;
+    if (m > 0.f) frexpf(448.f / m, &e);
+    s_scale = ldexpf(1.f, e - 1);
+    scale[t] = s_scale;
+  }
+  __syncthreads();
+  float s = s_scale;
+  uint8_t *q = op8 + (size_t)t * plane;
+  for (size_t e = threadIdx.x; e < plane; e += blockDim.x)
+    q[e] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(__ushort_as_bfloat16(x0[e])) * s, __NV_SATFINITE,
+                                          __NV_E4M3);
 }
 
 // FP32 panel TRSM for the low-precision tiles of column k:
@@ -383,6 +421,7 @@ enum { GR_S = 0, GR_G1 = 1, GR_G2A = 2, GR_G2 = 3, GR_N = 4 };
 struct StepPlan {
   int r64_1 = 0, n64_1 = 0, r32_1 = 0, n32_1 = 0;  // T1 (offset, count) in rows64 / rows32
   int r64_r = 0, n64_r = 0, r32_r = 0, n32_r = 0;  // TR
+  int q_1 = 0, nq_1 = 0, q_r = 0, nq_r = 0;        // panel tiles to quantize to E4M3 (row k+1 / rest)
   int p_off[GR_N] = {}, p_n[GR_N] = {};            // FP64 pairs per update group
   int i_off[GR_N] = {}, i_n[GR_N] = {};            // tensor-core items per update group
   double flops[GR_N] = {}, mma[GR_N] = {};
@@ -398,6 +437,9 @@ struct MixedPlan {
   gemm_tc::Item *d_items = nullptr;
   gemm_tc::Seg *d_segs = nullptr;
   int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
+  int *d_qtiles = nullptr;            // panel tiles quantized to E4M3, per step (see StepPlan)
+  bool any_e4m3 = false;
+  gemm_tc::Operands ops;
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
   CUtensorMap mapA, mapB;
@@ -427,7 +469,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->nb = nb;
   P->cls.assign(A->h_cls, A->h_cls + A->ntiles);
   auto C = [&](int i, int j) { return (int)P->cls[tile_index(i, j, NT)]; };
-  std::vector<int> rows64, rows32, tiles64, diag;
+  std::vector<int> rows64, rows32, tiles64, diag, qtiles;
   std::vector<int2> pairs;
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
@@ -445,16 +487,20 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
       sp.p_n[g]++;
       return;
     }
-    int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;  // TF32/E4M3 fall back
+    int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : (c == EMU_CLASS_E4M3) ? EMU_CLASS_E4M3 : EMU_CLASS_BF16;
+    bool f8 = cc == EMU_CLASS_E4M3;
+    if (f8) P->any_e4m3 = true;
+    long tik = tile_index(i, k, NT), tjk = tile_index(j, k, NT);
     for (int nbk = 0; nbk < nb / gemm_tc::BN; nbk++)
       for (int mb = 0; mb < nb / gemm_tc::BM; mb++) {
         if (i == j && mb * gemm_tc::BM + gemm_tc::BM - 1 < nbk * gemm_tc::BN) continue;  // above the diagonal
+        // BF16 pieces: row (tile*3 + piece)*nb + r; FP8 copies: row tile*nb + r
         gemm_tc::Seg s;
         s.ax = 0;
-        s.ay = (int)(tile_index(i, k, NT) * 3 * nb + mb * gemm_tc::BM);
+        s.ay = (int)(tik * (f8 ? 1 : 3) * nb + mb * gemm_tc::BM);
         s.ay_step = nb;
         s.bx = 0;
-        s.by = (int)(tile_index(j, k, NT) * 3 * nb + nbk * gemm_tc::BN);
+        s.by = (int)(tjk * (f8 ? 1 : 3) * nb + nbk * gemm_tc::BN);
         s.by_step = nb;
         s.cls = cc;
         s.pad = 0;
@@ -465,6 +511,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         it.out_off = tile_index(i, j, NT) * (long)nb * nb + mb * gemm_tc::BM + (long)nbk * gemm_tc::BN * nb;
         it.rows_valid = gemm_tc::BM;
         it.cols_valid = gemm_tc::BN;
+        it.sa = f8 ? (int)tik : -1;
+        it.sb = f8 ? (int)tjk : -1;
         items.push_back(it);
         double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
         sp.i_n[g]++;
@@ -506,6 +554,23 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
           for (int i = j; i < NT; i++) add_tile_update(sp, g, k, i, j);
       }
     }
+    // E4M3 consumers read FP8 copies of the panel tiles: quantize them all
+    // when the step has any E4M3 update
+    bool step_f8 = false;
+    for (int g = 0; g < GR_N; g++)
+      for (int q = sp.i_off[g]; q < sp.i_off[g] + sp.i_n[g]; q++)
+        if (items[q].sa >= 0) step_f8 = true;
+    sp.q_1 = (int)qtiles.size();
+    if (step_f8 && k + 1 < NT) {
+      qtiles.push_back((int)tile_index(k + 1, k, NT));
+      sp.nq_1 = 1;
+    }
+    sp.q_r = (int)qtiles.size();
+    if (step_f8)
+      for (int i = k + 2; i < NT; i++) {
+        qtiles.push_back((int)tile_index(i, k, NT));
+        sp.nq_r++;
+      }
     P->steps.push_back(sp);
   }
   // one allocation and one copy for all lists (256-byte aligned parts)
@@ -518,7 +583,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   auto vbytes = [](const auto &v) { return v.size() * sizeof(v[0]); };
   size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_pairs = part(vbytes(pairs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
-         o_diag = part(vbytes(diag)), o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
+         o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)),
+         o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
   size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
   P->host_blob.assign(copy_bytes, 0);
   auto put = [&](size_t o, const auto &v) {
@@ -531,6 +597,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   put(o_segs, segs);
   put(o_t64, tiles64);
   put(o_diag, diag);
+  put(o_q, qtiles);
   P->stream = ctx->stream;
   EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_blob, off, ctx->stream));
   char *b = static_cast<char *>(P->d_blob);
@@ -542,11 +609,27 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_segs = reinterpret_cast<gemm_tc::Seg *>(b + o_segs);
   P->d_tiles64 = reinterpret_cast<int *>(b + o_t64);
   P->d_diag_tiles = reinterpret_cast<int *>(b + o_diag);
+  P->d_qtiles = reinterpret_cast<int *>(b + o_q);
   P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
   emu_status s;
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapA, A->op_bf16, nb, rows, gemm_tc::BM)) != EMU_OK) return s;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapB, A->op_bf16, nb, rows, gemm_tc::BN)) != EMU_OK) return s;
+  P->ops.a16 = P->mapA;
+  P->ops.b16 = P->mapB;
+  P->ops.a8 = P->mapA;  // valid maps even when no FP8 copies exist (then never used)
+  P->ops.b8 = P->mapB;
+  P->ops.scale8 = nullptr;
+  if (P->any_e4m3) {
+    size_t te = (size_t)nb * nb;
+    if (!A->op_e4m3) EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->op_e4m3, (size_t)A->ntiles * te, ctx->stream));
+    if (!A->scale_e4m3)
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->scale_e4m3, (size_t)A->ntiles * sizeof(float), ctx->stream));
+    uint64_t rows8 = (uint64_t)A->ntiles * nb;
+    if ((s = gemm_tc::make_map_e4m3(ctx, &P->ops.a8, A->op_e4m3, nb, rows8, gemm_tc::BM)) != EMU_OK) return s;
+    if ((s = gemm_tc::make_map_e4m3(ctx, &P->ops.b8, A->op_e4m3, nb, rows8, gemm_tc::BN)) != EMU_OK) return s;
+    P->ops.scale8 = A->scale_e4m3;
+  }
   return EMU_OK;
 }
 
@@ -580,8 +663,8 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   double u[EMU_NCLASS] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8, 0x1p-4};
   for (int c = 0; c < EMU_NCLASS; c++)
     if (o->u[c] > 0.0) u[c] = o->u[c];
-  // TF32 and E4M3 classes are not built on the tensor cores yet: leave them out
-  unsigned mask = (o->prec_mask | 1u) & ((1u << EMU_CLASS_FP32) | (1u << EMU_CLASS_BF16) | 1u);
+  // the TF32 class is not built on the tensor cores yet: leave it out
+  unsigned mask = (o->prec_mask | 1u) & ((1u << EMU_CLASS_FP32) | (1u << EMU_CLASS_BF16) | (1u << EMU_CLASS_E4M3) | 1u);
   emu_status s = launch_precision_map(ctx, A, o->eps, u, mask, o->diag_fp64);
   if (s != EMU_OK) return s;
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(A->h_cls, A->d_cls, A->ntiles, cudaMemcpyDeviceToHost, ctx->stream));
@@ -626,6 +709,13 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
                                          (int)tsm4));
 
   // TRSM of the listed rows of panel k (FP64 rows on the FP64 pipe, then split)
+  auto quantize = [&](int q0, int nq) -> emu_status {
+    if (nq <= 0) return EMU_OK;
+    ProfScope ps(ctx, PROF_SPLIT, 0.0, 3.0 * nq * te);
+    k_quant_e4m3<<<nq, 1024, 0, ctx->stream>>>(A->op_bf16, A->op_e4m3, A->scale_e4m3, P->d_qtiles + q0, nb, st);
+    EMU_LAUNCHED(ctx);
+    return EMU_OK;
+  };
   auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
     emu_status e = EMU_OK;
     if (n64 > 0) {
@@ -661,7 +751,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
       ProfScope ps(ctx, PROF_TC_FACTOR, sp.flops[g], 0.0, sp.mma[g]);
       int in = sp.i_n[g];
       int ctas = std::max(1, max_ctas);
-      return gemm_tc::launch(ctx, P->mapA, P->mapB, P->d_items + sp.i_off[g], in, P->d_segs, nb / gemm_tc::BK,
+      return gemm_tc::launch(ctx, P->ops, P->d_items + sp.i_off[g], in, P->d_segs, nb / gemm_tc::BK,
                              gemm_tc::TC_SUB_F32, A->t32, nullptr, nb, ctas);
     }
     return EMU_OK;
@@ -686,6 +776,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
     if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
+    if ((s = quantize(sp.q_1, sp.nq_1)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T1), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G2), 0));  // G2A(k-1)
     if ((s = update_group(k, GR_S, ctx->sm_count)) != EMU_OK) break;
@@ -693,6 +784,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     ctx->stream = ctx->mid;
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_P), 0));
     if ((s = trsm_rows(k, sp.r64_r, sp.n64_r, sp.r32_r, sp.n32_r, false)) != EMU_OK) break;
+    if ((s = quantize(sp.q_r, sp.nq_r)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T), ctx->mid));
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_T1), 0));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k - 1, E_G2), 0));
@@ -764,6 +856,7 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
           sg.bx = k * nb;
           sg.by = nbk * gemm_tc::BN;
           sg.by_step = s_pad;
+          // the sampler reads E4M3-class tiles through their leading BF16 piece
           sg.cls = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;
           sg.pad = 0;
           segs.push_back(sg);
@@ -773,6 +866,7 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
         it.out_off = row0 + (long)nbk * gemm_tc::BN * ldy;
         it.rows_valid = (int)std::min<long>(gemm_tc::BM, L->n - row0);
         it.cols_valid = s - nbk * gemm_tc::BN;
+        it.sa = it.sb = -1;
         items.push_back(it);
       }
   if (items.empty()) return EMU_OK;
@@ -798,11 +892,11 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
       tf += f;
       tm += f * (segs[q].cls == EMU_CLASS_FP32 ? 6.0 : 1.0);
     }
-  CUtensorMap mapB;
-  st = gemm_tc::make_map_bf16(ctx, &mapB, zp, npad, (uint64_t)3 * s_pad, gemm_tc::BN);
+  gemm_tc::Operands ops = P->ops;
+  st = gemm_tc::make_map_bf16(ctx, &ops.b16, zp, npad, (uint64_t)3 * s_pad, gemm_tc::BN);
   ProfScope ps(ctx, PROF_TC_SAMPLE, tf, 0.0, tm);
   if (st == EMU_OK)
-    st = gemm_tc::launch(ctx, P->mapA, mapB, d_items, (int)items.size(), d_segs, nb / gemm_tc::BK,
+    st = gemm_tc::launch(ctx, ops, d_items, (int)items.size(), d_segs, nb / gemm_tc::BK,
                          gemm_tc::TC_ADD_F64, nullptr, Y, (int)ldy, ctx->sm_count);
   cudaFreeAsync(zp, ctx->stream);
   cudaFreeAsync(d_items, ctx->stream);

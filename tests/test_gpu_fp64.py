@@ -181,3 +181,14 @@ def test_profiler_counts_launches(E, ctx):
     ctx.prof_enable(False)
     assert prof["cov"]["launches"] >= 1 and prof["potrf"]["launches"] >= 3
     assert prof["update64"]["flops"] > 0 and prof["potrf"]["ms"] > 0
+
+
+def test_matrix_outliving_its_context(E):
+    # closing a context frees the matrices made in it; a Python handle that
+    # outlives the context then frees nothing (no use of the freed context)
+    c = E.Context(0)
+    A = E.emu_cov_build(c, 6, 2.0, 64)
+    c.close()
+    assert A.h is None
+    A.free()
+    del A

@@ -136,3 +136,81 @@ def test_mixed_refinement(E, ctx):
     Xo = O.potrs(Lo, B)
     print(f"refine: {ri.iters} iterations, forward error vs oracle "
           f"{np.linalg.norm(X - Xo) / np.linalg.norm(Xo):.2e}")
+
+
+MASK_WITH_E4M3 = 0b11011  # FP64, FP32, BF16, FP8-E4M3
+
+
+def _bf16_rn(x):
+    """Round float64 values to BF16 (8 significant bits, nearest, ties to
+    even), returned as float64; normal-range values only."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)
+
+
+@pytest.mark.parametrize("L,beta,eps", [(40, 5.0, 1e-2), (40, 5.0, 1e-4), (64, 4.0, 1e-6)])
+def test_e4m3_class_meets_eps(E, ctx, L, beta, eps):
+    # the rule puts the far tiles on FP8-E4M3 (u = 2^-4): their trailing
+    # updates run as kind::f8f6f4 products of per-tile power-of-two-scaled
+    # copies, and the factor must still meet the normwise target
+    nb = 256
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=MASK_WITH_E4M3)
+    assert info.status == E.EMU_OK
+    S = O.cov_build(L, beta)
+    cls, _ = E.emu_mat_tile_info(ctx, A)
+    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_WITH_E4M3)
+    assert info.tiles[4] > 0
+    G = _np(E.emu_mat_export(ctx, A))
+    be = _backward_error(G, S)
+    assert be <= eps, be
+    print(f"L={L} eps={eps:g}: backward {be:.2e}, tiles {info.tiles}")
+
+
+def test_e4m3_sampling_reads_bf16_piece(E, ctx):
+    # low-precision tiles of L are sampled on the tensor cores with both
+    # operands in BF16 (E4M3-class tiles too): block row i of Y is
+    # sum_k L_ik Z_k over FP64/FP32 tiles plus bf16(L_ik) bf16(Z_k) over the
+    # BF16/E4M3 tiles, up to FP32 accumulation
+    L, nb, beta, eps, s = 40, 256, 5.0, 1e-4, 200
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=MASK_WITH_E4M3)
+    cls, _ = E.emu_mat_tile_info(ctx, A)
+    assert (cls == 4).any()
+    G = _np(E.emu_mat_export(ctx, A))
+    Y, Z = E.emu_sample(ctx, A, s, seed=3, return_z=True)
+    Y, Z = _np(Y), _np(Z)
+    n, NT = L * L, cls.shape[0]
+    Zb = _bf16_rn(Z)
+    ref = np.zeros_like(Y)
+    for i in range(NT):
+        ri = np.s_[i * nb:min(n, (i + 1) * nb)]
+        for k in range(i + 1):
+            ck = np.s_[k * nb:min(n, (k + 1) * nb)]
+            if cls[i, k] in (3, 4):
+                ref[ri] += _bf16_rn(G[ri, ck]) @ Zb[ck]
+            else:
+                ref[ri] += G[ri, ck] @ Z[ck]
+    rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-6, rel
+    print(f"sampling with E4M3 tiles: {rel:.2e} vs the BF16-operand product")
+
+
+def test_e4m3_refinement(E, ctx):
+    import torch
+
+    L, nb, beta = 64, 256, 4.0
+    S_mat = E.emu_cov_build(ctx, L, beta, nb)
+    A = E.emu_mat_clone(ctx, S_mat)
+    info = E.emu_potrf_mp(ctx, A, eps=1e-6, prec_mask=MASK_WITH_E4M3)
+    assert info.tiles[4] > 0
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((L * L, 8))
+    X, ri = E.emu_solve_refine(ctx, A, S_mat, torch.from_numpy(B).cuda(), tol=1e-15, maxit=100)
+    assert ri.status == E.EMU_OK
+    X = _np(X)
+    S = O.cov_build(L, beta)
+    eta = np.linalg.norm(B - S @ X, axis=0) / (np.linalg.norm(S) * np.linalg.norm(X, axis=0)
+                                               + np.linalg.norm(B, axis=0))
+    assert eta.max() <= 2e-15
+    print(f"refine with E4M3 tiles: {ri.iters} iterations")
