@@ -57,9 +57,11 @@ typedef enum {
 
 /* Precision classes of a tile, most precise first.  The unit roundoff u that
  * the precision rule uses for each class is in emu_mp_opts.u (defaults:
- * 2^-53, 2^-24, 2^-11, 2^-8, 2^-4).  "fp32" is computed on the tensor cores
- * as a three-way BF16 split of each operand (six partial products, FP32
- * accumulation); "e4m3" carries a power-of-two scale per tile. */
+ * 2^-53, 2^-24 * sqrt(nb), 2^-11, 2^-8, 2^-4).  "fp32" is computed on the
+ * tensor cores as a three-way BF16 split of each operand (six partial
+ * products, FP32 accumulation); its default u carries the sqrt(nb) growth of
+ * the error of an nb-term FP32 accumulation relative to the tile norm.
+ * "e4m3" carries a power-of-two scale per tile. */
 enum {
   EMU_CLASS_FP64 = 0,
   EMU_CLASS_FP32 = 1,

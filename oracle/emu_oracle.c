@@ -55,6 +55,7 @@ void orc_cov_rows(int L, double beta, double sigma_exp, double nugget_rel,
     double s = pow(1.0 + l, -sigma_exp);
     if (s * s > dmax) dmax = s * s;
   }
+#pragma omp parallel for schedule(static)
   for (int q = 0; q < nrows; q++) {
     long i = rows[q];
     int li, mi;

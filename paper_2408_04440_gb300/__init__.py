@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "EMU_OK", 1: "EMU_EINVAL", 2: "EMU_ENOMEM", 3: "EMU_ENOTPD", 
 CLASS_FP64, CLASS_FP32, CLASS_TF32, CLASS_BF16, CLASS_E4M3 = range(5)
 NCLASS = 5
 CLASS_NAMES = ("fp64", "fp32", "tf32", "bf16", "e4m3")
-DEFAULT_U = (2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4)
+# u[c] <= 0 asks the library for its default unit roundoff of class c
+DEFAULT_U = (0.0,) * 5
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (

@@ -660,7 +660,13 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     ctx->last_error = "the mixed-precision factor needs nb to be a multiple of 256";
     return EMU_EINVAL;
   }
-  double u[EMU_NCLASS] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8, 0x1p-4};
+  // Default unit roundoffs.  The FP32 class takes the FP32 accumulation of
+  // an nb-term update into account: its error in tile (i,j) is bounded by
+  // 2^-24 sum_k ||L_ik||_F ||L_jk||_F, which on the diagonal tiles reaches
+  // sqrt(nb) 2^-24 ||S_ii||_F (trace against Frobenius norm), the same factor
+  // as the probabilistic bound on an nb-term FP32 sum.  For BF16 and E4M3 the
+  // operand rounding (2^-8, 2^-4) is far larger than that and stays the bound.
+  double u[EMU_NCLASS] = {0x1p-53, 0x1p-24 * sqrt((double)nb), 0x1p-11, 0x1p-8, 0x1p-4};
   for (int c = 0; c < EMU_NCLASS; c++)
     if (o->u[c] > 0.0) u[c] = o->u[c];
   // the TF32 class is not built on the tensor cores yet: leave it out

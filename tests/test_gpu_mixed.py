@@ -10,8 +10,13 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-U = np.array([2.0**-53, 2.0**-24, 2.0**-11, 2.0**-8, 2.0**-4])
 MASK_FP64_FP32_BF16 = 0b01011
+
+
+def U_of(nb):
+    """The library's default unit roundoffs: the FP32 class carries the
+    sqrt(nb) growth of an nb-term FP32 accumulation."""
+    return np.array([2.0**-53, 2.0**-24 * np.sqrt(nb), 2.0**-11, 2.0**-8, 2.0**-4])
 
 
 @pytest.fixture(scope="module")
@@ -38,9 +43,10 @@ def _backward_error(Lf, S):
     return np.linalg.norm(Lf @ Lf.T - S) / np.linalg.norm(S)
 
 
-def _map_matches(cls_gpu, t, eps, mask, diag_fp64=False):
+def _map_matches(cls_gpu, t, eps, mask, nb, diag_fp64=False):
     """Classes equal the oracle's, except where a tile sits within 1e-12 of a
     class threshold (both sides round their norms differently)."""
+    U = U_of(nb)
     cls_o = O.precision_map(t, eps, U, mask, diag_fp64)
     NT = t.shape[0]
     thr = eps * O.frob_from_tiles(t) / NT
@@ -60,7 +66,7 @@ def test_mixed_factor_meets_eps(E, ctx, L, nb, beta, eps):
     assert info.status == E.EMU_OK
     S = O.cov_build(L, beta)
     cls, _ = E.emu_mat_tile_info(ctx, A)
-    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_FP64_FP32_BF16)
+    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_FP64_FP32_BF16, nb)
     assert sum(info.tiles) == (info.nt * (info.nt + 1)) // 2
     G = _np(E.emu_mat_export(ctx, A))
     be = _backward_error(G, S)
@@ -91,7 +97,7 @@ def test_fp32_class_accuracy_against_oracle(E, ctx):
     S = O.cov_build(L, beta)
     t = O.tile_norms(S, nb)
     NT = t.shape[0]
-    eps = 1.01 * t.max() * U[1] * NT / O.frob_from_tiles(t)
+    eps = 1.01 * t.max() * U_of(nb)[1] * NT / O.frob_from_tiles(t)
     A = E.emu_cov_build(ctx, L, beta, nb)
     info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=0b00011)
     assert info.tiles[1] == NT * (NT + 1) // 2
@@ -159,7 +165,7 @@ def test_e4m3_class_meets_eps(E, ctx, L, beta, eps):
     assert info.status == E.EMU_OK
     S = O.cov_build(L, beta)
     cls, _ = E.emu_mat_tile_info(ctx, A)
-    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_WITH_E4M3)
+    _map_matches(cls, O.tile_norms(S, nb), eps, MASK_WITH_E4M3, nb)
     assert info.tiles[4] > 0
     G = _np(E.emu_mat_export(ctx, A))
     be = _backward_error(G, S)
