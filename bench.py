@@ -227,6 +227,7 @@ def run_ours(a):
             extra["fp64_factor_ms"] = round(i64.ms, 3)
             extra["fp64_tflops"] = round(flops / (i64.ms * 1e-3) / 1e12, 4)
             extra["speedup_vs_fp64"] = round(i64.ms / mixed_factor_ms, 2)
+            extra["cusolver_dpotrf"] = cusolver_reference(E, ctx, a, flops)
 
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
 
@@ -253,6 +254,16 @@ def run_ours(a):
 TRAFFIC = {"potrf": 1.21e6}
 
 
+FP64_NOTES = {
+    "potrf": "the diagonal-tile POTRF is bound by its FP64 dependency chain (one 16-column leaf after another)",
+    "update64": "FP64 tile updates are FP64-pipe bound; their launch times include sharing the SMs with the "
+                "concurrent streams",
+    "trsm64": "the FP64 panel TRSM is bound by its substitution chain and by the SMs left beside the bulk update",
+    "trmm64": "FP64-class tiles of the sampler, FP64-pipe bound",
+    "solve": "triangular solves, bound by their substitution chains",
+}
+
+
 def roofline(prof: dict, peaks: dict) -> dict:
     """Roofline of the kernel group with the largest device time in the step."""
     group = max(prof, key=lambda k: prof[k]["ms"])
@@ -275,8 +286,7 @@ def roofline(prof: dict, peaks: dict) -> dict:
         return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": fp64, "unit": "TFLOP/s",
                 "frac": round(achieved / fp64, 4), "traffic": TRAFFIC.get(group),
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
-                "peak_note": "FP64 DFMA peak measured with a DFMA loop; the kernel is bound by its FP64 "
-                             "dependency chain (see profiles/k_potrf_dag_full.md)"}
+                "peak_note": "FP64 DFMA peak measured with a DFMA loop; " + FP64_NOTES.get(group, "")}
     hbm = peaks.get("hbm_gbs") or 6800.0
     achieved = g["bytes"] / (g["ms"] * 1e-3) / 1e9
     return {"kernel": group, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -303,6 +313,31 @@ def backward_error_rows(E, ctx, a, rows: int) -> float:
     del Sd, Ld, R
     torch.cuda.empty_cache()
     return be
+
+
+def cusolver_reference(E, ctx, a, flops) -> dict:
+    """cuSOLVER's dense FP64 Cholesky (torch.linalg.cholesky) of the same
+    covariance on the same GPU: an extra reference row, not our path."""
+    import torch
+
+    A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+    Sd = E.emu_mat_export(ctx, A)
+    A.free()
+    Sd = Sd + Sd.t() - torch.diag(torch.diag(Sd))
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Lc = torch.linalg.cholesky(Sd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del Lc
+    del Sd
+    torch.cuda.empty_cache()
+    t = min(ms)
+    return {"ms": round(t, 3), "tflops": round(flops / (t * 1e-3) / 1e12, 4),
+            "call": "torch.linalg.cholesky (cuSOLVER potrf), FP64, dense n x n"}
 
 
 def run_e2e(E, ctx, a, flops) -> dict:

@@ -274,53 +274,62 @@ static size_t trsm32_smem(int nb, int rows) {
 
 // FP64-class trailing tiles: C_ij -= L_ik L_jk^T in FP64; each operand comes
 // from the FP64 master or (widened) from the FP32 master, by its class.
+// One CTA of 256 threads per (BMT x BMT output block, listed pair): 4x4
+// outputs per thread for BMT = 64, 2x2 for BMT = 32.  The FP64 pipe (about 2
+// FMA per clock per SM) is the bound, so a launch wants at least one CTA per
+// SM: a single tile (the critical-path SYRK) takes the 32 x 32 blocks.
 constexpr int GM = 64, GK = 16;
+template <int BMT>
 __global__ void __launch_bounds__(256)
     k_update64_list(double *__restrict__ t64, const float *__restrict__ t32,
                     const unsigned char *__restrict__ cls, int nb, int NT, int k, const int2 *__restrict__ pairs,
                     const int *st) {
+  constexpr int R = BMT / 16;  // outputs per thread along each dimension
   if (failed(st)) return;
   int2 pr = pairs[blockIdx.x];
   int i = pr.x, j = pr.y;
-  int nsub = nb / GM;
+  int nsub = nb / BMT;
   int bi = blockIdx.y % nsub, bj = blockIdx.y / nsub;
   if (i == j && bi < bj) return;
   long tik = tile_index(i, k, NT), tjk = tile_index(j, k, NT);
   bool i64 = cls[tik] == EMU_CLASS_FP64, j64 = cls[tjk] == EMU_CLASS_FP64;
-  size_t oi = (size_t)tik * nb * nb + bi * GM, oj = (size_t)tjk * nb * nb + bj * GM;
-  double *C = t64 + (size_t)tile_index(i, j, NT) * nb * nb + bi * GM + (size_t)bj * GM * nb;
-  __shared__ double as[GK][GM];
-  __shared__ double bs[GK][GM];
+  size_t oi = (size_t)tik * nb * nb + bi * BMT, oj = (size_t)tjk * nb * nb + bj * BMT;
+  double *C = t64 + (size_t)tile_index(i, j, NT) * nb * nb + bi * BMT + (size_t)bj * BMT * nb;
+  __shared__ double as[GK][BMT];
+  __shared__ double bs[GK][BMT];
   int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  int lc = t / 16, lr = (t % 16) * 4;
-  double acc[4][4] = {};
+  // loader: GK x BMT elements per operand, R per thread, consecutive rows
+  int lc = t / (BMT / R), lr = (t % (BMT / R)) * R;
+  double acc[R][R] = {};
   for (int p0 = 0; p0 < nb; p0 += GK) {
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
+    for (int e = 0; e < R; e++) {
       size_t o = (lr + e) + (size_t)(p0 + lc) * nb;
-      as[lc][lr + e] = i64 ? t64[oi + o] : (double)t32[oi + o];
-      bs[lc][lr + e] = j64 ? t64[oj + o] : (double)t32[oj + o];
+      if (lc < GK) {
+        as[lc][lr + e] = i64 ? t64[oi + o] : (double)t32[oi + o];
+        bs[lc][lr + e] = j64 ? t64[oj + o] : (double)t32[oj + o];
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < GK; p++) {
-      double av[4], bv[4];
+      double av[R], bv[R];
 #pragma unroll
-      for (int e = 0; e < 4; e++) {
+      for (int e = 0; e < R; e++) {
         av[e] = as[p][ty + 16 * e];
         bv[e] = bs[p][tx + 16 * e];
       }
 #pragma unroll
-      for (int x = 0; x < 4; x++)
+      for (int x = 0; x < R; x++)
 #pragma unroll
-        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
+        for (int y = 0; y < R; y++) acc[x][y] += av[x] * bv[y];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; x++)
+  for (int x = 0; x < R; x++)
 #pragma unroll
-    for (int y = 0; y < 4; y++) C[(ty + 16 * x) + (size_t)(tx + 16 * y) * nb] -= acc[x][y];
+    for (int y = 0; y < R; y++) C[(ty + 16 * x) + (size_t)(tx + 16 * y) * nb] -= acc[x][y];
 }
 
 // z pieces for the sampler: zp[q][n][k] = piece q of Z[k][n], n < s_pad
@@ -439,6 +448,7 @@ struct MixedPlan {
   int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
   int *d_qtiles = nullptr;            // panel tiles quantized to E4M3, per step (see StepPlan)
   bool any_e4m3 = false;
+  bool crit64 = false;  // FP64-class TRSM or SYRK on the critical path (see kReservedSMs)
   gemm_tc::Operands ops;
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
@@ -571,6 +581,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         qtiles.push_back((int)tile_index(i, k, NT));
         sp.nq_r++;
       }
+    if (sp.n64_1 > 0 || sp.p_n[GR_S] > 0) P->crit64 = true;
     P->steps.push_back(sp);
   }
   // one allocation and one copy for all lists (256-byte aligned parts)
@@ -633,8 +644,14 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   return EMU_OK;
 }
 
-// SMs the bulk trailing update leaves to the critical-path kernels.
+// SMs the bulk trailing update leaves to the critical-path kernels.  The
+// persistent bulk GEMM holds about 217 KB of shared memory per SM, so the
+// FP64 panel TRSM and FP64 SYRK of the critical path (more shared memory than
+// is left beside it) run only on these.  When the plan puts FP64-class work on
+// the critical path the critical stream bounds the factor and gets more SMs;
+// otherwise the bulk update is the bound and keeps them.
 constexpr int kReservedSMs = 16;
+constexpr int kReservedSMsCrit64 = 32;
 
 // Internal streams of the mixed schedule (created once per context) and at
 // least `nev` ordering events.
@@ -749,8 +766,12 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     const StepPlan &sp = P->steps[k];
     if (sp.p_n[g] > 0) {
       ProfScope ps(ctx, PROF_UPDATE64, 2.0 * sp.p_n[g] * nb3, 24.0 * sp.p_n[g] * te);
-      k_update64_list<<<dim3(sp.p_n[g], (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
-          A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
+      if ((long)sp.p_n[g] * (nb / GM) * (nb / GM) >= 2L * ctx->sm_count)
+        k_update64_list<GM><<<dim3(sp.p_n[g], (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
+            A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
+      else
+        k_update64_list<32><<<dim3(sp.p_n[g], (nb / 32) * (nb / 32)), 256, 0, ctx->stream>>>(
+            A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
       EMU_LAUNCHED(ctx);
     }
     if (sp.i_n[g] > 0) {
@@ -800,7 +821,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     // free for the critical and panel streams' kernels
     ctx->stream = ctx->bulk;
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev(k, E_T), 0));
-    int bulk_ctas = std::max(1, ctx->sm_count - kReservedSMs);
+    int bulk_ctas = std::max(1, ctx->sm_count - (P->crit64 ? kReservedSMsCrit64 : kReservedSMs));
     if ((s = update_group(k, GR_G2A, bulk_ctas)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G2), ctx->bulk));
     if ((s = update_group(k, GR_G2, bulk_ctas)) != EMU_OK) break;
