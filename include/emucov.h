@@ -243,6 +243,40 @@ emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu_mat *S,
                             int nrhs, double tol, int maxit,
                             emu_refine_info *info);
 
+/* ------------------------------------------------------------------ batches */
+/* Many independent covariances of uneven bandlimit (the batched workload:
+ * n = L_b^2 from 64 to 4096), each built, factored by the adaptive per-tile
+ * precision Cholesky and sampled, in one call.  Every step k of the tile
+ * algorithm ("Advancements in Dense Linear Algebra") runs once for all
+ * matrices that still have a step k, and the launches after the precision map
+ * are captured in one CUDA graph that the context keeps and replays when the
+ * same batch (parameters, nb, options, nsamples, dL given or not) comes
+ * again.  The paper factors one matrix at a time; batching is this library's.
+ *   count     number of matrices (>= 1)
+ *   p         count parameter sets; 1 <= p[b].L <= 256
+ *   nb        tile size: a multiple of 256 in [256, 1024], or 0 to let the
+ *             library time 512 and 256 on the first call of this batch and
+ *             keep the faster (later calls reuse the choice)
+ *   o         factor options for every matrix (NULL or eps <= 0: plain FP64)
+ *   nsamples  samples per matrix (0: factor only)
+ *   seed      Philox key; matrix b draws its normals with stream id b, the
+ *             draws emu_sample(L_b, nsamples, seed, b, ...) makes
+ *   dY        count device pointers: Y_b = L_b Z_b, n_b x nsamples,
+ *             column-major, leading dimension n_b (may be NULL if nsamples == 0)
+ *   dL        NULL, or count device pointers: the factor L_b, n_b x n_b,
+ *             column-major, leading dimension n_b, zeros above the diagonal
+ *   infos     NULL, or count records; ms is the device time of the graph
+ * Returns EMU_EINVAL for bad arguments, EMU_ENOMEM when the batch arenas do
+ * not fit, EMU_ENOTPD (infos[b].pivot set for one failing matrix),
+ * EMU_ETIMEOUT, EMU_ECUDA.  The arenas (about 18 bytes per element of every
+ * padded lower tile) stay allocated in the context until emu_batch_release or
+ * emu_destroy. */
+emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params *p, int nb,
+                                  const emu_mp_opts *o, int nsamples, uint64_t seed,
+                                  double *const *dY, double *const *dL, emu_factor_info *infos);
+/* Frees the context's batch arenas, plan and graph. */
+emu_status emu_batch_release(emu_ctx *ctx);
+
 /* ------------------------------------------------------- no-allocation build */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory while they call the library: code inside

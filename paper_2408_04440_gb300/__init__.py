@@ -34,7 +34,7 @@ EXPORTED = (
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
-    "emu_cov_build_dense_noalloc",
+    "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
 PROF_GROUPS = ("cov", "map", "potrf", "trsm64", "trsm32", "update64", "tc_factor", "tc_sample", "trmm64",
                "rng", "split", "solve")
@@ -111,12 +111,15 @@ def load() -> ctypes.CDLL:
     L.emu_potrs.argtypes = [vp, vp, vp, lg, vp, lg, i]
     L.emu_solve_refine.argtypes = [vp, vp, vp, vp, lg, vp, lg, i, d, i, ctypes.POINTER(emu_refine_info)]
     L.emu_cov_build_dense_noalloc.argtypes = [i, d, d, d, vp, lg, vp]
+    L.emu_batch_potrf_sample.argtypes = [vp, i, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(emu_mp_opts), i,
+                                         ctypes.c_uint64, vp, vp, ctypes.POINTER(emu_factor_info)]
+    L.emu_batch_release.argtypes = [vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
                  "emu_trace_enable", "emu_trace_read", "emu_prof_timeline",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
                  "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
-                 "emu_cov_build_dense_noalloc"):
+                 "emu_cov_build_dense_noalloc", "emu_batch_potrf_sample", "emu_batch_release"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -399,3 +402,35 @@ def emu_solve_refine(ctx: Context, L: Mat, S: Mat, B, tol: float = 1e-14, maxit:
     if raise_on_error and s != EMU_OK:
         ctx._check(s, "emu_solve_refine")
     return out, ri
+
+
+def emu_batch_potrf_sample(ctx: Context, params, nb: int = 256, eps: float = 0.0, prec_mask: int = 0b01011,
+                           diag_fp64: bool = False, u=None, nsamples: int = 0, seed: int = 0, want_L: bool = False,
+                           raise_on_error: bool = True):
+    """params: sequence of (L, beta) or (L, beta, sigma_exp, nugget_rel).
+    Returns (Ys, Ls, infos, status): lists of column-major CUDA tensors
+    (n_b x nsamples and n_b x n_b; None where not asked) and FactorInfo."""
+    count = len(params)
+    P = (emu_cov_params * count)()
+    for b, q in enumerate(params):
+        sexp = float(q[2]) if len(q) > 2 else 1.5
+        nug = float(q[3]) if len(q) > 3 else 1e-8
+        P[b] = emu_cov_params(int(q[0]), float(q[1]), sexp, nug)
+    Ys = [_colmajor_empty(int(q[0]) ** 2, nsamples, ctx.device) for q in params] if nsamples > 0 else None
+    Ls = [_colmajor_empty(int(q[0]) ** 2, int(q[0]) ** 2, ctx.device) for q in params] if want_L else None
+    yp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ys]) if Ys else None
+    lp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ls]) if Ls else None
+    o = mp_opts(eps, prec_mask, diag_fp64, u)
+    infos = (emu_factor_info * count)()
+    s = ctx.lib.emu_batch_potrf_sample(ctx.h, count, P, nb, ctypes.byref(o), nsamples, seed,
+                                       ctypes.cast(yp, ctypes.c_void_p) if yp else None,
+                                       ctypes.cast(lp, ctypes.c_void_p) if lp else None, infos)
+    fis = [FactorInfo(s, f.n, f.nb, f.nt, f.pivot, list(f.tiles), list(f.update_flops), f.frob, f.ms)
+           for f in infos]
+    if raise_on_error and s != EMU_OK:
+        ctx._check(s, "emu_batch_potrf_sample")
+    return Ys, Ls, fis, s
+
+
+def emu_batch_release(ctx: Context):
+    ctx._check(ctx.lib.emu_batch_release(ctx.h), "emu_batch_release")

@@ -145,6 +145,7 @@ emu_status emu_destroy(emu_ctx *ctx) {
   cudaFree(ctx->dag_ws);
   cudaFree(ctx->trace_buf);
   mixed_ctx_release(ctx);
+  batch_ctx_release(ctx);
   delete ctx;
   return EMU_OK;
 }

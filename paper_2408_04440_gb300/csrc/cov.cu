@@ -7,6 +7,8 @@
 // depends only on (l_i - l_j, m_i - m_j), so it is evaluated once per offset
 // into a table; every entry is then s(l_i) * s(l_j) * rho(dl, dm) -- the same
 // operations, in the same order, as evaluating the formula entry by entry.
+#include <algorithm>
+
 #include "emu_internal.h"
 
 namespace {
@@ -25,22 +27,20 @@ __device__ inline int degree_of(long k) {
 
 // sigma[l] = (1 + l)^(-sexp); rho[(dl + L - 1) * W + (dm + 2L - 2)] =
 // exp(-sqrt(dl^2 + dm^2) / beta), W = 4L - 3; out[0] = nugget added to
-// the diagonal = nugget_rel * max_l sigma[l]^2.
-__global__ void k_cov_tables(int L, double beta, double sexp, double nugget_rel,
-                             double *sigma, double *rho, double *nugget) {
+// the diagonal = nugget_rel * max_l sigma[l]^2.  Thread `tid` of `nthr`
+// strides over the entries; `leader` computes the nugget.
+__device__ inline void cov_tables_part(int L, double beta, double sexp, double nugget_rel, double *sigma,
+                                       double *rho, double *nugget, long tid, long nthr, bool leader) {
   int W = 4 * L - 3;
   long total = (long)(2 * L - 1) * W;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
+  for (long t = tid; t < total; t += nthr) {
     int a = (int)(t / W), b = (int)(t % W);
     double dl = (double)(a - (L - 1)), dm = (double)(b - (2 * L - 2));
     double d = sqrt(dl * dl + dm * dm);
     rho[t] = exp(-d / beta);
   }
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L;
-       l += gridDim.x * blockDim.x)
-    sigma[l] = pow(1.0 + l, -sexp);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  for (long l = tid; l < L; l += nthr) sigma[l] = pow(1.0 + l, -sexp);
+  if (leader) {
     double dmax = 0.0;
     for (int l = 0; l < L; l++) {
       double s = pow(1.0 + l, -sexp);
@@ -49,6 +49,23 @@ __global__ void k_cov_tables(int L, double beta, double sexp, double nugget_rel,
     }
     *nugget = nugget_rel * dmax;
   }
+}
+
+__global__ void k_cov_tables(int L, double beta, double sexp, double nugget_rel,
+                             double *sigma, double *rho, double *nugget) {
+  cov_tables_part(L, beta, sexp, nugget_rel, sigma, rho, nugget, blockIdx.x * (long)blockDim.x + threadIdx.x,
+                  (long)gridDim.x * blockDim.x, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Batch: blockIdx.y = matrix; its tables at tab_base (rho, then sigma, then
+// the nugget).
+__global__ void k_cov_tables_batch(const BatchInst *__restrict__ inst, double *tables) {
+  BatchInst I = inst[blockIdx.y];
+  double *rho = tables + I.tab_base;
+  double *sigma = rho + (long)(2 * I.L - 1) * (4 * I.L - 3);
+  cov_tables_part(I.L, I.beta, I.sigma_exp, I.nugget_rel, sigma, rho, sigma + I.L,
+                  blockIdx.x * (long)blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x,
+                  blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 // Deterministic block reduction of one double per thread (fixed tree).
@@ -68,20 +85,15 @@ __device__ inline double block_sum(double v, double *sh) {
 // One CTA per (tile, 32-column chunk): blockIdx.x = tile, blockIdx.y = chunk.  Writes the tile's chunk (padded
 // entries: unit diagonal, zeros elsewhere) and the chunk's sum of squares
 // over the real (unpadded) entries of the full symmetric tile.
-__global__ void __launch_bounds__(kThreads)
-    k_cov_build(int L, int n, int nb, int NT, const double *__restrict__ sigma,
-                const double *__restrict__ rho, const double *__restrict__ nugget,
-                double *__restrict__ t64, double *__restrict__ partial) {
-  __shared__ double sh[kThreads / 32];
-  long t = blockIdx.x;
-  int ti, tj;
-  tile_coords(t, NT, &ti, &tj);
+// Chunk `chunk` (kChunk columns) of tile (ti, tj) of the covariance of
+// bandlimit L; returns this thread's sum of squares of the real entries.
+__device__ inline double cov_tile_chunk(int L, int n, int nb, int ti, int tj, int chunk,
+                                        const double *__restrict__ sigma, const double *__restrict__ rho,
+                                        double nug, double *__restrict__ tile) {
   int W = 4 * L - 3;
-  double nug = *nugget;
-  double *tile = t64 + (size_t)t * nb * nb;
   double ss = 0.0;
   for (int cc = 0; cc < kChunk; cc++) {
-    int c = blockIdx.y * kChunk + cc;
+    int c = chunk * kChunk + cc;
     long gj = (long)tj * nb + c;
     int lj = 0, mj = 0;
     if (gj < n) {
@@ -104,8 +116,36 @@ __global__ void __launch_bounds__(kThreads)
       tile[r + (size_t)c * nb] = v;
     }
   }
+  return ss;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_cov_build(int L, int n, int nb, int NT, const double *__restrict__ sigma,
+                const double *__restrict__ rho, const double *__restrict__ nugget,
+                double *__restrict__ t64, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  double ss = cov_tile_chunk(L, n, nb, ti, tj, blockIdx.y, sigma, rho, *nugget, t64 + (size_t)t * nb * nb);
   double tot = block_sum(ss, sh);
   if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
+// Batch: blockIdx.x = tile of the batch arena, tile_inst = its matrix.
+__global__ void __launch_bounds__(kThreads)
+    k_cov_build_batch(const BatchInst *__restrict__ inst, const int *__restrict__ tile_inst, int nb,
+                      const double *__restrict__ tables, double *__restrict__ t64, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long g = blockIdx.x;
+  BatchInst I = inst[tile_inst[g]];
+  int ti, tj;
+  tile_coords(g - I.tile_base, I.NT, &ti, &tj);
+  const double *rho = tables + I.tab_base;
+  const double *sigma = rho + (long)(2 * I.L - 1) * (4 * I.L - 3);
+  double ss = cov_tile_chunk(I.L, I.n, nb, ti, tj, blockIdx.y, sigma, rho, sigma[I.L], t64 + (size_t)g * nb * nb);
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[g * gridDim.y + blockIdx.y] = tot;
 }
 
 // Same layout from a dense, column-major, lower-triangle user matrix.
@@ -174,8 +214,18 @@ __global__ void __launch_bounds__(1024)
                     const double *__restrict__ partial, double *__restrict__ tnorm,
                     double *__restrict__ frob, unsigned char *__restrict__ cls,
                     double eps, double u1, double u2, double u3, double u4,
-                    unsigned mask, int diag_fp64) {
+                    unsigned mask, int diag_fp64, const BatchInst *__restrict__ inst) {
   __shared__ double sh[32];
+  if (inst) {
+    // batch: one CTA per matrix, its tiles at tile_base
+    BatchInst I = inst[blockIdx.x];
+    NT = I.NT;
+    ntiles = (long)NT * (NT + 1) / 2;
+    partial += I.tile_base * nchunk;
+    tnorm += I.tile_base;
+    frob += blockIdx.x;
+    if (cls) cls += I.tile_base;
+  }
   double acc = 0.0;
   for (long t = threadIdx.x; t < ntiles; t += blockDim.x) {
     double s = 0.0;
@@ -213,15 +263,13 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Dense FP64 lower triangle from the tiles.  grid.x enumerates all NT*NT tile
-// pairs; upper tiles and the strict upper part of diagonal tiles become 0.
+// Dense FP64 lower triangle from the tiles, chunk `chunk` of the tile pair
+// (ti, tj): upper tiles and the strict upper part of diagonal tiles become 0.
 // Low-precision off-diagonal tiles of a mixed factor come from the FP32
-// master arena.
-__global__ void __launch_bounds__(kThreads)
-    k_export(int n, int nb, int NT, const double *__restrict__ t64,
-             const float *__restrict__ t32, const unsigned char *__restrict__ cls,
-             double *__restrict__ out, long ld) {
-  int ti = blockIdx.x % NT, tj = blockIdx.x / NT;
+// master arena (t32 and cls given).
+__device__ inline void export_chunk(int n, int nb, int NT, int ti, int tj, int chunk, const double *__restrict__ t64,
+                                    const float *__restrict__ t32, const unsigned char *__restrict__ cls,
+                                    double *__restrict__ out, long ld) {
   const double *tile = nullptr;
   const float *tile32 = nullptr;
   if (ti >= tj) {
@@ -232,7 +280,7 @@ __global__ void __launch_bounds__(kThreads)
       tile = t64 + (size_t)t * nb * nb;
   }
   for (int cc = 0; cc < kChunk; cc++) {
-    int c = blockIdx.y * kChunk + cc;
+    int c = chunk * kChunk + cc;
     long gj = (long)tj * nb + c;
     if (gj >= n) break;
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {
@@ -246,6 +294,27 @@ __global__ void __launch_bounds__(kThreads)
       out[gi + gj * ld] = v;
     }
   }
+}
+
+// grid.x enumerates all NT*NT tile pairs.
+__global__ void __launch_bounds__(kThreads)
+    k_export(int n, int nb, int NT, const double *__restrict__ t64,
+             const float *__restrict__ t32, const unsigned char *__restrict__ cls,
+             double *__restrict__ out, long ld) {
+  export_chunk(n, nb, NT, blockIdx.x % NT, blockIdx.x / NT, blockIdx.y, t64, t32, cls, out, ld);
+}
+
+// Batch: pairs[blockIdx.x] = {matrix, ti, tj}; matrix b goes to out[b]
+// (n_b x n_b, leading dimension n_b).
+__global__ void __launch_bounds__(kThreads)
+    k_export_batch(const BatchInst *__restrict__ inst, const int4 *__restrict__ pairs, int nb,
+                   const double *__restrict__ t64, const float *__restrict__ t32,
+                   const unsigned char *__restrict__ cls, double *const *__restrict__ out) {
+  int4 pr = pairs[blockIdx.x];
+  BatchInst I = inst[pr.x];
+  export_chunk(I.n, nb, I.NT, pr.y, pr.z, blockIdx.y, t64 + (size_t)I.tile_base * nb * nb,
+               t32 ? t32 + (size_t)I.tile_base * nb * nb : nullptr, cls ? cls + I.tile_base : nullptr, out[pr.x],
+               I.n);
 }
 
 }  // namespace
@@ -292,7 +361,33 @@ emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
   k_precision_map<<<1, 1024, 0, ctx->stream>>>(
       A->nt, A->ntiles, A->nchunk, A->d_partial, A->d_tnorm, A->d_frob,
       u ? A->d_cls : nullptr, eps, u ? u[1] : 0.0, u ? u[2] : 0.0,
-      u ? u[3] : 0.0, u ? u[4] : 0.0, mask, diag_fp64);
+      u ? u[3] : 0.0, u ? u[4] : 0.0, mask, diag_fp64, nullptr);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_cov_build_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int maxL, long ntab,
+                                  const int *d_tile_inst, long ntiles, int nb, double *tables, double *t64,
+                                  double *partial) {
+  long per = (long)(2 * maxL - 1) * (4 * maxL - 3);
+  int bx = (int)std::min<long>((per + 255) / 256, 64);
+  k_cov_tables_batch<<<dim3(bx, count), 256, 0, ctx->stream>>>(d_inst, tables);
+  EMU_LAUNCHED(ctx);
+  (void)ntab;
+  ProfScope ps(ctx, PROF_COV, 3.0 * ntiles * nb * nb, 8.0 * ntiles * nb * nb);
+  k_cov_build_batch<<<dim3((unsigned)ntiles, nb / kChunk), kThreads, 0, ctx->stream>>>(d_inst, d_tile_inst, nb,
+                                                                                       tables, t64, partial);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_precision_map_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int nb, double *partial,
+                                      double *tnorm, double *frob, unsigned char *cls, double eps,
+                                      const double *u, unsigned mask, int diag_fp64) {
+  ProfScope ps(ctx, PROF_MAP, 0.0, 0.0);
+  k_precision_map<<<count, 1024, 0, ctx->stream>>>(0, 0, nb / kChunk, partial, tnorm, frob, cls, eps,
+                                                   u ? u[1] : 0.0, u ? u[2] : 0.0, u ? u[3] : 0.0,
+                                                   u ? u[4] : 0.0, mask, diag_fp64, d_inst);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -303,6 +398,16 @@ emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld) 
   k_export<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, A->t64,
                                               mixed ? A->t32 : nullptr,
                                               mixed ? A->d_cls : nullptr, dOut, ld);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_export_batch(emu_ctx *ctx, const BatchInst *d_inst, const int4 *d_pairs, long npairs, int nb,
+                               const double *t64, const float *t32, const unsigned char *cls,
+                               double *const *d_out) {
+  if (npairs <= 0) return EMU_OK;
+  k_export_batch<<<dim3((unsigned)npairs, nb / kChunk), kThreads, 0, ctx->stream>>>(d_inst, d_pairs, nb, t64, t32,
+                                                                                    cls, d_out);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

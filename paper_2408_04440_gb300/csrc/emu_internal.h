@@ -83,6 +83,8 @@ struct emu_ctx {
   int *dag_ws = nullptr;
   size_t dag_ws_bytes = 0;
   int dag_ntasks = 0, dag_nbb = 0;
+  // batched factor (batch.cu): arenas, plan and captured graph of the last batch
+  void *batch = nullptr;
   // optional device-side task trace of the dataflow POTRF
   bool trace_on = false;
   unsigned long long *trace_buf = nullptr;
@@ -139,6 +141,23 @@ emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what);
     if (_e != cudaSuccess) return emu_cuda_fail((ctx), _e, "kernel launch"); \
   } while (0)
 
+// ------------------------------------------------------------- batches
+// One covariance of a batch (batch.cu): its tiles, rows and covariance tables
+// sit at these offsets of the batch's shared arenas.
+struct BatchInst {
+  long tile_base;  // first tile (packed lower tiles, column by column)
+  long row_base;   // first row of its padded block of the stacked Z and Y
+  long tab_base;   // first entry of its correlation table (sigma and nugget follow)
+  int L, n, NT, stream_id;
+  double beta, sigma_exp, nugget_rel;
+};
+
+// Block row i of one matrix of a batch for the FP64 TRMM (fp64.cu).
+struct TrmmJob {
+  long tile_base, row_base;
+  int NT, n, i, pad;
+};
+
 // Kernel launch wrappers (defined in the .cu files that own the kernels).
 // cov.cu
 emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
@@ -163,3 +182,38 @@ emu_status launch_potrs64(emu_ctx *ctx, const emu_mat *L, double *X, long ldx,
 // rng.cu
 emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id,
                           int nrows, int s, double *Z, long ldz);
+// batched kernels over explicit tile indices (batch.cu drives them)
+emu_status launch_cov_build_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int maxL, long ntab,
+                                  const int *d_tile_inst, long ntiles, int nb, double *tables, double *t64,
+                                  double *partial);
+emu_status launch_precision_map_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int nb, double *partial,
+                                      double *tnorm, double *frob, unsigned char *cls, double eps,
+                                      const double *u, unsigned mask, int diag_fp64);
+emu_status launch_export_batch(emu_ctx *ctx, const BatchInst *d_inst, const int4 *d_pairs, long npairs, int nb,
+                               const double *t64, const float *t32, const unsigned char *cls,
+                               double *const *d_out);
+emu_status launch_normals_batch(emu_ctx *ctx, const uint64_t *d_seed, const BatchInst *d_inst, int count,
+                                int maxNT, int nb, int s, double *Z, long ldz);
+emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs);
+emu_status launch_trmm64_jobs(emu_ctx *ctx, const double *t64, int nb, const unsigned char *cls,
+                              const TrmmJob *d_jobs, int njobs, const double *Z, long ldz, int s, double *Y,
+                              long ldy, double flops);
+emu_status launch_to_f32_tiles(emu_ctx *ctx, const double *t64, float *t32, const unsigned char *cls, long ntiles,
+                               size_t te);
+emu_status launch_tiles_to_f64(emu_ctx *ctx, const float *t32, double *t64, const long *d_tiles, int n, size_t te);
+emu_status launch_diag_to_f32_slots(emu_ctx *ctx, const double *t64, float *slots, const long *d_tiles, int n,
+                                    size_t te);
+emu_status launch_trsm32_jobs(emu_ctx *ctx, const float *slots, float *t32, uint16_t *op, int nb, const int2 *d_jobs,
+                              int njobs);
+emu_status launch_split_tiles64(emu_ctx *ctx, const double *t64, uint16_t *op, const int *d_tiles, int n, int nb,
+                                int lower_only);
+emu_status launch_quant_e4m3(emu_ctx *ctx, const uint16_t *op, uint8_t *op8, float *scales, const int *d_tiles, int n,
+                             int nb);
+emu_status launch_update64_jobs(emu_ctx *ctx, double *t64, const float *t32, const unsigned char *cls, int nb,
+                                const int4 *d_jobs, int njobs);
+emu_status launch_split_z(emu_ctx *ctx, const double *Z, long ldz, long npad, int s, int s_pad, uint16_t *zp);
+size_t potrf_dag_task_count(int nb);
+emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStream_t s);
+size_t potrf_batch_ws_ints(int nb, int nbat);
+emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const long *d_tiles, int nbat,
+                                const void *d_tasks, int ntasks, int *ws, double *rinv);

@@ -77,27 +77,34 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
 }
 
 __global__ void __launch_bounds__(PB * PB)
-    k_potrf_dag(double *__restrict__ D, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
-                int *__restrict__ ws, int *st, unsigned long long *__restrict__ trace) {
+    k_potrf_dag(double *__restrict__ D0, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
+                int *__restrict__ ws, double *__restrict__ rinv_all, int *st,
+                unsigned long long *__restrict__ trace, const long *__restrict__ dtiles, int nbat) {
   __shared__ double a[PB][PB + 1];   // L of the block solved against, then the block factored
   __shared__ double m[PB][PB + 1];   // L scaled by the pivot reciprocals (solves)
   __shared__ double xr[PB][PB + 1];  // panel rows of block r
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
   __shared__ int s_task, s_ok, bad;
+  // ws = {task counter, then state[nbb*nbb] per tile}; rinv_all = nb pivot
+  // reciprocals per tile.  A batch of nbat tiles (dtiles = their indices in
+  // D0) interleaves the tiles' task lists: task t is task t / nbat of tile
+  // t % nbat, so each tile's tasks stay in topological order.
   int *counter = ws;
-  int *state = ws + 1;
   const int nbb = nb / PB;
-  double *rinv_g = reinterpret_cast<double *>(ws + 2 + nbb * nbb + ((nbb * nbb) & 1));
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
-  auto blk = [&](int br, int bc) { return D + (size_t)(br * PB + ty) + (size_t)(bc * PB + tx) * ld; };
   while (true) {
     if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
     int t = s_task;
-    if (t >= ntasks) return;
-    short4 tk = tasks[t];
+    if (t >= ntasks * nbat) return;
+    const int bt = t % nbat;
+    double *D = dtiles ? D0 + (size_t)dtiles[bt] * nb * nb : D0;
+    int *state = ws + 1 + (size_t)bt * nbb * nbb;
+    double *rinv_g = rinv_all + (size_t)bt * nb;
+    auto blk = [&](int br, int bc) { return D + (size_t)(br * PB + ty) + (size_t)(bc * PB + tx) * ld; };
+    short4 tk = tasks[t / nbat];
     int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LT: (s, s-1, s); TRSM: (r, s, s); UPD: (r, c, s)
     unsigned long long t_fetch = 0;
     if (trace && threadIdx.x == 0) t_fetch = gtimer();
@@ -216,6 +223,7 @@ __global__ void __launch_bounds__(PB * PB)
         if (bad) {
           if (threadIdx.x == 0) {
             st[ST_PIVOT] = gcol0 + s * PB + bad;
+            if (dtiles) st[ST_AUX] = bt;  // which tile of the batch
             __threadfence();
             atomicExch(&st[ST_CODE], DEV_NOTPD);
           }
@@ -267,17 +275,27 @@ constexpr int T64_ROWS = 4;
 constexpr int T64_STRIP = 128;
 __global__ void __launch_bounds__(128)
     k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
-                   const int *st) {
+                   const int *st, const int2 *__restrict__ jobs = nullptr) {
   if (failed(st)) return;
   extern __shared__ double sm64[];
   const int ldx = nb + 1;
   const int lds = T64_STRIP + 1;
   double *X = sm64;                  // [4][ldx]
   double *S = X + T64_ROWS * ldx;    // [32][lds]
-  int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
   int r0 = blockIdx.x * T64_ROWS;
-  const double *Lkk = t64 + (size_t)tile_index(k, k, NT) * nb * nb;
-  double *A = t64 + (size_t)tile_index(i, k, NT) * nb * nb + r0;
+  // tiles (i, k) and (k, k) of one matrix, or (batched) explicit tile indices
+  long tik, tkk;
+  if (jobs) {
+    int2 jb = jobs[blockIdx.y];
+    tik = jb.x;
+    tkk = jb.y;
+  } else {
+    int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
+    tik = tile_index(i, k, NT);
+    tkk = tile_index(k, k, NT);
+  }
+  const double *Lkk = t64 + (size_t)tkk * nb * nb;
+  double *A = t64 + (size_t)tik * nb * nb + r0;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll 8
   for (int e = tid; e < T64_ROWS * nb; e += 128) {
@@ -419,10 +437,22 @@ __global__ void k_tril_diag(double *__restrict__ t64, int nb, int NT) {
 __global__ void __launch_bounds__(256)
     k_trmm64(const double *__restrict__ t64, int n, int nb, int NT,
              const double *__restrict__ Z, long ldz, int s, double *__restrict__ Y,
-             long ldy, const unsigned char *__restrict__ cls) {
+             long ldy, const unsigned char *__restrict__ cls, const TrmmJob *__restrict__ jobs) {
   int nsub = nb / GM;
   int i = blockIdx.x / nsub, bi = blockIdx.x % nsub;
   int c0 = blockIdx.y * GM;
+  if (jobs) {
+    // batched: block row i of one matrix of the batch, whose tiles start at
+    // tile_base and whose rows start at row_base of Z and Y
+    TrmmJob jb = jobs[blockIdx.x / nsub];
+    i = jb.i;
+    NT = jb.NT;
+    n = jb.n;
+    t64 += (size_t)jb.tile_base * nb * nb;
+    cls += jb.tile_base;
+    Z += jb.row_base;
+    Y += jb.row_base;
+  }
   __shared__ double as[GK][GM];
   __shared__ double bs[GK][GM];
   int t = threadIdx.x, tx = t % 16, ty = t / 16;
@@ -536,6 +566,13 @@ __global__ void k_solve_diag(const double *__restrict__ t64, int nb, int NT, int
 
 }  // namespace
 
+// Ints of the dataflow POTRF workspace for nbat tiles: the task counter and
+// each tile's block states, rounded up to a whole number of doubles.
+static size_t dag_ws_ints(int nbb, int nbat) {
+  size_t n = 1 + (size_t)nbat * nbb * nbb;
+  return (n + 1) & ~(size_t)1;
+}
+
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   int nb = A->nb, NT = A->nt;
   int nbb = nb / PB;
@@ -551,7 +588,7 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
     EMU_CUDA_TRY(ctx, cudaMemcpy(ctx->dag_tasks, tasks.data(), tasks.size() * sizeof(short4),
                                  cudaMemcpyHostToDevice));
     // counter, state[nbb*nbb], alignment pad, rinv[nb] doubles
-    ctx->dag_ws_bytes = (size_t)(2 + nbb * nbb + 1) * sizeof(int) + (size_t)nb * sizeof(double);
+    ctx->dag_ws_bytes = dag_ws_ints(nbb, 1) * sizeof(int) + (size_t)nb * sizeof(double);
     EMU_CUDA_TRY(ctx, cudaMalloc(&ctx->dag_ws, ctx->dag_ws_bytes));
     ctx->dag_ntasks = (int)tasks.size();
     ctx->dag_nbb = nbb;
@@ -581,8 +618,63 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
     trace = ctx->trace_buf + (size_t)k * ctx->dag_ntasks * 5;
     ctx->trace_records = (size_t)(k + 1) * ctx->dag_ntasks;
   }
+  double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
   k_potrf_dag<<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks, ctx->dag_ntasks,
-                                                ctx->dag_ws, ctx->d_status, trace);
+                                                ctx->dag_ws, rinv, ctx->d_status, trace, nullptr, 1);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs) {
+  if (njobs <= 0) return EMU_OK;
+  double nb3 = (double)nb * nb * nb;
+  ProfScope ps(ctx, PROF_TRSM64, njobs * nb3, 16.0 * njobs * nb * nb);
+  size_t sm = (size_t)(T64_ROWS * (nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_trsm64_panel<<<dim3(nb / T64_ROWS, njobs), 128, sm, ctx->stream>>>(t64, nb, 0, 0, nullptr, ctx->d_status,
+                                                                      d_jobs);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_trmm64_jobs(emu_ctx *ctx, const double *t64, int nb, const unsigned char *cls,
+                              const TrmmJob *d_jobs, int njobs, const double *Z, long ldz, int s, double *Y,
+                              long ldy, double flops) {
+  if (njobs <= 0 || s <= 0) return EMU_OK;
+  dim3 grid(njobs * (nb / GM), (s + GM - 1) / GM);
+  ProfScope ps(ctx, PROF_TRMM64, flops, 0.0);
+  k_trmm64<<<grid, 256, 0, ctx->stream>>>(t64, 0, nb, 0, Z, ldz, s, Y, ldy, cls, d_jobs);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+size_t potrf_dag_task_count(int nb) {
+  std::vector<short4> tasks;
+  dag_tasks(nb / PB, tasks);
+  return tasks.size();
+}
+
+emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStream_t s) {
+  std::vector<short4> tasks;
+  dag_tasks(nb / PB, tasks);
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(short4), cudaMemcpyHostToDevice, s));
+  // the host vector goes out of scope: wait for the copy
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return EMU_OK;
+}
+
+size_t potrf_batch_ws_ints(int nb, int nbat) { return dag_ws_ints(nb / PB, nbat); }
+
+emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const long *d_tiles, int nbat,
+                                const void *d_tasks, int ntasks, int *ws, double *rinv) {
+  if (nbat <= 0) return EMU_OK;
+  int nbb = nb / PB;
+  ProfScope ps(ctx, PROF_POTRF, (double)nbat * nb * nb * nb / 3.0, 16.0 * nbat * nb * nb);
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ws, 0, dag_ws_ints(nbb, nbat) * sizeof(int), ctx->stream));
+  long total = (long)ntasks * nbat;
+  int grid = (int)std::min<long>(total, 4L * ctx->sm_count);
+  k_potrf_dag<<<grid, PB * PB, 0, ctx->stream>>>(t64, nb, k * nb, (const short4 *)d_tasks, ntasks, ws, rinv,
+                                                ctx->d_status, nullptr, d_tiles, nbat);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -623,7 +715,7 @@ emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z, long l
                          int s, double *Y, long ldy, const unsigned char *cls) {
   dim3 grid(L->nt * (L->nb / GM), (s + GM - 1) / GM);
   ProfScope ps(ctx, PROF_TRMM64, (double)L->n * L->n * s, 8.0 * tile_count(L->nt) * L->nb * L->nb);
-  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls);
+  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls, nullptr);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

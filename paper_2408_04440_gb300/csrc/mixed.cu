@@ -165,8 +165,9 @@ constexpr int TS_STRIP = 128;  // columns of L_kk staged at once
 // CTAs in parallel mean less latency.
 template <int NW, int RPW>
 __global__ void __launch_bounds__(NW * 32)
-    k_trsm32_panel(const float *__restrict__ Lkk, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
-                   int NT, int k, const int *__restrict__ rows, const int *st) {
+    k_trsm32_panel(const float *__restrict__ Lkk0, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
+                   int NT, int k, const int *__restrict__ rows, const int *st,
+                   const int2 *__restrict__ jobs = nullptr) {
   constexpr int ROWS = NW * RPW, NTH = NW * 32;
   if (failed(st)) return;
   extern __shared__ float sm[];
@@ -174,9 +175,18 @@ __global__ void __launch_bounds__(NW * 32)
   const int lds = TS_STRIP + 1;
   float *X = sm;                // [ROWS][ldx]: the CTA's rows of A_ik, solved in place
   float *S = X + ROWS * ldx;    // [32][lds]: strip of L_kk rows cb*32 + lane
-  int i = rows[blockIdx.y];
   int r0 = blockIdx.x * ROWS;
-  long ti = tile_index(i, k, NT);
+  // tile (i, k) of one matrix, or (batched) an explicit tile index and the
+  // slot of its L_kk copy
+  long ti;
+  const float *Lkk = Lkk0;
+  if (jobs) {
+    int2 jb = jobs[blockIdx.y];
+    ti = jb.x;
+    Lkk = Lkk0 + (size_t)jb.y * nb * nb;
+  } else {
+    ti = tile_index(rows[blockIdx.y], k, NT);
+  }
   float *A = t32 + (size_t)ti * nb * nb + r0;
   int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll 8
@@ -283,18 +293,32 @@ template <int BMT>
 __global__ void __launch_bounds__(256)
     k_update64_list(double *__restrict__ t64, const float *__restrict__ t32,
                     const unsigned char *__restrict__ cls, int nb, int NT, int k, const int2 *__restrict__ pairs,
-                    const int *st) {
+                    const int *st, const int4 *__restrict__ jobs = nullptr) {
   constexpr int R = BMT / 16;  // outputs per thread along each dimension
   if (failed(st)) return;
-  int2 pr = pairs[blockIdx.x];
-  int i = pr.x, j = pr.y;
+  // tiles C = (i, j), A = (i, k), B = (j, k) of one matrix, or (batched) the
+  // explicit tile indices {C, A, B, C is diagonal}
+  long tij, tik, tjk;
+  bool diag;
+  if (jobs) {
+    int4 jb = jobs[blockIdx.x];
+    tij = jb.x;
+    tik = jb.y;
+    tjk = jb.z;
+    diag = jb.w != 0;
+  } else {
+    int2 pr = pairs[blockIdx.x];
+    tij = tile_index(pr.x, pr.y, NT);
+    tik = tile_index(pr.x, k, NT);
+    tjk = tile_index(pr.y, k, NT);
+    diag = pr.x == pr.y;
+  }
   int nsub = nb / BMT;
   int bi = blockIdx.y % nsub, bj = blockIdx.y / nsub;
-  if (i == j && bi < bj) return;
-  long tik = tile_index(i, k, NT), tjk = tile_index(j, k, NT);
+  if (diag && bi < bj) return;
   bool i64 = cls[tik] == EMU_CLASS_FP64, j64 = cls[tjk] == EMU_CLASS_FP64;
   size_t oi = (size_t)tik * nb * nb + bi * BMT, oj = (size_t)tjk * nb * nb + bj * BMT;
-  double *C = t64 + (size_t)tile_index(i, j, NT) * nb * nb + bi * BMT + (size_t)bj * BMT * nb;
+  double *C = t64 + (size_t)tij * nb * nb + bi * BMT + (size_t)bj * BMT * nb;
   __shared__ double as[GK][BMT];
   __shared__ double bs[GK][BMT];
   int t = threadIdx.x, tx = t % 16, ty = t / 16;
@@ -965,4 +989,111 @@ void mixed_ctx_release(emu_ctx *ctx) {
   if (ctx->mid) cudaStreamDestroy(ctx->mid);
   if (ctx->bulk) cudaStreamDestroy(ctx->bulk);
   ctx->crit = ctx->mid = ctx->bulk = nullptr;
+}
+
+// ------------------------------------------------ batched factor launchers
+// The batched factor (batch.cu) runs the same kernels over explicit tile
+// indices of one shared arena: lists of tiles or jobs instead of (k, NT).
+namespace {
+
+// FP32 -> FP64 of listed whole tiles (low-precision diagonal tiles before
+// their FP64 POTRF).
+__global__ void k_tiles_to_f64(const float *__restrict__ t32, double *__restrict__ t64, const long *__restrict__ tiles,
+                               size_t te, const int *st) {
+  if (failed(st)) return;
+  size_t base = (size_t)tiles[blockIdx.y] * te;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < te; e += (size_t)gridDim.x * blockDim.x)
+    t64[base + e] = (double)t32[base + e];
+}
+
+// FP32 copies of listed FP64 diagonal factor tiles into consecutive slots.
+__global__ void k_diag_to_f32_slots(const double *__restrict__ t64, float *__restrict__ slots,
+                                    const long *__restrict__ tiles, size_t te, const int *st) {
+  if (failed(st)) return;
+  size_t base = (size_t)tiles[blockIdx.y] * te;
+  float *d = slots + (size_t)blockIdx.y * te;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < te; e += (size_t)gridDim.x * blockDim.x)
+    d[e] = (float)t64[base + e];
+}
+
+}  // namespace
+
+emu_status launch_to_f32_tiles(emu_ctx *ctx, const double *t64, float *t32, const unsigned char *cls, long ntiles,
+                               size_t te) {
+  if (ntiles <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * ntiles * te);
+  k_to_f32<<<dim3(16, (unsigned)ntiles), 256, 0, ctx->stream>>>(t64, t32, cls, te);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_tiles_to_f64(emu_ctx *ctx, const float *t32, double *t64, const long *d_tiles, int n, size_t te) {
+  if (n <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * n * te);
+  k_tiles_to_f64<<<dim3(16, n), 256, 0, ctx->stream>>>(t32, t64, d_tiles, te, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_diag_to_f32_slots(emu_ctx *ctx, const double *t64, float *slots, const long *d_tiles, int n,
+                                    size_t te) {
+  if (n <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * n * te);
+  k_diag_to_f32_slots<<<dim3(16, n), 256, 0, ctx->stream>>>(t64, slots, d_tiles, te, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_trsm32_jobs(emu_ctx *ctx, const float *slots, float *t32, uint16_t *op, int nb, const int2 *d_jobs,
+                              int njobs) {
+  if (njobs <= 0) return EMU_OK;
+  size_t sm = trsm32_smem(nb, 16);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  double nb3 = (double)nb * nb * nb;
+  ProfScope ps(ctx, PROF_TRSM32, njobs * nb3, 14.0 * njobs * nb * nb);
+  k_trsm32_panel<8, 2><<<dim3(nb / 16, njobs), 256, sm, ctx->stream>>>(slots, t32, op, nb, 0, 0, nullptr,
+                                                                       ctx->d_status, d_jobs);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_split_tiles64(emu_ctx *ctx, const double *t64, uint16_t *op, const int *d_tiles, int n, int nb,
+                                int lower_only) {
+  if (n <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n * (double)nb * nb);
+  k_split_tiles<double><<<dim3((nb / B) * (nb / B), n), 256, 0, ctx->stream>>>(t64, op, d_tiles, nb, lower_only,
+                                                                            ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_quant_e4m3(emu_ctx *ctx, const uint16_t *op, uint8_t *op8, float *scales, const int *d_tiles, int n,
+                             int nb) {
+  if (n <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 3.0 * n * (double)nb * nb);
+  k_quant_e4m3<<<n, 1024, 0, ctx->stream>>>(op, op8, scales, d_tiles, nb, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_update64_jobs(emu_ctx *ctx, double *t64, const float *t32, const unsigned char *cls, int nb,
+                                const int4 *d_jobs, int njobs) {
+  if (njobs <= 0) return EMU_OK;
+  double nb3 = (double)nb * nb * nb;
+  ProfScope ps(ctx, PROF_UPDATE64, 2.0 * njobs * nb3, 24.0 * njobs * (double)nb * nb);
+  if ((long)njobs * (nb / GM) * (nb / GM) >= 2L * ctx->sm_count)
+    k_update64_list<GM><<<dim3(njobs, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
+        t64, t32, cls, nb, 0, 0, nullptr, ctx->d_status, d_jobs);
+  else
+    k_update64_list<32><<<dim3(njobs, (nb / 32) * (nb / 32)), 256, 0, ctx->stream>>>(
+        t64, t32, cls, nb, 0, 0, nullptr, ctx->d_status, d_jobs);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_split_z(emu_ctx *ctx, const double *Z, long ldz, long npad, int s, int s_pad, uint16_t *zp) {
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * npad * s_pad);
+  k_split_z<<<8 * ctx->sm_count, 256, 0, ctx->stream>>>(Z, ldz, npad, s, s_pad, zp);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
 }

@@ -9,6 +9,8 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
                         double *Y, long ldy);
 emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs);
 void mixed_ctx_release(emu_ctx *ctx);
+// batch.cu: arenas, plan and graph of the context's last batch
+void batch_ctx_release(emu_ctx *ctx);
 void mixed_mat_release(emu_mat *A);
 emu_status refine_solve(emu_ctx *ctx, const emu_mat *L, const emu_mat *S, const double *dB,
                         long ldb, double *dX, long ldx, int nrhs, double tol, int maxit,

@@ -5,6 +5,8 @@
 // {p mod 2^32, p >> 32, column, stream id}, key {seed mod 2^32, seed >> 32},
 // p = row / 2; two 53-bit uniforms u1 in (0,1], u2 in [0,1); Box-Muller gives
 // rows 2p (cosine) and 2p+1 (sine).
+#include <algorithm>
+
 #include "emu_internal.h"
 
 namespace {
@@ -27,30 +29,52 @@ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
   }
 }
 
+// Normals of pair p (rows 2p, 2p+1) of column col, written at z[0], z[1].
+__device__ inline void normal_pair(uint64_t seed, uint32_t stream_id, long p, int col, int nrows, double *z) {
+  const double two_pi = 6.283185307179586476925286766559;
+  uint32_t c[4] = {(uint32_t)((uint64_t)p & 0xffffffffu), (uint32_t)((uint64_t)p >> 32), (uint32_t)col,
+                   stream_id};
+  philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+  uint64_t a = ((uint64_t)c[0] << 21) | (uint64_t)(c[1] >> 11);
+  uint64_t b = ((uint64_t)c[2] << 21) | (uint64_t)(c[3] >> 11);
+  double u1 = ((double)a + 1.0) * 0x1.0p-53;
+  double u2 = (double)b * 0x1.0p-53;
+  double rad = sqrt(-2.0 * log(u1));
+  double th = two_pi * u2;
+  z[0] = rad * cos(th);
+  if (2 * p + 1 < nrows) z[1] = rad * sin(th);
+}
+
 __global__ void k_normals(uint64_t seed, uint32_t stream_id, int nrows, int s,
                           double *__restrict__ Z, long ldz) {
   long npairs = (nrows + 1) / 2;
   long total = npairs * s;
-  const double two_pi = 6.283185307179586476925286766559;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
        q += (long)gridDim.x * blockDim.x) {
     long p = q % npairs;
     int col = (int)(q / npairs);
-    uint32_t c[4] = {(uint32_t)((uint64_t)p & 0xffffffffu), (uint32_t)((uint64_t)p >> 32),
-                     (uint32_t)col, stream_id};
-    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-    uint64_t a = ((uint64_t)c[0] << 21) | (uint64_t)(c[1] >> 11);
-    uint64_t b = ((uint64_t)c[2] << 21) | (uint64_t)(c[3] >> 11);
-    double u1 = ((double)a + 1.0) * 0x1.0p-53;
-    double u2 = (double)b * 0x1.0p-53;
-    double rad = sqrt(-2.0 * log(u1));
-    double th = two_pi * u2;
-    double *z = Z + (size_t)col * ldz + 2 * p;
-    z[0] = rad * cos(th);
-    if (2 * p + 1 < nrows) z[1] = rad * sin(th);
+    normal_pair(seed, stream_id, p, col, nrows, Z + (size_t)col * ldz + 2 * p);
   }
 }
 
+// Batch: blockIdx.y = matrix b, all NT_b * nb padded rows of its block of the
+// stacked Z (rows row_base ..), with its own stream id.
+// The seed is read from device memory so that a captured graph can be
+// replayed with another seed.
+__global__ void k_normals_batch(const uint64_t *__restrict__ seed_p, const BatchInst *__restrict__ inst, int nb,
+                                int s, double *__restrict__ Z, long ldz) {
+  const uint64_t seed = *seed_p;
+  BatchInst I = inst[blockIdx.y];
+  int nrows = I.NT * nb;
+  long npairs = (nrows + 1) / 2;
+  long total = npairs * s;
+  double *Zb = Z + I.row_base;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    long p = q % npairs;
+    int col = (int)(q / npairs);
+    normal_pair(seed, (uint32_t)I.stream_id, p, col, nrows, Zb + (size_t)col * ldz + 2 * p);
+  }
+}
 }  // namespace
 
 emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id, int nrows,
@@ -61,6 +85,16 @@ emu_status launch_normals(emu_ctx *ctx, uint64_t seed, uint32_t stream_id, int n
   if (blocks < 1) blocks = 1;
   ProfScope ps(ctx, PROF_RNG, 0.0, 8.0 * nrows * (double)s);
   k_normals<<<(unsigned)blocks, 256, 0, ctx->stream>>>(seed, stream_id, nrows, s, Z, ldz);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_normals_batch(emu_ctx *ctx, const uint64_t *d_seed, const BatchInst *d_inst, int count,
+                                int maxNT, int nb, int s, double *Z, long ldz) {
+  long per = (long)((maxNT * nb + 1) / 2) * s;
+  int bx = (int)std::min<long>(std::max<long>((per + 255) / 256, 1), 64);
+  ProfScope ps(ctx, PROF_RNG, 0.0, 0.0);
+  k_normals_batch<<<dim3(bx, count), 256, 0, ctx->stream>>>(d_seed, d_inst, nb, s, Z, ldz);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
