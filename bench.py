@@ -46,10 +46,15 @@ def parse():
     ap.add_argument("--beta", type=float, default=8.0)
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--samples", type=int, default=256)
-    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=None, help="sample seed (default: 1 single, 3 batched)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="single: one n=L^2 covariance (default); batched: --count covariances of random "
+                         "bandlimit L in [8, 64], beta in [2, 8) (SplitMix64 draws from --batch-seed)")
+    ap.add_argument("--count", type=int, default=1024)
+    ap.add_argument("--batch-seed", type=int, default=3)
     return ap.parse_args()
 
 
@@ -444,9 +449,223 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------- batched
+def batched_name(a) -> str:
+    return (f"batched: {a.count} covariances, L ~ U{{8..64}} (n = 64..4096), beta ~ U[2,8) (SplitMix64 seed "
+            f"{a.batch_seed}), adaptive FP64/FP32/BF16 at eps={a.eps:g}, {a.samples} samples each, one graph")
+
+
+def run_batched(a):
+    import numpy as np
+    import torch
+
+    import paper_2408_04440_gb300 as E
+    from paper_2408_04440_gb300 import build as _b
+    from paper_2408_04440_gb300.inputs import batch_draws
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    if rank == 0 or world == 1:
+        _b.build()
+    if dist is not None:
+        dist.barrier()
+    eps = a.eps
+    s = a.samples
+    draws = batch_draws(a.count, a.batch_seed + rank)  # weak scaling: a batch per rank
+    flops = sum((L * L) ** 3 / 3.0 for L, _ in draws)
+    stream = torch.cuda.Stream()
+    ctx = E.Context(local, stream=stream)
+    Ys = [E._colmajor_empty(L * L, s, ctx.device) for L, _ in draws]
+
+    def step(nb=0, e=eps):
+        return E.emu_batch_potrf_sample(ctx, draws, nb=nb, eps=e, prec_mask=MASK_FP64_FP32_BF16, nsamples=s,
+                                        seed=a.seed, out_Y=Ys)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(a.warmup, 1)):  # the first call tunes the tile size and captures the graph
+            _, _, infos, _ = step()
+        clocks = ClockSampler(local)
+        barrier()
+        launches0 = ctx.launch_count
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+        barrier()
+        clk = clocks.stop()
+        gpu_launches = ctx.launch_count - launches0
+        t = torch.tensor([e0.elapsed_time(e1)], device=ctx.device)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item()) / a.steps
+        value = world * flops / (ms_per_step * 1e-3) / 1e12
+        if rank != 0:
+            ctx.close()
+            if dist is not None:
+                dist.barrier()
+                dist.destroy_process_group()
+            return
+        nb_used = infos[0].nb
+        tiles = [int(x) for x in np.sum([i.tiles for i in infos], axis=0)]
+        extra = {"tile_size": nb_used, "tiles_per_class": dict(zip(E.CLASS_NAMES, tiles)), "graph_ms": round(infos[0].ms, 3)}
+        ctx.prof_enable(True)
+        step()
+        prof = ctx.prof_read()
+        ctx.prof_enable(False)
+        step_ms = sum(v["ms"] for v in prof.values())
+        extra["kernel_groups"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                      "share": round(v["ms"] / step_ms, 4)} for k, v in prof.items() if v["launches"]}
+        roof = roofline(prof, load_peaks())
+        # the comparisons: the whole batch in plain FP64, and the single-matrix
+        # FP64 path launched matrix by matrix (a sample, scaled by its flops)
+        if not a.no_fp64:
+            step(nb=nb_used, e=0.0)
+            _, _, i64, _ = step(nb=nb_used, e=0.0)
+            E.emu_batch_release(ctx)
+            extra["fp64_batch_ms"] = round(i64[0].ms, 2)
+            extra["fp64_batch_tflops"] = round(flops / (i64[0].ms * 1e-3) / 1e12, 4)
+            sub = draws[:128]
+            fl_sub = sum((L * L) ** 3 / 3.0 for L, _ in sub)
+
+            def per_matrix():
+                for b, (L, beta) in enumerate(sub):
+                    M = E.emu_cov_build(ctx, L, beta, 256)
+                    E.emu_potrf_mp(ctx, M)
+                    E.emu_sample(ctx, M, s, seed=a.seed, stream_id=b)
+                    M.free()
+
+            per_matrix()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            per_matrix()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            extra["per_matrix_fp64_tflops"] = round(fl_sub / dt / 1e12, 4)
+            extra["per_matrix_fp64_sample"] = "first 128 matrices, single-matrix FP64 path, one call each"
+            extra["speedup_vs_per_matrix_fp64"] = round(value / (fl_sub / dt / 1e12), 2)
+        e2e = None
+        if not a.no_e2e:
+            # the same call with every Y_b read back into pinned host memory
+            hY = [torch.empty((s, L * L), dtype=torch.float64, pin_memory=True).t() for L, _ in draws]
+            step()
+            for h, y in zip(hY, Ys):
+                h.copy_(y, non_blocking=True)
+            torch.cuda.synchronize()
+            k = max(3, min(a.steps, 5))
+            t0 = time.perf_counter()
+            for _ in range(k):
+                step()
+                for h, y in zip(hY, Ys):
+                    h.copy_(y, non_blocking=True)
+                torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / k
+            e2e = {"value": round(flops / dt / 1e12, 4), "unit": "TFLOP/s", "ms_per_step": round(dt * 1e3, 3),
+                   "h2d_bytes_per_step": a.count * 32, "d2h_bytes_per_step": int(sum(L * L * s * 8 for L, _ in draws)),
+                   "steps": k, "path": "emu_batch_potrf_sample (parameters in, samples to pinned host memory)"}
+    cpu = None if (a.no_cpu or world > 1) else cpu_baseline_batched(a, draws)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed:f64+f32(3xbf16 split)+bf16", "data": "synthetic",
+        "config": {"workload": batched_name(a), "count": a.count, "eps": eps, "samples": s, "seed": a.seed,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2: every step rebuilds the ~19 GB FP64 tile arena"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_matrix_flops(L, beta, s, seed, b):
+    """One matrix of the batch through the oracle: build, blocked FP64 factor
+    (tile 256), samples; returns the factor's n^3/3."""
+    import oracle as O
+
+    n = L * L
+    S = O.cov_build(L, beta)
+    Lf, _ = O.potrf_blocked(S, 256)
+    O.trmm_lower(Lf, O.normal_matrix(seed, b, n, s))
+    return n ** 3 / 3.0
+
+
+def cpu_baseline_batched(a, draws, budget_s: float = 15.0) -> dict:
+    """The oracle on this host's cores, matrix after matrix of the batch until
+    about budget_s has passed."""
+    fl, dt, m = 0.0, 0.0, 0
+    while m < len(draws) and dt < budget_s:
+        t0 = time.perf_counter()
+        fl += _oracle_matrix_flops(draws[m][0], draws[m][1], a.samples, a.seed, m)
+        dt += time.perf_counter() - t0
+        m += 1
+    return {"value": round(fl / dt / 1e12, 5), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {m} of {len(draws)} matrices: build, blocked FP64 factor, {a.samples} samples "
+                      f"({fl:.3e} flop in {dt:.1f} s)"}
+
+
+def run_reference_batched(a):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from paper_2408_04440_gb300.inputs import batch_draws
+
+    draws = batch_draws(a.count, a.batch_seed)
+    state = {"m": 0}
+
+    def step():
+        m = state["m"] % len(draws)
+        state["m"] += 1
+        return _oracle_matrix_flops(draws[m][0], draws[m][1], a.samples, a.seed, m)
+
+    for _ in range(a.warmup):
+        step()
+    fl = 0.0
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        fl += step()
+    dt = time.perf_counter() - t0
+    value = fl / dt / 1e12
+    cpu = {"value": round(value, 5), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{a.steps} matrices of the batch per timed region (one matrix per step)"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / max(a.steps, 1) * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": batched_name(a), "count": a.count},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.seed is None:
+        a.seed = 3 if a.workload == "batched" else 1
+    if a.workload == "batched":
+        # the batched workload's own defaults (eps 1e-8, 256 samples, seed 3)
+        if a.impl == "reference":
+            run_reference_batched(a)
+        else:
+            run_batched(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

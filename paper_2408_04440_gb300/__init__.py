@@ -406,17 +406,20 @@ def emu_solve_refine(ctx: Context, L: Mat, S: Mat, B, tol: float = 1e-14, maxit:
 
 def emu_batch_potrf_sample(ctx: Context, params, nb: int = 256, eps: float = 0.0, prec_mask: int = 0b01011,
                            diag_fp64: bool = False, u=None, nsamples: int = 0, seed: int = 0, want_L: bool = False,
-                           raise_on_error: bool = True):
+                           raise_on_error: bool = True, out_Y=None):
     """params: sequence of (L, beta) or (L, beta, sigma_exp, nugget_rel).
     Returns (Ys, Ls, infos, status): lists of column-major CUDA tensors
-    (n_b x nsamples and n_b x n_b; None where not asked) and FactorInfo."""
+    (n_b x nsamples and n_b x n_b; None where not asked) and FactorInfo.
+    out_Y: optional list of preallocated Y_b (column-major, ld n_b)."""
     count = len(params)
     P = (emu_cov_params * count)()
     for b, q in enumerate(params):
         sexp = float(q[2]) if len(q) > 2 else 1.5
         nug = float(q[3]) if len(q) > 3 else 1e-8
         P[b] = emu_cov_params(int(q[0]), float(q[1]), sexp, nug)
-    Ys = [_colmajor_empty(int(q[0]) ** 2, nsamples, ctx.device) for q in params] if nsamples > 0 else None
+    Ys = None
+    if nsamples > 0:
+        Ys = out_Y if out_Y is not None else [_colmajor_empty(int(q[0]) ** 2, nsamples, ctx.device) for q in params]
     Ls = [_colmajor_empty(int(q[0]) ** 2, int(q[0]) ** 2, ctx.device) for q in params] if want_L else None
     yp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ys]) if Ys else None
     lp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ls]) if Ls else None

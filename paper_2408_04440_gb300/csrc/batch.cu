@@ -654,9 +654,15 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
     EMU_CUDA_TRY(ctx, cudaMemcpyAsync(B->d_Lptr, dL, count * sizeof(double *), cudaMemcpyHostToDevice, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(B->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
-  EMU_CUDA_TRY(ctx, cudaGraphLaunch(B->graph, ctx->stream));
+  if (ctx->prof) {
+    // profiling: the same launches issued one by one, so that each kernel
+    // group gets its own events
+    if ((s = batch_record(ctx, B)) != EMU_OK) return s;
+  } else {
+    EMU_CUDA_TRY(ctx, cudaGraphLaunch(B->graph, ctx->stream));
+    ctx->launches += B->graph_launches;
+  }
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
-  ctx->launches += B->graph_launches;
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(int), cudaMemcpyDeviceToHost,
                                     ctx->stream));
   EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
