@@ -76,6 +76,7 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
   return acc0 + acc1;
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(PB * PB)
     k_potrf_dag(double *__restrict__ D0, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
                 int *__restrict__ ws, double *__restrict__ rinv_all, int *st,
@@ -98,13 +99,14 @@ __global__ void __launch_bounds__(PB * PB)
     if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
     __syncthreads();
     int t = s_task;
-    if (t >= ntasks * nbat) return;
-    const int bt = t % nbat;
-    double *D = dtiles ? D0 + (size_t)dtiles[bt] * nb * nb : D0;
-    int *state = ws + 1 + (size_t)bt * nbb * nbb;
-    double *rinv_g = rinv_all + (size_t)bt * nb;
+    // one tile (the single-matrix factor) compiles without the batch indexing
+    const int bt = BATCH ? t % nbat : 0;
+    if (t >= (BATCH ? ntasks * nbat : ntasks)) return;
+    double *D = BATCH ? D0 + (size_t)dtiles[bt] * nb * nb : D0;
+    int *state = BATCH ? ws + 1 + (size_t)bt * nbb * nbb : ws + 1;
+    double *rinv_g = BATCH ? rinv_all + (size_t)bt * nb : rinv_all;
     auto blk = [&](int br, int bc) { return D + (size_t)(br * PB + ty) + (size_t)(bc * PB + tx) * ld; };
-    short4 tk = tasks[t / nbat];
+    short4 tk = tasks[BATCH ? t / nbat : t];
     int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LT: (s, s-1, s); TRSM: (r, s, s); UPD: (r, c, s)
     unsigned long long t_fetch = 0;
     if (trace && threadIdx.x == 0) t_fetch = gtimer();
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(PB * PB)
         if (bad) {
           if (threadIdx.x == 0) {
             st[ST_PIVOT] = gcol0 + s * PB + bad;
-            if (dtiles) st[ST_AUX] = bt;  // which tile of the batch
+            if (BATCH) st[ST_AUX] = bt;  // which tile of the batch
             __threadfence();
             atomicExch(&st[ST_CODE], DEV_NOTPD);
           }
@@ -619,8 +621,9 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
     ctx->trace_records = (size_t)(k + 1) * ctx->dag_ntasks;
   }
   double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
-  k_potrf_dag<<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks, ctx->dag_ntasks,
-                                                ctx->dag_ws, rinv, ctx->d_status, trace, nullptr, 1);
+  k_potrf_dag<false><<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks,
+                                                       ctx->dag_ntasks, ctx->dag_ws, rinv, ctx->d_status, trace,
+                                                       nullptr, 1);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -673,8 +676,8 @@ emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const 
   EMU_CUDA_TRY(ctx, cudaMemsetAsync(ws, 0, dag_ws_ints(nbb, nbat) * sizeof(int), ctx->stream));
   long total = (long)ntasks * nbat;
   int grid = (int)std::min<long>(total, 4L * ctx->sm_count);
-  k_potrf_dag<<<grid, PB * PB, 0, ctx->stream>>>(t64, nb, k * nb, (const short4 *)d_tasks, ntasks, ws, rinv,
-                                                ctx->d_status, nullptr, d_tiles, nbat);
+  k_potrf_dag<true><<<grid, PB * PB, 0, ctx->stream>>>(t64, nb, k * nb, (const short4 *)d_tasks, ntasks, ws,
+                                                      rinv, ctx->d_status, nullptr, d_tiles, nbat);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "gemm_f64.h"
 #include "gemm_tc.h"
 #include "mixed.h"
 
@@ -163,7 +164,7 @@ constexpr int TS_STRIP = 128;  // columns of L_kk staged at once
 // w + NW*q).  16-row CTAs (8 warps x 2) for throughput on the panel, 4-row
 // CTAs (4 warps x 1) for the single tile on the critical path, where more
 // CTAs in parallel mean less latency.
-template <int NW, int RPW>
+template <int NW, int RPW, bool JOBS = false>
 __global__ void __launch_bounds__(NW * 32)
     k_trsm32_panel(const float *__restrict__ Lkk0, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
                    int NT, int k, const int *__restrict__ rows, const int *st,
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(NW * 32)
   // slot of its L_kk copy
   long ti;
   const float *Lkk = Lkk0;
-  if (jobs) {
+  if (JOBS) {
     int2 jb = jobs[blockIdx.y];
     ti = jb.x;
     Lkk = Lkk0 + (size_t)jb.y * nb * nb;
@@ -455,7 +456,9 @@ struct StepPlan {
   int r64_1 = 0, n64_1 = 0, r32_1 = 0, n32_1 = 0;  // T1 (offset, count) in rows64 / rows32
   int r64_r = 0, n64_r = 0, r32_r = 0, n32_r = 0;  // TR
   int q_1 = 0, nq_1 = 0, q_r = 0, nq_r = 0;        // panel tiles to quantize to E4M3 (row k+1 / rest)
-  int p_off[GR_N] = {}, p_n[GR_N] = {};            // FP64 pairs per update group
+  int p_off[GR_N] = {}, p_n[GR_N] = {};            // FP64-class tensor-core items per update group
+  double p_flops[GR_N] = {};
+  int z1_off = 0, z1_n = 0, zr_off = 0, zr_n = 0;  // panel tiles digit-sliced for them (row k+1 / rest)
   int i_off[GR_N] = {}, i_n[GR_N] = {};            // tensor-core items per update group
   double flops[GR_N] = {}, mma[GR_N] = {};
   bool diag_low = false;
@@ -466,7 +469,12 @@ struct MixedPlan {
   std::vector<unsigned char> cls;  // packed by tile index
   std::vector<StepPlan> steps;
   int *d_rows64 = nullptr, *d_rows32 = nullptr;
-  int2 *d_pairs = nullptr;
+  gemm64::Item *d_items64 = nullptr;  // FP64-class updates on the tensor cores (digit products)
+  int2 *d_zjobs = nullptr;            // {tile, slot} of the panel tiles digit-sliced for them
+  int nslots = 0;
+  uint16_t *d_digits = nullptr;       // nslots * NS digit planes of nb x nb
+  double *d_scales64 = nullptr;       // nslots * nb row scales
+  CUtensorMap map64a, map64b;
   gemm_tc::Item *d_items = nullptr;
   gemm_tc::Seg *d_segs = nullptr;
   int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
@@ -489,6 +497,8 @@ struct MixedPlan {
 static void plan_free(MixedPlan *p) {
   if (!p) return;
   if (p->d_blob) cudaFreeAsync(p->d_blob, p->stream);
+  if (p->d_digits) cudaFreeAsync(p->d_digits, p->stream);
+  if (p->d_scales64) cudaFreeAsync(p->d_scales64, p->stream);
   delete p;
 }
 
@@ -504,7 +514,9 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->cls.assign(A->h_cls, A->h_cls + A->ntiles);
   auto C = [&](int i, int j) { return (int)P->cls[tile_index(i, j, NT)]; };
   std::vector<int> rows64, rows32, tiles64, diag, qtiles;
-  std::vector<int2> pairs;
+  std::vector<gemm64::Item> items64;
+  std::vector<int2> zjobs, z1_step, zr_step;
+  std::vector<int> slot_of_tile(A->ntiles, -1);
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
   double nb3 = (double)nb * nb * nb;
@@ -514,11 +526,34 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
       P->tiles[c]++;
       P->update_flops[c] += (i == j ? 1.0 : 2.0) * j * nb3 + (i > j ? nb3 : 0.0);
     }
+  // digit slot of panel tile (r, k), sliced after its TRSM
+  auto slot_of = [&](int k, int r) {
+    long t = tile_index(r, k, NT);
+    if (slot_of_tile[t] < 0) {
+      slot_of_tile[t] = P->nslots++;
+      (r == k + 1 ? z1_step : zr_step).push_back(make_int2((int)t, slot_of_tile[t]));
+    }
+    return slot_of_tile[t];
+  };
   auto add_tile_update = [&](StepPlan &sp, int g, int k, int i, int j) {
     int c = C(i, j);
     if (c == EMU_CLASS_FP64) {
-      pairs.push_back(make_int2(i, j));
-      sp.p_n[g]++;
+      // FP64 accuracy on the tensor cores: digit products of panel tiles (i, k), (j, k)
+      int si = slot_of(k, i), sj = slot_of(k, j);
+      for (int nbk = 0; nbk < nb / gemm64::BN; nbk++)
+        for (int mb = 0; mb < nb / gemm64::BM; mb++) {
+          if (i == j && mb * gemm64::BM + gemm64::BM - 1 < nbk * gemm64::BN) continue;  // above the diagonal
+          gemm64::Item it;
+          it.out_off = tile_index(i, j, NT) * (long)nb * nb + mb * gemm64::BM + (long)nbk * gemm64::BN * nb;
+          it.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
+          it.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
+          it.a_sc = si * nb + mb * gemm64::BM;
+          it.b_sc = sj * nb + nbk * gemm64::BN;
+          it.pad[0] = it.pad[1] = 0;
+          items64.push_back(it);
+          sp.p_n[g]++;
+        }
+      sp.p_flops[g] += 2.0 * nb3;
       return;
     }
     int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : (c == EMU_CLASS_E4M3) ? EMU_CLASS_E4M3 : EMU_CLASS_BF16;
@@ -575,7 +610,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     sp.r32_r = (int)rows32.size();
     for (int i = k + 2; i < NT; i++) add_row(k, i, sp.n64_r, sp.n32_r);
     for (int g = 0; g < GR_N; g++) {
-      sp.p_off[g] = (int)pairs.size();
+      sp.p_off[g] = (int)items64.size();
       sp.i_off[g] = (int)items.size();
       if (g == GR_S) {
         if (k + 1 < NT) add_tile_update(sp, g, k, k + 1, k + 1);
@@ -606,6 +641,14 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         sp.nq_r++;
       }
     if (sp.n64_1 > 0 || sp.p_n[GR_S] > 0) P->crit64 = true;
+    sp.z1_off = (int)zjobs.size();
+    zjobs.insert(zjobs.end(), z1_step.begin(), z1_step.end());
+    sp.z1_n = (int)z1_step.size();
+    sp.zr_off = (int)zjobs.size();
+    zjobs.insert(zjobs.end(), zr_step.begin(), zr_step.end());
+    sp.zr_n = (int)zr_step.size();
+    z1_step.clear();
+    zr_step.clear();
     P->steps.push_back(sp);
   }
   // one allocation and one copy for all lists (256-byte aligned parts)
@@ -616,7 +659,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     return o;
   };
   auto vbytes = [](const auto &v) { return v.size() * sizeof(v[0]); };
-  size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_pairs = part(vbytes(pairs)),
+  size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_i64 = part(vbytes(items64)),
+         o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
          o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)),
          o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
@@ -627,7 +671,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   };
   put(o_r64, rows64);
   put(o_r32, rows32);
-  put(o_pairs, pairs);
+  put(o_i64, items64);
+  put(o_z, zjobs);
   put(o_items, items);
   put(o_segs, segs);
   put(o_t64, tiles64);
@@ -639,7 +684,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(b, P->host_blob.data(), copy_bytes, cudaMemcpyHostToDevice, ctx->stream));
   P->d_rows64 = reinterpret_cast<int *>(b + o_r64);
   P->d_rows32 = reinterpret_cast<int *>(b + o_r32);
-  P->d_pairs = reinterpret_cast<int2 *>(b + o_pairs);
+  P->d_items64 = reinterpret_cast<gemm64::Item *>(b + o_i64);
+  P->d_zjobs = reinterpret_cast<int2 *>(b + o_z);
   P->d_items = reinterpret_cast<gemm_tc::Item *>(b + o_items);
   P->d_segs = reinterpret_cast<gemm_tc::Seg *>(b + o_segs);
   P->d_tiles64 = reinterpret_cast<int *>(b + o_t64);
@@ -655,6 +701,15 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->ops.a8 = P->mapA;  // valid maps even when no FP8 copies exist (then never used)
   P->ops.b8 = P->mapB;
   P->ops.scale8 = nullptr;
+  if (P->nslots > 0) {
+    size_t te = (size_t)nb * nb;
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_digits, (size_t)P->nslots * gemm64::NS * te * sizeof(uint16_t),
+                                      ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_scales64, (size_t)P->nslots * nb * sizeof(double), ctx->stream));
+    uint64_t drows = (uint64_t)P->nslots * gemm64::NS * nb;
+    if ((s = gemm64::make_map(ctx, &P->map64a, P->d_digits, nb, drows, gemm64::BM)) != EMU_OK) return s;
+    if ((s = gemm64::make_map(ctx, &P->map64b, P->d_digits, nb, drows, gemm64::BN)) != EMU_OK) return s;
+  }
   if (P->any_e4m3) {
     size_t te = (size_t)nb * nb;
     if (!A->op_e4m3) EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->op_e4m3, (size_t)A->ntiles * te, ctx->stream));
@@ -763,6 +818,9 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     EMU_LAUNCHED(ctx);
     return EMU_OK;
   };
+  auto slice64 = [&](int z0, int nz) -> emu_status {
+    return gemm64::launch_slice(ctx, A->t64, A->t32, A->d_cls, P->d_zjobs + z0, nz, nb, P->d_digits, P->d_scales64);
+  };
   auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
     emu_status e = EMU_OK;
     if (n64 > 0) {
@@ -789,14 +847,11 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   auto update_group = [&](int k, int g, int max_ctas) -> emu_status {
     const StepPlan &sp = P->steps[k];
     if (sp.p_n[g] > 0) {
-      ProfScope ps(ctx, PROF_UPDATE64, 2.0 * sp.p_n[g] * nb3, 24.0 * sp.p_n[g] * te);
-      if ((long)sp.p_n[g] * (nb / GM) * (nb / GM) >= 2L * ctx->sm_count)
-        k_update64_list<GM><<<dim3(sp.p_n[g], (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
-            A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
-      else
-        k_update64_list<32><<<dim3(sp.p_n[g], (nb / 32) * (nb / 32)), 256, 0, ctx->stream>>>(
-            A->t64, A->t32, A->d_cls, nb, NT, k, P->d_pairs + sp.p_off[g], st);
-      EMU_LAUNCHED(ctx);
+      // FP64-class tiles: 36 digit products per K step on the BF16 tensor cores
+      ProfScope ps(ctx, PROF_UPDATE64, sp.p_flops[g], 24.0 * sp.p_flops[g] / (2.0 * nb), 36.0 * sp.p_flops[g]);
+      emu_status e = gemm64::launch(ctx, P->map64a, P->map64b, P->d_items64 + sp.p_off[g], sp.p_n[g], nb,
+                                    P->d_scales64, A->t64, nb, std::max(1, max_ctas));
+      if (e != EMU_OK) return e;
     }
     if (sp.i_n[g] > 0) {
       ProfScope ps(ctx, PROF_TC_FACTOR, sp.flops[g], 0.0, sp.mma[g]);
@@ -828,6 +883,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
     if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
     if ((s = quantize(sp.q_1, sp.nq_1)) != EMU_OK) break;
+    if ((s = slice64(sp.z1_off, sp.z1_n)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T1), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G2), 0));  // G2A(k-1)
     if ((s = update_group(k, GR_S, ctx->sm_count)) != EMU_OK) break;
@@ -836,6 +892,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_P), 0));
     if ((s = trsm_rows(k, sp.r64_r, sp.n64_r, sp.r32_r, sp.n32_r, false)) != EMU_OK) break;
     if ((s = quantize(sp.q_r, sp.nq_r)) != EMU_OK) break;
+    if ((s = slice64(sp.zr_off, sp.zr_n)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T), ctx->mid));
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_T1), 0));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k - 1, E_G2), 0));
@@ -1048,11 +1105,12 @@ emu_status launch_trsm32_jobs(emu_ctx *ctx, const float *slots, float *t32, uint
                               int njobs) {
   if (njobs <= 0) return EMU_OK;
   size_t sm = trsm32_smem(nb, 16);
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm));
   double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM32, njobs * nb3, 14.0 * njobs * nb * nb);
-  k_trsm32_panel<8, 2><<<dim3(nb / 16, njobs), 256, sm, ctx->stream>>>(slots, t32, op, nb, 0, 0, nullptr,
-                                                                       ctx->d_status, d_jobs);
+  k_trsm32_panel<8, 2, true><<<dim3(nb / 16, njobs), 256, sm, ctx->stream>>>(slots, t32, op, nb, 0, 0, nullptr,
+                                                                             ctx->d_status, d_jobs);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -220,3 +220,24 @@ def test_e4m3_refinement(E, ctx):
                                                + np.linalg.norm(B, axis=0))
     assert eta.max() <= 2e-15
     print(f"refine with E4M3 tiles: {ri.iters} iterations")
+
+
+@pytest.mark.parametrize("L,nb,beta", [(20, 256, 4.0), (45, 256, 5.0), (32, 512, 4.0), (40, 1024, 6.0)])
+def test_fp64_class_on_tensor_cores_matches_oracle(E, ctx, L, nb, beta):
+    # every tile FP64-class: the trailing updates run as exact digit products
+    # on the BF16 tensor cores (fixed-point Ozaki scheme, 8 digits of 7 bits,
+    # FP64 sums of the digit groups), and the factor must match the FP64
+    # oracle as the plain FP64 path does.  nb = 256 / 512 / 1024 exercise 1,
+    # 2 and 4 exact FP32 accumulation chunks per update; L = 45 a ragged tile.
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=1e-3, prec_mask=0b00001)
+    assert info.tiles[0] == info.nt * (info.nt + 1) // 2
+    G = _np(E.emu_mat_export(ctx, A))
+    S = O.cov_build(L, beta)
+    Lo, oinfo = O.potrf_blocked(S, nb)
+    assert oinfo == 0
+    rel = np.linalg.norm(G - Lo) / np.linalg.norm(Lo)
+    assert rel <= 1e-12, rel
+    be = _backward_error(G, S)
+    assert be <= 1e-15, be
+    print(f"FP64 class on tensor cores L={L} nb={nb}: vs oracle {rel:.2e}, backward {be:.2e}")
