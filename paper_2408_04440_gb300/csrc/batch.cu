@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "emu_internal.h"
+#include "gemm_f64.h"
 #include "gemm_tc.h"
 
 namespace {
@@ -54,7 +55,9 @@ struct Step {
   int s64_off = 0, s64_n = 0;  // their tiles, split into BF16 pieces afterwards
   int t32_off = 0, t32_n = 0;  // FP32 TRSM jobs {tile (i,k), slot of L_kk}
   int q_off = 0, q_n = 0;      // panel tiles quantized to E4M3
-  int u_off = 0, u_n = 0;      // FP64 update jobs {C, A, B, diagonal}
+  int u_off = 0, u_n = 0;      // FP64-class updates: tensor-core digit-product items
+  int z_off = 0, z_n = 0;      // panel tiles digit-sliced for them {tile, slot}
+  double u_flops = 0.0;
   int it_off = 0, it_n = 0;    // tensor-core items
   double tc_flops = 0.0, tc_mma = 0.0;
 };
@@ -113,7 +116,13 @@ struct BatchState {
   int *d_all_diag_int = nullptr;
   int2 *d_t64 = nullptr, *d_t32 = nullptr;
   int *d_s64 = nullptr, *d_q = nullptr;
-  int4 *d_u64 = nullptr, *d_pairs = nullptr;
+  int4 *d_pairs = nullptr;
+  gemm64::Item *d_items64 = nullptr;
+  int2 *d_z = nullptr;
+  int nslots = 0;
+  uint16_t *digits = nullptr;
+  double *scales64 = nullptr;
+  CUtensorMap map64a, map64b;
   gemm_tc::Item *d_items = nullptr, *d_items_s = nullptr;
   gemm_tc::Seg *d_segs = nullptr, *d_segs_s = nullptr;
   TrmmJob *d_trmm = nullptr;
@@ -124,7 +133,8 @@ struct BatchState {
   void release() {
     void *ps[] = {t64, partial, tnorm, frob, tables, t32, slots, scale8, op, zp, op8, d_cls, d_inst, d_tile_inst,
                   Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_all_diag, d_all_diag_int, d_t64,
-                  d_t32, d_s64, d_q, d_u64, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_trmm};
+                  d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_trmm, d_items64, d_z,
+                  digits, scales64};
     for (void *p : ps)
       if (p) cudaFree(p);
     if (graph) cudaGraphExecDestroy(graph);
@@ -223,7 +233,9 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   std::vector<long> longs;
   std::vector<int2> j64, j32;
   std::vector<int> s64, q;
-  std::vector<int4> u64;
+  std::vector<gemm64::Item> items64;
+  std::vector<int2> zjobs;
+  std::vector<int> slot_of_tile(B->ntiles, -1);
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
   B->steps.assign(B->maxNT, Step());
@@ -262,7 +274,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     st.s64_off = (int)s64.size();
     st.t32_off = (int)j32.size();
     st.q_off = (int)q.size();
-    st.u_off = (int)u64.size();
+    st.u_off = (int)items64.size();
+    st.z_off = (int)zjobs.size();
     st.it_off = (int)items.size();
     for (int b = 0; b < count; b++) {
       const BatchInst &I = B->inst[b];
@@ -284,7 +297,26 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
           long gik = I.tile_base + tile_index(i, k, I.NT), gjk = I.tile_base + tile_index(j, k, I.NT);
           int c = C(gij);
           if (c == EMU_CLASS_FP64) {
-            u64.push_back(make_int4((int)gij, (int)gik, (int)gjk, i == j));
+            // digit products on the tensor cores; panel tiles sliced after this step's TRSMs
+            for (long t : {gik, gjk})
+              if (slot_of_tile[t] < 0) {
+                slot_of_tile[t] = B->nslots++;
+                zjobs.push_back(make_int2((int)t, slot_of_tile[t]));
+              }
+            int si = slot_of_tile[gik], sj = slot_of_tile[gjk];
+            for (int nbk = 0; nbk < nb / gemm64::BN; nbk++)
+              for (int mb = 0; mb < nb / gemm64::BM; mb++) {
+                if (i == j && mb * gemm64::BM + gemm64::BM - 1 < nbk * gemm64::BN) continue;
+                gemm64::Item it;
+                it.out_off = gij * (long)te + mb * gemm64::BM + (long)nbk * gemm64::BN * nb;
+                it.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
+                it.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
+                it.a_sc = si * nb + mb * gemm64::BM;
+                it.b_sc = sj * nb + nbk * gemm64::BN;
+                it.pad[0] = it.pad[1] = 0;
+                items64.push_back(it);
+              }
+            st.u_flops += 2.0 * nb3;
             continue;
           }
           int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : (c == EMU_CLASS_E4M3) ? EMU_CLASS_E4M3 : EMU_CLASS_BF16;
@@ -326,7 +358,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     st.s64_n = (int)s64.size() - st.s64_off;
     st.t32_n = (int)j32.size() - st.t32_off;
     st.q_n = (int)q.size() - st.q_off;
-    st.u_n = (int)u64.size() - st.u_off;
+    st.u_n = (int)items64.size() - st.u_off;
+    st.z_n = (int)zjobs.size() - st.z_off;
     st.it_n = (int)items.size() - st.it_off;
   }
   std::vector<long> all_diag;
@@ -401,7 +434,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   if ((s = upload(ctx, &B->d_diag, longs)) != EMU_OK || (s = upload(ctx, &B->d_all_diag, all_diag)) != EMU_OK ||
       (s = upload(ctx, &B->d_all_diag_int, all_diag_int)) != EMU_OK || (s = upload(ctx, &B->d_t64, j64)) != EMU_OK ||
       (s = upload(ctx, &B->d_t32, j32)) != EMU_OK || (s = upload(ctx, &B->d_s64, s64)) != EMU_OK ||
-      (s = upload(ctx, &B->d_q, q)) != EMU_OK || (s = upload(ctx, &B->d_u64, u64)) != EMU_OK ||
+      (s = upload(ctx, &B->d_q, q)) != EMU_OK || (s = upload(ctx, &B->d_items64, items64)) != EMU_OK ||
+      (s = upload(ctx, &B->d_z, zjobs)) != EMU_OK ||
       (s = upload(ctx, &B->d_pairs, pairs)) != EMU_OK || (s = upload(ctx, &B->d_items, items)) != EMU_OK ||
       (s = upload(ctx, &B->d_segs, segs)) != EMU_OK || (s = upload(ctx, &B->d_items_s, items_s)) != EMU_OK ||
       (s = upload(ctx, &B->d_segs_s, segs_s)) != EMU_OK || (s = upload(ctx, &B->d_trmm, trmm)) != EMU_OK)
@@ -416,6 +450,10 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   if (B->any_e4m3) {
     B->op8 = dalloc<uint8_t>(B->ntiles * te, &s);
     B->scale8 = dalloc<float>(B->ntiles, &s);
+  }
+  if (B->nslots > 0) {
+    B->digits = dalloc<uint16_t>((size_t)B->nslots * gemm64::NS * te, &s);
+    B->scales64 = dalloc<double>((size_t)B->nslots * nb, &s);
   }
   B->ntasks = (int)potrf_dag_task_count(nb);
   B->tasks = dalloc<short4>(B->ntasks, &s);
@@ -445,6 +483,15 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     uint64_t rows8 = (uint64_t)B->ntiles * nb;
     if ((s = gemm_tc::make_map_e4m3(ctx, &B->ops_f.a8, B->op8, nb, rows8, gemm_tc::BM)) != EMU_OK) return s;
     if ((s = gemm_tc::make_map_e4m3(ctx, &B->ops_f.b8, B->op8, nb, rows8, gemm_tc::BN)) != EMU_OK) return s;
+  }
+  if (B->nslots > 0) {
+    uint64_t drows = (uint64_t)B->nslots * gemm64::NS * nb;
+    if (drows >= (1ull << 31)) {
+      ctx->last_error = "batch digit arena too large for 32-bit TMA coordinates";
+      return EMU_EINVAL;
+    }
+    if ((s = gemm64::make_map(ctx, &B->map64a, B->digits, nb, drows, gemm64::BM)) != EMU_OK) return s;
+    if ((s = gemm64::make_map(ctx, &B->map64b, B->digits, nb, drows, gemm64::BN)) != EMU_OK) return s;
   }
   B->ops_s = B->ops_f;
   if (B->s > 0 &&
@@ -497,8 +544,15 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     if ((s = launch_trsm32_jobs(ctx, B->slots, B->t32, B->op, nb, B->d_t32 + st.t32_off, st.t32_n)) != EMU_OK)
       return s;
     if ((s = launch_quant_e4m3(ctx, B->op, B->op8, B->scale8, B->d_q + st.q_off, st.q_n, nb)) != EMU_OK) return s;
-    if ((s = launch_update64_jobs(ctx, B->t64, B->t32, B->d_cls, nb, B->d_u64 + st.u_off, st.u_n)) != EMU_OK)
+    if ((s = gemm64::launch_slice(ctx, B->t64, B->t32, B->d_cls, B->d_z + st.z_off, st.z_n, nb, B->digits,
+                                  B->scales64)) != EMU_OK)
       return s;
+    if (st.u_n > 0) {
+      ProfScope ps(ctx, PROF_UPDATE64, st.u_flops, 0.0, 36.0 * st.u_flops);
+      if ((s = gemm64::launch(ctx, B->map64a, B->map64b, B->d_items64 + st.u_off, st.u_n, nb, B->scales64, B->t64,
+                              nb, ctx->sm_count)) != EMU_OK)
+        return s;
+    }
     if (st.it_n > 0) {
       ProfScope ps(ctx, PROF_TC_FACTOR, st.tc_flops, 0.0, st.tc_mma);
       if ((s = gemm_tc::launch(ctx, B->ops_f, B->d_items + st.it_off, st.it_n, B->d_segs, nb / gemm_tc::BK,

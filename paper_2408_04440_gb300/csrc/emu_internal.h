@@ -209,8 +209,6 @@ emu_status launch_split_tiles64(emu_ctx *ctx, const double *t64, uint16_t *op, c
                                 int lower_only);
 emu_status launch_quant_e4m3(emu_ctx *ctx, const uint16_t *op, uint8_t *op8, float *scales, const int *d_tiles, int n,
                              int nb);
-emu_status launch_update64_jobs(emu_ctx *ctx, double *t64, const float *t32, const unsigned char *cls, int nb,
-                                const int4 *d_jobs, int njobs);
 emu_status launch_split_z(emu_ctx *ctx, const double *Z, long ldz, long npad, int s, int s_pad, uint16_t *zp);
 size_t potrf_dag_task_count(int nb);
 emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStream_t s);

@@ -283,80 +283,6 @@ static size_t trsm32_smem(int nb, int rows) {
   return (size_t)(rows * (nb + TS_LD_PAD) + 32 * (TS_STRIP + 1)) * sizeof(float);
 }
 
-// FP64-class trailing tiles: C_ij -= L_ik L_jk^T in FP64; each operand comes
-// from the FP64 master or (widened) from the FP32 master, by its class.
-// One CTA of 256 threads per (BMT x BMT output block, listed pair): 4x4
-// outputs per thread for BMT = 64, 2x2 for BMT = 32.  The FP64 pipe (about 2
-// FMA per clock per SM) is the bound, so a launch wants at least one CTA per
-// SM: a single tile (the critical-path SYRK) takes the 32 x 32 blocks.
-constexpr int GM = 64, GK = 16;
-template <int BMT>
-__global__ void __launch_bounds__(256)
-    k_update64_list(double *__restrict__ t64, const float *__restrict__ t32,
-                    const unsigned char *__restrict__ cls, int nb, int NT, int k, const int2 *__restrict__ pairs,
-                    const int *st, const int4 *__restrict__ jobs = nullptr) {
-  constexpr int R = BMT / 16;  // outputs per thread along each dimension
-  if (failed(st)) return;
-  // tiles C = (i, j), A = (i, k), B = (j, k) of one matrix, or (batched) the
-  // explicit tile indices {C, A, B, C is diagonal}
-  long tij, tik, tjk;
-  bool diag;
-  if (jobs) {
-    int4 jb = jobs[blockIdx.x];
-    tij = jb.x;
-    tik = jb.y;
-    tjk = jb.z;
-    diag = jb.w != 0;
-  } else {
-    int2 pr = pairs[blockIdx.x];
-    tij = tile_index(pr.x, pr.y, NT);
-    tik = tile_index(pr.x, k, NT);
-    tjk = tile_index(pr.y, k, NT);
-    diag = pr.x == pr.y;
-  }
-  int nsub = nb / BMT;
-  int bi = blockIdx.y % nsub, bj = blockIdx.y / nsub;
-  if (diag && bi < bj) return;
-  bool i64 = cls[tik] == EMU_CLASS_FP64, j64 = cls[tjk] == EMU_CLASS_FP64;
-  size_t oi = (size_t)tik * nb * nb + bi * BMT, oj = (size_t)tjk * nb * nb + bj * BMT;
-  double *C = t64 + (size_t)tij * nb * nb + bi * BMT + (size_t)bj * BMT * nb;
-  __shared__ double as[GK][BMT];
-  __shared__ double bs[GK][BMT];
-  int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  // loader: GK x BMT elements per operand, R per thread, consecutive rows
-  int lc = t / (BMT / R), lr = (t % (BMT / R)) * R;
-  double acc[R][R] = {};
-  for (int p0 = 0; p0 < nb; p0 += GK) {
-#pragma unroll
-    for (int e = 0; e < R; e++) {
-      size_t o = (lr + e) + (size_t)(p0 + lc) * nb;
-      if (lc < GK) {
-        as[lc][lr + e] = i64 ? t64[oi + o] : (double)t32[oi + o];
-        bs[lc][lr + e] = j64 ? t64[oj + o] : (double)t32[oj + o];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < GK; p++) {
-      double av[R], bv[R];
-#pragma unroll
-      for (int e = 0; e < R; e++) {
-        av[e] = as[p][ty + 16 * e];
-        bv[e] = bs[p][tx + 16 * e];
-      }
-#pragma unroll
-      for (int x = 0; x < R; x++)
-#pragma unroll
-        for (int y = 0; y < R; y++) acc[x][y] += av[x] * bv[y];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int x = 0; x < R; x++)
-#pragma unroll
-    for (int y = 0; y < R; y++) C[(ty + 16 * x) + (size_t)(tx + 16 * y) * nb] -= acc[x][y];
-}
-
 // z pieces for the sampler: zp[q][n][k] = piece q of Z[k][n], n < s_pad
 // (zero beyond s).
 __global__ void k_split_z(const double *__restrict__ Z, long ldz, long npad, int s, int s_pad,
@@ -1130,21 +1056,6 @@ emu_status launch_quant_e4m3(emu_ctx *ctx, const uint16_t *op, uint8_t *op8, flo
   if (n <= 0) return EMU_OK;
   ProfScope ps(ctx, PROF_SPLIT, 0.0, 3.0 * n * (double)nb * nb);
   k_quant_e4m3<<<n, 1024, 0, ctx->stream>>>(op, op8, scales, d_tiles, nb, ctx->d_status);
-  EMU_LAUNCHED(ctx);
-  return EMU_OK;
-}
-
-emu_status launch_update64_jobs(emu_ctx *ctx, double *t64, const float *t32, const unsigned char *cls, int nb,
-                                const int4 *d_jobs, int njobs) {
-  if (njobs <= 0) return EMU_OK;
-  double nb3 = (double)nb * nb * nb;
-  ProfScope ps(ctx, PROF_UPDATE64, 2.0 * njobs * nb3, 24.0 * njobs * (double)nb * nb);
-  if ((long)njobs * (nb / GM) * (nb / GM) >= 2L * ctx->sm_count)
-    k_update64_list<GM><<<dim3(njobs, (nb / GM) * (nb / GM)), 256, 0, ctx->stream>>>(
-        t64, t32, cls, nb, 0, 0, nullptr, ctx->d_status, d_jobs);
-  else
-    k_update64_list<32><<<dim3(njobs, (nb / 32) * (nb / 32)), 256, 0, ctx->stream>>>(
-        t64, t32, cls, nb, 0, 0, nullptr, ctx->d_status, d_jobs);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
