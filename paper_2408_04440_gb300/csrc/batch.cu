@@ -94,7 +94,7 @@ struct BatchState {
   bool any_low = false, any_e4m3 = false;
   int ntasks = 0, max_active = 0;
   int graph_launches = 0;
-  long n_trmm = 0, n_items_sample = 0;
+  long n_items_sample = 0;
   double sample_flops = 0.0, sample_mma = 0.0;
   std::vector<std::vector<double>> upd_flops;  // per matrix, per class
   // device arenas
@@ -117,15 +117,19 @@ struct BatchState {
   int2 *d_t64 = nullptr, *d_t32 = nullptr;
   int *d_s64 = nullptr, *d_q = nullptr;
   int4 *d_pairs = nullptr;
-  gemm64::Item *d_items64 = nullptr;
-  int2 *d_z = nullptr;
-  int nslots = 0;
-  uint16_t *digits = nullptr;
-  double *scales64 = nullptr;
-  CUtensorMap map64a, map64b;
+  gemm64::Item *d_items64 = nullptr, *d_items64s = nullptr;
+  gemm64::Seg *d_segs64 = nullptr, *d_segs64s = nullptr;
+  int4 *d_z = nullptr, *d_zs = nullptr;  // slice jobs: factor panel tiles / the sampler's FP64 tiles
+  int2 *d_zblk = nullptr;                 // per matrix: {first row, rows} of Z
+  int nslots = 0, nslots_s = 0, nzs = 0;
+  long n_items64s = 0;
+  double samp64_flops = 0.0;
+  uint16_t *digits = nullptr;  // factor digits, then (after the factor) the sampler's L and Z digits
+  int *exp64 = nullptr, *exp_s = nullptr, *exp_z = nullptr;
+  size_t dig_s_off = 0;        // where the sampler's Z digits start in `digits` (elements)
+  CUtensorMap map64a, map64b, map_sa, map_sz;
   gemm_tc::Item *d_items = nullptr, *d_items_s = nullptr;
   gemm_tc::Seg *d_segs = nullptr, *d_segs_s = nullptr;
-  TrmmJob *d_trmm = nullptr;
   long n_all_diag = 0, n_pairs = 0;
   gemm_tc::Operands ops_f, ops_s;
   cudaGraphExec_t graph = nullptr;
@@ -133,8 +137,8 @@ struct BatchState {
   void release() {
     void *ps[] = {t64, partial, tnorm, frob, tables, t32, slots, scale8, op, zp, op8, d_cls, d_inst, d_tile_inst,
                   Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_all_diag, d_all_diag_int, d_t64,
-                  d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_trmm, d_items64, d_z,
-                  digits, scales64};
+                  d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_items64,
+                  d_items64s, d_segs64, d_segs64s, d_z, d_zs, d_zblk, digits, exp64, exp_s, exp_z};
     for (void *p : ps)
       if (p) cudaFree(p);
     if (graph) cudaGraphExecDestroy(graph);
@@ -234,7 +238,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   std::vector<int2> j64, j32;
   std::vector<int> s64, q;
   std::vector<gemm64::Item> items64;
-  std::vector<int2> zjobs;
+  std::vector<gemm64::Seg> segs64;
+  std::vector<int4> zjobs;
   std::vector<int> slot_of_tile(B->ntiles, -1);
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
@@ -301,19 +306,25 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
             for (long t : {gik, gjk})
               if (slot_of_tile[t] < 0) {
                 slot_of_tile[t] = B->nslots++;
-                zjobs.push_back(make_int2((int)t, slot_of_tile[t]));
+                zjobs.push_back(make_int4((int)t, slot_of_tile[t], slot_of_tile[t] * nb, 0));
               }
             int si = slot_of_tile[gik], sj = slot_of_tile[gjk];
             for (int nbk = 0; nbk < nb / gemm64::BN; nbk++)
               for (int mb = 0; mb < nb / gemm64::BM; mb++) {
                 if (i == j && mb * gemm64::BM + gemm64::BM - 1 < nbk * gemm64::BN) continue;
+                gemm64::Seg sg;
+                sg.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
+                sg.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
+                sg.a_x = sg.b_x = 0;
                 gemm64::Item it;
                 it.out_off = gij * (long)te + mb * gemm64::BM + (long)nbk * gemm64::BN * nb;
-                it.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
-                it.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
                 it.a_sc = si * nb + mb * gemm64::BM;
                 it.b_sc = sj * nb + nbk * gemm64::BN;
-                it.pad[0] = it.pad[1] = 0;
+                it.seg_begin = (int)segs64.size();
+                segs64.push_back(sg);
+                it.seg_end = (int)segs64.size();
+                it.rows_valid = gemm64::BM;
+                it.cols_valid = gemm64::BN;
                 items64.push_back(it);
               }
             st.u_flops += 2.0 * nb3;
@@ -365,7 +376,13 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   std::vector<long> all_diag;
   std::vector<int> all_diag_int;
   std::vector<int4> pairs;
-  std::vector<TrmmJob> trmm;
+  std::vector<gemm64::Item> items64s;
+  std::vector<gemm64::Seg> segs64s;
+  std::vector<int4> zs;
+  std::vector<int2> zblk;
+  std::vector<int> slot_s(B->ntiles, -1);
+  B->nslots_s = 0;
+  B->samp64_flops = 0.0;
   std::vector<gemm_tc::Item> items_s;
   std::vector<gemm_tc::Seg> segs_s;
   B->s_pad = ((B->s + gemm_tc::BN - 1) / gemm_tc::BN) * gemm_tc::BN;
@@ -380,15 +397,44 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
       for (int tj = 0; tj < I.NT; tj++)
         for (int ti = 0; ti < I.NT; ti++) pairs.push_back(make_int4(b, ti, tj, 0));
     if (B->s <= 0) continue;
+    // the sampler's FP64-class tiles: digit slots, one exponent per row of the stacked rows
+    zblk.push_back(make_int2((int)I.row_base, I.NT * nb));
+    for (int j = 0; j < I.NT; j++)
+      for (int i = j; i < I.NT; i++) {
+        long t = I.tile_base + tile_index(i, j, I.NT);
+        if (C(t) != EMU_CLASS_FP64) continue;
+        slot_s[t] = B->nslots_s++;
+        zs.push_back(make_int4((int)t, slot_s[t], (int)(I.row_base + (long)i * nb), 0));
+      }
     for (int i = 0; i < I.NT; i++) {
-      TrmmJob jb;
-      jb.tile_base = I.tile_base;
-      jb.row_base = I.row_base;
-      jb.NT = I.NT;
-      jb.n = I.n;
-      jb.i = i;
-      jb.pad = 0;
-      trmm.push_back(jb);
+      for (int nbk = 0; nbk < B->s_pad / gemm64::BN; nbk++)
+        for (int mb = 0; mb < nb / gemm64::BM; mb++) {
+          long row0 = (long)i * nb + mb * gemm64::BM;
+          int cols = std::min(gemm64::BN, B->s - nbk * gemm64::BN);
+          if (row0 >= I.n || cols <= 0) continue;
+          gemm64::Item it;
+          it.seg_begin = (int)segs64s.size();
+          for (int k = 0; k <= i; k++) {
+            int sl = slot_s[I.tile_base + tile_index(i, k, I.NT)];
+            if (sl < 0) continue;
+            gemm64::Seg sg;
+            sg.a_row = sl * gemm64::NS * nb + mb * gemm64::BM;
+            sg.b_row = nbk * gemm64::BN;
+            sg.a_x = 0;
+            sg.b_x = (int)(I.row_base + (long)k * nb);
+            segs64s.push_back(sg);
+            B->samp64_flops += 2.0 * gemm64::BM * gemm64::BN * nb;
+          }
+          it.seg_end = (int)segs64s.size();
+          if (it.seg_end == it.seg_begin) continue;
+          it.out_off = I.row_base + row0 + (long)nbk * gemm64::BN * B->nrows;
+          it.a_sc = (int)(I.row_base + row0);
+          it.b_sc = (int)zblk.size() - 1;  // block index; times s_pad below
+          it.b_sc = it.b_sc * B->s_pad + nbk * gemm64::BN;
+          it.rows_valid = (int)std::min<long>(gemm64::BM, I.n - row0);
+          it.cols_valid = cols;
+          items64s.push_back(it);
+        }
       for (int nbk = 0; nbk < B->s_pad / gemm_tc::BN; nbk++)
         for (int mb = 0; mb < nb / gemm_tc::BM; mb++) {
           long row0 = (long)i * nb + mb * gemm_tc::BM;
@@ -426,7 +472,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   }
   B->n_all_diag = (long)all_diag.size();
   B->n_pairs = (long)pairs.size();
-  B->n_trmm = (long)trmm.size();
+  B->n_items64s = (long)items64s.size();
+  B->nzs = (int)zs.size();
   B->n_items_sample = (long)items_s.size();
   B->diag_lists = longs;
   // device lists
@@ -435,10 +482,12 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
       (s = upload(ctx, &B->d_all_diag_int, all_diag_int)) != EMU_OK || (s = upload(ctx, &B->d_t64, j64)) != EMU_OK ||
       (s = upload(ctx, &B->d_t32, j32)) != EMU_OK || (s = upload(ctx, &B->d_s64, s64)) != EMU_OK ||
       (s = upload(ctx, &B->d_q, q)) != EMU_OK || (s = upload(ctx, &B->d_items64, items64)) != EMU_OK ||
-      (s = upload(ctx, &B->d_z, zjobs)) != EMU_OK ||
+      (s = upload(ctx, &B->d_z, zjobs)) != EMU_OK || (s = upload(ctx, &B->d_segs64, segs64)) != EMU_OK ||
+      (s = upload(ctx, &B->d_items64s, items64s)) != EMU_OK || (s = upload(ctx, &B->d_segs64s, segs64s)) != EMU_OK ||
+      (s = upload(ctx, &B->d_zs, zs)) != EMU_OK || (s = upload(ctx, &B->d_zblk, zblk)) != EMU_OK ||
       (s = upload(ctx, &B->d_pairs, pairs)) != EMU_OK || (s = upload(ctx, &B->d_items, items)) != EMU_OK ||
       (s = upload(ctx, &B->d_segs, segs)) != EMU_OK || (s = upload(ctx, &B->d_items_s, items_s)) != EMU_OK ||
-      (s = upload(ctx, &B->d_segs_s, segs_s)) != EMU_OK || (s = upload(ctx, &B->d_trmm, trmm)) != EMU_OK)
+      (s = upload(ctx, &B->d_segs_s, segs_s)) != EMU_OK)
     return s;
   // remaining arenas
   s = EMU_OK;
@@ -451,9 +500,17 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     B->op8 = dalloc<uint8_t>(B->ntiles * te, &s);
     B->scale8 = dalloc<float>(B->ntiles, &s);
   }
-  if (B->nslots > 0) {
-    B->digits = dalloc<uint16_t>((size_t)B->nslots * gemm64::NS * te, &s);
-    B->scales64 = dalloc<double>((size_t)B->nslots * nb, &s);
+  // one digit arena: the factor's panel digits, reused after the factor for
+  // the sampler's FP64 tiles (first) and Z (from dig_s_off)
+  size_t need_f = (size_t)B->nslots * gemm64::NS * te;
+  size_t need_s = (size_t)B->nslots_s * gemm64::NS * te;
+  B->dig_s_off = need_s;
+  if (B->nslots_s > 0) need_s += (size_t)gemm64::NS * B->s_pad * B->nrows;
+  if (need_f + need_s > 0) B->digits = dalloc<uint16_t>(std::max(need_f, need_s), &s);
+  if (B->nslots > 0) B->exp64 = dalloc<int>((size_t)B->nslots * nb, &s);
+  if (B->nslots_s > 0) {
+    B->exp_s = dalloc<int>(B->nrows, &s);
+    B->exp_z = dalloc<int>((size_t)count * B->s_pad, &s);
   }
   B->ntasks = (int)potrf_dag_task_count(nb);
   B->tasks = dalloc<short4>(B->ntasks, &s);
@@ -493,6 +550,17 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     if ((s = gemm64::make_map(ctx, &B->map64a, B->digits, nb, drows, gemm64::BM)) != EMU_OK) return s;
     if ((s = gemm64::make_map(ctx, &B->map64b, B->digits, nb, drows, gemm64::BN)) != EMU_OK) return s;
   }
+  if (B->nslots_s > 0) {
+    uint64_t arows = (uint64_t)B->nslots_s * gemm64::NS * nb;
+    if (arows >= (1ull << 31)) {
+      ctx->last_error = "batch digit arena too large for 32-bit TMA coordinates";
+      return EMU_EINVAL;
+    }
+    if ((s = gemm64::make_map(ctx, &B->map_sa, B->digits, nb, arows, gemm64::BM)) != EMU_OK) return s;
+    if ((s = gemm64::make_map(ctx, &B->map_sz, B->digits + B->dig_s_off, B->nrows, (uint64_t)gemm64::NS * B->s_pad,
+                              gemm64::BN)) != EMU_OK)
+      return s;
+  }
   B->ops_s = B->ops_f;
   if (B->s > 0 &&
       (s = gemm_tc::make_map_bf16(ctx, &B->ops_s.b16, B->zp, B->nrows, (uint64_t)3 * B->s_pad, gemm_tc::BN)) !=
@@ -530,6 +598,9 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
   const size_t te = (size_t)nb * nb;
   emu_status s;
   if (B->any_low && (s = launch_to_f32_tiles(ctx, B->t64, B->t32, B->d_cls, B->ntiles, te)) != EMU_OK) return s;
+  // exponent arrays start at the floor on every run (atomic max)
+  if (B->exp64) EMU_CUDA_TRY(ctx, cudaMemsetAsync(B->exp64, 0, (size_t)B->nslots * nb * sizeof(int), ctx->stream));
+  if (B->exp_s) EMU_CUDA_TRY(ctx, cudaMemsetAsync(B->exp_s, 0, (size_t)B->nrows * sizeof(int), ctx->stream));
   for (int k = 0; k < B->maxNT; k++) {
     const Step &st = B->steps[k];
     if ((s = launch_tiles_to_f64(ctx, B->t32, B->t64, B->d_diag + st.dl_off, st.dl_n, te)) != EMU_OK) return s;
@@ -544,13 +615,15 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     if ((s = launch_trsm32_jobs(ctx, B->slots, B->t32, B->op, nb, B->d_t32 + st.t32_off, st.t32_n)) != EMU_OK)
       return s;
     if ((s = launch_quant_e4m3(ctx, B->op, B->op8, B->scale8, B->d_q + st.q_off, st.q_n, nb)) != EMU_OK) return s;
-    if ((s = gemm64::launch_slice(ctx, B->t64, B->t32, B->d_cls, B->d_z + st.z_off, st.z_n, nb, B->digits,
-                                  B->scales64)) != EMU_OK)
+    if ((s = gemm64::launch_row_exponents(ctx, B->t64, B->t32, B->d_cls, B->d_z + st.z_off, st.z_n, nb,
+                                          B->exp64)) != EMU_OK ||
+        (s = gemm64::launch_slice(ctx, B->t64, B->t32, B->d_cls, B->d_z + st.z_off, st.z_n, nb, B->exp64,
+                                  B->digits)) != EMU_OK)
       return s;
     if (st.u_n > 0) {
       ProfScope ps(ctx, PROF_UPDATE64, st.u_flops, 0.0, 36.0 * st.u_flops);
-      if ((s = gemm64::launch(ctx, B->map64a, B->map64b, B->d_items64 + st.u_off, st.u_n, nb, B->scales64, B->t64,
-                              nb, ctx->sm_count)) != EMU_OK)
+      if ((s = gemm64::launch(ctx, B->map64a, B->map64b, B->d_items64 + st.u_off, st.u_n, B->d_segs64, nb, nb, nb,
+                              B->exp64, B->exp64, gemm64::TC64_SUB, B->t64, nb, ctx->sm_count)) != EMU_OK)
         return s;
     }
     if (st.it_n > 0) {
@@ -570,17 +643,23 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     if ((s = launch_normals_batch(ctx, B->d_seed, B->d_inst, B->count, B->maxNT, nb, B->s, B->Z, B->nrows)) !=
         EMU_OK)
       return s;
-    // FP64-class tiles on the FP64 pipe; this also writes every row of Y
-    double f64 = 0.0;
-    for (int b = 0; b < B->count; b++) {
-      const BatchInst &I = B->inst[b];
-      for (int j = 0; j < I.NT; j++)
-        for (int i = j; i < I.NT; i++)
-          if (B->cls[I.tile_base + tile_index(i, j, I.NT)] == EMU_CLASS_FP64) f64 += 2.0 * te * B->s;
+    // Y = 0; FP64-class tiles as digit products (FP64 accurate) on the tensor cores
+    EMU_CUDA_TRY(ctx, cudaMemsetAsync(B->Y, 0, (size_t)B->nrows * B->s * sizeof(double), ctx->stream));
+    if (B->n_items64s > 0) {
+      uint16_t *dz = B->digits + B->dig_s_off;
+      if ((s = gemm64::launch_row_exponents(ctx, B->t64, B->t32, B->d_cls, B->d_zs, B->nzs, nb, B->exp_s)) !=
+              EMU_OK ||
+          (s = gemm64::launch_slice(ctx, B->t64, B->t32, B->d_cls, B->d_zs, B->nzs, nb, B->exp_s, B->digits)) !=
+              EMU_OK ||
+          (s = gemm64::launch_slice_z(ctx, B->Z, B->nrows, B->s, B->s_pad, B->d_zblk, B->count, B->nrows, B->exp_z,
+                                      dz)) != EMU_OK)
+        return s;
+      ProfScope ps(ctx, PROF_TRMM64, B->samp64_flops, 0.0, 36.0 * B->samp64_flops);
+      if ((s = gemm64::launch(ctx, B->map_sa, B->map_sz, B->d_items64s, (int)B->n_items64s, B->d_segs64s, nb, nb,
+                              B->s_pad, B->exp_s, B->exp_z, gemm64::TC64_ADD, B->Y, (int)B->nrows, ctx->sm_count)) !=
+          EMU_OK)
+        return s;
     }
-    if ((s = launch_trmm64_jobs(ctx, B->t64, nb, B->d_cls, B->d_trmm, (int)B->n_trmm, B->Z, B->nrows, B->s, B->Y,
-                                B->nrows, f64)) != EMU_OK)
-      return s;
     if (B->n_items_sample > 0) {
       if ((s = launch_split_z(ctx, B->Z, B->nrows, B->nrows, B->s, B->s_pad, B->zp)) != EMU_OK) return s;
       ProfScope ps(ctx, PROF_TC_SAMPLE, B->sample_flops, 0.0, B->sample_mma);

@@ -152,12 +152,6 @@ struct BatchInst {
   double beta, sigma_exp, nugget_rel;
 };
 
-// Block row i of one matrix of a batch for the FP64 TRMM (fp64.cu).
-struct TrmmJob {
-  long tile_base, row_base;
-  int NT, n, i, pad;
-};
-
 // Kernel launch wrappers (defined in the .cu files that own the kernels).
 // cov.cu
 emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
@@ -195,9 +189,6 @@ emu_status launch_export_batch(emu_ctx *ctx, const BatchInst *d_inst, const int4
 emu_status launch_normals_batch(emu_ctx *ctx, const uint64_t *d_seed, const BatchInst *d_inst, int count,
                                 int maxNT, int nb, int s, double *Z, long ldz);
 emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs);
-emu_status launch_trmm64_jobs(emu_ctx *ctx, const double *t64, int nb, const unsigned char *cls,
-                              const TrmmJob *d_jobs, int njobs, const double *Z, long ldz, int s, double *Y,
-                              long ldy, double flops);
 emu_status launch_to_f32_tiles(emu_ctx *ctx, const double *t64, float *t32, const unsigned char *cls, long ntiles,
                                size_t te);
 emu_status launch_tiles_to_f64(emu_ctx *ctx, const float *t32, double *t64, const long *d_tiles, int n, size_t te);

@@ -439,22 +439,10 @@ __global__ void k_tril_diag(double *__restrict__ t64, int nb, int NT) {
 __global__ void __launch_bounds__(256)
     k_trmm64(const double *__restrict__ t64, int n, int nb, int NT,
              const double *__restrict__ Z, long ldz, int s, double *__restrict__ Y,
-             long ldy, const unsigned char *__restrict__ cls, const TrmmJob *__restrict__ jobs) {
+             long ldy, const unsigned char *__restrict__ cls) {
   int nsub = nb / GM;
   int i = blockIdx.x / nsub, bi = blockIdx.x % nsub;
   int c0 = blockIdx.y * GM;
-  if (jobs) {
-    // batched: block row i of one matrix of the batch, whose tiles start at
-    // tile_base and whose rows start at row_base of Z and Y
-    TrmmJob jb = jobs[blockIdx.x / nsub];
-    i = jb.i;
-    NT = jb.NT;
-    n = jb.n;
-    t64 += (size_t)jb.tile_base * nb * nb;
-    cls += jb.tile_base;
-    Z += jb.row_base;
-    Y += jb.row_base;
-  }
   __shared__ double as[GK][GM];
   __shared__ double bs[GK][GM];
   int t = threadIdx.x, tx = t % 16, ty = t / 16;
@@ -640,17 +628,6 @@ emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_j
   return EMU_OK;
 }
 
-emu_status launch_trmm64_jobs(emu_ctx *ctx, const double *t64, int nb, const unsigned char *cls,
-                              const TrmmJob *d_jobs, int njobs, const double *Z, long ldz, int s, double *Y,
-                              long ldy, double flops) {
-  if (njobs <= 0 || s <= 0) return EMU_OK;
-  dim3 grid(njobs * (nb / GM), (s + GM - 1) / GM);
-  ProfScope ps(ctx, PROF_TRMM64, flops, 0.0);
-  k_trmm64<<<grid, 256, 0, ctx->stream>>>(t64, 0, nb, 0, Z, ldz, s, Y, ldy, cls, d_jobs);
-  EMU_LAUNCHED(ctx);
-  return EMU_OK;
-}
-
 size_t potrf_dag_task_count(int nb) {
   std::vector<short4> tasks;
   dag_tasks(nb / PB, tasks);
@@ -718,7 +695,7 @@ emu_status launch_trmm64(emu_ctx *ctx, const emu_mat *L, const double *Z, long l
                          int s, double *Y, long ldy, const unsigned char *cls) {
   dim3 grid(L->nt * (L->nb / GM), (s + GM - 1) / GM);
   ProfScope ps(ctx, PROF_TRMM64, (double)L->n * L->n * s, 8.0 * tile_count(L->nt) * L->nb * L->nb);
-  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls, nullptr);
+  k_trmm64<<<grid, 256, 0, ctx->stream>>>(L->t64, L->n, L->nb, L->nt, Z, ldz, s, Y, ldy, cls);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -58,14 +58,34 @@ __device__ inline void raise_timeout(Shared *sh, int *status) {
 }
 
 // ------------------------------------------------------------- digits
-// 2^e_r per row r of each listed tile, with max_c |x_rc| < 2^e_r (1 for a
-// zero row).  One CTA per (32 rows, tile): lane = row, warps stride columns.
+// 2^e for integer e in the normal range (exact).
+__device__ inline double exp2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ inline int exp_of(const int *exps, long i) { return max(exps[i] - kExpBias, kExpMin); }
+
+// The NS digits of v (|v| < 1) written d[0], d[plane], ...: v is rounded to
+// X = v 2^56 (an integer below 2^56; the unit of the last digit is 2^-56),
+// then the digits are peeled off from the top in integer arithmetic, each
+// rounded to nearest, so |digit 0| <= 128 and |digit p| <= 64 for p >= 1 and
+// sum_p digit_p 2^(7 (NS - 1 - p)) = X exactly.
+__device__ inline void write_digits(double v, uint16_t *d, size_t plane) {
+  long long X = __double2ll_rn(v * 0x1p56);
+#pragma unroll
+  for (int p = 0; p < NS; p++) {
+    const int sh = SLICE_BITS * (NS - 1 - p);
+    long long dg = (sh > 0) ? ((X + (1LL << (sh > 0 ? sh - 1 : 0))) >> sh) : X;
+    X -= dg << sh;
+    d[p * plane] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(int)dg));  // small integer: exact
+  }
+}
+
+// Row exponents: one CTA per (32 rows, listed tile): lane = row, warps stride
+// columns; exp[base + r] = max(exp[base + r], e_r) with every |x_rc| < 2^e_r.
 __global__ void __launch_bounds__(256)
-    k_rowscale64(const double *__restrict__ t64, const float *__restrict__ t32, const unsigned char *__restrict__ cls,
-                 const int2 *__restrict__ jobs, int nb, double *__restrict__ scales, const int *st) {
+    k_rowexp64(const double *__restrict__ t64, const float *__restrict__ t32, const unsigned char *__restrict__ cls,
+               const int4 *__restrict__ jobs, int nb, int *__restrict__ exps, const int *st) {
   if (failed(st)) return;
   __shared__ double red[8][33];
-  int2 jb = jobs[blockIdx.y];
+  int4 jb = jobs[blockIdx.y];
   size_t base = (size_t)jb.x * nb * nb;
   bool f64 = cls[jb.x] == EMU_CLASS_FP64;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -80,9 +100,11 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (w == 0) {
     for (int q = 1; q < 8; q++) m = fmax(m, red[q][lane]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |x| < 2^e
-    scales[(size_t)jb.y * nb + r] = ldexp(1.0, e);
+    if (m > 0.0) {
+      int e;
+      frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |x| < 2^e
+      atomicMax(&exps[jb.z + r], e + kExpBias);
+    }
   }
 }
 
@@ -92,11 +114,11 @@ __global__ void __launch_bounds__(256)
 // row (coalesced in the row-major plane).
 __global__ void __launch_bounds__(256)
     k_slice64(const double *__restrict__ t64, const float *__restrict__ t32, const unsigned char *__restrict__ cls,
-              const int2 *__restrict__ jobs, int nb, const double *__restrict__ scales, uint16_t *__restrict__ digits,
+              const int4 *__restrict__ jobs, int nb, const int *__restrict__ exps, uint16_t *__restrict__ digits,
               const int *st) {
   if (failed(st)) return;
   __shared__ double blk[32][33];
-  int2 jb = jobs[blockIdx.y];
+  int4 jb = jobs[blockIdx.y];
   size_t base = (size_t)jb.x * nb * nb;
   bool f64 = cls[jb.x] == EMU_CLASS_FP64;
   int nbb = nb / 32;
@@ -107,27 +129,52 @@ __global__ void __launch_bounds__(256)
     blk[lane][c] = f64 ? t64[o] : (double)t32[o];
   }
   __syncthreads();
-  const double radix = (double)(1 << SLICE_BITS);
+  size_t plane = (size_t)nb * nb;
   for (int q = 0; q < 4; q++) {
     int rr = w + 8 * q;
     int r = r0 + rr;
-    double v = blk[rr][lane] * (1.0 / scales[(size_t)jb.y * nb + r]);  // powers of two: exact, |v| < 1
-    size_t plane = (size_t)nb * nb;
-    uint16_t *d = digits + (size_t)jb.y * NS * plane + (size_t)r * nb + c0 + lane;
-#pragma unroll
-    for (int p = 0; p < NS; p++) {
-      v *= radix;                 // exact
-      double s = rint(v);         // digit p, |s| <= 2^SLICE_BITS
-      v -= s;                     // exact, |v| <= 1/2
-      d[p * plane] = __bfloat16_as_ushort(__double2bfloat16(s));  // small integer: exact
-    }
+    double v = blk[rr][lane] * exp2i(-exp_of(exps, (long)jb.z + r));  // exact: |v| < 1
+    write_digits(v, digits + (size_t)jb.y * NS * plane + (size_t)r * nb + c0 + lane, plane);
   }
 }
 
+// Digits of Z columns per matrix block: one CTA per (sample c < s_pad, block).
+// The exponent covers the block's rows of column c; samples c >= s are zero.
+__global__ void __launch_bounds__(256)
+    k_slicez64(const double *__restrict__ Z, long ldz, int s, int s_pad, const int2 *__restrict__ blocks, long zcols,
+               int *__restrict__ exps, uint16_t *__restrict__ digits, const int *st) {
+  if (failed(st)) return;
+  __shared__ double red[8];
+  __shared__ int s_e;
+  int c = blockIdx.x, b = blockIdx.y;
+  int2 blk = blocks[b];
+  const double *z = Z + blk.x + (size_t)c * ldz;
+  double m = 0.0;
+  if (c < s)
+    for (int r = threadIdx.x; r < blk.y; r += blockDim.x) m = fmax(m, fabs(z[r]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); q++) m = fmax(m, red[q]);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    s_e = e;
+    exps[(long)b * s_pad + c] = e + kExpBias;
+  }
+  __syncthreads();
+  const double inv = exp2i(-s_e);
+  size_t plane = (size_t)s_pad * zcols;
+  for (int r = threadIdx.x; r < blk.y; r += blockDim.x)
+    write_digits((c < s) ? z[r] * inv : 0.0, digits + (size_t)c * zcols + blk.x + r, plane);
+}
+
 // ------------------------------------------------------------- GEMM
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm64(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                const Item *__restrict__ items, int nitems, int nb, const double *__restrict__ scales,
+                const Item *__restrict__ items, int nitems, const Seg *__restrict__ segs, int nb, int a_plane,
+                int b_plane, const int *__restrict__ a_exp, const int *__restrict__ b_exp,
                 double *__restrict__ out, int ldo, int *status) {
   extern __shared__ uint8_t smem_raw[];
   uint32_t raw_addr = tc::smem_u32(smem_raw);
@@ -136,7 +183,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   Shared *sh = reinterpret_cast<Shared *>(ring + RING_BYTES);
   const uint32_t ring_addr = raw_addr + pad;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kstages = nb / BK;
+  const int kstages = nb / BK;  // stages per segment
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -170,21 +217,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = *abort == 0;
       for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         Item item = items[it];
-        for (int kc = 0; kc < kstages; kc++) {
-          if (!tc::mbar_wait(&sh->empty[stage], phase ^ 1u, abort)) {
-            raise_timeout(sh, status);
-            ok = false;
-            break;
-          }
-          tc::mbar_arrive_expect_tx(&sh->full[stage], (uint32_t)STAGE_BYTES);
-          uint8_t *st = ring + stage * STAGE_BYTES;
-          for (int p = 0; p < NS; p++)
-            tc::tma_load_2d(st + p * A_SL, &amap, &sh->full[stage], kc * BK, item.a_row + p * nb);
-          for (int q = 0; q < NS; q++)
-            tc::tma_load_2d(st + NS * A_SL + q * B_SL, &bmap, &sh->full[stage], kc * BK, item.b_row + q * nb);
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
+        for (int sg = item.seg_begin; sg < item.seg_end && ok; sg++) {
+          Seg sd = segs[sg];
+          for (int kc = 0; kc < kstages; kc++) {
+            if (!tc::mbar_wait(&sh->empty[stage], phase ^ 1u, abort)) {
+              raise_timeout(sh, status);
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&sh->full[stage], (uint32_t)STAGE_BYTES);
+            uint8_t *st = ring + stage * STAGE_BYTES;
+            for (int p = 0; p < NS; p++)
+              tc::tma_load_2d(st + p * A_SL, &amap, &sh->full[stage], sd.a_x + kc * BK, sd.a_row + p * a_plane);
+            for (int q = 0; q < NS; q++)
+              tc::tma_load_2d(st + NS * A_SL + q * B_SL, &bmap, &sh->full[stage], sd.b_x + kc * BK,
+                              sd.b_row + q * b_plane);
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -203,8 +254,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t started = 0;
       bool ok = *abort == 0;
       for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
-        for (int kc = 0; kc < kstages && ok; kc++) {
-          if (kc % CHUNK_STAGES == 0) {
+        Item item = items[it];
+        const int total = (item.seg_end - item.seg_begin) * kstages;  // K stages of the item
+        for (int ks_i = 0; ks_i < total && ok; ks_i++) {
+          if (ks_i % CHUNK_STAGES == 0) {
             // the epilogue has read the previous chunk's accumulators
             if (!tc::mbar_wait(&sh->tempty, (chunk & 1u) ^ 1u, abort)) {
               raise_timeout(sh, status);
@@ -240,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             stage = 0;
             phase ^= 1u;
           }
-          if (kc % CHUNK_STAGES == CHUNK_STAGES - 1 || kc == kstages - 1) {
+          if (ks_i % CHUNK_STAGES == CHUNK_STAGES - 1 || ks_i == total - 1) {
             tc::mma_commit(&sh->tfull);
             chunk++;
           }
@@ -254,10 +307,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int quarter = warp & 3;  // TMEM lanes this warp may access
     const int row = quarter * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int nchunks = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;
     uint32_t chunk = 0;
     bool ok = *abort == 0;
     for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      Item item = items[it];
+      const int total = (item.seg_end - item.seg_begin) * kstages;
+      const int nchunks = (total + CHUNK_STAGES - 1) / CHUNK_STAGES;
       double acc[BN];
 #pragma unroll
       for (int x = 0; x < BN; x++) acc[x] = 0.0;
@@ -285,17 +340,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         chunk++;
       }
       if (!ok) break;
-      Item item = items[it];
-      const double sa = scales[item.a_sc + row];
+      // scales 2^(e_row + e_col), exact; then the output block
+      const int ea = exp_of(a_exp, (long)item.a_sc + row);
       double *o = out + item.out_off + row;
+      // in groups of 8 columns: 8 loads in flight, then 8 stores
+      if (MODE == TC64_SUB || row < item.rows_valid) {
 #pragma unroll
-      for (int h = 0; h < BN / 32; h++) {
-        double cv[32];
+        for (int x0 = 0; x0 < BN; x0 += 8) {
+          double cv[8];
 #pragma unroll
-        for (int x = 0; x < 32; x++) cv[x] = __ldcg(o + (long)(h * 32 + x) * ldo);
+          for (int x = 0; x < 8; x++)
+            cv[x] = (MODE == TC64_SUB || x0 + x < item.cols_valid) ? __ldcg(o + (long)(x0 + x) * ldo) : 0.0;
 #pragma unroll
-        for (int x = 0; x < 32; x++)
-          __stcg(o + (long)(h * 32 + x) * ldo, cv[x] - acc[h * 32 + x] * (sa * scales[item.b_sc + h * 32 + x]));
+          for (int x = 0; x < 8; x++) {
+            double v = acc[x0 + x] * exp2i(ea + exp_of(b_exp, (long)item.b_sc + x0 + x));
+            if (MODE == TC64_SUB)
+              __stcg(o + (long)(x0 + x) * ldo, cv[x] - v);
+            else if (x0 + x < item.cols_valid)
+              __stcg(o + (long)(x0 + x) * ldo, cv[x] + v);
+          }
+        }
       }
     }
   }
@@ -315,30 +379,57 @@ emu_status make_map(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t i
   return gemm_tc::make_map_bf16(ctx, map, base, inner, rows, box_rows);
 }
 
+emu_status launch_row_exponents(emu_ctx *ctx, const double *t64, const float *t32, const unsigned char *cls,
+                                const int4 *d_jobs, int njobs, int nb, int *exps) {
+  if (njobs <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 8.0 * njobs * (double)nb * nb);
+  k_rowexp64<<<dim3(nb / 32, njobs), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, exps, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
 emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const unsigned char *cls,
-                        const int2 *d_jobs, int njobs, int nb, uint16_t *digits, double *scales) {
+                        const int4 *d_jobs, int njobs, int nb, const int *exps, uint16_t *digits) {
   if (njobs <= 0) return EMU_OK;
   ProfScope ps(ctx, PROF_SPLIT, 0.0, (8.0 + 2.0 * NS) * njobs * (double)nb * nb);
-  k_rowscale64<<<dim3(nb / 32, njobs), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, scales, ctx->d_status);
-  EMU_LAUNCHED(ctx);
-  k_slice64<<<dim3((nb / 32) * (nb / 32), njobs), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, scales, digits,
+  k_slice64<<<dim3((nb / 32) * (nb / 32), njobs), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, exps, digits,
                                                                          ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
 
-emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems, int nb,
-                  const double *scales, double *out64, int ldo, int max_ctas) {
+emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_pad, const int2 *d_blocks,
+                          int nblocks, long zcols, int *exps, uint16_t *digits) {
+  if (nblocks <= 0 || s_pad <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, (8.0 + 2.0 * NS) * (double)s_pad * zcols);
+  k_slicez64<<<dim3(s_pad, nblocks), 256, 0, ctx->stream>>>(Z, ldz, s, s_pad, d_blocks, zcols, exps, digits,
+                                                            ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems,
+                  const Seg *d_segs, int nb, int a_plane, int b_plane, const int *a_exp, const int *b_exp, int mode,
+                  double *out64, int ldo, int max_ctas) {
   if (nitems <= 0) return EMU_OK;
   if (nb % BK != 0) return EMU_EINVAL;
   static bool attr_done = false;
   if (!attr_done) {
-    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm64, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm64<TC64_SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_BYTES));
+    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm64<TC64_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_BYTES));
     attr_done = true;
   }
   int grid = nitems < max_ctas ? nitems : max_ctas;
-  k_tc_gemm64<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(a, b, d_items, nitems, nb, scales, out64, ldo,
-                                                           ctx->d_status);
+  if (mode == TC64_SUB)
+    k_tc_gemm64<TC64_SUB><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(a, b, d_items, nitems, d_segs, nb, a_plane,
+                                                                       b_plane, a_exp, b_exp, out64, ldo,
+                                                                       ctx->d_status);
+  else
+    k_tc_gemm64<TC64_ADD><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(a, b, d_items, nitems, d_segs, nb, a_plane,
+                                                                       b_plane, a_exp, b_exp, out64, ldo,
+                                                                       ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -29,30 +29,53 @@ constexpr int NS = 8;          // digits per operand entry
 constexpr int SLICE_BITS = 7;
 constexpr int KCHUNK = 256;    // K accumulated exactly in FP32 between FP64 flushes
 
-// One BM x BN output block.  The digit arena holds, per slot, NS digit
-// planes of nb x nb (row-major: row r, K index c), plane p of slot s at rows
-// (s * NS + p) * nb; `scales` holds 2^e_r for each row of each slot.
-struct Item {
-  long out_off;  // element offset of the block in the FP64 output
-  int a_row;     // arena row of digit plane 0 of the A block (its first row)
-  int b_row;     // same for the B block
-  int a_sc;      // index in `scales` of the A block's first row
-  int b_sc;      // same for the B block
-  int pad[2];
+// One BM x BN output block: the sum over its segments of A_seg B_seg^T.
+// Operand row r of digit plane p sits at arena row (row + p * plane); every
+// entry of a row carries the scale 2^e of that row, read from an exponent
+// array (A: a_exp[a_sc + r], B: b_exp[b_sc + c]), so all segments of an item
+// share one scale per row and their digit products add exactly.
+struct Seg {
+  int a_row, b_row;  // arena rows of digit plane 0 of the A and B blocks
+  int a_x, b_x;      // K offset of the segment in each arena
 };
+struct Item {
+  long out_off;                // element offset of the block in the FP64 output
+  int a_sc, b_sc;              // exponent indices of the block's first A row / B row
+  int seg_begin, seg_end;      // segments [seg_begin, seg_end)
+  int rows_valid, cols_valid;  // rows / columns of the block that exist (TC64_ADD)
+};
+enum { TC64_SUB = 0, TC64_ADD = 1 };  // out -= A B^T (factor) / out += A B^T (samples, bounded)
 
-// 2-D BF16 tensor map over the digit arena (inner = nb), box rows x 32.
+// 2-D BF16 tensor map over a digit arena of `inner` columns, box rows x 32.
 emu_status make_map(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows,
                     uint32_t box_rows);
 
-// Digits and row scales of the listed tiles: jobs {tile, slot}; a tile is read
-// from the FP64 arena when its class is FP64, else from the FP32 master.
-emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const unsigned char *cls,
-                        const int2 *d_jobs, int njobs, int nb, uint16_t *digits, double *scales);
+// Exponent arrays hold e + kExpBias, so that a zeroed array (cudaMemset 0)
+// holds the lowest exponent; readers clamp e at kExpMin, which only rows of
+// zeros reach.
+constexpr int kExpBias = 1024;
+constexpr int kExpMin = -960;
 
-// out64[item block] -= A B^T for every item (K = nb, ldo = leading dimension
-// of the output), on at most max_ctas persistent CTAs.
-emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems, int nb,
-                  const double *scales, double *out64, int ldo, int max_ctas);
+// Row exponents of listed tiles: jobs {tile, -, exponent base}; a tile is read
+// from the FP64 arena when its class is FP64, else from the FP32 master.  Row
+// r gets exp[base + r] = max(exp[base + r], e) with max_c |x_rc| < 2^e, so
+// tiles that share rows share the largest exponent.
+emu_status launch_row_exponents(emu_ctx *ctx, const double *t64, const float *t32, const unsigned char *cls,
+                                const int4 *d_jobs, int njobs, int nb, int *exps);
+// Digit planes of listed tiles: jobs {tile, slot, exponent base}; plane p of
+// slot s at rows (s * NS + p) * nb of a digit arena with nb columns.
+emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const unsigned char *cls,
+                        const int4 *d_jobs, int njobs, int nb, const int *exps, uint16_t *digits);
+// Digits of the columns of Z (samples) for each matrix block of rows
+// [row0, row0 + nrows): plane p, row c (sample), column = row of Z; one
+// exponent per (block, sample): exps[blk * s_pad + c].  blocks = {row0, nrows}.
+emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_pad, const int2 *d_blocks,
+                          int nblocks, long zcols, int *exps, uint16_t *digits);
+
+// out64 (-= or +=) per item, K = nb per segment, on at most max_ctas persistent
+// CTAs; a_plane / b_plane = arena rows between digit planes.
+emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems,
+                  const Seg *d_segs, int nb, int a_plane, int b_plane, const int *a_exp, const int *b_exp, int mode,
+                  double *out64, int ldo, int max_ctas);
 
 }  // namespace gemm64

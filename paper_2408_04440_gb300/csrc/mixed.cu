@@ -396,10 +396,18 @@ struct MixedPlan {
   std::vector<StepPlan> steps;
   int *d_rows64 = nullptr, *d_rows32 = nullptr;
   gemm64::Item *d_items64 = nullptr;  // FP64-class updates on the tensor cores (digit products)
-  int2 *d_zjobs = nullptr;            // {tile, slot} of the panel tiles digit-sliced for them
+  gemm64::Seg *d_segs64 = nullptr;
+  int4 *d_zjobs = nullptr;            // {tile, slot, exponent base} of the panel tiles sliced for them
   int nslots = 0;
   uint16_t *d_digits = nullptr;       // nslots * NS digit planes of nb x nb
-  double *d_scales64 = nullptr;       // nslots * nb row scales
+  int *d_exp64 = nullptr;             // nslots * nb row exponents (biased)
+  // the sampler's FP64-class tiles (sliced on the first draw after the factor)
+  bool samp_ready = false;
+  int nslots_s = 0;
+  uint16_t *d_dig_s = nullptr;
+  int *d_exp_s = nullptr;             // row exponents per row of the padded matrix
+  std::vector<int> slot_s;            // tile -> sampler slot (-1: not FP64 class)
+  CUtensorMap map_s;
   CUtensorMap map64a, map64b;
   gemm_tc::Item *d_items = nullptr;
   gemm_tc::Seg *d_segs = nullptr;
@@ -423,8 +431,8 @@ struct MixedPlan {
 static void plan_free(MixedPlan *p) {
   if (!p) return;
   if (p->d_blob) cudaFreeAsync(p->d_blob, p->stream);
-  if (p->d_digits) cudaFreeAsync(p->d_digits, p->stream);
-  if (p->d_scales64) cudaFreeAsync(p->d_scales64, p->stream);
+  for (void *q : {(void *)p->d_digits, (void *)p->d_exp64, (void *)p->d_dig_s, (void *)p->d_exp_s})
+    if (q) cudaFreeAsync(q, p->stream);
   delete p;
 }
 
@@ -441,7 +449,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   auto C = [&](int i, int j) { return (int)P->cls[tile_index(i, j, NT)]; };
   std::vector<int> rows64, rows32, tiles64, diag, qtiles;
   std::vector<gemm64::Item> items64;
-  std::vector<int2> zjobs, z1_step, zr_step;
+  std::vector<gemm64::Seg> segs64;
+  std::vector<int4> zjobs, z1_step, zr_step;
   std::vector<int> slot_of_tile(A->ntiles, -1);
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
@@ -457,7 +466,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     long t = tile_index(r, k, NT);
     if (slot_of_tile[t] < 0) {
       slot_of_tile[t] = P->nslots++;
-      (r == k + 1 ? z1_step : zr_step).push_back(make_int2((int)t, slot_of_tile[t]));
+      (r == k + 1 ? z1_step : zr_step)
+          .push_back(make_int4((int)t, slot_of_tile[t], slot_of_tile[t] * nb, 0));
     }
     return slot_of_tile[t];
   };
@@ -469,13 +479,19 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
       for (int nbk = 0; nbk < nb / gemm64::BN; nbk++)
         for (int mb = 0; mb < nb / gemm64::BM; mb++) {
           if (i == j && mb * gemm64::BM + gemm64::BM - 1 < nbk * gemm64::BN) continue;  // above the diagonal
+          gemm64::Seg sg;
+          sg.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
+          sg.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
+          sg.a_x = sg.b_x = 0;
           gemm64::Item it;
           it.out_off = tile_index(i, j, NT) * (long)nb * nb + mb * gemm64::BM + (long)nbk * gemm64::BN * nb;
-          it.a_row = si * gemm64::NS * nb + mb * gemm64::BM;
-          it.b_row = sj * gemm64::NS * nb + nbk * gemm64::BN;
           it.a_sc = si * nb + mb * gemm64::BM;
           it.b_sc = sj * nb + nbk * gemm64::BN;
-          it.pad[0] = it.pad[1] = 0;
+          it.seg_begin = (int)segs64.size();
+          segs64.push_back(sg);
+          it.seg_end = (int)segs64.size();
+          it.rows_valid = gemm64::BM;
+          it.cols_valid = gemm64::BN;
           items64.push_back(it);
           sp.p_n[g]++;
         }
@@ -586,7 +602,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   };
   auto vbytes = [](const auto &v) { return v.size() * sizeof(v[0]); };
   size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_i64 = part(vbytes(items64)),
-         o_z = part(vbytes(zjobs)),
+         o_s64 = part(vbytes(segs64)), o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
          o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)),
          o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
@@ -598,6 +614,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   put(o_r64, rows64);
   put(o_r32, rows32);
   put(o_i64, items64);
+  put(o_s64, segs64);
   put(o_z, zjobs);
   put(o_items, items);
   put(o_segs, segs);
@@ -611,7 +628,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_rows64 = reinterpret_cast<int *>(b + o_r64);
   P->d_rows32 = reinterpret_cast<int *>(b + o_r32);
   P->d_items64 = reinterpret_cast<gemm64::Item *>(b + o_i64);
-  P->d_zjobs = reinterpret_cast<int2 *>(b + o_z);
+  P->d_segs64 = reinterpret_cast<gemm64::Seg *>(b + o_s64);
+  P->d_zjobs = reinterpret_cast<int4 *>(b + o_z);
   P->d_items = reinterpret_cast<gemm_tc::Item *>(b + o_items);
   P->d_segs = reinterpret_cast<gemm_tc::Seg *>(b + o_segs);
   P->d_tiles64 = reinterpret_cast<int *>(b + o_t64);
@@ -631,7 +649,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     size_t te = (size_t)nb * nb;
     EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_digits, (size_t)P->nslots * gemm64::NS * te * sizeof(uint16_t),
                                       ctx->stream));
-    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_scales64, (size_t)P->nslots * nb * sizeof(double), ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_exp64, (size_t)P->nslots * nb * sizeof(int), ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMemsetAsync(P->d_exp64, 0, (size_t)P->nslots * nb * sizeof(int), ctx->stream));
     uint64_t drows = (uint64_t)P->nslots * gemm64::NS * nb;
     if ((s = gemm64::make_map(ctx, &P->map64a, P->d_digits, nb, drows, gemm64::BM)) != EMU_OK) return s;
     if ((s = gemm64::make_map(ctx, &P->map64b, P->d_digits, nb, drows, gemm64::BN)) != EMU_OK) return s;
@@ -745,7 +764,9 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     return EMU_OK;
   };
   auto slice64 = [&](int z0, int nz) -> emu_status {
-    return gemm64::launch_slice(ctx, A->t64, A->t32, A->d_cls, P->d_zjobs + z0, nz, nb, P->d_digits, P->d_scales64);
+    emu_status e = gemm64::launch_row_exponents(ctx, A->t64, A->t32, A->d_cls, P->d_zjobs + z0, nz, nb, P->d_exp64);
+    if (e != EMU_OK) return e;
+    return gemm64::launch_slice(ctx, A->t64, A->t32, A->d_cls, P->d_zjobs + z0, nz, nb, P->d_exp64, P->d_digits);
   };
   auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
     emu_status e = EMU_OK;
@@ -775,8 +796,9 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     if (sp.p_n[g] > 0) {
       // FP64-class tiles: 36 digit products per K step on the BF16 tensor cores
       ProfScope ps(ctx, PROF_UPDATE64, sp.p_flops[g], 24.0 * sp.p_flops[g] / (2.0 * nb), 36.0 * sp.p_flops[g]);
-      emu_status e = gemm64::launch(ctx, P->map64a, P->map64b, P->d_items64 + sp.p_off[g], sp.p_n[g], nb,
-                                    P->d_scales64, A->t64, nb, std::max(1, max_ctas));
+      emu_status e = gemm64::launch(ctx, P->map64a, P->map64b, P->d_items64 + sp.p_off[g], sp.p_n[g], P->d_segs64,
+                                    nb, nb, nb, P->d_exp64, P->d_exp64, gemm64::TC64_SUB, A->t64, nb,
+                                    std::max(1, max_ctas));
       if (e != EMU_OK) return e;
     }
     if (sp.i_n[g] > 0) {
@@ -863,14 +885,115 @@ void mixed_fill_info(const emu_mat *A, emu_factor_info *info) {
 // Y = L Z: FP64-class tiles on the FP64 pipe (this also initialises Y), the
 // FP32/BF16-class tiles on the tensor cores accumulated in FP32 per output
 // block over k in a fixed order, then added to Y.
+// Digit slices of the factor's FP64-class tiles for the sampler, with one
+// exponent per row of the matrix (shared by the row's FP64 tiles), made once
+// after the factor.
+static emu_status sampler_slices(emu_ctx *ctx, const emu_mat *L, MixedPlan *P) {
+  if (P->samp_ready) return EMU_OK;
+  int NT = L->nt, nb = L->nb;
+  long npad = (long)NT * nb;
+  P->slot_s.assign(L->ntiles, -1);
+  std::vector<int4> jobs;
+  for (int j = 0; j < NT; j++)
+    for (int i = j; i < NT; i++) {
+      long t = tile_index(i, j, NT);
+      if (P->cls[t] != EMU_CLASS_FP64) continue;
+      P->slot_s[t] = P->nslots_s++;
+      jobs.push_back(make_int4((int)t, P->slot_s[t], i * nb, 0));
+    }
+  P->samp_ready = true;
+  if (jobs.empty()) return EMU_OK;
+  size_t te = (size_t)nb * nb;
+  int4 *d_jobs = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_dig_s, (size_t)P->nslots_s * gemm64::NS * te * sizeof(uint16_t), ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_exp_s, npad * sizeof(int), ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&d_jobs, jobs.size() * sizeof(int4), ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(P->d_exp_s, 0, npad * sizeof(int), ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    ctx->stream));
+  emu_status s = gemm64::launch_row_exponents(ctx, L->t64, L->t32, L->d_cls, d_jobs, (int)jobs.size(), nb, P->d_exp_s);
+  if (s == EMU_OK)
+    s = gemm64::launch_slice(ctx, L->t64, L->t32, L->d_cls, d_jobs, (int)jobs.size(), nb, P->d_exp_s, P->d_dig_s);
+  cudaFreeAsync(d_jobs, ctx->stream);
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the host job list must outlive its copy
+  if (s != EMU_OK) return s;
+  return gemm64::make_map(ctx, &P->map_s, P->d_dig_s, nb, (uint64_t)P->nslots_s * gemm64::NS * nb, gemm64::BM);
+}
+
 emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ldz, int s, double *Y, long ldy) {
-  const MixedPlan *P = static_cast<const MixedPlan *>(L->plan);
+  MixedPlan *P = static_cast<MixedPlan *>(L->plan);
   if (!P) return EMU_ESTATE;
   int NT = L->nt, nb = L->nb;
   long npad = (long)NT * nb;
   int s_pad = ((s + gemm_tc::BN - 1) / gemm_tc::BN) * gemm_tc::BN;
-  emu_status st = launch_trmm64(ctx, L, Z, ldz, s, Y, ldy, L->d_cls);
+  // Y = 0, then the FP64-class tiles (digit products, FP64 accurate) and the
+  // low-precision tiles are added on the tensor cores
+  EMU_CUDA_TRY(ctx, cudaMemset2DAsync(Y, ldy * sizeof(double), 0, (size_t)L->n * sizeof(double), s, ctx->stream));
+  emu_status st = sampler_slices(ctx, L, P);
   if (st != EMU_OK) return st;
+  if (P->nslots_s > 0 && s > 0) {
+    std::vector<gemm64::Item> it64;
+    std::vector<gemm64::Seg> sg64;
+    double f64 = 0.0;
+    for (int i = 0; i < NT; i++)
+      for (int nbk = 0; nbk < s_pad / gemm64::BN; nbk++)
+        for (int mb = 0; mb < nb / gemm64::BM; mb++) {
+          long row0 = (long)i * nb + mb * gemm64::BM;
+          int cols = std::min(gemm64::BN, s - nbk * gemm64::BN);
+          if (row0 >= L->n || cols <= 0) continue;
+          gemm64::Item it;
+          it.seg_begin = (int)sg64.size();
+          for (int k = 0; k <= i; k++) {
+            int sl = P->slot_s[tile_index(i, k, NT)];
+            if (sl < 0) continue;
+            gemm64::Seg sg;
+            sg.a_row = sl * gemm64::NS * nb + mb * gemm64::BM;
+            sg.b_row = nbk * gemm64::BN;
+            sg.a_x = 0;
+            sg.b_x = k * nb;
+            sg64.push_back(sg);
+            f64 += 2.0 * gemm64::BM * gemm64::BN * nb;
+          }
+          it.seg_end = (int)sg64.size();
+          if (it.seg_end == it.seg_begin) continue;
+          it.out_off = row0 + (long)nbk * gemm64::BN * ldy;
+          it.a_sc = (int)row0;
+          it.b_sc = nbk * gemm64::BN;
+          it.rows_valid = (int)std::min<long>(gemm64::BM, L->n - row0);
+          it.cols_valid = cols;
+          it64.push_back(it);
+        }
+    if (!it64.empty()) {
+      uint16_t *zd = nullptr;
+      int *ze = nullptr;
+      int2 *blk = nullptr;
+      gemm64::Item *d_it = nullptr;
+      gemm64::Seg *d_sg = nullptr;
+      int2 hblk = make_int2(0, (int)npad);
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&zd, (size_t)gemm64::NS * s_pad * npad * sizeof(uint16_t), ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&ze, s_pad * sizeof(int) + 16, ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&blk, sizeof(int2), ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&d_it, it64.size() * sizeof(gemm64::Item), ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&d_sg, sg64.size() * sizeof(gemm64::Seg), ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMemcpyAsync(blk, &hblk, sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_it, it64.data(), it64.size() * sizeof(gemm64::Item),
+                                        cudaMemcpyHostToDevice, ctx->stream));
+      EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_sg, sg64.data(), sg64.size() * sizeof(gemm64::Seg), cudaMemcpyHostToDevice,
+                                        ctx->stream));
+      CUtensorMap zmap;
+      st = gemm64::launch_slice_z(ctx, Z, ldz, s, s_pad, blk, 1, npad, ze, zd);
+      if (st == EMU_OK) st = gemm64::make_map(ctx, &zmap, zd, npad, (uint64_t)gemm64::NS * s_pad, gemm64::BN);
+      if (st == EMU_OK) {
+        ProfScope ps(ctx, PROF_TRMM64, f64, 0.0, 36.0 * f64);
+        st = gemm64::launch(ctx, P->map_s, zmap, d_it, (int)it64.size(), d_sg, nb, nb, s_pad, P->d_exp_s, ze,
+                            gemm64::TC64_ADD, Y, (int)ldy, ctx->sm_count);
+      }
+      for (void *q : {(void *)zd, (void *)ze, (void *)blk, (void *)d_it, (void *)d_sg}) cudaFreeAsync(q, ctx->stream);
+      // the host item lists must outlive their copies
+      EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (st != EMU_OK) return st;
+    }
+  }
   std::vector<gemm_tc::Item> items;
   std::vector<gemm_tc::Seg> segs;
   for (int i = 0; i < NT; i++)
