@@ -76,8 +76,12 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
   return acc0 + acc1;
 }
 
+// One tile: at most 64 registers per thread (4 CTAs of 256 threads per SM),
+// because it shares every SM with the persistent bulk GEMM of the mixed
+// factor and a larger register footprint measurably slowed both.  The batch
+// form runs alone.
 template <bool BATCH>
-__global__ void __launch_bounds__(PB * PB)
+__global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     k_potrf_dag(double *__restrict__ D0, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
                 int *__restrict__ ws, double *__restrict__ rinv_all, int *st,
                 unsigned long long *__restrict__ trace, const long *__restrict__ dtiles, int nbat) {
@@ -113,9 +117,10 @@ __global__ void __launch_bounds__(PB * PB)
     if (threadIdx.x == 0) {
       bool ok;
       if (kind == T_LT)
-        ok = (s == 0) || (dag_wait(state, (s - 1) * nbb + (s - 1), s, st) &&
-                          (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
-                          dag_wait(state, s * nbb + (s - 1), s - 2, st));
+        // first the inputs other tasks produce (usually ready long before
+        // LT(s-1) ends): X_{s,s-2}, block (s,s-1) and the diagonal block
+        ok = (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
+             (s < 1 || dag_wait(state, s * nbb + (s - 1), s - 2, st)) && dag_wait(state, s * nbb + s, s - 1, st);
       else if (kind == T_TRSM)
         ok = dag_wait(state, s * nbb + s, s + 1, st) && (s == 0 || dag_wait(state, r * nbb + (s - 1), s, st)) &&
              dag_wait(state, r * nbb + s, s - 1, st);
@@ -145,21 +150,50 @@ __global__ void __launch_bounds__(PB * PB)
       double v = __ldcg(cp);
       __syncthreads();
       __stcg(cp, v - panel_dot(xr, xc, ty, tx));
+    } else if (kind == T_TRSM) {
+      // Solve block (r, s) against L_{s,s} after its fused update by panel
+      // s-1: row ty's 16 lanes exchange entries by shuffle.
+      a[ty][tx] = __ldcg(blk(s, s));
+      if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + s * PB + threadIdx.x);
+      double *bp = blk(r, s);
+      double v = __ldcg(bp);
+      if (s >= 1) {
+        xr[ty][tx] = __ldcg(blk(r, s - 1));
+        xc[ty][tx] = __ldcg(blk(s, s - 1));
+      }
+      __syncthreads();
+      m[ty][tx] = a[ty][tx] * rinv[tx];
+      if (s >= 1) v -= panel_dot(xr, xc, ty, tx);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < PB; j++) {
+        double vj = __shfl_sync(0xffffffffu, v, j, PB);
+        if (tx > j) v = fma(-vj, m[tx][j], v);
+      }
+      __stcg(bp, v * rinv[tx]);
     } else {
-      // Solve a block against L_{q,q} (q = s-1 for LT, s for TRSM) after its
-      // fused update by panel q-1: row ty's 16 lanes exchange entries by shuffle.
-      int q = (kind == T_LT) ? s - 1 : s;  // panel solved against
-      int br = (kind == T_LT) ? s : r;     // block row solved
-      double x = 0.0;
+      // LT(s): the inputs other tasks produce are loaded first; then, once
+      // LT(s-1) has ended, block (s, s-1) gets its fused update by panel s-2,
+      // is solved against L_{s-1,s-1}, is applied to the diagonal block, and
+      // the diagonal block is factored.
+      const int q = s - 1;
+      double *bp = blk(s, q >= 0 ? q : 0);
+      double dg = __ldcg(blk(s, s));
+      double v = 0.0;
+      if (q >= 0) {
+        v = __ldcg(bp);
+        if (q >= 1) xr[ty][tx] = __ldcg(blk(s, q - 1));
+      }
+      if (threadIdx.x == 0) {
+        if (q >= 0) s_ok = dag_wait(state, q * nbb + q, s, st);  // LT(s-1) has ended
+        __threadfence();
+      }
+      __syncthreads();
+      if (!s_ok) return;
       if (q >= 0) {
         a[ty][tx] = __ldcg(blk(q, q));
         if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + q * PB + threadIdx.x);
-        double *bp = blk(br, q);
-        double v = __ldcg(bp);
-        if (q >= 1) {
-          xr[ty][tx] = __ldcg(blk(br, q - 1));
-          xc[ty][tx] = __ldcg(blk(q, q - 1));
-        }
+        if (q >= 1) xc[ty][tx] = __ldcg(blk(q, q - 1));
         __syncthreads();
         m[ty][tx] = a[ty][tx] * rinv[tx];
         if (q >= 1) v -= panel_dot(xr, xc, ty, tx);
@@ -169,25 +203,14 @@ __global__ void __launch_bounds__(PB * PB)
           double vj = __shfl_sync(0xffffffffu, v, j, PB);
           if (tx > j) v = fma(-vj, m[tx][j], v);
         }
-        x = v * rinv[tx];
+        const double x = v * rinv[tx];
         __stcg(bp, x);
-      }
-      if (kind == T_LT) {
-        // apply the freshly solved panel row to the diagonal block, then factor it
-        if (q >= 0) {
-          __syncthreads();
-          xr[ty][tx] = x;
-          if (threadIdx.x == 0) {
-            __threadfence();
-            s_ok = dag_wait(state, s * nbb + s, s - 1, st);
-            __threadfence();
-          }
-        }
+        xr[ty][tx] = x;  // panel_dot above has read xr (the barrier after it)
         __syncthreads();
-        if (!s_ok) return;
-        double v2 = __ldcg(blk(s, s));
-        if (q >= 0) v2 -= panel_dot(xr, xr, ty, tx);
-        a[ty][tx] = v2;
+        dg -= panel_dot(xr, xr, ty, tx);
+      }
+      {
+        a[ty][tx] = dg;
         __syncthreads();
         // warp 0, lane l holds row (l mod 16) of the block in registers
         if (threadIdx.x < 32) {
