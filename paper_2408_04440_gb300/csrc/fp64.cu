@@ -35,10 +35,14 @@ __device__ inline bool failed(const int *st) {
 // kernel makes progress whatever number of CTAs is resident.  Every wait is
 // bounded (status DEV_TIMEOUT) and every CTA leaves as soon as the status
 // word reports a failure.  Data written by other CTAs is read through L2.
-// GB300 executes a dependent FP64 FMA in ~64 cycles and an FP64 rsqrt in
-// ~430, so the leaf keeps its block in registers (one lane per row), the
-// pivot column is broadcast by shuffles, and solves use L scaled by the
-// pivot reciprocals (one dependent FMA per substitution step).
+// On GB300 an FP64 warp instruction holds its SM sub-partition's FP64 pipe
+// for 64 cycles however many lanes are active, and an FP64 rsqrt costs ~430.
+// So the leaf spreads the block over four warps (one per sub-partition),
+// eliminates without square roots (pivot reciprocals on the chain, scaling
+// by rsqrt once at the end), and the solves use L scaled by the pivot
+// reciprocals (one dependent FMA per substitution step).  LT(s) publishes
+// X_{s,s-1} before its leaf, so that LT(s+1) applies panel s-1 to block
+// (s+1, s) while the leaf runs.
 constexpr int PB = 16;
 enum { T_LT = 0, T_TRSM = 1, T_UPD = 2 };
 constexpr uint64_t kDagWaitNs = 2000000000ull;
@@ -64,6 +68,23 @@ __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
     __nanosleep(32);
   }
 }
+
+// Pivot reciprocal: the hardware approximation y (relative error about
+// 2^-20, measured) refined by one third-order Newton-Raphson step for 1/d,
+// r = y (1 + e + e^2) with e = 1 - d y, whose truncation error e^3 is below
+// 2^-59; three dependent FMAs instead of the ~7 of an FP64 rsqrt.  The
+// approximation flushes subnormal inputs and results, so pivots outside
+// [2^-1000, 2^1000] take IEEE division (the branch is uniform: every thread
+// holds the same pivot).
+__device__ inline double pivot_rcp(double d) {
+  if (!(d > 0x1p-1000 && d < 0x1p+1000)) return 1.0 / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+__device__ inline void bar_sync_128(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
 // 16x16 products of panel rows: sum_p A[ty][p] B[tx][p], two chains.
 __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)[PB + 1], int ty, int tx) {
@@ -172,98 +193,122 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       }
       __stcg(bp, v * rinv[tx]);
     } else {
-      // LT(s): the inputs other tasks produce are loaded first; then, once
-      // LT(s-1) has ended, block (s, s-1) gets its fused update by panel s-2,
-      // is solved against L_{s-1,s-1}, is applied to the diagonal block, and
-      // the diagonal block is factored.
+      // LT(s): the inputs other tasks produce are loaded first; block (s, s-1)
+      // gets its fused update by panel s-2 as soon as LT(s-1) has published
+      // X_{s-1,s-2}; once LT(s-1) has ended it is solved against L_{s-1,s-1},
+      // published, applied to the diagonal block, and the diagonal block is
+      // factored.
       const int q = s - 1;
       double *bp = blk(s, q >= 0 ? q : 0);
-      double dg = __ldcg(blk(s, s));
+      const double dg = __ldcg(blk(s, s));
       double v = 0.0;
       if (q >= 0) {
         v = __ldcg(bp);
         if (q >= 1) xr[ty][tx] = __ldcg(blk(s, q - 1));
       }
-      if (threadIdx.x == 0) {
-        if (q >= 0) s_ok = dag_wait(state, q * nbb + q, s, st);  // LT(s-1) has ended
-        __threadfence();
+      if (q >= 1) {
+        if (threadIdx.x == 0) {
+          s_ok = dag_wait(state, q * nbb + (q - 1), q, st);  // X_{q,q-1} published
+          __threadfence();
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        xc[ty][tx] = __ldcg(blk(q, q - 1));
+        __syncthreads();
+        v -= panel_dot(xr, xc, ty, tx);
       }
-      __syncthreads();
-      if (!s_ok) return;
       if (q >= 0) {
+        if (threadIdx.x == 0) {
+          s_ok = dag_wait(state, q * nbb + q, s, st);  // LT(s-1) has ended
+          __threadfence();
+        }
+        __syncthreads();  // also orders the reads of xr / xc above before their reuse
+        if (!s_ok) return;
         a[ty][tx] = __ldcg(blk(q, q));
         if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + q * PB + threadIdx.x);
-        if (q >= 1) xc[ty][tx] = __ldcg(blk(q, q - 1));
         __syncthreads();
         m[ty][tx] = a[ty][tx] * rinv[tx];
-        if (q >= 1) v -= panel_dot(xr, xc, ty, tx);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < PB; j++) {
           double vj = __shfl_sync(0xffffffffu, v, j, PB);
           if (tx > j) v = fma(-vj, m[tx][j], v);
         }
-        const double x = v * rinv[tx];
-        __stcg(bp, x);
-        xr[ty][tx] = x;  // panel_dot above has read xr (the barrier after it)
-        __syncthreads();
-        dg -= panel_dot(xr, xr, ty, tx);
+        xr[ty][tx] = v * rinv[tx];  // X_{s,q}
       }
-      {
-        a[ty][tx] = dg;
-        __syncthreads();
-        // warp 0, lane l holds row (l mod 16) of the block in registers
-        if (threadIdx.x < 32) {
-          int lane = threadIdx.x;
-          int row = lane & (PB - 1);
-          double xx[PB];
-#pragma unroll
-          for (int k2 = 0; k2 < PB; k2++) xx[k2] = a[row][k2];
-          int fail = 0;
-#pragma unroll
-          for (int j = 0; j < PB; j++) {
-            double d = __shfl_sync(0xffffffffu, xx[j], j);  // pivot from lane j
-            if (!(d > 0.0) && !fail) fail = j + 1;        // also catches NaN; same in every lane
-            if (fail) d = 1.0;  // keep going without branching; the result is discarded
-            double rs = rsqrt(d);
-            double l = (row == j) ? d * rs : xx[j] * rs;  // L[row][j]
-            xx[j] = (row >= j) ? l : xx[j];
-            if (lane == 0) rinv[j] = rs;
-            double lm = (row > j) ? l : 0.0;
-            // branch-free rank-1 update keeps xx[] in registers
-#pragma unroll
-            for (int k2 = j + 1; k2 < PB; k2++) {
-              double lq = __shfl_sync(0xffffffffu, l, k2);  // L[k2][j]
-              xx[k2] = fma(-((row >= k2) ? lm : 0.0), lq, xx[k2]);
-            }
-          }
-          if (fail) {
-            if (lane == 0) bad = fail;
-          } else if (lane < PB) {
-#pragma unroll
-            for (int k2 = 0; k2 < PB; k2++) a[row][k2] = xx[k2];
-          }
+      xc[ty][tx] = dg;
+      __syncthreads();
+      if (threadIdx.x >= 128) {
+        // warps 4..7 publish X_{s,q} (lanes along columns of the block)
+        if (q >= 0) {
+          const int e = threadIdx.x - 128, rr = e & (PB - 1), cc = e >> 4;
+          double *xp = D + (size_t)(s * PB + rr) + (size_t)(q * PB + cc) * ld;
+          __stcg(xp, xr[rr][cc]);
+          __stcg(xp + 8 * ld, xr[rr][cc + 8]);
+          __threadfence();
+          bar_sync_128(2);
+          if (threadIdx.x == 128) atomicExch(&state[s * nbb + q], s);
         }
-        __syncthreads();
-        if (bad) {
-          if (threadIdx.x == 0) {
-            st[ST_PIVOT] = gcol0 + s * PB + bad;
-            if (BATCH) st[ST_AUX] = bt;  // which tile of the batch
-            __threadfence();
-            atomicExch(&st[ST_CODE], DEV_NOTPD);
-          }
-          return;
+      } else {
+        // warps 0..3: the diagonal block minus X X^T, then the leaf.  Thread
+        // (warp w, half h, row i) holds entries (i, k0) and (i, k1) with
+        // k0 = w + 4h, k1 = k0 + 8.  Step j: the owner of column j writes the
+        // unscaled column c_j to m[j][*]; then every thread updates its
+        // trailing entries, x_ik -= c_j[i] c_j[k] / c_jj.  At the end
+        // L_ik = c_k[i] / sqrt(c_kk).
+        const int w = threadIdx.x >> 5, i = threadIdx.x & (PB - 1);
+        const int k0 = w + 4 * ((threadIdx.x >> 4) & 1), k1 = k0 + 8;
+        double v0 = xc[i][k0], v1 = xc[i][k1];
+        if (q >= 0) {
+          v0 -= panel_dot(xr, xr, i, k0);
+          v1 -= panel_dot(xr, xr, i, k1);
         }
-        if (ty >= tx) __stcg(blk(s, s), a[ty][tx]);
-        if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
+        int fail = 0;
+#pragma unroll
+        for (int j = 0; j < PB; j++) {
+          if (j < 8) {
+            if (k0 == j) m[j][i] = v0;
+          } else {
+            if (k1 == j) m[j][i] = v1;
+          }
+          bar_sync_128(1);
+          double dj = m[j][j];
+          if (!(dj > 0.0)) {  // also catches NaN; the same in every thread
+            if (!fail) fail = j + 1;
+            dj = 1.0;  // keep going; the result is discarded
+          }
+          const double tt = m[j][i] * pivot_rcp(dj);
+          // warp-uniform guards: no lane of the warp has a column > j left
+          if (j < w + 4 && k0 > j && i >= k0) v0 = fma(-tt, m[j][k0], v0);
+          if (j < w + 12 && k1 > j && i >= k1) v1 = fma(-tt, m[j][k1], v1);
+        }
+        if (threadIdx.x < PB) rinv[threadIdx.x] = rsqrt(m[threadIdx.x][threadIdx.x]);
+        bar_sync_128(1);
+        if (fail) {
+          if (threadIdx.x == 0) bad = fail;
+        } else {
+          a[i][k0] = v0 * rinv[k0];  // the diagonal: c_kk / sqrt(c_kk)
+          a[i][k1] = v1 * rinv[k1];
+        }
       }
+      __syncthreads();
+      if (bad) {
+        if (threadIdx.x == 0) {
+          st[ST_PIVOT] = gcol0 + s * PB + bad;
+          if (BATCH) st[ST_AUX] = bt;  // which tile of the batch
+          __threadfence();
+          atomicExch(&st[ST_CODE], DEV_NOTPD);
+        }
+        return;
+      }
+      if (ty >= tx) __stcg(blk(s, s), a[ty][tx]);
+      if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
       if (kind == T_LT) {
-        if (s >= 1) atomicExch(&state[s * nbb + (s - 1)], s);
-        atomicExch(&state[s * nbb + s], s + 1);
+        atomicExch(&state[s * nbb + s], s + 1);  // X_{s,s-1} was published before the leaf
       } else {
         atomicExch(&state[r * nbb + c], s + 1);
       }
