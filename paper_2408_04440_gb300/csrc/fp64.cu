@@ -73,15 +73,20 @@ __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
 // 2^-20, measured) refined by one third-order Newton-Raphson step for 1/d,
 // r = y (1 + e + e^2) with e = 1 - d y, whose truncation error e^3 is below
 // 2^-59; three dependent FMAs instead of the ~7 of an FP64 rsqrt.  The
-// approximation flushes subnormal inputs and results, so pivots outside
-// [2^-1000, 2^1000] take IEEE division (the branch is uniform: every thread
-// holds the same pivot).
+// approximation flushes subnormal inputs and results, so it is used for
+// pivots in [2^-1000, 2^1000) only (pivot_in_range).
 __device__ inline double pivot_rcp(double d) {
-  if (!(d > 0x1p-1000 && d < 0x1p+1000)) return 1.0 / d;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
   const double e = fma(-d, y, 1.0);
   return fma(y, fma(e, e, e), y);
+}
+// d positive, finite and in [2^-1000, 2^1000): biased exponent in [23, 2023).
+// An integer test on the high word: FP64 comparisons occupy the FP64 pipe
+// like an FMA.
+__device__ inline bool pivot_in_range(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  return hi - (23u << 20) < (2000u << 20);
 }
 
 __device__ inline void bar_sync_128(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
@@ -272,12 +277,18 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
             if (k1 == j) m[j][i] = v1;
           }
           bar_sync_128(1);
-          double dj = m[j][j];
-          if (!(dj > 0.0)) {  // also catches NaN; the same in every thread
-            if (!fail) fail = j + 1;
-            dj = 1.0;  // keep going; the result is discarded
+          // the pivot is the same in every thread: the branches are uniform
+          double dj = m[j][j], r;
+          if (pivot_in_range(dj)) {
+            r = pivot_rcp(dj);
+          } else {
+            if (!(dj > 0.0)) {  // also catches NaN
+              if (!fail) fail = j + 1;
+              dj = 1.0;  // keep going; the result is discarded
+            }
+            r = 1.0 / dj;
           }
-          const double tt = m[j][i] * pivot_rcp(dj);
+          const double tt = m[j][i] * r;
           // warp-uniform guards: no lane of the warp has a column > j left
           if (j < w + 4 && k0 > j && i >= k0) v0 = fma(-tt, m[j][k0], v0);
           if (j < w + 12 && k1 > j && i >= k1) v1 = fma(-tt, m[j][k1], v1);

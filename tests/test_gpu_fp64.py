@@ -70,6 +70,26 @@ def test_fp64_factor_of_imported_matrix(E, ctx):
     assert np.linalg.norm(G - Lo) / np.linalg.norm(Lo) <= 1e-12
 
 
+@pytest.mark.parametrize("scale", [2.0**-1010, 2.0**1005])
+def test_fp64_factor_with_extreme_pivots(E, ctx, scale):
+    # pivots below 2^-1000 or above 2^1000 leave the hardware reciprocal's
+    # range and take IEEE division in the diagonal-block leaf
+    import torch
+
+    rng = np.random.default_rng(5)
+    n = 150
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    S = (Q * np.linspace(1.0, 8.0, n)) @ Q.T
+    S = 0.5 * (S + S.T) * scale
+    A = E.emu_mat_import(ctx, torch.from_numpy(S).cuda(), 64)
+    E.emu_potrf_mp(ctx, A)
+    G = _np(E.emu_mat_export(ctx, A))
+    Lo, info = O.potrf_blocked(S, 64)
+    assert info == 0
+    assert np.all(np.isfinite(G))
+    assert np.linalg.norm(G - Lo) / np.linalg.norm(Lo) <= 1e-12
+
+
 @pytest.mark.parametrize("bad", [1, 70, 199])
 def test_not_positive_definite_reports_pivot(E, ctx, bad):
     import torch
