@@ -44,8 +44,15 @@ __device__ inline bool failed(const int *st) {
 // X_{s,s-1} before its leaf, so that LT(s+1) applies panel s-1 to block
 // (s+1, s) while the leaf runs.
 constexpr int PB = 16;
-enum { T_LT = 0, T_TRSM = 1, T_UPD = 2 };
-constexpr uint64_t kDagWaitNs = 2000000000ull;
+enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3 };
+// wait bound in SM clock cycles (about 2 s at 2 GHz)
+constexpr long long kDagWaitCycles = 4000000000ll;
+
+// GPU-scope acquire-release fence.  A block publishes data with its threads'
+// stores, a barrier, then one thread's fence and flag write (the fence is
+// cumulative over the stores the barrier ordered before it); a reader's
+// thread polls the flag, fences, and a barrier passes the acquisition on.
+__device__ inline void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ inline uint64_t gtimer() {
   uint64_t t;
@@ -57,11 +64,11 @@ __device__ inline uint64_t gtimer() {
 __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
   volatile const int *p = state + idx;
   if (*p >= v) return true;
-  uint64_t t0 = gtimer();
+  const long long t0 = clock64();
   while (true) {
     if (*p >= v) return true;
     if (*((volatile const int *)st) != DEV_OK) return false;
-    if (gtimer() - t0 > kDagWaitNs) {
+    if (clock64() - t0 > kDagWaitCycles) {
       if (atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 2;
       return false;
     }
@@ -90,6 +97,8 @@ __device__ inline bool pivot_in_range(double d) {
 }
 
 __device__ inline void bar_sync_128(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ inline void bar_sync_256(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
+__device__ inline void bar_arrive_256(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
 
 // 16x16 products of panel rows: sum_p A[ty][p] B[tx][p], two chains.
 __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)[PB + 1], int ty, int tx) {
@@ -100,6 +109,227 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
     acc1 += A[ty][p + 1] * Bm[tx][p + 1];
   }
   return acc0 + acc1;
+}
+
+// The leaf on warps 0..3 (u = thread index 0..127): factors the 16x16 block
+// whose lower entries (i, k0) and (i, k1) the thread holds in v0, v1
+// (k0 = w + 4h for warp w, half-warp h; k1 = k0 + 8).  Step j: the owner of
+// column j writes the unscaled column c_j to mcol[j][*]; then every thread
+// updates its trailing entries, x_ik -= c_j[i] c_j[k] / c_jj.  At the end
+// L_ik = c_k[i] / sqrt(c_kk) goes to out[i][k] and 1/L_kk to rinv[k].
+// Returns 0, or the 1-based column of the first non-positive pivot (the
+// same in every thread; out and rinv are then not written).
+__device__ __forceinline__ int leaf16(int u, double v0, double v1, double (*mcol)[PB + 1], double (*out)[PB + 1],
+                                      double *rinv) {
+  const int w = u >> 5, i = u & (PB - 1);
+  const int k0 = w + 4 * ((u >> 4) & 1), k1 = k0 + 8;
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < PB; j++) {
+    if (j < 8) {
+      if (k0 == j) mcol[j][i] = v0;
+    } else {
+      if (k1 == j) mcol[j][i] = v1;
+    }
+    bar_sync_128(1);
+    // the pivot is the same in every thread: the branches are uniform
+    double dj = mcol[j][j], r;
+    if (pivot_in_range(dj)) {
+      r = pivot_rcp(dj);
+    } else {
+      if (!(dj > 0.0)) {  // also catches NaN
+        if (!fail) fail = j + 1;
+        dj = 1.0;  // keep going; the result is discarded
+      }
+      r = 1.0 / dj;
+    }
+    const double tt = mcol[j][i] * r;
+    // warp-uniform guards: no lane of the warp has a column > j left
+    if (j < w + 4 && k0 > j && i >= k0) v0 = fma(-tt, mcol[j][k0], v0);
+    if (j < w + 12 && k1 > j && i >= k1) v1 = fma(-tt, mcol[j][k1], v1);
+  }
+  if (u < PB) rinv[u] = rsqrt(mcol[u][u]);
+  bar_sync_128(1);
+  if (!fail) {
+    out[i][k0] = v0 * rinv[k0];  // the diagonal: c_kk / sqrt(c_kk)
+    out[i][k1] = v1 * rinv[k1];
+  }
+  return fail;
+}
+
+// The whole chain LT(0), LT(1), ... of one tile in one CTA (task T_MASTER
+// of the single-tile list), so that no step waits for another CTA's flag or
+// reloads L_{s-1,s-1} from L2.  Warps 0..3 compute: the solve of block
+// (s, s-1), the diagonal block minus X X^T and the leaf.  Warps 4..7 do the
+// memory traffic meanwhile: they publish L_{s-1,s-1} and X_{s,s-1}, wait for
+// the next step's inputs (X_{s+1,s-1} from TRSM(s+1, s-1), the updates of
+// blocks (s+1, s) and (s+1, s+1) by earlier panels), load them, and apply
+// panel s-1 to block (s+1, s) while the leaf runs.  Shared buffers at the
+// start of step s: a = L_{s-1,s-1}, m = L_{s-1,s-1} scaled by the pivot
+// reciprocals rinv, xr = block (s, s-1) after panels < s-1, xc = block (s, s)
+// after panels < s-1.  Other CTAs run the TRSM / UPD tasks, which finish
+// without waiting for anything but this chain and earlier tasks, so the
+// chain advances as soon as one other CTA of the launch is resident.
+// flags[0]: a wait failed (status already set); flags[1]: first
+// non-positive pivot column in the block (1-based).
+__device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int gcol0, int *__restrict__ state,
+                                             double *__restrict__ rinv_g, int *st,
+                                             unsigned long long *__restrict__ trace, double (*a)[PB + 1],
+                                             double (*m)[PB + 1], double (*xr)[PB + 1], double (*xc)[PB + 1],
+                                             double *rinv, volatile int *flags) {
+  const int nbb = nb / PB;
+  const size_t ld = nb;
+  const int tid = threadIdx.x, u = tid & 127;
+  const bool io = tid >= 128;
+  // warps 4..7: entries (ir, ic) and (ir, ic + 8), lanes along a column
+  const int ir = u & (PB - 1), ic = u >> 4;
+  // warps 0..3, solve: rows cr and cr + 8 of column ct (a row's 16 lanes shuffle)
+  const int cr = u >> 4, ct = u & (PB - 1);
+  auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
+  if (tid == 0) flags[0] = flags[1] = 0;
+  if (io) {
+    xc[ir][ic] = __ldcg(gp(0, 0, ir, ic));
+    xc[ir][ic + 8] = __ldcg(gp(0, 0, ir, ic + 8));
+  }
+  __syncthreads();
+  for (int s = 0; s < nbb; s++) {
+    const int q = s - 1, n1 = s + 1;
+    unsigned long long t0 = 0, t1 = 0;
+    if (trace && tid == 0) t0 = gtimer();
+    if (!io) {
+      // X_{s,q} = block (s, q) L_{q,q}^{-T}
+      if (q >= 0) {
+        double va = xr[cr][ct], vb = xr[cr + 8][ct];
+#pragma unroll
+        for (int j = 0; j < PB; j++) {
+          const double aj = __shfl_sync(0xffffffffu, va, j, PB), bj = __shfl_sync(0xffffffffu, vb, j, PB);
+          if (ct > j) {
+            const double mj = m[ct][j];
+            va = fma(-aj, mj, va);
+            vb = fma(-bj, mj, vb);
+          }
+        }
+        xr[cr][ct] = va * rinv[ct];
+        xr[cr + 8][ct] = vb * rinv[ct];
+      }
+    } else if (q >= 0) {
+      // publish L_{q,q} and its pivot reciprocals
+      if (ir >= ic) __stcg(gp(q, q, ir, ic), a[ir][ic]);
+      if (ir >= ic + 8) __stcg(gp(q, q, ir, ic + 8), a[ir][ic + 8]);
+      if (u < PB) __stcg(rinv_g + q * PB + u, rinv[u]);
+      bar_sync_128(2);
+      if (u == 0) {
+        fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+        atomicExch(&state[q * nbb + q], q + 1);
+      }
+    }
+    __syncthreads();
+    if (trace && tid == 0) t1 = gtimer();
+    if (!io) {
+      const int i = u & (PB - 1), k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;
+      double v0 = xc[i][k0], v1 = xc[i][k1];
+      if (q >= 0) {
+        v0 -= panel_dot(xr, xr, i, k0);
+        v1 -= panel_dot(xr, xr, i, k1);
+      }
+      bar_arrive_256(3);  // this step's reads of xr and xc are done
+      const int fail = leaf16(u, v0, v1, m, a, rinv);
+      if (fail) {
+        if (u == 0) flags[1] = fail;
+      } else {
+        bar_sync_128(1);  // a complete
+        m[cr][ct] = a[cr][ct] * rinv[ct];
+        m[cr + 8][ct] = a[cr + 8][ct] * rinv[ct];
+      }
+    } else {
+      if (q >= 0) {
+        // publish X_{s,q}
+        __stcg(gp(s, q, ir, ic), xr[ir][ic]);
+        __stcg(gp(s, q, ir, ic + 8), xr[ir][ic + 8]);
+        bar_sync_128(2);
+        if (u == 0) {
+          fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+          atomicExch(&state[s * nbb + q], s);
+        }
+      }
+      double pa = 0.0, pb = 0.0, ga = 0.0, gb = 0.0;
+      if (n1 < nbb) {
+        // block (n1, s) after panels < s-1 (and X_{n1,s-1})
+        if (u == 0) {
+          const bool ok = (s < 1 || dag_wait(state, n1 * nbb + (s - 1), s, st)) &&
+                          dag_wait(state, n1 * nbb + s, s - 1, st);
+          fence_acq_rel_gpu();
+          if (!ok) flags[0] = 1;
+        }
+        bar_sync_128(2);
+        if (!flags[0]) {
+          pa = __ldcg(gp(n1, s, ir, ic));
+          pb = __ldcg(gp(n1, s, ir, ic + 8));
+        }
+      }
+      bar_sync_256(3);  // the compute warps no longer read xr / xc
+      if (n1 < nbb && s >= 1 && !flags[0]) {
+        xc[ir][ic] = __ldcg(gp(n1, s - 1, ir, ic));
+        xc[ir][ic + 8] = __ldcg(gp(n1, s - 1, ir, ic + 8));
+      }
+      bar_sync_128(2);
+      if (n1 < nbb && s >= 1 && !flags[0]) {
+        // panel s-1 applied to block (n1, s): X_{n1,s-1} X_{s,s-1}^T
+        pa -= panel_dot(xc, xr, ir, ic);
+        pb -= panel_dot(xc, xr, ir, ic + 8);
+      }
+      if (n1 < nbb) {
+        // block (n1, n1) after panels < s
+        if (u == 0) {
+          const bool ok = !flags[0] && dag_wait(state, n1 * nbb + n1, s, st);
+          fence_acq_rel_gpu();
+          if (!ok) flags[0] = 1;
+        }
+        bar_sync_128(2);  // also: every read of xr / xc above is done
+        if (!flags[0]) {
+          ga = __ldcg(gp(n1, n1, ir, ic));
+          gb = __ldcg(gp(n1, n1, ir, ic + 8));
+        }
+        xr[ir][ic] = pa;
+        xr[ir][ic + 8] = pb;
+        xc[ir][ic] = ga;
+        xc[ir][ic + 8] = gb;
+      }
+    }
+    __syncthreads();
+    if (trace && tid == 0) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      unsigned long long *rec = trace + (size_t)s * 5;
+      rec[0] = (unsigned long long)T_LT | ((unsigned long long)s << 8) |
+               ((unsigned long long)(q < 0 ? 0 : q) << 24) | ((unsigned long long)s << 40);
+      rec[1] = smid;
+      rec[2] = t0;
+      rec[3] = t1;
+      rec[4] = gtimer();
+    }
+    if (flags[1]) {
+      if (tid == 0) {
+        st[ST_PIVOT] = gcol0 + s * PB + flags[1];
+        __threadfence();
+        atomicExch(&st[ST_CODE], DEV_NOTPD);
+      }
+      return;
+    }
+    if (flags[0]) return;
+  }
+  // publish the last diagonal block
+  if (io) {
+    const int q = nbb - 1;
+    if (ir >= ic) __stcg(gp(q, q, ir, ic), a[ir][ic]);
+    if (ir >= ic + 8) __stcg(gp(q, q, ir, ic + 8), a[ir][ic + 8]);
+    if (u < PB) __stcg(rinv_g + q * PB + u, rinv[u]);
+    bar_sync_128(2);
+    if (u == 0) {
+      fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+      atomicExch(&state[q * nbb + q], q + 1);
+    }
+  }
 }
 
 // One tile: at most 64 registers per thread (4 CTAs of 256 threads per SM),
@@ -117,6 +347,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
   __shared__ int s_task, s_ok, bad;
+  __shared__ int mflags[2];
   // ws = {task counter, then state[nbb*nbb] per tile}; rinv_all = nb pivot
   // reciprocals per tile.  A batch of nbat tiles (dtiles = their indices in
   // D0) interleaves the tiles' task lists: task t is task t / nbat of tile
@@ -138,11 +369,16 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     auto blk = [&](int br, int bc) { return D + (size_t)(br * PB + ty) + (size_t)(bc * PB + tx) * ld; };
     short4 tk = tasks[BATCH ? t / nbat : t];
     int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LT: (s, s-1, s); TRSM: (r, s, s); UPD: (r, c, s)
+    if (!BATCH && kind == T_MASTER) {
+      potrf_master(D, nb, gcol0, state, rinv_g, st, trace ? trace + (size_t)ntasks * 5 : nullptr, a, m, xr, xc, rinv,
+                   mflags);
+      return;
+    }
     unsigned long long t_fetch = 0;
     if (trace && threadIdx.x == 0) t_fetch = gtimer();
     if (threadIdx.x == 0) {
       bool ok;
-      if (kind == T_LT)
+      if (BATCH && kind == T_LT)
         // first the inputs other tasks produce (usually ready long before
         // LT(s-1) ends): X_{s,s-2}, block (s,s-1) and the diagonal block
         ok = (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
@@ -153,7 +389,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       else
         ok = dag_wait(state, r * nbb + s, s + 1, st) && dag_wait(state, c * nbb + s, s + 1, st) &&
              dag_wait(state, r * nbb + c, s, st);
-      __threadfence();
+      fence_acq_rel_gpu();
       s_ok = ok;
       bad = 0;
       if (trace) {
@@ -197,8 +433,9 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         if (tx > j) v = fma(-vj, m[tx][j], v);
       }
       __stcg(bp, v * rinv[tx]);
-    } else {
-      // LT(s): the inputs other tasks produce are loaded first; block (s, s-1)
+    } else if (BATCH) {
+      // LT(s) (batch form; one tile runs the chain in potrf_master): the
+      // inputs other tasks produce are loaded first; block (s, s-1)
       // gets its fused update by panel s-2 as soon as LT(s-1) has published
       // X_{s-1,s-2}; once LT(s-1) has ended it is solved against L_{s-1,s-1},
       // published, applied to the diagonal block, and the diagonal block is
@@ -214,7 +451,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       if (q >= 1) {
         if (threadIdx.x == 0) {
           s_ok = dag_wait(state, q * nbb + (q - 1), q, st);  // X_{q,q-1} published
-          __threadfence();
+          fence_acq_rel_gpu();
         }
         __syncthreads();
         if (!s_ok) return;
@@ -225,7 +462,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       if (q >= 0) {
         if (threadIdx.x == 0) {
           s_ok = dag_wait(state, q * nbb + q, s, st);  // LT(s-1) has ended
-          __threadfence();
+          fence_acq_rel_gpu();
         }
         __syncthreads();  // also orders the reads of xr / xc above before their reuse
         if (!s_ok) return;
@@ -250,57 +487,23 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
           double *xp = D + (size_t)(s * PB + rr) + (size_t)(q * PB + cc) * ld;
           __stcg(xp, xr[rr][cc]);
           __stcg(xp + 8 * ld, xr[rr][cc + 8]);
-          __threadfence();
           bar_sync_128(2);
-          if (threadIdx.x == 128) atomicExch(&state[s * nbb + q], s);
+          if (threadIdx.x == 128) {
+            fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+            atomicExch(&state[s * nbb + q], s);
+          }
         }
       } else {
-        // warps 0..3: the diagonal block minus X X^T, then the leaf.  Thread
-        // (warp w, half h, row i) holds entries (i, k0) and (i, k1) with
-        // k0 = w + 4h, k1 = k0 + 8.  Step j: the owner of column j writes the
-        // unscaled column c_j to m[j][*]; then every thread updates its
-        // trailing entries, x_ik -= c_j[i] c_j[k] / c_jj.  At the end
-        // L_ik = c_k[i] / sqrt(c_kk).
-        const int w = threadIdx.x >> 5, i = threadIdx.x & (PB - 1);
-        const int k0 = w + 4 * ((threadIdx.x >> 4) & 1), k1 = k0 + 8;
+        // warps 0..3: the diagonal block minus X X^T, then the leaf
+        const int u = threadIdx.x, i = u & (PB - 1);
+        const int k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;
         double v0 = xc[i][k0], v1 = xc[i][k1];
         if (q >= 0) {
           v0 -= panel_dot(xr, xr, i, k0);
           v1 -= panel_dot(xr, xr, i, k1);
         }
-        int fail = 0;
-#pragma unroll
-        for (int j = 0; j < PB; j++) {
-          if (j < 8) {
-            if (k0 == j) m[j][i] = v0;
-          } else {
-            if (k1 == j) m[j][i] = v1;
-          }
-          bar_sync_128(1);
-          // the pivot is the same in every thread: the branches are uniform
-          double dj = m[j][j], r;
-          if (pivot_in_range(dj)) {
-            r = pivot_rcp(dj);
-          } else {
-            if (!(dj > 0.0)) {  // also catches NaN
-              if (!fail) fail = j + 1;
-              dj = 1.0;  // keep going; the result is discarded
-            }
-            r = 1.0 / dj;
-          }
-          const double tt = m[j][i] * r;
-          // warp-uniform guards: no lane of the warp has a column > j left
-          if (j < w + 4 && k0 > j && i >= k0) v0 = fma(-tt, m[j][k0], v0);
-          if (j < w + 12 && k1 > j && i >= k1) v1 = fma(-tt, m[j][k1], v1);
-        }
-        if (threadIdx.x < PB) rinv[threadIdx.x] = rsqrt(m[threadIdx.x][threadIdx.x]);
-        bar_sync_128(1);
-        if (fail) {
-          if (threadIdx.x == 0) bad = fail;
-        } else {
-          a[i][k0] = v0 * rinv[k0];  // the diagonal: c_kk / sqrt(c_kk)
-          a[i][k1] = v1 * rinv[k1];
-        }
+        const int fail = leaf16(u, v0, v1, m, a, rinv);
+        if (fail && u == 0) bad = fail;
       }
       __syncthreads();
       if (bad) {
@@ -315,10 +518,10 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       if (ty >= tx) __stcg(blk(s, s), a[ty][tx]);
       if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (kind == T_LT) {
+      fence_acq_rel_gpu();
+      if (BATCH && kind == T_LT) {
         atomicExch(&state[s * nbb + s], s + 1);  // X_{s,s-1} was published before the leaf
       } else {
         atomicExch(&state[r * nbb + c], s + 1);
@@ -328,16 +531,21 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   }
 }
 
-// Task list of the dataflow POTRF for nbb blocks per side (see k_potrf_dag).
-static void dag_tasks(int nbb, std::vector<short4> &out) {
+// Task list of the dataflow POTRF for nbb blocks per side (see k_potrf_dag),
+// in topological, lookahead-first order.  With master = true the LT tasks
+// are replaced by one T_MASTER task at the head of the list (single tile).
+static void dag_tasks(int nbb, std::vector<short4> &out, bool master) {
   out.clear();
   auto push = [&](int kind, int r, int c, int s) {
     out.push_back(make_short4((short)kind, (short)r, (short)c, (short)s));
   };
-  push(T_LT, 0, 0, 0);
+  if (master)
+    push(T_MASTER, 0, 0, 0);
+  else
+    push(T_LT, 0, 0, 0);
   for (int r = 2; r < nbb; r++) push(T_TRSM, r, 0, 0);
   for (int s = 0; s + 1 < nbb; s++) {
-    push(T_LT, s + 1, s, s + 1);
+    if (!master) push(T_LT, s + 1, s, s + 1);
     for (int r = s + 3; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
     for (int c = s + 2; c < nbb; c++)
       for (int r = c; r < nbb; r++) push(T_UPD, r, c, s);
@@ -647,7 +855,7 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   int nbb = nb / PB;
   if (ctx->dag_nbb != nbb) {
     std::vector<short4> tasks;
-    dag_tasks(nbb, tasks);
+    dag_tasks(nbb, tasks, true);
     cudaFree(ctx->dag_tasks);
     cudaFree(ctx->dag_ws);
     ctx->dag_tasks = nullptr;
@@ -669,7 +877,9 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   int grid = ctx->sm_count < ctx->dag_ntasks ? ctx->sm_count : ctx->dag_ntasks;
   unsigned long long *trace = nullptr;
   if (ctx->trace_on) {
-    size_t need = (size_t)(k + 1) * ctx->dag_ntasks * 5;
+    // per tile: one record per task, then one per master step
+    const size_t per_tile = (size_t)(ctx->dag_ntasks + nbb) * 5;
+    size_t need = (size_t)(k + 1) * per_tile;
     if (need > ctx->trace_cap) {
       // grow: keep earlier tiles' records of this factor
       unsigned long long *nt = nullptr;
@@ -684,8 +894,8 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
       ctx->trace_buf = nt;
       ctx->trace_cap = cap;
     }
-    trace = ctx->trace_buf + (size_t)k * ctx->dag_ntasks * 5;
-    ctx->trace_records = (size_t)(k + 1) * ctx->dag_ntasks;
+    trace = ctx->trace_buf + (size_t)k * per_tile;
+    ctx->trace_records = (size_t)(k + 1) * (ctx->dag_ntasks + nbb);
   }
   double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
   k_potrf_dag<false><<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks,
@@ -709,13 +919,13 @@ emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_j
 
 size_t potrf_dag_task_count(int nb) {
   std::vector<short4> tasks;
-  dag_tasks(nb / PB, tasks);
+  dag_tasks(nb / PB, tasks, false);
   return tasks.size();
 }
 
 emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStream_t s) {
   std::vector<short4> tasks;
-  dag_tasks(nb / PB, tasks);
+  dag_tasks(nb / PB, tasks, false);
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(d_tasks, tasks.data(), tasks.size() * sizeof(short4), cudaMemcpyHostToDevice, s));
   // the host vector goes out of scope: wait for the copy
   EMU_CUDA_TRY(ctx, cudaStreamSynchronize(s));

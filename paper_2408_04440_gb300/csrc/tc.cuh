@@ -1,25 +1,20 @@
 // tc.cuh -- thin inline-PTX wrappers for the Blackwell (sm_100 family) data
 // path used by the tensor-core kernels: mbarriers, TMA tile loads, TMEM
-// allocation, tcgen05.mma / commit / ld.  Every wait is bounded by
-// %globaltimer so that a kernel whose producer never arrives reports a
-// timeout instead of hanging the GPU.
+// allocation, tcgen05.mma / commit / ld.  Every wait is bounded (SM clock
+// cycles) so that a kernel whose producer never arrives reports a timeout
+// instead of hanging the GPU.
 #pragma once
 #include <cuda.h>
 #include <stdint.h>
 
 namespace tc {
 
-// Upper bound of any single wait inside a kernel (nanoseconds).
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+// Upper bound of any single wait inside a kernel, in SM clock cycles (about
+// 2 s at 2 GHz).
+constexpr long long kWaitLimitCycles = 4000000000ll;
 
 __device__ inline uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ inline uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 
 // ---------------------------------------------------------------- mbarrier
@@ -48,14 +43,14 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase with the given parity to complete; false after
-// kWaitLimitNs or when *abort becomes nonzero.
+// kWaitLimitCycles or when *abort becomes nonzero.
 __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
-  uint64_t t0 = globaltimer();
+  const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (clock64() - t0 > kWaitLimitCycles) return false;
   }
 }
 
