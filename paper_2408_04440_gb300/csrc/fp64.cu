@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         ok = (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
              (s < 1 || dag_wait(state, s * nbb + (s - 1), s - 2, st)) && dag_wait(state, s * nbb + s, s - 1, st);
       else if (kind == T_TRSM)
-        ok = dag_wait(state, s * nbb + s, s + 1, st) && (s == 0 || dag_wait(state, r * nbb + (s - 1), s, st)) &&
+        // the inputs of the panel s-1 update first; L_{s,s} is awaited below
+        ok = (s == 0 || (dag_wait(state, r * nbb + (s - 1), s, st) && dag_wait(state, s * nbb + (s - 1), s, st))) &&
              dag_wait(state, r * nbb + s, s - 1, st);
       else
         ok = dag_wait(state, r * nbb + s, s + 1, st) && dag_wait(state, c * nbb + s, s + 1, st) &&
@@ -414,18 +415,27 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       __stcg(cp, v - panel_dot(xr, xc, ty, tx));
     } else if (kind == T_TRSM) {
       // Solve block (r, s) against L_{s,s} after its fused update by panel
-      // s-1: row ty's 16 lanes exchange entries by shuffle.
-      a[ty][tx] = __ldcg(blk(s, s));
-      if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + s * PB + threadIdx.x);
+      // s-1, which runs as soon as X_{s,s-1} is published, before L_{s,s}
+      // (the chain publishes X_{s,s-1} before it factors block (s, s)).  Row
+      // ty's 16 lanes exchange entries by shuffle.
       double *bp = blk(r, s);
       double v = __ldcg(bp);
       if (s >= 1) {
         xr[ty][tx] = __ldcg(blk(r, s - 1));
         xc[ty][tx] = __ldcg(blk(s, s - 1));
+        __syncthreads();
+        v -= panel_dot(xr, xc, ty, tx);
+      }
+      if (threadIdx.x == 0) {
+        s_ok = dag_wait(state, s * nbb + s, s + 1, st);  // L_{s,s}
+        fence_acq_rel_gpu();
       }
       __syncthreads();
+      if (!s_ok) return;
+      a[ty][tx] = __ldcg(blk(s, s));
+      if (threadIdx.x < PB) rinv[threadIdx.x] = __ldcg(rinv_g + s * PB + threadIdx.x);
+      __syncthreads();
       m[ty][tx] = a[ty][tx] * rinv[tx];
-      if (s >= 1) v -= panel_dot(xr, xc, ty, tx);
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < PB; j++) {
