@@ -260,14 +260,20 @@ def run_ours(a):
 TRAFFIC = {}
 
 
-FP64_NOTES = {
+ALU_NOTES = {
     "potrf": "the diagonal-tile POTRF is bound by its FP64 dependency chain (one 16-column leaf after another)",
     "update64": "FP64 tile updates are FP64-pipe bound; their launch times include sharing the SMs with the "
                 "concurrent streams",
     "trsm64": "the FP64 panel TRSM is bound by its substitution chain and by the SMs left beside the bulk update",
     "trmm64": "FP64-class tiles of the sampler, FP64-pipe bound",
     "solve": "triangular solves, bound by their substitution chains",
+    "trsm32": "the FP32 panel TRSM is bound by its substitution chain and by L_kk strip loads, on the SMs left beside "
+              "the bulk update",
 }
+# ALU peaks measured on this GPU model with dependent-free FMA loops (TFLOP/s)
+ALU_PEAK = {"fp64": 1.19, "fp32": 74.0}
+ALU_GROUPS = {"potrf": "fp64", "trsm64": "fp64", "update64": "fp64", "trmm64": "fp64", "solve": "fp64",
+              "trsm32": "fp32"}
 
 
 def roofline(prof: dict, peaks: dict) -> dict:
@@ -286,13 +292,14 @@ def roofline(prof: dict, peaks: dict) -> dict:
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
                 "peak_note": f"bf16 sustained {bf16} TF/s {src}, weighted by the class mix"}
-    if group in ("potrf", "trsm64", "update64", "trmm64", "solve"):
-        fp64 = 1.19  # DFMA loop measured on this GPU model
+    if group in ALU_GROUPS:
+        unit = ALU_GROUPS[group]
+        peak = ALU_PEAK[unit]
         achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
-        return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": fp64, "unit": "TFLOP/s",
-                "frac": round(achieved / fp64, 4), "traffic": TRAFFIC.get(group),
+        return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(group),
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
-                "peak_note": "FP64 DFMA peak measured with a DFMA loop; " + FP64_NOTES.get(group, "")}
+                "peak_note": f"{unit.upper()} FMA peak measured with an FMA loop; " + ALU_NOTES.get(group, "")}
     hbm = peaks.get("hbm_gbs") or 6800.0
     achieved = g["bytes"] / (g["ms"] * 1e-3) / 1e9
     return {"kernel": group, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

@@ -151,31 +151,43 @@ __global__ void __launch_bounds__(1024)
 // FP32 panel TRSM for the low-precision tiles of column k:
 // L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy of the
 // FP64 L_kk, written back to the master and, split, to the operand arena.
-// One CTA per (16-row block, tile), 8 warps: warp w owns rows w and w + 8, a
-// lane owns one column of the current 32-column block cb.  For each cb the
-// already-solved columns are subtracted (a small GEMM against L_kk rows staged
-// in shared memory in 128-column strips), then each warp solves its two rows
-// against the 32x32 diagonal block by forward substitution with shuffles.
-// About 50 KB of shared memory per CTA, so four CTAs share an SM and hide each
-// other's strip-load latency.
+// One CTA per (row block, tile); warp w owns rows w + NW*q, a lane owns one
+// column of the current 32-column block cb.  L_kk streams through shared
+// memory as 32x32 chunks (rows of block cb, columns of block c <= cb) in a
+// ring of NBUF buffers filled by cp.async several chunks ahead, the same
+// sequence for every CTA: a chunk c < cb is subtracted from the block's
+// columns (four independent partial sums per row), the diagonal chunk c = cb
+// is solved by forward substitution with shuffles.  One barrier per chunk.
 constexpr int TS_LD_PAD = 4;
-constexpr int TS_STRIP = 128;  // columns of L_kk staged at once
-// NW warps, RPW rows per warp: the CTA solves NW*RPW rows (warp w owns rows
-// w + NW*q).  16-row CTAs (8 warps x 2) for throughput on the panel, 4-row
-// CTAs (4 warps x 1) for the single tile on the critical path, where more
-// CTAs in parallel mean less latency.
-template <int NW, int RPW, bool JOBS = false>
+constexpr int TS_CHUNK = B * B;  // floats per chunk, column-major (32 columns x 32 rows)
+constexpr int TS_NBUF_CRIT = 8;   // chunk buffers, single critical-path tile (1 CTA per SM)
+constexpr int TS_NBUF_PANEL = 4;  // panel launches (4 CTAs per SM hide each other's latency)
+
+__device__ inline void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// NW warps, RPW rows per warp, NBUF chunk buffers: 16-row CTAs (8 warps x 2)
+// for throughput on the panel, 4-row CTAs (4 warps x 1, deeper ring) for the
+// single tile on the critical path, where more CTAs in parallel mean less
+// latency.
+template <int NW, int RPW, int NBUF, bool JOBS = false>
 __global__ void __launch_bounds__(NW * 32)
     k_trsm32_panel(const float *__restrict__ Lkk0, float *__restrict__ t32, uint16_t *__restrict__ op, int nb,
                    int NT, int k, const int *__restrict__ rows, const int *st,
                    const int2 *__restrict__ jobs = nullptr) {
   constexpr int ROWS = NW * RPW, NTH = NW * 32;
   if (failed(st)) return;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int ldx = nb + TS_LD_PAD;
-  const int lds = TS_STRIP + 1;
-  float *X = sm;                // [ROWS][ldx]: the CTA's rows of A_ik, solved in place
-  float *S = X + ROWS * ldx;    // [32][lds]: strip of L_kk rows cb*32 + lane
+  float *S = sm;                     // [NBUF][32][32]: chunk ring, S[p * 32 + r] = L_kk(cb*32 + r, c*32 + p)
+  float *X = sm + NBUF * TS_CHUNK;   // [ROWS][ldx]: the CTA's rows of A_ik, solved in place
   int r0 = blockIdx.x * ROWS;
   // tile (i, k) of one matrix, or (batched) an explicit tile index and the
   // slot of its L_kk copy
@@ -189,76 +201,89 @@ __global__ void __launch_bounds__(NW * 32)
     ti = tile_index(rows[blockIdx.y], k, NT);
   }
   float *A = t32 + (size_t)ti * nb * nb + r0;
-  int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nbc = nb / B, nchunks = nbc * (nbc + 1) / 2;
+  // chunk i = (cb, c) with i = cb (cb + 1) / 2 + c, c <= cb
+  int ic_cb = 0, ic_c = 0;  // the next chunk to issue
+  auto issue = [&]() {
+    const int i = ic_cb * (ic_cb + 1) / 2 + ic_c;
+    if (i < nchunks) {
+      float *dst = S + (i % NBUF) * TS_CHUNK;
+      const float *src = Lkk + (size_t)(ic_c * B) * nb + ic_cb * B;
+      for (int e = tid; e < TS_CHUNK / 4; e += NTH) {
+        const int pc = e >> 3, q = (e & 7) * 4;  // chunk column pc, rows q .. q+3
+        cp_async16(dst + pc * B + q, src + (size_t)pc * nb + q);
+      }
+      if (++ic_c > ic_cb) {
+        ic_cb++;
+        ic_c = 0;
+      }
+    }
+    cp_async_commit();  // an empty group at the tail keeps the count uniform
+  };
+  for (int u = 0; u < NBUF - 1; u++) issue();
 #pragma unroll 8
   for (int e = tid; e < ROWS * nb; e += NTH) {
     int r = e % ROWS, c = e / ROWS;
     X[r * ldx + c] = A[r + (size_t)c * nb];
   }
-  int nbb = nb / B;
-  for (int cb = 0; cb < nbb; cb++) {
-    const float *Lrow = Lkk + cb * B + lane;  // row cb*32 + lane of L_kk
-    float ld[B];
-#pragma unroll
-    for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.f;
-    __syncthreads();  // X of the previous column blocks is complete
-    float a[RPW], b[RPW];
-#pragma unroll
-    for (int q = 0; q < RPW; q++) {
-      a[q] = X[(w + NW * q) * ldx + cb * B + lane];
-      b[q] = 0.f;  // second accumulators halve the FMA chains
-    }
-    for (int p0 = 0; p0 < cb * B; p0 += TS_STRIP) {
-      int pw = min(TS_STRIP, cb * B - p0);
-      // all of this thread's strip loads in flight before the first store
-      {
-        constexpr int PER = TS_STRIP / NW;
-        float v[PER];
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-          int pp = w + NW * u;
-          v[u] = (pp < pw) ? Lrow[(size_t)(p0 + pp) * nb] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-          int pp = w + NW * u;
-          if (pp < pw) S[lane * lds + pp] = v[u];
-        }
-      }
-      __syncthreads();
-      const float *sl = S + lane * lds;
-#pragma unroll 4
-      for (int p = 0; p < pw; p += 2) {
-        float l0 = sl[p], l1 = sl[p + 1];
+  int i = 0;
+  for (int cb = 0; cb < nbc; cb++) {
+    float a0[RPW], a1[RPW], a2[RPW], a3[RPW];
+    for (int c = 0; c <= cb; c++, i++) {
+      cp_async_wait<NBUF - 2>();  // this thread's copies of chunk i have landed
+      __syncthreads();            // everyone's; and chunk i-1's buffer is free
+      issue();
+      const float *Sc = S + (i % NBUF) * TS_CHUNK;
+      if (c == 0) {
 #pragma unroll
         for (int q = 0; q < RPW; q++) {
-          const float *xq = X + (w + NW * q) * ldx + p0;
-          a[q] -= xq[p] * l0;
-          b[q] -= xq[p + 1] * l1;
+          a0[q] = X[(w + NW * q) * ldx + cb * B + lane];
+          a1[q] = a2[q] = a3[q] = 0.f;
         }
       }
-      __syncthreads();
-    }
-    float mydiag = ld[0];
+      if (c < cb) {
 #pragma unroll
-    for (int p = 1; p < B; p++)
-      if (p == lane) mydiag = ld[p];
-    float myrinv = 1.0f / mydiag;
+        for (int q = 0; q < RPW; q++) {
+          const float4 *xq = reinterpret_cast<const float4 *>(X + (w + NW * q) * ldx + c * B);
 #pragma unroll
-    for (int q = 0; q < RPW; q++) a[q] += b[q];
+          for (int p4 = 0; p4 < B / 4; p4++) {
+            const float4 xv = xq[p4];
+            a0[q] -= xv.x * Sc[(4 * p4 + 0) * B + lane];
+            a1[q] -= xv.y * Sc[(4 * p4 + 1) * B + lane];
+            a2[q] -= xv.z * Sc[(4 * p4 + 2) * B + lane];
+            a3[q] -= xv.w * Sc[(4 * p4 + 3) * B + lane];
+          }
+        }
+      } else {
+        // diagonal chunk: ld[p] = L_kk(cb*32 + lane, cb*32 + p) for p <= lane
+        float ld[B];
 #pragma unroll
-    for (int j = 0; j < B; j++) {
-      float rj = __shfl_sync(0xffffffffu, myrinv, j);
+        for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Sc[p * B + lane] : 0.f;
+        float mydiag = ld[0];
 #pragma unroll
-      for (int q = 0; q < RPW; q++) {
-        float xj = __shfl_sync(0xffffffffu, a[q], j) * rj;
-        if (lane == j) a[q] = xj;
-        if (lane > j) a[q] -= xj * ld[j];
+        for (int p = 1; p < B; p++)
+          if (p == lane) mydiag = ld[p];
+        const float myrinv = 1.0f / mydiag;
+        float a[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; q++) a[q] = (a0[q] + a1[q]) + (a2[q] + a3[q]);
+#pragma unroll
+        for (int j = 0; j < B; j++) {
+          float rj = __shfl_sync(0xffffffffu, myrinv, j);
+#pragma unroll
+          for (int q = 0; q < RPW; q++) {
+            float xj = __shfl_sync(0xffffffffu, a[q], j) * rj;
+            if (lane == j) a[q] = xj;
+            if (lane > j) a[q] -= xj * ld[j];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; q++) X[(w + NW * q) * ldx + cb * B + lane] = a[q];
       }
     }
-#pragma unroll
-    for (int q = 0; q < RPW; q++) X[(w + NW * q) * ldx + cb * B + lane] = a[q];
   }
+  cp_async_wait<0>();
   __syncthreads();
   // FP32 master (column-major) and the sender-side BF16 pieces (row-major)
 #pragma unroll 8
@@ -279,8 +304,8 @@ __global__ void __launch_bounds__(NW * 32)
   }
 }
 
-static size_t trsm32_smem(int nb, int rows) {
-  return (size_t)(rows * (nb + TS_LD_PAD) + 32 * (TS_STRIP + 1)) * sizeof(float);
+static size_t trsm32_smem(int nb, int rows, int nbuf) {
+  return (size_t)(nbuf * TS_CHUNK + rows * (nb + TS_LD_PAD)) * sizeof(float);
 }
 
 // z pieces for the sampler: zp[q][n][k] = piece q of Z[k][n], n < s_pad
@@ -388,6 +413,7 @@ struct StepPlan {
   int i_off[GR_N] = {}, i_n[GR_N] = {};            // tensor-core items per update group
   double flops[GR_N] = {}, mma[GR_N] = {};
   bool diag_low = false;
+  bool fp64_panel = false;  // FP64-class TRSM or SYRK on the critical or panel stream
 };
 
 struct MixedPlan {
@@ -414,7 +440,6 @@ struct MixedPlan {
   int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
   int *d_qtiles = nullptr;            // panel tiles quantized to E4M3, per step (see StepPlan)
   bool any_e4m3 = false;
-  bool crit64 = false;  // FP64-class TRSM or SYRK on the critical path (see kReservedSMs)
   gemm_tc::Operands ops;
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
@@ -582,7 +607,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         qtiles.push_back((int)tile_index(i, k, NT));
         sp.nq_r++;
       }
-    if (sp.n64_1 > 0 || sp.p_n[GR_S] > 0) P->crit64 = true;
+    sp.fp64_panel = sp.n64_1 > 0 || sp.n64_r > 0 || sp.p_n[GR_S] > 0;
     sp.z1_off = (int)zjobs.size();
     zjobs.insert(zjobs.end(), z1_step.begin(), z1_step.end());
     sp.z1_n = (int)z1_step.size();
@@ -668,14 +693,14 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   return EMU_OK;
 }
 
-// SMs the bulk trailing update leaves to the critical-path kernels.  The
-// persistent bulk GEMM holds about 217 KB of shared memory per SM, so the
-// FP64 panel TRSM and FP64 SYRK of the critical path (more shared memory than
-// is left beside it) run only on these.  When the plan puts FP64-class work on
-// the critical path the critical stream bounds the factor and gets more SMs;
-// otherwise the bulk update is the bound and keeps them.
+// SMs the bulk trailing update leaves to the critical-path and panel
+// kernels.  The persistent bulk GEMM holds about 217 KB of shared memory per
+// SM, so the panel TRSMs and the FP64-class SYRK (more shared memory than is
+// left beside it) run only on these.  While FP64-class TRSMs or SYRKs are
+// near (the first panels of a covariance) they bound the factor and get more
+// SMs; afterwards the bulk update is the bound and keeps them.
 constexpr int kReservedSMs = 16;
-constexpr int kReservedSMsCrit64 = 32;
+constexpr int kReservedSMsFP64 = 32;
 
 // Internal streams of the mixed schedule (created once per context) and at
 // least `nev` ordering events.
@@ -749,11 +774,11 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   cudaEvent_t ev_start = ctx->sched_ev[EV * NT], ev_end = ctx->sched_ev[EV * NT + 1];
   EMU_CUDA_TRY(ctx, cudaEventRecord(ev_start, user));
   for (cudaStream_t q : {ctx->crit, ctx->mid, ctx->bulk}) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(q, ev_start, 0));
-  size_t tsm16 = trsm32_smem(nb, 16), tsm4 = trsm32_smem(nb, 4);
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tsm16));
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tsm4));
+  size_t tsm16 = trsm32_smem(nb, 16, TS_NBUF_PANEL), tsm4 = trsm32_smem(nb, 4, TS_NBUF_CRIT);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2, TS_NBUF_PANEL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm16));
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<4, 1, TS_NBUF_CRIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm4));
 
   // TRSM of the listed rows of panel k (FP64 rows on the FP64 pipe, then split)
   auto quantize = [&](int q0, int nq) -> emu_status {
@@ -781,11 +806,11 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
       ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
       const float *lkk = P->d_lkk32 + (size_t)(k & 1) * te;
       if (critical)
-        k_trsm32_panel<4, 1><<<dim3(nb / 4, n32), 128, tsm4, ctx->stream>>>(lkk, A->t32, A->op_bf16, nb, NT, k,
-                                                                           P->d_rows32 + r32, st);
+        k_trsm32_panel<4, 1, TS_NBUF_CRIT><<<dim3(nb / 4, n32), 128, tsm4, ctx->stream>>>(
+            lkk, A->t32, A->op_bf16, nb, NT, k, P->d_rows32 + r32, st);
       else
-        k_trsm32_panel<8, 2><<<dim3(nb / 16, n32), 256, tsm16, ctx->stream>>>(lkk, A->t32, A->op_bf16, nb, NT, k,
-                                                                             P->d_rows32 + r32, st);
+        k_trsm32_panel<8, 2, TS_NBUF_PANEL><<<dim3(nb / 16, n32), 256, tsm16, ctx->stream>>>(
+            lkk, A->t32, A->op_bf16, nb, NT, k, P->d_rows32 + r32, st);
       EMU_LAUNCHED(ctx);
     }
     return e;
@@ -850,7 +875,11 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     // free for the critical and panel streams' kernels
     ctx->stream = ctx->bulk;
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->bulk, ev(k, E_T), 0));
-    int bulk_ctas = std::max(1, ctx->sm_count - (P->crit64 ? kReservedSMsCrit64 : kReservedSMs));
+    // the bulk GEMMs of step k run beside the critical and panel work of
+    // steps k and k+1: while that has FP64-class TRSMs or SYRKs (FP64-pipe
+    // bound, too much shared memory to fit beside the GEMM) more SMs stay free
+    const bool fp64_near = sp.fp64_panel || (k + 1 < NT && P->steps[k + 1].fp64_panel);
+    int bulk_ctas = std::max(1, ctx->sm_count - (fp64_near ? kReservedSMsFP64 : kReservedSMs));
     if ((s = update_group(k, GR_G2A, bulk_ctas)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G2), ctx->bulk));
     if ((s = update_group(k, GR_G2, bulk_ctas)) != EMU_OK) break;
@@ -1153,13 +1182,13 @@ emu_status launch_diag_to_f32_slots(emu_ctx *ctx, const double *t64, float *slot
 emu_status launch_trsm32_jobs(emu_ctx *ctx, const float *slots, float *t32, uint16_t *op, int nb, const int2 *d_jobs,
                               int njobs) {
   if (njobs <= 0) return EMU_OK;
-  size_t sm = trsm32_smem(nb, 16);
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm));
+  size_t sm = trsm32_smem(nb, 16, TS_NBUF_PANEL);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<8, 2, TS_NBUF_PANEL, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM32, njobs * nb3, 14.0 * njobs * nb * nb);
-  k_trsm32_panel<8, 2, true><<<dim3(nb / 16, njobs), 256, sm, ctx->stream>>>(slots, t32, op, nb, 0, 0, nullptr,
-                                                                             ctx->d_status, d_jobs);
+  k_trsm32_panel<8, 2, TS_NBUF_PANEL, true><<<dim3(nb / 16, njobs), 256, sm, ctx->stream>>>(
+      slots, t32, op, nb, 0, 0, nullptr, ctx->d_status, d_jobs);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
