@@ -6,6 +6,11 @@ POTRF (``emu_trace_*``) and the per-stream timeline of the kernel groups
 
 Prints a short text summary; ``--save PREFIX`` also writes the raw arrays as
 ``PREFIX_tasks.npy`` and ``PREFIX_timeline.npy``.
+
+Records: one per worker task (TRSM, UPD) and one per step of the chain
+(``LT``: the 16-column step run by the master CTA, from its start to its end).
+Tracing adds global stores inside the kernel, which the publishing fences then
+wait for, so traced times run longer than untraced ones.
 """
 from __future__ import annotations
 
@@ -15,7 +20,7 @@ import numpy as np
 
 from . import PROF_GROUPS, Context, emu_cov_build, emu_potrf_mp
 
-KINDS = ("LEAF", "TRSM", "UPD")
+KINDS = ("LT", "TRSM", "UPD")
 STREAMS = ("ctx", "crit", "panel", "bulk")
 
 
@@ -26,6 +31,9 @@ def summarize_tasks(tr: np.ndarray, ntiles: int) -> list[str]:
     per = len(tr) // ntiles
     for k in sorted({0, ntiles // 2, ntiles - 1}):
         t = tr[k * per:(k + 1) * per].astype(np.int64)
+        t = t[t[:, 4] > 0]  # records that were written (the master task itself has none)
+        if len(t) == 0:
+            continue
         kind = t[:, 0] & 0xFF
         t0 = t[:, 2].min()
         ready, done = t[:, 3] - t0, t[:, 4] - t0
@@ -36,7 +44,7 @@ def summarize_tasks(tr: np.ndarray, ntiles: int) -> list[str]:
                 line += f"; {nm} n={int(m.sum())} work {((done - ready)[m]).mean() / 1e3:.2f} us"
         leaf = np.sort(done[kind == 0])
         if len(leaf) > 1:
-            line += f"; leaf-to-leaf {np.diff(leaf).mean() / 1e3:.1f} us"
+            line += f"; LT step {np.median(np.diff(leaf)) / 1e3:.1f} us (median)"
         out.append(line)
     return out
 
