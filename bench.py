@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-bands", action="store_true", help="skip the paper's band-map variants (DP/SP, DP/SP/HP, "
+                                                             "DP/HP) of the same factor")
     ap.add_argument("--workload", choices=["single", "batched"], default="single",
                     help="single: one n=L^2 covariance (default); batched: --count covariances of random "
                          "bandlimit L in [8, 64], beta in [2, 8) (SplitMix64 draws from --batch-seed)")
@@ -234,6 +236,9 @@ def run_ours(a):
             extra["speedup_vs_fp64"] = round(i64.ms / mixed_factor_ms, 2)
             extra["cusolver_dpotrf"] = cusolver_reference(E, ctx, a, flops)
 
+        if not a.no_bands:
+            extra["band_maps"] = band_variants(E, ctx, a, flops, extra.get("fp64_factor_ms"))
+
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
 
     cpu = None if (a.no_cpu or world > 1) else cpu_baseline(a)
@@ -307,7 +312,7 @@ def roofline(prof: dict, peaks: dict) -> dict:
             "launches": g["launches"]}
 
 
-def backward_error_rows(E, ctx, a, rows: int) -> float:
+def backward_error_rows(E, ctx, a, rows: int, band: int = 0) -> float:
     import torch
 
     n = a.L * a.L
@@ -316,7 +321,7 @@ def backward_error_rows(E, ctx, a, rows: int) -> float:
     S.free()
     Sd = Sd + Sd.t() - torch.diag(torch.diag(Sd))
     A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
-    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16, band=band)
     Ld = E.emu_mat_export(ctx, A)
     A.free()
     g = torch.Generator().manual_seed(7)
@@ -326,6 +331,38 @@ def backward_error_rows(E, ctx, a, rows: int) -> float:
     del Sd, Ld, R
     torch.cuda.empty_cache()
     return be
+
+
+def band_variants(E, ctx, a, flops, fp64_ms) -> dict:
+    """The paper's band-map precision variants of the same factor (diagonal band
+    FP64; DP/SP: the rest FP32; DP/SP/HP: 5 % of the tiles FP32 in the bands
+    next to the diagonal, the rest BF16; DP/HP: the rest BF16): factor time
+    (median of two after a warm-up), class counts and the sampled-row backward
+    error.  Their accuracy is what the map gives, not a requested eps."""
+    out = {}
+    for band in (E.MAP_DP_SP, E.MAP_DP_SP_HP, E.MAP_DP_HP):
+        ts, info = [], None
+        for r in range(3):
+            A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+            info = E.emu_potrf_mp(ctx, A, band=band, raise_on_error=False)
+            A.free()
+            if info.status != E.EMU_OK:
+                break
+            if r:
+                ts.append(info.ms)
+        name = E.MAP_NAMES[band]
+        if info.status != E.EMU_OK:
+            out[name] = {"status": int(info.status),
+                         "pivot": info.pivot}
+            continue
+        fms = statistics.median(ts)
+        d = {"factor_ms": round(fms, 3), "tflops": round(flops / (fms * 1e-3) / 1e12, 3),
+             "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)),
+             "backward_error_rows64": backward_error_rows(E, ctx, a, rows=64, band=band)}
+        if fp64_ms:
+            d["speedup_vs_fp64"] = round(fp64_ms / fms, 2)
+        out[name] = d
+    return out
 
 
 def cusolver_reference(E, ctx, a, flops) -> dict:

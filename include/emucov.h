@@ -87,18 +87,37 @@ typedef struct {
   double nugget_rel;
 } emu_cov_params;
 
+/* Band-based precision maps of the paper's experiments ("Performance
+ * Results": DP, DP/SP, DP/SP/HP with 5 % SP, DP/HP), with SP the "fp32" class
+ * and HP the "bf16" class.  In every map the diagonal band (tiles i == j) is
+ * FP64.  DP/SP: all other tiles fp32.  DP/HP: all other tiles bf16.
+ * DP/SP/HP: the sub-diagonal bands i - j = 1 .. b are fp32 and the rest bf16,
+ * b the fewest whole bands that hold at least sp_frac of the NT(NT+1)/2
+ * tiles (sp_frac == 0 means 0.05; sp_frac < 0 gives b = 0). */
+enum {
+  EMU_MAP_NORM = 0,     /* the per-tile norm rule (eps, prec_mask, u) */
+  EMU_MAP_DP_SP = 1,
+  EMU_MAP_DP_SP_HP = 2,
+  EMU_MAP_DP_HP = 3
+};
+
 /* Options of the factorisation ("Mixed-Precision Computation Innovations").
- * eps <= 0 selects the plain FP64 tile Cholesky.  eps > 0 selects the adaptive
- * per-tile precision: tile (i,j) runs in the least precise class c allowed by
- * prec_mask for which ||S_ij||_F * u[c] <= eps * ||S||_F / NT (NT = number of
- * tile rows, ||S||_F over the full symmetric matrix); FP64 when none passes.
- * The diagonal POTRF is always FP64.  diag_fp64 != 0 also pins the diagonal
- * tiles' storage and updates to FP64.  u[c] <= 0 takes the default. */
+ * With band = EMU_MAP_NORM: eps <= 0 selects the plain FP64 tile Cholesky;
+ * eps > 0 selects the adaptive per-tile precision: tile (i,j) runs in the
+ * least precise class c allowed by prec_mask for which
+ * ||S_ij||_F * u[c] <= eps * ||S||_F / NT (NT = number of tile rows, ||S||_F
+ * over the full symmetric matrix); FP64 when none passes.  diag_fp64 != 0
+ * also pins the diagonal tiles' storage and updates to FP64.  u[c] <= 0 takes
+ * the default.  band = EMU_MAP_DP_SP .. EMU_MAP_DP_HP selects a band map
+ * instead (eps, prec_mask, diag_fp64 and u are then not used; sp_frac == 0
+ * means 0.05).  The diagonal POTRF is always FP64. */
 typedef struct {
   double eps;
   unsigned prec_mask; /* bit c enables class c; bit 0 (FP64) is implied */
   int diag_fp64;
   double u[EMU_NCLASS];
+  int band;           /* EMU_MAP_* */
+  double sp_frac;     /* DP/SP/HP: least fraction of the tiles in fp32 bands */
 } emu_mp_opts;
 
 typedef struct {

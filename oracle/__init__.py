@@ -65,6 +65,8 @@ def _declare(L):
     L.orc_frob_from_tiles.argtypes = [i, dp]
     L.orc_frob_from_tiles.restype = d
     L.orc_precision_map.argtypes = [i, dp, d, dp, i, ctypes.c_uint, i, u8p]
+    L.orc_precision_map_band.argtypes = [i, i, d, u8p]
+    L.orc_precision_map_band.restype = i
     L.orc_potrf_unblocked.argtypes = [i, dp, lg]
     L.orc_potrf_unblocked.restype = i
     L.orc_potrf_blocked.argtypes = [i, i, dp, lg, i]
@@ -135,6 +137,13 @@ def precision_map(t, eps: float, u, mask: int, diag_fp64: bool = False):
     lib().orc_precision_map(NT, _dp(t), eps, _dp(u), len(u), mask, int(diag_fp64),
                             cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return cls
+
+
+def precision_map_band(NT: int, band: int, sp_frac: float = 0.05):
+    """Band map of the paper's variants (1 DP/SP, 2 DP/SP/HP, 3 DP/HP): (classes NT x NT, number of SP bands)."""
+    cls = np.zeros((NT, NT), dtype=np.uint8, order="F")
+    nsp = lib().orc_precision_map_band(NT, band, sp_frac, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return cls, nsp
 
 
 def potrf_unblocked(A):

@@ -131,6 +131,42 @@ void orc_precision_map(int NT, const double *t, double eps, const double *u,
     }
 }
 
+/* Band-based precision maps of the paper's experiments ("Performance Results"
+ * section: DP, DP/SP, DP/SP/HP with 5 % SP, DP/HP).  band: 1 DP/SP, 2
+ * DP/SP/HP, 3 DP/HP.  Classes: 0 FP64 (DP), 1 FP32 (SP), 3 BF16 (HP).  The
+ * diagonal band is DP.  For DP/SP/HP the SP tiles are whole sub-diagonal
+ * bands nearest the diagonal, as few as hold at least sp_frac of the
+ * NT (NT + 1) / 2 lower tiles; the bands beyond are HP.  Returns that number
+ * of SP bands (0 for the other maps).  Upper tiles get 255. */
+int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls) {
+  int nsp = 0;
+  if (band == 2 && sp_frac > 0.0) {
+    /* count tiles band by band until the SP share is reached */
+    double total = 0.5 * (double)NT * (double)(NT + 1);
+    long in_sp = 0;
+    while (nsp < NT - 1 && (double)in_sp < sp_frac * total) {
+      nsp++;
+      in_sp += NT - nsp; /* band d holds the NT - d tiles (j + d, j) */
+    }
+  }
+  for (int j = 0; j < NT; j++)
+    for (int i = 0; i < NT; i++) {
+      unsigned char c;
+      if (i < j)
+        c = 255;
+      else if (i == j)
+        c = 0;
+      else if (band == 1)
+        c = 1;
+      else if (band == 3)
+        c = 3;
+      else
+        c = (i - j <= nsp) ? 1 : 3;
+      cls[i + (size_t)j * NT] = c;
+    }
+  return nsp;
+}
+
 /* -------------------------------------------------------------- Cholesky */
 int orc_potrf_unblocked(int n, double *A, long ld) {
   /* Cholesky-Banachiewicz: row i of L from rows 0..i-1. */

@@ -63,6 +63,7 @@ double orc_frob_from_tiles(int NT, const double *t);
 void orc_precision_map(int NT, const double *t, double eps, const double *u,
                        int nclass, unsigned mask, int diag_fp64,
                        unsigned char *cls);
+int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls);
 
 /* Unblocked Cholesky (row-by-row, the textbook Cholesky-Banachiewicz form):
  * A = L L^T, L lower with positive diagonal, overwritten in place.

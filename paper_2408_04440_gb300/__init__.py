@@ -27,6 +27,9 @@ NCLASS = 5
 CLASS_NAMES = ("fp64", "fp32", "tf32", "bf16", "e4m3")
 # u[c] <= 0 asks the library for its default unit roundoff of class c
 DEFAULT_U = (0.0,) * 5
+# precision maps: the norm rule, or the paper's band variants (DP/SP, DP/SP/HP, DP/HP)
+MAP_NORM, MAP_DP_SP, MAP_DP_SP_HP, MAP_DP_HP = range(4)
+MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
@@ -56,7 +59,7 @@ class emu_cov_params(ctypes.Structure):
 
 class emu_mp_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("prec_mask", ctypes.c_uint), ("diag_fp64", ctypes.c_int),
-                ("u", ctypes.c_double * NCLASS)]
+                ("u", ctypes.c_double * NCLASS), ("band", ctypes.c_int), ("sp_frac", ctypes.c_double)]
 
 
 class emu_factor_info(ctypes.Structure):
@@ -326,14 +329,17 @@ class FactorInfo:
     ms: float = 0.0
 
 
-def mp_opts(eps: float = 0.0, prec_mask: int = 0b01011, diag_fp64: bool = False, u=None) -> emu_mp_opts:
+def mp_opts(eps: float = 0.0, prec_mask: int = 0b01011, diag_fp64: bool = False, u=None, band: int = MAP_NORM,
+            sp_frac: float = 0.0) -> emu_mp_opts:
     uu = (ctypes.c_double * NCLASS)(*(u if u is not None else DEFAULT_U))
-    return emu_mp_opts(eps, prec_mask, int(diag_fp64), uu)
+    return emu_mp_opts(eps, prec_mask, int(diag_fp64), uu, int(band), float(sp_frac))
 
 
 def emu_potrf_mp(ctx: Context, A: Mat, eps: float = 0.0, prec_mask: int = 0b01011, diag_fp64: bool = False,
-                 u=None, raise_on_error: bool = True) -> FactorInfo:
-    o = mp_opts(eps, prec_mask, diag_fp64, u)
+                 u=None, raise_on_error: bool = True, band: int = MAP_NORM, sp_frac: float = 0.0) -> FactorInfo:
+    """band = MAP_NORM: eps <= 0 plain FP64, eps > 0 the norm rule; MAP_DP_SP / MAP_DP_SP_HP / MAP_DP_HP: the
+    band maps (sp_frac 0 means 0.05)."""
+    o = mp_opts(eps, prec_mask, diag_fp64, u, band, sp_frac)
     info = emu_factor_info()
     s = ctx.lib.emu_potrf_mp(ctx.h, A.h, ctypes.byref(o), ctypes.byref(info))
     fi = FactorInfo(s, info.n, info.nb, info.nt, info.pivot, list(info.tiles), list(info.update_flops),
@@ -406,7 +412,7 @@ def emu_solve_refine(ctx: Context, L: Mat, S: Mat, B, tol: float = 1e-14, maxit:
 
 def emu_batch_potrf_sample(ctx: Context, params, nb: int = 256, eps: float = 0.0, prec_mask: int = 0b01011,
                            diag_fp64: bool = False, u=None, nsamples: int = 0, seed: int = 0, want_L: bool = False,
-                           raise_on_error: bool = True, out_Y=None):
+                           raise_on_error: bool = True, out_Y=None, band: int = MAP_NORM, sp_frac: float = 0.0):
     """params: sequence of (L, beta) or (L, beta, sigma_exp, nugget_rel).
     Returns (Ys, Ls, infos, status): lists of column-major CUDA tensors
     (n_b x nsamples and n_b x n_b; None where not asked) and FactorInfo.
@@ -423,7 +429,7 @@ def emu_batch_potrf_sample(ctx: Context, params, nb: int = 256, eps: float = 0.0
     Ls = [_colmajor_empty(int(q[0]) ** 2, int(q[0]) ** 2, ctx.device) for q in params] if want_L else None
     yp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ys]) if Ys else None
     lp = (ctypes.c_void_p * count)(*[_ptr(t) for t in Ls]) if Ls else None
-    o = mp_opts(eps, prec_mask, diag_fp64, u)
+    o = mp_opts(eps, prec_mask, diag_fp64, u, band, sp_frac)
     infos = (emu_factor_info * count)()
     s = ctx.lib.emu_batch_potrf_sample(ctx.h, count, P, nb, ctypes.byref(o), nsamples, seed,
                                        ctypes.cast(yp, ctypes.c_void_p) if yp else None,

@@ -328,7 +328,7 @@ emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda, 
     if (e == cudaSuccess) s = launch_import_col(ctx, A, j, stage, n - r0);
   }
   if (stage) cudaFreeAsync(stage, ctx->stream);
-  if (e == cudaSuccess && s == EMU_OK) s = launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+  if (e == cudaSuccess && s == EMU_OK) s = launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
   if (e == cudaSuccess && s == EMU_OK) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "import_host");
   if (s != EMU_OK) {
@@ -444,7 +444,9 @@ extern "C" emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *
                                    emu_factor_info *info) {
   if (!ctx || !A) return EMU_EINVAL;
   if (A->state != MAT_COV) return fail_msg(ctx, EMU_ESTATE, "matrix is already factored");
-  bool mixed = o && o->eps > 0.0;
+  if (o && (o->band < EMU_MAP_NORM || o->band > EMU_MAP_DP_HP))
+    return fail_msg(ctx, EMU_EINVAL, "unknown precision map");
+  bool mixed = o && (o->eps > 0.0 || o->band != EMU_MAP_NORM);
   EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), ctx->stream));
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));

@@ -84,6 +84,8 @@ struct BatchState {
   double eps = 0.0, u[EMU_NCLASS] = {};
   unsigned mask = 0;
   int diag_fp64 = 0;
+  int band = EMU_MAP_NORM;
+  double sp_frac = 0.0;
   // layout
   int count = 0, maxNT = 0, maxL = 0, s_pad = 0;
   long ntiles = 0, nrows = 0, ntab = 0;
@@ -579,6 +581,8 @@ struct TuneRec {
   double eps;
   unsigned mask;
   int diag_fp64, s;
+  int band;
+  double sp_frac;
   bool want_L;
   int nb;
 };
@@ -705,9 +709,9 @@ emu_status batch_capture(emu_ctx *ctx, BatchCtx *BC, BatchState *B) {
 }
 
 bool state_matches(const BatchState *B, int count, const emu_cov_params *p, int nb, const double *u, double eps,
-                   unsigned mask, int diag_fp64, int s, bool want_L) {
+                   unsigned mask, int diag_fp64, int band, double sp_frac, int s, bool want_L) {
   if (!B || B->count != count || B->nb != nb || B->s != s || B->want_L != want_L || B->eps != eps ||
-      B->mask != mask || B->diag_fp64 != diag_fp64)
+      B->mask != mask || B->diag_fp64 != diag_fp64 || B->band != band || B->sp_frac != sp_frac)
     return false;
   for (int c = 0; c < EMU_NCLASS; c++)
     if (B->u[c] != u[c]) return false;
@@ -724,6 +728,8 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   double u[EMU_NCLASS] = {0x1p-53, 0x1p-24 * std::sqrt((double)nb), 0x1p-11, 0x1p-8, 0x1p-4};
   unsigned mask = 1u;
   int diag_fp64 = o ? o->diag_fp64 : 0;
+  const int band = o ? o->band : EMU_MAP_NORM;
+  const double sp_frac = o ? band_sp_frac(o) : 0.05;
   if (eps > 0.0) {
     for (int c = 0; c < EMU_NCLASS; c++)
       if (o->u[c] > 0.0) u[c] = o->u[c];
@@ -732,7 +738,7 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   }
   bool want_L = dL != nullptr;
   BatchState *B = BC->state;
-  bool reuse = state_matches(B, count, p, nb, u, eps, mask, diag_fp64, nsamples, want_L);
+  bool reuse = state_matches(B, count, p, nb, u, eps, mask, diag_fp64, band, sp_frac, nsamples, want_L);
   emu_status s;
   if (!reuse) {
     if (B) {
@@ -745,6 +751,8 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
     B->eps = eps;
     B->mask = mask;
     B->diag_fp64 = diag_fp64;
+    B->band = band;
+    B->sp_frac = sp_frac;
     std::memcpy(B->u, u, sizeof(u));
     if ((s = batch_layout(ctx, B, count, p, nb)) != EMU_OK) return s;
   }
@@ -754,7 +762,7 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
                                   B->t64, B->partial)) != EMU_OK)
     return s;
   if ((s = launch_precision_map_batch(ctx, B->d_inst, count, nb, B->partial, B->tnorm, B->frob, B->d_cls, eps, u,
-                                      mask, diag_fp64)) != EMU_OK)
+                                      mask, diag_fp64, band, sp_frac)) != EMU_OK)
     return s;
   std::vector<unsigned char> cls(B->ntiles);
   std::vector<double> frob(count);
@@ -769,6 +777,8 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
     nbs->eps = eps;
     nbs->mask = mask;
     nbs->diag_fp64 = diag_fp64;
+    nbs->band = band;
+    nbs->sp_frac = sp_frac;
     std::memcpy(nbs->u, u, sizeof(u));
     B->release();
     delete B;
@@ -862,6 +872,10 @@ emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params 
                                   int nsamples, uint64_t seed, double *const *dY, double *const *dL,
                                   emu_factor_info *infos) {
   if (!ctx || count < 1 || !p || nsamples < 0 || (nsamples > 0 && !dY)) return EMU_EINVAL;
+  if (o && (o->band < EMU_MAP_NORM || o->band > EMU_MAP_DP_HP)) {
+    ctx->last_error = "unknown precision map";
+    return EMU_EINVAL;
+  }
   if (!(nb == 0 || (nb >= 256 && nb <= 1024 && nb % 256 == 0))) {
     ctx->last_error = "batch tile size must be 0 (tuned) or a multiple of 256 in [256, 1024]";
     return EMU_EINVAL;
@@ -883,8 +897,11 @@ emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params 
   double eps = o ? o->eps : 0.0;
   unsigned mask = o ? o->prec_mask : 1u;
   int diag = o ? o->diag_fp64 : 0;
+  const int band = o ? o->band : EMU_MAP_NORM;
+  const double sp_frac = o ? band_sp_frac(o) : 0.05;
   for (const TuneRec &t : BC->tuned) {
     if (t.params.size() != (size_t)count || t.eps != eps || t.mask != mask || t.diag_fp64 != diag ||
+        t.band != band || t.sp_frac != sp_frac ||
         t.s != nsamples || t.want_L != (dL != nullptr))
       continue;
     bool same = true;
@@ -910,6 +927,8 @@ emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params 
   t.eps = eps;
   t.mask = mask;
   t.diag_fp64 = diag;
+  t.band = band;
+  t.sp_frac = sp_frac;
   t.s = nsamples;
   t.want_L = dL != nullptr;
   t.nb = best;

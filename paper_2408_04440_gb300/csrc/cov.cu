@@ -209,12 +209,37 @@ __global__ void __launch_bounds__(kThreads)
 
 // Single CTA: tile norms from the partial sums (fixed order), ||S||_F, and
 // the class of each tile under the rule t_ij * u[c] <= eps * ||S||_F / NT.
+// Band maps of the paper's precision variants (EMU_MAP_*): the diagonal band
+// FP64; DP/SP: the rest FP32; DP/HP: the rest BF16; DP/SP/HP: sub-diagonal
+// bands 1 .. nsp FP32, the rest BF16.
+__device__ inline int band_class(int band, int i, int j, int nsp) {
+  const int d = i - j;
+  if (d == 0) return EMU_CLASS_FP64;
+  if (band == EMU_MAP_DP_SP) return EMU_CLASS_FP32;
+  if (band == EMU_MAP_DP_HP) return EMU_CLASS_BF16;
+  return d <= nsp ? EMU_CLASS_FP32 : EMU_CLASS_BF16;
+}
+// The fewest whole sub-diagonal bands (band d holds NT - d tiles) that hold
+// at least frac of the NT (NT + 1) / 2 lower tiles.
+__device__ inline int sp_bands(int NT, double frac) {
+  if (!(frac > 0.0)) return 0;
+  const double need = frac * 0.5 * (double)NT * (double)(NT + 1);
+  long have = 0;
+  int b = 0;
+  while (b < NT - 1 && (double)have < need) {
+    b++;
+    have += NT - b;
+  }
+  return b;
+}
+
 __global__ void __launch_bounds__(1024)
     k_precision_map(int NT, long ntiles, int nchunk,
                     const double *__restrict__ partial, double *__restrict__ tnorm,
                     double *__restrict__ frob, unsigned char *__restrict__ cls,
                     double eps, double u1, double u2, double u3, double u4,
-                    unsigned mask, int diag_fp64, const BatchInst *__restrict__ inst) {
+                    unsigned mask, int diag_fp64, int band, double sp_frac,
+                    const BatchInst *__restrict__ inst) {
   __shared__ double sh[32];
   if (inst) {
     // batch: one CTA per matrix, its tiles at tile_base
@@ -244,6 +269,15 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   if (cls == nullptr) return;
+  if (band != EMU_MAP_NORM) {
+    const int nsp = sp_bands(NT, sp_frac);
+    for (long t = threadIdx.x; t < ntiles; t += blockDim.x) {
+      int i, j;
+      tile_coords(t, NT, &i, &j);
+      cls[t] = (unsigned char)band_class(band, i, j, nsp);
+    }
+    return;
+  }
   double thr = eps * s_frob / (double)NT;
   const double uu[EMU_NCLASS] = {0.0, u1, u2, u3, u4};
   for (long t = threadIdx.x; t < ntiles; t += blockDim.x) {
@@ -336,7 +370,7 @@ emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p) {
                                                  A->t64, A->d_partial);
   EMU_LAUNCHED(ctx);
   EMU_CUDA_TRY(ctx, cudaFreeAsync(buf, ctx->stream));
-  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
 }
 
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {
@@ -344,7 +378,7 @@ emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {
   k_import<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, dA, lda, A->t64,
                                               A->d_partial);
   EMU_LAUNCHED(ctx);
-  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0);
+  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
 }
 
 emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS, long ld) {
@@ -356,12 +390,12 @@ emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS,
 
 // With u == nullptr only the norms and ||S||_F are (re)computed.
 emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
-                                const double *u, unsigned mask, int diag_fp64) {
+                                const double *u, unsigned mask, int diag_fp64, int band, double sp_frac) {
   ProfScope ps(ctx, PROF_MAP, 0.0, 8.0 * A->ntiles * (A->nchunk + 1));
   k_precision_map<<<1, 1024, 0, ctx->stream>>>(
       A->nt, A->ntiles, A->nchunk, A->d_partial, A->d_tnorm, A->d_frob,
       u ? A->d_cls : nullptr, eps, u ? u[1] : 0.0, u ? u[2] : 0.0,
-      u ? u[3] : 0.0, u ? u[4] : 0.0, mask, diag_fp64, nullptr);
+      u ? u[3] : 0.0, u ? u[4] : 0.0, mask, diag_fp64, band, sp_frac, nullptr);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -383,11 +417,11 @@ emu_status launch_cov_build_batch(emu_ctx *ctx, const BatchInst *d_inst, int cou
 
 emu_status launch_precision_map_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int nb, double *partial,
                                       double *tnorm, double *frob, unsigned char *cls, double eps,
-                                      const double *u, unsigned mask, int diag_fp64) {
+                                      const double *u, unsigned mask, int diag_fp64, int band, double sp_frac) {
   ProfScope ps(ctx, PROF_MAP, 0.0, 0.0);
   k_precision_map<<<count, 1024, 0, ctx->stream>>>(0, 0, nb / kChunk, partial, tnorm, frob, cls, eps,
                                                    u ? u[1] : 0.0, u ? u[2] : 0.0, u ? u[3] : 0.0,
-                                                   u ? u[4] : 0.0, mask, diag_fp64, d_inst);
+                                                   u ? u[4] : 0.0, mask, diag_fp64, band, sp_frac, d_inst);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -158,7 +158,9 @@ emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda);
 emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS, long ld);
 emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
-                                const double *u, unsigned mask, int diag_fp64);
+                                const double *u, unsigned mask, int diag_fp64, int band, double sp_frac);
+// sp_frac of a band map: 0 means the paper's 5 %
+inline double band_sp_frac(const emu_mp_opts *o) { return o->sp_frac == 0.0 ? 0.05 : o->sp_frac; }
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
@@ -182,7 +184,7 @@ emu_status launch_cov_build_batch(emu_ctx *ctx, const BatchInst *d_inst, int cou
                                   double *partial);
 emu_status launch_precision_map_batch(emu_ctx *ctx, const BatchInst *d_inst, int count, int nb, double *partial,
                                       double *tnorm, double *frob, unsigned char *cls, double eps,
-                                      const double *u, unsigned mask, int diag_fp64);
+                                      const double *u, unsigned mask, int diag_fp64, int band, double sp_frac);
 emu_status launch_export_batch(emu_ctx *ctx, const BatchInst *d_inst, const int4 *d_pairs, long npairs, int nb,
                                const double *t64, const float *t32, const unsigned char *cls,
                                double *const *d_out);

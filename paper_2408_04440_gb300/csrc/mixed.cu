@@ -737,7 +737,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     if (o->u[c] > 0.0) u[c] = o->u[c];
   // the TF32 class is not built on the tensor cores yet: leave it out
   unsigned mask = (o->prec_mask | 1u) & ((1u << EMU_CLASS_FP32) | (1u << EMU_CLASS_BF16) | (1u << EMU_CLASS_E4M3) | 1u);
-  emu_status s = launch_precision_map(ctx, A, o->eps, u, mask, o->diag_fp64);
+  emu_status s = launch_precision_map(ctx, A, o->eps, u, mask, o->diag_fp64, o->band, band_sp_frac(o));
   if (s != EMU_OK) return s;
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(A->h_cls, A->d_cls, A->ntiles, cudaMemcpyDeviceToHost, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(&A->frob, A->d_frob, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -86,6 +86,25 @@ def test_mixed_batch_meets_eps(E, ctx, eps, mask):
     assert low > 0  # the batch exercises the tensor-core classes
 
 
+def test_band_map_batch(E, ctx):
+    # DP/SP/HP per matrix of the batch: each matrix's map is the oracle's band
+    # map for its own NT, and each factor meets the tolerance of that map
+    nb = 256
+    _, Ls, infos, st = _bf(E, ctx, PARAMS, nb=nb, band=E.MAP_DP_SP_HP, want_L=True)
+    assert st == E.EMU_OK
+    for b, (L, beta) in enumerate(PARAMS):
+        NT = infos[b].nt
+        co, _ = O.precision_map_band(NT, 2, 0.05)
+        counts = [int((co[np.tril_indices(NT)] == c).sum()) for c in range(5)]
+        assert infos[b].tiles == counts, (b, infos[b].tiles, counts)
+        S = O.cov_build(L, beta)
+        t = O.tile_norms(S, nb)
+        U = U_of(nb)
+        eps_map = NT * max(t[i, j] * U[co[i, j]] for i in range(NT) for j in range(i + 1)) / np.linalg.norm(S)
+        be = np.linalg.norm(Ls[b] @ Ls[b].T - S) / np.linalg.norm(S)
+        assert be <= max(eps_map, 1e-14), (b, be, eps_map)
+
+
 def test_batch_agrees_with_single_path(E, ctx):
     nb, s, seed, eps = 256, 64, 5, 1e-6
     Ys, Ls, infos, st = _bf(E, ctx, PARAMS, nb=nb, eps=eps, prec_mask=MASK_WITH_E4M3, nsamples=s, seed=seed,

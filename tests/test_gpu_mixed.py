@@ -77,6 +77,30 @@ def test_mixed_factor_meets_eps(E, ctx, L, nb, beta, eps):
           f"{np.linalg.norm(G - Lo) / np.linalg.norm(Lo):.2e}, tiles {info.tiles}")
 
 
+@pytest.mark.parametrize("band", [1, 2, 3])
+def test_band_maps_match_oracle_and_meet_their_bound(E, ctx, band):
+    # the paper's variants DP/SP, DP/SP/HP (5 % SP), DP/HP: the map equals the
+    # oracle's band map, and the backward error stays below the tolerance the
+    # norm rule would certify for that map, NT * max_ij ||S_ij|| u_c(ij) / ||S||
+    L, nb, beta = 48, 256, 6.0
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, band=band)
+    assert info.status == E.EMU_OK
+    G = _np(E.emu_mat_export(ctx, A))
+    A.free()
+    NT = info.nt
+    co, nsp = O.precision_map_band(NT, band, 0.05)
+    counts = [int((co[np.tril_indices(NT)] == c).sum()) for c in range(5)]
+    assert info.tiles == counts, (info.tiles, counts)
+    S = O.cov_build(L, beta)
+    t = O.tile_norms(S, nb)
+    U = U_of(nb)
+    eps_map = NT * max(t[i, j] * U[co[i, j]] for i in range(NT) for j in range(i + 1)) / np.linalg.norm(S)
+    be = _backward_error(G, S)
+    assert be <= eps_map, (be, eps_map)
+    print(f"band map {E.MAP_NAMES[band]}: tiles {info.tiles} (SP bands {nsp}), backward {be:.2e} <= {eps_map:.2e}")
+
+
 @pytest.mark.parametrize("mask,eps,tol", [(0b00011, 1e-6, 1e-6),   # FP64 diagonal region + FP32 tensor-core GEMMs
                                           (0b01001, 1e-2, 1e-2)])  # everything that can drops to BF16
 def test_forced_tensor_core_classes(E, ctx, mask, eps, tol):

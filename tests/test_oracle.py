@@ -211,6 +211,44 @@ def test_precision_map_properties():
     assert np.all(O.precision_map(t, 1e6, U, 0b01011)[np.tril_indices(NT)] == 3)
 
 
+# The paper's band variants ("Performance Results": DP, DP/SP, DP/SP/HP with
+# 5 % SP, DP/HP).  Counts below are worked by hand from the definition: NT(NT+1)/2
+# lower tiles, NT on the diagonal (DP), band d holding NT - d tiles.
+@pytest.mark.parametrize("NT,band,frac,expect", [
+    (7, 1, 0.05, (7, 21, 0)),          # DP/SP: the 21 off-diagonal tiles are SP
+    (7, 3, 0.05, (7, 0, 21)),          # DP/HP
+    (32, 2, 0.05, (32, 31, 465)),      # 5 % of 528 = 26.4 <= band 1 (31 tiles)
+    (100, 2, 0.05, (100, 294, 4656)),  # 5 % of 5050 = 252.5: bands 1..3 = 99+98+97 = 294
+    (100, 2, -1.0, (100, 0, 4950)),    # no SP bands
+    (4, 2, 0.99, (4, 6, 0)),           # the share cannot be reached: every off-diagonal band SP
+])
+def test_band_maps_hand_derived(NT, band, frac, expect):
+    c, nsp = O.precision_map_band(NT, band, frac)
+    low = c[np.tril_indices(NT)]
+    assert (int((low == 0).sum()), int((low == 1).sum()), int((low == 3).sum())) == expect
+    assert np.all(np.diag(c) == 0) and np.all(c[np.triu_indices(NT, 1)] == 255)
+    # classes depend only on the band i - j, and SP bands come before HP bands
+    for d in range(1, NT):
+        band_cls = {int(c[j + d, j]) for j in range(NT - d)}
+        assert len(band_cls) == 1
+        if band == 2:
+            assert band_cls == ({1} if d <= nsp else {3})
+
+
+def test_band_map_sp_share_is_minimal():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        NT = int(rng.integers(2, 300))
+        frac = float(rng.uniform(0.001, 0.5))
+        c, nsp = O.precision_map_band(NT, 2, frac)
+        total = NT * (NT + 1) // 2
+        sp = int((c[np.tril_indices(NT)] == 1).sum())
+        assert sp == sum(NT - d for d in range(1, nsp + 1))
+        if nsp < NT - 1:
+            assert sp >= frac * total
+        assert sp - (NT - nsp) < frac * total  # one band fewer falls short
+
+
 # -------------------------------------------------------------------- RNG
 def _kat():
     rows = []
