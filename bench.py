@@ -238,6 +238,7 @@ def run_ours(a):
 
         if not a.no_bands:
             extra["band_maps"] = band_variants(E, ctx, a, flops, extra.get("fp64_factor_ms"))
+            extra["tf32_variant"] = tf32_variant(E, ctx, a, flops, extra.get("fp64_factor_ms"))
 
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
 
@@ -312,7 +313,7 @@ def roofline(prof: dict, peaks: dict) -> dict:
             "launches": g["launches"]}
 
 
-def backward_error_rows(E, ctx, a, rows: int, band: int = 0) -> float:
+def backward_error_rows(E, ctx, a, rows: int, band: int = 0, mask: int = MASK_FP64_FP32_BF16) -> float:
     import torch
 
     n = a.L * a.L
@@ -321,7 +322,7 @@ def backward_error_rows(E, ctx, a, rows: int, band: int = 0) -> float:
     S.free()
     Sd = Sd + Sd.t() - torch.diag(torch.diag(Sd))
     A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
-    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16, band=band)
+    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=mask, band=band)
     Ld = E.emu_mat_export(ctx, A)
     A.free()
     g = torch.Generator().manual_seed(7)
@@ -363,6 +364,27 @@ def band_variants(E, ctx, a, flops, fp64_ms) -> dict:
             d["speedup_vs_fp64"] = round(fp64_ms / fms, 2)
         out[name] = d
     return out
+
+
+def tf32_variant(E, ctx, a, flops, fp64_ms) -> dict:
+    """The same factor and eps with the TF32 class enabled beside FP64/FP32/BF16
+    (tiles that pass at u = 2^-11 take one kind::tf32 product instead of six
+    BF16 split products)."""
+    mask = MASK_FP64_FP32_BF16 | (1 << 2)
+    ts, info = [], None
+    for r in range(3):
+        A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+        info = E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=mask)
+        A.free()
+        if r:
+            ts.append(info.ms)
+    fms = statistics.median(ts)
+    d = {"prec_mask": mask, "factor_ms": round(fms, 3), "tflops": round(flops / (fms * 1e-3) / 1e12, 3),
+         "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)),
+         "backward_error_rows64": backward_error_rows(E, ctx, a, rows=64, mask=mask)}
+    if fp64_ms:
+        d["speedup_vs_fp64"] = round(fp64_ms / fms, 2)
+    return d
 
 
 def cusolver_reference(E, ctx, a, flops) -> dict:

@@ -271,7 +271,7 @@ emu_status emu_mat_free(emu_mat *A) {
   cudaStream_t s = A->ctx ? A->ctx->stream : nullptr;
   if (A->ctx) cudaSetDevice(A->ctx->device);
   void *bufs[] = {A->t64, A->t32, A->d_partial, A->d_tnorm, A->d_frob, A->d_cls, A->op_bf16, A->op_e4m3,
-                  A->scale_e4m3};
+                  A->scale_e4m3, A->op_tf32};
   for (void *b : bufs)
     if (b) cudaFreeAsync(b, s);
   mixed_mat_release(A);

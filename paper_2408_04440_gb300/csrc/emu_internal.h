@@ -123,6 +123,7 @@ struct emu_mat {
   uint16_t *op_bf16 = nullptr; // ntiles * 3 * nb*nb
   uint8_t *op_e4m3 = nullptr;  // ntiles * nb*nb FP8-E4M3 copies (row-major), when E4M3 tiles exist
   float *scale_e4m3 = nullptr; // ntiles power-of-two scales of those copies
+  float *op_tf32 = nullptr;     // ntiles * nb*nb TF32 copies (row-major), when TF32 tiles exist
   void *plan = nullptr;        // mixed-factor schedule (mixed.cu)
 };
 

@@ -6,6 +6,8 @@
 // Precision classes on the tensor cores (FP32 accumulation):
 //   E4M3 class: one kind::f8f6f4 product of FP8-E4M3 copies carrying a
 //     power-of-two scale per tile; the epilogue divides the scales out.
+//   TF32 class: one kind::tf32 product of copies rounded to TF32 (nearest),
+//     K = 8 per instruction, at half the BF16 rate.
 //   BF16 class: one kind::f16 product a0 b0 of the round-to-nearest BF16 operands.
 //   FP32 class: each FP32 operand is split into three BF16 pieces
 //     x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1))
@@ -38,8 +40,12 @@ constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t IDESC = tc::idesc_f32acc(1u /*BF16*/, BM, BN);
 constexpr uint32_t IDESC8 = tc::idesc_f32acc(0u /*E4M3*/, BM, BN);
+constexpr uint32_t IDESC32 = tc::idesc_f32acc(2u /*TF32*/, BM, BN);
 constexpr int A8_BYTES = BM * BK;  // FP8: BK elements = BK bytes per row
 constexpr int B8_BYTES = BN * BK;
+constexpr int A32_BYTES = BM * BK * 4;  // TF32: 128 bytes per row (128-byte swizzle)
+constexpr int B32_BYTES = BN * BK * 4;
+static_assert(A32_BYTES <= NPIECE * A_PIECE && B32_BYTES <= NPIECE * B_PIECE, "TF32 operands fit a stage");
 
 struct Shared {
   uint64_t full[STAGES];
@@ -104,9 +110,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         Item item = items[it];
         for (int sg = item.seg_begin; sg < item.seg_end && ok; sg++) {
           Seg s = segs[sg];
-          bool f8 = s.cls == EMU_CLASS_E4M3;
+          bool f8 = s.cls == EMU_CLASS_E4M3, t32 = s.cls == EMU_CLASS_TF32;
           int np = (s.cls == EMU_CLASS_FP32) ? NPIECE : 1;
-          uint32_t bytes = f8 ? (uint32_t)(A8_BYTES + B8_BYTES) : (uint32_t)np * (A_PIECE + B_PIECE);
+          uint32_t bytes = f8    ? (uint32_t)(A8_BYTES + B8_BYTES)
+                           : t32 ? (uint32_t)(A32_BYTES + B32_BYTES)
+                                 : (uint32_t)np * (A_PIECE + B_PIECE);
           for (int kc = 0; kc < ksteps; kc++) {
             if (!tc::mbar_wait(&sh->empty[stage], phase ^ 1u, abort)) {
               raise_timeout(sh, status);
@@ -118,6 +126,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (f8) {
               tc::tma_load_2d(st, &ops.a8, &sh->full[stage], s.ax + kc * BK, s.ay);
               tc::tma_load_2d(st + NPIECE * A_PIECE, &ops.b8, &sh->full[stage], s.bx + kc * BK, s.by);
+            } else if (t32) {
+              tc::tma_load_2d(st, &ops.a32, &sh->full[stage], s.ax + kc * BK, s.ay);
+              tc::tma_load_2d(st + NPIECE * A_PIECE, &ops.b32, &sh->full[stage], s.bx + kc * BK, s.by);
             } else {
               for (int q = 0; q < np; q++) {
                 tc::tma_load_2d(st + q * A_PIECE, &ops.a16, &sh->full[stage], s.ax + kc * BK,
@@ -177,6 +188,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE, 16, 256, tc::kSwizzle32B);
               tc::mma_f8(d_tmem, ad, bd, IDESC8, accumulate);
               accumulate = 1;
+            } else if (cls == EMU_CLASS_TF32) {
+              // four K = 8 products of the TF32 copies (rows of 128 bytes, 128-byte swizzle)
+#pragma unroll
+              for (int ks = 0; ks < BK / 8; ks++) {
+                uint64_t ad = tc::smem_desc(st + ks * 32, 16, 1024, tc::kSwizzle128B);
+                uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE + ks * 32, 16, 1024, tc::kSwizzle128B);
+                tc::mma_tf32(d_tmem, ad, bd, IDESC32, accumulate);
+                accumulate = 1;
+              }
             } else {
 #pragma unroll
               for (int ks = 0; ks < BK / 16; ks++) {
@@ -320,6 +340,31 @@ emu_status make_map_e4m3(emu_ctx *ctx, CUtensorMap *map, const void *base, uint6
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed";
+    return EMU_ECUDA;
+  }
+  return EMU_OK;
+}
+
+emu_status make_map_f32(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows,
+                        uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    ctx->last_error = "cuTensorMapEncodeTiled unavailable";
+    return EMU_ECUDA;
+  }
+  if (((uintptr_t)base & 15u) != 0 || (inner * 4) % 16 != 0 || inner % BK != 0) {
+    ctx->last_error = "TMA operand base/stride not 16-byte aligned";
+    return EMU_EINVAL;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";

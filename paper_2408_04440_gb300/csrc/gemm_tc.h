@@ -4,8 +4,9 @@
 // item accumulates, in a TMEM FP32 accumulator, the sum over its segments of
 // A_seg * B_seg^T, where A_seg (BM x nb) and B_seg (BN x nb) are K-major
 // operand blocks fetched by TMA (three BF16 split pieces per operand for the
-// FP32 class, one BF16 piece for BF16, one FP8-E4M3 copy for E4M3, whose
-// per-tile scales the epilogue divides out), then applies the epilogue:
+// FP32 class, one TF32 copy for TF32, one BF16 piece for BF16, one FP8-E4M3
+// copy for E4M3, whose per-tile scales the epilogue divides out), then
+// applies the epilogue:
 //   mode TC_SUB_F32: out32[off + r + c*ldo] -= acc   (trailing tile update)
 //   mode TC_ADD_F64: out64[off + r + c*ldo] += acc   (sampling, r/c bounded)
 #pragma once
@@ -26,7 +27,8 @@ enum { TC_SUB_F32 = 0, TC_ADD_F64 = 1 };
 struct Seg {
   int ax, ay, ay_step;  // TMA coordinates of A piece 0 (x = K offset) and piece stride in rows
   int bx, by, by_step;  // same for B
-  int cls;              // EMU_CLASS_FP32 (6 products), EMU_CLASS_BF16 (1), EMU_CLASS_E4M3 (1, FP8 copies)
+  int cls;              // EMU_CLASS_FP32 (6 products), EMU_CLASS_TF32 (1, FP32 copies), EMU_CLASS_BF16 (1),
+                        // EMU_CLASS_E4M3 (1, FP8 copies)
   int pad;
 };
 
@@ -38,10 +40,11 @@ struct Item {
 };
 
 // Operand sources of a launch: BF16 pieces (A box 128 x 32, B box 256 x 32,
-// 64-byte swizzle) and FP8-E4M3 copies (same boxes in bytes, 32-byte swizzle)
-// with one power-of-two scale per tile.
+// 64-byte swizzle), FP8-E4M3 copies (same boxes in bytes, 32-byte swizzle)
+// with one power-of-two scale per tile, and TF32 copies (FP32 containers,
+// same boxes, 128-byte swizzle).
 struct Operands {
-  CUtensorMap a16, b16, a8, b8;
+  CUtensorMap a16, b16, a8, b8, a32, b32;
   const float *scale8;
 };
 
@@ -54,6 +57,11 @@ emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint6
 // [box_rows x 32], 32-byte swizzle.
 emu_status make_map_e4m3(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
                          uint64_t rows, uint32_t box_rows);
+
+// 2-D FP32 tensor map over a row-major [rows x inner] array (TF32 copies),
+// box [box_rows x 32], 128-byte swizzle.
+emu_status make_map_f32(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
+                        uint64_t rows, uint32_t box_rows);
 
 emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
                   int ksteps, int mode, float *out32, double *out64, int ldo, int max_ctas);

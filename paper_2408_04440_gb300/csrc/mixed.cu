@@ -111,6 +111,27 @@ __global__ void k_split_tiles(const T *__restrict__ src, uint16_t *__restrict__ 
   }
 }
 
+// TF32 copies of listed panel tiles for the TF32-class updates: each
+// element's FP32 value, rebuilt exactly from its three BF16 pieces (they split
+// the FP32 master exactly), rounded to TF32 (cvt.rna: nearest, ties away from
+// zero), row-major like the pieces.  blockIdx.y splits a tile into parts.
+__global__ void k_tf32_copy(const uint16_t *__restrict__ op, float *__restrict__ op32, const int *__restrict__ tiles,
+                            int nb, const int *st) {
+  if (failed(st)) return;
+  const long t = tiles[blockIdx.x];
+  const size_t plane = (size_t)nb * nb, part = plane / gridDim.y;
+  const uint16_t *p = op + (size_t)t * 3 * plane;
+  float *q = op32 + (size_t)t * plane;
+  for (size_t e = blockIdx.y * part + threadIdx.x; e < (blockIdx.y + 1) * part; e += blockDim.x) {
+    const float x = (__bfloat162float(__ushort_as_bfloat16(p[2 * plane + e])) +
+                     __bfloat162float(__ushort_as_bfloat16(p[plane + e]))) +
+                    __bfloat162float(__ushort_as_bfloat16(p[e]));
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    q[e] = __uint_as_float(r);
+  }
+}
+
 // FP8-E4M3 copies of whole panel tiles for E4M3-class consumers, from the
 // leading BF16 piece (already row-major / K-major).  One CTA per listed tile:
 // amax over the tile, power-of-two scale s = 2^floor(log2(448 / amax)) so
@@ -407,6 +428,7 @@ struct StepPlan {
   int r64_1 = 0, n64_1 = 0, r32_1 = 0, n32_1 = 0;  // T1 (offset, count) in rows64 / rows32
   int r64_r = 0, n64_r = 0, r32_r = 0, n32_r = 0;  // TR
   int q_1 = 0, nq_1 = 0, q_r = 0, nq_r = 0;        // panel tiles to quantize to E4M3 (row k+1 / rest)
+  int t_1 = 0, nt_1 = 0, t_r = 0, nt_r = 0;        // panel tiles copied to TF32 (row k+1 / rest)
   int p_off[GR_N] = {}, p_n[GR_N] = {};            // FP64-class tensor-core items per update group
   double p_flops[GR_N] = {};
   int z1_off = 0, z1_n = 0, zr_off = 0, zr_n = 0;  // panel tiles digit-sliced for them (row k+1 / rest)
@@ -440,6 +462,8 @@ struct MixedPlan {
   int *d_tiles64 = nullptr;           // tile index of every entry of rows64 (split after its TRSM)
   int *d_qtiles = nullptr;            // panel tiles quantized to E4M3, per step (see StepPlan)
   bool any_e4m3 = false;
+  int *d_ttiles = nullptr;            // panel tiles copied to TF32, per step (see StepPlan)
+  bool any_tf32 = false;
   gemm_tc::Operands ops;
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
@@ -472,7 +496,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->nb = nb;
   P->cls.assign(A->h_cls, A->h_cls + A->ntiles);
   auto C = [&](int i, int j) { return (int)P->cls[tile_index(i, j, NT)]; };
-  std::vector<int> rows64, rows32, tiles64, diag, qtiles;
+  std::vector<int> rows64, rows32, tiles64, diag, qtiles, ttiles;
   std::vector<gemm64::Item> items64;
   std::vector<gemm64::Seg> segs64;
   std::vector<int4> zjobs, z1_step, zr_step;
@@ -523,20 +547,22 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
       sp.p_flops[g] += 2.0 * nb3;
       return;
     }
-    int cc = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : (c == EMU_CLASS_E4M3) ? EMU_CLASS_E4M3 : EMU_CLASS_BF16;
-    bool f8 = cc == EMU_CLASS_E4M3;
+    int cc = (c == EMU_CLASS_FP32 || c == EMU_CLASS_TF32 || c == EMU_CLASS_E4M3) ? c : EMU_CLASS_BF16;
+    bool f8 = cc == EMU_CLASS_E4M3, t32 = cc == EMU_CLASS_TF32;
     if (f8) P->any_e4m3 = true;
+    if (t32) P->any_tf32 = true;
     long tik = tile_index(i, k, NT), tjk = tile_index(j, k, NT);
     for (int nbk = 0; nbk < nb / gemm_tc::BN; nbk++)
       for (int mb = 0; mb < nb / gemm_tc::BM; mb++) {
         if (i == j && mb * gemm_tc::BM + gemm_tc::BM - 1 < nbk * gemm_tc::BN) continue;  // above the diagonal
-        // BF16 pieces: row (tile*3 + piece)*nb + r; FP8 copies: row tile*nb + r
+        // BF16 pieces: row (tile*3 + piece)*nb + r; FP8 and TF32 copies: row tile*nb + r
+        const int rows_per_tile = (f8 || t32) ? 1 : 3;
         gemm_tc::Seg s;
         s.ax = 0;
-        s.ay = (int)(tik * (f8 ? 1 : 3) * nb + mb * gemm_tc::BM);
+        s.ay = (int)(tik * rows_per_tile * nb + mb * gemm_tc::BM);
         s.ay_step = nb;
         s.bx = 0;
-        s.by = (int)(tjk * (f8 ? 1 : 3) * nb + nbk * gemm_tc::BN);
+        s.by = (int)(tjk * rows_per_tile * nb + nbk * gemm_tc::BN);
         s.by_step = nb;
         s.cls = cc;
         s.pad = 0;
@@ -553,7 +579,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
         sp.i_n[g]++;
         sp.flops[g] += f;
-        sp.mma[g] += f * (cc == EMU_CLASS_FP32 ? 6.0 : 1.0);
+        // in BF16-product units: a TF32 product runs at half the BF16 rate
+        sp.mma[g] += f * (cc == EMU_CLASS_FP32 ? 6.0 : t32 ? 2.0 : 1.0);
       }
   };
   auto add_row = [&](int k, int i, int &n64, int &n32) {
@@ -607,6 +634,23 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         qtiles.push_back((int)tile_index(i, k, NT));
         sp.nq_r++;
       }
+    // TF32 consumers read TF32 copies of the panel tiles: copy them all when
+    // the step has any TF32 update
+    bool step_t32 = false;
+    for (int g = 0; g < GR_N; g++)
+      for (int q = sp.i_off[g]; q < sp.i_off[g] + sp.i_n[g]; q++)
+        if (segs[items[q].seg_begin].cls == EMU_CLASS_TF32) step_t32 = true;
+    sp.t_1 = (int)ttiles.size();
+    if (step_t32 && k + 1 < NT) {
+      ttiles.push_back((int)tile_index(k + 1, k, NT));
+      sp.nt_1 = 1;
+    }
+    sp.t_r = (int)ttiles.size();
+    if (step_t32)
+      for (int i = k + 2; i < NT; i++) {
+        ttiles.push_back((int)tile_index(i, k, NT));
+        sp.nt_r++;
+      }
     sp.fp64_panel = sp.n64_1 > 0 || sp.n64_r > 0 || sp.p_n[GR_S] > 0;
     sp.z1_off = (int)zjobs.size();
     zjobs.insert(zjobs.end(), z1_step.begin(), z1_step.end());
@@ -629,7 +673,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   size_t o_r64 = part(vbytes(rows64)), o_r32 = part(vbytes(rows32)), o_i64 = part(vbytes(items64)),
          o_s64 = part(vbytes(segs64)), o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
-         o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)),
+         o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)), o_tt = part(vbytes(ttiles)),
          o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
   size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
   P->host_blob.assign(copy_bytes, 0);
@@ -646,6 +690,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   put(o_t64, tiles64);
   put(o_diag, diag);
   put(o_q, qtiles);
+  put(o_tt, ttiles);
   P->stream = ctx->stream;
   EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_blob, off, ctx->stream));
   char *b = static_cast<char *>(P->d_blob);
@@ -660,6 +705,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_tiles64 = reinterpret_cast<int *>(b + o_t64);
   P->d_diag_tiles = reinterpret_cast<int *>(b + o_diag);
   P->d_qtiles = reinterpret_cast<int *>(b + o_q);
+  P->d_ttiles = reinterpret_cast<int *>(b + o_tt);
   P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
   emu_status s;
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
@@ -667,8 +713,10 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapB, A->op_bf16, nb, rows, gemm_tc::BN)) != EMU_OK) return s;
   P->ops.a16 = P->mapA;
   P->ops.b16 = P->mapB;
-  P->ops.a8 = P->mapA;  // valid maps even when no FP8 copies exist (then never used)
+  P->ops.a8 = P->mapA;  // valid maps even when no FP8 or TF32 copies exist (then never used)
   P->ops.b8 = P->mapB;
+  P->ops.a32 = P->mapA;
+  P->ops.b32 = P->mapB;
   P->ops.scale8 = nullptr;
   if (P->nslots > 0) {
     size_t te = (size_t)nb * nb;
@@ -689,6 +737,14 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     if ((s = gemm_tc::make_map_e4m3(ctx, &P->ops.a8, A->op_e4m3, nb, rows8, gemm_tc::BM)) != EMU_OK) return s;
     if ((s = gemm_tc::make_map_e4m3(ctx, &P->ops.b8, A->op_e4m3, nb, rows8, gemm_tc::BN)) != EMU_OK) return s;
     P->ops.scale8 = A->scale_e4m3;
+  }
+  if (P->any_tf32) {
+    size_t te = (size_t)nb * nb;
+    if (!A->op_tf32)
+      EMU_CUDA_TRY(ctx, cudaMallocAsync(&A->op_tf32, (size_t)A->ntiles * te * sizeof(float), ctx->stream));
+    uint64_t rows32 = (uint64_t)A->ntiles * nb;
+    if ((s = gemm_tc::make_map_f32(ctx, &P->ops.a32, A->op_tf32, nb, rows32, gemm_tc::BM)) != EMU_OK) return s;
+    if ((s = gemm_tc::make_map_f32(ctx, &P->ops.b32, A->op_tf32, nb, rows32, gemm_tc::BN)) != EMU_OK) return s;
   }
   return EMU_OK;
 }
@@ -735,8 +791,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   double u[EMU_NCLASS] = {0x1p-53, 0x1p-24 * sqrt((double)nb), 0x1p-11, 0x1p-8, 0x1p-4};
   for (int c = 0; c < EMU_NCLASS; c++)
     if (o->u[c] > 0.0) u[c] = o->u[c];
-  // the TF32 class is not built on the tensor cores yet: leave it out
-  unsigned mask = (o->prec_mask | 1u) & ((1u << EMU_CLASS_FP32) | (1u << EMU_CLASS_BF16) | (1u << EMU_CLASS_E4M3) | 1u);
+  unsigned mask = (o->prec_mask | 1u) & ((1u << EMU_NCLASS) - 1u);
   emu_status s = launch_precision_map(ctx, A, o->eps, u, mask, o->diag_fp64, o->band, band_sp_frac(o));
   if (s != EMU_OK) return s;
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(A->h_cls, A->d_cls, A->ntiles, cudaMemcpyDeviceToHost, ctx->stream));
@@ -785,6 +840,13 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     if (nq <= 0) return EMU_OK;
     ProfScope ps(ctx, PROF_SPLIT, 0.0, 3.0 * nq * te);
     k_quant_e4m3<<<nq, 1024, 0, ctx->stream>>>(A->op_bf16, A->op_e4m3, A->scale_e4m3, P->d_qtiles + q0, nb, st);
+    EMU_LAUNCHED(ctx);
+    return EMU_OK;
+  };
+  auto tf32copy = [&](int t0, int nt) -> emu_status {
+    if (nt <= 0) return EMU_OK;
+    ProfScope ps(ctx, PROF_SPLIT, 0.0, 10.0 * nt * te);
+    k_tf32_copy<<<dim3(nt, 32), 256, 0, ctx->stream>>>(A->op_bf16, A->op_tf32, P->d_ttiles + t0, nb, st);
     EMU_LAUNCHED(ctx);
     return EMU_OK;
   };
@@ -856,6 +918,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
     if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
     if ((s = quantize(sp.q_1, sp.nq_1)) != EMU_OK) break;
+    if ((s = tf32copy(sp.t_1, sp.nt_1)) != EMU_OK) break;
     if ((s = slice64(sp.z1_off, sp.z1_n)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T1), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G2), 0));  // G2A(k-1)
@@ -865,6 +928,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_P), 0));
     if ((s = trsm_rows(k, sp.r64_r, sp.n64_r, sp.r32_r, sp.n32_r, false)) != EMU_OK) break;
     if ((s = quantize(sp.q_r, sp.nq_r)) != EMU_OK) break;
+    if ((s = tf32copy(sp.t_r, sp.nt_r)) != EMU_OK) break;
     if ((s = slice64(sp.zr_off, sp.zr_n)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T), ctx->mid));
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_T1), 0));
@@ -1043,7 +1107,8 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
           sg.by = nbk * gemm_tc::BN;
           sg.by_step = s_pad;
           // the sampler reads E4M3-class tiles through their leading BF16 piece
-          sg.cls = (c == EMU_CLASS_FP32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;
+          // TF32-class tiles are drawn on the FP32 path (their three BF16 pieces exist)
+          sg.cls = (c == EMU_CLASS_FP32 || c == EMU_CLASS_TF32) ? EMU_CLASS_FP32 : EMU_CLASS_BF16;
           sg.pad = 0;
           segs.push_back(sg);
         }

@@ -90,6 +90,17 @@ __device__ inline void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, 
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A * B^T, kind::tf32 (TF32 inputs in 32-bit containers, FP32
+// accumulator, K = 8 per instruction).
+__device__ inline void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // D[tmem] (+)= A * B^T, kind::f8f6f4 (E4M3 inputs, FP32 accumulator).
 __device__ inline void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                               uint32_t accumulate) {
@@ -139,10 +150,11 @@ __device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_
   return d;
 }
 
-// Instruction descriptor of kind::f16 / kind::f8f6f4 with FP32 accumulation,
-// both operands K-major: D format F32 (bits 4-5 = 1), A/B format at bits 7-9
-// and 10-12 (BF16 = 1 for kind::f16; E4M3 = 0 for kind::f8f6f4), N >> 3 at
-// bits 17-22, M >> 4 at bits 24-28.
+// Instruction descriptor of kind::f16 / kind::tf32 / kind::f8f6f4 with FP32
+// accumulation, both operands K-major: D format F32 (bits 4-5 = 1), A/B
+// format at bits 7-9 and 10-12 (BF16 = 1 for kind::f16; TF32 = 2 for
+// kind::tf32; E4M3 = 0 for kind::f8f6f4), N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t ab_format, uint32_t M, uint32_t N) {
   return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }

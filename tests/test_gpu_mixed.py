@@ -77,6 +77,30 @@ def test_mixed_factor_meets_eps(E, ctx, L, nb, beta, eps):
           f"{np.linalg.norm(G - Lo) / np.linalg.norm(Lo):.2e}, tiles {info.tiles}")
 
 
+@pytest.mark.parametrize("mask,eps,need_tf32", [(0b00101, 1e-6, True), (0b00111, 1e-6, True),
+                                                (0b11111, 1e-6, True)])
+def test_tf32_class_meets_eps(E, ctx, mask, eps, need_tf32):
+    # TF32 class: one kind::tf32 product of copies rounded to TF32, u = 2^-11
+    L, nb, beta, s = 48, 256, 6.0, 64
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=mask)
+    assert info.status == E.EMU_OK
+    S = O.cov_build(L, beta)
+    cls, _ = E.emu_mat_tile_info(ctx, A)
+    _map_matches(cls, O.tile_norms(S, nb), eps, mask, nb)
+    if need_tf32:
+        assert info.tiles[E.CLASS_TF32] > 0
+    G = _np(E.emu_mat_export(ctx, A))
+    be = _backward_error(G, S)
+    assert be <= eps, be
+    # samples: TF32 tiles are drawn on the three-piece FP32 path
+    Y = _np(E.emu_sample(ctx, A, s, seed=3))
+    ref = G @ O.normal_matrix(3, 0, L * L, s)
+    assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) <= 1e-6
+    A.free()
+    print(f"TF32 mask {mask:05b} eps {eps:g}: tiles {info.tiles}, backward {be:.2e}")
+
+
 @pytest.mark.parametrize("band", [1, 2, 3])
 def test_band_maps_match_oracle_and_meet_their_bound(E, ctx, band):
     # the paper's variants DP/SP, DP/SP/HP (5 % SP), DP/HP: the map equals the
