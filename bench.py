@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-empirical", action="store_true", help="skip the empirical-covariance build from residuals")
     ap.add_argument("--no-bands", action="store_true", help="skip the paper's band-map variants (DP/SP, DP/SP/HP, "
                                                              "DP/HP) of the same factor")
     ap.add_argument("--workload", choices=["single", "batched"], default="single",
@@ -239,6 +240,8 @@ def run_ours(a):
         if not a.no_bands:
             extra["band_maps"] = band_variants(E, ctx, a, flops, extra.get("fp64_factor_ms"))
             extra["tf32_variant"] = tf32_variant(E, ctx, a, flops, extra.get("fp64_factor_ms"))
+        if not a.no_empirical:
+            extra["empirical_cov"] = empirical_variant(E, ctx, a)
 
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
 
@@ -384,6 +387,45 @@ def tf32_variant(E, ctx, a, flops, fp64_ms) -> dict:
          "backward_error_rows64": backward_error_rows(E, ctx, a, rows=64, mask=mask)}
     if fp64_ms:
         d["speedup_vs_fp64"] = round(fp64_ms / fms, 2)
+    return d
+
+
+def empirical_variant(E, ctx, a) -> dict:
+    """The empirical covariance of the paper's emulator (U-hat = sum of xi xi^T
+    over the residual vectors / their number) from m = n synthetic residuals
+    drawn through our own sampler (xi = L z with L the mixed factor of the
+    synthetic covariance), then its mixed factor at the same eps.  The build
+    is the symmetric product on the tensor cores with FP64 accuracy; its
+    algorithmic flops are n (n + 1) m."""
+    import time
+    import torch
+
+    n = a.L * a.L
+    m = n
+    A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+    Xi = E._colmajor_empty(n, m, ctx.device)
+    E.emu_sample(ctx, A, m, seed=11, out=Xi)
+    A.free()
+    ts, U = [], None
+    for r in range(3):
+        if U is not None:
+            U.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U, _ = E.emu_cov_from_residuals(ctx, Xi, nb=a.nb, nugget_rel=0.0)  # the call returns when U is built
+        t1 = time.perf_counter()
+        if r:
+            ts.append((t1 - t0) * 1e3)
+    del Xi
+    torch.cuda.empty_cache()
+    bms = statistics.median(ts)
+    info = E.emu_potrf_mp(ctx, U, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16, raise_on_error=False)
+    U.free()
+    d = {"residuals": m, "build_ms": round(bms, 2), "build_tflops": round(n * (n + 1) * m / (bms * 1e-3) / 1e12, 2),
+         "build_note": "host wall time of the synchronous call, planning included",
+         "factor_status": int(info.status), "factor_ms": round(info.ms, 3),
+         "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles))}
     return d
 
 

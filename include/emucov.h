@@ -200,6 +200,19 @@ emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda,
  * returning, so hA may be reused at once. */
 emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda,
                                int nb, emu_mat **out);
+/* Empirical covariance of residual vectors ("Modeling the Temporal
+ * Dependence", the estimate U-hat and the diagonal perturbation after it):
+ *   U[i,j] = (1/m) sum_t Xi[i,t] Xi[j,t],   U[k,k] += nugget_rel * max_k U[k,k],
+ * Xi: device, column-major n x m (leading dimension ldxi >= n), one residual
+ * vector per column (m = R (T - P) in the paper); read only during the call.
+ * The paper adds the perturbation when m < n; pass nugget_rel = 0 for none.
+ * The lower tiles are formed on the tensor cores with FP64 accuracy (exact
+ * digit products of the rows, FP64 accumulation), then scaled; the result is
+ * a matrix in the state emu_cov_build leaves (tiles, tile norms, ||U||_F).
+ * nb must be a multiple of 256.  EMU_EINVAL on bad arguments, EMU_ENOMEM if
+ * the tile arena does not fit, EMU_ETIMEOUT if a bounded device wait expired. */
+emu_status emu_cov_from_residuals(emu_ctx *ctx, const double *dXi, int n, long m, long ldxi,
+                                  double nugget_rel, int nb, emu_mat **out);
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);
 /* Write the matrix as a dense FP64 lower triangle (upper set to 0) into dOut

@@ -66,6 +66,7 @@ def _declare(L):
     L.orc_frob_from_tiles.restype = d
     L.orc_precision_map.argtypes = [i, dp, d, dp, i, ctypes.c_uint, i, u8p]
     L.orc_precision_map_band.argtypes = [i, i, d, u8p]
+    L.orc_cov_from_residuals.argtypes = [i, lg, dp, lg, d, dp]
     L.orc_precision_map_band.restype = i
     L.orc_potrf_unblocked.argtypes = [i, dp, lg]
     L.orc_potrf_unblocked.restype = i
@@ -144,6 +145,15 @@ def precision_map_band(NT: int, band: int, sp_frac: float = 0.05):
     cls = np.zeros((NT, NT), dtype=np.uint8, order="F")
     nsp = lib().orc_precision_map_band(NT, band, sp_frac, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return cls, nsp
+
+
+def cov_from_residuals(Xi, nugget_rel: float = 0.0):
+    """U = Xi Xi^T / m with nugget_rel * max diag added to the diagonal (full symmetric n x n)."""
+    Xi = np.asfortranarray(Xi, dtype=np.float64)
+    n, m = Xi.shape
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    lib().orc_cov_from_residuals(n, m, _dp(Xi), n, nugget_rel, _dp(U))
+    return U
 
 
 def potrf_unblocked(A):

@@ -167,6 +167,29 @@ int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls)
   return nsp;
 }
 
+/* Empirical covariance of residual vectors ("Modeling the Temporal
+ * Dependence": U-hat is the sum of xi xi^T over the R (T - P) residual vectors
+ * divided by their number, then a perturbation of the diagonal).  Xi is n x m
+ * column-major (leading dimension ld), one vector per column.  Writes the full
+ * symmetric U (n x n, column-major): U[i,j] = (1/m) sum_t Xi[i,t] Xi[j,t], then
+ * U[k,k] += nugget_rel * max_k U[k,k]. */
+void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nugget_rel, double *U) {
+  const double inv_m = 1.0 / (double)m;
+  for (int j = 0; j < n; j++)
+    for (int i = j; i < n; i++) {
+      double s = 0.0;
+      for (long t = 0; t < m; t++) s += Xi[i + t * ld] * Xi[j + t * ld];
+      U[i + (size_t)j * n] = s * inv_m;
+      U[j + (size_t)i * n] = s * inv_m;
+    }
+  if (nugget_rel > 0.0) {
+    double mx = 0.0;
+    for (int k = 0; k < n; k++)
+      if (U[k + (size_t)k * n] > mx) mx = U[k + (size_t)k * n];
+    for (int k = 0; k < n; k++) U[k + (size_t)k * n] += nugget_rel * mx;
+  }
+}
+
 /* -------------------------------------------------------------- Cholesky */
 int orc_potrf_unblocked(int n, double *A, long ld) {
   /* Cholesky-Banachiewicz: row i of L from rows 0..i-1. */

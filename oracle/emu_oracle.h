@@ -64,6 +64,7 @@ void orc_precision_map(int NT, const double *t, double eps, const double *u,
                        int nclass, unsigned mask, int diag_fp64,
                        unsigned char *cls);
 int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls);
+void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nugget_rel, double *U);
 
 /* Unblocked Cholesky (row-by-row, the textbook Cholesky-Banachiewicz form):
  * A = L L^T, L lower with positive diagonal, overwritten in place.

@@ -35,7 +35,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
-    "emu_mat_import_host", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_mat_import_host", "emu_cov_from_residuals", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
     "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
@@ -103,6 +103,7 @@ def load() -> ctypes.CDLL:
     L.emu_cov_build.argtypes = [vp, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(vp)]
     L.emu_mat_import_host.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
     L.emu_mat_import.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
+    L.emu_cov_from_residuals.argtypes = [vp, vp, i, lg, lg, ctypes.c_double, i, ctypes.POINTER(vp)]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
     L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
@@ -270,6 +271,27 @@ def emu_mat_import(ctx: Context, A, nb: int) -> Mat:
     m = Mat(ctx, h)
     m._keep = A
     return m
+
+
+def emu_cov_from_residuals(ctx: Context, Xi, nb: int = 256, nugget_rel=None, raise_on_error: bool = True):
+    """Empirical covariance U = Xi Xi^T / m (+ nugget_rel * max diag on the
+    diagonal) of the m columns of Xi, an (n x m) float64 CUDA tensor.  By
+    default the perturbation is 1e-8 when m < n (fewer residuals than
+    coefficients, as the paper does) and 0 otherwise.  Returns (Mat, status)."""
+    n, m = Xi.shape
+    if Xi.stride(0) != 1:
+        Xi = Xi.t().contiguous().t()  # column-major storage
+    ld = Xi.stride(1) if m > 1 else n
+    if nugget_rel is None:
+        nugget_rel = 1e-8 if m < n else 0.0
+    h = ctypes.c_void_p()
+    st = ctx.lib.emu_cov_from_residuals(ctx.h, ctypes.c_void_p(_ptr(Xi)), n, m, ld, float(nugget_rel), nb,
+                                        ctypes.byref(h))
+    if st != EMU_OK:
+        if raise_on_error:
+            ctx._check(st, "emu_cov_from_residuals")
+        return None, st
+    return Mat(ctx, h), st
 
 
 def emu_mat_import_host(ctx: Context, A, nb: int) -> Mat:

@@ -6,7 +6,10 @@
 
 #include <new>
 
+#include <vector>
+
 #include "emu_internal.h"
+#include "gemm_f64.h"
 #include "mixed.h"
 
 emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what) {
@@ -17,6 +20,8 @@ emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what) {
   }
   return EMU_ECUDA;
 }
+
+static emu_status collect_status(emu_ctx *ctx, int *pivot);
 
 static emu_status fail_msg(emu_ctx *ctx, emu_status s, const char *msg) {
   if (ctx) ctx->last_error = msg;
@@ -303,6 +308,94 @@ emu_status emu_mat_import(emu_ctx *ctx, const double *dA, int n, long lda, int n
   emu_status s = mat_alloc(ctx, n, nb, &A);
   if (s != EMU_OK) return s;
   s = launch_import(ctx, A, dA, lda);
+  if (s != EMU_OK) {
+    emu_mat_free(A);
+    return s;
+  }
+  *out = A;
+  return EMU_OK;
+}
+
+emu_status emu_cov_from_residuals(emu_ctx *ctx, const double *dXi, int n, long m, long ldxi, double nugget_rel,
+                                  int nb, emu_mat **out) {
+  if (!ctx || !dXi || !out || n < 1 || m < 1 || ldxi < n || !(nugget_rel >= 0.0)) return EMU_EINVAL;
+  if (nb % 256 != 0) return fail_msg(ctx, EMU_EINVAL, "the empirical covariance needs nb a multiple of 256");
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  emu_mat *A = nullptr;
+  emu_status s = mat_alloc(ctx, n, nb, &A);
+  if (s != EMU_OK) return s;
+  const int NT = A->nt, npad = NT * nb;
+  // K per segment (a multiple of the 256-column exact accumulation chunk) and
+  // per launch (the digit arena stays within 2 GB)
+  const long Kc = 512;
+  const long mpad = (m + Kc - 1) / Kc * Kc;
+  long kb = ((1L << 31) / (16L * npad)) / Kc * Kc;
+  kb = std::max(Kc, std::min(kb, mpad));
+  // every 128 x 64 block of every lower tile (diagonal tiles in full, so that
+  // their norms cover both triangles as the covariance build's do), one
+  // segment per Kc columns of a launch
+  std::vector<gemm64::Item> items;
+  std::vector<gemm64::Seg> segs;
+  for (int I = 0; I < NT; I++)
+    for (int J = 0; J <= I; J++)
+      for (int nbk = 0; nbk < nb / gemm64::BN; nbk++)
+        for (int mb = 0; mb < nb / gemm64::BM; mb++) {
+          gemm64::Item it;
+          it.out_off = tile_index(I, J, NT) * (long)nb * nb + mb * gemm64::BM + (long)nbk * gemm64::BN * nb;
+          it.a_sc = I * nb + mb * gemm64::BM;
+          it.b_sc = J * nb + nbk * gemm64::BN;
+          it.seg_begin = (int)segs.size();
+          for (long kc = 0; kc < kb / Kc; kc++) {
+            gemm64::Seg sg;
+            sg.a_row = it.a_sc;
+            sg.b_row = it.b_sc;
+            sg.a_x = sg.b_x = (int)(kc * Kc);
+            segs.push_back(sg);
+          }
+          it.seg_end = (int)segs.size();
+          it.rows_valid = gemm64::BM;
+          it.cols_valid = gemm64::BN;
+          items.push_back(it);
+        }
+  gemm64::Item *d_items = nullptr;
+  gemm64::Seg *d_segs = nullptr;
+  int *d_exps = nullptr;
+  uint16_t *d_digits = nullptr;
+  unsigned long long *d_maxbits = nullptr;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_items, items.size() * sizeof(gemm64::Item), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_segs, segs.size() * sizeof(gemm64::Seg), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_exps, (size_t)npad * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_digits, (size_t)gemm64::NS * npad * kb * sizeof(uint16_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_maxbits, sizeof(unsigned long long), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(gemm64::Item), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(gemm64::Seg), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->t64, 0, (size_t)A->ntiles * A->tile_elems * sizeof(double), st);
+  CUtensorMap ma, mbm;
+  if (e == cudaSuccess) s = gemm64::make_map(ctx, &ma, d_digits, kb, (uint64_t)gemm64::NS * npad, gemm64::BM);
+  if (e == cudaSuccess && s == EMU_OK)
+    s = gemm64::make_map(ctx, &mbm, d_digits, kb, (uint64_t)gemm64::NS * npad, gemm64::BN);
+  for (long k0 = 0; k0 < m && e == cudaSuccess && s == EMU_OK; k0 += kb) {
+    const long ncols = std::min(kb, m - k0);
+    s = gemm64::launch_dense_digits(ctx, dXi, ldxi, n, k0, ncols, npad, kb, d_exps, d_digits);
+    if (s == EMU_OK) {
+      ProfScope ps(ctx, PROF_UPDATE64, (double)npad * (npad + nb) * (double)kb, 0.0, 36.0 * npad * (double)npad * kb);
+      s = gemm64::launch(ctx, ma, mbm, d_items, (int)items.size(), d_segs, (int)Kc, npad, npad, d_exps, d_exps,
+                         gemm64::TC64_ADD, A->t64, nb, ctx->sm_count);
+    }
+  }
+  if (e == cudaSuccess && s == EMU_OK) s = launch_emp_finish(ctx, A, m, nugget_rel, d_maxbits);
+  for (void *p : {(void *)d_items, (void *)d_segs, (void *)d_exps, (void *)d_digits, (void *)d_maxbits})
+    if (p) cudaFreeAsync(p, st);
+  if (e == cudaSuccess && s == EMU_OK) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "cov_from_residuals");
+  if (s == EMU_OK) {
+    int pivot = 0;
+    s = collect_status(ctx, &pivot);
+  }
   if (s != EMU_OK) {
     emu_mat_free(A);
     return s;

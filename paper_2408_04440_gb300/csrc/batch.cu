@@ -733,7 +733,7 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   if (eps > 0.0) {
     for (int c = 0; c < EMU_NCLASS; c++)
       if (o->u[c] > 0.0) u[c] = o->u[c];
-    // the TF32 class is not built on the tensor cores: leave it out
+    // the batched plan makes no TF32 copies: the TF32 class is left out here
     mask = (o->prec_mask | 1u) & ((1u << EMU_CLASS_FP32) | (1u << EMU_CLASS_BF16) | (1u << EMU_CLASS_E4M3) | 1u);
   }
   bool want_L = dL != nullptr;

@@ -177,6 +177,57 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
 }
 
+// Empirical covariance ("Modeling the Temporal Dependence": U-hat = the sum
+// of xi xi^T over the residual vectors divided by their number m): the tiles
+// hold the raw sums.  k_emp_maxdiag: max_k U-hat_kk as the bits of a
+// non-negative double (atomicMax on the bits orders such doubles).
+__global__ void k_emp_maxdiag(int n, int nb, int NT, const double *__restrict__ t64, double inv_m,
+                              unsigned long long *__restrict__ maxbits) {
+  unsigned long long best = 0;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+    const int tk = (int)(k / nb), r = (int)(k % nb);
+    const double v = t64[(size_t)tile_index(tk, tk, NT) * nb * nb + r + (size_t)r * nb] * inv_m;
+    best = max(best, (unsigned long long)__double_as_longlong(fmax(v, 0.0)));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, best);
+}
+
+// Scale the sums by 1/m, add nugget_rel * max diag to the diagonal (the
+// paper's perturbation when there are fewer residual vectors than
+// coefficients), set the padding (identity diagonal), and write the tile-norm
+// partials as the covariance build does.
+__global__ void __launch_bounds__(kThreads)
+    k_emp_finish(int n, int nb, int NT, double inv_m, double nugget_rel,
+                 const unsigned long long *__restrict__ maxbits, double *__restrict__ t64,
+                 double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  double *tile = t64 + (size_t)t * nb * nb;
+  const double nug = nugget_rel * __longlong_as_double((long long)*maxbits);
+  double ss = 0.0;
+  for (int cc = 0; cc < kChunk; cc++) {
+    int c = blockIdx.y * kChunk + cc;
+    long gj = (long)tj * nb + c;
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      long gi = (long)ti * nb + r;
+      double v;
+      if (gi < n && gj < n) {
+        v = tile[r + (size_t)c * nb] * inv_m;
+        if (gi == gj) v += nug;
+        ss += v * v;
+      } else {
+        v = (gi == gj) ? 1.0 : 0.0;
+      }
+      tile[r + (size_t)c * nb] = v;
+    }
+  }
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
 // One tile column j from a staging block holding rows j*nb .. n-1 of
 // columns j*nb .. j*nb+nb-1 (column-major, leading dimension ld).
 __global__ void __launch_bounds__(kThreads)
@@ -377,6 +428,18 @@ emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {
   dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
   k_import<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, dA, lda, A->t64,
                                               A->d_partial);
+  EMU_LAUNCHED(ctx);
+  return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
+}
+
+emu_status launch_emp_finish(emu_ctx *ctx, emu_mat *A, long m, double nugget_rel, unsigned long long *d_maxbits) {
+  const double inv_m = 1.0 / (double)m;
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(d_maxbits, 0, sizeof(unsigned long long), ctx->stream));
+  k_emp_maxdiag<<<64, 256, 0, ctx->stream>>>(A->n, A->nb, A->nt, A->t64, inv_m, d_maxbits);
+  EMU_LAUNCHED(ctx);
+  dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+  k_emp_finish<<<grid, kThreads, 0, ctx->stream>>>(A->n, A->nb, A->nt, inv_m, nugget_rel, d_maxbits, A->t64,
+                                                  A->d_partial);
   EMU_LAUNCHED(ctx);
   return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
 }

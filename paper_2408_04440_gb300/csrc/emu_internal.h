@@ -157,6 +157,8 @@ struct BatchInst {
 // cov.cu
 emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda);
+// Empirical covariance: scale the raw sums by 1/m, nugget, padding, norms (cov.cu).
+emu_status launch_emp_finish(emu_ctx *ctx, emu_mat *A, long m, double nugget_rel, unsigned long long *d_maxbits);
 emu_status launch_import_col(emu_ctx *ctx, emu_mat *A, int tj, const double *dS, long ld);
 emu_status launch_precision_map(emu_ctx *ctx, emu_mat *A, double eps,
                                 const double *u, unsigned mask, int diag_fp64, int band, double sp_frac);

@@ -16,6 +16,8 @@
 // drain them before the next chunk.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "gemm_f64.h"
 #include "gemm_tc.h"
 #include "tc.cuh"
@@ -135,6 +137,57 @@ __global__ void __launch_bounds__(256)
     int r = r0 + rr;
     double v = blk[rr][lane] * exp2i(-exp_of(exps, (long)jb.z + r));  // exact: |v| < 1
     write_digits(v, digits + (size_t)jb.y * NS * plane + (size_t)r * nb + c0 + lane, plane);
+  }
+}
+
+// Row exponents of a dense column-major block X[0:nrows, col0:col0+ncols]
+// (the residuals of the empirical covariance): one CTA per (32 rows, column
+// stripe), lane = row, warps stride columns; exps[r] = max(exps[r], e) with
+// every |x| < 2^e.
+__global__ void __launch_bounds__(256)
+    k_rowexp_dense(const double *__restrict__ X, long ld, int nrows, long col0, long ncols, int *__restrict__ exps,
+                   const int *st) {
+  if (failed(st)) return;
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  double m = 0.0;
+  if (r < nrows)
+    for (long c = (long)blockIdx.y * 8 + w; c < ncols; c += 8L * gridDim.y) m = fmax(m, fabs(X[r + (col0 + c) * ld]));
+  red[w][lane] = m;
+  __syncthreads();
+  if (w == 0 && r < nrows) {
+    for (int q = 1; q < 8; q++) m = fmax(m, red[q][lane]);
+    if (m > 0.0) {
+      int e;
+      frexp(m, &e);
+      atomicMax(&exps[r], e + kExpBias);
+    }
+  }
+}
+
+// Digit planes of that block, K-major: plane p, row r (< npad), column c
+// (< kpad); rows >= nrows and columns >= ncols are zero.  One CTA per 32x32
+// block, transposed through shared memory.
+__global__ void __launch_bounds__(256)
+    k_slice_dense(const double *__restrict__ X, long ld, int nrows, long col0, long ncols, int npad, long kpad,
+                  const int *__restrict__ exps, uint16_t *__restrict__ digits, const int *st) {
+  if (failed(st)) return;
+  __shared__ double blk[32][33];
+  const long c0 = (long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int cc = w; cc < 32; cc += 8) {
+    const int r = r0 + lane;
+    const long c = c0 + cc;
+    blk[lane][cc] = (r < nrows && c < ncols) ? X[r + (col0 + c) * ld] : 0.0;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)npad * kpad;
+  for (int q = 0; q < 4; q++) {
+    const int rr = w + 8 * q, r = r0 + rr;
+    const double v = blk[rr][lane] * exp2i(-exp_of(exps, r));  // exact: |v| < 1
+    write_digits(v, digits + (size_t)r * kpad + c0 + lane, plane);
   }
 }
 
@@ -404,6 +457,21 @@ emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_
   ProfScope ps(ctx, PROF_SPLIT, 0.0, (8.0 + 2.0 * NS) * (double)s_pad * zcols);
   k_slicez64<<<dim3(s_pad, nblocks), 256, 0, ctx->stream>>>(Z, ldz, s, s_pad, d_blocks, zcols, exps, digits,
                                                             ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_dense_digits(emu_ctx *ctx, const double *X, long ld, int nrows, long col0, long ncols, int npad,
+                               long kpad, int *exps, uint16_t *digits) {
+  if (npad % 32 != 0 || kpad % 32 != 0 || nrows > npad || ncols > kpad) return EMU_EINVAL;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, (16.0 + 2.0 * NS) * (double)npad * kpad);
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(exps, 0, (size_t)npad * sizeof(int), ctx->stream));
+  const int ystripes = (int)std::min<long>(64, (ncols + 7) / 8);
+  k_rowexp_dense<<<dim3(npad / 32, std::max(ystripes, 1)), 256, 0, ctx->stream>>>(X, ld, nrows, col0, ncols, exps,
+                                                                                  ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  k_slice_dense<<<dim3((unsigned)(kpad / 32), npad / 32), 256, 0, ctx->stream>>>(X, ld, nrows, col0, ncols, npad,
+                                                                                 kpad, exps, digits, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

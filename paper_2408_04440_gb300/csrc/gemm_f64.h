@@ -72,6 +72,13 @@ emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const
 emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_pad, const int2 *d_blocks,
                           int nblocks, long zcols, int *exps, uint16_t *digits);
 
+// Row exponents and digit planes of a dense column-major FP64 block
+// X[0:nrows, col0:col0+ncols] (leading dimension ld): exps[r] for r < npad
+// (zeroed first), plane p of row r at digits + (p * npad + r) * kpad, K-major,
+// zero beyond nrows / ncols.  npad and kpad are multiples of 32.
+emu_status launch_dense_digits(emu_ctx *ctx, const double *X, long ld, int nrows, long col0, long ncols, int npad,
+                               long kpad, int *exps, uint16_t *digits);
+
 // out64 (-= or +=) per item, K = nb per segment, on at most max_ctas persistent
 // CTAs; a_plane / b_plane = arena rows between digit planes.
 emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems,

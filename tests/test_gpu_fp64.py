@@ -90,6 +90,77 @@ def test_fp64_factor_with_extreme_pivots(E, ctx, scale):
     assert np.linalg.norm(G - Lo) / np.linalg.norm(Lo) <= 1e-12
 
 
+def _hadamard(m):
+    H = np.array([[1.0]])
+    while H.shape[0] < m:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+@pytest.mark.parametrize("n,m", [(700, 500), (700, 1300), (256, 64)])
+def test_empirical_covariance_matches_oracle(E, ctx, n, m):
+    import torch
+
+    rng = np.random.default_rng(n + m)
+    Xi = rng.standard_normal((n, m)) * np.logspace(0, -3, n)[:, None]
+    U, st = E.emu_cov_from_residuals(ctx, torch.from_numpy(np.asfortranarray(Xi)).cuda(), nb=256)
+    assert st == E.EMU_OK
+    G = _np(E.emu_mat_export(ctx, U))
+    nug = 1e-8 if m < n else 0.0
+    Uo = O.cov_from_residuals(Xi, nug)
+    assert np.abs(G - np.tril(Uo)).max() <= 1e-13 * np.abs(Uo).max()
+    # the matrix is in the covariance state: its norms feed the precision map
+    cls, tn = E.emu_mat_tile_info(ctx, U)
+    to = O.tile_norms(Uo, 256)
+    NT = to.shape[0]
+    assert np.allclose(tn[np.tril_indices(NT)], to[np.tril_indices(NT)], rtol=1e-12, atol=0)
+    U.free()
+
+
+def test_empirical_covariance_exact_for_integer_factor(E, ctx):
+    # Xi = L0 H[:n] with Hadamard rows: the estimate is L0 L0^T, exactly (integer digit products)
+    import torch
+
+    rng = np.random.default_rng(9)
+    n, m = 300, 512
+    L0 = np.tril(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+    np.fill_diagonal(L0, rng.integers(1, 4, size=n))
+    Xi = L0 @ _hadamard(m)[:n]
+    U, _ = E.emu_cov_from_residuals(ctx, torch.from_numpy(np.asfortranarray(Xi)).cuda(), nb=256, nugget_rel=0.0)
+    G = _np(E.emu_mat_export(ctx, U))
+    assert np.array_equal(G, np.tril(L0 @ L0.T))
+    U.free()
+
+
+def test_empirical_covariance_in_several_launches_then_factor(E, ctx):
+    # n = 2048 rows: the digit arena holds 65536 columns, so 70000 residuals take two
+    # launches; sampled entries against the oracle on the same rows; then the
+    # mixed factor of the estimate meets eps
+    import torch
+
+    n, m, nb = 2048, 70000, 256
+    S = O.cov_build(46, 6.0)[:n, :n]  # n = 2116, leading 2048 x 2048 block
+    Lo, _ = O.potrf_blocked(S, nb)
+    rng = np.random.default_rng(2)
+    Xg = torch.from_numpy(np.asfortranarray(Lo)).cuda() @ torch.randn(n, m, dtype=torch.float64, device="cuda",
+                                                                       generator=torch.Generator("cuda").manual_seed(4))
+    U, st = E.emu_cov_from_residuals(ctx, Xg, nb=nb)
+    assert st == E.EMU_OK
+    G = _np(E.emu_mat_export(ctx, U))
+    rows = np.sort(rng.choice(n, 24, replace=False))
+    Xr = Xg[torch.from_numpy(rows).cuda()].cpu().numpy()
+    Uo = O.cov_from_residuals(Xr)  # entries (rows x rows) of the estimate
+    Gr = G[np.ix_(rows, rows)]
+    low = np.tril(np.ones_like(Gr, dtype=bool))
+    assert np.abs(Gr[low] - Uo[low]).max() <= 1e-13 * np.abs(Uo).max()
+    info = E.emu_potrf_mp(ctx, U, eps=1e-8)
+    assert info.status == E.EMU_OK
+    L = _np(E.emu_mat_export(ctx, U))
+    Uf = G + np.tril(G, -1).T
+    assert np.linalg.norm(L @ L.T - Uf) / np.linalg.norm(Uf) <= 1e-8
+    U.free()
+
+
 @pytest.mark.parametrize("bad", [1, 70, 199])
 def test_not_positive_definite_reports_pivot(E, ctx, bad):
     import torch

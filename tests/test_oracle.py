@@ -249,6 +249,55 @@ def test_band_map_sp_share_is_minimal():
         assert sp - (NT - nsp) < frac * total  # one band fewer falls short
 
 
+# Empirical covariance U = Xi Xi^T / m (+ nugget_rel * max diag on the diagonal):
+# pins that do not restate the sum.
+def _hadamard(m):
+    H = np.array([[1.0]])
+    while H.shape[0] < m:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def test_empirical_cov_recovers_integer_factor_exactly():
+    # rows of a Hadamard matrix are orthogonal with H H^T = m I, so for an
+    # integer lower-triangular L0 and Xi = L0 H[:n] the estimate is L0 L0^T exactly
+    rng = np.random.default_rng(3)
+    for n, m in [(5, 8), (12, 16), (16, 64)]:
+        L0 = np.tril(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+        np.fill_diagonal(L0, rng.integers(1, 4, size=n))
+        Xi = L0 @ _hadamard(m)[:n]
+        assert np.array_equal(O.cov_from_residuals(Xi), L0 @ L0.T)
+
+
+def test_empirical_cov_closed_forms_and_invariants():
+    rng = np.random.default_rng(5)
+    # scaled identity columns: U = c^2 / n I
+    assert np.array_equal(O.cov_from_residuals(2.0 * np.eye(4)), np.eye(4))
+    # one nonzero entry among m columns: U = a^2 / m at (i, i) only
+    Xi = np.zeros((6, 8))
+    Xi[2, 5] = 3.0
+    U = O.cov_from_residuals(Xi)
+    E = np.zeros((6, 6))
+    E[2, 2] = 9.0 / 8.0
+    assert np.array_equal(U, E)
+    # trace = squared Frobenius norm / m; symmetric; positive semidefinite
+    Xi = rng.standard_normal((30, 17))
+    U = O.cov_from_residuals(Xi)
+    assert abs(np.trace(U) - np.linalg.norm(Xi) ** 2 / 17) <= 1e-14 * np.trace(U)
+    assert np.array_equal(U, U.T)
+    assert np.linalg.eigvalsh(U).min() >= -1e-13 * np.trace(U)
+    assert np.linalg.matrix_rank(U) == 17  # m < n: singular without the perturbation
+    # the order of the residual vectors does not matter
+    perm = rng.permutation(17)
+    assert np.allclose(O.cov_from_residuals(Xi[:, perm]), U, rtol=0, atol=1e-14 * np.abs(U).max())
+    # the perturbation touches the diagonal only, by nugget_rel * max diag
+    Un = O.cov_from_residuals(Xi, 1e-3)
+    off = ~np.eye(30, dtype=bool)
+    assert np.array_equal(Un[off], U[off])
+    assert np.allclose(np.diag(Un) - np.diag(U), 1e-3 * np.diag(U).max(), rtol=1e-12, atol=0)
+    assert np.linalg.eigvalsh(Un).min() > 0
+
+
 # -------------------------------------------------------------------- RNG
 def _kat():
     rows = []
