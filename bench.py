@@ -242,6 +242,7 @@ def run_ours(a):
             extra["tf32_variant"] = tf32_variant(E, ctx, a, flops, extra.get("fp64_factor_ms"))
         if not a.no_empirical:
             extra["empirical_cov"] = empirical_variant(E, ctx, a)
+            extra["emulation"] = emulation_variant(E, ctx, a)
 
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
 
@@ -427,6 +428,41 @@ def empirical_variant(E, ctx, a) -> dict:
          "factor_status": int(info.status), "factor_ms": round(info.ms, 3),
          "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles))}
     return d
+
+
+def emulation_variant(E, ctx, a, T: int = 256) -> dict:
+    """Emulations from the mixed factor: T draws xi_t = L z_t, the VAR(3)
+    recursion with diagonal Phi (0.5, 0.2, 0.1 for every coefficient), and the
+    inverse SHT to an (L+1) x 2L grid per time step.  Times of the VAR and SHT
+    calls (host wall time of the synchronous calls) and grid points per second."""
+    import time
+    import torch
+
+    n = a.L * a.L
+    A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+    E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+    Xi = E._colmajor_empty(n, T, ctx.device)
+    E.emu_sample(ctx, A, T, seed=12, out=Xi)
+    A.free()
+    Ph = torch.tensor([0.5, 0.2, 0.1], dtype=torch.float64, device=Xi.device).repeat(n, 1)
+    nt, nph = a.L + 1, 2 * a.L
+    tv, ti = [], []
+    for r in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F = E.emu_var_recursion(ctx, Xi, Ph)
+        t1 = time.perf_counter()
+        Z = E.emu_isht(ctx, F, a.L, nt, nph)
+        t2 = time.perf_counter()
+        if r:
+            tv.append((t1 - t0) * 1e3)
+            ti.append((t2 - t1) * 1e3)
+    ims = statistics.median(ti)
+    out = {"time_steps": T, "grid": [nt, nph], "var_ms": round(statistics.median(tv), 3), "isht_ms": round(ims, 3),
+           "grid_points_per_s": round(nt * nph * T / (ims * 1e-3), 1), "finite": bool(torch.isfinite(Z).all())}
+    del Xi, F, Z
+    torch.cuda.empty_cache()
+    return out
 
 
 def cusolver_reference(E, ctx, a, flops) -> dict:

@@ -213,6 +213,30 @@ emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda,
  * the tile arena does not fit, EMU_ETIMEOUT if a bounded device wait expired. */
 emu_status emu_cov_from_residuals(emu_ctx *ctx, const double *dXi, int n, long m, long ldxi,
                                   double nugget_rel, int nb, emu_mat **out);
+/* The steps after sampling that turn draws into emulations ("Generating
+ * Emulations").  Coefficients are real-form, row k = l^2 + l + m as in
+ * emu_cov_params, one time step per column (column-major, device memory).
+ *
+ * emu_var_recursion: the VAR(P) recursion with diagonal Phi_p ("Modeling the
+ * Temporal Dependence"), f_t = sum_{p=1..P} Phi_p f_{t-p} + xi_t for
+ * t = 0 .. T-1 with f before t = 0 taken as zero.  Xi: n x T (ld ldxi);
+ * Phi: n x P (the diagonal of Phi_p in column p-1); F: n x T (ld ldf), may
+ * not overlap Xi.  0 <= P <= 8.
+ *
+ * emu_isht: the inverse spherical-harmonic transform of each column of F
+ * (n = L^2, ld ldf) to a grid of ntheta colatitudes t_i = pi i/(ntheta-1)
+ * (poles included) by nphi longitudes p_j = 2 pi j/nphi:
+ *   Z[i + j ntheta, t] = sum_{l<L, |m|<=l} F[l^2+l+m, t] Y_lm(t_i, p_j)
+ * with the real orthonormal basis Y_l0 = N_l0 P_l(cos t),
+ * Y_lm = sqrt(2) N_lm P_l^m(cos t) cos(m p), Y_l,-m = sqrt(2) N_lm P_l^m(cos t) sin(m p)
+ * (m > 0), N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!, P_l^m with the
+ * Condon-Shortley phase.  Z: ld ldz >= ntheta nphi.  1 <= L <= 2048.
+ * Both return EMU_EINVAL on bad arguments and synchronise the stream. */
+emu_status emu_var_recursion(emu_ctx *ctx, const double *dXi, int n, int T, long ldxi, const double *dPhi, int P,
+                             double *dF, long ldf);
+emu_status emu_isht(emu_ctx *ctx, const double *dF, int L, int T, long ldf, int ntheta, int nphi, double *dZ,
+                    long ldz);
+
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);
 /* Write the matrix as a dense FP64 lower triangle (upper set to 0) into dOut

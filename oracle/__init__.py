@@ -67,6 +67,10 @@ def _declare(L):
     L.orc_precision_map.argtypes = [i, dp, d, dp, i, ctypes.c_uint, i, u8p]
     L.orc_precision_map_band.argtypes = [i, i, d, u8p]
     L.orc_cov_from_residuals.argtypes = [i, lg, dp, lg, d, dp]
+    L.orc_var_recursion.argtypes = [i, i, dp, lg, dp, i, dp, lg]
+    L.orc_real_sh.argtypes = [i, i, d, d]
+    L.orc_real_sh.restype = d
+    L.orc_isht.argtypes = [i, i, dp, lg, i, i, dp, lg]
     L.orc_precision_map_band.restype = i
     L.orc_potrf_unblocked.argtypes = [i, dp, lg]
     L.orc_potrf_unblocked.restype = i
@@ -154,6 +158,30 @@ def cov_from_residuals(Xi, nugget_rel: float = 0.0):
     U = np.zeros((n, n), dtype=np.float64, order="F")
     lib().orc_cov_from_residuals(n, m, _dp(Xi), n, nugget_rel, _dp(U))
     return U
+
+
+def var_recursion(Xi, Phi):
+    """f_t = sum_p Phi[:, p-1] f_{t-p} + Xi[:, t], f before t = 0 zero (n x T)."""
+    Xi = np.asfortranarray(Xi, dtype=np.float64)
+    n, T = Xi.shape
+    P = 0 if Phi is None else Phi.shape[1]
+    Ph = np.asfortranarray(Phi if P else np.zeros((n, 1)), dtype=np.float64)
+    F = np.zeros((n, T), dtype=np.float64, order="F")
+    lib().orc_var_recursion(n, T, _dp(Xi), n, _dp(Ph), P, _dp(F), n)
+    return F
+
+
+def real_sh(l: int, m: int, theta: float, phi: float) -> float:
+    return lib().orc_real_sh(l, m, theta, phi)
+
+
+def isht(F, L: int, ntheta: int, nphi: int):
+    """Synthesis of each column of F (L^2 x T) on the grid: (ntheta*nphi x T), point (i, j) at row i + j*ntheta."""
+    F = np.asfortranarray(F, dtype=np.float64)
+    n, T = F.shape
+    Z = np.zeros((ntheta * nphi, T), dtype=np.float64, order="F")
+    lib().orc_isht(L, T, _dp(F), n, ntheta, nphi, _dp(Z), ntheta * nphi)
+    return Z
 
 
 def potrf_unblocked(A):

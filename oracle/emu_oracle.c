@@ -190,6 +190,70 @@ void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nug
   }
 }
 
+static const double ORC_PI = 3.14159265358979323846;
+
+/* VAR(P) recursion of the coefficients with diagonal Phi_p ("Modeling the
+ * Temporal Dependence"): f_t = sum_{p=1..P} Phi_p f_{t-p} + xi_t, f before
+ * t = 0 zero.  Column-major n x T arrays, phi n x P (column p-1 = diag Phi_p). */
+void orc_var_recursion(int n, int T, const double *xi, long ldxi, const double *phi, int P, double *f, long ldf) {
+  for (int k = 0; k < n; k++)
+    for (int t = 0; t < T; t++) {
+      double v = 0.0;
+      for (int p = 1; p <= P; p++)
+        if (t - p >= 0) v += phi[k + (long)(p - 1) * n] * f[k + (long)(t - p) * ldf];
+      f[k + (long)t * ldf] = v + xi[k + (long)t * ldxi];
+    }
+}
+
+/* Real orthonormal spherical harmonic of degree l, order m (|m| <= l) at
+ * colatitude theta, longitude phi ("Spherical Harmonic Transform": the
+ * orthonormal Y_lm, real form): N_l|m| P_l^|m|(cos theta) times 1 (m = 0),
+ * sqrt(2) cos(m phi) (m > 0) or sqrt(2) sin(|m| phi) (m < 0), with
+ * N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)! and P_l^m carrying the
+ * Condon-Shortley phase.  P_l^m from the unnormalised three-term recurrence
+ * in l, the normalisation through log-factorials (valid while (2m-1)!! stays
+ * in range, l < 150). */
+double orc_real_sh(int l, int m, double theta, double phi) {
+  const int am = m < 0 ? -m : m;
+  const double x = cos(theta), sx = sin(theta);
+  double pmm = 1.0; /* P_am^am = (-1)^am (2am-1)!! sin^am */
+  for (int q = 1; q <= am; q++) pmm *= -(2.0 * q - 1.0) * sx;
+  double p = pmm;
+  if (l > am) {
+    double p0 = pmm, p1 = x * (2.0 * am + 1.0) * pmm; /* l = am + 1 */
+    for (int ll = am + 2; ll <= l; ll++) {
+      double p2 = ((2.0 * ll - 1.0) * x * p1 - (ll + am - 1.0) * p0) / (double)(ll - am);
+      p0 = p1;
+      p1 = p2;
+    }
+    p = p1;
+  }
+  const double lognorm = 0.5 * (log((2.0 * l + 1.0) / (4.0 * ORC_PI)) + lgamma(l - am + 1.0) - lgamma(l + am + 1.0));
+  double y = exp(lognorm) * p;
+  if (m > 0) y *= sqrt(2.0) * cos(m * phi);
+  if (m < 0) y *= sqrt(2.0) * sin(am * phi);
+  return y;
+}
+
+/* Inverse spherical-harmonic transform by the synthesis sum: for each column
+ * t of F (row k = l^2 + l + m), Z[i + j ntheta, t] = sum_{l,m} F[k, t]
+ * Y_lm(theta_i, phi_j), theta_i = pi i / (ntheta - 1), phi_j = 2 pi j / nphi. */
+void orc_isht(int L, int T, const double *F, long ldf, int ntheta, int nphi, double *Z, long ldz) {
+  for (int i = 0; i < ntheta; i++) {
+    const double th = ORC_PI * (double)i / (double)(ntheta - 1);
+    for (int j = 0; j < nphi; j++) {
+      const double ph = 2.0 * ORC_PI * (double)j / (double)nphi;
+      for (int t = 0; t < T; t++) Z[i + (long)j * ntheta + (long)t * ldz] = 0.0;
+      for (int l = 0; l < L; l++)
+        for (int m = -l; m <= l; m++) {
+          const double y = orc_real_sh(l, m, th, ph);
+          const long k = (long)l * l + l + m;
+          for (int t = 0; t < T; t++) Z[i + (long)j * ntheta + (long)t * ldz] += F[k + (long)t * ldf] * y;
+        }
+    }
+  }
+}
+
 /* -------------------------------------------------------------- Cholesky */
 int orc_potrf_unblocked(int n, double *A, long ld) {
   /* Cholesky-Banachiewicz: row i of L from rows 0..i-1. */

@@ -65,6 +65,9 @@ void orc_precision_map(int NT, const double *t, double eps, const double *u,
                        unsigned char *cls);
 int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls);
 void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nugget_rel, double *U);
+void orc_var_recursion(int n, int T, const double *xi, long ldxi, const double *phi, int P, double *f, long ldf);
+double orc_real_sh(int l, int m, double theta, double phi);
+void orc_isht(int L, int T, const double *F, long ldf, int ntheta, int nphi, double *Z, long ldz);
 
 /* Unblocked Cholesky (row-by-row, the textbook Cholesky-Banachiewicz form):
  * A = L L^T, L lower with positive diagonal, overwritten in place.

@@ -35,7 +35,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
-    "emu_mat_import_host", "emu_cov_from_residuals", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
     "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
@@ -104,6 +104,8 @@ def load() -> ctypes.CDLL:
     L.emu_mat_import_host.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
     L.emu_mat_import.argtypes = [vp, vp, i, lg, i, ctypes.POINTER(vp)]
     L.emu_cov_from_residuals.argtypes = [vp, vp, i, lg, lg, ctypes.c_double, i, ctypes.POINTER(vp)]
+    L.emu_var_recursion.argtypes = [vp, vp, i, i, lg, vp, i, vp, lg]
+    L.emu_isht.argtypes = [vp, vp, i, i, lg, i, i, vp, lg]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
     L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
@@ -292,6 +294,33 @@ def emu_cov_from_residuals(ctx: Context, Xi, nb: int = 256, nugget_rel=None, rai
             ctx._check(st, "emu_cov_from_residuals")
         return None, st
     return Mat(ctx, h), st
+
+
+def emu_var_recursion(ctx: Context, Xi, Phi):
+    """f_t = sum_p Phi[:, p-1] * f_{t-p} + Xi[:, t] (f before t = 0 zero): Xi (n x T),
+    Phi (n x P) float64 CUDA tensors; returns F (n x T, column-major)."""
+    n, T = Xi.shape
+    Xi = Xi if Xi.stride(0) == 1 else Xi.t().contiguous().t()
+    P = 0 if Phi is None else Phi.shape[1]
+    if P:
+        Phi = Phi if Phi.stride(0) == 1 and Phi.stride(1) == n else Phi.t().contiguous().t()
+    F = _colmajor_empty(n, T, ctx.device)
+    ctx._check(ctx.lib.emu_var_recursion(ctx.h, ctypes.c_void_p(_ptr(Xi)), n, T, Xi.stride(1) if T > 1 else n,
+                                         ctypes.c_void_p(_ptr(Phi)) if P else None, P, ctypes.c_void_p(_ptr(F)), n),
+               "emu_var_recursion")
+    return F
+
+
+def emu_isht(ctx: Context, F, L: int, ntheta: int, nphi: int):
+    """Inverse SHT of each column of F (L^2 x T) to an (ntheta x nphi) grid per
+    time step: returns Z as a (ntheta*nphi x T) column-major tensor, grid point
+    (i, j) at row i + j*ntheta."""
+    n, T = F.shape
+    F = F if F.stride(0) == 1 else F.t().contiguous().t()
+    Z = _colmajor_empty(ntheta * nphi, T, ctx.device)
+    ctx._check(ctx.lib.emu_isht(ctx.h, ctypes.c_void_p(_ptr(F)), L, T, F.stride(1) if T > 1 else n, ntheta, nphi,
+                                ctypes.c_void_p(_ptr(Z)), ntheta * nphi), "emu_isht")
+    return Z
 
 
 def emu_mat_import_host(ctx: Context, A, nb: int) -> Mat:

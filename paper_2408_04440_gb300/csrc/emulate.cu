@@ -1,0 +1,176 @@
+// emulate.cu -- the steps after sampling that turn draws of the coefficient
+// covariance into emulations ("Generating Emulations"): the VAR(P) recursion
+// of the spherical-harmonic coefficients with diagonal Phi_p, and the inverse
+// spherical-harmonic transform of the coefficients to a latitude-longitude
+// grid ("Spherical Harmonic Transform", the synthesis sum over (l, m)).
+//
+// Coefficients are real-form and ordered by degree then order,
+// k = l^2 + l + m, |m| <= l < L, as the covariance's rows.  The real basis:
+//   Y_l0 = N_l0 P_l(cos t),  Y_lm = sqrt(2) N_lm P_l^m(cos t) cos(m p) (m > 0),
+//   Y_l,-m = sqrt(2) N_lm P_l^m(cos t) sin(m p),  N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!,
+// P_l^m with the Condon-Shortley phase (-1)^m.  Grid: colatitudes
+// t_i = pi i / (ntheta - 1) (poles included), longitudes p_j = 2 pi j / nphi.
+#include <cmath>
+
+#include "emu_internal.h"
+
+namespace {
+
+__device__ inline bool failed(const int *st) { return *((volatile const int *)st) != DEV_OK; }
+
+// f_t = sum_p phi_p f_{t-p} + xi_t per coefficient (f before t = 0 is zero):
+// one thread per coefficient, the P previous values in registers.
+constexpr int kMaxP = 8;
+__global__ void k_var(const double *__restrict__ xi, long ldxi, int n, int T, const double *__restrict__ phi, int P,
+                      double *__restrict__ f, long ldf, const int *st) {
+  if (failed(st)) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double c[kMaxP], h[kMaxP];
+#pragma unroll
+  for (int p = 0; p < kMaxP; p++) {
+    c[p] = p < P ? phi[k + (long)p * n] : 0.0;
+    h[p] = 0.0;  // h[p] = f_{t-1-p}
+  }
+  for (int t = 0; t < T; t++) {
+    double v = 0.0;
+#pragma unroll
+    for (int p = 0; p < kMaxP; p++) v = fma(c[p], h[p], v);
+    v += xi[k + (long)t * ldxi];
+#pragma unroll
+    for (int p = kMaxP - 1; p > 0; p--) h[p] = h[p - 1];
+    h[0] = v;
+    f[k + (long)t * ldf] = v;
+  }
+}
+
+// Normalised associated Legendre table: lam[off(m) + (l - m) * ntheta + i] =
+// c_m N_lm P_l^m(cos t_i), c_0 = 1, c_m = sqrt(2), off(m) = ntheta * (m L - m(m-1)/2).
+// One thread per (m, i): the standard stable recursion in l,
+//   Pb_mm = -sqrt((2m+1)/(2m)) sin t Pb_{m-1,m-1},  Pb_00 = 1/sqrt(4 pi),
+//   Pb_{m+1,m} = sqrt(2m+3) cos t Pb_mm,
+//   Pb_lm = a_lm (cos t Pb_{l-1,m} - Pb_{l-2,m} / a_{l-1,m}),  a_lm = sqrt((4l^2-1)/(l^2-m^2)).
+__global__ void k_legendre(int L, int ntheta, double *__restrict__ lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+  if (i >= ntheta || m >= L) return;
+  const double th = M_PI * (double)i / (double)(ntheta - 1);
+  double s, c;
+  sincos(th, &s, &c);
+  double pmm = 0.28209479177387814;  // 1 / sqrt(4 pi)
+  for (int q = 1; q <= m; q++) pmm *= -sqrt((2.0 * q + 1.0) / (2.0 * q)) * s;
+  const double cm = m > 0 ? 1.4142135623730951 : 1.0;
+  double *out = lam + (size_t)ntheta * ((size_t)m * L - (size_t)m * (m - 1) / 2);
+  out[i] = cm * pmm;
+  if (m + 1 >= L) return;
+  double p1 = sqrt(2.0 * m + 3.0) * c * pmm;  // l = m + 1
+  out[(size_t)ntheta + i] = cm * p1;
+  double p0 = pmm, a_prev = sqrt(2.0 * m + 3.0);
+  for (int l = m + 2; l < L; l++) {
+    const double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+    const double p = a * (c * p1 - p0 / a_prev);
+    out[(size_t)(l - m) * ntheta + i] = cm * p;
+    p0 = p1;
+    p1 = p;
+    a_prev = a;
+  }
+}
+
+// Per order m and time t: A_m(t_i) = sum_l f_{l,m} lam_lm(t_i) and
+// B_m(t_i) = sum_l f_{l,-m} lam_lm(t_i) (m > 0).  ab[(m * 2 + {0,1}) * ntheta + i, t].
+__global__ void k_isht_legendre(int L, int T, const double *__restrict__ f, long ldf, int ntheta,
+                                const double *__restrict__ lam, double *__restrict__ ab, long ldab, const int *st) {
+  if (failed(st)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y, t = blockIdx.z;
+  if (i >= ntheta) return;
+  const double *lm = lam + (size_t)ntheta * ((size_t)m * L - (size_t)m * (m - 1) / 2);
+  const double *ft = f + (long)t * ldf;
+  double a = 0.0, b = 0.0;
+  for (int l = m; l < L; l++) {
+    const double y = lm[(size_t)(l - m) * ntheta + i];
+    a = fma(ft[(long)l * l + l + m], y, a);
+    if (m > 0) b = fma(ft[(long)l * l + l - m], y, b);
+  }
+  ab[(size_t)(2 * m) * ntheta + i + (long)t * ldab] = a;
+  ab[(size_t)(2 * m + 1) * ntheta + i + (long)t * ldab] = b;
+}
+
+// Z(t_i, p_j) = sum_m A_m(t_i) cos(m p_j) + B_m(t_i) sin(m p_j): one CTA per
+// (latitude ring, time), the ring's 2L sums in shared memory; cos / sin of
+// (m j mod nphi) 2 pi / nphi from a table.
+__global__ void k_isht_fourier(int L, int ntheta, int nphi, const double *__restrict__ ab, long ldab,
+                               const double *__restrict__ cs, double *__restrict__ z, long ldz, const int *st) {
+  if (failed(st)) return;
+  extern __shared__ double sab[];  // [2L]
+  const int i = blockIdx.x, t = blockIdx.y;
+  for (int q = threadIdx.x; q < 2 * L; q += blockDim.x) sab[q] = ab[(size_t)q * ntheta + i + (long)t * ldab];
+  __syncthreads();
+  for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+    double v = 0.0;
+    for (int m = 0; m < L; m++) {
+      const long r = ((long)m * j) % nphi;
+      v = fma(sab[2 * m], cs[2 * r], v);
+      v = fma(sab[2 * m + 1], cs[2 * r + 1], v);
+    }
+    z[i + (long)j * ntheta + (long)t * ldz] = v;
+  }
+}
+
+__global__ void k_cossin(int nphi, double *__restrict__ cs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nphi) return;
+  double s, c;
+  sincospi(2.0 * (double)r / (double)nphi, &s, &c);
+  cs[2 * r] = c;
+  cs[2 * r + 1] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+emu_status emu_var_recursion(emu_ctx *ctx, const double *dXi, int n, int T, long ldxi, const double *dPhi, int P,
+                             double *dF, long ldf) {
+  if (!ctx || !dXi || !dF || n < 1 || T < 1 || ldxi < n || ldf < n || P < 0 || P > kMaxP || (P > 0 && !dPhi))
+    return EMU_EINVAL;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), ctx->stream));
+  k_var<<<(n + 127) / 128, 128, 0, ctx->stream>>>(dXi, ldxi, n, T, dPhi, P, dF, ldf, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return EMU_OK;
+}
+
+emu_status emu_isht(emu_ctx *ctx, const double *dF, int L, int T, long ldf, int ntheta, int nphi, double *dZ,
+                    long ldz) {
+  if (!ctx || !dF || !dZ || L < 1 || L > 2048 || T < 1 || ldf < (long)L * L || ntheta < 2 || nphi < 1 ||
+      ldz < (long)ntheta * nphi)
+    return EMU_EINVAL;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), s));
+  const size_t nlam = (size_t)ntheta * ((size_t)L * (L + 1) / 2);
+  const long ldab = 2L * L * ntheta;
+  double *lam = nullptr, *ab = nullptr, *cs = nullptr;
+  cudaError_t e = cudaMallocAsync(&lam, nlam * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&ab, (size_t)ldab * T * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&cs, 2 * (size_t)nphi * sizeof(double), s);
+  emu_status st = EMU_OK;
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, PROF_SOLVE, 2.0 * (double)L * L * ntheta * T + 4.0 * (double)L * ntheta * nphi * T, 0.0);
+    k_legendre<<<dim3((ntheta + 127) / 128, L), 128, 0, s>>>(L, ntheta, lam);
+    k_cossin<<<(nphi + 255) / 256, 256, 0, s>>>(nphi, cs);
+    k_isht_legendre<<<dim3((ntheta + 127) / 128, L, T), 128, 0, s>>>(L, T, dF, ldf, ntheta, lam, ab, ldab,
+                                                                     ctx->d_status);
+    k_isht_fourier<<<dim3(ntheta, T), 256, 2 * L * sizeof(double), s>>>(L, ntheta, nphi, ab, ldab, cs, dZ, ldz,
+                                                                        ctx->d_status);
+    e = cudaGetLastError();
+    ctx->launches += 4;
+  }
+  for (void *p : {(void *)lam, (void *)ab, (void *)cs})
+    if (p) cudaFreeAsync(p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) st = emu_cuda_fail(ctx, e, "isht");
+  return st;
+}
+
+}  // extern "C"

@@ -161,6 +161,51 @@ def test_empirical_covariance_in_several_launches_then_factor(E, ctx):
     U.free()
 
 
+def test_var_recursion_matches_oracle(E, ctx):
+    import torch
+
+    rng = np.random.default_rng(6)
+    n, T, P = 500, 300, 3
+    Xi = rng.standard_normal((n, T))
+    Ph = rng.uniform(-0.3, 0.3, (n, P))
+    F = _np(E.emu_var_recursion(ctx, torch.from_numpy(np.asfortranarray(Xi)).cuda(),
+                                torch.from_numpy(np.asfortranarray(Ph)).cuda()))
+    Fo = O.var_recursion(Xi, Ph)
+    assert np.abs(F - Fo).max() <= 1e-13 * np.abs(Fo).max()
+
+
+@pytest.mark.parametrize("L,nt,nph", [(24, 25, 48), (9, 10, 17)])
+def test_isht_matches_oracle(E, ctx, L, nt, nph):
+    import torch
+
+    rng = np.random.default_rng(L)
+    T = 4
+    F = rng.standard_normal((L * L, T)) / (1.0 + np.repeat(np.arange(L), 2 * np.arange(L) + 1))[:, None]
+    Z = _np(E.emu_isht(ctx, torch.from_numpy(np.asfortranarray(F)).cuda(), L, nt, nph))
+    Zo = O.isht(F, L, nt, nph)
+    assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()
+
+
+def test_emulation_chain_from_the_mixed_factor(E, ctx):
+    # draws xi = L z of the mixed factor, VAR(3) in time, synthesis on the grid:
+    # the chain runs in our kernels and equals the oracle's VAR and synthesis of
+    # the same draws
+    import torch
+
+    Lb, nb, beta, T = 16, 256, 4.0, 40
+    A = E.emu_cov_build(ctx, Lb, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=1e-8)
+    Xi = E.emu_sample(ctx, A, T, seed=8)
+    A.free()
+    n = Lb * Lb
+    Ph = torch.from_numpy(np.asfortranarray(np.tile([0.5, 0.2, 0.1], (n, 1)))).cuda()
+    F = E.emu_var_recursion(ctx, Xi, Ph)
+    Z = _np(E.emu_isht(ctx, F, Lb, Lb + 1, 2 * Lb))
+    Fo = O.var_recursion(_np(Xi), _np(Ph))
+    Zo = O.isht(Fo, Lb, Lb + 1, 2 * Lb)
+    assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()
+
+
 @pytest.mark.parametrize("bad", [1, 70, 199])
 def test_not_positive_definite_reports_pivot(E, ctx, bad):
     import torch

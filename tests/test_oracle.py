@@ -298,6 +298,57 @@ def test_empirical_cov_closed_forms_and_invariants():
     assert np.linalg.eigvalsh(Un).min() > 0
 
 
+# VAR recursion and inverse SHT of the emulation steps ("Generating Emulations").
+def test_var_recursion_closed_forms():
+    rng = np.random.default_rng(1)
+    Xi = rng.standard_normal((5, 9))
+    assert np.array_equal(O.var_recursion(Xi, None), Xi)            # no lags: f = xi
+    assert np.array_equal(O.var_recursion(Xi, np.zeros((5, 2))), Xi)
+    imp = np.zeros((3, 12))
+    imp[:, 0] = 1.0
+    F = O.var_recursion(imp, np.full((3, 1), 0.5))                   # AR(1) impulse: phi^t
+    assert np.array_equal(F[0], 0.5 ** np.arange(12))
+    F = O.var_recursion(imp, np.tile([1.0, -1.0], (3, 1)))           # f_t = f_{t-1} - f_{t-2}: period 6
+    assert np.array_equal(F[1], np.resize([1.0, 1.0, 0.0, -1.0, -1.0, 0.0], 12))
+    # linearity in the innovations
+    X2 = rng.standard_normal((5, 9))
+    Ph = rng.uniform(-0.3, 0.3, (5, 3))
+    assert np.allclose(O.var_recursion(Xi + X2, Ph), O.var_recursion(Xi, Ph) + O.var_recursion(X2, Ph), atol=1e-14)
+
+
+def test_real_spherical_harmonics_pins():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        th, ph = rng.uniform(0, math.pi), rng.uniform(0, 2 * math.pi)
+        # closed forms (Condon-Shortley phase, real form)
+        c = math.sqrt(3 / (4 * math.pi))
+        assert abs(O.real_sh(0, 0, th, ph) - 1 / math.sqrt(4 * math.pi)) < 1e-15
+        assert abs(O.real_sh(1, 0, th, ph) - c * math.cos(th)) < 1e-15
+        assert abs(O.real_sh(1, 1, th, ph) + c * math.sin(th) * math.cos(ph)) < 1e-15
+        assert abs(O.real_sh(1, -1, th, ph) + c * math.sin(th) * math.sin(ph)) < 1e-15
+        assert abs(O.real_sh(2, 0, th, ph) - math.sqrt(5 / (16 * math.pi)) * (3 * math.cos(th) ** 2 - 1)) < 1e-14
+        # addition theorem: sum_m Y_lm^2 = (2l+1)/(4 pi) at every point
+        for l in (3, 17, 60):
+            s2 = sum(O.real_sh(l, m, th, ph) ** 2 for m in range(-l, l + 1))
+            assert abs(s2 - (2 * l + 1) / (4 * math.pi)) <= 1e-12 * (2 * l + 1)
+
+
+def test_isht_single_coefficients_and_orthonormality():
+    L, nt, nph = 5, 181, 64
+    n = L * L
+    Z = O.isht(np.eye(n), L, nt, nph)  # column k: Y_k on the grid
+    th = np.pi * np.arange(nt) / (nt - 1)
+    # column of Y_10 is sqrt(3/4pi) cos(theta) on every longitude
+    y10 = Z[:, 2].reshape(nph, nt)
+    assert np.allclose(y10, np.sqrt(3 / (4 * np.pi)) * np.cos(th)[None, :], atol=1e-15)
+    # orthonormality by quadrature (trapezoid in theta with sin weights, exact in phi)
+    w = np.sin(th) * (np.pi / (nt - 1))
+    w[[0, -1]] *= 0.5
+    W = np.tile(w, nph) * (2 * np.pi / nph)
+    G = Z.T @ (Z * W[:, None])
+    assert np.abs(G - np.eye(n)).max() < 1e-3  # the trapezoid rule in theta is second order: h^2 ~ 3e-4
+
+
 # -------------------------------------------------------------------- RNG
 def _kat():
     rows = []
