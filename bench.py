@@ -432,9 +432,10 @@ def empirical_variant(E, ctx, a) -> dict:
 
 def emulation_variant(E, ctx, a, T: int = 256) -> dict:
     """Emulations from the mixed factor: T draws xi_t = L z_t, the VAR(3)
-    recursion with diagonal Phi (0.5, 0.2, 0.1 for every coefficient), and the
-    inverse SHT to an (L+1) x 2L grid per time step.  Times of the VAR and SHT
-    calls (host wall time of the synchronous calls) and grid points per second."""
+    recursion with diagonal Phi (0.5, 0.2, 0.1 for every coefficient), the
+    inverse SHT to an (L+1) x 2L grid per time step, and the forward SHT of
+    those grids back to coefficients.  Times of the calls (host wall time of
+    the synchronous calls), grid points per second, round-trip error."""
     import time
     import torch
 
@@ -458,9 +459,20 @@ def emulation_variant(E, ctx, a, T: int = 256) -> dict:
             tv.append((t1 - t0) * 1e3)
             ti.append((t2 - t1) * 1e3)
     ims = statistics.median(ti)
+    # the forward transform of the same grids recovers the coefficients (band-limited data, ntheta = L + 1)
+    tf = []
+    for r in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F2 = E.emu_sht(ctx, Z, a.L, nt, nph)
+        t1 = time.perf_counter()
+        if r:
+            tf.append((t1 - t0) * 1e3)
+    rt = float((F2 - F).abs().max() / F.abs().max())
     out = {"time_steps": T, "grid": [nt, nph], "var_ms": round(statistics.median(tv), 3), "isht_ms": round(ims, 3),
-           "grid_points_per_s": round(nt * nph * T / (ims * 1e-3), 1), "finite": bool(torch.isfinite(Z).all())}
-    del Xi, F, Z
+           "sht_ms": round(statistics.median(tf), 3), "grid_points_per_s": round(nt * nph * T / (ims * 1e-3), 1),
+           "sht_round_trip_rel_err": rt, "finite": bool(torch.isfinite(Z).all())}
+    del Xi, F, Z, F2
     torch.cuda.empty_cache()
     return out
 

@@ -236,6 +236,19 @@ emu_status emu_var_recursion(emu_ctx *ctx, const double *dXi, int n, int T, long
                              double *dF, long ldf);
 emu_status emu_isht(emu_ctx *ctx, const double *dF, int L, int T, long ldf, int ntheta, int nphi, double *dZ,
                     long ldz);
+/* emu_sht: the forward transform of grid data Z (layout of emu_isht) to the
+ * real-form coefficients F (L^2 x T, ld ldf), by the paper's method
+ * ("Spherical Harmonic Transform"): the integral in longitude by a DFT
+ * (C_m, S_m), the extension of each to the full circle in colatitude
+ * (g(2 pi - t) = (-1)^m g(t)), its Fourier coefficients K_q, and their
+ * contraction with S_{l,m,q} = sum_q' c_{l,m,q'} I(q + q'), c the Fourier
+ * coefficients of the extended Legendre factor of Y_lm and
+ * I(k) = int_0^pi e^{ikt} sin t dt.  Exact for data band-limited at L when
+ * ntheta > L and nphi >= 2L - 1 (the synthesis of emu_isht is then inverted).
+ * Shared-memory bound: (4 (2L-1) + ntheta) doubles <= 48 KB; EMU_EINVAL
+ * beyond it. */
+emu_status emu_sht(emu_ctx *ctx, const double *dZ, int ntheta, int nphi, int T, long ldz, int L, double *dF,
+                   long ldf);
 
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);

@@ -71,6 +71,8 @@ def _declare(L):
     L.orc_real_sh.argtypes = [i, i, d, d]
     L.orc_real_sh.restype = d
     L.orc_isht.argtypes = [i, i, dp, lg, i, i, dp, lg]
+    L.orc_sht.argtypes = [i, i, dp, lg, i, i, dp, lg]
+    L.orc_I_pub.argtypes = [i, dp, dp]
     L.orc_precision_map_band.restype = i
     L.orc_potrf_unblocked.argtypes = [i, dp, lg]
     L.orc_potrf_unblocked.restype = i
@@ -182,6 +184,22 @@ def isht(F, L: int, ntheta: int, nphi: int):
     Z = np.zeros((ntheta * nphi, T), dtype=np.float64, order="F")
     lib().orc_isht(L, T, _dp(F), n, ntheta, nphi, _dp(Z), ntheta * nphi)
     return Z
+
+
+def sht(Z, L: int, ntheta: int, nphi: int):
+    """Forward SHT (the paper's method: DFT in longitude, circle extension in colatitude, I(q) contraction) of
+    each column of Z ((ntheta*nphi) x T, point (i, j) at row i + j*ntheta): real-form coefficients (L^2 x T)."""
+    Z = np.asfortranarray(Z, dtype=np.float64)
+    T = Z.shape[1]
+    F = np.zeros((L * L, T), dtype=np.float64, order="F")
+    lib().orc_sht(L, T, _dp(Z), ntheta * nphi, ntheta, nphi, _dp(F), L * L)
+    return F
+
+
+def I_of(k: int) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_I_pub(k, ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
 
 
 def potrf_unblocked(A):

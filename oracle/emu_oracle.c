@@ -254,6 +254,110 @@ void orc_isht(int L, int T, const double *F, long ldf, int ntheta, int nphi, dou
   }
 }
 
+/* Forward spherical-harmonic transform on the equiangular grid of orc_isht
+ * ("Spherical Harmonic Transform": the coefficient as the integral of Z times
+ * Y_lm over the sphere, computed through G_m(theta), its extension to the
+ * full circle in theta, its Fourier coefficients K, and the integrals
+ * I(q) = int_0^pi e^{i q t} sin t dt).  Real-form coefficients of the basis of
+ * orc_real_sh.  Steps, per column t of Z:
+ *   C_m(t_i) = (2 pi / nphi) sum_j Z_ij cos(m p_j),  S_m(t_i) = (same) sin(m p_j);
+ *   g(t_{M-i}) = (-1)^m g(t_i) extends g in {C_m, S_m} to M = 2 ntheta - 2 points
+ *     t_i = 2 pi i / M of the circle (Z(2pi - t, p) = Z(t, p + pi));
+ *   K_q = (1/M) sum_i g(t_i) e^{-i q t_i},  |q| < L;
+ *   h_lm(t) = c_m N_lm P_l^m(cos t) extends the same way; its coefficients
+ *     c_q' likewise; S_{l,m,q} = sum_q' c_q' I(q + q');
+ *   f_{l,m} = Re sum_q K_q(C_m) S_{l,m,q},  f_{l,-m} = Re sum_q K_q(S_m) S_{l,m,q}.
+ * Exact for data band-limited at L when ntheta > L and nphi >= 2L - 1. */
+static void orc_I(int k, double *re, double *im) {
+  if (k == 1 || k == -1) {
+    *re = 0.0;
+    *im = k * ORC_PI / 2.0;
+  } else {
+    *re = (k % 2 == 0) ? 2.0 / (1.0 - (double)k * k) : 0.0;
+    *im = 0.0;
+  }
+}
+void orc_I_pub(int k, double *re, double *im) { orc_I(k, re, im); }
+
+void orc_sht(int L, int T, const double *Z, long ldz, int ntheta, int nphi, double *F, long ldf) {
+  const int M = 2 * ntheta - 2, Q = 2 * L - 1;
+  double *g = (double *)malloc(sizeof(double) * M);
+  double *Kr = (double *)malloc(sizeof(double) * Q), *Ki = (double *)malloc(sizeof(double) * Q);
+  double *cr = (double *)malloc(sizeof(double) * Q), *ci = (double *)malloc(sizeof(double) * Q);
+  double *Sr = (double *)malloc(sizeof(double) * Q), *Si = (double *)malloc(sizeof(double) * Q);
+  double *CS = (double *)malloc(sizeof(double) * 2 * (size_t)L * ntheta);
+  for (int t = 0; t < T; t++) {
+    const double *z = Z + (long)t * ldz;
+    /* C_m, S_m on the ntheta rings */
+    for (int m = 0; m < L; m++)
+      for (int i = 0; i < ntheta; i++) {
+        double c = 0.0, sn = 0.0;
+        for (int j = 0; j < nphi; j++) {
+          const double ph = 2.0 * ORC_PI * (double)(((long)m * j) % nphi) / (double)nphi;
+          c += z[i + (long)j * ntheta] * cos(ph);
+          sn += z[i + (long)j * ntheta] * sin(ph);
+        }
+        CS[(2 * m) * ntheta + i] = c * 2.0 * ORC_PI / nphi;
+        CS[(2 * m + 1) * ntheta + i] = sn * 2.0 * ORC_PI / nphi;
+      }
+    for (int m = 0; m < L; m++) {
+      const double sgn = (m % 2 == 0) ? 1.0 : -1.0;
+      for (int cs = 0; cs < 2; cs++) {
+        if (m == 0 && cs == 1) continue;
+        /* extension and Fourier coefficients of g */
+        for (int i = 0; i < ntheta; i++) g[i] = CS[(2 * m + cs) * ntheta + i];
+        for (int i = ntheta; i < M; i++) g[i] = sgn * g[M - i];
+        for (int q = -(L - 1); q <= L - 1; q++) {
+          double re = 0.0, im = 0.0;
+          for (int i = 0; i < M; i++) {
+            const double a = 2.0 * ORC_PI * (double)((((long)q * i) % M + M) % M) / (double)M;
+            re += g[i] * cos(a);
+            im -= g[i] * sin(a);
+          }
+          Kr[q + L - 1] = re / M;
+          Ki[q + L - 1] = im / M;
+        }
+        for (int l = m; l < L; l++) {
+          /* coefficients of h_lm on the same circle, then S and the contraction */
+          for (int i = 0; i < ntheta; i++) g[i] = orc_real_sh(l, m, 2.0 * ORC_PI * i / M, 0.0);
+          for (int i = ntheta; i < M; i++) g[i] = sgn * g[M - i];
+          for (int q = -(L - 1); q <= L - 1; q++) {
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < M; i++) {
+              const double a = 2.0 * ORC_PI * (double)((((long)q * i) % M + M) % M) / (double)M;
+              re += g[i] * cos(a);
+              im -= g[i] * sin(a);
+            }
+            cr[q + L - 1] = re / M;
+            ci[q + L - 1] = im / M;
+          }
+          double fr = 0.0;
+          for (int q = -(L - 1); q <= L - 1; q++) {
+            double sr = 0.0, si = 0.0;
+            for (int q2 = -(L - 1); q2 <= L - 1; q2++) {
+              double ir, ii;
+              orc_I(q + q2, &ir, &ii);
+              sr += cr[q2 + L - 1] * ir - ci[q2 + L - 1] * ii;
+              si += cr[q2 + L - 1] * ii + ci[q2 + L - 1] * ir;
+            }
+            fr += Kr[q + L - 1] * sr - Ki[q + L - 1] * si;
+          }
+          const long k = (long)l * l + l + (cs == 0 ? m : -m);
+          F[k + (long)t * ldf] = fr;
+        }
+      }
+    }
+  }
+  free(g);
+  free(Kr);
+  free(Ki);
+  free(cr);
+  free(ci);
+  free(Sr);
+  free(Si);
+  free(CS);
+}
+
 /* -------------------------------------------------------------- Cholesky */
 int orc_potrf_unblocked(int n, double *A, long ld) {
   /* Cholesky-Banachiewicz: row i of L from rows 0..i-1. */

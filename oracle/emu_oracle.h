@@ -68,6 +68,8 @@ void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nug
 void orc_var_recursion(int n, int T, const double *xi, long ldxi, const double *phi, int P, double *f, long ldf);
 double orc_real_sh(int l, int m, double theta, double phi);
 void orc_isht(int L, int T, const double *F, long ldf, int ntheta, int nphi, double *Z, long ldz);
+void orc_sht(int L, int T, const double *Z, long ldz, int ntheta, int nphi, double *F, long ldf);
+void orc_I_pub(int k, double *re, double *im);
 
 /* Unblocked Cholesky (row-by-row, the textbook Cholesky-Banachiewicz form):
  * A = L L^T, L lower with positive diagonal, overwritten in place.

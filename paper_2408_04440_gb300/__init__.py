@@ -35,7 +35,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
-    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
     "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
@@ -106,6 +106,7 @@ def load() -> ctypes.CDLL:
     L.emu_cov_from_residuals.argtypes = [vp, vp, i, lg, lg, ctypes.c_double, i, ctypes.POINTER(vp)]
     L.emu_var_recursion.argtypes = [vp, vp, i, i, lg, vp, i, vp, lg]
     L.emu_isht.argtypes = [vp, vp, i, i, lg, i, i, vp, lg]
+    L.emu_sht.argtypes = [vp, vp, i, i, i, lg, i, vp, lg]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
     L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
@@ -321,6 +322,17 @@ def emu_isht(ctx: Context, F, L: int, ntheta: int, nphi: int):
     ctx._check(ctx.lib.emu_isht(ctx.h, ctypes.c_void_p(_ptr(F)), L, T, F.stride(1) if T > 1 else n, ntheta, nphi,
                                 ctypes.c_void_p(_ptr(Z)), ntheta * nphi), "emu_isht")
     return Z
+
+
+def emu_sht(ctx: Context, Z, L: int, ntheta: int, nphi: int):
+    """Forward SHT of each column of Z ((ntheta*nphi) x T, grid point (i, j) at row
+    i + j*ntheta) to real-form coefficients: returns F (L^2 x T, column-major)."""
+    npts, T = Z.shape
+    Z = Z if Z.stride(0) == 1 else Z.t().contiguous().t()
+    F = _colmajor_empty(L * L, T, ctx.device)
+    ctx._check(ctx.lib.emu_sht(ctx.h, ctypes.c_void_p(_ptr(Z)), ntheta, nphi, T, Z.stride(1) if T > 1 else npts, L,
+                               ctypes.c_void_p(_ptr(F)), L * L), "emu_sht")
+    return F
 
 
 def emu_mat_import_host(ctx: Context, A, nb: int) -> Mat:

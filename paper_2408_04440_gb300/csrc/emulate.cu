@@ -124,6 +124,127 @@ __global__ void k_cossin(int nphi, double *__restrict__ cs) {
   cs[2 * r + 1] = s;
 }
 
+// ---------------------------------------------------------------- forward SHT
+// The forward transform of the grid data (the coefficient as the integral of
+// Z Y_lm over the sphere): C_m / S_m by a DFT in longitude, the circle
+// extension g(t_{M-i}) = (-1)^m g(t_i) over M = 2 ntheta - 2 colatitudes,
+// Fourier coefficients K_q of g, and the contraction with
+// S_{l,m,q} = sum_q' c_{l,m,q'} I(q + q'), c the Fourier coefficients of the
+// extended Legendre factor and I(k) = int_0^pi e^{ikt} sin t dt.
+
+// I(k): 2/(1-k^2) for even k, 0 for odd k other than +-1, +-i pi/2 at k = +-1.
+__device__ inline void I_of(int k, double &re, double &im) {
+  if (k == 1 || k == -1) {
+    re = 0.0;
+    im = k * 1.5707963267948966;
+  } else {
+    re = (k & 1) ? 0.0 : 2.0 / (1.0 - (double)k * k);
+    im = 0.0;
+  }
+}
+
+// C_m(t_i), S_m(t_i) = (2 pi / nphi) sum_j Z_ij {cos, sin}(m p_j): one CTA per
+// (ring, time), the ring in shared memory.  cs[(2m + {0,1}) * ntheta + i, t].
+__global__ void k_sht_fourier(const double *__restrict__ z, long ldz, int ntheta, int nphi, int L,
+                              const double *__restrict__ csp, double *__restrict__ cs, long ldcs, const int *st) {
+  if (failed(st)) return;
+  extern __shared__ double ring[];  // [nphi]
+  const int i = blockIdx.x, t = blockIdx.y;
+  for (int j = threadIdx.x; j < nphi; j += blockDim.x) ring[j] = z[i + (long)j * ntheta + (long)t * ldz];
+  __syncthreads();
+  const double w = 6.283185307179586 / (double)nphi;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    double c = 0.0, sn = 0.0;
+    for (int j = 0; j < nphi; j++) {
+      const long r = ((long)m * j) % nphi;
+      c = fma(ring[j], csp[2 * r], c);
+      sn = fma(ring[j], csp[2 * r + 1], sn);
+    }
+    cs[(size_t)(2 * m) * ntheta + i + (long)t * ldcs] = c * w;
+    cs[(size_t)(2 * m + 1) * ntheta + i + (long)t * ldcs] = sn * w;
+  }
+}
+
+// Fourier coefficients over the M-point circle of an extended function whose
+// first ntheta samples are v[0 .. ntheta) (v[i] at t_i = 2 pi i / M) and whose
+// reflection sign is sgn: out[q + L - 1] for |q| < L, complex.  cm: table of
+// cos / sin (2 pi r / M).
+__device__ inline void circle_coeffs(const double *v, double sgn, int ntheta, int M, int L, const double *cm,
+                                     double *outr, double *outi) {
+  for (int q = threadIdx.x - (L - 1); q <= L - 1; q += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < M; i++) {
+      const double g = i < ntheta ? v[i] : sgn * v[M - i];
+      const long r = (((long)q * i) % M + M) % M;
+      re = fma(g, cm[2 * r], re);
+      im = fma(-g, cm[2 * r + 1], im);
+    }
+    outr[q + L - 1] = re / M;
+    outi[q + L - 1] = im / M;
+  }
+}
+
+// S_{l,m,q} for one (l, m) per CTA: the Legendre factor's circle coefficients
+// in shared memory, then their convolution with I.  sq[(pair) * 2Q + {re, im} * Q + q].
+__global__ void k_sht_S(int L, int ntheta, const double *__restrict__ lam, const double *__restrict__ cm,
+                        double *__restrict__ sq) {
+  extern __shared__ double sh[];  // cr[Q], ci[Q], v[ntheta]
+  const int Q = 2 * L - 1, M = 2 * ntheta - 2;
+  double *cr = sh, *ci = sh + Q, *v = sh + 2 * Q;
+  const int pair = blockIdx.x;  // m * L - m (m - 1) / 2 + (l - m)
+  int m = 0;
+  while (pair >= (m + 1) * L - (m + 1) * m / 2) m++;
+  const int l = m + pair - (m * L - m * (m - 1) / 2);
+  const double *h = lam + (size_t)ntheta * pair;
+  for (int i = threadIdx.x; i < ntheta; i += blockDim.x) v[i] = h[i];
+  __syncthreads();
+  circle_coeffs(v, (m & 1) ? -1.0 : 1.0, ntheta, M, L, cm, cr, ci);
+  __syncthreads();
+  double *o = sq + (size_t)pair * 2 * Q;
+  for (int q = threadIdx.x - (L - 1); q <= L - 1; q += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int q2 = -(L - 1); q2 <= L - 1; q2++) {
+      double ir, ii;
+      I_of(q + q2, ir, ii);
+      sr += cr[q2 + L - 1] * ir - ci[q2 + L - 1] * ii;
+      si += cr[q2 + L - 1] * ii + ci[q2 + L - 1] * ir;
+    }
+    o[q + L - 1] = sr;
+    o[Q + q + L - 1] = si;
+  }
+  (void)l;
+}
+
+// K_q of C_m and S_m for one (m, time) per CTA, then the contraction
+// f_{l,+-m} = Re sum_q K_q S_{l,m,q} for l = m .. L-1.
+__global__ void k_sht_contract(int L, int T, int ntheta, const double *__restrict__ cs, long ldcs,
+                               const double *__restrict__ cm, const double *__restrict__ sq, double *__restrict__ f,
+                               long ldf, const int *st) {
+  if (failed(st)) return;
+  extern __shared__ double sh[];  // kc_r, kc_i, ks_r, ks_i [Q each], v [ntheta]
+  const int Q = 2 * L - 1, M = 2 * ntheta - 2;
+  const int m = blockIdx.x, t = blockIdx.y;
+  double *kcr = sh, *kci = sh + Q, *ksr = sh + 2 * Q, *ksi = sh + 3 * Q, *v = sh + 4 * Q;
+  const double sgn = (m & 1) ? -1.0 : 1.0;
+  for (int c = 0; c < 2; c++) {
+    for (int i = threadIdx.x; i < ntheta; i += blockDim.x) v[i] = cs[(size_t)(2 * m + c) * ntheta + i + (long)t * ldcs];
+    __syncthreads();
+    circle_coeffs(v, sgn, ntheta, M, L, cm, c ? ksr : kcr, c ? ksi : kci);
+    __syncthreads();
+  }
+  const size_t pair0 = (size_t)m * L - (size_t)m * (m - 1) / 2;
+  for (int l = m + threadIdx.x; l < L; l += blockDim.x) {
+    const double *o = sq + (pair0 + (l - m)) * 2 * Q;
+    double fc = 0.0, fs = 0.0;
+    for (int q = 0; q < Q; q++) {
+      fc += kcr[q] * o[q] - kci[q] * o[Q + q];
+      fs += ksr[q] * o[q] - ksi[q] * o[Q + q];
+    }
+    f[(long)l * l + l + m + (long)t * ldf] = fc;
+    if (m > 0) f[(long)l * l + l - m + (long)t * ldf] = fs;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -171,6 +292,48 @@ emu_status emu_isht(emu_ctx *ctx, const double *dF, int L, int T, long ldf, int 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) st = emu_cuda_fail(ctx, e, "isht");
   return st;
+}
+
+
+emu_status emu_sht(emu_ctx *ctx, const double *dZ, int ntheta, int nphi, int T, long ldz, int L, double *dF,
+                   long ldf) {
+  if (!ctx || !dZ || !dF || L < 1 || L > 1024 || T < 1 || ntheta < 2 || nphi < 1 || ldz < (long)ntheta * nphi ||
+      ldf < (long)L * L)
+    return EMU_EINVAL;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), s));
+  const int Q = 2 * L - 1, M = 2 * ntheta - 2;
+  const size_t npair = (size_t)L * (L + 1) / 2;
+  const long ldcs = 2L * L * ntheta;
+  double *lam = nullptr, *csp = nullptr, *cm = nullptr, *sq = nullptr, *cs = nullptr;
+  cudaError_t e = cudaMallocAsync(&lam, npair * ntheta * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&csp, 2 * (size_t)nphi * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&cm, 2 * (size_t)M * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&sq, npair * 2 * Q * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&cs, (size_t)ldcs * T * sizeof(double), s);
+  const size_t sm_S = (2 * (size_t)Q + ntheta) * sizeof(double), sm_K = (4 * (size_t)Q + ntheta) * sizeof(double);
+  if (e == cudaSuccess && (sm_S > 48 * 1024 || sm_K > 48 * 1024 || nphi * sizeof(double) > 48 * 1024)) {
+    e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, PROF_SOLVE, 2.0 * (double)L * ntheta * nphi * T + 8.0 * (double)L * Q * M * T, 0.0);
+    k_legendre<<<dim3((ntheta + 127) / 128, L), 128, 0, s>>>(L, ntheta, lam);
+    k_cossin<<<(nphi + 255) / 256, 256, 0, s>>>(nphi, csp);
+    k_cossin<<<(M + 255) / 256, 256, 0, s>>>(M, cm);
+    k_sht_S<<<(unsigned)npair, 128, sm_S, s>>>(L, ntheta, lam, cm, sq);
+    k_sht_fourier<<<dim3(ntheta, T), 128, nphi * sizeof(double), s>>>(dZ, ldz, ntheta, nphi, L, csp, cs, ldcs,
+                                                                      ctx->d_status);
+    k_sht_contract<<<dim3(L, T), 128, sm_K, s>>>(L, T, ntheta, cs, ldcs, cm, sq, dF, ldf, ctx->d_status);
+    e = cudaGetLastError();
+    ctx->launches += 6;
+  }
+  for (void *p : {(void *)lam, (void *)csp, (void *)cm, (void *)sq, (void *)cs})
+    if (p) cudaFreeAsync(p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaErrorInvalidValue) return EMU_EINVAL;
+  if (e != cudaSuccess) return emu_cuda_fail(ctx, e, "sht");
+  return EMU_OK;
 }
 
 }  // extern "C"

@@ -186,6 +186,21 @@ def test_isht_matches_oracle(E, ctx, L, nt, nph):
     assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()
 
 
+@pytest.mark.parametrize("L,nt,nph", [(24, 25, 48), (9, 20, 31)])
+def test_sht_matches_oracle_and_inverts_isht(E, ctx, L, nt, nph):
+    import torch
+
+    rng = np.random.default_rng(L + nt)
+    T = 3
+    Z = rng.standard_normal((nt * nph, T))  # not band-limited: the method's estimate
+    F = _np(E.emu_sht(ctx, torch.from_numpy(np.asfortranarray(Z)).cuda(), L, nt, nph))
+    Fo = O.sht(Z, L, nt, nph)
+    assert np.abs(F - Fo).max() <= 1e-12 * np.abs(Fo).max()
+    f0 = rng.standard_normal((L * L, T))
+    Zb = E.emu_isht(ctx, torch.from_numpy(np.asfortranarray(f0)).cuda(), L, nt, nph)
+    assert np.abs(_np(E.emu_sht(ctx, Zb, L, nt, nph)) - f0).max() <= 1e-12  # exact recovery
+
+
 def test_emulation_chain_from_the_mixed_factor(E, ctx):
     # draws xi = L z of the mixed factor, VAR(3) in time, synthesis on the grid:
     # the chain runs in our kernels and equals the oracle's VAR and synthesis of

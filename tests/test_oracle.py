@@ -349,6 +349,26 @@ def test_isht_single_coefficients_and_orthonormality():
     assert np.abs(G - np.eye(n)).max() < 1e-3  # the trapezoid rule in theta is second order: h^2 ~ 3e-4
 
 
+def test_forward_sht_pins():
+    # I(q) = int_0^pi e^{iqt} sin t dt, worked by hand
+    assert O.I_of(0) == 2.0 and abs(O.I_of(2) + 2.0 / 3.0) < 1e-16 and O.I_of(3) == 0.0
+    assert abs(O.I_of(1) - 1j * math.pi / 2) < 1e-16 and abs(O.I_of(-1) + 1j * math.pi / 2) < 1e-16
+    # the constant field 1 has f_00 = int Y_00 = sqrt(4 pi) and nothing else
+    L, nt, nph = 5, 6, 10
+    F = O.sht(np.ones((nt * nph, 1)), L, nt, nph)
+    assert abs(F[0, 0] - math.sqrt(4 * math.pi)) < 1e-13 and np.abs(F[1:, 0]).max() < 1e-13
+    # exact recovery of band-limited data on the paper's minimal grid (ntheta = L + 1,
+    # nphi = 2L) and on a larger one: the synthesis sum is inverted
+    rng = np.random.default_rng(7)
+    for L, nt, nph in [(6, 7, 12), (9, 10, 17), (8, 20, 31)]:
+        f0 = rng.standard_normal((L * L, 3))
+        assert np.abs(O.sht(O.isht(f0, L, nt, nph), L, nt, nph) - f0).max() < 1e-12
+    # one coarser grid (ntheta = L) is no longer exact
+    L = 8
+    f0 = rng.standard_normal((L * L, 1))
+    assert np.abs(O.sht(O.isht(f0, L, L, 2 * L), L, L, 2 * L) - f0).max() > 1e-6
+
+
 # -------------------------------------------------------------------- RNG
 def _kat():
     rows = []
