@@ -9,7 +9,8 @@
 //               products with p + q < NS, product (p, q) into the group
 //               accumulator g = p + q (TMEM columns g * 64 .. g * 64 + 63).
 //   warps 2..5  epilogue: every KCHUNK of K, the 8 group accumulators are
-//               added in FP64 into per-thread registers, smallest group first;
+//               folded in integer arithmetic and added in FP64 into
+//               per-thread registers (fold_groups);
 //               after the last chunk the row scales are applied and the block
 //               is subtracted from the FP64 output.
 // The 8 accumulators fill TMEM, so the MMA warp waits for the epilogue to
@@ -48,9 +49,27 @@ struct Shared {
 };
 static_assert(sizeof(Shared) <= BAR_BYTES, "barrier block");
 
-// Weight 2^-7(g+2) of the digit products of group g = p + q.
-__constant__ double kGroupWeight[NS] = {0x1p-14, 0x1p-21, 0x1p-28, 0x1p-35, 0x1p-42, 0x1p-49, 0x1p-56, 0x1p-63};
-static_assert(NS == 8 && SLICE_BITS == 7, "kGroupWeight is written for 8 digits of 7 bits");
+// acc + sum_g G_g 2^-7(g+2) for the group sums G_g of one output (column x
+// of r[g]).  Each G_g is an integer held exactly in FP32 (below 2^24, see
+// the header), so the sum is formed in integer arithmetic: groups 2..7 by
+// Horner in 64 bits, T = sum_{g>=2} G_g 2^(7(7-g)), |T| < 2^59 (|G_g| <
+// 2^23.4 for g >= 1 with KCHUNK = 256: at most two products of a leading
+// digit, |d_0| <= 128, and g - 1 of trailing digits, |d_p| <= 64, per K
+// term), and groups 0..1 as Q = 2^7 G_0 + G_1, |Q| < 2^30 (|G_0| <= 2^22).
+// Then acc + T 2^-63 + Q 2^-21 takes two conversions and two FP64 FMAs
+// instead of eight of each: the FP64 pipe, GB300's slowest unit, bounds this
+// epilogue.  T is rounded once (its weight is below 2^-4 of the total).
+static_assert(NS == 8 && SLICE_BITS == 7 && KCHUNK <= 256, "fold_groups is written for 8 digits of 7 bits");
+__device__ __forceinline__ double fold_groups(const uint32_t (&r)[NS][4], int x, double acc) {
+  int gi[NS];
+#pragma unroll
+  for (int g = 0; g < NS; g++) gi[g] = __float2int_rn(__uint_as_float(r[g][x]));  // exact: integers below 2^24
+  long long t = gi[2];
+#pragma unroll
+  for (int g = 3; g < NS; g++) t = t * 128 + gi[g];
+  const int q = gi[0] * 128 + gi[1];
+  return fma((double)q, 0x1p-21, fma((double)t, 0x1p-63, acc));
+}
 
 __device__ inline bool failed(const int *st) { return *((volatile const int *)st) != DEV_OK; }
 
@@ -188,6 +207,56 @@ __global__ void __launch_bounds__(256)
     const int rr = w + 8 * q, r = r0 + rr;
     const double v = blk[rr][lane] * exp2i(-exp_of(exps, r));  // exact: |v| < 1
     write_digits(v, digits + (size_t)r * kpad + c0 + lane, plane);
+  }
+}
+
+// Row exponents and digit planes of a column block of listed FP64 tiles:
+// X = tile[:, col0 : col0 + w] (column-major, nb rows), slot s = blockIdx.z
+// of the list: exps[s * nb + r], plane p of row r at
+// digits + ((s * NS + p) * nb + r) * w, K-major.  lower != 0 treats the
+// entries above the tile's diagonal (column > row) as zero.
+__global__ void __launch_bounds__(256)
+    k_rowexp_cols(const double *__restrict__ t64, const int *__restrict__ tiles, int nb, int col0, int w, int lower,
+                  int *__restrict__ exps, const int *st) {
+  if (failed(st)) return;
+  __shared__ double red[8][33];
+  const int s = blockIdx.y;
+  const double *X = t64 + (size_t)tiles[s] * nb * nb;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  double m = 0.0;
+  for (int c = wp; c < w; c += 8)
+    if (!lower || col0 + c <= r) m = fmax(m, fabs(X[r + (size_t)(col0 + c) * nb]));
+  red[wp][lane] = m;
+  __syncthreads();
+  if (wp == 0) {
+    for (int q = 1; q < 8; q++) m = fmax(m, red[q][lane]);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    exps[(size_t)s * nb + r] = (m > 0.0 ? e : kExpMin) + kExpBias;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_slice_cols(const double *__restrict__ t64, const int *__restrict__ tiles, int nb, int col0, int w, int lower,
+                 const int *__restrict__ exps, uint16_t *__restrict__ digits, const int *st) {
+  if (failed(st)) return;
+  __shared__ double blk[32][33];
+  const int s = blockIdx.z;
+  const double *X = t64 + (size_t)tiles[s] * nb * nb;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int cc = wp; cc < 32; cc += 8) {
+    const int r = r0 + lane, c = col0 + c0 + cc;
+    blk[lane][cc] = (lower && c > r) ? 0.0 : X[r + (size_t)c * nb];
+  }
+  __syncthreads();
+  const size_t plane = (size_t)nb * w;
+  uint16_t *d = digits + (size_t)s * NS * plane;
+  for (int q = 0; q < 4; q++) {
+    const int rr = wp + 8 * q, r = r0 + rr;
+    const double v = blk[rr][lane] * exp2i(-exp_of(exps, (long)s * nb + r));  // exact: |v| < 1
+    write_digits(v, d + (size_t)r * w + c0 + lane, plane);
   }
 }
 
@@ -377,16 +446,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc::fence_after_sync();
 #pragma unroll
-        for (int h = 0; h < BN / 32; h++) {
+        for (int h = 0; h < BN / 4; h++) {
+          uint32_t r[NS][4];
 #pragma unroll
-          for (int g = NS - 1; g >= 0; g--) {
-            uint32_t r[32];
-            tc::tmem_ld_32x32b_x32(tlane + (uint32_t)(g * BN + h * 32), r);
-            tc::tmem_ld_wait();
-            const double wg = kGroupWeight[g];
+          for (int g = 0; g < NS; g++) tc::tmem_ld_32x32b_x4(tlane + (uint32_t)(g * BN + h * 4), r[g]);
+          tc::tmem_ld_wait();
 #pragma unroll
-            for (int x = 0; x < 32; x++) acc[h * 32 + x] = fma((double)__uint_as_float(r[x]), wg, acc[h * 32 + x]);
-          }
+          for (int x = 0; x < 4; x++) acc[h * 4 + x] = fold_groups(r, x, acc[h * 4 + x]);
         }
         tc::fence_before_sync();
         tc::mbar_arrive(&sh->tempty);
@@ -457,6 +523,19 @@ emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_
   ProfScope ps(ctx, PROF_SPLIT, 0.0, (8.0 + 2.0 * NS) * (double)s_pad * zcols);
   k_slicez64<<<dim3(s_pad, nblocks), 256, 0, ctx->stream>>>(Z, ldz, s, s_pad, d_blocks, zcols, exps, digits,
                                                             ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_col_digits(emu_ctx *ctx, const double *t64, const int *d_tiles, int ntiles, int nb, int col0, int w,
+                             int lower, int *exps, uint16_t *digits) {
+  if (ntiles <= 0) return EMU_OK;
+  if (nb % 32 != 0 || w % 32 != 0 || col0 % 32 != 0 || col0 + w > nb) return EMU_EINVAL;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, (16.0 + 2.0 * NS) * (double)ntiles * nb * w);
+  k_rowexp_cols<<<dim3(nb / 32, ntiles), 256, 0, ctx->stream>>>(t64, d_tiles, nb, col0, w, lower, exps, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  k_slice_cols<<<dim3(w / 32, nb / 32, ntiles), 256, 0, ctx->stream>>>(t64, d_tiles, nb, col0, w, lower, exps, digits,
+                                                                      ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -10,8 +10,9 @@
 // every digit exact in BF16.  A product of two digits is an integer below
 // 2^14; the sum of the (g + 1) products with p + q = g over K <= KCHUNK terms
 // stays below 2^24, so the tensor cores accumulate each diagonal group g
-// exactly in FP32.  The epilogue adds the groups, scaled by 2^-7(g+2), in
-// FP64 (smallest first) every KCHUNK, and applies the row scales at the end.
+// exactly in FP32.  Every KCHUNK the epilogue folds the groups, scaled by
+// 2^-7(g+2), in integer arithmetic and adds them in FP64; it applies the row
+// scales at the end.
 // NS = 8 digits carry 57 bits, so the products with p + q < NS give the dot
 // products to FP64 accuracy relative to the rows' largest entries.
 #pragma once
@@ -71,6 +72,14 @@ emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const
 // exponent per (block, sample): exps[blk * s_pad + c].  blocks = {row0, nrows}.
 emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_pad, const int2 *d_blocks,
                           int nblocks, long zcols, int *exps, uint16_t *digits);
+
+// Row exponents and digit planes of the column block [col0, col0 + w) of
+// listed FP64 tiles (nb x nb, column-major): slot s of the list writes
+// exps[s * nb + r] (not max-accumulated: each launch sets them) and plane p of
+// row r at digits + ((s * NS + p) * nb + r) * w.  lower != 0 ignores the
+// entries above the tile's diagonal.
+emu_status launch_col_digits(emu_ctx *ctx, const double *t64, const int *d_tiles, int ntiles, int nb, int col0, int w,
+                             int lower, int *exps, uint16_t *digits);
 
 // Row exponents and digit planes of a dense column-major FP64 block
 // X[0:nrows, col0:col0+ncols] (leading dimension ld): exps[r] for r < npad
