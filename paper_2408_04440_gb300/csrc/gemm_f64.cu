@@ -8,9 +8,11 @@
 //   warp 1      TMEM allocator + MMA issuer: per 16-deep K step the 36 digit
 //               products with p + q < NS, product (p, q) into the group
 //               accumulator g = p + q (TMEM columns g * 64 .. g * 64 + 63).
-//   warps 2..5  epilogue: every KCHUNK of K, the 8 group accumulators are
-//               folded in integer arithmetic and added in FP64 into
-//               per-thread registers (fold_groups);
+//   warps 2..3  idle (registers come in groups of four warps)
+//   warps 4..11 epilogue (two warps per TMEM lane quarter, 32 columns each):
+//               every KCHUNK of K, the 8 group accumulators are folded in
+//               integer arithmetic into exact fixed-point accumulators
+//               (fold_groups), converted to FP64 once per item;
 //               after the last chunk the row scales are applied and the block
 //               is subtracted from the FP64 output.
 // The 8 accumulators fill TMEM, so the MMA warp waits for the epilogue to
@@ -32,7 +34,11 @@ constexpr int STAGE_BYTES = NS * (A_SL + B_SL);       // 96 KB
 constexpr int RING_BYTES = STAGES * STAGE_BYTES;
 constexpr int BAR_BYTES = 128;
 constexpr int SMEM_BYTES = RING_BYTES + BAR_BYTES + 1024;  // + alignment slack
-constexpr int NTHREADS = 192;
+// 12 warps: registers are granted per group of four warps, so a 10-warp
+// CTA would be charged for 12 at the same per-thread count.
+constexpr int NTHREADS = 384;
+constexpr int EPI_WARP0 = 4;                                // warps 4..11: epilogue
+constexpr int EPI_THREADS = NTHREADS - 32 * EPI_WARP0;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t IDESC = tc::idesc_f32acc(1u /*BF16*/, BM, BN);
 constexpr int CHUNK_STAGES = KCHUNK / BK;
@@ -49,26 +55,34 @@ struct Shared {
 };
 static_assert(sizeof(Shared) <= BAR_BYTES, "barrier block");
 
-// acc + sum_g G_g 2^-7(g+2) for the group sums G_g of one output (column x
-// of r[g]).  Each G_g is an integer held exactly in FP32 (below 2^24, see
-// the header), so the sum is formed in integer arithmetic: groups 2..7 by
-// Horner in 64 bits, T = sum_{g>=2} G_g 2^(7(7-g)), |T| < 2^59 (|G_g| <
-// 2^23.4 for g >= 1 with KCHUNK = 256: at most two products of a leading
-// digit, |d_0| <= 128, and g - 1 of trailing digits, |d_p| <= 64, per K
-// term), and groups 0..1 as Q = 2^7 G_0 + G_1, |Q| < 2^30 (|G_0| <= 2^22).
-// Then acc + T 2^-63 + Q 2^-21 takes two conversions and two FP64 FMAs
-// instead of eight of each: the FP64 pipe, GB300's slowest unit, bounds this
-// epilogue.  T is rounded once (its weight is below 2^-4 of the total).
+// Adds the chunk's sum_g G_g 2^-7(g+2), for the group sums G_g of one output
+// (column x of r[g]), to the exact fixed-point accumulator (hi, lo) of value
+// hi 2^-31 + lo 2^-63 (lo unsigned, below 2^32).  Each G_g is an integer held
+// exactly in FP32 (below 2^24, see the header), so the chunk's sum is formed
+// in integer arithmetic: groups 2..7 by Horner in 64 bits, T = sum_{g>=2}
+// G_g 2^(7(7-g)), |T| < 2^59 (|G_g| < 2^23.4 for g >= 1 with KCHUNK = 256:
+// at most two products of a leading digit, |d_0| <= 128, and g - 1 of
+// trailing digits, |d_p| <= 64, per K term), and groups 0..1 as Q = 2^7 G_0
+// + G_1, |Q| < 2^30 (|G_0| <= 2^22).  The chunk's value is Q 2^-21 + T 2^-63
+// = (2^10 Q + floor(T / 2^32)) 2^-31 + (T mod 2^32) 2^-63; the low word's
+// carry moves into hi, which grows by less than 2^41 per chunk.  No FP64
+// instruction runs per chunk: the FP64 pipe, GB300's slowest unit, is used
+// once per output at the end of the item (fixed_to_double).
 static_assert(NS == 8 && SLICE_BITS == 7 && KCHUNK <= 256, "fold_groups is written for 8 digits of 7 bits");
-__device__ __forceinline__ double fold_groups(const uint32_t (&r)[NS][4], int x, double acc) {
+__device__ __forceinline__ void fold_groups(const uint32_t (&r)[NS][2], int x, long long &hi, unsigned &lo) {
   int gi[NS];
 #pragma unroll
   for (int g = 0; g < NS; g++) gi[g] = __float2int_rn(__uint_as_float(r[g][x]));  // exact: integers below 2^24
   long long t = gi[2];
 #pragma unroll
   for (int g = 3; g < NS; g++) t = t * 128 + gi[g];
-  const int q = gi[0] * 128 + gi[1];
-  return fma((double)q, 0x1p-21, fma((double)t, 0x1p-63, acc));
+  const long long q = gi[0] * 128 + gi[1];
+  const unsigned l = lo + (unsigned)t;  // low 32 bits of T, modulo 2^32
+  hi += q * 1024 + (t >> 32) + (l < lo ? 1 : 0);  // arithmetic shift: floor; carry of the low word
+  lo = l;
+}
+__device__ __forceinline__ double fixed_to_double(long long hi, unsigned lo) {
+  return fma((double)hi, 0x1p-31, (double)lo * 0x1p-63);
 }
 
 __device__ inline bool failed(const int *st) { return *((volatile const int *)st) != DEV_OK; }
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(256)
 
 // ------------------------------------------------------------- GEMM
 template <int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __maxnreg__(168)
     k_tc_gemm64(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                 const Item *__restrict__ items, int nitems, const Seg *__restrict__ segs, int nb, int a_plane,
                 int b_plane, const int *__restrict__ a_exp, const int *__restrict__ b_exp,
@@ -313,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_init(&sh->empty[s], 1);
     }
     tc::mbar_init(&sh->tfull, 1);
-    tc::mbar_init(&sh->tempty, 128);
+    tc::mbar_init(&sh->tempty, EPI_THREADS);
     tc::mbar_init(&sh->done, 1);
     // one reading of the status word for all roles: an earlier failure skips the work
     sh->abort = failed(status) ? 1 : 0;
@@ -424,20 +438,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mma_commit(&sh->done);
       tc::mbar_wait(&sh->done, 0, abort);
     }
-  } else {
+  } else if (warp >= EPI_WARP0) {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    // warps 4..11: TMEM lane quarter warp % 4 (the lanes a warp may access),
+    // columns [half * 32, half * 32 + 32) of the block
+    const int quarter = warp & 3;
+    const int half = (warp - EPI_WARP0) >> 2;
     const int row = quarter * 32 + lane;
-    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int col0 = half * 32;
+    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
     uint32_t chunk = 0;
     bool ok = *abort == 0;
     for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
       Item item = items[it];
       const int total = (item.seg_end - item.seg_begin) * kstages;
       const int nchunks = (total + CHUNK_STAGES - 1) / CHUNK_STAGES;
-      double acc[BN];
+      long long hi[32];
+      unsigned lo[32];
 #pragma unroll
-      for (int x = 0; x < BN; x++) acc[x] = 0.0;
+      for (int x = 0; x < 32; x++) {
+        hi[x] = 0;
+        lo[x] = 0u;
+      }
       for (int c = 0; c < nchunks; c++) {
         if (!tc::mbar_wait(&sh->tfull, chunk & 1u, abort)) {
           raise_timeout(sh, status);
@@ -446,13 +468,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc::fence_after_sync();
 #pragma unroll
-        for (int h = 0; h < BN / 4; h++) {
-          uint32_t r[NS][4];
+        for (int h = 0; h < 16; h++) {
+          uint32_t r[NS][2];
 #pragma unroll
-          for (int g = 0; g < NS; g++) tc::tmem_ld_32x32b_x4(tlane + (uint32_t)(g * BN + h * 4), r[g]);
+          for (int g = 0; g < NS; g++) tc::tmem_ld_32x32b_x2(tlane + (uint32_t)(g * BN + h * 2), r[g]);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int x = 0; x < 4; x++) acc[h * 4 + x] = fold_groups(r, x, acc[h * 4 + x]);
+          for (int x = 0; x < 2; x++) fold_groups(r, x, hi[h * 2 + x], lo[h * 2 + x]);
         }
         tc::fence_before_sync();
         tc::mbar_arrive(&sh->tempty);
@@ -465,18 +487,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // in groups of 8 columns: 8 loads in flight, then 8 stores
       if (MODE == TC64_SUB || row < item.rows_valid) {
 #pragma unroll
-        for (int x0 = 0; x0 < BN; x0 += 8) {
+        for (int x0 = 0; x0 < 32; x0 += 8) {
           double cv[8];
 #pragma unroll
-          for (int x = 0; x < 8; x++)
-            cv[x] = (MODE == TC64_SUB || x0 + x < item.cols_valid) ? __ldcg(o + (long)(x0 + x) * ldo) : 0.0;
+          for (int x = 0; x < 8; x++) {
+            const int cx = col0 + x0 + x;
+            cv[x] = (MODE == TC64_SUB || cx < item.cols_valid) ? __ldcg(o + (long)cx * ldo) : 0.0;
+          }
 #pragma unroll
           for (int x = 0; x < 8; x++) {
-            double v = acc[x0 + x] * exp2i(ea + exp_of(b_exp, (long)item.b_sc + x0 + x));
+            const int cx = col0 + x0 + x;
+            double v = fixed_to_double(hi[x0 + x], lo[x0 + x]) * exp2i(ea + exp_of(b_exp, (long)item.b_sc + cx));
             if (MODE == TC64_SUB)
-              __stcg(o + (long)(x0 + x) * ldo, cv[x] - v);
-            else if (x0 + x < item.cols_valid)
-              __stcg(o + (long)(x0 + x) * ldo, cv[x] + v);
+              __stcg(o + (long)cx * ldo, cv[x] - v);
+            else if (cx < item.cols_valid)
+              __stcg(o + (long)cx * ldo, cv[x] + v);
           }
         }
       }
