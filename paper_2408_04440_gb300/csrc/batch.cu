@@ -22,6 +22,7 @@
 #include "emu_internal.h"
 #include "gemm_f64.h"
 #include "gemm_tc.h"
+#include "trsm_tc.h"
 
 namespace {
 
@@ -103,6 +104,9 @@ struct BatchState {
   double *t64 = nullptr, *partial = nullptr, *tnorm = nullptr, *frob = nullptr, *tables = nullptr;
   float *t32 = nullptr, *slots = nullptr, *scale8 = nullptr;
   uint16_t *op = nullptr, *zp = nullptr;
+  uint16_t *lpieces = nullptr;  // BF16 pieces of the step's L_kk, per slot (tensor-core TRSM)
+  CUtensorMap lmap;
+  bool tc_trsm = false;
   uint8_t *op8 = nullptr;
   unsigned char *d_cls = nullptr;
   BatchInst *d_inst = nullptr;
@@ -140,7 +144,7 @@ struct BatchState {
     void *ps[] = {t64, partial, tnorm, frob, tables, t32, slots, scale8, op, zp, op8, d_cls, d_inst, d_tile_inst,
                   Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_all_diag, d_all_diag_int, d_t64,
                   d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_items64,
-                  d_items64s, d_segs64, d_segs64s, d_z, d_zs, d_zblk, digits, exp64, exp_s, exp_z};
+                  d_items64s, d_segs64, d_segs64s, d_z, d_zs, d_zblk, digits, exp64, exp_s, exp_z, lpieces};
     for (void *p : ps)
       if (p) cudaFree(p);
     if (graph) cudaGraphExecDestroy(graph);
@@ -493,9 +497,11 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
     return s;
   // remaining arenas
   s = EMU_OK;
+  B->tc_trsm = trsm_tc::supports(nb);
   if (B->any_low) {
     B->t32 = dalloc<float>(B->ntiles * te, &s);
     B->slots = dalloc<float>((size_t)B->max_active * te, &s);
+    if (B->tc_trsm) B->lpieces = dalloc<uint16_t>((size_t)B->max_active * 3 * te, &s);
   }
   B->op = dalloc<uint16_t>(B->ntiles * 3 * te, &s);
   if (B->any_e4m3) {
@@ -563,6 +569,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
                               gemm64::BN)) != EMU_OK)
       return s;
   }
+  if (B->any_low && B->tc_trsm && (s = trsm_tc::make_map(ctx, &B->lmap, B->lpieces, nb, B->max_active)) != EMU_OK)
+    return s;
   B->ops_s = B->ops_f;
   if (B->s > 0 &&
       (s = gemm_tc::make_map_bf16(ctx, &B->ops_s.b16, B->zp, B->nrows, (uint64_t)3 * B->s_pad, gemm_tc::BN)) !=
@@ -611,13 +619,18 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     if ((s = launch_potrf64_batch(ctx, B->t64, nb, k, B->d_diag + st.d_off, st.d_n, B->tasks, B->ntasks, B->ws,
                                   B->rinv)) != EMU_OK)
       return s;
-    if (st.t32_n > 0 &&
-        (s = launch_diag_to_f32_slots(ctx, B->t64, B->slots, B->d_diag + st.d_off, st.d_n, te)) != EMU_OK)
-      return s;
+    if (st.t32_n > 0) {
+      // FP32 copies (and, for the tensor-core TRSM, BF16 pieces) of the step's L_kk, one slot per matrix
+      s = B->tc_trsm ? trsm_tc::launch_prep(ctx, B->t64, 0, B->d_diag + st.d_off, st.d_n, B->slots, B->lpieces, nb)
+                     : launch_diag_to_f32_slots(ctx, B->t64, B->slots, B->d_diag + st.d_off, st.d_n, te);
+      if (s != EMU_OK) return s;
+    }
     if ((s = launch_trsm64_jobs(ctx, B->t64, nb, B->d_t64 + st.t64_off, st.t64_n)) != EMU_OK) return s;
     if ((s = launch_split_tiles64(ctx, B->t64, B->op, B->d_s64 + st.s64_off, st.s64_n, nb, 0)) != EMU_OK) return s;
-    if ((s = launch_trsm32_jobs(ctx, B->slots, B->t32, B->op, nb, B->d_t32 + st.t32_off, st.t32_n)) != EMU_OK)
-      return s;
+    s = B->tc_trsm ? trsm_tc::launch(ctx, B->lmap, B->slots, B->t32, B->op, nb, 0, 0, nullptr,
+                                     B->d_t32 + st.t32_off, st.t32_n)
+                   : launch_trsm32_jobs(ctx, B->slots, B->t32, B->op, nb, B->d_t32 + st.t32_off, st.t32_n);
+    if (s != EMU_OK) return s;
     if ((s = launch_quant_e4m3(ctx, B->op, B->op8, B->scale8, B->d_q + st.q_off, st.q_n, nb)) != EMU_OK) return s;
     if ((s = gemm64::launch_row_exponents(ctx, B->t64, B->t32, B->d_cls, B->d_z + st.z_off, st.z_n, nb,
                                           B->exp64)) != EMU_OK ||

@@ -378,7 +378,7 @@ __global__ void __maxnreg__(168)
       // every stage's last load must have landed before the CTA exits
       for (int s = 0; s < STAGES; s++) {
         uint32_t par = (s < stage) ? phase : (phase ^ 1u);
-        tc::mbar_wait(&sh->full[s], par, abort);
+        tc::mbar_wait_inflight(&sh->full[s], par);
       }
     }
   } else if (warp == 1) {
@@ -436,7 +436,7 @@ __global__ void __maxnreg__(168)
         }
       }
       tc::mma_commit(&sh->done);
-      tc::mbar_wait(&sh->done, 0, abort);
+      tc::mbar_wait_inflight(&sh->done, 0);
     }
   } else if (warp >= EPI_WARP0) {
     // ------------------------------------------------------------ epilogue

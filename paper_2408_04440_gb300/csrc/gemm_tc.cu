@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int s = 0; s < STAGES; s++) {
         // the most recent use of stage s completed phase (phase ^ (s >= stage))
         uint32_t par = (s < stage) ? phase : (phase ^ 1u);
-        tc::mbar_wait(&sh->full[s], par, abort);
+        tc::mbar_wait_inflight(&sh->full[s], par);
       }
     }
   } else if (warp == 1) {
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // all issued MMAs complete before TMEM is released
       tc::mma_commit(&sh->done);
-      tc::mbar_wait(&sh->done, 0, abort);
+      tc::mbar_wait_inflight(&sh->done, 0);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -315,6 +315,31 @@ emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint6
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed";
+    return EMU_ECUDA;
+  }
+  return EMU_OK;
+}
+
+emu_status make_map_bf16_sw128(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows,
+                               uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    ctx->last_error = "cuTensorMapEncodeTiled unavailable";
+    return EMU_ECUDA;
+  }
+  if (((uintptr_t)base & 15u) != 0 || inner % 64 != 0) {
+    ctx->last_error = "TMA operand base/stride not 16-byte aligned";
+    return EMU_EINVAL;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {64u, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";

@@ -53,6 +53,11 @@ struct Operands {
 emu_status make_map_bf16(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,
                          uint64_t rows, uint32_t box_rows);
 
+// 2-D BF16 tensor map over a row-major [rows x inner] array, box
+// [box_rows x 64] (128-byte rows), 128-byte swizzle.
+emu_status make_map_bf16_sw128(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows,
+                               uint32_t box_rows);
+
 // 2-D FP8 tensor map over a row-major [rows x inner] byte array, box
 // [box_rows x 32], 32-byte swizzle.
 emu_status make_map_e4m3(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64_t inner,

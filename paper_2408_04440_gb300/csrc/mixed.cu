@@ -22,6 +22,7 @@
 #include "gemm_f64.h"
 #include "gemm_tc.h"
 #include "mixed.h"
+#include "trsm_tc.h"
 
 namespace {
 
@@ -467,6 +468,9 @@ struct MixedPlan {
   gemm_tc::Operands ops;
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
+  uint16_t *d_lkkp = nullptr;         // three BF16 pieces of L_kk (row-major), same slots (tensor-core TRSM)
+  CUtensorMap lmap;                   // over d_lkkp
+  bool tc_trsm = false;               // FP32-class panel TRSMs on the tensor cores (trsm_tc.cu)
   CUtensorMap mapA, mapB;
   double update_flops[EMU_NCLASS] = {};
   int tiles[EMU_NCLASS] = {};
@@ -674,7 +678,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
          o_s64 = part(vbytes(segs64)), o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
          o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)), o_tt = part(vbytes(ttiles)),
-         o_lkk = part(2 * (size_t)nb * nb * sizeof(float));
+         o_lkk = part(2 * (size_t)nb * nb * sizeof(float)), o_lkkp = part(2 * 3 * (size_t)nb * nb * sizeof(uint16_t));
   size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
   P->host_blob.assign(copy_bytes, 0);
   auto put = [&](size_t o, const auto &v) {
@@ -707,6 +711,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_qtiles = reinterpret_cast<int *>(b + o_q);
   P->d_ttiles = reinterpret_cast<int *>(b + o_tt);
   P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
+  P->d_lkkp = reinterpret_cast<uint16_t *>(b + o_lkkp);
   emu_status s;
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapA, A->op_bf16, nb, rows, gemm_tc::BM)) != EMU_OK) return s;
@@ -718,6 +723,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->ops.a32 = P->mapA;
   P->ops.b32 = P->mapB;
   P->ops.scale8 = nullptr;
+  P->tc_trsm = trsm_tc::supports(nb);
+  if (P->tc_trsm && (s = trsm_tc::make_map(ctx, &P->lmap, P->d_lkkp, nb, 2)) != EMU_OK) return s;
   if (P->nslots > 0) {
     size_t te = (size_t)nb * nb;
     EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_digits, (size_t)P->nslots * gemm64::NS * te * sizeof(uint16_t),
@@ -864,6 +871,8 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
                                                                                     P->d_tiles64 + r64, nb, 0, st);
       EMU_LAUNCHED(ctx);
     }
+    if (n32 > 0 && P->tc_trsm)
+      return trsm_tc::launch(ctx, P->lmap, P->d_lkk32, A->t32, A->op_bf16, nb, NT, k, P->d_rows32 + r32, nullptr, n32);
     if (n32 > 0) {
       ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
       const float *lkk = P->d_lkk32 + (size_t)(k & 1) * te;
@@ -910,9 +919,16 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     }
     if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) break;
     if (sp.n32_1 + sp.n32_r > 0) {
-      k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te, P->d_lkk32 + (size_t)(k & 1) * te,
-                                                               te, st);
-      EMU_LAUNCHED(ctx);
+      if (P->tc_trsm) {
+        // FP32 copy and BF16 pieces of L_kk for the tensor-core TRSMs
+        if ((s = trsm_tc::launch_prep(ctx, A->t64, tkk, nullptr, 1, P->d_lkk32 + (size_t)(k & 1) * te,
+                                      P->d_lkkp + (size_t)(k & 1) * 3 * te, nb)) != EMU_OK)
+          break;
+      } else {
+        k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te,
+                                                                 P->d_lkk32 + (size_t)(k & 1) * te, te, st);
+        EMU_LAUNCHED(ctx);
+      }
     }
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));

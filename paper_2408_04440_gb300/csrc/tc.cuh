@@ -54,6 +54,14 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *a
   }
 }
 
+// Wait for a completion that always comes (committed MMAs, issued TMA
+// loads), bounded in time but not cut short by an abort flag: a CTA that
+// aborts must still not release TMEM or exit under work in flight.
+__device__ inline bool mbar_wait_inflight(uint64_t *bar, uint32_t parity) {
+  int zero = 0;
+  return mbar_wait(bar, parity, &zero);
+}
+
 // ------------------------------------------------------------------- TMA
 __device__ inline void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
   asm volatile(
@@ -137,6 +145,23 @@ __device__ inline void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ inline void tmem_ld_32x32b_x2(uint32_t taddr, uint32_t (&r)[2]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
 }
+// Store: thread t of the warp writes lane (base lane + t), columns col ..
+// col+31 (the layout of tmem_ld_32x32b_x32).
+__device__ inline void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ inline void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// Makes this thread's generic-proxy shared-memory writes visible to the
+// async proxy (tcgen05.mma operand reads, TMA).
+__device__ inline void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ inline void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------ descriptors
