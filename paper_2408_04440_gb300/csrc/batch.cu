@@ -105,7 +105,7 @@ struct BatchState {
   float *t32 = nullptr, *slots = nullptr, *scale8 = nullptr;
   uint16_t *op = nullptr, *zp = nullptr;
   uint16_t *lpieces = nullptr;  // BF16 pieces of the step's L_kk, per slot (tensor-core TRSM)
-  CUtensorMap lmap;
+  CUtensorMap lmap, opmap;
   bool tc_trsm = false;
   uint8_t *op8 = nullptr;
   unsigned char *d_cls = nullptr;
@@ -569,7 +569,9 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
                               gemm64::BN)) != EMU_OK)
       return s;
   }
-  if (B->any_low && B->tc_trsm && (s = trsm_tc::make_map(ctx, &B->lmap, B->lpieces, nb, B->max_active)) != EMU_OK)
+  if (B->any_low && B->tc_trsm &&
+      ((s = trsm_tc::make_map(ctx, &B->lmap, B->lpieces, nb, B->max_active)) != EMU_OK ||
+       (s = trsm_tc::make_op_map(ctx, &B->opmap, B->op, nb, B->ntiles)) != EMU_OK))
     return s;
   B->ops_s = B->ops_f;
   if (B->s > 0 &&
@@ -627,7 +629,7 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     }
     if ((s = launch_trsm64_jobs(ctx, B->t64, nb, B->d_t64 + st.t64_off, st.t64_n)) != EMU_OK) return s;
     if ((s = launch_split_tiles64(ctx, B->t64, B->op, B->d_s64 + st.s64_off, st.s64_n, nb, 0)) != EMU_OK) return s;
-    s = B->tc_trsm ? trsm_tc::launch(ctx, B->lmap, B->slots, B->t32, B->op, nb, 0, 0, nullptr,
+    s = B->tc_trsm ? trsm_tc::launch(ctx, B->lmap, B->opmap, B->slots, B->t32, nb, 0, 0, nullptr,
                                      B->d_t32 + st.t32_off, st.t32_n)
                    : launch_trsm32_jobs(ctx, B->slots, B->t32, B->op, nb, B->d_t32 + st.t32_off, st.t32_n);
     if (s != EMU_OK) return s;

@@ -410,15 +410,17 @@ __global__ void __maxnreg__(168)
           }
           tc::fence_after_sync();
           uint32_t st = ring_addr + stage * STAGE_BYTES;
+          const uint64_t a0 = tc::smem_desc(st, 16, 512, tc::kSwizzle64B);
+          const uint64_t b0 = tc::smem_desc(st + NS * A_SL, 16, 512, tc::kSwizzle64B);
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ks++) {
 #pragma unroll
             for (int p = 0; p < NS; p++) {
-              uint64_t ad = tc::smem_desc(st + p * A_SL + ks * 32, 16, 512, tc::kSwizzle64B);
+              const uint64_t ad = tc::desc_add(a0, p * A_SL + ks * 32);
 #pragma unroll
               for (int q = 0; q < NS - p; q++) {
                 const int g = p + q;
-                uint64_t bd = tc::smem_desc(st + NS * A_SL + q * B_SL + ks * 32, 16, 512, tc::kSwizzle64B);
+                const uint64_t bd = tc::desc_add(b0, q * B_SL + ks * 32);
                 tc::mma_f16(tmem + (uint32_t)(g * BN), ad, bd, IDESC, (started >> g) & 1u);
                 started |= 1u << g;
               }

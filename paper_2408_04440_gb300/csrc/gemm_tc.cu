@@ -198,12 +198,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 accumulate = 1;
               }
             } else {
+              const uint64_t a0 = tc::smem_desc(st, 16, 512, tc::kSwizzle64B);
+              const uint64_t b0 = tc::smem_desc(st + NPIECE * A_PIECE, 16, 512, tc::kSwizzle64B);
 #pragma unroll
               for (int ks = 0; ks < BK / 16; ks++) {
                 for (int p = p0; p < 6; p++) {
-                  uint64_t ad = tc::smem_desc(st + pa[p] * A_PIECE + ks * 32, 16, 512, tc::kSwizzle64B);
-                  uint64_t bd = tc::smem_desc(st + NPIECE * A_PIECE + pb[p] * B_PIECE + ks * 32, 16, 512,
-                                              tc::kSwizzle64B);
+                  const uint64_t ad = tc::desc_add(a0, pa[p] * A_PIECE + ks * 32);
+                  const uint64_t bd = tc::desc_add(b0, pb[p] * B_PIECE + ks * 32);
                   tc::mma_f16(d_tmem, ad, bd, IDESC, accumulate);
                   accumulate = 1;
                 }

@@ -470,6 +470,7 @@ struct MixedPlan {
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
   uint16_t *d_lkkp = nullptr;         // three BF16 pieces of L_kk (row-major), same slots (tensor-core TRSM)
   CUtensorMap lmap;                   // over d_lkkp
+  CUtensorMap opmap;                  // over the piece arena (the TRSM's tile stores)
   bool tc_trsm = false;               // FP32-class panel TRSMs on the tensor cores (trsm_tc.cu)
   CUtensorMap mapA, mapB;
   double update_flops[EMU_NCLASS] = {};
@@ -724,7 +725,9 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->ops.b32 = P->mapB;
   P->ops.scale8 = nullptr;
   P->tc_trsm = trsm_tc::supports(nb);
-  if (P->tc_trsm && (s = trsm_tc::make_map(ctx, &P->lmap, P->d_lkkp, nb, 2)) != EMU_OK) return s;
+  if (P->tc_trsm && ((s = trsm_tc::make_map(ctx, &P->lmap, P->d_lkkp, nb, 2)) != EMU_OK ||
+                     (s = trsm_tc::make_op_map(ctx, &P->opmap, A->op_bf16, nb, A->ntiles)) != EMU_OK))
+    return s;
   if (P->nslots > 0) {
     size_t te = (size_t)nb * nb;
     EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_digits, (size_t)P->nslots * gemm64::NS * te * sizeof(uint16_t),
@@ -872,7 +875,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
       EMU_LAUNCHED(ctx);
     }
     if (n32 > 0 && P->tc_trsm)
-      return trsm_tc::launch(ctx, P->lmap, P->d_lkk32, A->t32, A->op_bf16, nb, NT, k, P->d_rows32 + r32, nullptr, n32);
+      return trsm_tc::launch(ctx, P->lmap, P->opmap, P->d_lkk32, A->t32, nb, NT, k, P->d_rows32 + r32, nullptr, n32);
     if (n32 > 0) {
       ProfScope ps(ctx, PROF_TRSM32, n32 * nb3, 14.0 * n32 * te);
       const float *lkk = P->d_lkk32 + (size_t)(k & 1) * te;

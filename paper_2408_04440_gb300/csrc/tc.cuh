@@ -69,6 +69,22 @@ __device__ inline void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *
       ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// Tile store shared -> global (bulk-group completion): the box at (x, y),
+// x >= 0 and y >= 0, x times the element size a multiple of 16 bytes.
+__device__ inline void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"((uint64_t)map), "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// This thread's bulk stores except the newest N have finished reading shared memory.
+template <int N>
+__device__ inline void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// This thread's bulk stores have completed.
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ inline void tma_prefetch_desc(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -178,6 +194,11 @@ __device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_
   d |= (uint64_t)(swizzle & 7u) << 61;
   return d;
 }
+
+// The descriptor of saddr + off_bytes from that of saddr: the start address
+// field holds saddr >> 4 in 14 bits, and shared-memory addresses stay below
+// 2^18 bytes, so the sum never carries out of the field.
+__device__ inline uint64_t desc_add(uint64_t desc, uint32_t off_bytes) { return desc + (uint64_t)(off_bytes >> 4); }
 
 // Instruction descriptor of kind::f16 / kind::tf32 / kind::f8f6f4 with FP32
 // accumulation, both operands K-major: D format F32 (bits 4-5 = 1), A/B

@@ -6,16 +6,17 @@
 //               (rows of column block n > J, columns of block J, 64 x 64)
 //               through a STAGES-deep ring.
 //   warp 1      TMEM allocator + MMA issuer (one lane): for each n > J the
-//               six products of -X_J pieces (A, 128 x 64) and L_{n,J} pieces
+//               six products of X_J pieces (A, 128 x 64) and -L_{n,J} pieces
 //               (B, 64 x 64) accumulate into the TMEM columns of block n.
 //   warps 2..5  the leaf, one thread per row (TMEM lane): TMEM <- A_ik's
 //               columns 64.., then per J the block's current values (from
 //               TMEM once an update has reached them), forward substitution
-//               against L_JJ in FP32, X_J to the FP32 master and the piece
-//               arena, and -X_J's pieces into shared memory for the MMAs.
+//               against L_JJ in FP32, X_J to the FP32 master, and X_J's
+//               pieces into shared memory: the MMAs' A operand, and the source
+//               of three TMA tile stores into the piece arena.
 // The MMAs of block n = J + 1 are issued first and committed on their own,
-// so the leaf of J + 1 starts while those of the later blocks run; the
-// -X_J operand is double-buffered.  Every wait is bounded (DEV_TIMEOUT).
+// so the leaf of J + 1 starts while those of the later blocks run; the X_J
+// operand is double-buffered.  Every wait is bounded (DEV_TIMEOUT).
 #include <cuda_bf16.h>
 
 #include "gemm_tc.h"
@@ -33,9 +34,9 @@ constexpr int B_STAGE = NPIECE * B_PIECE;   // 24 KB
 constexpr int STAGES = 3;
 constexpr int OFF_A = 0;                            // two -X_J buffers
 constexpr int OFF_B = 2 * A_BYTES;                  // ring of L pieces
-constexpr int OFF_L = OFF_B + STAGES * B_STAGE;     // L_JJ, FP32 column-major
-constexpr int OFF_R = OFF_L + W * W * 4;            // 1 / L_JJ(c, c)
-constexpr int OFF_BAR = OFF_R + W * 4;
+constexpr int OFF_L = OFF_B + STAGES * B_STAGE;     // two L_JJ buffers, FP32 column-major
+constexpr int OFF_R = OFF_L + 2 * W * W * 4;        // two rows of 1 / L_JJ(c, c)
+constexpr int OFF_BAR = OFF_R + 2 * W * 4;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES + 1024;  // + alignment slack
 constexpr int NTHREADS = 192;
@@ -75,6 +76,19 @@ __device__ inline void split3(T x, uint16_t &p0, uint16_t &p1, uint16_t &p2) {
   p2 = __bfloat16_as_ushort(b2);
 }
 
+// The three pieces of x0 and x1, packed two per word (x0 in the low half):
+// the same values as split3 on each, with paired conversions.
+__device__ inline void split3_pair(float x0, float x1, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float r0 = x0 - __low2float(h), r1 = x1 - __high2float(h);
+  const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+  const float s0 = r0 - __low2float(m), s1 = r1 - __high2float(m);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(s0, s1);
+  w0 = *reinterpret_cast<const uint32_t *>(&h);
+  w1 = *reinterpret_cast<const uint32_t *>(&m);
+  w2 = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 // All 128 leaf threads: barrier 1, and whether every one of them is still ok.
 __device__ inline bool leaf_all(bool ok) {
   int r;
@@ -90,8 +104,16 @@ __device__ inline bool leaf_all(bool ok) {
 }
 __device__ inline void leaf_sync() { asm volatile("barrier.cta.sync 1, 128;" ::: "memory"); }
 
+__device__ inline void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // blockIdx.z = list entry z: diagonal tile tiles[z] (or tile0) of the FP64
-// arena t64; outputs at slot z of L32 (nb^2 floats) and pieces (3 nb^2).
+// arena t64; outputs at slot z of L32 (nb^2 floats, L) and pieces (3 nb^2,
+// the pieces of -L, so that the MMAs subtract X_J L^T by accumulating).
 __global__ void k_lkk_prep(const double *__restrict__ t64, const long *__restrict__ tiles, long tile0,
                            float *__restrict__ L32, uint16_t *__restrict__ pieces, int nb, const int *st) {
   if (failed(st)) return;
@@ -113,7 +135,7 @@ __global__ void k_lkk_prep(const double *__restrict__ t64, const long *__restric
   for (int r = ty; r < 32; r += 8) {
     const int row = rb * 32 + r, col = cb * 32 + tx;
     uint16_t p0, p1, p2;
-    split3(col > row ? 0.0 : blk[r][tx], p0, p1, p2);
+    split3(col > row ? 0.0 : -blk[r][tx], p0, p1, p2);  // pieces of -L
     const size_t o = (size_t)row * nb + col;
     Pz[o] = p0;
     Pz[plane + o] = p1;
@@ -122,8 +144,9 @@ __global__ void k_lkk_prep(const double *__restrict__ t64, const long *__restric
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_trsm32_tc(const __grid_constant__ CUtensorMap lmap, const float *__restrict__ lkk0, float *__restrict__ t32,
-                uint16_t *__restrict__ op, int nb, int NT, int k, const int *__restrict__ rows,
+    k_trsm32_tc(const __grid_constant__ CUtensorMap lmap, const __grid_constant__ CUtensorMap opmap,
+                const float *__restrict__ lkk0, float *__restrict__ t32, int nb, int NT, int k,
+                const int *__restrict__ rows,
                 const int2 *__restrict__ jobs, int *status) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = tc::smem_u32(smem_raw);
@@ -163,6 +186,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     sh->abort = failed(status) ? 1 : 0;
     tc::fence_barrier_init();
     tc::tma_prefetch_desc(&lmap);
+    tc::tma_prefetch_desc(&opmap);
   }
   if (warp == 1) {
     tc::tmem_alloc(&sh->tmem_base, TMEM_COLS);
@@ -229,12 +253,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc::fence_after_sync();
           const uint32_t b_addr = base_addr + OFF_B + stage * B_STAGE;
           const uint32_t d = tmem + (uint32_t)(n * W - W);
+          const uint64_t a0 = tc::smem_desc(a_addr, 16, 1024, tc::kSwizzle128B);
+          const uint64_t b0 = tc::smem_desc(b_addr, 16, 1024, tc::kSwizzle128B);
 #pragma unroll
           for (int ks = 0; ks < W / 16; ks++) {
 #pragma unroll
             for (int p = 0; p < 6; p++) {
-              const uint64_t ad = tc::smem_desc(a_addr + pa[p] * A_PIECE + ks * 32, 16, 1024, tc::kSwizzle128B);
-              const uint64_t bd = tc::smem_desc(b_addr + pb[p] * B_PIECE + ks * 32, 16, 1024, tc::kSwizzle128B);
+              const uint64_t ad = tc::desc_add(a0, pa[p] * A_PIECE + ks * 32);
+              const uint64_t bd = tc::desc_add(b0, pb[p] * B_PIECE + ks * 32);
               tc::mma_f16(d, ad, bd, IDESC, 1u);
             }
           }
@@ -257,28 +283,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int lt = threadIdx.x - LEAF0;
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
     const size_t plane = (size_t)nb * nb;
-    float *Ab = t32 + (size_t)ti * plane + r0 + row;                      // (row, c) at Ab[c * nb]
-    uint16_t *P = op + (size_t)ti * NPIECE * plane + (size_t)(r0 + row) * nb;  // piece p, column c: P[p * plane + c]
+    float *Ab = t32 + (size_t)ti * plane + r0 + row;  // (row, c) at Ab[c * nb]
+    const int oprow0 = (int)(ti * NPIECE * nb) + r0;  // op tensor-map row of piece 0, row r0
     bool ok = *abort == 0;
+    // L_JJ of block J into buffer J & 1 (one cp.async group per block; an
+    // empty group past the last block keeps the count uniform)
+    auto prefetch = [&](int J) {
+      if (J < NJ) {
+        float *dst = LJJ + (J & 1) * W * W;
+        for (int e = lt; e < W * W / 4; e += RB) {
+          const int j = e >> 4, i4 = (e & 15) * 4;  // column j, rows i4 .. i4+3
+          cp_async16(dst + j * W + i4, Lkk + (size_t)(J * W + j) * nb + J * W + i4);
+        }
+      }
+      cp_async_commit();
+    };
+    prefetch(0);
     if (ok) {
-      // the trailing columns 64 .. nb-1 of the row block into TMEM
-      for (int c0 = W; c0 < nb; c0 += 32) {
-        uint32_t v[32];
+      // the trailing columns 64 .. nb-1 of the row block into TMEM, four
+      // 32-column chunks of loads in flight at a time
+      for (int c0 = W; c0 < nb; c0 += 128) {
+        uint32_t v[4][32];
 #pragma unroll
-        for (int x = 0; x < 32; x++) v[x] = __float_as_uint(__ldcg(Ab + (size_t)(c0 + x) * nb));
-        tc::tmem_st_32x32b_x32(tl + (uint32_t)(c0 - W), v);
+        for (int h = 0; h < 4; h++)
+          if (c0 + 32 * h < nb) {
+#pragma unroll
+            for (int x = 0; x < 32; x++) v[h][x] = __float_as_uint(__ldcg(Ab + (size_t)(c0 + 32 * h + x) * nb));
+          }
+#pragma unroll
+        for (int h = 0; h < 4; h++)
+          if (c0 + 32 * h < nb) tc::tmem_st_32x32b_x32(tl + (uint32_t)(c0 + 32 * h - W), v[h]);
       }
       tc::tmem_st_wait();
     }
     for (int J = 0; J < NJ; J++) {
-      // every leaf thread is past block J - 1 (L_JJ may be overwritten) and ok
+      // the piece stores of block J - 2 have read their buffer
+      if (lt == 0) tc::bulk_wait_read<1>();
+      // every leaf thread is past block J - 1 (its L_JJ buffer may be
+      // refilled) and ok
       ok = leaf_all(ok && *abort == 0);
       if (!ok) break;
-      for (int e = lt; e < W * W; e += RB) {
-        const int i = e & (W - 1), j = e >> 6;
-        LJJ[j * W + i] = __ldg(Lkk + (size_t)(J * W + j) * nb + J * W + i);
-      }
-      if (lt < W) rinv[lt] = 1.0f / __ldg(Lkk + (size_t)(J * W + lt) * nb + J * W + lt);
+      prefetch(J + 1);
+      cp_async_wait1();  // this thread's copies of block J have landed
+      leaf_sync();       // everyone's
+      const float *LJ = LJJ + (J & 1) * W * W;
+      float *rinvJ = rinv + (J & 1) * W;
+      if (lt < W) rinvJ[lt] = 1.0f / LJ[lt * W + lt];
       leaf_sync();
       float v[W];
       if (J == 0) {
@@ -304,10 +354,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // forward substitution: x_c = (v_c - sum_{c' < c} x_c' L(c, c')) / L(c, c)
 #pragma unroll
       for (int c = 0; c < W; c++) {
-        const float x = v[c] * rinv[c];
+        const float x = v[c] * rinvJ[c];
         v[c] = x;
         // column c of L_JJ in 16-byte loads (rows 4g .. 4g+3 at or below c skipped)
-        const float4 *Lc4 = reinterpret_cast<const float4 *>(LJJ + c * W);
+        const float4 *Lc4 = reinterpret_cast<const float4 *>(LJ + c * W);
 #pragma unroll
         for (int g = (c + 1) / 4; g < W / 4; g++) {
           const float4 l = Lc4[g];
@@ -320,43 +370,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int c = 0; c < W; c++) Ab[(size_t)(J * W + c) * nb] = v[c];
       const bool feed = J + 1 < NJ;  // the last block updates nothing
-      if (feed && !tc::mbar_wait(&sh->aempty[J & 1], (uint32_t)(((J >> 1) & 1) ^ 1), abort)) {
+      // the MMAs of block J - 2 have read this buffer
+      if (!tc::mbar_wait(&sh->aempty[J & 1], (uint32_t)(((J >> 1) & 1) ^ 1), abort)) {
         raise_timeout(sh, status);
         ok = false;
         continue;
       }
+      // X_J's pieces, K-major with the 128-byte swizzle (16-byte chunk ch of
+      // row `row` at chunk position ch ^ (row & 7)): the A operand of the
+      // MMAs and the source of the tile stores into the piece arena
       uint8_t *As = base + OFF_A + (J & 1) * A_BYTES;
 #pragma unroll
       for (int ch = 0; ch < W / 8; ch++) {
         uint32_t w[NPIECE][4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-          uint16_t a0, a1, a2, b0, b1, b2;
-          split3(v[ch * 8 + 2 * e], a0, a1, a2);
-          split3(v[ch * 8 + 2 * e + 1], b0, b1, b2);
-          w[0][e] = (uint32_t)a0 | ((uint32_t)b0 << 16);
-          w[1][e] = (uint32_t)a1 | ((uint32_t)b1 << 16);
-          w[2][e] = (uint32_t)a2 | ((uint32_t)b2 << 16);
-        }
+        for (int e = 0; e < 4; e++) split3_pair(v[ch * 8 + 2 * e], v[ch * 8 + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+        const uint32_t off = (uint32_t)row * 128u + (uint32_t)((ch ^ (row & 7)) << 4);
 #pragma unroll
-        for (int p = 0; p < NPIECE; p++) {
-          *reinterpret_cast<uint4 *>(P + p * plane + J * W + ch * 8) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-          if (feed) {
-            // -X_J (sign bits flipped), K-major with the 128-byte swizzle:
-            // 16-byte chunk ch of row `row` at chunk position ch ^ (row & 7)
-            const uint32_t off = (uint32_t)row * 128u + (uint32_t)((ch ^ (row & 7)) << 4);
-            *reinterpret_cast<uint4 *>(As + p * A_PIECE + off) =
-                make_uint4(w[p][0] ^ 0x80008000u, w[p][1] ^ 0x80008000u, w[p][2] ^ 0x80008000u,
-                           w[p][3] ^ 0x80008000u);
-          }
-        }
+        for (int p = 0; p < NPIECE; p++)
+          *reinterpret_cast<uint4 *>(As + p * A_PIECE + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
       }
+      tc::fence_proxy_async_smem();
       if (feed) {
-        tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         tc::mbar_arrive(&sh->afull[J & 1]);
       }
+      leaf_sync();  // every row's pieces are in the buffer
+      if (lt == 0) {
+        for (int p = 0; p < NPIECE; p++) tc::tma_store_2d(&opmap, As + p * A_PIECE, J * W, oprow0 + p * nb);
+        tc::bulk_commit();
+      }
     }
+    if (lt == 0) tc::bulk_wait_all();
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into shared memory outlives the loop
   }
 
   tc::fence_before_sync();
@@ -383,8 +429,16 @@ emu_status make_map(emu_ctx *ctx, CUtensorMap *map, const uint16_t *pieces, int 
   return gemm_tc::make_map_bf16_sw128(ctx, map, pieces, (uint64_t)nb, (uint64_t)nslots * NPIECE * nb, (uint32_t)W);
 }
 
-emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const float *lkk0, float *t32, uint16_t *op, int nb,
-                  int NT, int k, const int *d_rows, const int2 *d_jobs, int n) {
+emu_status make_op_map(emu_ctx *ctx, CUtensorMap *map, const uint16_t *op, int nb, long ntiles) {
+  if ((uint64_t)ntiles * NPIECE * nb >= (1ull << 31)) {
+    ctx->last_error = "piece arena too large for 32-bit TMA coordinates";
+    return EMU_EINVAL;
+  }
+  return gemm_tc::make_map_bf16_sw128(ctx, map, op, (uint64_t)nb, (uint64_t)ntiles * NPIECE * nb, (uint32_t)RB);
+}
+
+emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const CUtensorMap &opmap, const float *lkk0, float *t32,
+                  int nb, int NT, int k, const int *d_rows, const int2 *d_jobs, int n) {
   if (n <= 0) return EMU_OK;
   if (!supports(nb)) return EMU_EINVAL;
   static bool attr_done = false;
@@ -394,8 +448,8 @@ emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const float *lkk0, floa
   }
   const double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM32, n * nb3, 14.0 * n * (double)nb * nb, 6.0 * n * (nb3 - (double)nb * nb * W));
-  k_trsm32_tc<<<dim3(nb / RB, n), NTHREADS, SMEM_BYTES, ctx->stream>>>(lmap, lkk0, t32, op, nb, NT, k, d_rows, d_jobs,
-                                                                       ctx->d_status);
+  k_trsm32_tc<<<dim3(nb / RB, n), NTHREADS, SMEM_BYTES, ctx->stream>>>(lmap, opmap, lkk0, t32, nb, NT, k, d_rows,
+                                                                       d_jobs, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

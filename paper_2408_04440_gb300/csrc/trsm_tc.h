@@ -25,8 +25,9 @@ constexpr int W = 64;    // column block
 // columns (nb - 64) fit in the 512 TMEM columns.
 inline bool supports(int nb) { return nb % RB == 0 && nb - W <= 512; }
 
-// FP32 copy (column-major, as the SIMT TRSM reads it) and three BF16 pieces
-// (row-major, strict upper triangle zero) of FP64 diagonal factor tiles of
+// FP32 copy (column-major, as the SIMT TRSM reads it) and the three BF16
+// pieces of the negated tile (row-major, strict upper triangle zero) of FP64
+// diagonal factor tiles of
 // the arena t64 (nb x nb, column-major): entry z of the list, tile d_tiles[z]
 // (or `tile` when d_tiles is null, n = 1), goes to slot z: L32 + z nb^2 and
 // pieces + 3 z nb^2.
@@ -37,12 +38,18 @@ emu_status launch_prep(emu_ctx *ctx, const double *t64, long tile, const long *d
 // launch_prep, box 64 x 64, 128-byte swizzle.
 emu_status make_map(emu_ctx *ctx, CUtensorMap *map, const uint16_t *pieces, int nb, int nslots);
 
-// Solves the listed tiles in place (t32 FP32 masters, op = the BF16 piece
-// arena: tile t's piece p at op + (t * 3 + p) nb^2, row-major).  Either
-// d_rows (tile (rows[i], k) of an NT x NT tile matrix, L slot k & 1) or
-// d_jobs ({tile index, L slot}) lists the n tiles.  lkk0 / lmap: the FP32
-// copies and the pieces of the L slots (launch_prep).
-emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const float *lkk0, float *t32, uint16_t *op, int nb,
-                  int NT, int k, const int *d_rows, const int2 *d_jobs, int n);
+// 2-D tensor map over the BF16 piece arena op (ntiles * 3 rows of nb x nb,
+// row-major), box 128 rows x 64, 128-byte swizzle: the solved pieces are
+// stored through it.
+emu_status make_op_map(emu_ctx *ctx, CUtensorMap *map, const uint16_t *op, int nb, long ntiles);
+
+// Solves the listed tiles in place: t32 holds the FP32 masters; the three
+// BF16 pieces of each solved tile t go to the piece arena behind opmap (piece
+// p at rows (t * 3 + p) nb, row-major).  Either d_rows (tile (rows[i], k) of
+// an NT x NT tile matrix, L slot k & 1) or d_jobs ({tile index, L slot})
+// lists the n tiles.  lkk0 / lmap: the FP32 copies and the pieces of the L
+// slots (launch_prep).
+emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const CUtensorMap &opmap, const float *lkk0, float *t32,
+                  int nb, int NT, int k, const int *d_rows, const int2 *d_jobs, int n);
 
 }  // namespace trsm_tc
