@@ -89,6 +89,19 @@ __device__ inline void split3_pair(float x0, float x1, uint32_t &w0, uint32_t &w
   w2 = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// Two floats in one 64-bit register pair (lo in the low half), and the
+// packed FP32 FMA of sm_100 (two lanes per instruction, each rounded as fmaf).
+__device__ __forceinline__ unsigned long long pk(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float pk_lo(unsigned long long p) { return __uint_as_float((unsigned)p); }
+__device__ __forceinline__ float pk_hi(unsigned long long p) { return __uint_as_float((unsigned)(p >> 32)); }
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // All 128 leaf threads: barrier 1, and whether every one of them is still ok.
 __device__ inline bool leaf_all(bool ok) {
   int r;
@@ -112,8 +125,8 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;"
 __device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // blockIdx.z = list entry z: diagonal tile tiles[z] (or tile0) of the FP64
-// arena t64; outputs at slot z of L32 (nb^2 floats, L) and pieces (3 nb^2,
-// the pieces of -L, so that the MMAs subtract X_J L^T by accumulating).
+// arena t64; outputs at slot z of L32 (nb^2 floats) and pieces (3 nb^2), both
+// of -L: the MMAs and the leaf subtract X L^T by accumulating.
 __global__ void k_lkk_prep(const double *__restrict__ t64, const long *__restrict__ tiles, long tile0,
                            float *__restrict__ L32, uint16_t *__restrict__ pieces, int nb, const int *st) {
   if (failed(st)) return;
@@ -128,7 +141,7 @@ __global__ void k_lkk_prep(const double *__restrict__ t64, const long *__restric
   for (int c = ty; c < 32; c += 8) {
     const size_t o = (size_t)(rb * 32 + tx) + (size_t)(cb * 32 + c) * nb;
     const double x = L[o];
-    L32z[o] = (float)x;
+    L32z[o] = (float)-x;
     blk[tx][c] = x;
   }
   __syncthreads();
@@ -328,12 +341,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       leaf_sync();       // everyone's
       const float *LJ = LJJ + (J & 1) * W * W;
       float *rinvJ = rinv + (J & 1) * W;
-      if (lt < W) rinvJ[lt] = 1.0f / LJ[lt * W + lt];
+      if (lt < W) rinvJ[lt] = -1.0f / LJ[lt * W + lt];  // LJ holds -L_JJ
       leaf_sync();
-      float v[W];
+      unsigned long long vp[W / 2];  // the row's block J, two columns per register pair
       if (J == 0) {
 #pragma unroll
-        for (int c = 0; c < W; c++) v[c] = __ldcg(Ab + (size_t)c * nb);
+        for (int j = 0; j < W / 2; j++) vp[j] = pk(__ldcg(Ab + (size_t)(2 * j) * nb), __ldcg(Ab + (size_t)(2 * j + 1) * nb));
       } else {
         if (!tc::mbar_wait(&sh->colready, (uint32_t)((J - 1) & 1), abort)) {
           raise_timeout(sh, status);
@@ -345,27 +358,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::tmem_ld_32x32b_x32(tl + (uint32_t)(J * W - W), r);
         tc::tmem_ld_wait();
 #pragma unroll
-        for (int x = 0; x < 32; x++) v[x] = __uint_as_float(r[x]);
+        for (int j = 0; j < 16; j++) vp[j] = pk(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
         tc::tmem_ld_32x32b_x32(tl + (uint32_t)(J * W - W + 32), r);
         tc::tmem_ld_wait();
 #pragma unroll
-        for (int x = 0; x < 32; x++) v[32 + x] = __uint_as_float(r[x]);
+        for (int j = 0; j < 16; j++) vp[16 + j] = pk(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
       }
-      // forward substitution: x_c = (v_c - sum_{c' < c} x_c' L(c, c')) / L(c, c)
+      // forward substitution: x_c = (v_c - sum_{c' < c} x_c' L(c, c')) / L(c, c),
+      // the updates of later columns by x_c two at a time (LJ = -L_JJ,
+      // column-major, read in 16-byte loads)
 #pragma unroll
       for (int c = 0; c < W; c++) {
-        const float x = v[c] * rinvJ[c];
-        v[c] = x;
-        // column c of L_JJ in 16-byte loads (rows 4g .. 4g+3 at or below c skipped)
-        const float4 *Lc4 = reinterpret_cast<const float4 *>(LJ + c * W);
-#pragma unroll
-        for (int g = (c + 1) / 4; g < W / 4; g++) {
-          const float4 l = Lc4[g];
-          if (4 * g + 0 > c) v[4 * g + 0] = fmaf(-x, l.x, v[4 * g + 0]);
-          if (4 * g + 1 > c) v[4 * g + 1] = fmaf(-x, l.y, v[4 * g + 1]);
-          if (4 * g + 2 > c) v[4 * g + 2] = fmaf(-x, l.z, v[4 * g + 2]);
-          if (4 * g + 3 > c) v[4 * g + 3] = fmaf(-x, l.w, v[4 * g + 3]);
+        const int j0 = c >> 1;
+        const float *Lc = LJ + c * W;
+        float x;
+        if (c & 1) {
+          x = pk_hi(vp[j0]) * rinvJ[c];
+          vp[j0] = pk(pk_lo(vp[j0]), x);
+        } else {
+          x = pk_lo(vp[j0]) * rinvJ[c];
+          vp[j0] = pk(x, fmaf(x, Lc[c + 1], pk_hi(vp[j0])));  // the partner column c + 1
         }
+        const unsigned long long xx = pk(x, x);
+        const float4 *Lc4 = reinterpret_cast<const float4 *>(Lc);
+#pragma unroll
+        for (int g = (j0 + 1) / 2; g < W / 4; g++) {
+          const float4 l = Lc4[g];
+          if (2 * g >= j0 + 1) vp[2 * g] = ffma2(xx, pk(l.x, l.y), vp[2 * g]);
+          if (2 * g + 1 >= j0 + 1) vp[2 * g + 1] = ffma2(xx, pk(l.z, l.w), vp[2 * g + 1]);
+        }
+      }
+      float v[W];
+#pragma unroll
+      for (int j = 0; j < W / 2; j++) {
+        v[2 * j] = pk_lo(vp[j]);
+        v[2 * j + 1] = pk_hi(vp[j]);
       }
 #pragma unroll
       for (int c = 0; c < W; c++) Ab[(size_t)(J * W + c) * nb] = v[c];

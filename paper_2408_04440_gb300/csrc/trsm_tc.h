@@ -25,9 +25,8 @@ constexpr int W = 64;    // column block
 // columns (nb - 64) fit in the 512 TMEM columns.
 inline bool supports(int nb) { return nb % RB == 0 && nb - W <= 512; }
 
-// FP32 copy (column-major, as the SIMT TRSM reads it) and the three BF16
-// pieces of the negated tile (row-major, strict upper triangle zero) of FP64
-// diagonal factor tiles of
+// FP32 copy (column-major) and three BF16 pieces (row-major, strict upper
+// triangle zero) of the negated FP64 diagonal factor tiles -L of
 // the arena t64 (nb x nb, column-major): entry z of the list, tile d_tiles[z]
 // (or `tile` when d_tiles is null, n = 1), goes to slot z: L32 + z nb^2 and
 // pieces + 3 z nb^2.
