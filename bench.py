@@ -277,8 +277,8 @@ ALU_NOTES = {
     "trsm64": "the FP64 panel TRSM is bound by its substitution chain and by the SMs left beside the bulk update",
     "trmm64": "FP64-class tiles of the sampler, FP64-pipe bound",
     "solve": "triangular solves, bound by their substitution chains",
-    "trsm32": "the FP32 panel TRSM is bound by its substitution chain and by L_kk strip loads, on the SMs left beside "
-              "the bulk update",
+    "trsm32": "the SIMT FP32 panel TRSM (tile sizes whose trailing columns do not fit in TMEM) is bound by its "
+              "substitution chain and by L_kk strip loads, on the SMs left beside the bulk update",
 }
 # ALU peaks measured on this GPU model with dependent-free FMA loops (TFLOP/s)
 ALU_PEAK = {"fp64": 1.19, "fp32": 74.0}

@@ -41,13 +41,12 @@ __device__ inline void cov_tables_part(int L, double beta, double sexp, double n
   }
   for (long l = tid; l < L; l += nthr) sigma[l] = pow(1.0 + l, -sexp);
   if (leader) {
-    double dmax = 0.0;
-    for (int l = 0; l < L; l++) {
-      double s = pow(1.0 + l, -sexp);
-      double v = s * s * 1.0;  // rho(0, 0) = exp(0) = 1
-      if (v > dmax) dmax = v;
-    }
-    *nugget = nugget_rel * dmax;
+    // max_l sigma[l]^2 rho(0, 0): (1 + l)^(-sexp) is monotone in l, so the
+    // largest square is at l = 0 or l = L - 1 (the same two pow values the
+    // whole scan would compare; rho(0, 0) = exp(0) = 1)
+    const double s0 = pow(1.0, -sexp), s1 = pow((double)L, -sexp);
+    const double v0 = s0 * s0 * 1.0, v1 = s1 * s1 * 1.0;
+    *nugget = nugget_rel * (v1 > v0 ? v1 : v0);
   }
 }
 
@@ -90,24 +89,48 @@ __device__ inline double block_sum(double v, double *sh) {
 __device__ inline double cov_tile_chunk(int L, int n, int nb, int ti, int tj, int chunk,
                                         const double *__restrict__ sigma, const double *__restrict__ rho,
                                         double nug, double *__restrict__ tile) {
-  int W = 4 * L - 3;
+  const int W = 4 * L - 3;
+  // this thread's rows (r = threadIdx.x + k blockDim.x): degree, order and
+  // sigma once per row; rho's index is then rbase - (l_j W + m_j) per entry
+  constexpr int kMaxRows = 8;  // nb <= 8 * kThreads
+  int rbase[kMaxRows];
+  double si[kMaxRows];
+  bool real[kMaxRows];
+#pragma unroll
+  for (int k = 0; k < kMaxRows; k++) {
+    const int r = threadIdx.x + k * blockDim.x;
+    const long gi = (long)ti * nb + r;
+    real[k] = r < nb && gi < n;
+    rbase[k] = 0;
+    si[k] = 0.0;
+    if (real[k]) {
+      const int li = degree_of(gi);
+      const int mi = (int)(gi - (long)li * li - li);
+      rbase[k] = (li + L - 1) * W + (mi + 2 * L - 2);
+      si[k] = sigma[li];
+    }
+  }
   double ss = 0.0;
   for (int cc = 0; cc < kChunk; cc++) {
-    int c = chunk * kChunk + cc;
-    long gj = (long)tj * nb + c;
-    int lj = 0, mj = 0;
+    const int c = chunk * kChunk + cc;
+    const long gj = (long)tj * nb + c;
+    int cbase = 0;
+    double sj = 0.0;
     if (gj < n) {
-      lj = degree_of(gj);
-      mj = (int)(gj - (long)lj * lj - lj);
+      const int lj = degree_of(gj);
+      const int mj = (int)(gj - (long)lj * lj - lj);
+      cbase = lj * W + mj;
+      sj = sigma[lj];
     }
-    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-      long gi = (long)ti * nb + r;
+#pragma unroll
+    for (int k = 0; k < kMaxRows; k++) {
+      const int r = threadIdx.x + k * blockDim.x;
+      if (r >= nb) break;
+      const long gi = (long)ti * nb + r;
       double v;
-      if (gi < n && gj < n) {
-        int li = degree_of(gi);
-        int mi = (int)(gi - (long)li * li - li);
-        double e = rho[(long)(li - lj + L - 1) * W + (mi - mj + 2 * L - 2)];
-        v = __dmul_rn(__dmul_rn(sigma[li], sigma[lj]), e);  // no FMA contraction
+      if (real[k] && gj < n) {
+        const double e = rho[rbase[k] - cbase];
+        v = __dmul_rn(__dmul_rn(si[k], sj), e);  // (sigma_i sigma_j) rho, no FMA contraction
         if (gi == gj) v = __dadd_rn(v, nug);
         ss += v * v;
       } else {
