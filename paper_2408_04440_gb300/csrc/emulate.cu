@@ -155,32 +155,52 @@ __global__ void k_sht_fourier(const double *__restrict__ z, long ldz, int ntheta
   const double w = 6.283185307179586 / (double)nphi;
   for (int m = threadIdx.x; m < L; m += blockDim.x) {
     double c = 0.0, sn = 0.0;
+    // r = m j mod nphi, stepped without a division
+    const int step = m % nphi;
+    int r = 0;
     for (int j = 0; j < nphi; j++) {
-      const long r = ((long)m * j) % nphi;
       c = fma(ring[j], csp[2 * r], c);
       sn = fma(ring[j], csp[2 * r + 1], sn);
+      r += step;
+      if (r >= nphi) r -= nphi;
     }
     cs[(size_t)(2 * m) * ntheta + i + (long)t * ldcs] = c * w;
     cs[(size_t)(2 * m + 1) * ntheta + i + (long)t * ldcs] = sn * w;
   }
 }
 
-// Fourier coefficients over the M-point circle of an extended function whose
-// first ntheta samples are v[0 .. ntheta) (v[i] at t_i = 2 pi i / M) and whose
-// reflection sign is sgn: out[q + L - 1] for |q| < L, complex.  cm: table of
-// cos / sin (2 pi r / M).
+// Fourier coefficients over the M-point circle (M = 2N, N = ntheta - 1) of
+// the extended function g: g_i = v[i] for i <= N (v[i] at t_i = 2 pi i / M)
+// and g_i = sgn v[M - i] above: out[q + L - 1] for |q| < L, complex, of
+// (1/M) sum_i g_i exp(-2 pi i q i / M).  The samples i and M - i (0 < i < N)
+// pair up: for sgn = +1 their sum is 2 v[i] cos(2 pi q i / M) and the sines
+// cancel, for sgn = -1 the cosines cancel and -2 v[i] sin(2 pi q i / M) is
+// left; i = 0 and i = N add v[0] + (-1)^q v[N].  g is real, so the
+// coefficient at -q is the conjugate of the one at q.  cm: table of
+// cos / sin (2 pi r / M); r = q i mod M is stepped without a division.
 __device__ inline void circle_coeffs(const double *v, double sgn, int ntheta, int M, int L, const double *cm,
                                      double *outr, double *outi) {
-  for (int q = threadIdx.x - (L - 1); q <= L - 1; q += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int i = 0; i < M; i++) {
-      const double g = i < ntheta ? v[i] : sgn * v[M - i];
-      const long r = (((long)q * i) % M + M) % M;
-      re = fma(g, cm[2 * r], re);
-      im = fma(-g, cm[2 * r + 1], im);
+  const int N = ntheta - 1;
+  const double invM = 1.0 / (double)M;
+  const int odd = sgn < 0.0 ? 1 : 0;  // sine sums
+  for (int q = threadIdx.x; q <= L - 1; q += blockDim.x) {
+    const int step = q % M;
+    int r = step;
+    double acc = 0.0;
+    for (int i = 1; i < N; i++) {
+      acc = fma(v[i], cm[2 * r + odd], acc);
+      r += step;
+      if (r >= M) r -= M;
     }
-    outr[q + L - 1] = re / M;
-    outi[q + L - 1] = im / M;
+    const double ends = v[0] + ((q & 1) ? -v[N] : v[N]);
+    const double re = odd ? ends * invM : (ends + 2.0 * acc) * invM;
+    const double im = odd ? -2.0 * acc * invM : 0.0;
+    outr[q + L - 1] = re;
+    outi[q + L - 1] = im;
+    if (q > 0) {
+      outr[L - 1 - q] = re;
+      outi[L - 1 - q] = -im;
+    }
   }
 }
 
