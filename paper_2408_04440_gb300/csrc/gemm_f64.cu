@@ -224,56 +224,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Row exponents and digit planes of a column block of listed FP64 tiles:
-// X = tile[:, col0 : col0 + w] (column-major, nb rows), slot s = blockIdx.z
-// of the list: exps[s * nb + r], plane p of row r at
-// digits + ((s * NS + p) * nb + r) * w, K-major.  lower != 0 treats the
-// entries above the tile's diagonal (column > row) as zero.
-__global__ void __launch_bounds__(256)
-    k_rowexp_cols(const double *__restrict__ t64, const int *__restrict__ tiles, int nb, int col0, int w, int lower,
-                  int *__restrict__ exps, const int *st) {
-  if (failed(st)) return;
-  __shared__ double red[8][33];
-  const int s = blockIdx.y;
-  const double *X = t64 + (size_t)tiles[s] * nb * nb;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int r = blockIdx.x * 32 + lane;
-  double m = 0.0;
-  for (int c = wp; c < w; c += 8)
-    if (!lower || col0 + c <= r) m = fmax(m, fabs(X[r + (size_t)(col0 + c) * nb]));
-  red[wp][lane] = m;
-  __syncthreads();
-  if (wp == 0) {
-    for (int q = 1; q < 8; q++) m = fmax(m, red[q][lane]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    exps[(size_t)s * nb + r] = (m > 0.0 ? e : kExpMin) + kExpBias;
-  }
-}
-
-__global__ void __launch_bounds__(256)
-    k_slice_cols(const double *__restrict__ t64, const int *__restrict__ tiles, int nb, int col0, int w, int lower,
-                 const int *__restrict__ exps, uint16_t *__restrict__ digits, const int *st) {
-  if (failed(st)) return;
-  __shared__ double blk[32][33];
-  const int s = blockIdx.z;
-  const double *X = t64 + (size_t)tiles[s] * nb * nb;
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int cc = wp; cc < 32; cc += 8) {
-    const int r = r0 + lane, c = col0 + c0 + cc;
-    blk[lane][cc] = (lower && c > r) ? 0.0 : X[r + (size_t)c * nb];
-  }
-  __syncthreads();
-  const size_t plane = (size_t)nb * w;
-  uint16_t *d = digits + (size_t)s * NS * plane;
-  for (int q = 0; q < 4; q++) {
-    const int rr = wp + 8 * q, r = r0 + rr;
-    const double v = blk[rr][lane] * exp2i(-exp_of(exps, (long)s * nb + r));  // exact: |v| < 1
-    write_digits(v, d + (size_t)r * w + c0 + lane, plane);
-  }
-}
-
 // Digits of Z columns per matrix block: one CTA per (sample c < s_pad, block).
 // The exponent covers the block's rows of column c; samples c >= s are zero.
 __global__ void __launch_bounds__(256)
@@ -550,19 +500,6 @@ emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_
   ProfScope ps(ctx, PROF_SPLIT, 0.0, (8.0 + 2.0 * NS) * (double)s_pad * zcols);
   k_slicez64<<<dim3(s_pad, nblocks), 256, 0, ctx->stream>>>(Z, ldz, s, s_pad, d_blocks, zcols, exps, digits,
                                                             ctx->d_status);
-  EMU_LAUNCHED(ctx);
-  return EMU_OK;
-}
-
-emu_status launch_col_digits(emu_ctx *ctx, const double *t64, const int *d_tiles, int ntiles, int nb, int col0, int w,
-                             int lower, int *exps, uint16_t *digits) {
-  if (ntiles <= 0) return EMU_OK;
-  if (nb % 32 != 0 || w % 32 != 0 || col0 % 32 != 0 || col0 + w > nb) return EMU_EINVAL;
-  ProfScope ps(ctx, PROF_SPLIT, 0.0, (16.0 + 2.0 * NS) * (double)ntiles * nb * w);
-  k_rowexp_cols<<<dim3(nb / 32, ntiles), 256, 0, ctx->stream>>>(t64, d_tiles, nb, col0, w, lower, exps, ctx->d_status);
-  EMU_LAUNCHED(ctx);
-  k_slice_cols<<<dim3(w / 32, nb / 32, ntiles), 256, 0, ctx->stream>>>(t64, d_tiles, nb, col0, w, lower, exps, digits,
-                                                                      ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

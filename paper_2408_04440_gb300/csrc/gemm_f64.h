@@ -73,14 +73,6 @@ emu_status launch_slice(emu_ctx *ctx, const double *t64, const float *t32, const
 emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_pad, const int2 *d_blocks,
                           int nblocks, long zcols, int *exps, uint16_t *digits);
 
-// Row exponents and digit planes of the column block [col0, col0 + w) of
-// listed FP64 tiles (nb x nb, column-major): slot s of the list writes
-// exps[s * nb + r] (not max-accumulated: each launch sets them) and plane p of
-// row r at digits + ((s * NS + p) * nb + r) * w.  lower != 0 ignores the
-// entries above the tile's diagonal.
-emu_status launch_col_digits(emu_ctx *ctx, const double *t64, const int *d_tiles, int ntiles, int nb, int col0, int w,
-                             int lower, int *exps, uint16_t *digits);
-
 // Row exponents and digit planes of a dense column-major FP64 block
 // X[0:nrows, col0:col0+ncols] (leading dimension ld): exps[r] for r < npad
 // (zeroed first), plane p of row r at digits + (p * npad + r) * kpad, K-major,
