@@ -151,6 +151,9 @@ emu_status emu_destroy(emu_ctx *ctx) {
   cudaFree(ctx->trace_buf);
   mixed_ctx_release(ctx);
   batch_ctx_release(ctx);
+  for (cudaEvent_t e : ctx->xev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->xfer) cudaStreamDestroy(ctx->xfer);
   delete ctx;
   return EMU_OK;
 }
@@ -410,17 +413,37 @@ emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda, 
   emu_mat *A = nullptr;
   emu_status s = mat_alloc(ctx, n, nb, &A);
   if (s != EMU_OK) return s;
-  double *stage = nullptr;
-  cudaError_t e = cudaMallocAsync(&stage, (size_t)n * nb * sizeof(double), ctx->stream);
+  // Tile column j: its lower part (rows r0 .. n-1) is copied on the copy
+  // stream into staging buffer j % 2 while the import kernel of column j - 1
+  // reads the other one; events order copy -> import and import -> reuse.
+  cudaError_t e = cudaSuccess;
+  if (!ctx->xfer) e = cudaStreamCreateWithFlags(&ctx->xfer, cudaStreamNonBlocking);
+  for (int i = 0; i < 5 && e == cudaSuccess; i++)
+    if (!ctx->xev[i]) e = cudaEventCreateWithFlags(&ctx->xev[i], cudaEventDisableTiming);
+  cudaEvent_t ev_alloc = ctx->xev[0], ev_copied[2] = {ctx->xev[1], ctx->xev[2]}, ev_free[2] = {ctx->xev[3], ctx->xev[4]};
+  double *stage[2] = {nullptr, nullptr};
+  for (int b = 0; b < 2 && e == cudaSuccess; b++)
+    e = cudaMallocAsync(&stage[b], (size_t)n * nb * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_alloc, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer, ev_alloc, 0);
   for (int j = 0; j < A->nt && e == cudaSuccess && s == EMU_OK; j++) {
+    const int b = j & 1;
     long r0 = (long)j * nb;
     long cols = (r0 + nb <= n) ? nb : n - r0;
+    if (j >= 2) e = cudaStreamWaitEvent(ctx->xfer, ev_free[b], 0);  // column j - 2 is imported
     // rows r0 .. n-1 of columns r0 .. r0+cols-1: the lower part of tile column j
-    e = cudaMemcpy2DAsync(stage, (size_t)(n - r0) * sizeof(double), hA + r0 + r0 * lda, lda * sizeof(double),
-                          (size_t)(n - r0) * sizeof(double), cols, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) s = launch_import_col(ctx, A, j, stage, n - r0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(stage[b], (size_t)(n - r0) * sizeof(double), hA + r0 + r0 * lda, lda * sizeof(double),
+                            (size_t)(n - r0) * sizeof(double), cols, cudaMemcpyHostToDevice, ctx->xfer);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_copied[b], ctx->xfer);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ev_copied[b], 0);
+    if (e == cudaSuccess) s = launch_import_col(ctx, A, j, stage[b], n - r0);
+    if (e == cudaSuccess && s == EMU_OK) e = cudaEventRecord(ev_free[b], ctx->stream);
   }
-  if (stage) cudaFreeAsync(stage, ctx->stream);
+  // every copy issued (also on an error path) is ordered before the frees
+  if (cudaEventRecord(ev_alloc, ctx->xfer) == cudaSuccess) cudaStreamWaitEvent(ctx->stream, ev_alloc, 0);
+  for (int b = 0; b < 2; b++)
+    if (stage[b]) cudaFreeAsync(stage[b], ctx->stream);
   if (e == cudaSuccess && s == EMU_OK) s = launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
   if (e == cudaSuccess && s == EMU_OK) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) s = emu_cuda_fail(ctx, e, "import_host");

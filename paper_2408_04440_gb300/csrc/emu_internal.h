@@ -78,6 +78,10 @@ struct emu_ctx {
   // trailing update, and events ordering them
   cudaStream_t crit = nullptr, mid = nullptr, bulk = nullptr;
   std::vector<cudaEvent_t> sched_ev;
+  // host imports: copy stream and its ordering events (allocation, copied[2],
+  // staging buffer free[2]), created on first use
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t xev[5] = {};
   // dataflow POTRF of a diagonal tile: task list and workspace (per nb)
   void *dag_tasks = nullptr;
   int *dag_ws = nullptr;
