@@ -172,8 +172,11 @@ emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
 // d_rows: device list of the tile rows i > k to solve (nullptr: all of them)
-emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows = nullptr,
-                               int nrows = 0);
+emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows = nullptr, int nrows = 0,
+                               const double *Ls = nullptr, const double *rinvs = nullptr);
+// Pre-scaled 32x32 diagonal blocks of the FP64 factor tile L (nb x nb,
+// column-major) for launch_trsm64_panel: Ls[nb * 32], rinvs[nb].
+emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs);
 emu_status launch_update64(emu_ctx *ctx, emu_mat *A, int k);
 emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A);
 // cls != nullptr: only the FP64-class tiles contribute (mixed factors)

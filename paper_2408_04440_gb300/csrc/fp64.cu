@@ -572,9 +572,29 @@ static void dag_tasks(int nbb, std::vector<short4> &out, bool master) {
 // against the 32x32 diagonal block by forward substitution with shuffles.
 constexpr int T64_ROWS = 4;
 constexpr int T64_STRIP = 128;
+// Optional pre-scaled diagonal blocks (k_trsm64_prep): Ls[(cb*32 + p)*32 + l]
+// = L(cb*32 + l, cb*32 + p) / L(cb*32 + p, cb*32 + p) for p < l and rinvs[c] =
+// 1 / L(c, c); the block solve then takes one FMA per step (a_l -= a_p Ls)
+// and one multiply at the end, where it otherwise scales each x_p first.
+__global__ void k_trsm64_prep(const double *__restrict__ L, int nb, double *__restrict__ Ls,
+                              double *__restrict__ rinvs, const int *st) {
+  if (failed(st)) return;
+  __shared__ double rj[B];
+  const int cb = blockIdx.x, l = threadIdx.x & (B - 1), p = threadIdx.x >> 5;  // 32 x 32
+  const double v = L[(size_t)(cb * B + l) + (size_t)(cb * B + p) * nb];
+  if (l == p) {
+    const double r = 1.0 / v;
+    rj[p] = r;
+    rinvs[cb * B + p] = r;
+  }
+  __syncthreads();
+  Ls[(size_t)(cb * B + p) * B + l] = (p < l) ? v * rj[p] : 0.0;
+}
+
 __global__ void __launch_bounds__(128)
     k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
-                   const int *st, const int2 *__restrict__ jobs = nullptr) {
+                   const int *st, const int2 *__restrict__ jobs = nullptr, const double *__restrict__ Ls = nullptr,
+                   const double *__restrict__ rinvs = nullptr) {
   if (failed(st)) return;
   extern __shared__ double sm64[];
   const int ldx = nb + 1;
@@ -605,8 +625,13 @@ __global__ void __launch_bounds__(128)
   for (int cb = 0; cb < nbb; cb++) {
     const double *Lrow = Lkk + cb * B + lane;  // row cb*32 + lane of L_kk
     double ld[B];
+    if (Ls) {
 #pragma unroll
-    for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.0;
+      for (int p = 0; p < B; p++) ld[p] = (p < lane) ? Ls[(size_t)(cb * B + p) * B + lane] : 0.0;
+    } else {
+#pragma unroll
+      for (int p = 0; p < B; p++) ld[p] = (p <= lane) ? Lrow[(size_t)(cb * B + p) * nb] : 0.0;
+    }
     __syncthreads();
     double a0 = X[w * ldx + cb * B + lane], a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int p0 = 0; p0 < cb * B; p0 += T64_STRIP) {
@@ -635,17 +660,26 @@ __global__ void __launch_bounds__(128)
       __syncthreads();
     }
     double a = (a0 + a1) + (a2 + a3);
-    double mydiag = ld[0];
+    if (Ls) {
 #pragma unroll
-    for (int p = 1; p < B; p++)
-      if (p == lane) mydiag = ld[p];
-    double myrinv = 1.0 / mydiag;  // off the dependency chain
+      for (int j = 0; j < B; j++) {
+        const double aj = __shfl_sync(0xffffffffu, a, j);
+        if (lane > j) a = fma(-aj, ld[j], a);
+      }
+      a *= rinvs[cb * B + lane];
+    } else {
+      double mydiag = ld[0];
 #pragma unroll
-    for (int j = 0; j < B; j++) {
-      double rj = __shfl_sync(0xffffffffu, myrinv, j);
-      double xj = __shfl_sync(0xffffffffu, a, j) * rj;
-      if (lane == j) a = xj;
-      if (lane > j) a -= xj * ld[j];
+      for (int p = 1; p < B; p++)
+        if (p == lane) mydiag = ld[p];
+      double myrinv = 1.0 / mydiag;  // off the dependency chain
+#pragma unroll
+      for (int j = 0; j < B; j++) {
+        double rj = __shfl_sync(0xffffffffu, myrinv, j);
+        double xj = __shfl_sync(0xffffffffu, a, j) * rj;
+        if (lane == j) a = xj;
+        if (lane > j) a -= xj * ld[j];
+      }
     }
     X[w * ldx + cb * B + lane] = a;
   }
@@ -958,7 +992,16 @@ emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const 
   return EMU_OK;
 }
 
-emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows, int nrows) {
+emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs) {
+  if (nb % B != 0) return EMU_EINVAL;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 16.0 * (double)nb * B);
+  k_trsm64_prep<<<nb / B, B * B, 0, ctx->stream>>>(L, nb, Ls, rinvs, ctx->d_status);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows, int nrows, const double *Ls,
+                               const double *rinvs) {
   int m = d_rows ? nrows : A->nt - k - 1;
   if (m <= 0) return EMU_OK;
   double nb3 = (double)A->nb * A->nb * A->nb;
@@ -966,7 +1009,7 @@ emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_row
   size_t sm = (size_t)(T64_ROWS * (A->nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
   EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_trsm64_panel<<<dim3(A->nb / T64_ROWS, m), 128, sm, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
-                                                                     ctx->d_status);
+                                                                     ctx->d_status, nullptr, Ls, rinvs);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

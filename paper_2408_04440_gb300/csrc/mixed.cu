@@ -469,6 +469,8 @@ struct MixedPlan {
   int *d_diag_tiles = nullptr;        // all diagonal tiles (split after the factor)
   float *d_lkk32 = nullptr;           // FP32 copies of L_kk, double-buffered by step parity
   uint16_t *d_lkkp = nullptr;         // three BF16 pieces of L_kk (row-major), same slots (tensor-core TRSM)
+  double *d_ls64 = nullptr;           // pre-scaled diagonal blocks of L_kk for the FP64 TRSM (nb x 32), same slots
+  double *d_rinv64 = nullptr;         // 1 / L_kk(c, c), same slots
   CUtensorMap lmap;                   // over d_lkkp
   CUtensorMap opmap;                  // over the piece arena (the TRSM's tile stores)
   bool tc_trsm = false;               // FP32-class panel TRSMs on the tensor cores (trsm_tc.cu)
@@ -679,7 +681,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
          o_s64 = part(vbytes(segs64)), o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
          o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)), o_tt = part(vbytes(ttiles)),
-         o_lkk = part(2 * (size_t)nb * nb * sizeof(float)), o_lkkp = part(2 * 3 * (size_t)nb * nb * sizeof(uint16_t));
+         o_lkk = part(2 * (size_t)nb * nb * sizeof(float)), o_lkkp = part(2 * 3 * (size_t)nb * nb * sizeof(uint16_t)),
+         o_ls64 = part(2 * (size_t)nb * 32 * sizeof(double)), o_rinv64 = part(2 * (size_t)nb * sizeof(double));
   size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
   P->host_blob.assign(copy_bytes, 0);
   auto put = [&](size_t o, const auto &v) {
@@ -713,6 +716,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_ttiles = reinterpret_cast<int *>(b + o_tt);
   P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
   P->d_lkkp = reinterpret_cast<uint16_t *>(b + o_lkkp);
+  P->d_ls64 = reinterpret_cast<double *>(b + o_ls64);
+  P->d_rinv64 = reinterpret_cast<double *>(b + o_rinv64);
   emu_status s;
   uint64_t rows = (uint64_t)A->ntiles * 3 * nb;
   if ((s = gemm_tc::make_map_bf16(ctx, &P->mapA, A->op_bf16, nb, rows, gemm_tc::BM)) != EMU_OK) return s;
@@ -868,7 +873,9 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
     emu_status e = EMU_OK;
     if (n64 > 0) {
-      if ((e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64)) != EMU_OK) return e;
+      if ((e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64, P->d_ls64 + (size_t)(k & 1) * nb * 32,
+                                   P->d_rinv64 + (size_t)(k & 1) * nb)) != EMU_OK)
+        return e;
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
       k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
                                                                                     P->d_tiles64 + r64, nb, 0, st);
@@ -933,6 +940,10 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
         EMU_LAUNCHED(ctx);
       }
     }
+    if (sp.n64_1 + sp.n64_r > 0 &&
+        (s = launch_trsm64_prep(ctx, A->t64 + tkk * te, nb, P->d_ls64 + (size_t)(k & 1) * nb * 32,
+                                P->d_rinv64 + (size_t)(k & 1) * nb)) != EMU_OK)
+      break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
     if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
