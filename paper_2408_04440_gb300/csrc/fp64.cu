@@ -576,17 +576,11 @@ constexpr int T64_STRIP = 128;
 // = L(cb*32 + l, cb*32 + p) / L(cb*32 + p, cb*32 + p) for p < l and rinvs[c] =
 // 1 / L(c, c); the block solve then takes one FMA per step (a_l -= a_p Ls)
 // and one multiply at the end, where it otherwise scales each x_p first.
-// blockIdx.y = z: tile tiles[z] of t64 (or t64 itself when tiles is null),
-// outputs in slot z (Ls + z nb 32, rinvs + z nb).
-__global__ void k_trsm64_prep(const double *__restrict__ t64, const long *__restrict__ tiles, int nb,
-                              double *__restrict__ Ls, double *__restrict__ rinvs, const int *st) {
+__global__ void k_trsm64_prep(const double *__restrict__ L, int nb, double *__restrict__ Ls,
+                              double *__restrict__ rinvs, const int *st) {
   if (failed(st)) return;
   __shared__ double rj[B];
   const int cb = blockIdx.x, l = threadIdx.x & (B - 1), p = threadIdx.x >> 5;  // 32 x 32
-  const int z = blockIdx.y;
-  const double *L = t64 + (tiles ? (size_t)tiles[z] * nb * nb : 0);
-  Ls += (size_t)z * nb * B;
-  rinvs += (size_t)z * nb;
   const double v = L[(size_t)(cb * B + l) + (size_t)(cb * B + p) * nb];
   if (l == p) {
     const double r = 1.0 / v;
@@ -600,7 +594,7 @@ __global__ void k_trsm64_prep(const double *__restrict__ t64, const long *__rest
 __global__ void __launch_bounds__(128)
     k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
                    const int *st, const int2 *__restrict__ jobs = nullptr, const double *__restrict__ Ls = nullptr,
-                   const double *__restrict__ rinvs = nullptr, const int *__restrict__ jslots = nullptr) {
+                   const double *__restrict__ rinvs = nullptr) {
   if (failed(st)) return;
   extern __shared__ double sm64[];
   const int ldx = nb + 1;
@@ -614,10 +608,6 @@ __global__ void __launch_bounds__(128)
     int2 jb = jobs[blockIdx.y];
     tik = jb.x;
     tkk = jb.y;
-    if (Ls && jslots) {  // pre-scaled blocks of this job's L_kk
-      Ls += (size_t)jslots[blockIdx.y] * nb * B;
-      rinvs += (size_t)jslots[blockIdx.y] * nb;
-    }
   } else {
     int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
     tik = tile_index(i, k, NT);
@@ -959,15 +949,14 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   return EMU_OK;
 }
 
-emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs, const double *Ls,
-                              const double *rinvs, const int *d_jslots) {
+emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs) {
   if (njobs <= 0) return EMU_OK;
   double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM64, njobs * nb3, 16.0 * njobs * nb * nb);
   size_t sm = (size_t)(T64_ROWS * (nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
   EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_trsm64_panel<<<dim3(nb / T64_ROWS, njobs), 128, sm, ctx->stream>>>(t64, nb, 0, 0, nullptr, ctx->d_status,
-                                                                      d_jobs, Ls, rinvs, d_jslots);
+                                                                      d_jobs);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -1003,12 +992,10 @@ emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const 
   return EMU_OK;
 }
 
-emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs, const long *d_tiles,
-                              int n) {
+emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs) {
   if (nb % B != 0) return EMU_EINVAL;
-  if (n <= 0) return EMU_OK;
-  ProfScope ps(ctx, PROF_SPLIT, 0.0, 16.0 * n * (double)nb * B);
-  k_trsm64_prep<<<dim3(nb / B, n), B * B, 0, ctx->stream>>>(L, d_tiles, nb, Ls, rinvs, ctx->d_status);
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 16.0 * (double)nb * B);
+  k_trsm64_prep<<<nb / B, B * B, 0, ctx->stream>>>(L, nb, Ls, rinvs, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
