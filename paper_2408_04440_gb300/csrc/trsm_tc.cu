@@ -348,10 +348,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int j = 0; j < W / 2; j++) vp[j] = pk(__ldcg(Ab + (size_t)(2 * j) * nb), __ldcg(Ab + (size_t)(2 * j + 1) * nb));
       } else {
-        if (!tc::mbar_wait(&sh->colready, (uint32_t)((J - 1) & 1), abort)) {
-          raise_timeout(sh, status);
+        // every wait's outcome is agreed by all leaf threads at once, so that
+        // they all take the same path through barrier 1
+        const bool got = tc::mbar_wait(&sh->colready, (uint32_t)((J - 1) & 1), abort);
+        if (!got) raise_timeout(sh, status);
+        if (!leaf_all(got)) {
           ok = false;
-          continue;  // to the agreement at the top of the loop
+          break;
         }
         tc::fence_after_sync();
         uint32_t r[32];
@@ -397,11 +400,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int c = 0; c < W; c++) Ab[(size_t)(J * W + c) * nb] = v[c];
       const bool feed = J + 1 < NJ;  // the last block updates nothing
-      // the MMAs of block J - 2 have read this buffer
-      if (!tc::mbar_wait(&sh->aempty[J & 1], (uint32_t)(((J >> 1) & 1) ^ 1), abort)) {
-        raise_timeout(sh, status);
+      // the MMAs of block J - 2 have read this buffer (outcome agreed as above)
+      const bool got = tc::mbar_wait(&sh->aempty[J & 1], (uint32_t)(((J >> 1) & 1) ^ 1), abort);
+      if (!got) raise_timeout(sh, status);
+      if (!leaf_all(got)) {
         ok = false;
-        continue;
+        break;
       }
       // X_J's pieces, K-major with the 128-byte swizzle (16-byte chunk ch of
       // row `row` at chunk position ch ^ (row & 7)): the A operand of the
