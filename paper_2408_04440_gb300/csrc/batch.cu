@@ -121,6 +121,8 @@ struct BatchState {
   long *d_diag = nullptr, *d_all_diag = nullptr;
   int *d_all_diag_int = nullptr;
   int2 *d_t64 = nullptr, *d_t32 = nullptr;
+  int *d_t64slot = nullptr;  // per FP64 TRSM job: the step slot of its L_kk (pre-scaled blocks)
+  double *ls64 = nullptr, *rinv64 = nullptr;  // pre-scaled diagonal blocks of the step's L_kk, per slot
   int *d_s64 = nullptr, *d_q = nullptr;
   int4 *d_pairs = nullptr;
   gemm64::Item *d_items64 = nullptr, *d_items64s = nullptr;
@@ -143,6 +145,7 @@ struct BatchState {
   void release() {
     void *ps[] = {t64, partial, tnorm, frob, tables, t32, slots, scale8, op, zp, op8, d_cls, d_inst, d_tile_inst,
                   Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_all_diag, d_all_diag_int, d_t64,
+                  d_t64slot, ls64, rinv64,
                   d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_items64,
                   d_items64s, d_segs64, d_segs64s, d_z, d_zs, d_zblk, digits, exp64, exp_s, exp_z, lpieces};
     for (void *p : ps)
@@ -242,6 +245,7 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   auto C = [&](long g) { return (int)B->cls[g]; };
   std::vector<long> longs;
   std::vector<int2> j64, j32;
+  std::vector<int> j64slot;
   std::vector<int> s64, q;
   std::vector<gemm64::Item> items64;
   std::vector<gemm64::Seg> segs64;
@@ -296,6 +300,7 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
         long gik = I.tile_base + tile_index(i, k, I.NT);
         if (C(gik) == EMU_CLASS_FP64) {
           j64.push_back(make_int2((int)gik, (int)gkk));
+          j64slot.push_back(slot[b]);
           if (B->any_low) s64.push_back((int)gik);  // BF16 pieces only feed tensor-core updates
         } else {
           j32.push_back(make_int2((int)gik, slot[b]));
@@ -486,6 +491,7 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   emu_status s;
   if ((s = upload(ctx, &B->d_diag, longs)) != EMU_OK || (s = upload(ctx, &B->d_all_diag, all_diag)) != EMU_OK ||
       (s = upload(ctx, &B->d_all_diag_int, all_diag_int)) != EMU_OK || (s = upload(ctx, &B->d_t64, j64)) != EMU_OK ||
+      (s = upload(ctx, &B->d_t64slot, j64slot)) != EMU_OK ||
       (s = upload(ctx, &B->d_t32, j32)) != EMU_OK || (s = upload(ctx, &B->d_s64, s64)) != EMU_OK ||
       (s = upload(ctx, &B->d_q, q)) != EMU_OK || (s = upload(ctx, &B->d_items64, items64)) != EMU_OK ||
       (s = upload(ctx, &B->d_z, zjobs)) != EMU_OK || (s = upload(ctx, &B->d_segs64, segs64)) != EMU_OK ||
@@ -519,6 +525,10 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   if (B->nslots_s > 0) {
     B->exp_s = dalloc<int>(B->nrows, &s);
     B->exp_z = dalloc<int>((size_t)count * B->s_pad, &s);
+  }
+  if (!j64.empty()) {
+    B->ls64 = dalloc<double>((size_t)B->max_active * nb * 32, &s);
+    B->rinv64 = dalloc<double>((size_t)B->max_active * nb, &s);
   }
   B->ntasks = (int)potrf_dag_task_count(nb);
   B->tasks = dalloc<short4>(B->ntasks, &s);
@@ -627,7 +637,13 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
                      : launch_diag_to_f32_slots(ctx, B->t64, B->slots, B->d_diag + st.d_off, st.d_n, te);
       if (s != EMU_OK) return s;
     }
-    if ((s = launch_trsm64_jobs(ctx, B->t64, nb, B->d_t64 + st.t64_off, st.t64_n)) != EMU_OK) return s;
+    if (st.t64_n > 0) {
+      // the step's L_kk with their diagonal blocks pre-scaled, one slot per matrix, then the FP64 TRSMs
+      if ((s = launch_trsm64_prep(ctx, B->t64, nb, B->ls64, B->rinv64, B->d_diag + st.d_off, st.d_n)) != EMU_OK ||
+          (s = launch_trsm64_jobs(ctx, B->t64, nb, B->d_t64 + st.t64_off, st.t64_n, B->ls64, B->rinv64,
+                                  B->d_t64slot + st.t64_off)) != EMU_OK)
+        return s;
+    }
     if ((s = launch_split_tiles64(ctx, B->t64, B->op, B->d_s64 + st.s64_off, st.s64_n, nb, 0)) != EMU_OK) return s;
     s = B->tc_trsm ? trsm_tc::launch(ctx, B->lmap, B->opmap, B->slots, B->t32, nb, 0, 0, nullptr,
                                      B->d_t32 + st.t32_off, st.t32_n)

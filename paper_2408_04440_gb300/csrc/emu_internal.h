@@ -174,9 +174,12 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
 // d_rows: device list of the tile rows i > k to solve (nullptr: all of them)
 emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows = nullptr, int nrows = 0,
                                const double *Ls = nullptr, const double *rinvs = nullptr);
-// Pre-scaled 32x32 diagonal blocks of the FP64 factor tile L (nb x nb,
-// column-major) for launch_trsm64_panel: Ls[nb * 32], rinvs[nb].
-emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs);
+// Pre-scaled 32x32 diagonal blocks of FP64 factor tiles (nb x nb,
+// column-major) for the FP64 panel TRSM: slot z of Ls[n][nb * 32] and
+// rinvs[n][nb] from tile d_tiles[z] of the arena L (or L itself, n = 1, when
+// d_tiles is null).
+emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs,
+                              const long *d_tiles = nullptr, int n = 1);
 emu_status launch_update64(emu_ctx *ctx, emu_mat *A, int k);
 emu_status launch_tril_diag(emu_ctx *ctx, emu_mat *A);
 // cls != nullptr: only the FP64-class tiles contribute (mixed factors)
@@ -200,7 +203,10 @@ emu_status launch_export_batch(emu_ctx *ctx, const BatchInst *d_inst, const int4
                                double *const *d_out);
 emu_status launch_normals_batch(emu_ctx *ctx, const uint64_t *d_seed, const BatchInst *d_inst, int count,
                                 int maxNT, int nb, int s, double *Z, long ldz);
-emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs);
+// jobs {tile (i,k), tile (k,k)}; with Ls / rinvs, job j's L_kk is pre-scaled in slot d_jslots[j]
+emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs,
+                              const double *Ls = nullptr, const double *rinvs = nullptr,
+                              const int *d_jslots = nullptr);
 emu_status launch_to_f32_tiles(emu_ctx *ctx, const double *t64, float *t32, const unsigned char *cls, long ntiles,
                                size_t te);
 emu_status launch_tiles_to_f64(emu_ctx *ctx, const float *t32, double *t64, const long *d_tiles, int n, size_t te);

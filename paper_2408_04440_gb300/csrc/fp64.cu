@@ -576,11 +576,17 @@ constexpr int T64_STRIP = 128;
 // = L(cb*32 + l, cb*32 + p) / L(cb*32 + p, cb*32 + p) for p < l and rinvs[c] =
 // 1 / L(c, c); the block solve then takes one FMA per step (a_l -= a_p Ls)
 // and one multiply at the end, where it otherwise scales each x_p first.
-__global__ void k_trsm64_prep(const double *__restrict__ L, int nb, double *__restrict__ Ls,
-                              double *__restrict__ rinvs, const int *st) {
+// blockIdx.y = z: tile tiles[z] of t64 (or t64 itself when tiles is null),
+// outputs in slot z (Ls + z nb 32, rinvs + z nb).
+__global__ void k_trsm64_prep(const double *__restrict__ t64, const long *__restrict__ tiles, int nb,
+                              double *__restrict__ Ls, double *__restrict__ rinvs, const int *st) {
   if (failed(st)) return;
   __shared__ double rj[B];
   const int cb = blockIdx.x, l = threadIdx.x & (B - 1), p = threadIdx.x >> 5;  // 32 x 32
+  const int z = blockIdx.y;
+  const double *L = t64 + (tiles ? (size_t)tiles[z] * nb * nb : 0);
+  Ls += (size_t)z * nb * B;
+  rinvs += (size_t)z * nb;
   const double v = L[(size_t)(cb * B + l) + (size_t)(cb * B + p) * nb];
   if (l == p) {
     const double r = 1.0 / v;
@@ -591,10 +597,14 @@ __global__ void k_trsm64_prep(const double *__restrict__ L, int nb, double *__re
   Ls[(size_t)(cb * B + p) * B + l] = (p < l) ? v * rj[p] : 0.0;
 }
 
+// JOBS = false: the tiles (rows[y], k) of one matrix; JOBS = true: explicit
+// jobs (batched factor), each with the slot of its pre-scaled L_kk blocks.
+// Two instances, so that the single-matrix code does not carry the job path.
+template <bool JOBS>
 __global__ void __launch_bounds__(128)
     k_trsm64_panel(double *__restrict__ t64, int nb, int NT, int k, const int *__restrict__ rows,
-                   const int *st, const int2 *__restrict__ jobs = nullptr, const double *__restrict__ Ls = nullptr,
-                   const double *__restrict__ rinvs = nullptr) {
+                   const int *st, const int2 *__restrict__ jobs, const double *__restrict__ Ls,
+                   const double *__restrict__ rinvs, const int *__restrict__ jslots) {
   if (failed(st)) return;
   extern __shared__ double sm64[];
   const int ldx = nb + 1;
@@ -604,10 +614,14 @@ __global__ void __launch_bounds__(128)
   int r0 = blockIdx.x * T64_ROWS;
   // tiles (i, k) and (k, k) of one matrix, or (batched) explicit tile indices
   long tik, tkk;
-  if (jobs) {
+  if (JOBS) {
     int2 jb = jobs[blockIdx.y];
     tik = jb.x;
     tkk = jb.y;
+    if (Ls) {  // pre-scaled blocks of this job's L_kk
+      Ls += (size_t)jslots[blockIdx.y] * nb * B;
+      rinvs += (size_t)jslots[blockIdx.y] * nb;
+    }
   } else {
     int i = rows ? rows[blockIdx.y] : k + 1 + blockIdx.y;
     tik = tile_index(i, k, NT);
@@ -949,14 +963,15 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   return EMU_OK;
 }
 
-emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs) {
+emu_status launch_trsm64_jobs(emu_ctx *ctx, double *t64, int nb, const int2 *d_jobs, int njobs, const double *Ls,
+                              const double *rinvs, const int *d_jslots) {
   if (njobs <= 0) return EMU_OK;
   double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM64, njobs * nb3, 16.0 * njobs * nb * nb);
   size_t sm = (size_t)(T64_ROWS * (nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_trsm64_panel<<<dim3(nb / T64_ROWS, njobs), 128, sm, ctx->stream>>>(t64, nb, 0, 0, nullptr, ctx->d_status,
-                                                                      d_jobs);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_trsm64_panel<true><<<dim3(nb / T64_ROWS, njobs), 128, sm, ctx->stream>>>(t64, nb, 0, 0, nullptr, ctx->d_status,
+                                                                            d_jobs, Ls, rinvs, d_jslots);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -992,10 +1007,12 @@ emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const 
   return EMU_OK;
 }
 
-emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs) {
+emu_status launch_trsm64_prep(emu_ctx *ctx, const double *L, int nb, double *Ls, double *rinvs, const long *d_tiles,
+                              int n) {
   if (nb % B != 0) return EMU_EINVAL;
-  ProfScope ps(ctx, PROF_SPLIT, 0.0, 16.0 * (double)nb * B);
-  k_trsm64_prep<<<nb / B, B * B, 0, ctx->stream>>>(L, nb, Ls, rinvs, ctx->d_status);
+  if (n <= 0) return EMU_OK;
+  ProfScope ps(ctx, PROF_SPLIT, 0.0, 16.0 * n * (double)nb * B);
+  k_trsm64_prep<<<dim3(nb / B, n), B * B, 0, ctx->stream>>>(L, d_tiles, nb, Ls, rinvs, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -1007,9 +1024,9 @@ emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_row
   double nb3 = (double)A->nb * A->nb * A->nb;
   ProfScope ps(ctx, PROF_TRSM64, m * nb3, 16.0 * m * A->nb * A->nb);
   size_t sm = (size_t)(T64_ROWS * (A->nb + 1) + 32 * (T64_STRIP + 1)) * sizeof(double);
-  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_trsm64_panel<<<dim3(A->nb / T64_ROWS, m), 128, sm, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
-                                                                     ctx->d_status, nullptr, Ls, rinvs);
+  EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm64_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_trsm64_panel<false><<<dim3(A->nb / T64_ROWS, m), 128, sm, ctx->stream>>>(A->t64, A->nb, A->nt, k, d_rows,
+                                                                            ctx->d_status, nullptr, Ls, rinvs, nullptr);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
