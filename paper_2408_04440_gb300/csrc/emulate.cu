@@ -130,18 +130,8 @@ __global__ void k_cossin(int nphi, double *__restrict__ cs) {
 // extension g(t_{M-i}) = (-1)^m g(t_i) over M = 2 ntheta - 2 colatitudes,
 // Fourier coefficients K_q of g, and the contraction with
 // S_{l,m,q} = sum_q' c_{l,m,q'} I(q + q'), c the Fourier coefficients of the
-// extended Legendre factor and I(k) = int_0^pi e^{ikt} sin t dt.
-
-// I(k): 2/(1-k^2) for even k, 0 for odd k other than +-1, +-i pi/2 at k = +-1.
-__device__ inline void I_of(int k, double &re, double &im) {
-  if (k == 1 || k == -1) {
-    re = 0.0;
-    im = k * 1.5707963267948966;
-  } else {
-    re = (k & 1) ? 0.0 : 2.0 / (1.0 - (double)k * k);
-    im = 0.0;
-  }
-}
+// extended Legendre factor and I(k) = int_0^pi e^{ikt} sin t dt: 2/(1-k^2)
+// for even k, +-i pi/2 at k = +-1, and 0 for the other odd k.
 
 // C_m(t_i), S_m(t_i) = (2 pi / nphi) sum_j Z_ij {cos, sin}(m p_j): one CTA per
 // (ring, time), the ring in shared memory.  cs[(2m + {0,1}) * ntheta + i, t].
@@ -223,11 +213,21 @@ __global__ void k_sht_S(int L, int ntheta, const double *__restrict__ lam, const
   double *o = sq + (size_t)pair * 2 * Q;
   for (int q = threadIdx.x - (L - 1); q <= L - 1; q += blockDim.x) {
     double sr = 0.0, si = 0.0;
-    for (int q2 = -(L - 1); q2 <= L - 1; q2++) {
-      double ir, ii;
-      I_of(q + q2, ir, ii);
-      sr += cr[q2 + L - 1] * ir - ci[q2 + L - 1] * ii;
-      si += cr[q2 + L - 1] * ii + ci[q2 + L - 1] * ir;
+    // I(k) is real for even k, +-i pi/2 at k = +-1 and zero at the other odd
+    // k: the even k first (q2 of q's parity), then the two imaginary terms
+    for (int q2 = -(L - 1) + ((q - (L - 1)) & 1); q2 <= L - 1; q2 += 2) {
+      const int k = q + q2;
+      const double ir = 2.0 / (1.0 - (double)k * k);
+      sr = fma(cr[q2 + L - 1], ir, sr);
+      si = fma(ci[q2 + L - 1], ir, si);
+    }
+    for (int sgn1 = -1; sgn1 <= 1; sgn1 += 2) {
+      const int q2 = sgn1 - q;
+      if (q2 >= -(L - 1) && q2 <= L - 1) {
+        const double ii = sgn1 * 1.5707963267948966;
+        sr = fma(-ci[q2 + L - 1], ii, sr);
+        si = fma(cr[q2 + L - 1], ii, si);
+      }
     }
     o[q + L - 1] = sr;
     o[Q + q + L - 1] = si;
