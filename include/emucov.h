@@ -207,7 +207,8 @@ emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda,
  * vector per column (m = R (T - P) in the paper); read only during the call.
  * The paper adds the perturbation when m < n; pass nugget_rel = 0 for none.
  * The lower tiles are formed on the tensor cores with FP64 accuracy (exact
- * digit products of the rows, FP64 accumulation), then scaled; the result is
+ * digit products of the rows, accumulated exactly in fixed point and rounded
+ * once to FP64), then scaled; the result is
  * a matrix in the state emu_cov_build leaves (tiles, tile norms, ||U||_F).
  * nb must be a multiple of 256.  EMU_EINVAL on bad arguments, EMU_ENOMEM if
  * the tile arena does not fit, EMU_ETIMEOUT if a bounded device wait expired. */
