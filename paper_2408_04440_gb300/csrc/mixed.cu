@@ -170,9 +170,11 @@ __global__ void __launch_bounds__(1024)
                                           __NV_E4M3);
 }
 
-// FP32 panel TRSM for the low-precision tiles of column k:
-// L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy of the
-// FP64 L_kk, written back to the master and, split, to the operand arena.
+// SIMT FP32 panel TRSM for the low-precision tiles of column k, used where
+// the tensor-core TRSM (trsm_tc.cu) does not apply (nb - 64 > 512 TMEM
+// columns): L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy
+// of the FP64 L_kk, written back to the master and, split, to the operand
+// arena.
 // One CTA per (row block, tile); warp w owns rows w + NW*q, a lane owns one
 // column of the current 32-column block cb.  L_kk streams through shared
 // memory as 32x32 chunks (rows of block cb, columns of block c <= cb) in a
@@ -850,7 +852,8 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_panel<4, 1, TS_NBUF_CRIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm4));
 
-  // TRSM of the listed rows of panel k (FP64 rows on the FP64 pipe, then split)
+  // TRSM of the listed rows of panel k: FP64 rows on the FP64 pipe, then split;
+  // low-class rows on the tensor cores (trsm_tc.cu), else the SIMT kernel
   auto quantize = [&](int q0, int nq) -> emu_status {
     if (nq <= 0) return EMU_OK;
     ProfScope ps(ctx, PROF_SPLIT, 0.0, 3.0 * nq * te);
