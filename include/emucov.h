@@ -363,13 +363,17 @@ emu_status emu_batch_release(emu_ctx *ctx);
  * Scratch: the correlation and scale tables live in a fixed 1 MiB file-scope
  * device array instead of allocated memory, which bounds L to 128 (n <= 16384);
  * a larger L returns EMU_ENOMEM.  Every device that loads the library holds
- * the array until the process exits.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array: calls whose work
- * overlaps on the GPU (different streams, no ordering between them) race and
- * may produce wrong values.  No cudaMalloc, cudaFree or allocating library
- * routine is called.  Returns EMU_EINVAL for bad arguments, EMU_ECUDA for a
- * launch failure. */
+ * the array until the process exits.  Each call on a stream that is not being
+ * captured looks up the array's device address on the current device
+ * (cudaGetSymbolAddress), so a device reset between calls is harmless; a call
+ * on a capturing stream reuses the address of the last uncaptured call on that
+ * device, so make at least one uncaptured call first, and none after a device
+ * reset until an uncaptured one has run.  All calls share the one array: calls
+ * whose work overlaps on the GPU (different streams, no ordering between them)
+ * race and may produce wrong values.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  Returns EMU_EINVAL for bad arguments, EMU_ECUDA
+ * for a launch failure or for a CUDA error already pending on the calling
+ * thread (checked before any launch and left in place for the caller). */
 emu_status emu_cov_build_dense_noalloc(int L, double beta, double sigma_exp,
                                        double nugget_rel, double *dS, long ld,
                                        void *stream);

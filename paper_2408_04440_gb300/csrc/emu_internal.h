@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -145,6 +146,17 @@ emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what);
     cudaError_t _e = cudaGetLastError();                                    \
     if (_e != cudaSuccess) return emu_cuda_fail((ctx), _e, "kernel launch"); \
   } while (0)
+
+// Kernel attributes belong to the device's context: raise a kernel's dynamic
+// shared-memory limit once per device (bit `device` of `done`), from any
+// thread.  Devices beyond 63 set it on every call.
+inline cudaError_t smem_limit_once(std::atomic<uint64_t> &done, int device, const void *func, int bytes) {
+  uint64_t bit = (device >= 0 && device < 64) ? (1ull << device) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // ------------------------------------------------------------- batches
 // One covariance of a batch (batch.cu): its tiles, rows and covariance tables

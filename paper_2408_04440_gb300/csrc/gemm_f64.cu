@@ -524,14 +524,9 @@ emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, cons
                   double *out64, int ldo, int max_ctas) {
   if (nitems <= 0) return EMU_OK;
   if (nb % BK != 0) return EMU_EINVAL;
-  static bool attr_done = false;
-  if (!attr_done) {
-    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm64<TC64_SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_BYTES));
-    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm64<TC64_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_BYTES));
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_sub{0}, attr_add{0};
+  EMU_CUDA_TRY(ctx, smem_limit_once(attr_sub, ctx->device, (const void *)k_tc_gemm64<TC64_SUB>, SMEM_BYTES));
+  EMU_CUDA_TRY(ctx, smem_limit_once(attr_add, ctx->device, (const void *)k_tc_gemm64<TC64_ADD>, SMEM_BYTES));
   int grid = nitems < max_ctas ? nitems : max_ctas;
   if (mode == TC64_SUB)
     k_tc_gemm64<TC64_SUB><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(a, b, d_items, nitems, d_segs, nb, a_plane,

@@ -402,11 +402,8 @@ emu_status make_map_f32(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64
 emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
                   int ksteps, int mode, float *out32, double *out64, int ldo, int max_ctas) {
   if (nitems <= 0) return EMU_OK;
-  static bool attr_done = false;
-  if (!attr_done) {
-    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  EMU_CUDA_TRY(ctx, smem_limit_once(attr_done, ctx->device, (const void *)k_tc_gemm, SMEM_BYTES));
   int grid = nitems < max_ctas ? nitems : max_ctas;
   k_tc_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(ops, d_items, nitems, d_segs, ksteps, mode, out32,
                                                          out64, ldo, ctx->d_status);

@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(1024)
 }
 
 // SIMT FP32 panel TRSM for the low-precision tiles of column k, used where
-// the tensor-core TRSM (trsm_tc.cu) does not apply (nb - 64 > 512 TMEM
-// columns): L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy
+// trsm_tc::supports(nb) is false (nb not a multiple of the tensor-core
+// TRSM's 128-row block, or nb - 64 > 512 TMEM columns): L_ik = A_ik L_kk^{-T} from the FP32 master A_ik and an FP32 copy
 // of the FP64 L_kk, written back to the master and, split, to the operand
 // arena.
 // One CTA per (row block, tile); warp w owns rows w + NW*q, a lane owns one
@@ -588,8 +588,9 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
         sp.i_n[g]++;
         sp.flops[g] += f;
-        // in BF16-product units: a TF32 product runs at half the BF16 rate
-        sp.mma[g] += f * (cc == EMU_CLASS_FP32 ? 6.0 : t32 ? 2.0 : 1.0);
+        // in BF16-product units: a TF32 product runs at half the BF16 rate,
+        // an E4M3 product (kind::f8f6f4) at twice it
+        sp.mma[g] += f * (cc == EMU_CLASS_FP32 ? 6.0 : t32 ? 2.0 : f8 ? 0.5 : 1.0);
       }
   };
   auto add_row = [&](int k, int i, int &n64, int &n32) {

@@ -25,7 +25,9 @@ __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 // Host-side record of the array's device address, per device.  In host code
 // the symbol name is only a stand-in, so the address comes from
-// cudaGetSymbolAddress with that device current.
+// cudaGetSymbolAddress with that device current.  It is looked up again on
+// every call whose stream is not being captured (the module may sit at a new
+// address after a device reset); a captured call uses the last address seen.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double *g_noalloc_ptr[kMaxDevices] = {};
@@ -79,13 +81,15 @@ __global__ void k_noalloc_dense(int L, long n, const double *__restrict__ sigma,
   }
 }
 
-// Device address of the scratch array on the current device (set up once).
-emu_status noalloc_scratch(double **out) {
+// Device address of the scratch array on the current device.
+emu_status noalloc_scratch(cudaStream_t st, double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EMU_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return EMU_EINVAL;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return EMU_ECUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return EMU_ECUDA;
     g_noalloc_ptr[dev] = static_cast<double *>(p);
@@ -100,10 +104,13 @@ extern "C" emu_status emu_cov_build_dense_noalloc(int L, double beta, double sig
                                                   double *dS, long ld, void *stream) {
   if (!dS || L < 1 || !(beta > 0.0) || !(nugget_rel >= 0.0) || ld < (long)L * L) return EMU_EINVAL;
   if (L > kNoAllocMaxL) return EMU_ENOMEM;  // tables would not fit the fixed scratch array
-  double *scratch = nullptr;
-  emu_status s = noalloc_scratch(&scratch);
-  if (s != EMU_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // an error already pending on this thread is not this call's: report it
+  // before launching anything, and leave it for the caller to read
+  if (cudaPeekAtLastError() != cudaSuccess) return EMU_ECUDA;
+  double *scratch = nullptr;
+  emu_status s = noalloc_scratch(st, &scratch);
+  if (s != EMU_OK) return s;
   size_t ntab = (size_t)(2 * L - 1) * (4 * L - 3);
   double *rho = scratch, *sigma = scratch + ntab, *nug = scratch + ntab + L;
   // every table entry used below is rewritten by this call before it is read

@@ -472,11 +472,8 @@ emu_status launch(emu_ctx *ctx, const CUtensorMap &lmap, const CUtensorMap &opma
                   int nb, int NT, int k, const int *d_rows, const int2 *d_jobs, int n) {
   if (n <= 0) return EMU_OK;
   if (!supports(nb)) return EMU_EINVAL;
-  static bool attr_done = false;
-  if (!attr_done) {
-    EMU_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr_done = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  EMU_CUDA_TRY(ctx, smem_limit_once(attr_done, ctx->device, (const void *)k_trsm32_tc, SMEM_BYTES));
   const double nb3 = (double)nb * nb * nb;
   ProfScope ps(ctx, PROF_TRSM32, n * nb3, 14.0 * n * (double)nb * nb, 6.0 * n * (nb3 - (double)nb * nb * W));
   k_trsm32_tc<<<dim3(nb / RB, n), NTHREADS, SMEM_BYTES, ctx->stream>>>(lmap, opmap, lkk0, t32, nb, NT, k, d_rows,

@@ -153,6 +153,36 @@ def test_covariance_limits_and_definiteness():
     assert lam.min() >= 1e-8 * (1 - 1e-6)
 
 
+@pytest.mark.parametrize("L,beta,sigma_exp,nugget", [
+    (5, 2.0, 1.5, 1e-8),
+    (16, 8.0, 1.5, 1e-8),
+    (33, 12.0, 1.5, 1e-8),
+    # growing sigma_l: the largest diagonal entry is the last degree's, not
+    # sigma_0's, so the nugget's max-diagonal rule is exercised off l = 0
+    (9, 3.0, -0.75, 1e-3),
+])
+def test_cov_rows_equals_rows_of_full_build(L, beta, sigma_exp, nugget):
+    """The row generator (used as the expected value at sizes where the full
+    matrix does not fit) is the full build's rows bit for bit: same entries,
+    same nugget, same index decode (Modeling the Temporal Dependence...: the
+    covariance and its diagonal perturbation)."""
+    n = L * L
+    S = O.cov_build(L, beta, sigma_exp=sigma_exp, nugget_rel=nugget)
+    rows = {0, n - 1, n // 2, n // 3 + 1}
+    rows |= {l * l + l for l in range(L)}          # m = 0 of every degree
+    rows |= {l * l for l in range(L)}              # m = -l
+    rows |= {l * l + 2 * l for l in range(L)}      # m = +l
+    rows = np.array(sorted(rows), dtype=np.int64)
+    R = O.cov_rows(L, beta, rows, sigma_exp=sigma_exp, nugget_rel=nugget)
+    assert R.shape == (len(rows), n)
+    assert np.array_equal(R, S[rows, :])
+    # every row carries the nugget on its diagonal entry and nowhere else
+    dmax = max((1.0 + l) ** (-2 * sigma_exp) for l in range(L))
+    for q, i in enumerate(rows):
+        l = int(math.isqrt(int(i)))
+        assert abs(R[q, i] - ((1.0 + l) ** (-2 * sigma_exp) + nugget * dmax)) <= 4e-16 * R[q, i]
+
+
 def test_tile_norms_against_numpy():
     S = O.cov_build(10, 3.0)  # n = 100, ragged with nb = 32
     nb = 32
