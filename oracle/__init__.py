@@ -68,6 +68,9 @@ def _declare(L):
     L.orc_precision_map_band.argtypes = [i, i, d, u8p]
     L.orc_cov_from_residuals.argtypes = [i, lg, dp, lg, d, dp]
     L.orc_var_recursion.argtypes = [i, i, dp, lg, dp, i, dp, lg]
+    L.orc_mean_trend.argtypes = [lg, d, d, d, d, d, i, dp, dp, dp]
+    L.orc_mean_trend.restype = d
+    L.orc_emulate_grid.argtypes = [lg, i, dp, lg, dp, lg, i, d, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, lg]
     L.orc_real_sh.argtypes = [i, i, d, d]
     L.orc_real_sh.restype = d
     L.orc_isht.argtypes = [i, i, dp, lg, i, i, dp, lg]
@@ -171,6 +174,32 @@ def var_recursion(Xi, Phi):
     F = np.zeros((n, T), dtype=np.float64, order="F")
     lib().orc_var_recursion(n, T, _dp(Xi), n, _dp(Ph), P, _dp(F), n)
     return F
+
+
+def mean_trend(t: int, tau: float, b0: float, b1: float, b2: float, rho: float, a, b, x) -> float:
+    """m_t at one grid point (Eq. decouple's trend): a, b the K harmonic amplitudes, x the forcing x[0..Y]."""
+    K = len(a)
+    a = np.ascontiguousarray(list(a) + [0.0], dtype=np.float64)  # never empty
+    b = np.ascontiguousarray(list(b) + [0.0], dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_mean_trend(t, tau, b0, b1, b2, rho, K, _dp(a), _dp(b), _dp(x))
+
+
+def emulate_grid(Zs, E, tau: float, b0, b1, b2, rho, A, B, x, sigma, v):
+    """y_t(g) = m_t(g) + sigma(g) (Zs_t(g) + v(g) E_t(g)) for t = 1..T (columns); Zs, E are G x T; A, B are K x G."""
+    Zs = np.asfortranarray(Zs, dtype=np.float64)
+    E = np.asfortranarray(E, dtype=np.float64)
+    G, T = Zs.shape
+    A = np.asfortranarray(A, dtype=np.float64).reshape(-1, G, order="F")
+    B = np.asfortranarray(B, dtype=np.float64).reshape(-1, G, order="F")
+    K = A.shape[0]
+    if K == 0:
+        A = B = np.zeros((1, G), order="F")
+    vec = [np.ascontiguousarray(q, dtype=np.float64) for q in (b0, b1, b2, rho, x, sigma, v)]
+    Y = np.zeros((G, T), dtype=np.float64, order="F")
+    lib().orc_emulate_grid(G, T, _dp(Zs), G, _dp(E), G, K, tau, _dp(vec[0]), _dp(vec[1]), _dp(vec[2]),
+                           _dp(vec[3]), _dp(A), _dp(B), _dp(vec[4]), _dp(vec[5]), _dp(vec[6]), _dp(Y), G)
+    return Y
 
 
 def real_sh(l: int, m: int, theta: float, phi: float) -> float:

@@ -205,6 +205,51 @@ void orc_var_recursion(int n, int T, const double *xi, long ldxi, const double *
     }
 }
 
+/* Mean trend of the decoupled model (Eq. decouple and the distributed-lag
+ * trend of "Climate Emulator Design -- Formulation") at one grid point and
+ * time step t >= 1:
+ *   m_t = b0 + b1 x_y + b2 (1 - rho) sum_{s>=1} rho^(s-1) x_(y-s)
+ *         + sum_{k=1..K} { a_k cos(2 pi t k / tau) + b_k sin(2 pi t k / tau) },
+ * y = ceil(t / tau).  The forcing trajectory is x[0..nyears]; every year
+ * before the first (index <= 0) carries x[0], so the lag terms with y - s <= 0
+ * sum in closed form to rho^(y-1) x[0] / (1 - rho) and the infinite sum is
+ *   (1 - rho) sum_{s=1..y-1} rho^(s-1) x[y-s] + rho^(y-1) x[0].
+ * a and b hold the K harmonic amplitudes of this grid point. */
+double orc_mean_trend(long t, double tau, double b0, double b1, double b2, double rho, int K, const double *a,
+                      const double *b, const double *x) {
+  const double pi = 3.14159265358979323846;
+  long y = (long)ceil((double)t / tau);
+  double lag = 0.0;
+  for (long s = 1; s <= y - 1; s++) lag += pow(rho, (double)(s - 1)) * x[y - s];
+  lag = (1.0 - rho) * lag + pow(rho, (double)(y - 1)) * x[0];
+  double m = b0 + b1 * x[y] + b2 * lag;
+  for (int k = 1; k <= K; k++) {
+    double w = 2.0 * pi * (double)t * (double)k / tau;
+    m += a[k - 1] * cos(w) + b[k - 1] * sin(w);
+  }
+  return m;
+}
+
+/* Emulations on the grid ("Generating Emulations" and Eq. decouple): for grid
+ * point g and time step t = 1..T (column t-1),
+ *   Z_t(g) = Zs_t(g) + v(g) e_t(g)          (the nugget eps_t ~ N(0, v^2))
+ *   y_t(g) = m_t(g) + sigma(g) Z_t(g),
+ * Zs the inverse SHT of the coefficients (G x T, ld ldz), e the standard
+ * normals of the nugget (G x T, ld lde; an input, drawn by the caller),
+ * per-point trend parameters b0, b1, b2, rho (length G) and amplitudes
+ * a, bh (K x G, amplitude k-1 of point g at [k-1 + g K]). */
+void orc_emulate_grid(long G, int T, const double *Zs, long ldz, const double *e, long lde, int K, double tau,
+                      const double *b0, const double *b1, const double *b2, const double *rho, const double *a,
+                      const double *bh, const double *x, const double *sigma, const double *v, double *Y,
+                      long ldy) {
+  for (long g = 0; g < G; g++)
+    for (int t = 1; t <= T; t++) {
+      double m = orc_mean_trend(t, tau, b0[g], b1[g], b2[g], rho[g], K, a + g * K, bh + g * K, x);
+      double Z = Zs[g + (long)(t - 1) * ldz] + v[g] * e[g + (long)(t - 1) * lde];
+      Y[g + (long)(t - 1) * ldy] = m + sigma[g] * Z;
+    }
+}
+
 /* Real orthonormal spherical harmonic of degree l, order m (|m| <= l) at
  * colatitude theta, longitude phi ("Spherical Harmonic Transform": the
  * orthonormal Y_lm, real form): N_l|m| P_l^|m|(cos theta) times 1 (m = 0),

@@ -67,6 +67,12 @@ int orc_precision_map_band(int NT, int band, double sp_frac, unsigned char *cls)
 void orc_cov_from_residuals(int n, long m, const double *Xi, long ld, double nugget_rel, double *U);
 void orc_var_recursion(int n, int T, const double *xi, long ldxi, const double *phi, int P, double *f, long ldf);
 double orc_real_sh(int l, int m, double theta, double phi);
+double orc_mean_trend(long t, double tau, double b0, double b1, double b2, double rho, int K, const double *a,
+                      const double *b, const double *x);
+void orc_emulate_grid(long G, int T, const double *Zs, long ldz, const double *e, long lde, int K, double tau,
+                      const double *b0, const double *b1, const double *b2, const double *rho, const double *a,
+                      const double *bh, const double *x, const double *sigma, const double *v, double *Y,
+                      long ldy);
 void orc_isht(int L, int T, const double *F, long ldf, int ntheta, int nphi, double *Z, long ldz);
 void orc_sht(int L, int T, const double *Z, long ldz, int ntheta, int nphi, double *F, long ldf);
 void orc_I_pub(int k, double *re, double *im);

@@ -476,3 +476,74 @@ def test_blocked_steps_compose():
     for k in range(4):
         assert O.lib().orc_potrf_blocked_steps(200, 64, O._dp(A2), 200, k, k + 1) == 0
     assert np.array_equal(np.tril(A2), A1)
+
+
+# ------------------------------------------- mean trend and grid emulations
+def test_mean_trend_closed_forms():
+    """Eq. decouple's trend m_t: lag weights (1 - rho) rho^(s-1) and the
+    harmonic terms, checked on cases whose value is known without the sum."""
+    x = np.array([0.5, 1.0, 2.0, 4.0, 8.0, 16.0])
+    # rho = 0: only the previous year's forcing carries the lag slope
+    for t, tau in [(1, 12.0), (13, 12.0), (30, 12.0), (5, 1.0)]:
+        y = math.ceil(t / tau)
+        want = 0.3 + 2.0 * x[y] + 5.0 * x[y - 1]
+        assert O.mean_trend(t, tau, 0.3, 2.0, 5.0, 0.0, [], [], x) == pytest.approx(want, rel=1e-15)
+    # the lag weights sum to one: a constant forcing c gives b0 + (b1 + b2) c for any rho
+    c = np.full(9, 3.25)
+    for rho in (0.0, 0.3, 0.9, 1.0):
+        for t in (1, 7, 40):
+            got = O.mean_trend(t, 5.0, 1.0, 0.5, 2.0, rho, [], [], c)
+            assert got == pytest.approx(1.0 + 2.5 * 3.25, rel=1e-14)
+    # an impulse in year j reaches year y with weight (1 - rho) rho^(y - j - 1)
+    imp = np.zeros(12)
+    imp[4] = 1.0
+    rho = 0.6
+    for y in range(1, 12):
+        want = 0.0 if y <= 4 else (1 - rho) * rho ** (y - 5)
+        if y == 4:
+            want = 0.0  # the current year's forcing has slope b1 = 0 here
+        assert O.mean_trend(y, 1.0, 0.0, 0.0, 1.0, rho, [], [], imp) == pytest.approx(want, abs=1e-16)
+    # years before the trajectory carry x[0]: at y = 1 the lag term is x[0], whatever rho
+    assert O.mean_trend(1, 12.0, 0.0, 0.0, 1.0, 0.7, [], [], x) == pytest.approx(x[0], rel=1e-15)
+    # rho = 1 keeps the pre-trajectory level for ever
+    assert O.mean_trend(50, 12.0, 0.0, 0.0, 1.0, 1.0, [], [], x) == pytest.approx(x[0], rel=1e-15)
+    # harmonics with tau = 12: a_1 cos(2 pi t / 12) + b_2 sin(4 pi t / 12)
+    z = np.zeros(3)
+    for t, want in [(3, 0.0 + math.sin(math.pi)), (6, -1.0 + 0.0), (12, 1.0), (1, math.cos(math.pi / 6) + math.sin(math.pi / 3))]:
+        got = O.mean_trend(t, 12.0, 0.0, 0.0, 0.0, 0.0, [1.0, 0.0], [0.0, 1.0], z)
+        assert abs(got - want) < 1e-14
+    # a full period of any harmonic sums to zero
+    tot = sum(O.mean_trend(t, 12.0, 0.0, 0.0, 0.0, 0.0, [0.7, -0.2, 1.3], [0.4, 0.9, -0.6], z) for t in range(1, 13))
+    assert abs(tot) < 1e-13
+
+
+def test_emulate_grid_pins():
+    """Eq. decouple with the nugget of "Generating Emulations":
+    y = m + sigma (Zs + v e)."""
+    rng = np.random.default_rng(5)
+    G, T, K = 7, 30, 2
+    Zs = rng.standard_normal((G, T))
+    E = rng.standard_normal((G, T))
+    zero, one = np.zeros(G), np.ones(G)
+    x = rng.standard_normal(4)
+    AB0 = np.zeros((K, G))
+    # no trend, unit scale, no nugget: the synthesis itself, bit for bit
+    Y = O.emulate_grid(Zs, E, 12.0, zero, zero, zero, zero, AB0, AB0, x, one, zero)
+    assert np.array_equal(Y, Zs)
+    # no trend, Zs = 0: the nugget scaled by sigma v, exactly
+    sig, v = np.full(G, 2.0), np.full(G, 3.0)
+    Y = O.emulate_grid(np.zeros((G, T)), E, 12.0, zero, zero, zero, zero, AB0, AB0, x, sig, v)
+    assert np.array_equal(Y, 6.0 * E)
+    # full model: each entry equals the single-point trend plus the scaled stochastic part
+    b0, b1, b2 = rng.standard_normal(G), rng.standard_normal(G), rng.standard_normal(G)
+    rho = rng.uniform(0, 1, G)
+    A, B = rng.standard_normal((K, G)), rng.standard_normal((K, G))
+    sig, v = rng.uniform(0.5, 2, G), rng.uniform(0, 0.3, G)
+    Y = O.emulate_grid(Zs, E, 12.0, b0, b1, b2, rho, A, B, x, sig, v)
+    for g in (0, 3, 6):
+        for t in (1, 12, 13, 30):
+            m = O.mean_trend(t, 12.0, b0[g], b1[g], b2[g], rho[g], A[:, g], B[:, g], x)
+            assert Y[g, t - 1] == m + sig[g] * (Zs[g, t - 1] + v[g] * E[g, t - 1])
+    # the trend is shared by all ensembles: two draws differ only by sigma (Zs + v e)
+    Y2 = O.emulate_grid(Zs + 1.0, E, 12.0, b0, b1, b2, rho, A, B, x, sig, v)
+    assert np.allclose(Y2 - Y, np.outer(sig, np.ones(T)), rtol=0, atol=1e-13)
