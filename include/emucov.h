@@ -179,6 +179,18 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
 emu_status emu_trace_enable(emu_ctx *ctx, int on);
 emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records,
                           size_t *n_records);
+/* Test hook of the timeout path (failure detection; the paper has no
+ * counterpart).  Every wait of the dataflow FP64 diagonal POTRF on another
+ * task's flag is bounded; this sets that bound, in SM clock cycles, for every
+ * context on ctx's device (wait_cycles <= 0 restores the default, about 2 s)
+ * and names one flag that every such wait treats as never set:
+ * withhold_index = r * (nb / 16) + c for the 16 x 16 block (r, c) of a
+ * diagonal tile, -1 for none.  A factor that meets a withheld flag returns
+ * EMU_ETIMEOUT once the bound runs out: the waiting kernel records the
+ * timeout in the status word and returns, the others see the status and
+ * leave, and the context stays usable.  Synchronises the device.  For tests
+ * of failure detection only. */
+emu_status emu_test_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index);
 emu_status emu_prof_read(emu_ctx *ctx, int group, int *launches, double *total_ms,
                          double *flops, double *bytes, double *mma_flops);
 
@@ -250,6 +262,40 @@ emu_status emu_isht(emu_ctx *ctx, const double *dF, int L, int T, long ldf, int 
  * beyond it. */
 emu_status emu_sht(emu_ctx *ctx, const double *dZ, int ntheta, int nphi, int T, long ldz, int L, double *dF,
                    long ldf);
+
+/* emu_emulate_grid: the last step of "Generating Emulations" and Eq.
+ * decouple ("Climate Emulator Design -- Formulation"): from the synthesis Zs
+ * of emu_isht (G grid points x T time steps, ld ldz, device) it forms, for
+ * t = 1..T (column t-1),
+ *   Z_t(g) = Zs_t(g) + v(g) e_t(g)        (the nugget eps_t ~ N(0, v^2)),
+ *   y_t(g) = m_t(g) + sigma(g) Z_t(g),
+ * into Y (G x T, ld ldy, device; Y == Zs with ldy == ldz is allowed, other
+ * overlaps are not).  e_t(g) is the library's standard normal of row g and
+ * column t-1 for (seed, stream_id) (the generator of emu_sample).  The mean
+ * trend is the paper's distributed-lag model of the forcing x plus K
+ * harmonics:
+ *   m_t = beta0 + beta1 x_y + beta2 (1 - rho) sum_{s>=1} rho^(s-1) x_(y-s)
+ *         + sum_{k=1..K} a_k cos(2 pi t k / tau) + b_k sin(2 pi t k / tau),
+ * y = ceil(t / tau), with every year before the trajectory taken at x[0].
+ * Per-point parameters beta0, beta1, beta2, rho (rho in [0, 1]), sigma and v
+ * are device arrays of length G; a and b are K x G (amplitude k of point g at
+ * [k-1 + g K]).  The paper fits these parameters to data; the library takes
+ * them as given.  Returns EMU_EINVAL for bad arguments (K > 8, tau <= 0,
+ * nyears < ceil(T / tau), G > 2^31 - 1) and synchronises the stream. */
+typedef struct emu_trend {
+  int K;                 /* harmonic pairs, 0..8 */
+  double tau;            /* period of the harmonics in time steps (12, 365, 8760 ...) */
+  const double *beta0;   /* intercept, G */
+  const double *beta1;   /* slope on the current forcing, G */
+  const double *beta2;   /* slope on the lagged forcing, G */
+  const double *rho;     /* lag decay in [0, 1], G */
+  const double *a, *b;   /* K x G cosine / sine amplitudes; NULL when K = 0 */
+  const double *x;       /* forcing x[0..nyears] (device); x[0] also stands for earlier years */
+  int nyears;
+} emu_trend;
+emu_status emu_emulate_grid(emu_ctx *ctx, const double *dZs, long G, int T, long ldz, const emu_trend *m,
+                            const double *dsigma, const double *dv, uint64_t seed, uint32_t stream_id, double *dY,
+                            long ldy);
 
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);

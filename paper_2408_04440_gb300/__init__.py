@@ -34,8 +34,8 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_cov_build", "emu_mat_import",
-    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_cov_build", "emu_mat_import",
+    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
     "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
@@ -55,6 +55,12 @@ class EmuError(RuntimeError):
 class emu_cov_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("beta", ctypes.c_double), ("sigma_exp", ctypes.c_double),
                 ("nugget_rel", ctypes.c_double)]
+
+
+class emu_trend(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("tau", ctypes.c_double), ("beta0", ctypes.c_void_p),
+                ("beta1", ctypes.c_void_p), ("beta2", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("nyears", ctypes.c_int)]
 
 
 class emu_mp_opts(ctypes.Structure):
@@ -97,6 +103,7 @@ def load() -> ctypes.CDLL:
     dpp = ctypes.POINTER(ctypes.c_double)
     L.emu_prof_enable.argtypes = [vp, i]
     L.emu_trace_enable.argtypes = [vp, i]
+    L.emu_test_wait_hook.argtypes = [vp, ctypes.c_longlong, i]
     L.emu_prof_timeline.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_trace_read.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_prof_read.argtypes = [vp, i, ctypes.POINTER(i), dpp, dpp, dpp, dpp]
@@ -107,6 +114,8 @@ def load() -> ctypes.CDLL:
     L.emu_var_recursion.argtypes = [vp, vp, i, i, lg, vp, i, vp, lg]
     L.emu_isht.argtypes = [vp, vp, i, i, lg, i, i, vp, lg]
     L.emu_sht.argtypes = [vp, vp, i, i, i, lg, i, vp, lg]
+    L.emu_emulate_grid.argtypes = [vp, vp, lg, i, lg, ctypes.POINTER(emu_trend), vp, vp, ctypes.c_uint64,
+                                   ctypes.c_uint32, vp, lg]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
     L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
@@ -122,8 +131,8 @@ def load() -> ctypes.CDLL:
                                          ctypes.c_uint64, vp, vp, ctypes.POINTER(emu_factor_info)]
     L.emu_batch_release.argtypes = [vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
-                 "emu_trace_enable", "emu_trace_read", "emu_prof_timeline",
-                 "emu_mat_import_host", "emu_cov_build", "emu_mat_import",
+                 "emu_trace_enable", "emu_trace_read", "emu_prof_timeline", "emu_test_wait_hook",
+                 "emu_mat_import_host", "emu_cov_build", "emu_mat_import", "emu_emulate_grid",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
                  "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
                  "emu_cov_build_dense_noalloc", "emu_batch_potrf_sample", "emu_batch_release"):
@@ -196,6 +205,10 @@ class Context:
             self._check(self.lib.emu_prof_timeline(self.h, ctypes.c_void_p(out.ctypes.data), n.value,
                                                    ctypes.byref(n)), "emu_prof_timeline")
         return out
+
+    def test_wait_hook(self, wait_cycles: int = 0, withhold_index: int = -1):
+        """Bound of the diagonal POTRF's flag waits (cycles, 0 = default) and one flag index they never see set."""
+        self._check(self.lib.emu_test_wait_hook(self.h, int(wait_cycles), int(withhold_index)), "emu_test_wait_hook")
 
     def trace_enable(self, on: bool = True):
         self._check(self.lib.emu_trace_enable(self.h, int(on)), "emu_trace_enable")
@@ -333,6 +346,27 @@ def emu_sht(ctx: Context, Z, L: int, ntheta: int, nphi: int):
     ctx._check(ctx.lib.emu_sht(ctx.h, ctypes.c_void_p(_ptr(Z)), ntheta, nphi, T, Z.stride(1) if T > 1 else npts, L,
                                ctypes.c_void_p(_ptr(F)), L * L), "emu_sht")
     return F
+
+
+def emu_emulate_grid(ctx: Context, Zs, tau: float, beta0, beta1, beta2, rho, A, B, x, sigma, v, seed: int,
+                     stream_id: int = 0, out=None):
+    """Emulations y_t = m_t + sigma (Zs_t + v e_t), t = 1..T (Eq. decouple): Zs (G x T) from emu_isht,
+    per-point beta0/beta1/beta2/rho/sigma/v (G), harmonic amplitudes A, B (K x G, or None), forcing x[0..Y];
+    all float64 CUDA tensors.  Returns Y (G x T, column-major)."""
+    G, T = Zs.shape
+    Zs = Zs if Zs.stride(0) == 1 else Zs.t().contiguous().t()
+    K = 0 if A is None else A.shape[0]
+    vecs = [q.contiguous() for q in (beta0, beta1, beta2, rho, sigma, v, x)]
+    AB = [q.t().contiguous() for q in (A, B)] if K else [None, None]  # amplitude k of point g at [k + g K]
+    m = emu_trend(K, tau, _ptr(vecs[0]), _ptr(vecs[1]), _ptr(vecs[2]), _ptr(vecs[3]),
+                  _ptr(AB[0]) if K else None, _ptr(AB[1]) if K else None, _ptr(vecs[6]), x.numel() - 1)
+    Y = _colmajor_empty(G, T, ctx.device) if out is None else out
+    ctx._check(ctx.lib.emu_emulate_grid(ctx.h, ctypes.c_void_p(_ptr(Zs)), G, T, Zs.stride(1) if T > 1 else G,
+                                        ctypes.byref(m), ctypes.c_void_p(_ptr(vecs[4])),
+                                        ctypes.c_void_p(_ptr(vecs[5])), seed, stream_id,
+                                        ctypes.c_void_p(_ptr(Y)), Y.stride(1) if T > 1 else G),
+               "emu_emulate_grid")
+    return Y
 
 
 def emu_mat_import_host(ctx: Context, A, nb: int) -> Mat:

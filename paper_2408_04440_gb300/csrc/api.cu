@@ -204,6 +204,12 @@ emu_status emu_trace_enable(emu_ctx *ctx, int on) {
   return EMU_OK;
 }
 
+emu_status emu_test_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index) {
+  if (!ctx) return EMU_EINVAL;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return set_dag_wait_hook(ctx, wait_cycles, withhold_index);
+}
+
 emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records, size_t *n_records) {
   if (!ctx || !n_records) return EMU_EINVAL;
   *n_records = ctx->trace_records;

@@ -183,6 +183,8 @@ inline double band_sp_frac(const emu_mp_opts *o) { return o->sp_frac == 0.0 ? 0.
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
+// Test hook of the timeout path (emu_test_wait_hook).
+emu_status set_dag_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index);
 // d_rows: device list of the tile rows i > k to solve (nullptr: all of them)
 emu_status launch_trsm64_panel(emu_ctx *ctx, emu_mat *A, int k, const int *d_rows = nullptr, int nrows = 0,
                                const double *Ls = nullptr, const double *rinvs = nullptr);

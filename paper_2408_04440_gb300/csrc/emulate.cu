@@ -10,9 +10,14 @@
 //   Y_l,-m = sqrt(2) N_lm P_l^m(cos t) sin(m p),  N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!,
 // P_l^m with the Condon-Shortley phase (-1)^m.  Grid: colatitudes
 // t_i = pi i / (ntheta - 1) (poles included), longitudes p_j = 2 pi j / nphi.
+//
+// The last step builds the emulations of Eq. decouple from the synthesis Zs:
+// y_t = m_t + sigma (Zs_t + v e_t), with the nugget e drawn by the library's
+// Philox generator and the distributed-lag mean trend m_t.
 #include <cmath>
 
 #include "emu_internal.h"
+#include "rng.cuh"
 
 namespace {
 
@@ -265,7 +270,77 @@ __global__ void k_sht_contract(int L, int T, int ntheta, const double *__restric
   }
 }
 
+// Emulations of Eq. decouple on the grid, for time steps t = 1..T (column
+// t-1): y_t(g) = m_t(g) + sigma(g) (Zs_t(g) + v(g) e_t(g)), e_t(g) the
+// library's normal of row g, column t-1 (Philox stream `sid`), and
+//   m_t = b0 + b1 x_y + b2 D_y + sum_k a_k cos(2 pi t k / tau) + b_k sin(2 pi t k / tau),
+// y = ceil(t / tau), D_y = (1 - rho) sum_{s>=1} rho^(s-1) x_(y-s) with the
+// years before the trajectory at x[0]: D_1 = x[0], D_(y+1) = (1 - rho) x_y + rho D_y.
+// One thread per grid-point pair (the two rows of one Box-Muller pair) and
+// chunk of kEmTC time steps (blockIdx.y); the harmonic values of the chunk
+// are shared by the block.  HBM-bound: 16 bytes in, 8 out per entry.
+constexpr int kMaxK = 8, kEmTC = 32;
+struct TrendDev {
+  int K, nyears;
+  double tau;
+  const double *b0, *b1, *b2, *rho, *a, *b, *x;
+};
+__global__ void __launch_bounds__(128) k_emulate_grid(const double *__restrict__ Zs, long G, int T, long ldz,
+                                                      TrendDev m, const double *__restrict__ sigma,
+                                                      const double *__restrict__ v, uint64_t seed, uint32_t sid,
+                                                      double *Y, long ldy) {
+  __shared__ double cs[kMaxK][kEmTC], sn[kMaxK][kEmTC];
+  const int t0 = blockIdx.y * kEmTC + 1;
+  const int nt = min(kEmTC, T - t0 + 1);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int q = threadIdx.x; q < m.K * kEmTC; q += blockDim.x) {
+    int k = q / kEmTC + 1, tt = q % kEmTC;
+    sincos(two_pi * (double)(t0 + tt) * (double)k / m.tau, &sn[k - 1][tt], &cs[k - 1][tt]);
+  }
+  __syncthreads();
+  const long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (2 * p >= G) return;
+  const int npt = (2 * p + 1 < G) ? 2 : 1;
+  double b0[2], b1[2], b2[2], rho[2], sg[2], vv[2], D[2], a[2][kMaxK], b[2][kMaxK];
+  long yc = (long)ceil((double)t0 / m.tau);  // forcing year of the chunk's first step
+  for (int u = 0; u < 2; u++) {
+    long g = 2 * p + (u < npt ? u : 0);
+    b0[u] = m.b0[g];
+    b1[u] = m.b1[g];
+    b2[u] = m.b2[g];
+    rho[u] = m.rho[g];
+    sg[u] = sigma[g];
+    vv[u] = v[g];
+#pragma unroll
+    for (int k = 0; k < kMaxK; k++) {
+      a[u][k] = k < m.K ? m.a[k + g * m.K] : 0.0;
+      b[u][k] = k < m.K ? m.b[k + g * m.K] : 0.0;
+    }
+    D[u] = m.x[0];
+    for (long yy = 1; yy < yc; yy++) D[u] = (1.0 - rho[u]) * m.x[yy] + rho[u] * D[u];
+  }
+  for (int tt = 0; tt < nt; tt++) {
+    const int t = t0 + tt;
+    const long y = (long)ceil((double)t / m.tau);
+    while (yc < y) {
+      for (int u = 0; u < 2; u++) D[u] = (1.0 - rho[u]) * m.x[yc] + rho[u] * D[u];
+      yc++;
+    }
+    double e[2] = {0.0, 0.0};
+    normal_pair(seed, sid, p, t - 1, (int)(G < 0x7fffffff ? G : 0x7fffffff), e);
+    const double xy = m.x[y];
+    for (int u = 0; u < npt; u++) {
+      double mt = b0[u] + b1[u] * xy + b2[u] * D[u];
+      for (int k = 0; k < m.K; k++) mt += a[u][k] * cs[k][tt] + b[u][k] * sn[k][tt];
+      const long g = 2 * p + u;
+      const double z = Zs[g + (long)(t - 1) * ldz] + vv[u] * e[u];
+      Y[g + (long)(t - 1) * ldy] = mt + sg[u] * z;
+    }
+  }
+}
+
 }  // namespace
+
 
 extern "C" {
 
@@ -353,6 +428,31 @@ emu_status emu_sht(emu_ctx *ctx, const double *dZ, int ntheta, int nphi, int T, 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaErrorInvalidValue) return EMU_EINVAL;
   if (e != cudaSuccess) return emu_cuda_fail(ctx, e, "sht");
+  return EMU_OK;
+}
+
+
+emu_status emu_emulate_grid(emu_ctx *ctx, const double *dZs, long G, int T, long ldz, const emu_trend *m,
+                            const double *dsigma, const double *dv, uint64_t seed, uint32_t stream_id, double *dY,
+                            long ldy) {
+  if (!ctx || !dZs || !dY || !m || !dsigma || !dv || G < 1 || T < 1 || ldz < G || ldy < G) return EMU_EINVAL;
+  if (!(m->tau > 0.0) || m->K < 0 || m->K > kMaxK || (m->K > 0 && (!m->a || !m->b)) || !m->beta0 || !m->beta1 ||
+      !m->beta2 || !m->rho || !m->x || m->nyears < 0)
+    return EMU_EINVAL;
+  if ((long)std::ceil((double)T / m->tau) > (long)m->nyears) return EMU_EINVAL;  // forcing too short
+  if (G > 0x7fffffffL) return EMU_EINVAL;  // Philox row counter of one column
+  if (dY == dZs && ldy != ldz) return EMU_EINVAL;
+  if (dY != dZs && (dY < dZs + G + (long)(T - 1) * ldz && dZs < dY + G + (long)(T - 1) * ldy)) return EMU_EINVAL;
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  TrendDev td{m->K, m->nyears, m->tau, m->beta0, m->beta1, m->beta2, m->rho, m->a, m->b, m->x};
+  long pairs = (G + 1) / 2;
+  dim3 grid((unsigned)((pairs + 127) / 128), (unsigned)((T + kEmTC - 1) / kEmTC));
+  {
+    ProfScope ps(ctx, PROF_RNG, 0.0, 24.0 * (double)G * T);
+    k_emulate_grid<<<grid, 128, 0, ctx->stream>>>(dZs, G, T, ldz, td, dsigma, dv, seed, stream_id, dY, ldy);
+    EMU_LAUNCHED(ctx);
+  }
+  EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return EMU_OK;
 }
 

@@ -60,15 +60,21 @@ __device__ inline uint64_t gtimer() {
   return t;
 }
 
+// Test hooks of the timeout path (emu_test_wait_hook): the bound of the flag
+// waits, and one flag index that every wait treats as never set.
+__constant__ long long c_dag_wait_cycles = kDagWaitCycles;
+__constant__ int c_dag_withhold = -1;
+
 // Thread 0 waits until state[idx] >= v (or failure / timeout).
 __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
   volatile const int *p = state + idx;
-  if (*p >= v) return true;
-  const long long t0 = clock64();
+  const bool held = idx == c_dag_withhold;
+  if (!held && *p >= v) return true;
+  const long long t0 = clock64(), limit = c_dag_wait_cycles;
   while (true) {
-    if (*p >= v) return true;
+    if (!held && *p >= v) return true;
     if (*((volatile const int *)st) != DEV_OK) return false;
-    if (clock64() - t0 > kDagWaitCycles) {
+    if (clock64() - t0 > limit) {
       if (atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 2;
       return false;
     }
@@ -906,6 +912,15 @@ __global__ void k_solve_diag(const double *__restrict__ t64, int nb, int NT, int
 static size_t dag_ws_ints(int nbb, int nbat) {
   size_t n = 1 + (size_t)nbat * nbb * nbb;
   return (n + 1) & ~(size_t)1;
+}
+
+emu_status set_dag_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index) {
+  const long long cyc = wait_cycles > 0 ? wait_cycles : kDagWaitCycles;
+  const int idx = withhold_index >= 0 ? withhold_index : -1;
+  EMU_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  EMU_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_dag_wait_cycles, &cyc, sizeof(cyc)));
+  EMU_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_dag_withhold, &idx, sizeof(idx)));
+  return EMU_OK;
 }
 
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {

@@ -221,6 +221,104 @@ def test_emulation_chain_from_the_mixed_factor(E, ctx):
     assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()
 
 
+def _trend_inputs(G, T, K, tau, seed):
+    rng = np.random.default_rng(seed)
+    ny = -(-T // int(tau)) if float(tau).is_integer() else int(np.ceil(T / tau))
+    return dict(beta0=rng.standard_normal(G), beta1=rng.standard_normal(G), beta2=rng.standard_normal(G),
+                rho=np.concatenate([[0.0, 1.0], rng.uniform(0, 1, G - 2)]), A=rng.standard_normal((K, G)),
+                B=rng.standard_normal((K, G)), x=rng.standard_normal(ny + 1), sigma=rng.uniform(0.5, 2.0, G),
+                v=rng.uniform(0.0, 0.5, G))
+
+
+@pytest.mark.parametrize("G,T,K,tau", [(1175, 70, 3, 12.0), (33, 5, 0, 1.0), (64, 40, 8, 7.5)])
+def test_emulate_grid_matches_oracle(E, ctx, G, T, K, tau):
+    # y = m + sigma (Zs + v e), Eq. decouple: trend, nugget and scale against
+    # the oracle, given the oracle's own Philox normals for the nugget
+    import torch
+
+    p = _trend_inputs(G, T, K, tau, seed=G + T)
+    Zs = np.random.default_rng(1).standard_normal((G, T))
+    seed, sid = 77, 5
+    cu = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in p.items()}
+    Y = _np(E.emu_emulate_grid(ctx, torch.from_numpy(np.asfortranarray(Zs)).cuda(), tau, cu["beta0"],
+                               cu["beta1"], cu["beta2"], cu["rho"], cu["A"] if K else None,
+                               cu["B"] if K else None, cu["x"], cu["sigma"], cu["v"], seed, sid))
+    e = O.normal_matrix(seed, sid, G, T)
+    Yo = O.emulate_grid(Zs, e, tau, p["beta0"], p["beta1"], p["beta2"], p["rho"], p["A"], p["B"], p["x"],
+                        p["sigma"], p["v"])
+    assert np.abs(Y - Yo).max() <= 1e-12 * np.abs(Yo).max()
+    # zero nugget and trend, unit scale: the synthesis itself, bit for bit
+    z = torch.zeros(G, dtype=torch.float64, device="cuda")
+    Y1 = _np(E.emu_emulate_grid(ctx, torch.from_numpy(np.asfortranarray(Zs)).cuda(), tau, z, z, z, z, None, None,
+                                cu["x"], torch.ones_like(z), z, seed, sid))
+    assert np.array_equal(Y1, Zs)
+
+
+def test_emulation_chain_to_the_grid_fields(E, ctx):
+    # the whole of "Generating Emulations": draws of the mixed factor, VAR(2),
+    # synthesis, nugget, trend and scale, against the oracle's chain on the
+    # same draws and nugget normals
+    import torch
+
+    Lb, nb, beta, T, tau, K = 12, 128, 4.0, 36, 12.0, 2
+    A = E.emu_cov_build(ctx, Lb, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=1e-8)
+    Xi = E.emu_sample(ctx, A, T, seed=9)
+    A.free()
+    n = Lb * Lb
+    Ph = torch.from_numpy(np.asfortranarray(np.tile([0.6, 0.2], (n, 1)))).cuda()
+    nt, nph = Lb + 1, 2 * Lb
+    G = nt * nph
+    Zs = E.emu_isht(ctx, E.emu_var_recursion(ctx, Xi, Ph), Lb, nt, nph)
+    p = _trend_inputs(G, T, K, tau, seed=3)
+    cu = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in p.items()}
+    Y = _np(E.emu_emulate_grid(ctx, Zs, tau, cu["beta0"], cu["beta1"], cu["beta2"], cu["rho"], cu["A"], cu["B"],
+                               cu["x"], cu["sigma"], cu["v"], 11, 2))
+    Zo = O.isht(O.var_recursion(_np(Xi), _np(Ph)), Lb, nt, nph)
+    Yo = O.emulate_grid(Zo, O.normal_matrix(11, 2, G, T), tau, p["beta0"], p["beta1"], p["beta2"], p["rho"],
+                        p["A"], p["B"], p["x"], p["sigma"], p["v"])
+    assert np.abs(Y - Yo).max() <= 1e-12 * np.abs(Yo).max()
+
+
+def test_emulate_grid_rejects_a_short_forcing(E, ctx):
+    import torch
+
+    G, T = 10, 25
+    z = torch.zeros(G, dtype=torch.float64, device="cuda")
+    x = torch.zeros(2, dtype=torch.float64, device="cuda")  # one year; 25 monthly steps need three
+    Zs = torch.zeros((T, G), dtype=torch.float64, device="cuda").t()
+    with pytest.raises(E.EmuError):
+        E.emu_emulate_grid(ctx, Zs, 12.0, z, z, z, z, None, None, x, z, z, 1)
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-8])
+def test_withheld_flag_times_out_and_the_context_recovers(E, ctx, eps):
+    # failure detection without a GPU fault: a flag that nothing sets (the
+    # test hook withholds block (1, 0)'s flag of the diagonal POTRF) and a wait
+    # bound of 2e5 cycles; the factor reports EMU_ETIMEOUT, every kernel
+    # returns, and the same context then factors correctly
+    L, nb, beta = 16, 128, 4.0
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    ctx.test_wait_hook(wait_cycles=200000, withhold_index=1 * (nb // 16) + 0)
+    try:
+        with pytest.raises(E.EmuError) as err:
+            E.emu_potrf_mp(ctx, A, eps=eps)
+        assert err.value.status == E.EMU_ETIMEOUT
+    finally:
+        ctx.test_wait_hook(0, -1)
+    A.free()
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=eps)
+    Lg = _np(E.emu_mat_export(ctx, A))
+    A.free()
+    S = O.cov_build(L, beta)
+    if eps == 0.0:
+        Lo, _ = O.potrf_blocked(S, nb)
+        assert np.linalg.norm(Lg - Lo) / np.linalg.norm(Lo) <= 1e-12
+    else:
+        assert np.linalg.norm(Lg @ Lg.T - S) / np.linalg.norm(S) <= eps
+
+
 @pytest.mark.parametrize("bad", [1, 70, 199])
 def test_not_positive_definite_reports_pivot(E, ctx, bad):
     import torch
