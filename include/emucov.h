@@ -297,6 +297,40 @@ emu_status emu_emulate_grid(emu_ctx *ctx, const double *dZs, long G, int T, long
                             const double *dsigma, const double *dv, uint64_t seed, uint32_t stream_id, double *dY,
                             long ldy);
 
+/* -------------------------------------------- class-format tile storage */
+/* emu_cov_build_classfmt: the synthetic covariance of emu_cov_build stored
+ * tile by tile in the format of its precision class ("Mixed-Precision
+ * Computation Innovations": tiles allocated at the size of their precision),
+ * for covariances whose FP64 lower triangle does not fit the device.  The
+ * precision map is computed first from a norm pass that stores nothing (the
+ * rule of emu_mp_opts o; every diagonal tile FP64; TF32 is stored as FP32),
+ * then every tile is computed again and stored: FP64 8 bytes, FP32 4, BF16 2
+ * (nearest), E4M3 1 byte per entry (codes of v * s, s = 2^floor(log2(448 /
+ * sqrt(max S_rr max S_cc))) over the tile's rows and columns, so that no
+ * Schur complement entry saturates).  nb must be a multiple of 256.
+ * emu_potrf_mp factors such a matrix in place with this map (o is not read):
+ * each trailing update is accumulated in FP32 on the tensor cores and the tile
+ * is re-rounded to its format; each panel is decoded, solved as in the
+ * FP32-master factor, rounded back to its format, and the operands of later
+ * updates are made from the rounded values.  emu_sample, emu_mat_export,
+ * emu_mat_tile_info and emu_backward_error_est accept it; emu_potrs,
+ * emu_solve_refine and emu_mat_clone return EMU_ESTATE.  Device memory:
+ * about the stored bytes plus, while factoring, a ring of three panels
+ * (FP64 + FP32 + three BF16 pieces + FP8 + eight digit planes per tile of a
+ * tile column, about 35 bytes per element of nb x NT rows). */
+emu_status emu_cov_build_classfmt(emu_ctx *ctx, const emu_cov_params *p, int nb, const emu_mp_opts *o,
+                                  emu_mat **out);
+/* emu_backward_error_est: an estimate of ||L L^T - S||_F / ||S||_F for a
+ * factor L of the covariance with parameters p, without S in memory (the
+ * randomised trace estimate of Hutchinson): with nprobes Gaussian probe
+ * columns G (the library's normals for `seed`, stream id 7),
+ * ||(L L^T - S) G||_F^2 / nprobes estimates ||L L^T - S||_F^2; L^T G and
+ * L (L^T G) are computed from the stored tiles and S G from p (the entries
+ * regenerated as the builder computes them), all in FP64.  Any storage.
+ * Relative spread of the estimate about sqrt(2 / nprobes). */
+emu_status emu_backward_error_est(emu_ctx *ctx, const emu_mat *L, const emu_cov_params *p, int nprobes,
+                                  uint64_t seed, double *est);
+
 /* Deep copy (device to device), e.g. to keep S for emu_solve_refine. */
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out);
 /* Write the matrix as a dense FP64 lower triangle (upper set to 0) into dOut

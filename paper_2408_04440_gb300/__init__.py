@@ -35,7 +35,8 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
     "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_cov_build", "emu_mat_import",
-    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
+    "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_cov_build_classfmt",
+    "emu_backward_error_est", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
     "emu_batch_potrf_sample", "emu_batch_release", "emu_cov_build_dense_noalloc",
 )
@@ -114,6 +115,10 @@ def load() -> ctypes.CDLL:
     L.emu_var_recursion.argtypes = [vp, vp, i, i, lg, vp, i, vp, lg]
     L.emu_isht.argtypes = [vp, vp, i, i, lg, i, i, vp, lg]
     L.emu_sht.argtypes = [vp, vp, i, i, i, lg, i, vp, lg]
+    L.emu_cov_build_classfmt.argtypes = [vp, ctypes.POINTER(emu_cov_params), i, ctypes.POINTER(emu_mp_opts),
+                                         ctypes.POINTER(vp)]
+    L.emu_backward_error_est.argtypes = [vp, vp, ctypes.POINTER(emu_cov_params), i, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_double)]
     L.emu_emulate_grid.argtypes = [vp, vp, lg, i, lg, ctypes.POINTER(emu_trend), vp, vp, ctypes.c_uint64,
                                    ctypes.c_uint32, vp, lg]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
@@ -133,6 +138,7 @@ def load() -> ctypes.CDLL:
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
                  "emu_trace_enable", "emu_trace_read", "emu_prof_timeline", "emu_test_wait_hook",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import", "emu_emulate_grid",
+                 "emu_cov_build_classfmt", "emu_backward_error_est",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
                  "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
                  "emu_cov_build_dense_noalloc", "emu_batch_potrf_sample", "emu_batch_release"):
@@ -274,6 +280,29 @@ def emu_cov_build(ctx: Context, L: int, beta: float, nb: int, sigma_exp: float =
     h = ctypes.c_void_p()
     ctx._check(ctx.lib.emu_cov_build(ctx.h, ctypes.byref(p), nb, ctypes.byref(h)), "emu_cov_build")
     return Mat(ctx, h)
+
+
+def emu_cov_build_classfmt(ctx: Context, L: int, beta: float, nb: int, eps: float = 1e-6, prec_mask: int = 0b11011,
+                           band: int = MAP_NORM, sigma_exp: float = 1.5, nugget_rel: float = 1e-8, u=None,
+                           sp_frac: float = 0.0) -> Mat:
+    """The covariance stored tile by tile in the format of its precision class (map of the norm rule at eps, or
+    a band map); factor it with emu_potrf_mp."""
+    p = emu_cov_params(L, beta, sigma_exp, nugget_rel)
+    o = mp_opts(eps, prec_mask, True, u, band, sp_frac)
+    h = ctypes.c_void_p()
+    ctx._check(ctx.lib.emu_cov_build_classfmt(ctx.h, ctypes.byref(p), nb, ctypes.byref(o), ctypes.byref(h)),
+               "emu_cov_build_classfmt")
+    return Mat(ctx, h)
+
+
+def emu_backward_error_est(ctx: Context, A: Mat, L: int, beta: float, nprobes: int = 32, seed: int = 0,
+                           sigma_exp: float = 1.5, nugget_rel: float = 1e-8) -> float:
+    """Hutchinson estimate of ||A A^T - S||_F / ||S||_F for the factor A of the covariance (L, beta, ...)."""
+    p = emu_cov_params(L, beta, sigma_exp, nugget_rel)
+    est = ctypes.c_double()
+    ctx._check(ctx.lib.emu_backward_error_est(ctx.h, A.h, ctypes.byref(p), nprobes, seed, ctypes.byref(est)),
+               "emu_backward_error_est")
+    return est.value
 
 
 def emu_mat_import(ctx: Context, A, nb: int) -> Mat:

@@ -236,7 +236,7 @@ emu_status emu_prof_read(emu_ctx *ctx, int group, int *launches, double *total_m
 }  // extern "C"
 
 // ---------------------------------------------------------------- matrices
-static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out) {
+static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out, bool arena64 = true) {
   if (!ctx || !out || n <= 0 || nb < 64 || nb > 2048 || (nb % 64) != 0)
     return fail_msg(ctx, EMU_EINVAL, "need n > 0 and nb a multiple of 64 in [64, 2048]");
   *out = nullptr;
@@ -250,7 +250,7 @@ static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out) {
   A->ntiles = tile_count(A->nt);
   A->tile_elems = (size_t)nb * nb;
   A->nchunk = nb / 32;
-  size_t bytes64 = (size_t)A->ntiles * A->tile_elems * sizeof(double);
+  size_t bytes64 = arena64 ? (size_t)A->ntiles * A->tile_elems * sizeof(double) : 0;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   if (bytes64 + (64u << 20) > free_b) {
@@ -258,7 +258,7 @@ static emu_status mat_alloc(emu_ctx *ctx, int n, int nb, emu_mat **out) {
     return fail_msg(ctx, EMU_ENOMEM, "FP64 tile arena does not fit in free device memory");
   }
   cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaMallocAsync(&A->t64, bytes64, s);
+  cudaError_t e = arena64 ? cudaMallocAsync(&A->t64, bytes64, s) : cudaSuccess;
   if (e == cudaSuccess) e = cudaMallocAsync(&A->d_partial, (size_t)A->ntiles * A->nchunk * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMallocAsync(&A->d_tnorm, (size_t)A->ntiles * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMallocAsync(&A->d_frob, sizeof(double), s);
@@ -289,9 +289,39 @@ emu_status emu_mat_free(emu_mat *A) {
   for (void *b : bufs)
     if (b) cudaFreeAsync(b, s);
   mixed_mat_release(A);
+  classfmt_release(A);
   delete[] A->h_cls;
   delete A;
   return EMU_OK;
+}
+
+emu_status emu_cov_build_classfmt(emu_ctx *ctx, const emu_cov_params *p, int nb, const emu_mp_opts *o,
+                                  emu_mat **out) {
+  if (!ctx || !p || !o || !out) return EMU_EINVAL;
+  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel >= 0.0))
+    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, nugget_rel >= 0");
+  if (o->band < EMU_MAP_NORM || o->band > EMU_MAP_DP_HP) return fail_msg(ctx, EMU_EINVAL, "unknown precision map");
+  if (nb % 256 != 0) return fail_msg(ctx, EMU_EINVAL, "class-format storage needs nb a multiple of 256");
+  emu_mat *A = nullptr;
+  emu_status s = mat_alloc(ctx, p->L * p->L, nb, &A, false);
+  if (s != EMU_OK) return s;
+  s = classfmt_build(ctx, A, p, o);
+  if (s != EMU_OK) {
+    emu_mat_free(A);
+    return s;
+  }
+  *out = A;
+  return EMU_OK;
+}
+
+emu_status emu_backward_error_est(emu_ctx *ctx, const emu_mat *L, const emu_cov_params *p, int nprobes,
+                                  uint64_t seed, double *est) {
+  if (!ctx || !L || !p || !est || nprobes < 1) return EMU_EINVAL;
+  if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
+    return fail_msg(ctx, EMU_ESTATE, "the estimate needs a factored matrix");
+  if (p->L * p->L != L->n) return fail_msg(ctx, EMU_EINVAL, "the parameters' n = L^2 differs from the factor's");
+  EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return factor_backward_error_est(ctx, L, p, nprobes, seed, est);
 }
 
 emu_status emu_cov_build(emu_ctx *ctx, const emu_cov_params *p, int nb, emu_mat **out) {
@@ -464,6 +494,7 @@ emu_status emu_mat_import_host(emu_ctx *ctx, const double *hA, int n, long lda, 
 emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out) {
   if (!ctx || !A || !out) return EMU_EINVAL;
   if (A->state != MAT_COV) return fail_msg(ctx, EMU_ESTATE, "clone supports covariance matrices");
+  if (A->cs) return fail_msg(ctx, EMU_ESTATE, "clone supports FP64-tiled matrices");
   emu_mat *B = nullptr;
   emu_status s = mat_alloc(ctx, A->n, A->nb, &B);
   if (s != EMU_OK) return s;
@@ -487,6 +518,7 @@ emu_status emu_mat_clone(emu_ctx *ctx, const emu_mat *A, emu_mat **out) {
 
 emu_status emu_mat_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld) {
   if (!ctx || !A || !dOut || ld < A->n) return EMU_EINVAL;
+  if (A->cs) return classfmt_export(ctx, A, dOut, ld);
   return launch_export(ctx, A, dOut, ld);
 }
 
@@ -573,7 +605,10 @@ extern "C" emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *
   EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, ST_WORDS * sizeof(int), ctx->stream));
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   emu_status s;
-  if (mixed) {
+  if (A->cs) {
+    mixed = true;  // the precision map was fixed when the matrix was built
+    s = classfmt_factor(ctx, A);
+  } else if (mixed) {
     s = factor_mixed(ctx, A, o);
   } else {
     s = factor64(ctx, A);
@@ -593,7 +628,9 @@ extern "C" emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     info->ms = ms;
     double nb3 = (double)A->nb * A->nb * A->nb;
-    if (mixed) {
+    if (A->cs) {
+      classfmt_fill_info(A, info);
+    } else if (mixed) {
       mixed_fill_info(A, info);
     } else {
       info->tiles[EMU_CLASS_FP64] = (int)A->ntiles;
@@ -619,7 +656,9 @@ extern "C" emu_status emu_sample(emu_ctx *ctx, const emu_mat *L, int nsamples, u
   EMU_CUDA_TRY(ctx, cudaMallocAsync(&Z, (size_t)npad * nsamples * sizeof(double), ctx->stream));
   emu_status s = launch_normals(ctx, seed, stream_id, (int)npad, nsamples, Z, npad);
   if (s == EMU_OK) {
-    if (L->state == MAT_FACTOR64)
+    if (L->cs)
+      s = classfmt_sample(ctx, L, Z, npad, nsamples, dY, ldy);
+    else if (L->state == MAT_FACTOR64)
       s = launch_trmm64(ctx, L, Z, npad, nsamples, dY, ldy);
     else
       s = mixed_sample(ctx, L, Z, npad, nsamples, dY, ldy);
@@ -666,6 +705,7 @@ extern "C" emu_status emu_potrs(emu_ctx *ctx, const emu_mat *L, const double *dB
   if (!ctx || !L || !dB || !dX || nrhs < 0 || ldb < L->n || ldx < L->n) return EMU_EINVAL;
   if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
     return fail_msg(ctx, EMU_ESTATE, "solve needs a factored matrix");
+  if (L->cs) return fail_msg(ctx, EMU_ESTATE, "solves need the FP32-master storage (emu_cov_build)");
   if (nrhs == 0) return EMU_OK;
   EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   long npad = (long)L->nt * L->nb;
@@ -695,5 +735,6 @@ extern "C" emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu
     return fail_msg(ctx, EMU_ESTATE, "S must be the unfactored covariance with the factor's tiling");
   if (L->state != MAT_FACTOR64 && L->state != MAT_FACTOR_MIXED)
     return fail_msg(ctx, EMU_ESTATE, "refinement needs a factored matrix");
+  if (L->cs || S->cs) return fail_msg(ctx, EMU_ESTATE, "refinement needs the FP32-master storage (emu_cov_build)");
   return refine_solve(ctx, L, S, dB, ldb, dX, ldx, nrhs, tol, maxit, info);
 }

@@ -7,6 +7,9 @@
 // depends only on (l_i - l_j, m_i - m_j), so it is evaluated once per offset
 // into a table; every entry is then s(l_i) * s(l_j) * rho(dl, dm) -- the same
 // operations, in the same order, as evaluating the formula entry by entry.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include <algorithm>
 
 #include "emu_internal.h"
@@ -86,9 +89,11 @@ __device__ inline double block_sum(double v, double *sh) {
 // over the real (unpadded) entries of the full symmetric tile.
 // Chunk `chunk` (kChunk columns) of tile (ti, tj) of the covariance of
 // bandlimit L; returns this thread's sum of squares of the real entries.
-__device__ inline double cov_tile_chunk(int L, int n, int nb, int ti, int tj, int chunk,
-                                        const double *__restrict__ sigma, const double *__restrict__ rho,
-                                        double nug, double *__restrict__ tile) {
+// `store(r, c, v)` receives every entry of the chunk (the padded ones too).
+template <class Store>
+__device__ inline double cov_tile_chunk_t(int L, int n, int nb, int ti, int tj, int chunk,
+                                          const double *__restrict__ sigma, const double *__restrict__ rho,
+                                          double nug, const Store &store) {
   const int W = 4 * L - 3;
   // this thread's rows (r = threadIdx.x + k blockDim.x): degree, order and
   // sigma once per row; rho's index is then rbase - (l_j W + m_j) per entry
@@ -136,10 +141,40 @@ __device__ inline double cov_tile_chunk(int L, int n, int nb, int ti, int tj, in
       } else {
         v = (gi == gj) ? 1.0 : 0.0;
       }
-      tile[r + (size_t)c * nb] = v;
+      store(r, c, v);
     }
   }
   return ss;
+}
+
+struct StoreF64 {
+  double *tile;
+  int nb;
+  __device__ void operator()(int r, int c, double v) const { tile[r + (size_t)c * nb] = v; }
+};
+struct StoreNone {
+  __device__ void operator()(int, int, double) const {}
+};
+// Class-format storage: the entry rounded to the tile's class (nearest; E4M3
+// codes of v * s, saturating, s a power of two).
+struct StoreClass {
+  int cls, nb;
+  size_t base;
+  ClassArenas ar;
+  double s8;
+  __device__ void operator()(int r, int c, double v) const {
+    const size_t e = base + r + (size_t)c * nb;
+    if (cls == EMU_CLASS_FP64) ar.t64[e] = v;
+    else if (cls == EMU_CLASS_FP32) ar.t32[e] = (float)v;
+    else if (cls == EMU_CLASS_BF16) ar.t16[e] = __bfloat16_as_ushort(__double2bfloat16(v));
+    else ar.t8[e] = (uint8_t)__nv_cvt_double_to_fp8(v * s8, __NV_SATFINITE, __NV_E4M3);
+  }
+};
+
+__device__ inline double cov_tile_chunk(int L, int n, int nb, int ti, int tj, int chunk,
+                                        const double *__restrict__ sigma, const double *__restrict__ rho,
+                                        double nug, double *__restrict__ tile) {
+  return cov_tile_chunk_t(L, n, nb, ti, tj, chunk, sigma, rho, nug, StoreF64{tile, nb});
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -153,6 +188,31 @@ __global__ void __launch_bounds__(kThreads)
   double ss = cov_tile_chunk(L, n, nb, ti, tj, blockIdx.y, sigma, rho, *nugget, t64 + (size_t)t * nb * nb);
   double tot = block_sum(ss, sh);
   if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
+// Class format, pass 1: the norm partials only.  Pass 2 (classes known):
+// every tile stored in its class's arena.
+__global__ void __launch_bounds__(kThreads)
+    k_cov_norms(int L, int n, int nb, int NT, const double *__restrict__ sigma, const double *__restrict__ rho,
+                const double *__restrict__ nugget, double *__restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  double ss = cov_tile_chunk_t(L, n, nb, ti, tj, blockIdx.y, sigma, rho, *nugget, StoreNone{});
+  double tot = block_sum(ss, sh);
+  if (threadIdx.x == 0) partial[t * gridDim.y + blockIdx.y] = tot;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_cov_store_class(int L, int n, int nb, int NT, const double *__restrict__ sigma,
+                      const double *__restrict__ rho, const double *__restrict__ nugget, ClassArenas ar) {
+  long t = blockIdx.x;
+  int ti, tj;
+  tile_coords(t, NT, &ti, &tj);
+  const int c = ar.cls[t], sl = ar.slot[t];
+  StoreClass st{c, nb, (size_t)sl * nb * nb, ar, c == EMU_CLASS_E4M3 ? (double)ar.sc8[sl] : 1.0};
+  (void)cov_tile_chunk_t(L, n, nb, ti, tj, blockIdx.y, sigma, rho, *nugget, st);
 }
 
 // Batch: blockIdx.x = tile of the batch arena, tile_inst = its matrix.
@@ -445,6 +505,51 @@ emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p) {
   EMU_LAUNCHED(ctx);
   EMU_CUDA_TRY(ctx, cudaFreeAsync(buf, ctx->stream));
   return launch_precision_map(ctx, A, 0.0, nullptr, 0u, 0, EMU_MAP_NORM, 0.0);
+}
+
+emu_status launch_cov_tables(emu_ctx *ctx, const emu_cov_params *p, double *tables) {
+  const int L = p->L;
+  const size_t ntab = (size_t)(2 * L - 1) * (4 * L - 3);
+  int blocks = (int)((ntab + 255) / 256);
+  if (blocks > 4 * ctx->sm_count) blocks = 4 * ctx->sm_count;
+  k_cov_tables<<<blocks, 256, 0, ctx->stream>>>(L, p->beta, p->sigma_exp, p->nugget_rel, tables + ntab, tables,
+                                               tables + ntab + L);
+  EMU_LAUNCHED(ctx);
+  return EMU_OK;
+}
+
+emu_status launch_cov_norms(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p) {
+  const int L = p->L;
+  const size_t ntab = (size_t)(2 * L - 1) * (4 * L - 3);
+  double *buf = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&buf, (ntab + L + 1) * sizeof(double), ctx->stream));
+  emu_status s = launch_cov_tables(ctx, p, buf);
+  if (s == EMU_OK) {
+    dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+    ProfScope ps(ctx, PROF_COV, 3.0 * A->ntiles * A->tile_elems, 0.0);
+    k_cov_norms<<<grid, kThreads, 0, ctx->stream>>>(L, A->n, A->nb, A->nt, buf + ntab, buf, buf + ntab + L,
+                                                   A->d_partial);
+    EMU_LAUNCHED(ctx);
+  }
+  cudaFreeAsync(buf, ctx->stream);
+  return s;
+}
+
+emu_status launch_cov_store_class(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p, const ClassArenas &ar) {
+  const int L = p->L;
+  const size_t ntab = (size_t)(2 * L - 1) * (4 * L - 3);
+  double *buf = nullptr;
+  EMU_CUDA_TRY(ctx, cudaMallocAsync(&buf, (ntab + L + 1) * sizeof(double), ctx->stream));
+  emu_status s = launch_cov_tables(ctx, p, buf);
+  if (s == EMU_OK) {
+    dim3 grid((unsigned)A->ntiles, A->nb / kChunk);
+    ProfScope ps(ctx, PROF_COV, 3.0 * A->ntiles * A->tile_elems, 0.0);
+    k_cov_store_class<<<grid, kThreads, 0, ctx->stream>>>(L, A->n, A->nb, A->nt, buf + ntab, buf, buf + ntab + L,
+                                                         ar);
+    EMU_LAUNCHED(ctx);
+  }
+  cudaFreeAsync(buf, ctx->stream);
+  return s;
 }
 
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda) {

@@ -108,6 +108,36 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// Class-format storage (classfmt.cu): every tile in the format of its
+// precision class, column-major nb x nb, in the arena of its class at index
+// slot[tile]; diagonal tiles are FP64.  E4M3 entries are codes q of the value
+// q / sc8[slot].
+struct ClassStore {
+  std::vector<unsigned char> cls;  // per tile (TF32 is stored as FP32)
+  std::vector<int> slot;           // per tile
+  int nslot[EMU_NCLASS] = {};
+  int *d_slot = nullptr;
+  double *t64 = nullptr;
+  float *t32 = nullptr;
+  uint16_t *t16 = nullptr;
+  uint8_t *t8 = nullptr;
+  float *sc8 = nullptr;
+  void *work = nullptr;            // factor plan (classfmt.cu)
+  bool samp_ready = false;         // sampler digit slices of the FP64 tiles made
+  uint16_t *samp_dig = nullptr;
+  int *samp_exp = nullptr;
+};
+// Device pointers of the class arenas, for the class-format covariance store.
+struct ClassArenas {
+  const int *slot;
+  const unsigned char *cls;
+  double *t64;
+  float *t32;
+  uint16_t *t16;
+  uint8_t *t8;
+  const float *sc8;
+};
+
 struct emu_mat {
   emu_ctx *ctx = nullptr;
   int n = 0, nb = 0, nt = 0;
@@ -130,6 +160,7 @@ struct emu_mat {
   float *scale_e4m3 = nullptr; // ntiles power-of-two scales of those copies
   float *op_tf32 = nullptr;     // ntiles * nb*nb TF32 copies (row-major), when TF32 tiles exist
   void *plan = nullptr;        // mixed-factor schedule (mixed.cu)
+  ClassStore *cs = nullptr;    // class-format storage (t64 / t32 / op unused)
 };
 
 // ------------------------------------------------------------- bookkeeping
@@ -172,6 +203,11 @@ struct BatchInst {
 // Kernel launch wrappers (defined in the .cu files that own the kernels).
 // cov.cu
 emu_status launch_cov_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
+// Class-format build (cov.cu): the norm partials without storing any tile;
+// then every tile stored in its class's arena.  Tables: rho, sigma, nugget.
+emu_status launch_cov_norms(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p);
+emu_status launch_cov_store_class(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p, const ClassArenas &ar);
+emu_status launch_cov_tables(emu_ctx *ctx, const emu_cov_params *p, double *tables);
 emu_status launch_import(emu_ctx *ctx, emu_mat *A, const double *dA, long lda);
 // Empirical covariance: scale the raw sums by 1/m, nugget, padding, norms (cov.cu).
 emu_status launch_emp_finish(emu_ctx *ctx, emu_mat *A, long m, double nugget_rel, unsigned long long *d_maxbits);
@@ -183,6 +219,8 @@ inline double band_sp_frac(const emu_mp_opts *o) { return o->sp_frac == 0.0 ? 0.
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
+// The same on the tile at D (nb x nb, column-major), step k (pivot columns k nb + ..).
+emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k);
 // Test hook of the timeout path (emu_test_wait_hook).
 emu_status set_dag_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index);
 // d_rows: device list of the tile rows i > k to solve (nullptr: all of them)

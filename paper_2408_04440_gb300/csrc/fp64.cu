@@ -924,7 +924,10 @@ emu_status set_dag_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_i
 }
 
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
-  int nb = A->nb, NT = A->nt;
+  return launch_potrf64_ptr(ctx, A->t64 + (size_t)tile_index(k, k, A->nt) * A->nb * A->nb, A->nb, k);
+}
+
+emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
   int nbb = nb / PB;
   if (ctx->dag_nbb != nbb) {
     std::vector<short4> tasks;
@@ -943,7 +946,6 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
     ctx->dag_ntasks = (int)tasks.size();
     ctx->dag_nbb = nbb;
   }
-  double *D = A->t64 + (size_t)tile_index(k, k, NT) * nb * nb;
   ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
   size_t state_bytes = (size_t)(1 + nbb * nbb) * sizeof(int);
   EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dag_ws, 0, state_bytes, ctx->stream));

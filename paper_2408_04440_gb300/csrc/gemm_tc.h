@@ -9,6 +9,9 @@
 // applies the epilogue:
 //   mode TC_SUB_F32: out32[off + r + c*ldo] -= acc   (trailing tile update)
 //   mode TC_ADD_F64: out64[off + r + c*ldo] += acc   (sampling, r/c bounded)
+//   mode TC_SUB_CLASS: out[off + r + c*ldo] -= acc in the format of the
+//     item's output class oc (FP32, BF16 rounded to nearest, or E4M3 codes
+//     of the value q / sc8[osc], saturating): class-format tile storage
 #pragma once
 #include <cuda.h>
 
@@ -22,7 +25,7 @@ constexpr int BK = 32;    // K per pipeline stage (BF16: 64 bytes, 64B swizzle)
 constexpr int STAGES = 3;
 constexpr int NPIECE = 3; // split pieces of an FP32-class operand
 
-enum { TC_SUB_F32 = 0, TC_ADD_F64 = 1 };
+enum { TC_SUB_F32 = 0, TC_ADD_F64 = 1, TC_SUB_CLASS = 2 };
 
 struct Seg {
   int ax, ay, ay_step;  // TMA coordinates of A piece 0 (x = K offset) and piece stride in rows
@@ -37,6 +40,16 @@ struct Item {
   long out_off;
   int rows_valid, cols_valid;  // TC_ADD_F64 only
   int sa, sb;                  // E4M3 items: tiles whose scales multiply A and B (else -1)
+  int oc = EMU_CLASS_FP32;     // TC_SUB_CLASS: output format
+  int osc = 0;                 // TC_SUB_CLASS, E4M3 output: index of its scale
+};
+
+// Output arenas of a TC_SUB_CLASS launch (element offsets out_off in each).
+struct Outputs {
+  float *f32;
+  uint16_t *bf16;
+  uint8_t *e8;
+  const float *sc8;
 };
 
 // Operand sources of a launch: BF16 pieces (A box 128 x 32, B box 256 x 32,
@@ -70,5 +83,8 @@ emu_status make_map_f32(emu_ctx *ctx, CUtensorMap *map, const void *base, uint64
 
 emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
                   int ksteps, int mode, float *out32, double *out64, int ldo, int max_ctas);
+// TC_SUB_CLASS: each item updates its tile in the format of its class.
+emu_status launch_class(emu_ctx *ctx, const Operands &ops, const Item *d_items, int nitems, const Seg *d_segs,
+                        int ksteps, const Outputs &outs, int ldo, int max_ctas);
 
 }  // namespace gemm_tc

@@ -778,7 +778,9 @@ constexpr int kReservedSMsFP64 = 32;
 
 // Internal streams of the mixed schedule (created once per context) and at
 // least `nev` ordering events.
-static emu_status sched_streams(emu_ctx *ctx, int nev) {
+int mixed_reserved_sms(bool fp64_near) { return fp64_near ? kReservedSMsFP64 : kReservedSMs; }
+
+emu_status mixed_sched_streams(emu_ctx *ctx, int nev) {
   if (!ctx->crit) {
     int least = 0, greatest = 0;
     EMU_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
@@ -841,7 +843,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   // for G1(k-1), which finished the update of its tile.
   cudaStream_t user = ctx->stream;
   const int EV = 5;  // per step: POTRF done, TRSM(k+1) done, TRSM rest done, G1 done, G2 done
-  if ((s = sched_streams(ctx, EV * NT + 2)) != EMU_OK) return s;
+  if ((s = mixed_sched_streams(ctx, EV * NT + 2)) != EMU_OK) return s;
   auto ev = [&](int k, int w) { return ctx->sched_ev[EV * k + w]; };
   enum { E_P = 0, E_T1 = 1, E_T = 2, E_G1 = 3, E_G2 = 4 };
   cudaEvent_t ev_start = ctx->sched_ev[EV * NT], ev_end = ctx->sched_ev[EV * NT + 1];

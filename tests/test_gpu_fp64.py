@@ -260,7 +260,7 @@ def test_emulation_chain_to_the_grid_fields(E, ctx):
     # same draws and nugget normals
     import torch
 
-    Lb, nb, beta, T, tau, K = 12, 128, 4.0, 36, 12.0, 2
+    Lb, nb, beta, T, tau, K = 12, 256, 4.0, 36, 12.0, 2
     A = E.emu_cov_build(ctx, Lb, beta, nb)
     E.emu_potrf_mp(ctx, A, eps=1e-8)
     Xi = E.emu_sample(ctx, A, T, seed=9)
@@ -297,7 +297,7 @@ def test_withheld_flag_times_out_and_the_context_recovers(E, ctx, eps):
     # test hook withholds block (1, 0)'s flag of the diagonal POTRF) and a wait
     # bound of 2e5 cycles; the factor reports EMU_ETIMEOUT, every kernel
     # returns, and the same context then factors correctly
-    L, nb, beta = 16, 128, 4.0
+    L, nb, beta = 32, 256, 4.0
     A = E.emu_cov_build(ctx, L, beta, nb)
     ctx.test_wait_hook(wait_cycles=200000, withhold_index=1 * (nb // 16) + 0)
     try:
