@@ -179,6 +179,23 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
 emu_status emu_trace_enable(emu_ctx *ctx, int on);
 emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records,
                           size_t *n_records);
+/* Schedule of the single-matrix mixed factor (FP32-master storage).  With
+ * use_graphs != 0 (the default) the launches after the precision map are
+ * recorded once into a CUDA graph over the factor's four streams and replayed
+ * while the map, the tiling and the arenas' addresses stay the same (one host
+ * launch per factor; profiling or tracing turns replay off).  With
+ * tuning != 0 (the default) the first factors of each (NT, nb, class map)
+ * each try one of four counts of SMs left free of the bulk trailing update
+ * (16/32, 8/16, 24/48, 32/64, without/with FP64-class panel work near), timed
+ * on the device; later factors use the fastest.  Every choice gives the same
+ * factor bit for bit. */
+emu_status emu_schedule(emu_ctx *ctx, int use_graphs, int tuning);
+/* The tuner's state for the last signature factored: choices timed so far
+ * (0..4), and the SMs left free without / with FP64-class panel work in the
+ * choice the next factor of that signature uses.  All 0 before any mixed
+ * factor. */
+emu_status emu_schedule_info(emu_ctx *ctx, int *tried, int *reserved, int *reserved_fp64);
+
 /* Test hook of the timeout path (failure detection; the paper has no
  * counterpart).  Every wait of the dataflow FP64 diagonal POTRF on another
  * task's flag is bounded; this sets that bound, in SM clock cycles, for every

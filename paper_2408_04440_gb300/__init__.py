@@ -34,7 +34,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_cov_build", "emu_mat_import",
+    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_schedule", "emu_schedule_info", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_cov_build_classfmt",
     "emu_backward_error_est", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
     L.emu_prof_enable.argtypes = [vp, i]
     L.emu_trace_enable.argtypes = [vp, i]
     L.emu_test_wait_hook.argtypes = [vp, ctypes.c_longlong, i]
+    L.emu_schedule.argtypes = [vp, i, i]
+    L.emu_schedule_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.emu_prof_timeline.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_trace_read.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_prof_read.argtypes = [vp, i, ctypes.POINTER(i), dpp, dpp, dpp, dpp]
@@ -137,6 +139,7 @@ def load() -> ctypes.CDLL:
     L.emu_batch_release.argtypes = [vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
                  "emu_trace_enable", "emu_trace_read", "emu_prof_timeline", "emu_test_wait_hook",
+                 "emu_schedule", "emu_schedule_info",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import", "emu_emulate_grid",
                  "emu_cov_build_classfmt", "emu_backward_error_est",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
@@ -211,6 +214,17 @@ class Context:
             self._check(self.lib.emu_prof_timeline(self.h, ctypes.c_void_p(out.ctypes.data), n.value,
                                                    ctypes.byref(n)), "emu_prof_timeline")
         return out
+
+    def schedule(self, graphs: bool = True, tuning: bool = True):
+        """Graph replay and reserved-SM tuning of the single-matrix mixed factor (both on by default)."""
+        self._check(self.lib.emu_schedule(self.h, int(graphs), int(tuning)), "emu_schedule")
+
+    def schedule_info(self):
+        """(choices timed, SMs left free, SMs left free near FP64-class panel work) of the tuner."""
+        t, r, r64 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.emu_schedule_info(self.h, ctypes.byref(t), ctypes.byref(r), ctypes.byref(r64)),
+                    "emu_schedule_info")
+        return t.value, r.value, r64.value
 
     def test_wait_hook(self, wait_cycles: int = 0, withhold_index: int = -1):
         """Bound of the diagonal POTRF's flag waits (cycles, 0 = default) and one flag index they never see set."""

@@ -204,6 +204,22 @@ emu_status emu_trace_enable(emu_ctx *ctx, int on) {
   return EMU_OK;
 }
 
+emu_status emu_schedule(emu_ctx *ctx, int use_graphs, int tuning) {
+  if (!ctx) return EMU_EINVAL;
+  mixed_set_schedule(ctx, use_graphs, tuning);
+  return EMU_OK;
+}
+
+emu_status emu_schedule_info(emu_ctx *ctx, int *tried, int *reserved, int *reserved_fp64) {
+  if (!ctx) return EMU_EINVAL;
+  int t = 0, r = 0, r64 = 0;
+  if (mixed_tuned_choice(ctx, &t, &r, &r64) < 0) t = r = r64 = 0;
+  if (tried) *tried = t;
+  if (reserved) *reserved = r;
+  if (reserved_fp64) *reserved_fp64 = r64;
+  return EMU_OK;
+}
+
 emu_status emu_test_wait_hook(emu_ctx *ctx, long long wait_cycles, int withhold_index) {
   if (!ctx) return EMU_EINVAL;
   EMU_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -617,6 +633,7 @@ extern "C" emu_status emu_potrf_mp(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
   int pivot = 0;
   s = collect_status(ctx, &pivot);
+  mixed_tune_record(ctx, s == EMU_OK);  // the device time of the schedule choice, for the tuner
   A->state = mixed ? MAT_FACTOR_MIXED : MAT_FACTOR64;
   if (info) {
     memset(info, 0, sizeof *info);

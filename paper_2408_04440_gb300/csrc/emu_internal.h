@@ -90,6 +90,8 @@ struct emu_ctx {
   int dag_ntasks = 0, dag_nbb = 0;
   // batched factor (batch.cu): arenas, plan and captured graph of the last batch
   void *batch = nullptr;
+  // single-matrix mixed factor (mixed.cu): captured graph, tuning table
+  void *mixed = nullptr;
   // optional device-side task trace of the dataflow POTRF
   bool trace_on = false;
   unsigned long long *trace_buf = nullptr;
@@ -219,6 +221,9 @@ inline double band_sp_frac(const emu_mp_opts *o) { return o->sp_frac == 0.0 ? 0.
 emu_status launch_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld);
 // fp64.cu
 emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k);
+// Task list and workspace of the dataflow POTRF for tile size nb (allocated on
+// first use; called before any stream capture).
+emu_status potrf_dag_prepare(emu_ctx *ctx, int nb);
 // The same on the tile at D (nb x nb, column-major), step k (pivot columns k nb + ..).
 emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k);
 // Test hook of the timeout path (emu_test_wait_hook).

@@ -927,7 +927,7 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
   return launch_potrf64_ptr(ctx, A->t64 + (size_t)tile_index(k, k, A->nt) * A->nb * A->nb, A->nb, k);
 }
 
-emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
+emu_status potrf_dag_prepare(emu_ctx *ctx, int nb) {
   int nbb = nb / PB;
   if (ctx->dag_nbb != nbb) {
     std::vector<short4> tasks;
@@ -946,6 +946,13 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
     ctx->dag_ntasks = (int)tasks.size();
     ctx->dag_nbb = nbb;
   }
+  return EMU_OK;
+}
+
+emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
+  int nbb = nb / PB;
+  emu_status ps0 = potrf_dag_prepare(ctx, nb);
+  if (ps0 != EMU_OK) return ps0;
   ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
   size_t state_bytes = (size_t)(1 + nbb * nbb) * sizeof(int);
   EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dag_ws, 0, state_bytes, ctx->stream));

@@ -796,6 +796,181 @@ emu_status mixed_sched_streams(emu_ctx *ctx, int nev) {
   return EMU_OK;
 }
 
+// ------------------------------------------- graph replay and schedule tuning
+// After the precision map (one host round trip) the factor's launches depend
+// only on the map, the tiling and the arenas' addresses.  They are recorded
+// once into a CUDA graph over the four streams and replayed while those are
+// unchanged (one host launch per factor).  The tuner times the reserved-SM
+// choices below on the first factors of each (NT, nb, class map) and keeps
+// the fastest; every choice gives the same result bit for bit (it only moves
+// CTAs between SMs).
+static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, int R, int R64);
+struct MixedCtx;
+static emu_status factor_mixed_launch(emu_ctx *ctx, emu_mat *A, MixedPlan *P, MixedCtx *M, int R, int R64);
+constexpr int kTuneR[][2] = {{kReservedSMs, kReservedSMsFP64}, {8, 16}, {24, 48}, {32, 64}};
+constexpr int kTuneN = 4;
+struct TuneEntry {
+  std::vector<char> sig;
+  float ms[kTuneN] = {};
+  int tried = 0, best = 0;
+};
+struct MixedCtx {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<char> key;
+  uint64_t graph_launches = 0;
+  std::vector<TuneEntry> tune;
+  int pending = -1, pending_cand = 0;  // tuning entry and choice of the factor in flight
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // around the factor's launches
+  bool use_graphs = true, tuning = true;
+};
+static MixedCtx *mctx(emu_ctx *ctx) {
+  if (!ctx->mixed) ctx->mixed = new MixedCtx();
+  return static_cast<MixedCtx *>(ctx->mixed);
+}
+template <typename T>
+static void key_put(std::vector<char> &k, const T &v) {
+  const char *b = reinterpret_cast<const char *>(&v);
+  k.insert(k.end(), b, b + sizeof(T));
+}
+
+void mixed_set_schedule(emu_ctx *ctx, int use_graphs, int tuning) {
+  MixedCtx *M = mctx(ctx);
+  M->use_graphs = use_graphs != 0;
+  M->tuning = tuning != 0;
+}
+
+void mixed_tune_record(emu_ctx *ctx, bool ok) {
+  MixedCtx *M = static_cast<MixedCtx *>(ctx->mixed);
+  if (!M || M->pending < 0) return;
+  float ms = 0.f;
+  if (!ok || cudaEventElapsedTime(&ms, M->ev_a, M->ev_b) != cudaSuccess) {
+    cudaGetLastError();
+    M->pending = -1;
+    return;
+  }
+  TuneEntry &t = M->tune[M->pending];
+  if (M->pending_cand == t.tried && t.tried < kTuneN) {
+    t.ms[t.tried++] = ms;
+    if (t.tried == kTuneN) {
+      t.best = 0;
+      for (int c = 1; c < kTuneN; c++)
+        if (t.ms[c] < t.ms[t.best]) t.best = c;
+    }
+  }
+  M->pending = -1;
+}
+
+int mixed_tuned_choice(emu_ctx *ctx, int *tried, int *R, int *R64) {
+  MixedCtx *M = static_cast<MixedCtx *>(ctx->mixed);
+  if (!M || M->tune.empty()) return -1;
+  const TuneEntry &t = M->tune.back();
+  if (tried) *tried = t.tried;
+  const int c = t.tried < kTuneN ? t.tried : t.best;
+  if (R) *R = kTuneR[c][0];
+  if (R64) *R64 = kTuneR[c][1];
+  return c;
+}
+
+static emu_status factor_mixed_run(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
+  MixedCtx *M = mctx(ctx);
+  // schedule choice: the next untimed candidate of this signature, else the best
+  std::vector<char> sig;
+  key_put(sig, A->nt);
+  key_put(sig, A->nb);
+  sig.insert(sig.end(), P->cls.begin(), P->cls.end());
+  int cand = 0;
+  M->pending = -1;
+  if (M->tuning) {
+    int e = -1;
+    for (int i = 0; i < (int)M->tune.size(); i++)
+      if (M->tune[i].sig == sig) e = i;
+    if (e < 0) {
+      if (M->tune.size() >= 16) M->tune.erase(M->tune.begin());
+      M->tune.push_back(TuneEntry{sig});
+      e = (int)M->tune.size() - 1;
+    }
+    TuneEntry &t = M->tune[e];
+    cand = t.tried < kTuneN ? t.tried : t.best;
+    M->pending = e;
+    M->pending_cand = cand;
+  }
+  const int R = kTuneR[cand][0], R64 = kTuneR[cand][1];
+  emu_status s = potrf_dag_prepare(ctx, A->nb);
+  if (s != EMU_OK) return s;
+  if (!M->ev_a) {
+    EMU_CUDA_TRY(ctx, cudaEventCreate(&M->ev_a));
+    EMU_CUDA_TRY(ctx, cudaEventCreate(&M->ev_b));
+  }
+  EMU_CUDA_TRY(ctx, cudaEventRecord(M->ev_a, ctx->stream));
+  s = factor_mixed_launch(ctx, A, P, M, R, R64);
+  if (s == EMU_OK) EMU_CUDA_TRY(ctx, cudaEventRecord(M->ev_b, ctx->stream));
+  return s;
+}
+
+static emu_status factor_mixed_launch(emu_ctx *ctx, emu_mat *A, MixedPlan *P, MixedCtx *M, int R, int R64) {
+  emu_status s = EMU_OK;
+  if (!M->use_graphs || ctx->prof || ctx->trace_on) return factor_mixed_record(ctx, A, P, R, R64);
+  std::vector<char> sig;
+  key_put(sig, A->nt);
+  key_put(sig, A->nb);
+  sig.insert(sig.end(), P->cls.begin(), P->cls.end());
+  // everything a replay depends on
+  std::vector<char> key = sig;
+  for (const void *q : {(const void *)A->t64, (const void *)A->t32, (const void *)A->op_bf16, (const void *)A->op_e4m3,
+                        (const void *)A->scale_e4m3, (const void *)A->op_tf32, (const void *)A->d_cls,
+                        (const void *)P->d_blob, (const void *)P->d_digits, (const void *)P->d_exp64,
+                        (const void *)ctx->dag_ws, (const void *)ctx->dag_tasks, (const void *)ctx->d_status})
+    key_put(key, q);
+  key_put(key, R);
+  key_put(key, R64);
+  key_put(key, ctx->sm_count);
+  cudaStream_t user = ctx->stream;
+  if (M->exec && M->key == key) {
+    EMU_CUDA_TRY(ctx, cudaGraphLaunch(M->exec, user));
+    ctx->launches += M->graph_launches;
+    return EMU_OK;
+  }
+  if (!M->cap) EMU_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+  const uint64_t l0 = ctx->launches;
+  ctx->stream = M->cap;
+  // relaxed: the launchers set kernel attributes while the streams are captured
+  cudaError_t e = cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeRelaxed);
+  s = (e == cudaSuccess) ? factor_mixed_record(ctx, A, P, R, R64) : emu_cuda_fail(ctx, e, "begin capture");
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) e = cudaStreamEndCapture(M->cap, &g);
+  ctx->stream = user;
+  const uint64_t nl = ctx->launches - l0;
+  ctx->launches = l0;
+  if (s != EMU_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    M->key.clear();
+    return s != EMU_OK ? s : emu_cuda_fail(ctx, e, "end capture");
+  }
+  bool ok = false;
+  if (M->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(M->exec, g, &info) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();  // the update error is not a launch error
+      cudaGraphExecDestroy(M->exec);
+      M->exec = nullptr;
+    }
+  }
+  if (!ok) e = cudaGraphInstantiate(&M->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    M->exec = nullptr;
+    M->key.clear();
+    return emu_cuda_fail(ctx, e, "graph instantiate");
+  }
+  M->key = key;
+  M->graph_launches = nl;
+  EMU_CUDA_TRY(ctx, cudaGraphLaunch(M->exec, user));
+  ctx->launches += nl;
+  return EMU_OK;
+}
+
 emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   int NT = A->nt, nb = A->nb;
   if (nb % gemm_tc::BN != 0) {
@@ -825,7 +1000,17 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
   MixedPlan *P = new MixedPlan();
   A->plan = P;
   if ((s = build_plan(ctx, A, P)) != EMU_OK) return s;
+  return factor_mixed_run(ctx, A, P);
+}
 
+// The launches of the factor after its plan: on ctx->stream (the context
+// stream, or a capture stream when the factor is recorded into a graph) and
+// the three internal streams joined to it.  R / R64: SMs the bulk GEMM leaves
+// free, without / with FP64-class panel work near.
+static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, int R, int R64) {
+  const int NT = A->nt, nb = A->nb;
+  const size_t te = A->tile_elems;
+  emu_status s = EMU_OK;
   int *st = ctx->d_status;
   double nb3 = (double)nb * nb * nb;
   {
@@ -979,7 +1164,7 @@ emu_status factor_mixed(emu_ctx *ctx, emu_mat *A, const emu_mp_opts *o) {
     // steps k and k+1: while that has FP64-class TRSMs or SYRKs (FP64-pipe
     // bound, too much shared memory to fit beside the GEMM) more SMs stay free
     const bool fp64_near = sp.fp64_panel || (k + 1 < NT && P->steps[k + 1].fp64_panel);
-    int bulk_ctas = std::max(1, ctx->sm_count - (fp64_near ? kReservedSMsFP64 : kReservedSMs));
+    int bulk_ctas = std::max(1, ctx->sm_count - (fp64_near ? R64 : R));
     if ((s = update_group(k, GR_G2A, bulk_ctas)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G2), ctx->bulk));
     if ((s = update_group(k, GR_G2, bulk_ctas)) != EMU_OK) break;
@@ -1194,6 +1379,8 @@ emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ld
 }
 
 emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs) {
+  if (mixed_potrs_blocked_supports(L->nb)) return mixed_potrs_blocked(ctx, L, X, ldx, nrhs);
+  // nb > 1024: one thread per row and right-hand side
   int nb = L->nb, NT = L->nt;
   int thr = 256;
   ProfScope ps(ctx, PROF_SOLVE, 2.0 * L->n * L->n * nrhs, 0.0);
@@ -1219,6 +1406,14 @@ emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int 
 }
 
 void mixed_ctx_release(emu_ctx *ctx) {
+  if (MixedCtx *M = static_cast<MixedCtx *>(ctx->mixed)) {
+    if (M->exec) cudaGraphExecDestroy(M->exec);
+    if (M->cap) cudaStreamDestroy(M->cap);
+    if (M->ev_a) cudaEventDestroy(M->ev_a);
+    if (M->ev_b) cudaEventDestroy(M->ev_b);
+    delete M;
+    ctx->mixed = nullptr;
+  }
   for (cudaEvent_t e : ctx->sched_ev) cudaEventDestroy(e);
   ctx->sched_ev.clear();
   if (ctx->crit) cudaStreamDestroy(ctx->crit);

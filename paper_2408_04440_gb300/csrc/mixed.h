@@ -8,7 +8,14 @@ void mixed_fill_info(const emu_mat *A, emu_factor_info *info);
 emu_status mixed_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long ldz, int s,
                         double *Y, long ldy);
 emu_status mixed_potrs(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs);
+// blocked right-looking sweeps (solve.cu), for nb a multiple of 64 up to 1024
+bool mixed_potrs_blocked_supports(int nb);
+emu_status mixed_potrs_blocked(emu_ctx *ctx, const emu_mat *L, double *X, long ldx, int nrhs);
 void mixed_ctx_release(emu_ctx *ctx);
+// graph replay and reserved-SM tuning of the single-matrix factor
+void mixed_set_schedule(emu_ctx *ctx, int use_graphs, int tuning);
+void mixed_tune_record(emu_ctx *ctx, bool ok);
+int mixed_tuned_choice(emu_ctx *ctx, int *tried, int *R, int *R64);
 // the internal streams of the lookahead schedule and at least nev events
 emu_status mixed_sched_streams(emu_ctx *ctx, int nev);
 // SMs left free of the bulk GEMM beside FP64-class panel work or not

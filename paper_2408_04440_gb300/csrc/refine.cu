@@ -10,34 +10,63 @@
 
 namespace {
 
-constexpr int NR = 16;  // right-hand sides per thread
-
-// R[:, c0:c0+NR] = B - S X, S symmetric from its packed lower FP64 tiles.
-// One thread per row; tiles j > i are read transposed from tile (j, i).
+// R[:, c0:c0+P] = B - S X for S symmetric from its packed lower FP64 tiles,
+// FP64 on the SIMT pipes: one CTA per (64-row slab of the padded matrix,
+// group of P right-hand sides), a loop over every tile column j of the slab's
+// block row i (tile (i, j) for j <= i, tile (j, i) read transposed for
+// j > i), operands staged through shared memory in 32-wide K chunks so that
+// every global read is coalesced.  Deterministic: one CTA owns each output.
+constexpr int RS = 64, RK = 32;
+template <int P>
 __global__ void __launch_bounds__(256)
-    k_symm_residual(const double *__restrict__ t64, int nb, int NT, const double *__restrict__ X,
-                    const double *__restrict__ Bm, double *__restrict__ R, long ld, int nrhs) {
-  long npad = (long)NT * nb;
-  long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int c0 = blockIdx.y * NR;
-  if (g >= npad) return;
-  int i = (int)(g / nb), r = (int)(g % nb);
-  double acc[NR];
+    k_symm_res(const double *__restrict__ t64, int nb, int NT, const double *__restrict__ X,
+               const double *__restrict__ Bm, double *__restrict__ R, long ld, int nrhs) {
+  constexpr int NQ = P / 4;  // right-hand sides per thread
+  __shared__ double a[RK][RS + 1];
+  __shared__ double x[RK][P + 1];
+  const long g0 = (long)blockIdx.x * RS;
+  const int i = (int)(g0 / nb), m0 = (int)(g0 % nb);
+  const int c0 = blockIdx.y * P;
+  const int p = min(P, nrhs - c0);
+  const int tid = threadIdx.x, mm = tid & (RS - 1), q0 = tid >> 6;
+  double acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NR; q++) acc[q] = 0.0;
+  for (int w = 0; w < NQ; w++) acc[w] = 0.0;
   for (int j = 0; j < NT; j++) {
-    const double *T = t64 + (size_t)(j <= i ? tile_index(i, j, NT) : tile_index(j, i, NT)) * nb * nb;
-    const double *xj = X + (size_t)j * nb;
-    for (int p = 0; p < nb; p++) {
-      double s = (j <= i) ? T[r + (size_t)p * nb] : T[p + (size_t)r * nb];
+    const bool lower = j <= i;
+    const double *T = t64 + (size_t)(lower ? tile_index(i, j, NT) : tile_index(j, i, NT)) * nb * nb;
+    for (int k0 = 0; k0 < nb; k0 += RK) {
+      for (int e = tid; e < RK * RS; e += 256) {
+        if (lower) {
+          const int m = e % RS, k = e / RS;
+          a[k][m] = T[(size_t)(m0 + m) + (size_t)(k0 + k) * nb];
+        } else {
+          const int k = e % RK, m = e / RK;
+          a[k][m] = T[(size_t)(k0 + k) + (size_t)(m0 + m) * nb];
+        }
+      }
+      for (int e = tid; e < RK * P; e += 256) {
+        const int k = e % RK, q = e / RK;
+        x[k][q] = q < p ? X[(size_t)j * nb + k0 + k + (size_t)(c0 + q) * ld] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < RK; k++) {
+        const double av = a[k][mm];
 #pragma unroll
-      for (int q = 0; q < NR; q++)
-        if (c0 + q < nrhs) acc[q] += s * xj[p + (size_t)(c0 + q) * ld];
+        for (int w = 0; w < NQ; w++) acc[w] = fma(av, x[k][q0 + 4 * w], acc[w]);
+      }
+      __syncthreads();
     }
   }
 #pragma unroll
-  for (int q = 0; q < NR; q++)
-    if (c0 + q < nrhs) R[g + (size_t)(c0 + q) * ld] = Bm[g + (size_t)(c0 + q) * ld] - acc[q];
+  for (int w = 0; w < NQ; w++) {
+    const int q = q0 + 4 * w;
+    if (q < p) {
+      const size_t o = (size_t)(g0 + mm) + (size_t)(c0 + q) * ld;
+      R[o] = Bm[o] - acc[w];
+    }
+  }
 }
 
 // Column sums of squares of R, X and B (one CTA per column, fixed order).
@@ -120,8 +149,15 @@ emu_status refine_solve(emu_ctx *ctx, const emu_mat *L, const emu_mat *S, const 
     s = (e == cudaSuccess) ? solve_with_factor(ctx, L, X, npad, nrhs) : emu_cuda_fail(ctx, e, "refine x0");
   }
   while (s == EMU_OK) {
-    dim3 g((unsigned)((npad + 255) / 256), (nrhs + NR - 1) / NR);
-    k_symm_residual<<<g, 256, 0, ctx->stream>>>(S->t64, nb, NT, X, Bp, R, npad, nrhs);
+    {
+      ProfScope ps(ctx, PROF_SOLVE, 2.0 * (double)npad * npad * nrhs, 8.0 * (double)npad * npad);
+      if (nrhs <= 16)
+        k_symm_res<16><<<dim3((unsigned)(npad / RS), 1), 256, 0, ctx->stream>>>(S->t64, nb, NT, X, Bp, R, npad,
+                                                                                nrhs);
+      else
+        k_symm_res<32><<<dim3((unsigned)(npad / RS), (nrhs + 31) / 32), 256, 0, ctx->stream>>>(S->t64, nb, NT, X,
+                                                                                              Bp, R, npad, nrhs);
+    }
     ctx->launches++;
     k_col_norms<<<nrhs, 256, 0, ctx->stream>>>(R, X, Bp, npad, npad, norms);
     ctx->launches++;

@@ -82,12 +82,13 @@ def test_classfmt_build_stores_each_tile_in_its_class(E, ctx, L, nb, beta, eps):
             got = G[ri, cj]
             c = cls[i, j]
             err = np.abs(got - ref)
+            # the device's pow may differ from libm's in the last places of s(l)
             if c == 0:
-                assert err.max() <= 4e-16 * np.abs(ref).max()
+                assert np.all(err <= 1e-15 * np.abs(ref))
             elif c == 1:
-                assert np.all(err <= 2.0**-24 * np.abs(ref) + 1e-300)
+                assert np.all(err <= (2.0**-24 + 1e-15) * np.abs(ref))
             elif c == 3:
-                assert np.all(err <= 2.0**-8 * np.abs(ref) + 1e-300)
+                assert np.all(err <= (2.0**-8 + 1e-15) * np.abs(ref))
             else:
                 # E4M3 with the storage scale s = 2^floor(log2(448 / bound)),
                 # bound = sqrt(max S_rr max S_cc) over the tile's rows and

@@ -289,3 +289,35 @@ def test_fp64_class_on_tensor_cores_matches_oracle(E, ctx, L, nb, beta):
     be = _backward_error(G, S)
     assert be <= 1e-15, be
     print(f"FP64 class on tensor cores L={L} nb={nb}: vs oracle {rel:.2e}, backward {be:.2e}")
+
+
+def test_graph_replay_and_tuning_keep_the_factor(E, ctx):
+    # the factor recorded once into a CUDA graph and replayed, and the tuner's
+    # four reserved-SM choices, all give the factor of the direct launches bit
+    # for bit; after four factors of one signature the tuner has its choice
+    L, nb, beta, eps = 44, 256, 5.5, 2e-8  # a signature no other test factors
+    S = O.cov_build(L, beta)
+    ctx.schedule(graphs=False, tuning=False)
+    A = E.emu_cov_build(ctx, L, beta, nb)
+    E.emu_potrf_mp(ctx, A, eps=eps)
+    G0 = _np(E.emu_mat_export(ctx, A))
+    A.free()
+    assert _backward_error(G0, S) <= eps
+    ctx.schedule(graphs=True, tuning=True)
+    try:
+        for it in range(6):
+            A = E.emu_cov_build(ctx, L, beta, nb)
+            E.emu_potrf_mp(ctx, A, eps=eps)
+            G = _np(E.emu_mat_export(ctx, A))
+            A.free()
+            assert np.array_equal(G, G0), it
+            tried, R, R64 = ctx.schedule_info()
+            assert tried == min(it + 1, 4)
+        assert (R, R64) in {(16, 32), (8, 16), (24, 48), (32, 64)}
+        # the choice is kept
+        A = E.emu_cov_build(ctx, L, beta, nb)
+        E.emu_potrf_mp(ctx, A, eps=eps)
+        A.free()
+        assert ctx.schedule_info() == (4, R, R64)
+    finally:
+        ctx.schedule(graphs=True, tuning=True)
