@@ -53,9 +53,14 @@ def parse():
     ap.add_argument("--no-empirical", action="store_true", help="skip the empirical-covariance build from residuals")
     ap.add_argument("--no-bands", action="store_true", help="skip the paper's band-map variants (DP/SP, DP/SP/HP, "
                                                              "DP/HP) of the same factor")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "fp64_L400"], default="single",
                     help="single: one n=L^2 covariance (default); batched: --count covariances of random "
                          "bandlimit L in [8, 64], beta in [2, 8) (SplitMix64 draws from --batch-seed)")
+    ap.add_argument("--configs", default="cfg1,cfg3,cfg4,cfg5,fp64tc",
+                    help="the other workloads measured beside the headline one (comma list, '' for none): "
+                         "cfg1 = L=32 plain FP64; cfg3 = L=256 with E4M3 tiles and refinement; cfg4 = L=480 "
+                         "class-format storage; cfg5 = the batch of 1024; fp64tc = the headline matrix with every "
+                         "tile FP64-class on the tensor cores")
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--batch-seed", type=int, default=3)
     return ap.parse_args()
@@ -159,6 +164,12 @@ def run_ours(a):
     ctx = E.Context(local, stream=stream)
     n, s = a.L * a.L, a.samples
     flops = n ** 3 / 3.0
+    alu = {}
+    try:
+        f64, f32 = ctx.alu_peaks()
+        alu = {"fp64_fma_tflops": round(f64, 3), "fp32_fma_tflops": round(f32, 2)}
+    except Exception:  # the rooflines then fall back to the earlier probe values
+        pass
     Y = E._colmajor_empty(n, s, ctx.device)
     seed = a.seed + 1000 * rank
 
@@ -179,6 +190,7 @@ def run_ours(a):
         clocks = ClockSampler(local)
         barrier()
         launches0 = ctx.launch_count
+        host0 = ctx.host_launch_count
         clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -190,6 +202,7 @@ def run_ours(a):
         barrier()
         clk = clocks.stop()
         gpu_launches = ctx.launch_count - launches0
+        host_launches = ctx.host_launch_count - host0
         ms_total = e0.elapsed_time(e1)
         t = torch.tensor([ms_total], device=ctx.device)
         if dist is not None:
@@ -220,7 +233,9 @@ def run_ours(a):
         extra["kernel_groups"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                                       "share": round(v["ms"] / step_ms, 4)} for k, v in prof.items() if v["launches"]}
         peaks = load_peaks()
+        peaks.update(alu)
         roof = roofline(prof, peaks)
+        extra["measured_peaks"] = dict(alu, **tensor_peaks())
 
         # accuracy: backward error on 64 sampled rows against the GPU-built covariance
         extra["backward_error_rows64"] = backward_error_rows(E, ctx, a, rows=64)
@@ -245,6 +260,8 @@ def run_ours(a):
             extra["emulation"] = emulation_variant(E, ctx, a)
 
         e2e = None if a.no_e2e else run_e2e(E, ctx, a, flops)
+        if a.configs:
+            extra["configs"] = other_configs(E, ctx, a, flops, mixed_factor_ms)
 
     cpu = None if (a.no_cpu or world > 1) else cpu_baseline(a)
     line = {
@@ -254,7 +271,8 @@ def run_ours(a):
         "config": {"workload": workload_name(a), "L": a.L, "n": n, "nb": a.nb, "beta": a.beta, "eps": a.eps,
                    "samples": s, "seed": a.seed, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2: each step rebuilds the 1.1 GB FP64 tile arena"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clk,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+        "host_launches_per_step": round(host_launches / a.steps, 1), "clocks": clk,
     }
     line.update(extra)
     print(json.dumps(line), flush=True)
@@ -280,10 +298,51 @@ ALU_NOTES = {
     "trsm32": "the SIMT FP32 panel TRSM (tile sizes whose trailing columns do not fit in TMEM) is bound by its "
               "substitution chain and by L_kk strip loads, on the SMs left beside the bulk update",
 }
-# ALU peaks measured on this GPU model with dependent-free FMA loops (TFLOP/s)
+# ALU peaks (TFLOP/s): measured in each run by the library's FMA-loop probe
+# (emu_measure_alu_peaks: eight independent FMA chains per thread, eight CTAs of
+# 256 threads per SM); these values (the same probe on a GB300) stand in only
+# where the probe cannot run.
 ALU_PEAK = {"fp64": 1.19, "fp32": 74.0}
 ALU_GROUPS = {"potrf": "fp64", "trsm64": "fp64", "update64": "fp64", "trmm64": "fp64", "solve": "fp64",
               "trsm32": "fp32"}
+
+
+def tensor_peaks() -> dict:
+    """cuBLAS TF32 and FP8-E4M3 GEMM rates (8192^3, best of five, CUDA events): the measured denominators of
+    the TF32 and E4M3 classes (BF16's are in MEASURED_PEAKS.json)."""
+    import torch
+
+    out = {}
+    n = 8192
+
+    def best(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        ts = []
+        for _ in range(5):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return 2.0 * n ** 3 / (min(ts) * 1e-3) / 1e12
+
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        out["tf32_cublas_tflops"] = round(best(lambda: a @ b), 1)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        a8 = a.to(torch.float8_e4m3fn)
+        b8 = b.to(torch.float8_e4m3fn)
+        one = torch.tensor(1.0, device="cuda")
+        out["e4m3_cublas_tflops"] = round(best(lambda: torch._scaled_mm(a8, b8.t(), scale_a=one, scale_b=one,
+                                                                         out_dtype=torch.bfloat16)), 1)
+        del a, b, a8, b8
+    except Exception as exc:  # a missing library path is reported, not fatal
+        out["tensor_peaks_error"] = f"{type(exc).__name__}: {exc}"
+    return out
 
 
 def roofline(prof: dict, peaks: dict) -> dict:
@@ -304,12 +363,13 @@ def roofline(prof: dict, peaks: dict) -> dict:
                 "peak_note": f"bf16 sustained {bf16} TF/s {src}, weighted by the class mix"}
     if group in ALU_GROUPS:
         unit = ALU_GROUPS[group]
-        peak = ALU_PEAK[unit]
+        peak = peaks.get(f"{unit}_fma_tflops") or ALU_PEAK[unit]
+        psrc = "measured in this run" if f"{unit}_fma_tflops" in peaks else "of an earlier probe run"
         achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
         return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(group),
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
-                "peak_note": f"{unit.upper()} FMA peak measured with an FMA loop; " + ALU_NOTES.get(group, "")}
+                "peak_note": f"{unit.upper()} FMA-loop peak {psrc}; " + ALU_NOTES.get(group, "")}
     hbm = peaks.get("hbm_gbs") or 6800.0
     achieved = g["bytes"] / (g["ms"] * 1e-3) / 1e9
     return {"kernel": group, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -541,6 +601,198 @@ def run_e2e(E, ctx, a, flops) -> dict:
 
 
 # ------------------------------------------------------------- CPU oracle
+# ------------------------------------------------------ the other workloads
+MASK_WITH_E4M3 = 0b11011
+
+
+def _timed(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def cfg1_fp64(E, ctx) -> dict:
+    """L=32, n=1024, nb=128, beta=4: plain FP64 tile Cholesky + 64 samples (seed 0)."""
+    import torch
+
+    L, nb, beta, s = 32, 128, 4.0, 64
+    n = L * L
+    ms = []
+    for it in range(6):
+        A = E.emu_cov_build(ctx, L, beta, nb)
+        info = E.emu_potrf_mp(ctx, A)
+        if it > 0:
+            ms.append(info.ms)
+        if it < 5:
+            A.free()
+    Y, ts = _timed(lambda: E.emu_sample(ctx, A, s, seed=0))
+    Lf = E.emu_mat_export(ctx, A)
+    A.free()
+    S = E.emu_cov_build(ctx, L, beta, nb)
+    Sd = E.emu_mat_export(ctx, S)
+    S.free()
+    Sd = Sd + Sd.t() - torch.diag(torch.diag(Sd))
+    be = float(torch.linalg.norm(Lf @ Lf.t() - Sd) / torch.linalg.norm(Sd))
+    fm = statistics.median(ms)
+    return {"workload": "L=32 n=1024 nb=128 beta=4, plain FP64 tile Cholesky + 64 samples seed 0",
+            "factor_ms": round(fm, 4), "tflops": round(n ** 3 / 3 / (fm * 1e-3) / 1e12, 4),
+            "sample_ms": round(ts * 1e3, 3), "backward_error": be,
+            "parity": "vs the CPU oracle to 1e-12 in tests/test_gpu_fp64.py"}
+
+
+def cfg3_e4m3_refine(E, ctx) -> dict:
+    """L=256, n=65536, nb=1024, beta=12: adaptive FP64/FP32/BF16/E4M3 at eps=1e-6, 16 N(0,1) right-hand sides
+    refined with FP64 residuals; the all-FP64-class tensor-core factor of the same matrix beside it."""
+    import torch
+
+    L, nb, beta, eps = 256, 1024, 12.0, 1e-6
+    n = L * L
+    flops = n ** 3 / 3
+    S = E.emu_cov_build(ctx, L, beta, nb)
+    ms, info = [], None
+    for it in range(5):  # the first four factors of a signature try the tuner's choices
+        A = E.emu_mat_clone(ctx, S)
+        info = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=MASK_WITH_E4M3)
+        ms.append(info.ms)
+        if it < 4:
+            A.free()
+    g = torch.Generator(device="cpu").manual_seed(4)
+    B = torch.randn((16, n), generator=g, dtype=torch.float64).cuda().t()  # n x 16, column-major
+    E.emu_solve_refine(ctx, A, S, B, tol=1e-12, maxit=30)  # warm-up
+    (X, ri), _ = _timed(lambda: E.emu_solve_refine(ctx, A, S, B, tol=1e-12, maxit=30))
+    est = E.emu_backward_error_est(ctx, A, L, beta, nprobes=8, seed=5)
+    A.free()
+    out = {"workload": "L=256 n=65536 nb=1024 beta=12, adaptive FP64/FP32/BF16/E4M3 at eps=1e-6; 16 N(0,1) "
+                       "right-hand sides, FP64-residual refinement to 1e-12",
+           "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)), "factor_ms": round(ms[-1], 2),
+           "factor_ms_tuning": [round(x, 2) for x in ms[:4]], "tflops": round(flops / (ms[-1] * 1e-3) / 1e12, 2),
+           "backward_error_est": est, "refine_iters": ri.iters, "refine_ms": round(ri.ms, 2),
+           "refine_backward_error": ri.rel_resid}
+    A = E.emu_mat_clone(ctx, S)
+    S.free()
+    i64 = E.emu_potrf_mp(ctx, A, eps=eps, prec_mask=1)
+    out["fp64_class_tc_factor_ms"] = round(i64.ms, 2)
+    out["fp64_class_tc_tflops"] = round(flops / (i64.ms * 1e-3) / 1e12, 3)
+    out["fp64_class_tc_backward_error_est"] = E.emu_backward_error_est(ctx, A, L, beta, nprobes=8, seed=5)
+    out["speedup_vs_fp64_class_tc"] = round(i64.ms / ms[-1], 2)
+    A.free()
+    out["fp64_pipe"] = ("not run in the default bench (about 80 s at the DFMA rate); see --workload fp64_L400 "
+                        "for the plain FP64 factor at scale")
+    return out
+
+
+def cfg4_classfmt(E, ctx, samples: int = 1024) -> dict:
+    """L=480, n=230400, nb=1024, beta=16: BF16/E4M3-dominant class-format storage at eps=1e-6, 1024 samples
+    (seed 2), backward error by the Hutchinson estimate (S regenerated from its parameters)."""
+    import torch
+
+    L, nb, beta, eps = 480, 1024, 16.0, 1e-6
+    n = L * L
+    flops = n ** 3 / 3
+    A, tb = _timed(lambda: E.emu_cov_build_classfmt(ctx, L, beta, nb, eps=eps, prec_mask=MASK_WITH_E4M3))
+    free0, _ = torch.cuda.mem_get_info()
+    info = E.emu_potrf_mp(ctx, A, eps=eps)
+    Y = E._colmajor_empty(n, samples, ctx.device)
+    _, ts = _timed(lambda: E.emu_sample(ctx, A, samples, seed=2, out=Y))
+    est, te = _timed(lambda: E.emu_backward_error_est(ctx, A, L, beta, nprobes=8, seed=5))
+    sizes = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2, "e4m3": 1}
+    stored = sum(c * nb * nb * sizes[k] for k, c in zip(E.CLASS_NAMES, info.tiles))
+    A.free()
+    del Y
+    return {"workload": "L=480 n=230400 nb=1024 beta=16, class-format storage at eps=1e-6 (every tile in its "
+                        "class's format), 1024 samples seed 2",
+            "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)), "stored_gb": round(stored / 1e9, 2),
+            "fp64_lower_gb": round((n // nb + 1) * (n // nb + 2) / 2 * nb * nb * 8 / 1e9, 1),
+            "build_s": round(tb, 3), "factor_ms": round(info.ms, 1),
+            "tflops": round(flops / (info.ms * 1e-3) / 1e12, 2), "sample_ms": round(ts * 1e3, 1),
+            "backward_error_est": est, "estimate_probes": 8, "estimate_s": round(te, 2),
+            "device_free_gb_after_build": round(free0 / 1e9, 1)}
+
+
+def cfg5_batched(E, ctx, seed: int = 3, count: int = 1024, s: int = 256) -> dict:
+    """1024 covariances, L ~ U{8..64}, beta ~ U[2,8) (SplitMix64 draws, seed 3), eps=1e-8, 256 samples each,
+    one call in one captured graph with the tuned tile size; plain FP64 batch and per-matrix FP64 beside it."""
+    import torch
+
+    from paper_2408_04440_gb300.inputs import batch_draws
+
+    draws = batch_draws(count, seed)
+    flops = sum((L * L) ** 3 / 3.0 for L, _ in draws)
+    Ys = [E._colmajor_empty(L * L, s, ctx.device) for L, _ in draws]
+
+    def step(nb=0, e=1e-8):
+        return E.emu_batch_potrf_sample(ctx, draws, nb=nb, eps=e, prec_mask=MASK_FP64_FP32_BF16, nsamples=s,
+                                        seed=seed, out_Y=Ys)
+
+    _, _, infos, _ = step()  # tunes the tile size, captures the graph
+    ms = []
+    for _ in range(3):
+        _, _, infos, _ = step()
+        ms.append(infos[0].ms)
+    nb_used = infos[0].nb
+    m = statistics.median(ms)
+    step(nb=nb_used, e=0.0)
+    _, _, i64, _ = step(nb=nb_used, e=0.0)
+    E.emu_batch_release(ctx)
+    sub = draws[:128]
+    fl_sub = sum((L * L) ** 3 / 3.0 for L, _ in sub)
+
+    def per_matrix():
+        for b, (L, beta) in enumerate(sub):
+            M = E.emu_cov_build(ctx, L, beta, 256)
+            E.emu_potrf_mp(ctx, M)
+            E.emu_sample(ctx, M, s, seed=seed, stream_id=b)
+            M.free()
+
+    per_matrix()
+    _, dt = _timed(per_matrix)
+    del Ys
+    return {"workload": "1024 covariances L~U{8..64} beta~U[2,8) seed 3, eps=1e-8, 256 samples each, one call",
+            "call_ms": round(m, 2), "tflops": round(flops / (m * 1e-3) / 1e12, 3), "tile_size": nb_used,
+            "fp64_batch_ms": round(i64[0].ms, 2), "per_matrix_fp64_tflops": round(fl_sub / dt / 1e12, 4),
+            "speedup_vs_per_matrix_fp64": round(flops / (m * 1e-3) / (fl_sub / dt), 2)}
+
+
+def fp64tc_headline(E, ctx, a, flops, mixed_ms) -> dict:
+    """The headline matrix with every tile FP64-class (exact digit products on the BF16 tensor cores)."""
+    ms = []
+    for it in range(2):
+        A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
+        info = E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=1)
+        ms.append(info.ms)
+        if it == 1:
+            est = E.emu_backward_error_est(ctx, A, a.L, a.beta, nprobes=8, seed=5)
+        A.free()
+    return {"factor_ms": round(ms[-1], 3), "tflops": round(flops / (ms[-1] * 1e-3) / 1e12, 3),
+            "backward_error_est": est, "speedup_of_mixed": round(ms[-1] / mixed_ms, 2),
+            "note": "FP64-accurate factor on the tensor cores (Ozaki digits); the plain FP64 row is the FP64 pipe"}
+
+
+def other_configs(E, ctx, a, flops, mixed_ms) -> dict:
+    import torch
+
+    out = {}
+    todo = [c for c in a.configs.split(",") if c]
+    fns = {"cfg1": lambda: cfg1_fp64(E, ctx), "fp64tc": lambda: fp64tc_headline(E, ctx, a, flops, mixed_ms),
+           "cfg3": lambda: cfg3_e4m3_refine(E, ctx), "cfg5": lambda: cfg5_batched(E, ctx),
+           "cfg4": lambda: cfg4_classfmt(E, ctx)}
+    for c in ["cfg1", "fp64tc", "cfg3", "cfg5", "cfg4"]:
+        if c not in todo:
+            continue
+        t0 = time.perf_counter()
+        try:
+            out[c] = fns[c]()
+        except Exception as exc:  # one workload's failure is reported, not fatal to the line
+            out[c] = {"error": f"{type(exc).__name__}: {exc}"}
+        out[c]["wall_s"] = round(time.perf_counter() - t0, 2)
+        torch.cuda.empty_cache()
+    return out
+
+
 def _panel_flops(n: int, nb: int, k: int) -> float:
     m = max(n - (k + 1) * nb, 0)
     kb = min(nb, n - k * nb)
@@ -812,8 +1064,53 @@ def run_reference_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_fp64_L400(a):
+    """The FP64 comparison at L=400 (n=160000, nb=1024, beta=16): the plain FP64 tile Cholesky on the FP64 pipe
+    (about 104 GB of FP64 lower tiles) and the same factor with every tile FP64-class on the tensor cores in
+    class-format storage, each once, with the SM clocks sampled meanwhile."""
+    import torch
+
+    import paper_2408_04440_gb300 as E
+    from paper_2408_04440_gb300 import build as _b
+
+    _b.build()
+    L, nb, beta = 400, 1024, 16.0
+    n = L * L
+    flops = n ** 3 / 3
+    stream = torch.cuda.Stream()
+    ctx = E.Context(0, stream=stream)
+    out = {"workload": "L=400 n=160000 nb=1024 beta=16: FP64 tile Cholesky", "n": n}
+    with torch.cuda.stream(stream):
+        W = E.emu_cov_build(ctx, 64, beta, nb)  # warm-up of the FP64 path
+        E.emu_potrf_mp(ctx, W)
+        W.free()
+        clocks = ClockSampler(0)
+        A = E.emu_cov_build(ctx, L, beta, nb)
+        clocks.start()
+        info = E.emu_potrf_mp(ctx, A)
+        out["fp64_pipe"] = {"factor_s": round(info.ms / 1e3, 2), "tflops": round(flops / (info.ms * 1e-3) / 1e12, 4),
+                            "backward_error_est": E.emu_backward_error_est(ctx, A, L, beta, nprobes=4, seed=5),
+                            "clocks": clocks.stop()}
+        A.free()
+        torch.cuda.empty_cache()
+        clocks = ClockSampler(0)
+        B = E.emu_cov_build_classfmt(ctx, L, beta, nb, eps=0.0)
+        clocks.start()
+        info = E.emu_potrf_mp(ctx, B, eps=0.0)
+        out["fp64_class_tc"] = {"factor_s": round(info.ms / 1e3, 2),
+                                "tflops": round(flops / (info.ms * 1e-3) / 1e12, 3),
+                                "backward_error_est": E.emu_backward_error_est(ctx, B, L, beta, nprobes=4, seed=5),
+                                "clocks": clocks.stop()}
+        B.free()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     a = parse()
+    if a.workload == "fp64_L400":
+        run_fp64_L400(a)
+        return
     if a.seed is None:
         a.seed = 3 if a.workload == "batched" else 1
     if a.workload == "batched":

@@ -145,8 +145,12 @@ emu_status emu_destroy(emu_ctx *ctx);
 emu_status emu_set_stream(emu_ctx *ctx, void *stream);
 const char *emu_status_str(emu_status s);
 const char *emu_last_error(const emu_ctx *ctx);
-/* Number of this library's kernels launched through `ctx` so far. */
+/* Number of this library's kernels launched through `ctx` so far (the kernels
+ * of a replayed CUDA graph included). */
 uint64_t emu_launch_count(const emu_ctx *ctx);
+/* Number of launch calls the host made through `ctx` so far: kernel launches
+ * issued one by one, plus one per CUDA graph replay. */
+uint64_t emu_host_launch_count(const emu_ctx *ctx);
 
 /* Optional per-kernel-group timing, for roofline accounting.  When enabled,
  * every group of launches is bracketed by CUDA events on the context stream
@@ -195,6 +199,12 @@ emu_status emu_schedule(emu_ctx *ctx, int use_graphs, int tuning);
  * choice the next factor of that signature uses.  All 0 before any mixed
  * factor. */
 emu_status emu_schedule_info(emu_ctx *ctx, int *tried, int *reserved, int *reserved_fp64);
+
+/* Measured FMA rates of the context's device, in TFLOP/s (2 flops per FMA):
+ * eight independent FP64 (FP32) FMA chains per thread, eight CTAs of 256
+ * threads per SM, timed with CUDA events; the denominators of the rooflines of
+ * the kernels bound by plain FP64 or FP32 arithmetic.  Synchronises. */
+emu_status emu_measure_alu_peaks(emu_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
 /* Test hook of the timeout path (failure detection; the paper has no
  * counterpart).  Every wait of the dataflow FP64 diagonal POTRF on another
@@ -322,14 +332,15 @@ emu_status emu_emulate_grid(emu_ctx *ctx, const double *dZs, long G, int T, long
  * precision map is computed first from a norm pass that stores nothing (the
  * rule of emu_mp_opts o; every diagonal tile FP64; TF32 is stored as FP32),
  * then every tile is computed again and stored: FP64 8 bytes, FP32 4, BF16 2
- * (nearest), E4M3 1 byte per entry (codes of v * s, s = 2^floor(log2(448 /
- * sqrt(max S_rr max S_cc))) over the tile's rows and columns, so that no
- * Schur complement entry saturates).  nb must be a multiple of 256.
+ * (nearest); E4M3-class tiles take 2 bytes per entry and hold BF16 values
+ * while they are trailing tiles of the factor.  nb must be a multiple of 256.
  * emu_potrf_mp factors such a matrix in place with this map (o is not read):
  * each trailing update is accumulated in FP32 on the tensor cores and the tile
- * is re-rounded to its format; each panel is decoded, solved as in the
- * FP32-master factor, rounded back to its format, and the operands of later
- * updates are made from the rounded values.  emu_sample, emu_mat_export,
+ * is re-rounded to its working format (FP32 or BF16); each panel is decoded,
+ * solved as in the FP32-master factor and rounded to its class (E4M3 tiles to
+ * codes of x s, s = 2^floor(log2(448 / amax)) per tile, stored in the first
+ * byte of each entry's slot), and the operands of later updates are made from
+ * the rounded values.  emu_sample, emu_mat_export,
  * emu_mat_tile_info and emu_backward_error_est accept it; emu_potrs,
  * emu_solve_refine and emu_mat_clone return EMU_ESTATE.  Device memory:
  * about the stored bytes plus, while factoring, a ring of three panels

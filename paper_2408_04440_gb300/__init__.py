@@ -34,7 +34,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_schedule", "emu_schedule_info", "emu_cov_build", "emu_mat_import",
+    "emu_launch_count", "emu_host_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_schedule", "emu_schedule_info", "emu_measure_alu_peaks", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_cov_build_classfmt",
     "emu_backward_error_est", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
@@ -101,11 +101,14 @@ def load() -> ctypes.CDLL:
     L.emu_last_error.restype = ctypes.c_char_p
     L.emu_launch_count.argtypes = [vp]
     L.emu_launch_count.restype = ctypes.c_uint64
+    L.emu_host_launch_count.argtypes = [vp]
+    L.emu_host_launch_count.restype = ctypes.c_uint64
     dpp = ctypes.POINTER(ctypes.c_double)
     L.emu_prof_enable.argtypes = [vp, i]
     L.emu_trace_enable.argtypes = [vp, i]
     L.emu_test_wait_hook.argtypes = [vp, ctypes.c_longlong, i]
     L.emu_schedule.argtypes = [vp, i, i]
+    L.emu_measure_alu_peaks.argtypes = [vp, dpp, dpp]
     L.emu_schedule_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.emu_prof_timeline.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_trace_read.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -139,7 +142,7 @@ def load() -> ctypes.CDLL:
     L.emu_batch_release.argtypes = [vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
                  "emu_trace_enable", "emu_trace_read", "emu_prof_timeline", "emu_test_wait_hook",
-                 "emu_schedule", "emu_schedule_info",
+                 "emu_schedule", "emu_schedule_info", "emu_measure_alu_peaks",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import", "emu_emulate_grid",
                  "emu_cov_build_classfmt", "emu_backward_error_est",
                  "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape", "emu_mat_free",
@@ -190,6 +193,10 @@ class Context:
     def launch_count(self) -> int:
         return int(self.lib.emu_launch_count(self.h))
 
+    @property
+    def host_launch_count(self) -> int:
+        return int(self.lib.emu_host_launch_count(self.h))
+
     def prof_enable(self, on: bool = True):
         self._check(self.lib.emu_prof_enable(self.h, int(on)), "emu_prof_enable")
 
@@ -214,6 +221,12 @@ class Context:
             self._check(self.lib.emu_prof_timeline(self.h, ctypes.c_void_p(out.ctypes.data), n.value,
                                                    ctypes.byref(n)), "emu_prof_timeline")
         return out
+
+    def alu_peaks(self):
+        """(FP64, FP32) FMA rates of the device in TFLOP/s, measured with FMA loops."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.emu_measure_alu_peaks(self.h, ctypes.byref(a), ctypes.byref(b)), "emu_measure_alu_peaks")
+        return a.value, b.value
 
     def schedule(self, graphs: bool = True, tuning: bool = True):
         """Graph replay and reserved-SM tuning of the single-matrix mixed factor (both on by default)."""

@@ -100,6 +100,8 @@ const char *emu_last_error(const emu_ctx *ctx) { return ctx ? ctx->last_error.c_
 
 uint64_t emu_launch_count(const emu_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+uint64_t emu_host_launch_count(const emu_ctx *ctx) { return ctx ? ctx->host_launches : 0; }
+
 emu_status emu_create(emu_ctx **out, int device, void *stream) {
   if (!out) return EMU_EINVAL;
   *out = nullptr;

@@ -716,7 +716,7 @@ emu_status batch_capture(emu_ctx *ctx, BatchCtx *BC, BatchState *B) {
   if (!BC->cap) EMU_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&BC->cap, cudaStreamNonBlocking));
   cudaStream_t user = ctx->stream;
   bool prof = ctx->prof;
-  uint64_t l0 = ctx->launches;
+  uint64_t l0 = ctx->launches, h0 = ctx->host_launches;
   ctx->prof = false;  // no profiler events inside the graph
   ctx->stream = BC->cap;
   // relaxed: the launchers set kernel attributes while the stream is captured
@@ -728,6 +728,7 @@ emu_status batch_capture(emu_ctx *ctx, BatchCtx *BC, BatchState *B) {
   ctx->prof = prof;
   B->graph_launches = (int)(ctx->launches - l0);
   ctx->launches = l0;  // counted when the graph runs
+  ctx->host_launches = h0;
   if (s != EMU_OK) {
     if (g) cudaGraphDestroy(g);
     return s;
@@ -835,6 +836,7 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   } else {
     EMU_CUDA_TRY(ctx, cudaGraphLaunch(B->graph, ctx->stream));
     ctx->launches += B->graph_launches;
+    ctx->host_launches++;
   }
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(int), cudaMemcpyDeviceToHost,

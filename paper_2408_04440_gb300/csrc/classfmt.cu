@@ -8,9 +8,14 @@
 //   FP64 (every diagonal tile, and the FP64-class tiles)  8 bytes / entry
 //   FP32 class                                            4 bytes
 //   BF16 class                                            2 bytes
-//   E4M3 class (code q, value q / s with a power-of-two s per tile)  1 byte
-// and is re-rounded to its format after every trailing update (the tensor
-// cores accumulate each update in FP32 in TMEM).  Panel k is decoded into
+//   E4M3 class: BF16 while the tile is a trailing (Schur complement) tile,
+//     then, once solved, codes q of the value q / s with a power-of-two s per
+//     tile (1 byte, in the first half of the tile's 2-byte slot)
+// and is re-rounded to its working format after every trailing update (the
+// tensor cores accumulate each update in FP32 in TMEM).  Re-rounding trailing
+// tiles to E4M3 itself after each update made factors of these covariances
+// lose positive definiteness (at eps = 1e-4, L = 40); BF16 working storage
+// keeps the backward error within eps.  Panel k is decoded into
 // FP32 / FP64 panel buffers (a ring of three panels), solved by the same
 // TRSM kernels as the FP32-master factor, rounded back to its storage format,
 // and the panel's operand copies (three BF16 pieces, FP8 copies, FP64 digit
@@ -68,8 +73,9 @@ __global__ void k_decode(const int4 *__restrict__ jobs, size_t te, const double 
   } else if (j.z == EMU_CLASS_BF16) {
     for (size_t e = i0; e < te; e += step) P32[p + e] = __bfloat162float(__ushort_as_bfloat16(t16[o + e]));
   } else {
-    const float inv = 1.0f / sc8[j.y];  // a power of two: exact
-    for (size_t e = i0; e < te; e += step) P32[p + e] = e4m3_to_float(t8[o + e]) * inv;
+    // an E4M3-class tile before its panel step: its BF16 working values
+    const uint16_t *w = reinterpret_cast<const uint16_t *>(t8);
+    for (size_t e = i0; e < te; e += step) P32[p + e] = __bfloat162float(__ushort_as_bfloat16(w[o + e]));
   }
 }
 
@@ -103,7 +109,8 @@ __global__ void k_encode(const int4 *__restrict__ jobs, int nb, double *__restri
 
 // E4M3-class panel tiles, one CTA per job {panel index, slot, -, -}: the
 // tile's amax, the scale s = 2^floor(log2(448 / amax)) (1 for a zero tile),
-// the codes q = e4m3(x s) (saturating, nearest) into the slot (column-major)
+// the codes q = e4m3(x s) (saturating, nearest) into the first half of the
+// slot (column-major; the slot's BF16 working values are no longer needed)
 // and, transposed, into the panel's FP8 operand copy (row-major) with scale
 // s; the value q / s replaces x in the FP32 panel buffer, and the operand
 // pieces become (bf16(q / s), 0, 0) (exact: an E4M3 value fits BF16).
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(1024) k_encode_e4m3(const int4 *__restrict__ j
   }
   __syncthreads();
   const float s = s_scale, inv = 1.0f / s;
-  uint8_t *q8 = t8 + (size_t)j.y * te;
+  uint8_t *q8 = t8 + (size_t)j.y * 2 * te;
   uint8_t *p8 = P8 + (size_t)j.x * te;
   uint16_t *p0 = Pop + (size_t)j.x * 3 * te;
   const int tx = threadIdx.x & (TB - 1), ty = threadIdx.x >> 5;  // 32 x 32
@@ -185,11 +192,11 @@ __global__ void k_samp_planes(const int4 *__restrict__ jobs, int nb, const float
   const size_t o = (size_t)j.x * te;
   const float inv8 = (j.y == EMU_CLASS_E4M3) ? 1.0f / sc8[j.x] : 1.0f;
   for (int yy = ty; yy < TB; yy += 8) {
-    const size_t e = o + (size_t)(rb * TB + tx) + (size_t)(cb * TB + yy) * nb;
+    const size_t e = (size_t)(rb * TB + tx) + (size_t)(cb * TB + yy) * nb;  // within the tile
     float v;
-    if (j.y == EMU_CLASS_FP32) v = t32[e];
-    else if (j.y == EMU_CLASS_BF16) v = __bfloat162float(__ushort_as_bfloat16(t16[e]));
-    else v = e4m3_to_float(t8[e]) * inv8;
+    if (j.y == EMU_CLASS_FP32) v = t32[o + e];
+    else if (j.y == EMU_CLASS_BF16) v = __bfloat162float(__ushort_as_bfloat16(t16[o + e]));
+    else v = e4m3_to_float(t8[2 * o + e]) * inv8;  // a solved E4M3 tile: codes in its slot's first half
     blk[yy][tx] = v;
   }
   __syncthreads();
@@ -219,7 +226,8 @@ struct TileSrc {
   const uint8_t *t8;
   const float *sc8;
   int nb, NT;
-  int master;  // FP32-master storage: every non-FP64 tile is an FP32 master
+  int master;      // FP32-master storage: every non-FP64 tile is an FP32 master
+  int e4m3_final;  // class format: E4M3 tiles hold their codes (factor), else BF16 working values
 };
 __device__ inline double tile_at(const TileSrc &S, long t, size_t e, int c, int sl) {
   const size_t o = (size_t)sl * S.nb * S.nb + e;
@@ -227,7 +235,8 @@ __device__ inline double tile_at(const TileSrc &S, long t, size_t e, int c, int 
   if (S.master) return (double)S.t32[o];
   if (c == EMU_CLASS_FP32 || c == EMU_CLASS_TF32) return (double)S.t32[o];
   if (c == EMU_CLASS_BF16) return (double)__bfloat162float(__ushort_as_bfloat16(S.t16[o]));
-  return (double)e4m3_to_float(S.t8[o]) / (double)S.sc8[sl];
+  if (!S.e4m3_final) return (double)__bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t *>(S.t8)[o]));
+  return (double)e4m3_to_float(S.t8[(size_t)sl * S.nb * S.nb + o]) / (double)S.sc8[sl];
 }
 
 // Dense lower triangle of a stored matrix (export): one CTA per (tile, column).
@@ -520,33 +529,8 @@ emu_status classfmt_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p, con
     if (c == EMU_CLASS_TF32) c = cs->cls[t] = EMU_CLASS_FP32;
     cs->slot[t] = cs->nslot[c]++;
   }
-  // E4M3 storage scales: every Schur complement entry of tile (i, j) is
-  // bounded by sqrt(max_r S_rr max_c S_cc) over its rows and columns (a
-  // positive semidefinite matrix's entries are bounded by its diagonal), so
-  // s = 2^floor(log2(448 / bound)) never saturates during the factor.
-  std::vector<double> dmax(NT, 0.0);
-  {
-    const double nug_rel = p->nugget_rel;
-    double sg0 = pow(1.0, -p->sigma_exp), sg1 = pow((double)p->L, -p->sigma_exp);
-    const double nug = nug_rel * std::max(sg0 * sg0, sg1 * sg1);
-    for (long r = 0; r < A->n; r++) {
-      long l = (long)floor(sqrt((double)r));
-      while (l * l > r) l--;
-      while ((l + 1) * (l + 1) <= r) l++;
-      const double sl = pow(1.0 + (double)l, -p->sigma_exp);
-      dmax[r / nb] = std::max(dmax[r / nb], sl * sl + nug);
-    }
-    for (int i = 0; i < NT; i++)
-      if ((long)(i + 1) * nb > A->n) dmax[i] = std::max(dmax[i], 1.0);  // the padding's unit diagonal
-  }
+  // E4M3 scales are set when each tile is solved (its final codes)
   std::vector<float> sc8(std::max(1, cs->nslot[EMU_CLASS_E4M3]), 1.0f);
-  for (int j = 0; j < NT; j++)
-    for (int i = j; i < NT; i++) {
-      long t = tile_index(i, j, NT);
-      if (cs->cls[t] != EMU_CLASS_E4M3) continue;
-      const double bound = sqrt(dmax[i] * dmax[j]);
-      sc8[cs->slot[t]] = (float)exp2(floor(log2(448.0 / bound)));
-    }
   cudaStream_t st = ctx->stream;
   auto alloc = [&](void **q, size_t bytes) -> cudaError_t {
     return bytes ? cudaMallocAsync(q, bytes, st) : cudaSuccess;
@@ -555,7 +539,7 @@ emu_status classfmt_build(emu_ctx *ctx, emu_mat *A, const emu_cov_params *p, con
   if (e == cudaSuccess) e = alloc((void **)&cs->t64, cs->nslot[EMU_CLASS_FP64] * te * sizeof(double));
   if (e == cudaSuccess) e = alloc((void **)&cs->t32, cs->nslot[EMU_CLASS_FP32] * te * sizeof(float));
   if (e == cudaSuccess) e = alloc((void **)&cs->t16, cs->nslot[EMU_CLASS_BF16] * te * sizeof(uint16_t));
-  if (e == cudaSuccess) e = alloc((void **)&cs->t8, cs->nslot[EMU_CLASS_E4M3] * te);
+  if (e == cudaSuccess) e = alloc((void **)&cs->t8, cs->nslot[EMU_CLASS_E4M3] * te * 2);  // BF16 working values
   if (e == cudaSuccess) e = alloc((void **)&cs->sc8, sc8.size() * sizeof(float));
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EMU_ENOMEM : emu_cuda_fail(ctx, e, "class arenas");
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(cs->d_slot, cs->slot.data(), A->ntiles * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -656,7 +640,6 @@ emu_status build_cplan(emu_ctx *ctx, emu_mat *A, ClassPlan *P) {
           it.sa = f8 ? pi : -1;
           it.sb = f8 ? pj : -1;
           it.oc = c;
-          it.osc = f8 ? SL(i, j) : 0;
           items.push_back(it);
           const double f = 2.0 * gemm_tc::BM * gemm_tc::BN * nb;
           sp.tc[g].n++;
@@ -879,7 +862,7 @@ emu_status classfmt_factor(emu_ctx *ctx, emu_mat *A) {
     }
     return e;
   };
-  gemm_tc::Outputs outs{cs->t32, cs->t16, cs->t8, cs->sc8};
+  gemm_tc::Outputs outs{cs->t32, cs->t16, reinterpret_cast<uint16_t *>(cs->t8)};
   auto update_group = [&](int k, int g, int max_ctas) -> emu_status {
     const CStep &sp = P->steps[k];
     if (sp.g64[g].n > 0) {
@@ -1176,7 +1159,6 @@ emu_status classfmt_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long
           it.cols_valid = s - nbk * gemm_tc::BN;
           it.sa = it.sb = -1;
           it.oc = EMU_CLASS_FP64;
-          it.osc = 0;
           items.push_back(it);
         }
     int4 *d_jobs = nullptr;
@@ -1215,7 +1197,8 @@ emu_status classfmt_sample(emu_ctx *ctx, const emu_mat *L, const double *Z, long
 // ------------------------------------------------------------------ export
 emu_status classfmt_export(emu_ctx *ctx, const emu_mat *A, double *dOut, long ld) {
   const ClassStore *cs = A->cs;
-  TileSrc S{A->d_cls, cs->d_slot, cs->t64, cs->t32, cs->t16, cs->t8, cs->sc8, A->nb, A->nt, 0};
+  TileSrc S{A->d_cls, cs->d_slot, cs->t64, cs->t32, cs->t16, cs->t8, cs->sc8, A->nb, A->nt, 0,
+            A->state != MAT_COV};
   EMU_CUDA_TRY(ctx, cudaMemset2DAsync(dOut, ld * sizeof(double), 0, (size_t)A->n * sizeof(double), A->n, ctx->stream));
   k_export_class<<<dim3((unsigned)A->ntiles, A->nb), 128, 0, ctx->stream>>>(S, A->n, dOut, ld);
   EMU_LAUNCHED(ctx);
@@ -1234,14 +1217,14 @@ emu_status factor_backward_error_est(emu_ctx *ctx, const emu_mat *A, const emu_c
   TileSrc S{};
   int *ident = nullptr;
   if (A->cs) {
-    S = TileSrc{A->d_cls, A->cs->d_slot, A->cs->t64, A->cs->t32, A->cs->t16, A->cs->t8, A->cs->sc8, nb, NT, 0};
+    S = TileSrc{A->d_cls, A->cs->d_slot, A->cs->t64, A->cs->t32, A->cs->t16, A->cs->t8, A->cs->sc8, nb, NT, 0, 1};
   } else {
     std::vector<int> id(A->ntiles);
     for (long t = 0; t < A->ntiles; t++) id[t] = (int)t;
     EMU_CUDA_TRY(ctx, cudaMallocAsync(&ident, A->ntiles * sizeof(int), st));
     EMU_CUDA_TRY(ctx, cudaMemcpyAsync(ident, id.data(), A->ntiles * sizeof(int), cudaMemcpyHostToDevice, st));
     EMU_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    S = TileSrc{A->d_cls, ident, A->t64, A->t32, nullptr, nullptr, nullptr, nb, NT, 1};
+    S = TileSrc{A->d_cls, ident, A->t64, A->t32, nullptr, nullptr, nullptr, nb, NT, 1, 0};
     if (A->state == MAT_FACTOR64) {
       // every tile of a plain FP64 factor is in the FP64 arena
       unsigned char *z = nullptr;

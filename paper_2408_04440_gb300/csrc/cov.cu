@@ -155,19 +155,18 @@ struct StoreF64 {
 struct StoreNone {
   __device__ void operator()(int, int, double) const {}
 };
-// Class-format storage: the entry rounded to the tile's class (nearest; E4M3
-// codes of v * s, saturating, s a power of two).
+// Class-format storage: the entry rounded to the tile's class (nearest);
+// E4M3-class tiles hold BF16 working values until the factor solves them.
 struct StoreClass {
   int cls, nb;
   size_t base;
   ClassArenas ar;
-  double s8;
   __device__ void operator()(int r, int c, double v) const {
     const size_t e = base + r + (size_t)c * nb;
     if (cls == EMU_CLASS_FP64) ar.t64[e] = v;
     else if (cls == EMU_CLASS_FP32) ar.t32[e] = (float)v;
     else if (cls == EMU_CLASS_BF16) ar.t16[e] = __bfloat16_as_ushort(__double2bfloat16(v));
-    else ar.t8[e] = (uint8_t)__nv_cvt_double_to_fp8(v * s8, __NV_SATFINITE, __NV_E4M3);
+    else reinterpret_cast<uint16_t *>(ar.t8)[e] = __bfloat16_as_ushort(__double2bfloat16(v));
   }
 };
 
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(kThreads)
   int ti, tj;
   tile_coords(t, NT, &ti, &tj);
   const int c = ar.cls[t], sl = ar.slot[t];
-  StoreClass st{c, nb, (size_t)sl * nb * nb, ar, c == EMU_CLASS_E4M3 ? (double)ar.sc8[sl] : 1.0};
+  StoreClass st{c, nb, (size_t)sl * nb * nb, ar};
   (void)cov_tile_chunk_t(L, n, nb, ti, tj, blockIdx.y, sigma, rho, *nugget, st);
 }
 

@@ -59,7 +59,8 @@ struct emu_ctx {
   int *d_status = nullptr;    // ST_WORDS ints
   int *h_status = nullptr;    // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  uint64_t launches = 0;
+  uint64_t launches = 0;       // kernels of this library, graph nodes included
+  uint64_t host_launches = 0;  // launch calls the host made (a graph replay counts once)
   std::string last_error;
   bool prof = false;
   std::vector<ProfRec> prof_open;   // recorded, not yet collected
@@ -176,6 +177,7 @@ emu_status emu_cuda_fail(emu_ctx *ctx, cudaError_t e, const char *what);
 #define EMU_LAUNCHED(ctx)                                                   \
   do {                                                                      \
     (ctx)->launches++;                                                      \
+    (ctx)->host_launches++;                                                 \
     cudaError_t _e = cudaGetLastError();                                    \
     if (_e != cudaSuccess) return emu_cuda_fail((ctx), _e, "kernel launch"); \
   } while (0)

@@ -24,7 +24,6 @@
 // of the next.
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
 
 #include "gemm_tc.h"
 #include "tc.cuh"
@@ -249,9 +248,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::tmem_ld_wait();
         // all 32 loads of the chunk are issued before any store, so their
         // latencies overlap (each warp-wide access is one 128-byte column piece)
-        if (mode == TC_SUB_CLASS && item.oc == EMU_CLASS_BF16) {
-          // BF16 storage: c - acc rounded to nearest BF16
-          uint16_t *o = outs.bf16 + item.out_off + row + (long)(ch * 32) * ldo;
+        if (mode == TC_SUB_CLASS && (item.oc == EMU_CLASS_BF16 || item.oc == EMU_CLASS_E4M3)) {
+          // BF16 storage (the E4M3 class's working tiles too): c - acc rounded to nearest BF16
+          uint16_t *o = (item.oc == EMU_CLASS_BF16 ? outs.bf16 : outs.e8w) + item.out_off + row +
+                        (long)(ch * 32) * ldo;
           unsigned short c[32];
 #pragma unroll
           for (int x = 0; x < 32; x++) c[x] = __ldcg((const unsigned short *)(o + (long)x * ldo));
@@ -260,21 +260,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int x = 0; x < 32; x++) {
             const float v = __bfloat162float(__ushort_as_bfloat16(c[x])) - __uint_as_float(r[x]) * sc;
             __stcg((unsigned short *)(o + (long)x * ldo), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
-          }
-        } else if (mode == TC_SUB_CLASS && item.oc == EMU_CLASS_E4M3) {
-          // E4M3 storage: codes of the value q / so, re-encoded (saturating, nearest)
-          uint8_t *o = outs.e8 + item.out_off + row + (long)(ch * 32) * ldo;
-          unsigned char c[32];
-#pragma unroll
-          for (int x = 0; x < 32; x++) c[x] = __ldcg((const unsigned char *)(o + (long)x * ldo));
-          const float sc = (item.sa >= 0) ? 1.0f / (ops.scale8[item.sa] * ops.scale8[item.sb]) : 1.0f;
-          const float so = outs.sc8[item.osc], iso = 1.0f / so;
-#pragma unroll
-          for (int x = 0; x < 32; x++) {
-            const float q = __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c[x], __NV_E4M3)));
-            const float v = q * iso - __uint_as_float(r[x]) * sc;
-            __stcg((unsigned char *)(o + (long)x * ldo),
-                   (unsigned char)__nv_cvt_float_to_fp8(v * so, __NV_SATFINITE, __NV_E4M3));
           }
         } else if (mode == TC_SUB_F32 || mode == TC_SUB_CLASS) {
           float *o = (mode == TC_SUB_F32 ? out32 : outs.f32) + item.out_off + row + (long)(ch * 32) * ldo;
@@ -434,7 +419,7 @@ emu_status launch(emu_ctx *ctx, const Operands &ops, const Item *d_items, int ni
   static std::atomic<uint64_t> attr_done{0};
   EMU_CUDA_TRY(ctx, smem_limit_once(attr_done, ctx->device, (const void *)k_tc_gemm, SMEM_BYTES));
   int grid = nitems < max_ctas ? nitems : max_ctas;
-  const Outputs none{nullptr, nullptr, nullptr, nullptr};
+  const Outputs none{nullptr, nullptr, nullptr};
   k_tc_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(ops, d_items, nitems, d_segs, ksteps, mode, out32,
                                                          out64, none, ldo, ctx->d_status);
   EMU_LAUNCHED(ctx);

@@ -9,9 +9,10 @@
 // applies the epilogue:
 //   mode TC_SUB_F32: out32[off + r + c*ldo] -= acc   (trailing tile update)
 //   mode TC_ADD_F64: out64[off + r + c*ldo] += acc   (sampling, r/c bounded)
-//   mode TC_SUB_CLASS: out[off + r + c*ldo] -= acc in the format of the
-//     item's output class oc (FP32, BF16 rounded to nearest, or E4M3 codes
-//     of the value q / sc8[osc], saturating): class-format tile storage
+//   mode TC_SUB_CLASS: out[off + r + c*ldo] -= acc in the working format of
+//     the item's output class oc: FP32, or BF16 rounded to nearest (the BF16
+//     class, and the E4M3 class before its tiles are solved): class-format
+//     tile storage
 #pragma once
 #include <cuda.h>
 
@@ -40,16 +41,16 @@ struct Item {
   long out_off;
   int rows_valid, cols_valid;  // TC_ADD_F64 only
   int sa, sb;                  // E4M3 items: tiles whose scales multiply A and B (else -1)
-  int oc = EMU_CLASS_FP32;     // TC_SUB_CLASS: output format
-  int osc = 0;                 // TC_SUB_CLASS, E4M3 output: index of its scale
+  int oc = EMU_CLASS_FP32;     // TC_SUB_CLASS: output class
+  int pad2 = 0;
 };
 
-// Output arenas of a TC_SUB_CLASS launch (element offsets out_off in each).
+// Output arenas of a TC_SUB_CLASS launch (element offsets out_off in each):
+// FP32 tiles, BF16 tiles, and the BF16 working tiles of the E4M3 class.
 struct Outputs {
   float *f32;
   uint16_t *bf16;
-  uint8_t *e8;
-  const float *sc8;
+  uint16_t *e8w;
 };
 
 // Operand sources of a launch: BF16 pieces (A box 128 x 32, B box 256 x 32,

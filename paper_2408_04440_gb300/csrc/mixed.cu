@@ -929,10 +929,11 @@ static emu_status factor_mixed_launch(emu_ctx *ctx, emu_mat *A, MixedPlan *P, Mi
   if (M->exec && M->key == key) {
     EMU_CUDA_TRY(ctx, cudaGraphLaunch(M->exec, user));
     ctx->launches += M->graph_launches;
+    ctx->host_launches++;
     return EMU_OK;
   }
   if (!M->cap) EMU_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
-  const uint64_t l0 = ctx->launches;
+  const uint64_t l0 = ctx->launches, h0 = ctx->host_launches;
   ctx->stream = M->cap;
   // relaxed: the launchers set kernel attributes while the streams are captured
   cudaError_t e = cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeRelaxed);
@@ -942,6 +943,7 @@ static emu_status factor_mixed_launch(emu_ctx *ctx, emu_mat *A, MixedPlan *P, Mi
   ctx->stream = user;
   const uint64_t nl = ctx->launches - l0;
   ctx->launches = l0;
+  ctx->host_launches = h0;
   if (s != EMU_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     M->key.clear();
@@ -968,6 +970,7 @@ static emu_status factor_mixed_launch(emu_ctx *ctx, emu_mat *A, MixedPlan *P, Mi
   M->graph_launches = nl;
   EMU_CUDA_TRY(ctx, cudaGraphLaunch(M->exec, user));
   ctx->launches += nl;
+  ctx->host_launches++;
   return EMU_OK;
 }
 

@@ -87,18 +87,10 @@ def test_classfmt_build_stores_each_tile_in_its_class(E, ctx, L, nb, beta, eps):
                 assert np.all(err <= 1e-15 * np.abs(ref))
             elif c == 1:
                 assert np.all(err <= (2.0**-24 + 1e-15) * np.abs(ref))
-            elif c == 3:
-                assert np.all(err <= (2.0**-8 + 1e-15) * np.abs(ref))
             else:
-                # E4M3 with the storage scale s = 2^floor(log2(448 / bound)),
-                # bound = sqrt(max S_rr max S_cc) over the tile's rows and
-                # columns: half a unit in the last place of a 4-bit
-                # significand, or of the subnormal step 2^-9 / s
-                def dmax(b):
-                    d = np.diag(S)[b * nb:min(n, (b + 1) * nb)].max()
-                    return max(d, 1.0) if (b + 1) * nb > n else d
-                bound = np.sqrt(dmax(i) * dmax(j))
-                assert np.all(err <= 2.0**-4 * np.abs(ref) + 2.0**-17 * bound), (i, j)
+                # BF16, and the E4M3 class's BF16 working values (its codes are
+                # written when the factor solves the tile)
+                assert np.all(err <= (2.0**-8 + 1e-15) * np.abs(ref))
     print(f"L={L} eps={eps:g}: tiles per class {np.bincount(cls[np.tril_indices(NT)], minlength=5)}")
 
 
