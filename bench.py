@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--nb", type=int, default=512)
     ap.add_argument("--beta", type=float, default=8.0)
     ap.add_argument("--eps", type=float, default=1e-8)
+    ap.add_argument("--mask", type=int, default=MASK_FP64_FP32_BF16,
+                    help="classes the norm rule may use (bit c = class c: 1 FP64, 2 FP32, 4 TF32, 8 BF16, 16 E4M3)")
     ap.add_argument("--samples", type=int, default=256)
     ap.add_argument("--seed", type=int, default=None, help="sample seed (default: 1 single, 3 batched)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
@@ -67,7 +69,9 @@ def parse():
 
 
 def workload_name(a) -> str:
-    return (f"L={a.L} n={a.L * a.L} nb={a.nb} beta={a.beta:g}: adaptive FP64/FP32/BF16 tile Cholesky at "
+    names = ("FP64", "FP32", "TF32", "BF16", "E4M3")
+    cls = "/".join(nm for c, nm in enumerate(names) if (a.mask | 1) >> c & 1)
+    return (f"L={a.L} n={a.L * a.L} nb={a.nb} beta={a.beta:g}: adaptive {cls} tile Cholesky at "
             f"eps={a.eps:g}, FP32 accumulate, + {a.samples} samples seed {a.seed}")
 
 
@@ -177,7 +181,7 @@ def run_ours(a):
 
     def step():
         A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
-        info = E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=MASK_FP64_FP32_BF16)
+        info = E.emu_potrf_mp(ctx, A, eps=a.eps, prec_mask=a.mask)
         factor_ms.append(info.ms)
         E.emu_sample(ctx, A, s, seed=seed, out=Y)
         A.free()
