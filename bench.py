@@ -238,11 +238,14 @@ def run_ours(a):
                                       "share": round(v["ms"] / step_ms, 4)} for k, v in prof.items() if v["launches"]}
         peaks = load_peaks()
         peaks.update(alu)
-        roof = roofline(prof, peaks)
+        roof = roofline(prof, peaks, (a.L, a.nb, a.eps, a.mask))
         extra["measured_peaks"] = dict(alu, **tensor_peaks())
 
         # accuracy: backward error on 64 sampled rows against the GPU-built covariance
         extra["backward_error_rows64"] = backward_error_rows(E, ctx, a, rows=64)
+        extra["backward_error_note"] = ("||(L L^T - S)[rows, :]||_F / ||S[rows, :]||_F over 64 sampled rows, S the "
+                                        "GPU-built covariance; the full backward error against the oracle's S is "
+                                        "checked in tests/test_gpu_full_size.py")
 
         if not a.no_fp64:
             A = E.emu_cov_build(ctx, a.L, a.beta, a.nb)
@@ -287,9 +290,10 @@ def run_ours(a):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of the current kernel code (profiles/); None where no capture of the
-# bench's own launches applies (the FP64 update's launches differ in size).
-TRAFFIC = {}
+# capture of the current kernel code, keyed by (group, L, nb, eps, mask) of the
+# captured workload (profiles/k_tc_gemm_L128_n16384_traffic.md: 112 launches per
+# factor, 11.15 GB); None for any other workload or group.
+TRAFFIC = {("tc_factor", 128, 512, 1e-8, MASK_FP64_FP32_BF16): 99.6e6}
 
 
 ALU_NOTES = {
@@ -349,8 +353,9 @@ def tensor_peaks() -> dict:
     return out
 
 
-def roofline(prof: dict, peaks: dict) -> dict:
-    """Roofline of the kernel group with the largest device time in the step."""
+def roofline(prof: dict, peaks: dict, wl=None) -> dict:
+    """Roofline of the kernel group with the largest device time in the step; wl = (L, nb, eps, mask) of the
+    workload, for the DRAM traffic of its ncu capture."""
     group = max(prof, key=lambda k: prof[k]["ms"])
     g = prof[group]
     per_launch_ms = g["ms"] / max(g["launches"], 1)
@@ -362,7 +367,8 @@ def roofline(prof: dict, peaks: dict) -> dict:
         achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
         peak = bf16 * g["flops"] / g["mma_flops"]
         return {"kernel": group, "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": TRAFFIC.get((group,) + tuple(wl)) if wl else None,
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
                 "peak_note": f"bf16 sustained {bf16} TF/s {src}, weighted by the class mix"}
     if group in ALU_GROUPS:
@@ -371,7 +377,8 @@ def roofline(prof: dict, peaks: dict) -> dict:
         psrc = "measured in this run" if f"{unit}_fma_tflops" in peaks else "of an earlier probe run"
         achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12
         return {"kernel": group, "bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(group),
+                "frac": round(achieved / peak, 4),
+                "traffic": TRAFFIC.get((group,) + tuple(wl)) if wl else None,
                 "per_launch_ms": round(per_launch_ms, 4), "launches": g["launches"],
                 "peak_note": f"{unit.upper()} FMA-loop peak {psrc}; " + ALU_NOTES.get(group, "")}
     hbm = peaks.get("hbm_gbs") or 6800.0

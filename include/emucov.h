@@ -405,8 +405,14 @@ emu_status emu_sample_host(emu_ctx *ctx, const emu_mat *L, int nsamples,
                            long ldy);
 
 /* ------------------------------------------------------------------ solves */
-/* X = (L L^T)^{-1} B with the factor L (two triangular solves in the stored
- * tile precisions).  dB, dX: n x nrhs, column-major; dX may equal dB. */
+/* X = (L L^T)^{-1} B with the factor L: a forward and a backward triangular
+ * sweep over the tile rows.  A plain FP64 factor solves in FP64.  A mixed
+ * factor solves in FP32 arithmetic: the diagonal blocks against FP32 values
+ * of their FP64 factor tiles, the off-diagonal tiles as stored (FP64 tiles
+ * rounded to FP32, FP32 masters as they are), each tile's product accumulated
+ * in FP32 and added to the FP64 right-hand sides (it is the preconditioner of
+ * emu_solve_refine, whose residual and update are FP64).  dB, dX: n x nrhs,
+ * column-major; dX may equal dB. */
 emu_status emu_potrs(emu_ctx *ctx, const emu_mat *L, const double *dB,
                      long ldb, double *dX, long ldx, int nrhs);
 

@@ -107,65 +107,79 @@ __global__ void k_encode(const int4 *__restrict__ jobs, int nb, double *__restri
   }
 }
 
-// E4M3-class panel tiles, one CTA per job {panel index, slot, -, -}: the
-// tile's amax, the scale s = 2^floor(log2(448 / amax)) (1 for a zero tile),
-// the codes q = e4m3(x s) (saturating, nearest) into the first half of the
-// slot (column-major; the slot's BF16 working values are no longer needed)
-// and, transposed, into the panel's FP8 operand copy (row-major) with scale
-// s; the value q / s replaces x in the FP32 panel buffer, and the operand
-// pieces become (bf16(q / s), 0, 0) (exact: an E4M3 value fits BF16).
-__global__ void __launch_bounds__(1024) k_encode_e4m3(const int4 *__restrict__ jobs, int nb, uint8_t *__restrict__ t8,
-                                                      float *__restrict__ sc8, float *__restrict__ P32,
-                                                      uint16_t *__restrict__ Pop, uint8_t *__restrict__ P8,
-                                                      float *__restrict__ Psc8, const int *st) {
+// E4M3-class panel tiles, jobs {panel index, slot, -, -}: the tile's amax
+// (k_amax_tiles: partial maxima of 64 CTAs per tile folded by an integer
+// atomicMax on the bits, which order non-negative floats), then
+// (k_encode_e4m3, one CTA per 32 x 32 block and tile) the scale
+// s = 2^floor(log2(448 / amax)) (1 for a zero tile), the codes q = e4m3(x s)
+// (saturating, nearest) into the first half of the slot (column-major; the
+// slot's BF16 working values are no longer needed) and, transposed, into the
+// panel's FP8 operand copy (row-major) with scale s; the value q / s replaces
+// x in the FP32 panel buffer, and the operand pieces become (bf16(q / s), 0, 0)
+// (exact: an E4M3 value fits BF16).
+__global__ void __launch_bounds__(256) k_amax_tiles(const int4 *__restrict__ jobs, int nb,
+                                                    const float *__restrict__ P32, unsigned *__restrict__ amax_bits,
+                                                    const int *st) {
   if (failed(st)) return;
-  __shared__ float red[32];
-  __shared__ float s_scale;
-  __shared__ float blk[TB][TB + 1];
-  const int4 j = jobs[blockIdx.x];
+  const int4 j = jobs[blockIdx.y];
   const size_t te = (size_t)nb * nb;
-  float *x = P32 + (size_t)j.x * te;
-  float amax = 0.0f;
-  for (size_t e = threadIdx.x; e < te; e += blockDim.x) amax = fmaxf(amax, fabsf(x[e]));
-  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
-    float s = 1.0f;
-    if (m > 0.0f) s = exp2f(floorf(log2f(448.0f / m)));
-    // guard the float rounding of log2f at exact powers of two
-    while (m * s > 448.0f) s *= 0.5f;
-    s_scale = s;
+  const float4 *x = reinterpret_cast<const float4 *>(P32 + (size_t)j.x * te);
+  float m = 0.0f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < te / 4; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = x[e];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&amax_bits[j.x], __float_as_uint(m));
+}
+
+__device__ inline float e4m3_scale(float m) {
+  if (!(m > 0.0f)) return 1.0f;
+  // 448 / m = f 2^e with f in [0.5, 1): the largest power of two not above it is 2^(e-1)
+  int e = 1;
+  frexpf(448.0f / m, &e);
+  return ldexpf(1.0f, e - 1);
+}
+
+__global__ void __launch_bounds__(256) k_encode_e4m3(const int4 *__restrict__ jobs, int nb, uint8_t *__restrict__ t8,
+                                                     float *__restrict__ sc8, float *__restrict__ P32,
+                                                     uint16_t *__restrict__ Pop, uint8_t *__restrict__ P8,
+                                                     float *__restrict__ Psc8, const unsigned *__restrict__ amax_bits,
+                                                     const int *st) {
+  if (failed(st)) return;
+  __shared__ float blk[TB][TB + 1];
+  const int4 j = jobs[blockIdx.y];
+  const size_t te = (size_t)nb * nb;
+  const float s = e4m3_scale(__uint_as_float(amax_bits[j.x])), inv = 1.0f / s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc8[j.y] = s;
     Psc8[j.x] = s;
   }
-  __syncthreads();
-  const float s = s_scale, inv = 1.0f / s;
+  const int nbb = nb / TB;
+  const int rb = blockIdx.x % nbb, cb = blockIdx.x / nbb;
+  const int tx = threadIdx.x & (TB - 1), ty = threadIdx.x >> 5;  // 32 x 8
+  float *x = P32 + (size_t)j.x * te;
   uint8_t *q8 = t8 + (size_t)j.y * 2 * te;
   uint8_t *p8 = P8 + (size_t)j.x * te;
   uint16_t *p0 = Pop + (size_t)j.x * 3 * te;
-  const int tx = threadIdx.x & (TB - 1), ty = threadIdx.x >> 5;  // 32 x 32
-  const int nbb = nb / TB;
-  for (int b = 0; b < nbb * nbb; b++) {
-    const int rb = b % nbb, cb = b / nbb;
-    // element (r, c) = (rb*32 + tx, cb*32 + ty): column-major reads
-    const size_t e = (size_t)(rb * TB + tx) + (size_t)(cb * TB + ty) * nb;
+  for (int yy = ty; yy < TB; yy += 8) {
+    // element (r, c) = (rb*32 + tx, cb*32 + yy): column-major, coalesced over tx
+    const size_t e = (size_t)(rb * TB + tx) + (size_t)(cb * TB + yy) * nb;
     const uint8_t q = float_to_e4m3(x[e] * s);
     q8[e] = q;
     const float v = e4m3_to_float(q) * inv;
     x[e] = v;
-    blk[ty][tx] = v;
-    __syncthreads();
-    // transposed: row r = rb*32 + ty, column c = cb*32 + tx (row-major writes)
-    const float w = blk[tx][ty];
-    const size_t f = (size_t)(rb * TB + ty) * nb + (cb * TB + tx);
+    blk[yy][tx] = v;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < TB; yy += 8) {
+    // transposed: row r = rb*32 + yy, column c = cb*32 + tx (row-major, coalesced over tx)
+    const float w = blk[tx][yy];
+    const size_t f = (size_t)(rb * TB + yy) * nb + (cb * TB + tx);
     p8[f] = float_to_e4m3(w * s);
     p0[f] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
     p0[f + te] = 0;
     p0[f + 2 * te] = 0;
-    __syncthreads();
   }
 }
 
@@ -459,6 +473,7 @@ struct ClassPlan {
   float *Psc8 = nullptr;
   uint16_t *digits = nullptr;
   int *exps = nullptr;
+  unsigned *amax = nullptr;    // per panel index: amax bits of the E4M3-class tiles being encoded
   float *lkk32 = nullptr;      // FP32 copies of L_kk (two slots)
   uint16_t *lkkp = nullptr;    // their pieces (tensor-core TRSM)
   double *ls64 = nullptr, *rinv64 = nullptr;  // pre-scaled L_kk blocks for the FP64 TRSM
@@ -474,8 +489,8 @@ struct ClassPlan {
 void cplan_free(ClassPlan *P) {
   if (!P) return;
   for (void *q : {(void *)P->d_blob, (void *)P->P64, (void *)P->P32, (void *)P->Pop, (void *)P->P8,
-                  (void *)P->Psc8, (void *)P->digits, (void *)P->exps, (void *)P->lkk32, (void *)P->lkkp,
-                  (void *)P->ls64, (void *)P->rinv64})
+                  (void *)P->Psc8, (void *)P->digits, (void *)P->exps, (void *)P->amax, (void *)P->lkk32,
+                  (void *)P->lkkp, (void *)P->ls64, (void *)P->rinv64})
     if (q) cudaFreeAsync(q, P->stream);
   delete P;
 }
@@ -765,6 +780,7 @@ emu_status build_cplan(emu_ctx *ctx, emu_mat *A, ClassPlan *P) {
   if (s == EMU_OK) s = alloc((void **)&P->Psc8, np * sizeof(float));
   if (s == EMU_OK) s = alloc((void **)&P->digits, np * gemm64::NS * te * sizeof(uint16_t));
   if (s == EMU_OK) s = alloc((void **)&P->exps, np * nb * sizeof(int));
+  if (s == EMU_OK) s = alloc((void **)&P->amax, np * sizeof(unsigned));
   if (s == EMU_OK) s = alloc((void **)&P->lkk32, 2 * te * sizeof(float));
   if (s == EMU_OK) s = alloc((void **)&P->lkkp, 2 * 3 * te * sizeof(uint16_t));
   if (s == EMU_OK) s = alloc((void **)&P->ls64, 2 * (size_t)nb * 32 * sizeof(double));
@@ -846,9 +862,11 @@ emu_status classfmt_factor(emu_ctx *ctx, emu_mat *A) {
       EMU_LAUNCHED(ctx);
     }
     if (pt.enc8.n > 0) {
-      ProfScope ps(ctx, PROF_SPLIT, 0.0, 15.0 * pt.enc8.n * te);
-      k_encode_e4m3<<<pt.enc8.n, 1024, 0, ctx->stream>>>(P->d_j4 + pt.enc8.off, nb, cs->t8, cs->sc8, P->P32,
-                                                         P->Pop, P->P8, P->Psc8, st);
+      ProfScope ps(ctx, PROF_SPLIT, 0.0, 19.0 * pt.enc8.n * te);
+      k_amax_tiles<<<dim3(64, pt.enc8.n), 256, 0, ctx->stream>>>(P->d_j4 + pt.enc8.off, nb, P->P32, P->amax, st);
+      EMU_LAUNCHED(ctx);
+      k_encode_e4m3<<<dim3((nb / TB) * (nb / TB), pt.enc8.n), 256, 0, ctx->stream>>>(
+          P->d_j4 + pt.enc8.off, nb, cs->t8, cs->sc8, P->P32, P->Pop, P->P8, P->Psc8, P->amax, st);
       EMU_LAUNCHED(ctx);
     }
     if (pt.quant.n > 0 &&
@@ -887,6 +905,7 @@ emu_status classfmt_factor(emu_ctx *ctx, emu_mat *A) {
     ctx->stream = ctx->crit;
     if (k >= RING) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - RING, E_END), 0));  // ring slot free
     EMU_CUDA_TRY(ctx, cudaMemsetAsync(P->exps + (size_t)ps_ * NT * nb, 0, (size_t)NT * nb * sizeof(int), ctx->crit));
+    EMU_CUDA_TRY(ctx, cudaMemsetAsync(P->amax + (size_t)ps_ * NT, 0, (size_t)NT * sizeof(unsigned), ctx->crit));
     if ((s = launch_potrf64_ptr(ctx, Lkk, nb, k)) != EMU_OK) break;
     if (sp.low_panel) {
       if (P->tc_trsm) {
@@ -952,8 +971,8 @@ emu_status classfmt_factor(emu_ctx *ctx, emu_mat *A) {
   EMU_CUDA_TRY(ctx, cudaStreamSynchronize(user));  // dslots
   // the panel ring is no longer needed; the plan's counts stay for info
   for (void **q : {(void **)&P->P64, (void **)&P->P32, (void **)&P->Pop, (void **)&P->P8, (void **)&P->Psc8,
-                   (void **)&P->digits, (void **)&P->exps, (void **)&P->lkk32, (void **)&P->lkkp, (void **)&P->ls64,
-                   (void **)&P->rinv64, (void **)&P->d_blob}) {
+                   (void **)&P->digits, (void **)&P->exps, (void **)&P->amax, (void **)&P->lkk32, (void **)&P->lkkp,
+                   (void **)&P->ls64, (void **)&P->rinv64, (void **)&P->d_blob}) {
     if (*q) cudaFreeAsync(*q, user);
     *q = nullptr;
   }

@@ -147,9 +147,20 @@ __global__ void __launch_bounds__(1024)
   long t = tiles[blockIdx.x];
   size_t plane = (size_t)nb * nb;
   const uint16_t *x0 = op + (size_t)t * 3 * plane;
+  // 16-byte accesses (eight entries per thread and load), so that the
+  // loads of a tile are in flight together
+  const uint4 *x8 = reinterpret_cast<const uint4 *>(x0);
+  const size_t n8 = plane / 8;
   float amax = 0.f;
-  for (size_t e = threadIdx.x; e < plane; e += blockDim.x)
-    amax = fmaxf(amax, fabsf(__bfloat162float(__ushort_as_bfloat16(x0[e]))));
+  for (size_t e = threadIdx.x; e < n8; e += blockDim.x) {
+    const uint4 v = __ldg(x8 + e);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      amax = fmaxf(amax, fabsf(__uint_as_float(w[h] << 16)));
+      amax = fmaxf(amax, fabsf(__uint_as_float(w[h] & 0xffff0000u)));
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
   __syncthreads();
@@ -164,10 +175,20 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   float s = s_scale;
-  uint8_t *q = op8 + (size_t)t * plane;
-  for (size_t e = threadIdx.x; e < plane; e += blockDim.x)
-    q[e] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(__ushort_as_bfloat16(x0[e])) * s, __NV_SATFINITE,
-                                          __NV_E4M3);
+  uint2 *q8 = reinterpret_cast<uint2 *>(op8 + (size_t)t * plane);
+  for (size_t e = threadIdx.x; e < n8; e += blockDim.x) {
+    const uint4 v = __ldg(x8 + e);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t o[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      // a BF16 value is the high half of the FP32 with the same bits
+      const uint32_t lo = __nv_cvt_float_to_fp8(__uint_as_float(w[h] << 16) * s, __NV_SATFINITE, __NV_E4M3);
+      const uint32_t hi = __nv_cvt_float_to_fp8(__uint_as_float(w[h] & 0xffff0000u) * s, __NV_SATFINITE, __NV_E4M3);
+      o[h >> 1] |= (lo | (hi << 8)) << (16 * (h & 1));
+    }
+    q8[e] = make_uint2(o[0], o[1]);
+  }
 }
 
 // SIMT FP32 panel TRSM for the low-precision tiles of column k, used where
