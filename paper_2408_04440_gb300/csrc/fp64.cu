@@ -218,18 +218,33 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
         xr[cr][ct] = va * rinv[ct];
         xr[cr + 8][ct] = vb * rinv[ct];
       }
-    } else if (q >= 0) {
-      // publish L_{q,q} and its pivot reciprocals
-      if (ir >= ic) __stcg(gp(q, q, ir, ic), a[ir][ic]);
-      if (ir >= ic + 8) __stcg(gp(q, q, ir, ic + 8), a[ir][ic + 8]);
-      if (u < PB) __stcg(rinv_g + q * PB + u, rinv[u]);
-      bar_sync_128(2);
-      if (u == 0) {
-        fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
-        atomicExch(&state[q * nbb + q], q + 1);
+      // X_{s,q} written (the I/O warps publish it); then wait until the I/O
+      // warps hold L_{q,q}, which this step's leaf overwrites: the leaf does
+      // not wait for the publishing fence
+      bar_arrive_256(5);
+      bar_sync_256(4);
+    } else {
+      // publish L_{q,q} and its pivot reciprocals, read out of shared memory
+      // before the compute warps' leaf overwrites them
+      double la = 0.0, lb = 0.0, lr = 0.0;
+      if (q >= 0) {
+        la = a[ir][ic];
+        lb = a[ir][ic + 8];
+        if (u < PB) lr = rinv[u];
       }
+      bar_arrive_256(4);
+      if (q >= 0) {
+        if (ir >= ic) __stcg(gp(q, q, ir, ic), la);
+        if (ir >= ic + 8) __stcg(gp(q, q, ir, ic + 8), lb);
+        if (u < PB) __stcg(rinv_g + q * PB + u, lr);
+        bar_sync_128(2);
+        if (u == 0) {
+          fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+          atomicExch(&state[q * nbb + q], q + 1);
+        }
+      }
+      bar_sync_256(5);  // X_{s,q} is in xr
     }
-    __syncthreads();
     if (trace && tid == 0) t1 = gtimer();
     if (!io) {
       const int i = u & (PB - 1), k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;

@@ -234,43 +234,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const Item item = items[it];
+      // FP32 or BF16 output tiles: the output's columns are loaded one
+      // 32-column chunk ahead, the first chunk before the accumulator is
+      // ready (the MMAs do not write the output), so that two chunks of
+      // loads are in flight per warp
+      const bool o32 = mode == TC_SUB_F32 || (mode == TC_SUB_CLASS && item.oc == EMU_CLASS_FP32);
+      const bool o16 = mode == TC_SUB_CLASS && (item.oc == EMU_CLASS_BF16 || item.oc == EMU_CLASS_E4M3);
+      float *p32 = o32 ? (mode == TC_SUB_F32 ? out32 : outs.f32) + item.out_off + row : nullptr;
+      uint16_t *p16 = o16 ? (item.oc == EMU_CLASS_BF16 ? outs.bf16 : outs.e8w) + item.out_off + row : nullptr;
+      // E4M3 items: undo the operands' power-of-two scales (exact)
+      const float sc = (item.sa >= 0) ? 1.0f / (ops.scale8[item.sa] * ops.scale8[item.sb]) : 1.0f;
+      float nf[32];  // the next chunk's output values (BF16 outputs widened on load)
+      if (o32) {
+#pragma unroll
+        for (int x = 0; x < 32; x++) nf[x] = __ldcg(p32 + (long)x * ldo);
+      } else if (o16) {
+#pragma unroll
+        for (int x = 0; x < 32; x++)
+          nf[x] = __bfloat162float(__ushort_as_bfloat16(__ldcg((const unsigned short *)(p16 + (long)x * ldo))));
+      }
       if (!tc::mbar_wait(&sh->tfull[acc], acc_phase, abort)) {
         raise_timeout(sh, status);
         break;
       }
       tc::fence_after_sync();
-      Item item = items[it];
       uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ch++) {
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + ch * 32, r);
-        tc::tmem_ld_wait();
-        // all 32 loads of the chunk are issued before any store, so their
-        // latencies overlap (each warp-wide access is one 128-byte column piece)
-        if (mode == TC_SUB_CLASS && (item.oc == EMU_CLASS_BF16 || item.oc == EMU_CLASS_E4M3)) {
-          // BF16 storage (the E4M3 class's working tiles too): c - acc rounded to nearest BF16
-          uint16_t *o = (item.oc == EMU_CLASS_BF16 ? outs.bf16 : outs.e8w) + item.out_off + row +
-                        (long)(ch * 32) * ldo;
-          unsigned short c[32];
-#pragma unroll
-          for (int x = 0; x < 32; x++) c[x] = __ldcg((const unsigned short *)(o + (long)x * ldo));
-          const float sc = (item.sa >= 0) ? 1.0f / (ops.scale8[item.sa] * ops.scale8[item.sb]) : 1.0f;
-#pragma unroll
-          for (int x = 0; x < 32; x++) {
-            const float v = __bfloat162float(__ushort_as_bfloat16(c[x])) - __uint_as_float(r[x]) * sc;
-            __stcg((unsigned short *)(o + (long)x * ldo), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
-          }
-        } else if (mode == TC_SUB_F32 || mode == TC_SUB_CLASS) {
-          float *o = (mode == TC_SUB_F32 ? out32 : outs.f32) + item.out_off + row + (long)(ch * 32) * ldo;
+        const bool more = ch + 1 < BN / 32;
+        if (o32) {
           float c[32];
 #pragma unroll
-          for (int x = 0; x < 32; x++) c[x] = __ldcg(o + (long)x * ldo);
-          // E4M3 items: undo the operands' power-of-two scales (exact)
-          float sc = (item.sa >= 0) ? 1.0f / (ops.scale8[item.sa] * ops.scale8[item.sb]) : 1.0f;
+          for (int x = 0; x < 32; x++) c[x] = nf[x];
+          if (more) {
+            const float *q = p32 + (long)((ch + 1) * 32) * ldo;
+#pragma unroll
+            for (int x = 0; x < 32; x++) nf[x] = __ldcg(q + (long)x * ldo);
+          }
+          tc::tmem_ld_wait();
+          float *o = p32 + (long)(ch * 32) * ldo;
 #pragma unroll
           for (int x = 0; x < 32; x++) __stcg(o + (long)x * ldo, c[x] - __uint_as_float(r[x]) * sc);
+        } else if (o16) {
+          // BF16 storage (the E4M3 class's working tiles too): c - acc rounded to nearest BF16
+          float c[32];
+#pragma unroll
+          for (int x = 0; x < 32; x++) c[x] = nf[x];
+          if (more) {
+            const uint16_t *q = p16 + (long)((ch + 1) * 32) * ldo;
+#pragma unroll
+            for (int x = 0; x < 32; x++)
+              nf[x] = __bfloat162float(__ushort_as_bfloat16(__ldcg((const unsigned short *)(q + (long)x * ldo))));
+          }
+          tc::tmem_ld_wait();
+          uint16_t *o = p16 + (long)(ch * 32) * ldo;
+#pragma unroll
+          for (int x = 0; x < 32; x++) {
+            const float v = c[x] - __uint_as_float(r[x]) * sc;
+            __stcg((unsigned short *)(o + (long)x * ldo), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+          }
         } else {
+          tc::tmem_ld_wait();
           if (row < item.rows_valid) {
             double *o = out64 + item.out_off + row + (long)(ch * 32) * ldo;
             int nval = item.cols_valid - ch * 32;
