@@ -132,16 +132,25 @@ __device__ __forceinline__ int leaf16(int u, double v0, double v1, double (*mcol
   int fail = 0;
 #pragma unroll
   for (int j = 0; j < PB; j++) {
+    // the owner of the pivot computes its reciprocal once, into the padding
+    // column of mcol: FP64 instructions, not lanes, are what the master's
+    // SM runs short of
     if (j < 8) {
-      if (k0 == j) mcol[j][i] = v0;
+      if (k0 == j) {
+        mcol[j][i] = v0;
+        if (i == j && pivot_in_range(v0)) mcol[j][PB] = pivot_rcp(v0);
+      }
     } else {
-      if (k1 == j) mcol[j][i] = v1;
+      if (k1 == j) {
+        mcol[j][i] = v1;
+        if (i == j && pivot_in_range(v1)) mcol[j][PB] = pivot_rcp(v1);
+      }
     }
     bar_sync_128(1);
     // the pivot is the same in every thread: the branches are uniform
     double dj = mcol[j][j], r;
     if (pivot_in_range(dj)) {
-      r = pivot_rcp(dj);
+      r = mcol[j][PB];
     } else {
       if (!(dj > 0.0)) {  // also catches NaN
         if (!fail) fail = j + 1;
