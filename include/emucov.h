@@ -178,6 +178,12 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
  * solve, 1 = TRSM, 2 = update of
  * 16x16 block (r,c) by panel s), the SM id, and %globaltimer nanoseconds when
  * the task was fetched, when its inputs were ready, and when it completed.
+ * The master CTA's records (one per 16-column step, after the tile's task
+ * records) hold the step's start, the end of its first phase (the solve of
+ * block (s, s-1) and its hand-over) and its end; their second word packs the
+ * SM id (bits 0-7) with three saturated durations in SM clock cycles: the
+ * solve (bits 8-25), the compute warps' second phase (bits 26-44) and the
+ * whole step (bits 45-63).
  * emu_trace_read copies up to max_records records to host memory and reports
  * how many the last factor wrote. */
 emu_status emu_trace_enable(emu_ctx *ctx, int on);

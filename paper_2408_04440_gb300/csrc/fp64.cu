@@ -210,7 +210,11 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
   for (int s = 0; s < nbb; s++) {
     const int q = s - 1, n1 = s + 1;
     unsigned long long t0 = 0, t1 = 0;
-    if (trace && tid == 0) t0 = gtimer();
+    long long c0 = 0, cx = 0, c1 = 0, cl = 0;  // trace only: SM cycles of the sub-phases
+    if (trace && tid == 0) {
+      t0 = gtimer();
+      c0 = clock64();
+    }
     if (!io) {
       // X_{s,q} = block (s, q) L_{q,q}^{-T}
       if (q >= 0) {
@@ -227,6 +231,7 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
         xr[cr][ct] = va * rinv[ct];
         xr[cr + 8][ct] = vb * rinv[ct];
       }
+      if (trace && tid == 0) cx = clock64();
       // X_{s,q} written (the I/O warps publish it); then wait until the I/O
       // warps hold L_{q,q}, which this step's leaf overwrites: the leaf does
       // not wait for the publishing fence
@@ -254,7 +259,10 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
       }
       bar_sync_256(5);  // X_{s,q} is in xr
     }
-    if (trace && tid == 0) t1 = gtimer();
+    if (trace && tid == 0) {
+      t1 = gtimer();
+      c1 = clock64();
+    }
     if (!io) {
       const int i = u & (PB - 1), k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;
       double v0 = xc[i][k0], v1 = xc[i][k1];
@@ -271,6 +279,7 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
         m[cr][ct] = a[cr][ct] * rinv[ct];
         m[cr + 8][ct] = a[cr + 8][ct] * rinv[ct];
       }
+      if (trace && tid == 0) cl = clock64();
     } else {
       if (q >= 0) {
         // publish X_{s,q}
@@ -333,7 +342,11 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
       unsigned long long *rec = trace + (size_t)s * 5;
       rec[0] = (unsigned long long)T_LT | ((unsigned long long)s << 8) |
                ((unsigned long long)(q < 0 ? 0 : q) << 24) | ((unsigned long long)s << 40);
-      rec[1] = smid;
+      // SM id | SM cycles (saturated) of the solve, of the compute warps'
+      // second phase, and of the whole step
+      const unsigned long long ce = (unsigned long long)(clock64() - c0);
+      rec[1] = (smid & 0xFFull) | (min((unsigned long long)(cx - c0), 0x3ffffull) << 8) |
+               (min((unsigned long long)(cl - c1), 0x7ffffull) << 26) | (min(ce, 0x7ffffull) << 45);
       rec[2] = t0;
       rec[3] = t1;
       rec[4] = gtimer();

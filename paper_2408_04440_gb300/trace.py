@@ -45,6 +45,14 @@ def summarize_tasks(tr: np.ndarray, ntiles: int) -> list[str]:
         leaf = np.sort(done[kind == 0])
         if len(leaf) > 1:
             line += f"; LT step {np.median(np.diff(leaf)) / 1e3:.1f} us (median)"
+            # the master's packed sub-phase durations in SM cycles: the
+            # solve, the compute warps' phase 2, the whole step
+            w = t[kind == 0, 1]
+            solve, comp, step = (w >> 8) & 0x3FFFF, (w >> 26) & 0x7FFFF, (w >> 45) & 0x7FFFF
+            p1 = ready[kind == 0] - t[kind == 0, 2] + t0
+            line += (f" [phase 1 {np.median(p1) / 1e3:.2f} us, phase 2 {np.median((done - ready)[kind == 0]) / 1e3:.2f} us;"
+                     f" cycles: solve {np.median(solve):.0f}, compute phase 2 {np.median(comp):.0f},"
+                     f" step {np.median(step):.0f}]")
         out.append(line)
     return out
 
