@@ -599,9 +599,14 @@ static void dag_tasks(int nbb, std::vector<short4> &out, bool master) {
   for (int r = 2; r < nbb; r++) push(T_TRSM, r, 0, 0);
   for (int s = 0; s + 1 < nbb; s++) {
     if (!master) push(T_LT, s + 1, s, s + 1);
+    // the master's step s+1 waits for UPD(s+2, s+2, s) before the step that
+    // releases L_{s+1,s+1}, which the TRSMs of column s+1 wait for: listing
+    // it first keeps the list topological whatever number of CTAs is resident
+    if (master && s + 2 < nbb) push(T_UPD, s + 2, s + 2, s);
     for (int r = s + 3; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
     for (int c = s + 2; c < nbb; c++)
-      for (int r = c; r < nbb; r++) push(T_UPD, r, c, s);
+      for (int r = c; r < nbb; r++)
+        if (!master || r != s + 2 || c != s + 2) push(T_UPD, r, c, s);
   }
 }
 
