@@ -189,6 +189,20 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
 emu_status emu_trace_enable(emu_ctx *ctx, int on);
 emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records,
                           size_t *n_records);
+/* The task list of the dataflow POTRF of one nb x nb FP64 diagonal tile (the
+ * "POTRF on the diagonal tile" step of the tile Cholesky), in the order the
+ * kernel's CTAs fetch it.  Host only: no device work, no context.  Four
+ * int16 per task: kind (0 = step s of the chain: solve block (s, s-1) against
+ * L_{s-1,s-1}, update and factor block (s, s); 1 = TRSM of block (r, c)
+ * against L_cc after applying panel c-1; 2 = update of block (r, c) by panel
+ * s; 3 = the single-tile master that runs every step of the chain), r, c, s
+ * (16x16 blocks).  No task applies panel s to blocks (s+1, s+1) and
+ * (s+2, s+1): the chain does.  single_tile != 0 gives the list of the
+ * single-matrix factor (one master task at the head), 0 the batch form (one
+ * kind-0 task per step).  Writes min(n, max_tasks) tasks to h_tasks (may be
+ * NULL with max_tasks 0) and n to *n_tasks.  EMU_EINVAL unless nb is a
+ * positive multiple of 16 no larger than 2048. */
+emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_tasks, size_t max_tasks, size_t *n_tasks);
 /* Schedule of the single-matrix mixed factor (FP32-master storage).  With
  * use_graphs != 0 (the default) the launches after the precision map are
  * recorded once into a CUDA graph over the factor's four streams and replayed

@@ -34,7 +34,7 @@ MAP_NAMES = ("norm", "dp_sp", "dp_sp_hp", "dp_hp")
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = (
     "emu_create", "emu_destroy", "emu_set_stream", "emu_status_str", "emu_last_error",
-    "emu_launch_count", "emu_host_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_test_wait_hook", "emu_schedule", "emu_schedule_info", "emu_measure_alu_peaks", "emu_cov_build", "emu_mat_import",
+    "emu_launch_count", "emu_host_launch_count", "emu_prof_enable", "emu_prof_read", "emu_prof_timeline", "emu_trace_enable", "emu_trace_read", "emu_potrf_task_list", "emu_test_wait_hook", "emu_schedule", "emu_schedule_info", "emu_measure_alu_peaks", "emu_cov_build", "emu_mat_import",
     "emu_mat_import_host", "emu_cov_from_residuals", "emu_var_recursion", "emu_isht", "emu_sht", "emu_emulate_grid", "emu_cov_build_classfmt",
     "emu_backward_error_est", "emu_mat_clone", "emu_mat_export", "emu_mat_tile_info", "emu_mat_shape",
     "emu_mat_free", "emu_potrf_mp", "emu_sample", "emu_sample_host", "emu_potrs", "emu_solve_refine",
@@ -126,6 +126,7 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_double)]
     L.emu_emulate_grid.argtypes = [vp, vp, lg, i, lg, ctypes.POINTER(emu_trend), vp, vp, ctypes.c_uint64,
                                    ctypes.c_uint32, vp, lg]
+    L.emu_potrf_task_list.argtypes = [i, i, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.emu_mat_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.emu_mat_export.argtypes = [vp, vp, vp, lg]
     L.emu_mat_tile_info.argtypes = [vp, vp, vp, vp]
@@ -141,7 +142,8 @@ def load() -> ctypes.CDLL:
                                          ctypes.c_uint64, vp, vp, ctypes.POINTER(emu_factor_info)]
     L.emu_batch_release.argtypes = [vp]
     for name in ("emu_create", "emu_destroy", "emu_set_stream", "emu_prof_enable", "emu_prof_read",
-                 "emu_trace_enable", "emu_trace_read", "emu_prof_timeline", "emu_test_wait_hook",
+                 "emu_trace_enable", "emu_trace_read", "emu_potrf_task_list", "emu_prof_timeline",
+                 "emu_test_wait_hook",
                  "emu_schedule", "emu_schedule_info", "emu_measure_alu_peaks",
                  "emu_mat_import_host", "emu_cov_build", "emu_mat_import", "emu_emulate_grid",
                  "emu_cov_build_classfmt", "emu_backward_error_est",
@@ -457,6 +459,21 @@ def emu_mat_export(ctx: Context, A: Mat, out=None):
     if out is None:
         out = _colmajor_empty(n, n, ctx.device)
     ctx._check(ctx.lib.emu_mat_export(ctx.h, A.h, ctypes.c_void_p(_ptr(out)), out.stride(1)), "emu_mat_export")
+    return out
+
+
+def emu_potrf_task_list(nb: int, single_tile: bool = True) -> np.ndarray:
+    """Task list of the dataflow POTRF of one nb x nb diagonal tile, rows
+    (kind, r, c, s) in fetch order (host only; see emucov.h)."""
+    L = load()
+    n = ctypes.c_size_t(0)
+    st = L.emu_potrf_task_list(int(nb), int(bool(single_tile)), None, 0, ctypes.byref(n))
+    if st != 0:
+        raise EmuError(st, "emu_potrf_task_list")
+    out = np.zeros((n.value, 4), dtype=np.int16)
+    st = L.emu_potrf_task_list(int(nb), int(bool(single_tile)), out.ctypes.data, n.value, ctypes.byref(n))
+    if st != 0:
+        raise EmuError(st, "emu_potrf_task_list")
     return out
 
 

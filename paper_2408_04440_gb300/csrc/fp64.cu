@@ -949,6 +949,22 @@ __global__ void k_solve_diag(const double *__restrict__ t64, int nb, int NT, int
 
 }  // namespace
 
+extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_tasks, size_t max_tasks,
+                                          size_t *n_tasks) {
+  if (nb <= 0 || nb % PB != 0 || nb > 2048 || !n_tasks || (max_tasks > 0 && !h_tasks)) return EMU_EINVAL;
+  std::vector<short4> tasks;
+  dag_tasks(nb / PB, tasks, single_tile != 0);
+  *n_tasks = tasks.size();
+  const size_t n = tasks.size() < max_tasks ? tasks.size() : max_tasks;
+  for (size_t t = 0; t < n; t++) {
+    h_tasks[4 * t + 0] = tasks[t].x;
+    h_tasks[4 * t + 1] = tasks[t].y;
+    h_tasks[4 * t + 2] = tasks[t].z;
+    h_tasks[4 * t + 3] = tasks[t].w;
+  }
+  return EMU_OK;
+}
+
 // Ints of the dataflow POTRF workspace for nbat tiles: the task counter and
 // each tile's block states, rounded up to a whole number of doubles.
 static size_t dag_ws_ints(int nbb, int nbat) {
