@@ -6,6 +6,7 @@
 // GB300 runs FP64 on the SIMT pipe at about 2 DFMA per clock per SM (the FP64
 // MMA path measured slower), so these kernels are FP64-issue bound: the
 // register/shared-memory blocking below only has to keep that pipe busy.
+#include <climits>
 #include <vector>
 
 #include "emu_internal.h"
@@ -47,6 +48,8 @@ constexpr int PB = 16;
 enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3 };
 // wait bound in SM clock cycles (about 2 s at 2 GHz)
 constexpr long long kDagWaitCycles = 4000000000ll;
+// CTAs that may leave the master's SM (one tile); the launch has sm_count CTAs
+constexpr int kMaxLeave = 16;
 
 // GPU-scope acquire-release fence.  A block publishes data with its threads'
 // stores, a barrier, then one thread's fence and flag write (the fence is
@@ -389,18 +392,32 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   __shared__ double xr[PB][PB + 1];  // panel rows of block r
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
-  __shared__ int s_task, s_ok, bad;
+  __shared__ int s_task, s_ok, bad, s_leave;
   __shared__ int mflags[2];
-  // ws = {task counter, then state[nbb*nbb] per tile}; rinv_all = nb pivot
-  // reciprocals per tile.  A batch of nbat tiles (dtiles = their indices in
-  // D0) interleaves the tiles' task lists: task t is task t / nbat of tile
-  // t % nbat, so each tile's tasks stay in topological order.
+  // ws = {task counter, then state[nbb*nbb] per tile, then (single tile) the
+  // master's SM id + 1 and the number of CTAs that left it}; rinv_all = nb
+  // pivot reciprocals per tile.  A batch of nbat tiles (dtiles = their
+  // indices in D0) interleaves the tiles' task lists: task t is task t / nbat
+  // of tile t % nbat, so each tile's tasks stay in topological order.
   int *counter = ws;
   const int nbb = nb / PB;
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
+  int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
+  unsigned my_sm = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
+    s_leave = 0;
+  }
   while (true) {
-    if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      // single tile: a CTA on the master's SM leaves after its current task,
+      // so that the chain has that SM's FP64 pipes to itself (at most
+      // kMaxLeave CTAs leave, so the launch always keeps workers)
+      const int m = BATCH ? 0 : *((volatile int *)master_sm);
+      s_task = s_leave ? INT_MAX : atomicAdd(counter, 1);
+      if (!BATCH && !s_leave && m == (int)my_sm + 1 && atomicAdd(master_sm + 1, 1) < kMaxLeave) s_leave = 1;
+    }
     __syncthreads();
     int t = s_task;
     // one tile (the single-matrix factor) compiles without the batch indexing
@@ -413,6 +430,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     short4 tk = tasks[BATCH ? t / nbat : t];
     int kind = tk.x, r = tk.y, c = tk.z, s = tk.w;  // LT: (s, s-1, s); TRSM: (r, s, s); UPD: (r, c, s)
     if (!BATCH && kind == T_MASTER) {
+      if (threadIdx.x == 0) atomicExch(master_sm, (int)my_sm + 1);
       potrf_master(D, nb, gcol0, state, rinv_g, st, trace ? trace + (size_t)ntasks * 5 : nullptr, a, m, xr, xc, rinv,
                    mflags);
       return;
@@ -967,8 +985,10 @@ extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_ta
 
 // Ints of the dataflow POTRF workspace for nbat tiles: the task counter and
 // each tile's block states, rounded up to a whole number of doubles.
+// counter, state[nbb*nbb] per tile, master SM id + 1, CTAs that left it;
+// even, so that the pivot reciprocals after it are 8-byte aligned
 static size_t dag_ws_ints(int nbb, int nbat) {
-  size_t n = 1 + (size_t)nbat * nbb * nbb;
+  size_t n = 3 + (size_t)nbat * nbb * nbb;
   return (n + 1) & ~(size_t)1;
 }
 
@@ -1012,8 +1032,7 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
   emu_status ps0 = potrf_dag_prepare(ctx, nb);
   if (ps0 != EMU_OK) return ps0;
   ProfScope ps(ctx, PROF_POTRF, (double)nb * nb * nb / 3.0, 16.0 * nb * nb);
-  size_t state_bytes = (size_t)(1 + nbb * nbb) * sizeof(int);
-  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dag_ws, 0, state_bytes, ctx->stream));
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dag_ws, 0, dag_ws_ints(nbb, 1) * sizeof(int), ctx->stream));
   int grid = ctx->sm_count < ctx->dag_ntasks ? ctx->sm_count : ctx->dag_ntasks;
   unsigned long long *trace = nullptr;
   if (ctx->trace_on) {
