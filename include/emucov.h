@@ -79,7 +79,10 @@ typedef struct emu_mat emu_mat;
  * U-hat, and the diagonal perturbation that follows it).  Row k holds the
  * coefficient (l, m), k = l^2 + l + m, 0 <= l < L, |m| <= l, n = L^2:
  *   S[i,j] = s(l_i) s(l_j) exp(-sqrt((l_i-l_j)^2 + (m_i-m_j)^2) / beta),
- *   s(l) = (1 + l)^(-sigma_exp),   S[k,k] += nugget_rel * max_k S[k,k]. */
+ *   s(l) = (1 + l)^(-sigma_exp),   S[k,k] += nugget_rel * max_k S[k,k].
+ * nugget_rel is finite and > -1; a negative value shifts the diagonal down,
+ * and S may then not be positive definite (the factor reports EMU_ENOTPD with
+ * the first non-positive pivot). */
 typedef struct {
   int L;
   double beta;
@@ -471,8 +474,10 @@ emu_status emu_solve_refine(emu_ctx *ctx, const emu_mat *L, const emu_mat *S,
  *             column-major, leading dimension n_b, zeros above the diagonal
  *   infos     NULL, or count records; ms is the device time of the graph
  * Returns EMU_EINVAL for bad arguments, EMU_ENOMEM when the batch arenas do
- * not fit, EMU_ENOTPD (infos[b].pivot set for one failing matrix),
- * EMU_ETIMEOUT, EMU_ECUDA.  The arenas (about 18 bytes per element of every
+ * not fit, EMU_ENOTPD when some matrices are not positive definite (each of
+ * them has infos[b].pivot, its first non-positive pivot column; every other
+ * matrix's factor and samples are complete and valid), EMU_ETIMEOUT,
+ * EMU_ECUDA.  The arenas (about 18 bytes per element of every
  * padded lower tile) stay allocated in the context until emu_batch_release or
  * emu_destroy. */
 emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params *p, int nb,

@@ -316,8 +316,8 @@ emu_status emu_mat_free(emu_mat *A) {
 emu_status emu_cov_build_classfmt(emu_ctx *ctx, const emu_cov_params *p, int nb, const emu_mp_opts *o,
                                   emu_mat **out) {
   if (!ctx || !p || !o || !out) return EMU_EINVAL;
-  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel >= 0.0))
-    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, nugget_rel >= 0");
+  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel > -1.0 && p->nugget_rel < 1e300))
+    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, finite nugget_rel > -1");
   if (o->band < EMU_MAP_NORM || o->band > EMU_MAP_DP_HP) return fail_msg(ctx, EMU_EINVAL, "unknown precision map");
   if (nb % 256 != 0) return fail_msg(ctx, EMU_EINVAL, "class-format storage needs nb a multiple of 256");
   emu_mat *A = nullptr;
@@ -344,8 +344,8 @@ emu_status emu_backward_error_est(emu_ctx *ctx, const emu_mat *L, const emu_cov_
 
 emu_status emu_cov_build(emu_ctx *ctx, const emu_cov_params *p, int nb, emu_mat **out) {
   if (!ctx || !p || !out) return EMU_EINVAL;
-  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel >= 0.0))
-    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, nugget_rel >= 0");
+  if (p->L < 1 || p->L > 4096 || !(p->beta > 0.0) || !(p->nugget_rel > -1.0 && p->nugget_rel < 1e300))
+    return fail_msg(ctx, EMU_EINVAL, "need 1 <= L <= 4096, beta > 0, finite nugget_rel > -1");
   emu_mat *A = nullptr;
   emu_status s = mat_alloc(ctx, p->L * p->L, nb, &A);
   if (s != EMU_OK) return s;

@@ -119,6 +119,7 @@ struct BatchState {
   uint64_t *d_seed = nullptr;
   // device lists
   long *d_diag = nullptr, *d_all_diag = nullptr;
+  int *d_bad = nullptr;  // per (step, diagonal slot): first non-positive pivot column, 0 = none
   int *d_all_diag_int = nullptr;
   int2 *d_t64 = nullptr, *d_t32 = nullptr;
   int *d_t64slot = nullptr;  // per FP64 TRSM job: the step slot of its L_kk (pre-scaled blocks)
@@ -144,7 +145,7 @@ struct BatchState {
 
   void release() {
     void *ps[] = {t64, partial, tnorm, frob, tables, t32, slots, scale8, op, zp, op8, d_cls, d_inst, d_tile_inst,
-                  Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_all_diag, d_all_diag_int, d_t64,
+                  Z, Y, ws, rinv, tasks, d_Yptr, d_Lptr, d_seed, d_diag, d_bad, d_all_diag, d_all_diag_int, d_t64,
                   d_t64slot, ls64, rinv64,
                   d_t32, d_s64, d_q, d_pairs, d_items, d_items_s, d_segs, d_segs_s, d_items64,
                   d_items64s, d_segs64, d_segs64s, d_z, d_zs, d_zblk, digits, exp64, exp_s, exp_z, lpieces};
@@ -489,6 +490,8 @@ emu_status batch_plan(emu_ctx *ctx, BatchState *B) {
   B->diag_lists = longs;
   // device lists
   emu_status s;
+  B->d_bad = dalloc<int>(longs.size(), &s);
+  if (!B->d_bad) return s;
   if ((s = upload(ctx, &B->d_diag, longs)) != EMU_OK || (s = upload(ctx, &B->d_all_diag, all_diag)) != EMU_OK ||
       (s = upload(ctx, &B->d_all_diag_int, all_diag_int)) != EMU_OK || (s = upload(ctx, &B->d_t64, j64)) != EMU_OK ||
       (s = upload(ctx, &B->d_t64slot, j64slot)) != EMU_OK ||
@@ -629,7 +632,7 @@ emu_status batch_record(emu_ctx *ctx, BatchState *B) {
     const Step &st = B->steps[k];
     if ((s = launch_tiles_to_f64(ctx, B->t32, B->t64, B->d_diag + st.dl_off, st.dl_n, te)) != EMU_OK) return s;
     if ((s = launch_potrf64_batch(ctx, B->t64, nb, k, B->d_diag + st.d_off, st.d_n, B->tasks, B->ntasks, B->ws,
-                                  B->rinv)) != EMU_OK)
+                                  B->rinv, B->d_bad + st.d_off)) != EMU_OK)
       return s;
     if (st.t32_n > 0) {
       // FP32 copies (and, for the tensor-core TRSM, BF16 pieces) of the step's L_kk, one slot per matrix
@@ -828,6 +831,8 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   if (want_L)
     EMU_CUDA_TRY(ctx, cudaMemcpyAsync(B->d_Lptr, dL, count * sizeof(double *), cudaMemcpyHostToDevice, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(B->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, ctx->stream));
+  // the per-matrix pivot records (allocated with the step plan, after the map)
+  EMU_CUDA_TRY(ctx, cudaMemsetAsync(B->d_bad, 0, B->diag_lists.size() * sizeof(int), ctx->stream));
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   if (ctx->prof) {
     // profiling: the same launches issued one by one, so that each kernel
@@ -841,21 +846,29 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
   EMU_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
   EMU_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(int), cudaMemcpyDeviceToHost,
                                     ctx->stream));
+  std::vector<int> hbad(B->diag_lists.size());
+  EMU_CUDA_TRY(ctx, cudaMemcpyAsync(hbad.data(), B->d_bad, hbad.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
   EMU_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   if (ms_out) *ms_out = ms;
   int code = ctx->h_status[ST_CODE];
-  int bad = -1, pivot = 0;
-  if (code == DEV_NOTPD) {
-    // pivot: 1-based column of the failing matrix; its step and slot tell which
-    pivot = ctx->h_status[ST_PIVOT];
-    int k = (pivot - 1) / nb, slot = ctx->h_status[ST_AUX];
-    if (k >= 0 && k < B->maxNT && slot >= 0 && slot < B->steps[k].d_n) {
-      long g = B->diag_lists[B->steps[k].d_off + slot];
+  // matrices that met a non-positive pivot: the first such column of each
+  // (the other matrices of the batch went on and are complete)
+  std::vector<int> pivots(count, 0);
+  int nbad = 0;
+  for (int k = 0; k < B->maxNT; k++) {
+    const Step &st = B->steps[k];
+    for (int slot = 0; slot < st.d_n; slot++) {
+      const int col = hbad[st.d_off + slot];
+      if (col <= 0) continue;
+      const long g = B->diag_lists[st.d_off + slot];
       for (int b = 0; b < count; b++)
-        if (g >= B->inst[b].tile_base && g < B->inst[b].tile_base + (long)B->inst[b].NT * (B->inst[b].NT + 1) / 2)
-          bad = b;
+        if (g >= B->inst[b].tile_base && g < B->inst[b].tile_base + (long)B->inst[b].NT * (B->inst[b].NT + 1) / 2) {
+          if (pivots[b] == 0) nbad++;
+          if (pivots[b] == 0 || col < pivots[b]) pivots[b] = col;
+        }
     }
   }
   if (infos) {
@@ -866,20 +879,20 @@ emu_status batch_run(emu_ctx *ctx, int count, const emu_cov_params *p, int nb, c
       f.n = I.n;
       f.nb = nb;
       f.nt = I.NT;
-      f.pivot = (b == bad) ? pivot : 0;
+      f.pivot = pivots[b];
       for (long t = 0; t < (long)I.NT * (I.NT + 1) / 2; t++) f.tiles[B->cls[I.tile_base + t]]++;
       for (int c = 0; c < EMU_NCLASS; c++) f.update_flops[c] = B->upd_flops[b][c];
       f.frob = frob[b];
       f.ms = ms;
     }
   }
-  if (code == DEV_NOTPD) {
-    ctx->last_error = "a covariance of the batch is not positive definite (see its info.pivot)";
-    return EMU_ENOTPD;
-  }
   if (code == DEV_TIMEOUT) {
     ctx->last_error = "device wait timed out";
     return EMU_ETIMEOUT;
+  }
+  if (nbad > 0 || code == DEV_NOTPD) {
+    ctx->last_error = "covariances of the batch are not positive definite (see their info.pivot; the others are complete)";
+    return EMU_ENOTPD;
   }
   return EMU_OK;
 }
@@ -914,8 +927,8 @@ emu_status emu_batch_potrf_sample(emu_ctx *ctx, int count, const emu_cov_params 
     return EMU_EINVAL;
   }
   for (int b = 0; b < count; b++) {
-    if (p[b].L < 1 || p[b].L > 256 || !(p[b].beta > 0.0) || !(p[b].nugget_rel >= 0.0)) {
-      ctx->last_error = "batch needs 1 <= L <= 256, beta > 0, nugget_rel >= 0 for every matrix";
+    if (p[b].L < 1 || p[b].L > 256 || !(p[b].beta > 0.0) || !(p[b].nugget_rel > -1.0 && p[b].nugget_rel < 1e300)) {
+      ctx->last_error = "batch needs 1 <= L <= 256, beta > 0, finite nugget_rel > -1 for every matrix";
       return EMU_EINVAL;
     }
     if ((nsamples > 0 && !dY[b]) || (dL && !dL[b])) return EMU_EINVAL;

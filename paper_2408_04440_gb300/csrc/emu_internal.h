@@ -281,5 +281,8 @@ emu_status launch_split_z(emu_ctx *ctx, const double *Z, long ldz, long npad, in
 size_t potrf_dag_task_count(int nb);
 emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStream_t s);
 size_t potrf_batch_ws_ints(int nb, int nbat);
+// bad: nbat ints, zero before the launch; a tile whose factor meets a
+// non-positive pivot gets its 1-based global column there and the launch
+// goes on (only that matrix is flagged)
 emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const long *d_tiles, int nbat,
-                                const void *d_tasks, int ntasks, int *ws, double *rinv);
+                                const void *d_tasks, int ntasks, int *ws, double *rinv, int *bad);

@@ -48,8 +48,6 @@ constexpr int PB = 16;
 enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3 };
 // wait bound in SM clock cycles (about 2 s at 2 GHz)
 constexpr long long kDagWaitCycles = 4000000000ll;
-// CTAs that may leave the master's SM (one tile); the launch has sm_count CTAs
-constexpr int kMaxLeave = 16;
 
 // GPU-scope acquire-release fence.  A block publishes data with its threads'
 // stores, a barrier, then one thread's fence and flag write (the fence is
@@ -355,11 +353,9 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
       rec[4] = gtimer();
     }
     if (flags[1]) {
-      if (tid == 0) {
-        st[ST_PIVOT] = gcol0 + s * PB + flags[1];
-        __threadfence();
-        atomicExch(&st[ST_CODE], DEV_NOTPD);
-      }
+      // the first failure of the factor keeps its pivot (later diagonal
+      // tiles, factored from skipped updates, may fail too)
+      if (tid == 0 && atomicCAS(&st[ST_CODE], DEV_OK, DEV_NOTPD) == DEV_OK) st[ST_PIVOT] = gcol0 + s * PB + flags[1];
       return;
     }
     if (flags[0]) return;
@@ -386,7 +382,8 @@ template <bool BATCH>
 __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     k_potrf_dag(double *__restrict__ D0, int nb, int gcol0, const short4 *__restrict__ tasks, int ntasks,
                 int *__restrict__ ws, double *__restrict__ rinv_all, int *st,
-                unsigned long long *__restrict__ trace, const long *__restrict__ dtiles, int nbat) {
+                unsigned long long *__restrict__ trace, const long *__restrict__ dtiles, int nbat,
+                int *__restrict__ bad_out) {
   __shared__ double a[PB][PB + 1];   // L of the block solved against, then the block factored
   __shared__ double m[PB][PB + 1];   // L scaled by the pivot reciprocals (solves)
   __shared__ double xr[PB][PB + 1];  // panel rows of block r
@@ -403,20 +400,25 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   const int nbb = nb / PB;
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
+  // Single tile: a CTA on the master's SM leaves (before its first task if
+  // it starts there after the master, else after its current task), so that
+  // the chain has that SM's FP64 pipes to itself.  At most half the launch
+  // leaves, so the chain always keeps workers.
+  // a factor that has already failed (status set by an earlier launch) stops
+  if (*((volatile const int *)st) != DEV_OK) return;
   int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
   unsigned my_sm = 0;
   if (threadIdx.x == 0) {
     asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
-    s_leave = 0;
+    s_leave = !BATCH && *((volatile int *)master_sm) == (int)my_sm + 1 &&
+              atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2;
   }
   while (true) {
     if (threadIdx.x == 0) {
-      // single tile: a CTA on the master's SM leaves after its current task,
-      // so that the chain has that SM's FP64 pipes to itself (at most
-      // kMaxLeave CTAs leave, so the launch always keeps workers)
       const int m = BATCH ? 0 : *((volatile int *)master_sm);
       s_task = s_leave ? INT_MAX : atomicAdd(counter, 1);
-      if (!BATCH && !s_leave && m == (int)my_sm + 1 && atomicAdd(master_sm + 1, 1) < kMaxLeave) s_leave = 1;
+      if (!BATCH && !s_leave && m == (int)my_sm + 1 && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2)
+        s_leave = 1;
     }
     __syncthreads();
     int t = s_task;
@@ -579,12 +581,16 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       __syncthreads();
       if (bad) {
         if (threadIdx.x == 0) {
-          st[ST_PIVOT] = gcol0 + s * PB + bad;
-          if (BATCH) st[ST_AUX] = bt;  // which tile of the batch
-          __threadfence();
-          atomicExch(&st[ST_CODE], DEV_NOTPD);
+          if (bad_out) {
+            // the batch goes on: only this matrix is flagged, with its first
+            // non-positive pivot column (its factor is not used)
+            atomicCAS(&bad_out[bt], 0, gcol0 + s * PB + bad);
+          } else if (atomicCAS(&st[ST_CODE], DEV_OK, DEV_NOTPD) == DEV_OK) {
+            st[ST_PIVOT] = gcol0 + s * PB + bad;
+            st[ST_AUX] = bt;  // which tile of the batch
+          }
         }
-        return;
+        if (!bad_out) return;
       }
       if (ty >= tx) __stcg(blk(s, s), a[ty][tx]);
       if (threadIdx.x < PB) __stcg(rinv_g + s * PB + threadIdx.x, rinv[threadIdx.x]);
@@ -1059,7 +1065,7 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
   double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
   k_potrf_dag<false><<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks,
                                                        ctx->dag_ntasks, ctx->dag_ws, rinv, ctx->d_status, trace,
-                                                       nullptr, 1);
+                                                       nullptr, 1, nullptr);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }
@@ -1095,7 +1101,7 @@ emu_status potrf_dag_tasks_upload(emu_ctx *ctx, int nb, void *d_tasks, cudaStrea
 size_t potrf_batch_ws_ints(int nb, int nbat) { return dag_ws_ints(nb / PB, nbat); }
 
 emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const long *d_tiles, int nbat,
-                                const void *d_tasks, int ntasks, int *ws, double *rinv) {
+                                const void *d_tasks, int ntasks, int *ws, double *rinv, int *bad) {
   if (nbat <= 0) return EMU_OK;
   int nbb = nb / PB;
   ProfScope ps(ctx, PROF_POTRF, (double)nbat * nb * nb * nb / 3.0, 16.0 * nbat * nb * nb);
@@ -1103,7 +1109,7 @@ emu_status launch_potrf64_batch(emu_ctx *ctx, double *t64, int nb, int k, const 
   long total = (long)ntasks * nbat;
   int grid = (int)std::min<long>(total, 4L * ctx->sm_count);
   k_potrf_dag<true><<<grid, PB * PB, 0, ctx->stream>>>(t64, nb, k * nb, (const short4 *)d_tasks, ntasks, ws,
-                                                      rinv, ctx->d_status, nullptr, d_tiles, nbat);
+                                                      rinv, ctx->d_status, nullptr, d_tiles, nbat, bad);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -102,7 +102,7 @@ emu_status noalloc_scratch(cudaStream_t st, double **out) {
 
 extern "C" emu_status emu_cov_build_dense_noalloc(int L, double beta, double sigma_exp, double nugget_rel,
                                                   double *dS, long ld, void *stream) {
-  if (!dS || L < 1 || !(beta > 0.0) || !(nugget_rel >= 0.0) || ld < (long)L * L) return EMU_EINVAL;
+  if (!dS || L < 1 || !(beta > 0.0) || !(nugget_rel > -1.0 && nugget_rel < 1e300) || ld < (long)L * L) return EMU_EINVAL;
   if (L > kNoAllocMaxL) return EMU_ENOMEM;  // tables would not fit the fixed scratch array
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // an error already pending on this thread is not this call's: report it

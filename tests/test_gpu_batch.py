@@ -159,3 +159,45 @@ def test_batch_bad_arguments(E, ctx):
         assert st == E.EMU_EINVAL
     _, _, _, st = E.emu_batch_potrf_sample(ctx, [(8, 2.0)], nb=128, raise_on_error=False)
     assert st == E.EMU_EINVAL
+
+
+# nugget below the smallest conditional variances of the row order: not
+# positive definite, with the first non-positive pivot well inside the matrix
+BAD = (20, 3.0, 1.5, -1e-3)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-8])
+def test_non_spd_instance_flags_only_that_instance(E, ctx, eps):
+    """One matrix of the batch is not positive definite: the call reports
+    EMU_ENOTPD, only that matrix's info.pivot is set (for the FP64 factor, the
+    oracle's first non-positive pivot column), and every other matrix of the
+    batch is complete and correct; the context stays usable."""
+    params = PARAMS[:4] + [BAD] + PARAMS[4:6]
+    nb, s, seed = 256, 16, 4
+    Ys, Ls, infos, st = _bf(E, ctx, params, nb=nb, eps=eps, nsamples=s, seed=seed, want_L=True,
+                            raise_on_error=False)
+    assert st == E.EMU_ENOTPD
+    _, piv = O.potrf_blocked(O.cov_build(*BAD), nb)
+    assert piv > 16
+    for b, q in enumerate(params):
+        if q is BAD:
+            assert infos[b].pivot > 0
+            if eps == 0.0:
+                assert infos[b].pivot == piv
+            continue
+        assert infos[b].pivot == 0, b
+        L, beta = q
+        n = L * L
+        S = O.cov_build(L, beta)
+        if eps == 0.0:
+            Lo, _ = O.potrf_blocked(S, nb)
+            assert _rel(Ls[b], Lo) <= 1e-12, b
+            assert _rel(Ys[b], Lo @ O.normal_matrix(seed, b, n, s)) <= 1e-12, b
+        else:
+            assert _rel(Ls[b] @ Ls[b].T, S) <= eps, b
+    _, _, _, st2 = _bf(E, ctx, PARAMS[:3], nb=nb, eps=eps)
+    assert st2 == E.EMU_OK

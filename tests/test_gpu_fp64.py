@@ -335,6 +335,19 @@ def test_not_positive_definite_reports_pivot(E, ctx, bad):
     assert E.emu_potrf_mp(ctx, B).status == E.EMU_OK
 
 
+@pytest.mark.parametrize("nugget", [-1e-3, -0.05])
+def test_negative_nugget_reports_the_oracles_pivot(E, ctx, nugget):
+    """A negative nugget makes the covariance indefinite; the FP64 factor
+    reports EMU_ENOTPD at the oracle's first non-positive pivot column."""
+    L, beta, nb = 20, 3.0, 64
+    _, piv = O.potrf_blocked(O.cov_build(L, beta, 1.5, nugget), nb)
+    assert piv > 0
+    A = E.emu_cov_build(ctx, L, beta, nb, nugget_rel=nugget)
+    info = E.emu_potrf_mp(ctx, A, raise_on_error=False)
+    assert info.status == E.EMU_ENOTPD
+    assert info.pivot == piv
+
+
 @pytest.mark.parametrize("L,nb,s", [(12, 64, 5), (32, 128, 64)])
 def test_fp64_sampling(E, ctx, L, nb, s):
     A = E.emu_cov_build(ctx, L, 4.0, nb)

@@ -160,6 +160,8 @@ def test_covariance_limits_and_definiteness():
     # growing sigma_l: the largest diagonal entry is the last degree's, not
     # sigma_0's, so the nugget's max-diagonal rule is exercised off l = 0
     (9, 3.0, -0.75, 1e-3),
+    # a negative nugget (the indefinite inputs of the not-positive-definite tests)
+    (12, 3.0, 1.5, -1e-3),
 ])
 def test_cov_rows_equals_rows_of_full_build(L, beta, sigma_exp, nugget):
     """The row generator (used as the expected value at sizes where the full
@@ -180,7 +182,9 @@ def test_cov_rows_equals_rows_of_full_build(L, beta, sigma_exp, nugget):
     dmax = max((1.0 + l) ** (-2 * sigma_exp) for l in range(L))
     for q, i in enumerate(rows):
         l = int(math.isqrt(int(i)))
-        assert abs(R[q, i] - ((1.0 + l) ** (-2 * sigma_exp) + nugget * dmax)) <= 4e-16 * R[q, i]
+        s2 = (1.0 + l) ** (-2 * sigma_exp)
+        # relative to the terms, not to their sum (a negative nugget cancels)
+        assert abs(R[q, i] - (s2 + nugget * dmax)) <= 4e-16 * (s2 + abs(nugget) * dmax)
 
 
 def test_tile_norms_against_numpy():
@@ -547,3 +551,18 @@ def test_emulate_grid_pins():
     # the trend is shared by all ensembles: two draws differ only by sigma (Zs + v e)
     Y2 = O.emulate_grid(Zs + 1.0, E, 12.0, b0, b1, b2, rho, A, B, x, sig, v)
     assert np.allclose(Y2 - Y, np.outer(sig, np.ones(T)), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("L,beta,nugget,nb", [(12, 3.0, -1e-3, 16), (20, 3.0, -1e-3, 64), (12, 2.0, -0.05, 32)])
+def test_potrf_failure_column_is_the_first_indefinite_leading_block(L, beta, nugget, nb):
+    """The oracle's blocked Cholesky reports the 1-based column p of its first
+    non-positive pivot.  Sylvester's criterion fixes p independently: the
+    leading (p-1) x (p-1) block of S is positive definite and the leading
+    p x p block is not (numpy's symmetric eigensolver, not the oracle)."""
+    S = O.cov_build(L, beta, 1.5, nugget)
+    _, p = O.potrf_blocked(S, nb)
+    assert p > 1
+    lam_prev = np.linalg.eigvalsh(S[:p - 1, :p - 1])[0]
+    lam = np.linalg.eigvalsh(S[:p, :p])[0]
+    assert lam_prev > 1e-12 * np.abs(S).max()
+    assert lam < 0.0
