@@ -182,11 +182,18 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
  * 16x16 block (r,c) by panel s), the SM id, and %globaltimer nanoseconds when
  * the task was fetched, when its inputs were ready, and when it completed.
  * The master CTA's records (one per 16-column step, after the tile's task
- * records) hold the step's start, the end of its first phase (the solve of
- * block (s, s-1) and its hand-over) and its end; their second word packs the
- * SM id (bits 0-7) with three saturated durations in SM clock cycles: the
- * solve (bits 8-25), the compute warps' second phase (bits 26-44) and the
- * whole step (bits 45-63).
+ * records) hold the step's start, the end of its leaf and its end; their
+ * second word packs the SM id (bits 0-7) with three saturated durations in SM
+ * clock cycles: the leaf (bits 8-25), the wait for the next sub-diagonal
+ * block after it (bits 26-44) and the whole step (bits 45-63).  (When the
+ * chain runs on one CTA because clusters of two cannot be resident, the
+ * second word holds the solve of block (s, s-1) and the compute warps' second
+ * phase instead, and the middle timestamp ends the solve.)  In the pair form
+ * the helper's records follow (kind 5, one per step s < nb/16 - 1): r = s+1,
+ * c = s, the start of its step, the arrival of its inputs (X_{s+1,s-1} and
+ * blocks (s+1, s), (s+1, s+1)) and the time X_{s+1,s} was sent and
+ * published; the second word packs the SM id with the nanoseconds from the
+ * inputs to the end of the solve (bits 8-25).
  * emu_trace_read copies up to max_records records to host memory and reports
  * how many the last factor wrote. */
 emu_status emu_trace_enable(emu_ctx *ctx, int on);
@@ -200,9 +207,11 @@ emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records,
  * against L_cc after applying panel c-1; 2 = update of block (r, c) by panel
  * s; 3 = the single-tile master that runs every step of the chain), r, c, s
  * (16x16 blocks).  No task applies panel s to blocks (s+1, s+1) and
- * (s+2, s+1): the chain does.  single_tile != 0 gives the list of the
- * single-matrix factor (one master task at the head), 0 the batch form (one
- * kind-0 task per step).  Writes min(n, max_tasks) tasks to h_tasks (may be
+ * (s+2, s+1): the chain does.  single_tile = 1 gives the list of the
+ * single-matrix factor whose chain runs on one CTA (one master task at the
+ * head), 2 the list when the chain runs on a cluster of two CTAs (the head
+ * task is not fetched, and the chain also applies panel s to block
+ * (s+2, s+2)), 0 the batch form (one kind-0 task per step).  Writes min(n, max_tasks) tasks to h_tasks (may be
  * NULL with max_tasks 0) and n to *n_tasks.  EMU_EINVAL unless nb is a
  * positive multiple of 16 no larger than 2048. */
 emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_tasks, size_t max_tasks, size_t *n_tasks);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "emu_internal.h"
+#include "tc.cuh"
 
 namespace {
 
@@ -45,7 +46,7 @@ __device__ inline bool failed(const int *st) {
 // X_{s,s-1} before its leaf, so that LT(s+1) applies panel s-1 to block
 // (s+1, s) while the leaf runs.
 constexpr int PB = 16;
-enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3 };
+enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3, T_HELP = 5 };
 // wait bound in SM clock cycles (about 2 s at 2 GHz)
 constexpr long long kDagWaitCycles = 4000000000ll;
 
@@ -83,6 +84,32 @@ __device__ inline bool dag_wait(const int *state, int idx, int v, int *st) {
   }
 }
 
+// Thread 0 waits until state[i] >= v for up to three flags (an index < 0 is
+// no flag), or failure / timeout, polling every flag in each round so that
+// one L2 round trip serves them all.
+__device__ inline bool dag_wait3(const int *state, int i0, int v0, int i1, int v1, int i2, int v2, int *st) {
+  const int w = c_dag_withhold;
+  long long t0 = 0;
+  for (int it = 0;; it++) {
+    const int a = i0 >= 0 ? *((volatile const int *)(state + i0)) : INT_MAX;
+    const int b = i1 >= 0 ? *((volatile const int *)(state + i1)) : INT_MAX;
+    const int c = i2 >= 0 ? *((volatile const int *)(state + i2)) : INT_MAX;
+    const bool held = (i0 >= 0 && i0 == w) || (i1 >= 0 && i1 == w) || (i2 >= 0 && i2 == w);
+    if (a >= v0 && b >= v1 && c >= v2 && !held) return true;
+    if (*((volatile const int *)st) != DEV_OK) return false;
+    if (it == 0) {
+      t0 = clock64();
+    } else if (clock64() - t0 > c_dag_wait_cycles) {
+      if (atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 2;
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+__device__ inline bool dag_wait2(const int *state, int i0, int v0, int i1, int v1, int *st) {
+  return dag_wait3(state, i0, v0, i1, v1, -1, 0, st);
+}
+
 // Pivot reciprocal: the hardware approximation y (relative error about
 // 2^-20, measured) refined by one third-order Newton-Raphson step for 1/d,
 // r = y (1 + e + e^2) with e = 1 - d y, whose truncation error e^3 is below
@@ -107,6 +134,66 @@ __device__ inline void bar_sync_128(int id) { asm volatile("bar.sync %0, 128;" :
 __device__ inline void bar_sync_256(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
 __device__ inline void bar_arrive_256(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
 
+// ---- thread-block cluster of two (the single-tile chain on two SMs)
+__device__ inline uint32_t cluster_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ inline uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ inline uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared object in CTA `rank`
+__device__ inline uint32_t peer_addr(const void *local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(local)), "r"(rank));
+  return r;
+}
+__device__ inline void st_peer_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ inline void st_peer_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// arrive on an mbarrier of the peer CTA; releases this thread's earlier
+// stores (local and remote) at cluster scope
+__device__ inline void arrive_peer(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// wait, with cluster-scope acquire, for phase `parity` of a local mbarrier
+// that the peer CTA arrives on; false after the wait bound or when *abort
+// becomes nonzero
+__device__ inline bool wait_from_peer(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  const uint32_t a = tc::smem_u32(bar);
+  long long t0 = 0;
+  for (int it = 0;; it++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    if (it == 0) t0 = clock64();
+    else if (clock64() - t0 > c_dag_wait_cycles) return false;
+  }
+}
+// every thread of both CTAs; orders each CTA's remote stores before the
+// other's exit
+__device__ inline void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // 16x16 products of panel rows: sum_p A[ty][p] B[tx][p], two chains.
 __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)[PB + 1], int ty, int tx) {
   double acc0 = 0.0, acc1 = 0.0;
@@ -125,9 +212,15 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
 // updates its trailing entries, x_ik -= c_j[i] c_j[k] / c_jj.  At the end
 // L_ik = c_k[i] / sqrt(c_kk) goes to out[i][k] and 1/L_kk to rinv[k].
 // Returns 0, or the 1-based column of the first non-positive pivot (the
-// same in every thread; out and rinv are then not written).
+// same in every thread; out is then not written).  With ms given (the pair
+// form of the chain): at step j the 16 threads of rows i = u < 16 store the
+// scaled column c_j[i] / c_jj (= L_ij / L_jj) into ms[j][i] and thread j the
+// pivot reciprocal 1/c_jj into ms[j][16]; after columns 3, 7, 11, 13, 14 and
+// 15 each arrives on the local mbarrier mb[j] (16 arrivals); at the end they
+// arrive on mb[16] once rinv is written.  Every phase completes whether or not a pivot
+// fails.
 __device__ __forceinline__ int leaf16(int u, double v0, double v1, double (*mcol)[PB + 1], double (*out)[PB + 1],
-                                      double *rinv) {
+                                      double *rinv, double (*ms)[PB + 1] = nullptr, uint64_t *mb = nullptr) {
   const int w = u >> 5, i = u & (PB - 1);
   const int k0 = w + 4 * ((u >> 4) & 1), k1 = k0 + 8;
   int fail = 0;
@@ -163,8 +256,18 @@ __device__ __forceinline__ int leaf16(int u, double v0, double v1, double (*mcol
     // warp-uniform guards: no lane of the warp has a column > j left
     if (j < w + 4 && k0 > j && i >= k0) v0 = fma(-tt, mcol[j][k0], v0);
     if (j < w + 12 && k1 > j && i >= k1) v1 = fma(-tt, mcol[j][k1], v1);
+    if (ms && u < PB) {
+      ms[j][i] = tt;
+      if (i == j) ms[j][PB] = r;  // the pivot reciprocal 1/c_jj
+      // after columns 3, 7, 11, 13, 14, 15: one release (CTA scope) covers
+      // this thread's stores since the previous one
+      if ((j & 3) == 3 || j >= 13) tc::mbar_arrive(&mb[j]);
+    }
   }
-  if (u < PB) rinv[u] = rsqrt(mcol[u][u]);
+  if (u < PB) {
+    rinv[u] = rsqrt(mcol[u][u]);
+    if (ms) tc::mbar_arrive(&mb[16]);
+  }
   bar_sync_128(1);
   if (!fail) {
     out[i][k0] = v0 * rinv[k0];  // the diagonal: c_kk / sqrt(c_kk)
@@ -374,6 +477,303 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
   }
 }
 
+// The chain of one tile on a cluster of two CTAs (CTA ranks 0 and 1 of
+// cluster 0; the other clusters run the TRSM / UPD tasks).  The master (rank
+// 0) keeps the four FP64 pipes of its SM for the leaf and the product that
+// forms the next diagonal block; the helper (rank 1) does the rest of the
+// step on its own SM and the two exchange data through distributed shared
+// memory:
+//   master, warps 0..3: factor C_s (block (s, s) after every panel < s, in
+//     registers v0, v1) with the leaf, which leaves each scaled column
+//     c_j / c_jj in xr[j] (local mbar[j]) and 1/L_kk in rinv (mbar[16]); then
+//     wait for C_{s+1} (written into this CTA's xc, mbar[17]);
+//   master, warps 4..7: 16 threads forward each column and then 1/L_kk into
+//     the helper's ms and rinv (arriving on its mbar[j], mbar[16]); then all
+//     publish L_{s,s} and its pivot reciprocals as soon as the leaf ends;
+//   helper, warps 0..3: load block (s+1, s) after the panels < s-1, wait
+//     for X_{s+1,s-1} (TRSM(s+1, s-1)), apply panel s-1 (B), solve
+//     X_{s+1,s} = B L_{s,s}^{-T} one column behind the leaf, scale it by
+//     1/L_jj and publish it;
+//   helper, warps 4..7: C' = block (s+1, s+1) after the panels < s-1, minus
+//     X_{s+1,s-1} X_{s+1,s-1}^T;
+//   helper, all: C_{s+1} = C' - X_{s+1,s} X_{s+1,s}^T, one entry per thread,
+//     into the master's xc.
+// mbar phases advance once per step (parity s & 1).  flags[2] of each CTA
+// is set by the other when it stops (a failed pivot or wait), and every wait
+// on the peer also gives up at that flag or the wait bound; both CTAs end at
+// one cluster barrier, so neither leaves while the other may still write into
+// its shared memory.
+__device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb, int gcol0, int *__restrict__ state,
+                                                  double *__restrict__ rinv_g, int *st,
+                                                  unsigned long long *__restrict__ trace, double (*lout)[PB + 1],
+                                                  double (*mcol)[PB + 1], double (*xr)[PB + 1],
+                                                  double (*xc)[PB + 1], double *rinv, volatile int *flags,
+                                                  uint64_t *mbar) {
+  const int nbb = nb / PB;
+  const size_t ld = nb;
+  const int tid = threadIdx.x, u = tid & 127;
+  const bool io = tid >= 128;
+  const int ir = u & (PB - 1), ic = u >> 4;                                 // warps 4..7
+  const int i = u & (PB - 1), k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;  // warps 0..3
+  auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
+  // the helper's objects (same layout: its ms is the array this CTA calls mcol)
+  const uint32_t ms_h = peer_addr(mcol, 1), rinv_h = peer_addr(rinv, 1);
+  const uint32_t mbcol_h = peer_addr(&mbar[0], 1), mbr_h = peer_addr(&mbar[16], 1);
+  const uint32_t stop_h = peer_addr((const void *)&flags[2], 1);
+  if (io) {
+    xc[ir][ic] = __ldcg(gp(0, 0, ir, ic));
+    xc[ir][ic + 8] = __ldcg(gp(0, 0, ir, ic + 8));
+  }
+  __syncthreads();
+  double v0 = 0.0, v1 = 0.0;
+  if (!io) {
+    v0 = xc[i][k0];
+    v1 = xc[i][k1];
+  }
+  for (int s = 0; s < nbb; s++) {
+    const bool more = s + 1 < nbb;
+    unsigned long long t0 = 0, t1 = 0;
+    long long c0 = 0, c1 = 0, c7 = 0;  // trace only: SM cycles of the sub-phases
+    if (trace && tid == 0) {
+      t0 = gtimer();
+      c0 = clock64();
+    }
+    if (!io) {
+      // the scaled columns go to xr and mbar[0..16], from where warps 4..7
+      // forward them
+      const int fail = leaf16(u, v0, v1, mcol, lout, rinv, xr, mbar);
+      if (fail && u == 0) flags[1] = fail;
+      if (trace && tid == 0) {
+        t1 = gtimer();
+        c1 = clock64();
+      }
+      bar_arrive_256(6);  // L_{s,s} and 1/L_kk are in lout and rinv
+      if (more && !fail) {
+        // C_{s+1}, formed by the helper
+        if (!wait_from_peer(&mbar[17], (uint32_t)s & 1u, &flags[2])) {
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 4;
+          flags[0] = 1;
+        }
+        if (trace && tid == 0) c7 = clock64();
+        v0 = xc[i][k0];
+        v1 = xc[i][k1];
+      }
+    } else {
+      if (u < PB) {
+        // forward the leaf's scaled columns, then 1/L_kk, to the helper as
+        // each is formed (the remote store and its cluster-scope release stay
+        // off the leaf's pivot chain)
+        const uint32_t par = (uint32_t)s & 1u;
+#pragma unroll 1
+        for (int j = 0; j <= PB; j++) {
+          // the leaf releases columns 0-3, 4-7, 8-11, 12-13, 14, 15 (mbar[3],
+          // [7], [11], [13], [14], [15]), then rinv (mbar[16])
+          const int wb = j < 12 ? ((j & 3) == 0 ? j + 3 : -1) : (j == 12 ? 13 : (j == 13 ? -1 : j));
+          if (wb >= 0 && !tc::mbar_wait(&mbar[wb], par, &flags[2])) {
+            if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 7;
+            flags[0] = 1;
+          }
+          if (j < PB) {
+            st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + u) * 8u, xr[j][u]);
+            if (u == j) st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + PB) * 8u, xr[j][PB]);
+          } else {
+            st_peer_f64(rinv_h + 8u * u, rinv[u]);
+          }
+          // one arrival per column: thread 0's cluster-scope release covers
+          // the stores its partners ordered before it
+          __syncwarp(0x0000ffffu);
+          if (u == 0) arrive_peer(j < PB ? mbcol_h + 8u * j : mbr_h);
+        }
+      }
+      bar_sync_256(6);
+      if (!flags[1]) {
+        if (ir >= ic) __stcg(gp(s, s, ir, ic), lout[ir][ic]);
+        if (ir >= ic + 8) __stcg(gp(s, s, ir, ic + 8), lout[ir][ic + 8]);
+        if (u < PB) __stcg(rinv_g + s * PB + u, rinv[u]);
+        bar_sync_128(2);
+        if (u == 0) {
+          fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+          atomicExch(&state[s * nbb + s], s + 1);
+        }
+      }
+    }
+    __syncthreads();
+    if (trace && tid == 0) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      unsigned long long *rec = trace + (size_t)s * 5;
+      rec[0] = (unsigned long long)T_LT | ((unsigned long long)s << 8) |
+               ((unsigned long long)(s > 0 ? s - 1 : 0) << 24) | ((unsigned long long)s << 40);
+      // SM id | SM cycles (saturated) of the leaf, of the wait for X_{s+1,s}
+      // after it, and of the whole step
+      const unsigned long long ce = (unsigned long long)(clock64() - c0);
+      rec[1] = (smid & 0xFFull) | (min((unsigned long long)(c1 - c0), 0x3ffffull) << 8) |
+               (min((unsigned long long)(c7 > c1 ? c7 - c1 : 0), 0x7ffffull) << 26) | (min(ce, 0x7ffffull) << 45);
+      rec[2] = t0;
+      rec[3] = t1;
+      rec[4] = gtimer();
+    }
+    if (flags[1] || flags[0] || flags[2]) {
+      if (tid == 0) {
+        // the first failure of the factor keeps its pivot
+        if (flags[1] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_NOTPD) == DEV_OK) st[ST_PIVOT] = gcol0 + s * PB + flags[1];
+        st_peer_s32(stop_h, 1);
+      }
+      break;
+    }
+  }
+  cluster_barrier();
+}
+
+__device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
+                                                  unsigned long long *__restrict__ trace, double (*ms)[PB + 1],
+                                                  double (*xprev)[PB + 1], double (*xo)[PB + 1],
+                                                  double (*uu)[PB + 1], double *rinv, volatile int *flags,
+                                                  uint64_t *mbar) {
+  const int nbb = nb / PB;
+  const size_t ld = nb;
+  const int tid = threadIdx.x, u = tid & 127;
+  const bool cw = tid < 128;                        // warps 0..3: B and the solve; 4..7: C'
+  const int cr = u >> 4, ct = u & (PB - 1);         // warps 0..3: rows cr, cr + 8 of column ct
+  const int ir = u & (PB - 1), ic = u >> 4;         // warps 4..7: entries (ir, ic), (ir, ic + 8)
+  auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
+  // the master's objects: C_{s+1} goes to its xc (this CTA's xo at the same
+  // address); its mbar[17] counts one arrival per warp of this CTA
+  const uint32_t xc_m = peer_addr(xo, 0);
+  const uint32_t mbx_m = peer_addr(&mbar[17], 0), stop_m = peer_addr((const void *)&flags[2], 0);
+  for (int s = 0; s + 1 < nbb; s++) {
+    const int n1 = s + 1;
+    const uint32_t par = (uint32_t)s & 1u;
+    unsigned long long t0 = 0, t1 = 0, t2 = 0;  // trace only
+    // blocks (n1, s) and (n1, n1) after the panels < s-1 (UPD tasks, usually
+    // complete long before); they load while X_{n1,s-1} is awaited
+    if (tid == 0) {
+      if (trace) t0 = gtimer();
+      if (!dag_wait2(state, n1 * nbb + s, s - 1, n1 * nbb + n1, s - 1, st)) flags[0] = 1;
+      fence_acq_rel_gpu();
+    }
+    __syncthreads();
+    if (flags[0] || flags[2]) break;
+    double va, vb;
+    if (cw) {
+      va = __ldcg(gp(n1, s, cr, ct));
+      vb = __ldcg(gp(n1, s, cr + 8, ct));
+    } else {
+      va = __ldcg(gp(n1, n1, ir, ic));  // C' entries (ir, ic), (ir, ic + 8)
+      vb = __ldcg(gp(n1, n1, ir, ic + 8));
+    }
+    if (s >= 1) {
+      // X_{n1,s-1} from TRSM(n1, s-1)
+      if (tid == 0) {
+        if (!dag_wait(state, n1 * nbb + (s - 1), s, st)) flags[0] = 1;
+        fence_acq_rel_gpu();
+        if (trace) t1 = gtimer();
+      }
+      __syncthreads();
+      if (flags[0] || flags[2]) break;
+      if (!cw) {
+        xo[ir][ic] = __ldcg(gp(n1, s - 1, ir, ic));
+        xo[ir][ic + 8] = __ldcg(gp(n1, s - 1, ir, ic + 8));
+      }
+      __syncthreads();  // X_{n1,s-1} is in xo
+      if (cw) {
+        // panel s-1 applied to block (n1, s): B -= X_{n1,s-1} X_{s,s-1}^T
+        va -= panel_dot(xo, xprev, cr, ct);
+        vb -= panel_dot(xo, xprev, cr + 8, ct);
+      } else {
+        // panel s-1 applied to block (n1, n1): C' -= X_{n1,s-1} X_{n1,s-1}^T
+        va -= panel_dot(xo, xo, ir, ic);
+        vb -= panel_dot(xo, xo, ir, ic + 8);
+      }
+    } else if (trace && tid == 0) {
+      t1 = gtimer();
+    }
+    if (cw) {
+      // X_{n1,s} L_{s,s}^T = B, column j as soon as the master's leaf has
+      // formed column j of L_{s,s} (in the unscaled form x_j L_jj)
+#pragma unroll
+      for (int j = 0; j < PB; j++) {
+        if (!wait_from_peer(&mbar[j], par, &flags[2])) {
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 5;
+          flags[0] = 1;
+        }
+        if (ct == j) {
+          // u_{cr,j}, u_{cr+8,j} are final: to the C accumulation (warps 4..7)
+          uu[j][cr] = va;
+          uu[j][cr + 8] = vb;
+          tc::mbar_arrive(&mbar[18 + j]);
+        }
+        const double aj = __shfl_sync(0xffffffffu, va, j, PB), bj = __shfl_sync(0xffffffffu, vb, j, PB);
+        if (ct > j) {
+          const double mj = ms[j][ct];
+          va = fma(-aj, mj, va);
+          vb = fma(-bj, mj, vb);
+        }
+      }
+      if (trace && tid == 0) t2 = gtimer();
+    } else {
+      // C_{n1} = C' - X X^T needs no square root: with u_j = x_j L_jj (the
+      // solve's unscaled columns) and r_j = 1/c_jj = 1/L_jj^2,
+      // X X^T = sum_j u_j r_j u_j^T, accumulated column by column as the
+      // solve finishes each one
+#pragma unroll 1
+      for (int j = 0; j < PB; j++) {
+        if (!wait_from_peer(&mbar[18 + j], par, &flags[2])) {  // CTA-local arrivals; cluster acquire is stronger
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
+          flags[0] = 1;
+        }
+        const double p = uu[j][ir] * ms[j][PB];
+        va = fma(-p, uu[j][ic], va);
+        vb = fma(-p, uu[j][ic + 8], vb);
+      }
+      // C_{n1} (entries (ir, ic), (ir, ic + 8)) into the master's xc: its
+      // next leaf starts from it
+      st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic) * 8u, va);
+      st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic + 8) * 8u, vb);
+      __syncwarp();
+      if ((tid & 31) == 0) arrive_peer(mbx_m);  // one per warp (warps 4..7)
+    }
+    // X_{n1,s} = u / L_jj, for TRSM tasks and the next step's B
+    if (cw && !wait_from_peer(&mbar[16], par, &flags[2])) {
+      if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 6;
+      flags[0] = 1;
+    }
+    __syncthreads();  // every read of xo and xprev above is done
+    if (flags[0] || flags[2]) break;
+    if (cw) {
+      const double xa = va * rinv[ct], xb = vb * rinv[ct];
+      xprev[cr][ct] = xa;
+      xprev[cr + 8][ct] = xb;
+      __stcg(gp(n1, s, cr, ct), xa);
+      __stcg(gp(n1, s, cr + 8, ct), xb);
+    }
+    if (cw) {
+      // publish X_{n1,s}
+      bar_sync_128(2);
+      if (tid == 0) {
+        fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+        atomicExch(&state[n1 * nbb + s], s + 1);
+        if (trace) {
+          unsigned smid;
+          asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+          unsigned long long *rec = trace + (size_t)s * 5;
+          rec[0] = (unsigned long long)T_HELP | ((unsigned long long)n1 << 8) | ((unsigned long long)s << 24) |
+                   ((unsigned long long)s << 40);
+          // SM id | ns from the inputs to the end of the solve (saturated)
+          rec[1] = (smid & 0xFFull) | (min(t2 - t1, 0x3ffffull) << 8);
+          rec[2] = t0;
+          rec[3] = t1;
+          rec[4] = gtimer();  // C sent, X published
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // a stop of this CTA (failed wait) stops the master's wait for X as well
+  if (tid == 0 && flags[0]) st_peer_s32(stop_m, 1);
+  cluster_barrier();
+}
+
 // One tile: at most 64 registers per thread (4 CTAs of 256 threads per SM),
 // because it shares every SM with the persistent bulk GEMM of the mixed
 // factor and a larger register footprint measurably slowed both.  The batch
@@ -390,7 +790,8 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
   __shared__ int s_task, s_ok, bad, s_leave;
-  __shared__ int mflags[2];
+  __shared__ int mflags[3];
+  __shared__ uint64_t mbar[2 * PB + 2];  // the pair form's hand-over barriers
   // ws = {task counter, then state[nbb*nbb] per tile, then (single tile) the
   // master's SM id + 1 and the number of CTAs that left it}; rinv_all = nb
   // pivot reciprocals per tile.  A batch of nbat tiles (dtiles = their
@@ -404,20 +805,53 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   // it starts there after the master, else after its current task), so that
   // the chain has that SM's FP64 pipes to itself.  At most half the launch
   // leaves, so the chain always keeps workers.
-  // a factor that has already failed (status set by an earlier launch) stops
-  if (*((volatile const int *)st) != DEV_OK) return;
+  // ws extras: master SM id + 1, CTAs that left, helper SM id + 1
   int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
   unsigned my_sm = 0;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
+  // Pair form (one tile launched as clusters of two): cluster 0 runs the
+  // chain (rank 0 the master, rank 1 the helper) and never fetches a task;
+  // the other CTAs fetch tasks 1, 2, ...  Cluster 0 always reaches its final
+  // cluster barrier: its loops stop on the status word inside their bounded
+  // waits rather than returning here.
+  const bool pair = !BATCH && cluster_nctarank() == 2;
+  if (pair && cluster_id_x() == 0) {
+    const uint32_t rank = cluster_ctarank();
+    if (threadIdx.x == 0) {
+      mflags[0] = mflags[1] = mflags[2] = 0;
+      // per column / rinv: the 16 leaf threads (master) or one arrival of
+      // the master's forwarding warp (helper); mbar[17]: one per warp of the
+      // helper
+      for (int j = 0; j < PB + 1; j++) tc::mbar_init(&mbar[j], rank == 0 ? PB : 1);
+      if (rank == 0) tc::mbar_init(&mbar[17], 4);  // warps 4..7 of the helper
+      else
+        for (int j = 0; j < PB; j++) tc::mbar_init(&mbar[18 + j], 8);  // column j of u: one thread per half-warp
+      tc::fence_barrier_init();
+      atomicExch(master_sm + (rank == 0 ? 0 : 2), (int)my_sm + 1);
+    }
+    cluster_barrier();  // both CTAs' barriers exist before any remote access
+    double *rinv_g = rinv_all;
+    unsigned long long *tr = trace ? trace + (size_t)ntasks * 5 : nullptr;
+    if (rank == 0)
+      potrf_pair_master(D0, nb, gcol0, ws + 1, rinv_g, st, tr, a, m, xr, xc, rinv, mflags, mbar);
+    else
+      potrf_pair_helper(D0, nb, ws + 1, st, trace ? trace + (size_t)(ntasks + nbb) * 5 : nullptr, m, xr, xc, a,
+                        rinv, mflags, mbar);
+    return;
+  }
+  // a factor that has already failed (status set by an earlier launch) stops
+  if (*((volatile const int *)st) != DEV_OK) return;
   if (threadIdx.x == 0) {
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
-    s_leave = !BATCH && *((volatile int *)master_sm) == (int)my_sm + 1 &&
+    const int m0 = BATCH ? 0 : *((volatile int *)master_sm), h0 = BATCH ? 0 : *((volatile int *)(master_sm + 2));
+    s_leave = !BATCH && (m0 == (int)my_sm + 1 || h0 == (int)my_sm + 1) &&
               atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2;
   }
   while (true) {
     if (threadIdx.x == 0) {
-      const int m = BATCH ? 0 : *((volatile int *)master_sm);
-      s_task = s_leave ? INT_MAX : atomicAdd(counter, 1);
-      if (!BATCH && !s_leave && m == (int)my_sm + 1 && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2)
+      const int m = BATCH ? 0 : *((volatile int *)master_sm), h = BATCH ? 0 : *((volatile int *)(master_sm + 2));
+      s_task = s_leave ? INT_MAX : atomicAdd(counter, 1) + (pair ? 1 : 0);  // pair: task 0 is cluster 0's
+      if (!BATCH && !s_leave && (m == (int)my_sm + 1 || h == (int)my_sm + 1) &&
+          atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2)
         s_leave = 1;
     }
     __syncthreads();
@@ -444,15 +878,14 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
       if (BATCH && kind == T_LT)
         // first the inputs other tasks produce (usually ready long before
         // LT(s-1) ends): X_{s,s-2}, block (s,s-1) and the diagonal block
-        ok = (s < 2 || dag_wait(state, s * nbb + (s - 2), s - 1, st)) &&
-             (s < 1 || dag_wait(state, s * nbb + (s - 1), s - 2, st)) && dag_wait(state, s * nbb + s, s - 1, st);
+        ok = dag_wait3(state, s >= 2 ? s * nbb + (s - 2) : -1, s - 1, s >= 1 ? s * nbb + (s - 1) : -1, s - 2,
+                       s * nbb + s, s - 1, st);
       else if (kind == T_TRSM)
         // the inputs of the panel s-1 update first; L_{s,s} is awaited below
-        ok = (s == 0 || (dag_wait(state, r * nbb + (s - 1), s, st) && dag_wait(state, s * nbb + (s - 1), s, st))) &&
-             dag_wait(state, r * nbb + s, s - 1, st);
+        ok = dag_wait3(state, s >= 1 ? r * nbb + (s - 1) : -1, s, s >= 1 ? s * nbb + (s - 1) : -1, s,
+                       r * nbb + s, s - 1, st);
       else
-        ok = dag_wait(state, r * nbb + s, s + 1, st) && dag_wait(state, c * nbb + s, s + 1, st) &&
-             dag_wait(state, r * nbb + c, s, st);
+        ok = dag_wait3(state, r * nbb + s, s + 1, c * nbb + s, s + 1, r * nbb + c, s, st);
       fence_acq_rel_gpu();
       s_ok = ok;
       bad = 0;
@@ -611,7 +1044,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
 // Task list of the dataflow POTRF for nbb blocks per side (see k_potrf_dag),
 // in topological, lookahead-first order.  With master = true the LT tasks
 // are replaced by one T_MASTER task at the head of the list (single tile).
-static void dag_tasks(int nbb, std::vector<short4> &out, bool master) {
+static void dag_tasks(int nbb, std::vector<short4> &out, bool master, bool pair = false) {
   out.clear();
   auto push = [&](int kind, int r, int c, int s) {
     out.push_back(make_short4((short)kind, (short)r, (short)c, (short)s));
@@ -620,17 +1053,26 @@ static void dag_tasks(int nbb, std::vector<short4> &out, bool master) {
     push(T_MASTER, 0, 0, 0);
   else
     push(T_LT, 0, 0, 0);
-  for (int r = 2; r < nbb; r++) push(T_TRSM, r, 0, 0);
+  // Pair form: the helper's step c+1 waits for TRSM(c+2, c), which is
+  // therefore listed right after its last input, UPD(c+2, c, c-2), ahead of
+  // the other updates by panel c-2 (TRSM(3, 1) right after TRSM(3, 0)).
+  for (int r = 2; r < nbb; r++) {
+    push(T_TRSM, r, 0, 0);
+    if (pair && r == 3) push(T_TRSM, 3, 1, 1);
+  }
   for (int s = 0; s + 1 < nbb; s++) {
     if (!master) push(T_LT, s + 1, s, s + 1);
     // the master's step s+1 waits for UPD(s+2, s+2, s) before the step that
     // releases L_{s+1,s+1}, which the TRSMs of column s+1 wait for: listing
     // it first keeps the list topological whatever number of CTAs is resident
-    if (master && s + 2 < nbb) push(T_UPD, s + 2, s + 2, s);
-    for (int r = s + 3; r < nbb; r++) push(T_TRSM, r, s + 1, s + 1);
+    if (master && !pair && s + 2 < nbb) push(T_UPD, s + 2, s + 2, s);
+    for (int r = s + 3; r < nbb; r++)
+      if (!pair || r != s + 3) push(T_TRSM, r, s + 1, s + 1);
     for (int c = s + 2; c < nbb; c++)
-      for (int r = c; r < nbb; r++)
-        if (!master || r != s + 2 || c != s + 2) push(T_UPD, r, c, s);
+      for (int r = c; r < nbb; r++) {
+        if (!master || r != s + 2 || c != s + 2) push(T_UPD, r, c, s);  // pair: the helper applies it
+        if (pair && c == s + 2 && r == s + 4) push(T_TRSM, s + 4, s + 2, s + 2);
+      }
   }
 }
 
@@ -977,7 +1419,7 @@ extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_ta
                                           size_t *n_tasks) {
   if (nb <= 0 || nb % PB != 0 || nb > 2048 || !n_tasks || (max_tasks > 0 && !h_tasks)) return EMU_EINVAL;
   std::vector<short4> tasks;
-  dag_tasks(nb / PB, tasks, single_tile != 0);
+  dag_tasks(nb / PB, tasks, single_tile != 0, single_tile == 2);
   *n_tasks = tasks.size();
   const size_t n = tasks.size() < max_tasks ? tasks.size() : max_tasks;
   for (size_t t = 0; t < n; t++) {
@@ -991,10 +1433,11 @@ extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_ta
 
 // Ints of the dataflow POTRF workspace for nbat tiles: the task counter and
 // each tile's block states, rounded up to a whole number of doubles.
-// counter, state[nbb*nbb] per tile, master SM id + 1, CTAs that left it;
-// even, so that the pivot reciprocals after it are 8-byte aligned
+// counter, state[nbb*nbb] per tile, master SM id + 1, CTAs that left it,
+// helper SM id + 1; even, so that the pivot reciprocals after it are 8-byte
+// aligned
 static size_t dag_ws_ints(int nbb, int nbat) {
-  size_t n = 3 + (size_t)nbat * nbb * nbb;
+  size_t n = 4 + (size_t)nbat * nbb * nbb;
   return (n + 1) & ~(size_t)1;
 }
 
@@ -1013,9 +1456,26 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
 
 emu_status potrf_dag_prepare(emu_ctx *ctx, int nb) {
   int nbb = nb / PB;
+  if (ctx->dag_pair < 0) {
+    // can a cluster of two CTAs of this kernel be resident?
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(PB * PB);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 2;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_dag<false>, &cfg);
+    ctx->dag_pair = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
+    if (e != cudaSuccess) cudaGetLastError();
+  }
   if (ctx->dag_nbb != nbb) {
     std::vector<short4> tasks;
-    dag_tasks(nbb, tasks, true);
+    dag_tasks(nbb, tasks, true, ctx->dag_pair == 1);
     cudaFree(ctx->dag_tasks);
     cudaFree(ctx->dag_ws);
     ctx->dag_tasks = nullptr;
@@ -1042,8 +1502,9 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
   int grid = ctx->sm_count < ctx->dag_ntasks ? ctx->sm_count : ctx->dag_ntasks;
   unsigned long long *trace = nullptr;
   if (ctx->trace_on) {
-    // per tile: one record per task, then one per master step
-    const size_t per_tile = (size_t)(ctx->dag_ntasks + nbb) * 5;
+    // per tile: one record per task, then one per step of the chain's
+    // master, then one per step of its helper (pair form)
+    const size_t per_tile = (size_t)(ctx->dag_ntasks + 2 * nbb) * 5;
     size_t need = (size_t)(k + 1) * per_tile;
     if (need > ctx->trace_cap) {
       // grow: keep earlier tiles' records of this factor
@@ -1060,12 +1521,35 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
       ctx->trace_cap = cap;
     }
     trace = ctx->trace_buf + (size_t)k * per_tile;
-    ctx->trace_records = (size_t)(k + 1) * (ctx->dag_ntasks + nbb);
+    ctx->trace_records = (size_t)(k + 1) * (ctx->dag_ntasks + 2 * nbb);
   }
   double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
-  k_potrf_dag<false><<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks,
-                                                       ctx->dag_ntasks, ctx->dag_ws, rinv, ctx->d_status, trace,
-                                                       nullptr, 1, nullptr);
+  if (ctx->dag_pair == 1) {
+    // the chain on cluster 0 (two CTAs), the tasks on the other clusters
+    // two workers per SM: the task throughput paces the chain
+    int g = ctx->dag_ntasks + 1 < 2 * ctx->sm_count ? ctx->dag_ntasks + 1 : 2 * ctx->sm_count;
+    g = (g + 1) & ~1;
+    if (g < 4) g = 4;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(PB * PB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 2;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    EMU_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_potrf_dag<false>, D, nb, k * nb, (const short4 *)ctx->dag_tasks,
+                                         ctx->dag_ntasks, ctx->dag_ws, rinv, ctx->d_status, trace,
+                                         (const long *)nullptr, 1, (int *)nullptr));
+  } else {
+    k_potrf_dag<false><<<grid, PB * PB, 0, ctx->stream>>>(D, nb, k * nb, (const short4 *)ctx->dag_tasks,
+                                                         ctx->dag_ntasks, ctx->dag_ws, rinv, ctx->d_status, trace,
+                                                         nullptr, 1, nullptr);
+  }
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

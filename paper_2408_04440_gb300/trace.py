@@ -7,8 +7,10 @@ POTRF (``emu_trace_*``) and the per-stream timeline of the kernel groups
 Prints a short text summary; ``--save PREFIX`` also writes the raw arrays as
 ``PREFIX_tasks.npy`` and ``PREFIX_timeline.npy``.
 
-Records: one per worker task (TRSM, UPD) and one per step of the chain
-(``LT``: the 16-column step run by the master CTA, from its start to its end).
+Records: one per worker task (TRSM, UPD), one per step of the chain (``LT``:
+the 16-column step run by the master CTA, from its start to its end; "work" is
+the part after its leaf) and, when the chain runs on a cluster of two CTAs,
+one per step of its helper (``HELP``: from its inputs' arrival to X sent).
 Tracing adds global stores inside the kernel, which the publishing fences then
 wait for, so traced times run longer than untraced ones.
 """
@@ -20,7 +22,7 @@ import numpy as np
 
 from . import PROF_GROUPS, Context, emu_cov_build, emu_potrf_mp
 
-KINDS = ("LT", "TRSM", "UPD")
+KINDS = ("LT", "TRSM", "UPD", "", "", "HELP")
 STREAMS = ("ctx", "crit", "panel", "bulk")
 
 
@@ -40,18 +42,16 @@ def summarize_tasks(tr: np.ndarray, ntiles: int) -> list[str]:
         line = f"tile {k}: span {done.max() / 1e3:.1f} us"
         for kk, nm in enumerate(KINDS):
             m = kind == kk
-            if m.any():
+            if nm and m.any():
                 line += f"; {nm} n={int(m.sum())} work {((done - ready)[m]).mean() / 1e3:.2f} us"
         leaf = np.sort(done[kind == 0])
         if len(leaf) > 1:
             line += f"; LT step {np.median(np.diff(leaf)) / 1e3:.1f} us (median)"
-            # the master's packed sub-phase durations in SM cycles: the
-            # solve, the compute warps' phase 2, the whole step
+            # the chain's packed sub-phase durations in SM cycles (pair form:
+            # the leaf, the wait for X_{s+1,s} after it, the whole step)
             w = t[kind == 0, 1]
-            solve, comp, step = (w >> 8) & 0x3FFFF, (w >> 26) & 0x7FFFF, (w >> 45) & 0x7FFFF
-            p1 = ready[kind == 0] - t[kind == 0, 2] + t0
-            line += (f" [phase 1 {np.median(p1) / 1e3:.2f} us, phase 2 {np.median((done - ready)[kind == 0]) / 1e3:.2f} us;"
-                     f" cycles: solve {np.median(solve):.0f}, compute phase 2 {np.median(comp):.0f},"
+            f1, f2, step = (w >> 8) & 0x3FFFF, (w >> 26) & 0x7FFFF, (w >> 45) & 0x7FFFF
+            line += (f" [cycles: leaf {np.median(f1):.0f}, wait for X {np.median(f2):.0f},"
                      f" step {np.median(step):.0f}]")
         out.append(line)
     return out

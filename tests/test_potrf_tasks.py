@@ -125,6 +125,40 @@ class Master:
         return False
 
 
+class PairMaster(Master):
+    """The chain on a cluster of two CTAs: step s factors block (s, s) (C_s
+    from step s-1) and releases L_{s,s} at once; then the helper waits for
+    X_{s+1,s-1} and blocks (s+1, s) and (s+1, s+1) after the panels < s-1,
+    applies panel s-1 to both, solves and publishes X_{s+1,s} and forms
+    C_{s+1} = block (s+1, s+1) after panel s-1, minus X_{s+1,s} X_{s+1,s}^T."""
+
+    def step(self):
+        T, s = self.T, self.s
+        if self.phase == 0:
+            C = T.blk(0, 0).copy() if s == 0 else self.C
+            T.put(s, s, np.linalg.cholesky(C))
+            T.st[s, s] = s + 1
+            self.phase = 1
+            return True
+        n1, st = s + 1, T.st
+        if n1 >= T.nbb:
+            self.s += 1
+            return True
+        if (s < 1 or st[n1, s - 1] >= s) and st[n1, s] >= s - 1 and st[n1, n1] >= s - 1:
+            B, Cp = T.blk(n1, s).copy(), T.blk(n1, n1).copy()
+            if s >= 1:
+                B -= T.blk(n1, s - 1) @ T.blk(s, s - 1).T
+                Cp -= T.blk(n1, s - 1) @ T.blk(n1, s - 1).T
+            X = _solve_lt(T.blk(s, s), B)
+            T.put(n1, s, X)
+            st[n1, s] = s + 1
+            self.C = Cp - X @ X.T
+            self.s += 1
+            self.phase = 0
+            return True
+        return False
+
+
 def replay(nb, single_tile, window, seed):
     tasks = E.emu_potrf_task_list(nb, single_tile)
     T = Tile(nb, seed)
@@ -133,7 +167,7 @@ def replay(nb, single_tile, window, seed):
     if single_tile:
         assert tuple(tasks[0]) == (T_MASTER, 0, 0, 0)
         assert not np.any(tasks[1:, 0] == T_MASTER)
-        master = Master(T)
+        master = Master(T) if single_tile == 1 else PairMaster(T)
         tasks = tasks[1:]
     nxt, fetched = 0, []
     while nxt < len(tasks) or fetched or (master is not None and not master.done()):
@@ -151,7 +185,7 @@ def replay(nb, single_tile, window, seed):
     return np.abs(np.tril(T.D) - np.linalg.cholesky(T.A)).max()
 
 
-@pytest.mark.parametrize("single_tile", [True, False])
+@pytest.mark.parametrize("single_tile", [1, 2, 0])
 @pytest.mark.parametrize("nb", [16, 32, 48, 128, 512])
 def test_task_list_never_stalls_and_factors(nb, single_tile):
     for window in (1, 2, 5, 64):
@@ -164,14 +198,16 @@ def test_task_list_never_stalls_and_factors(nb, single_tile):
 def test_task_list_covers_every_update_once():
     nb = 256
     nbb = nb // PB
-    for single_tile in (True, False):
+    for single_tile in (1, 2, 0):
         t = E.emu_potrf_task_list(nb, single_tile)
         upd = {(int(r), int(c), int(s)) for k, r, c, s in t if k == T_UPD}
         assert len(upd) == sum(1 for k in t[:, 0] if k == T_UPD)
         # every panel s updates every block (r, c), c >= s+1, except those
         # the chain (or the fused TRSM / LT update) applies: (s+1, s+1),
-        # (r, s+1) for r >= s+2 (fused into TRSM(r, s+1) / LT(s+2))
-        want = {(r, c, s) for s in range(nbb) for c in range(s + 2, nbb) for r in range(c, nbb)}
+        # (r, s+1) for r >= s+2 (fused into TRSM(r, s+1) / LT(s+2)), and in
+        # the pair form also (s+2, s+2)
+        want = {(r, c, s) for s in range(nbb) for c in range(s + 2, nbb) for r in range(c, nbb)
+                if single_tile != 2 or (r, c) != (s + 2, s + 2)}
         assert upd == want
         trsm = {(int(r), int(c)) for k, r, c, s in t if k == T_TRSM}
         assert trsm == {(r, c) for c in range(nbb) for r in range(c + 2, nbb)}
