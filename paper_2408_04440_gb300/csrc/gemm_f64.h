@@ -80,6 +80,25 @@ emu_status launch_slice_z(emu_ctx *ctx, const double *Z, long ldz, int s, int s_
 emu_status launch_dense_digits(emu_ctx *ctx, const double *X, long ld, int nrows, long col0, long ncols, int npad,
                                long kpad, int *exps, uint16_t *digits);
 
+// Blocked FP64-class panel TRSM X = A L_kk^{-T} (gemm_f64.cu): column block J
+// (TW columns) of every listed tile is solved on the FP64 pipe against the
+// TW x TW diagonal block of L_kk (launch_trsm_block), then its contribution to
+// the later blocks, X_J L_{>J,J}^T, is subtracted as digit products on the
+// tensor cores (launch, K = TW), so the FP64 pipe runs TW/nb of the nb^3 flops
+// of a tile.
+constexpr int TW = 64;
+// Digits of L_kk's column blocks J < nb/TW - 1, rows r >= (J+1) TW (the rows
+// the products read): exps[J nb + r] (biased), plane p of row r at arena row
+// (J NS + p) nb + r of an arena with TW columns.  nb a multiple of BM.
+emu_status launch_lkk_digits(emu_ctx *ctx, const double *Lkk, int nb, int *exps, uint16_t *digits);
+// Column block J of the tiles d_tiles[0..ntiles) of t64 solved in place; Ls /
+// rinvs are L_kk's pre-scaled 32 x 32 diagonal blocks and pivot reciprocals
+// (launch_trsm64_prep).  With digits (not null), the solved block's row
+// exponents and digits for the products: tile z in slot s = slot0 + z,
+// exps[s nb + r], plane p of row r at arena row (s NS + p) nb + r (TW columns).
+emu_status launch_trsm_block(emu_ctx *ctx, double *t64, int nb, const int *d_tiles, int ntiles, const double *Lkk,
+                             int J, const double *Ls, const double *rinvs, int slot0, int *exps, uint16_t *digits);
+
 // out64 (-= or +=) per item, K = nb per segment, on at most max_ctas persistent
 // CTAs; a_plane / b_plane = arena rows between digit planes.
 emu_status launch(emu_ctx *ctx, const CUtensorMap &a, const CUtensorMap &b, const Item *d_items, int nitems,

@@ -460,6 +460,7 @@ struct StepPlan {
   double flops[GR_N] = {}, mma[GR_N] = {};
   bool diag_low = false;
   bool fp64_panel = false;  // FP64-class TRSM or SYRK on the critical or panel stream
+  int b_off1 = 0, b_offr = 0;  // blocked FP64 TRSM: first product item of T1 / TR in items_tr
 };
 
 struct MixedPlan {
@@ -494,6 +495,16 @@ struct MixedPlan {
   uint16_t *d_lkkp = nullptr;         // three BF16 pieces of L_kk (row-major), same slots (tensor-core TRSM)
   double *d_ls64 = nullptr;           // pre-scaled diagonal blocks of L_kk for the FP64 TRSM (nb x 32), same slots
   double *d_rinv64 = nullptr;         // 1 / L_kk(c, c), same slots
+  // blocked FP64-class TRSM (gemm64::launch_trsm_block): products X_J L_{>J,J}^T
+  bool blk64 = false;
+  int nslots_x = 0;                   // digit slots of solved blocks: 0 = row k+1, 1.. = rows >= k+2
+  gemm64::Item *d_items_tr = nullptr;
+  gemm64::Seg *d_segs_tr = nullptr;
+  uint16_t *d_xdig = nullptr;         // nslots_x * NS planes of nb x TW
+  int *d_xexp = nullptr;              // nslots_x * nb
+  uint16_t *d_ldig = nullptr;         // L_kk's column blocks, double-buffered by step parity
+  int *d_lexp = nullptr;
+  CUtensorMap map_xa, map_lb[2];
   CUtensorMap lmap;                   // over d_lkkp
   CUtensorMap opmap;                  // over the piece arena (the TRSM's tile stores)
   bool tc_trsm = false;               // FP32-class panel TRSMs on the tensor cores (trsm_tc.cu)
@@ -510,7 +521,8 @@ struct MixedPlan {
 static void plan_free(MixedPlan *p) {
   if (!p) return;
   if (p->d_blob) cudaFreeAsync(p->d_blob, p->stream);
-  for (void *q : {(void *)p->d_digits, (void *)p->d_exp64, (void *)p->d_dig_s, (void *)p->d_exp_s})
+  for (void *q : {(void *)p->d_digits, (void *)p->d_exp64, (void *)p->d_dig_s, (void *)p->d_exp_s,
+                  (void *)p->d_xdig, (void *)p->d_xexp, (void *)p->d_ldig, (void *)p->d_lexp})
     if (q) cudaFreeAsync(q, p->stream);
   delete p;
 }
@@ -693,6 +705,44 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     zr_step.clear();
     P->steps.push_back(sp);
   }
+  // blocked FP64-class TRSM: per step and list (row k+1 in slot 0, rows >= k+2
+  // in slots 1..), for each column block J < nJ - 1 the products of every
+  // listed tile's (BM-row block, later TW-column block) pairs, J-major
+  std::vector<gemm64::Item> items_tr;
+  std::vector<gemm64::Seg> segs_tr;
+  const int nJ = nb / gemm64::TW;
+  P->blk64 = nb % gemm64::BM == 0 && nJ >= 2;
+  if (P->blk64) {
+    int max_r = 0;
+    for (StepPlan &sp : P->steps) {
+      max_r = std::max(max_r, sp.n64_r);
+      for (int list = 0; list < 2; list++) {
+        const int r0 = list ? sp.r64_r : sp.r64_1, n = list ? sp.n64_r : sp.n64_1, slot0 = list;
+        (list ? sp.b_offr : sp.b_off1) = (int)items_tr.size();
+        for (int J = 0; J + 1 < nJ; J++)
+          for (int z = 0; z < n; z++)
+            for (int rb = 0; rb < nb / gemm64::BM; rb++)
+              for (int cb = J + 1; cb < nJ; cb++) {
+                gemm64::Seg sg;
+                sg.a_row = (slot0 + z) * gemm64::NS * nb + rb * gemm64::BM;
+                sg.b_row = J * gemm64::NS * nb + cb * gemm64::TW;
+                sg.a_x = sg.b_x = 0;
+                gemm64::Item it;
+                it.out_off = (long)tiles64[r0 + z] * nb * nb + rb * gemm64::BM + (long)cb * gemm64::TW * nb;
+                it.a_sc = (slot0 + z) * nb + rb * gemm64::BM;
+                it.b_sc = J * nb + cb * gemm64::TW;
+                it.seg_begin = (int)segs_tr.size();
+                segs_tr.push_back(sg);
+                it.seg_end = (int)segs_tr.size();
+                it.rows_valid = gemm64::BM;
+                it.cols_valid = gemm64::TW;
+                items_tr.push_back(it);
+              }
+      }
+    }
+    P->nslots_x = 1 + max_r;
+    if (items_tr.empty()) P->blk64 = false;
+  }
   // one allocation and one copy for all lists (256-byte aligned parts)
   size_t off = 0;
   auto part = [&](size_t bytes) {
@@ -705,6 +755,7 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
          o_s64 = part(vbytes(segs64)), o_z = part(vbytes(zjobs)),
          o_items = part(vbytes(items)), o_segs = part(vbytes(segs)), o_t64 = part(vbytes(tiles64)),
          o_diag = part(vbytes(diag)), o_q = part(vbytes(qtiles)), o_tt = part(vbytes(ttiles)),
+         o_itr = part(vbytes(items_tr)), o_str = part(vbytes(segs_tr)),
          o_lkk = part(2 * (size_t)nb * nb * sizeof(float)), o_lkkp = part(2 * 3 * (size_t)nb * nb * sizeof(uint16_t)),
          o_ls64 = part(2 * (size_t)nb * 32 * sizeof(double)), o_rinv64 = part(2 * (size_t)nb * sizeof(double));
   size_t copy_bytes = o_lkk;  // everything before the L_kk buffers comes from the host
@@ -723,6 +774,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   put(o_diag, diag);
   put(o_q, qtiles);
   put(o_tt, ttiles);
+  put(o_itr, items_tr);
+  put(o_str, segs_tr);
   P->stream = ctx->stream;
   EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_blob, off, ctx->stream));
   char *b = static_cast<char *>(P->d_blob);
@@ -738,6 +791,8 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   P->d_diag_tiles = reinterpret_cast<int *>(b + o_diag);
   P->d_qtiles = reinterpret_cast<int *>(b + o_q);
   P->d_ttiles = reinterpret_cast<int *>(b + o_tt);
+  P->d_items_tr = reinterpret_cast<gemm64::Item *>(b + o_itr);
+  P->d_segs_tr = reinterpret_cast<gemm64::Seg *>(b + o_str);
   P->d_lkk32 = reinterpret_cast<float *>(b + o_lkk);
   P->d_lkkp = reinterpret_cast<uint16_t *>(b + o_lkkp);
   P->d_ls64 = reinterpret_cast<double *>(b + o_ls64);
@@ -766,6 +821,22 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
     uint64_t drows = (uint64_t)P->nslots * gemm64::NS * nb;
     if ((s = gemm64::make_map(ctx, &P->map64a, P->d_digits, nb, drows, gemm64::BM)) != EMU_OK) return s;
     if ((s = gemm64::make_map(ctx, &P->map64b, P->d_digits, nb, drows, gemm64::BN)) != EMU_OK) return s;
+  }
+  if (P->blk64) {
+    const size_t xplane = (size_t)nb * gemm64::TW, lbuf = (size_t)(nJ - 1) * gemm64::NS * xplane;
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_xdig, (size_t)P->nslots_x * gemm64::NS * xplane * sizeof(uint16_t),
+                                      ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_xexp, (size_t)P->nslots_x * nb * sizeof(int), ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_ldig, 2 * lbuf * sizeof(uint16_t), ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMallocAsync(&P->d_lexp, 2 * (size_t)(nJ - 1) * nb * sizeof(int), ctx->stream));
+    EMU_CUDA_TRY(ctx, cudaMemsetAsync(P->d_lexp, 0, 2 * (size_t)(nJ - 1) * nb * sizeof(int), ctx->stream));
+    if ((s = gemm64::make_map(ctx, &P->map_xa, P->d_xdig, gemm64::TW, (uint64_t)P->nslots_x * gemm64::NS * nb,
+                              gemm64::BM)) != EMU_OK)
+      return s;
+    for (int q = 0; q < 2; q++)
+      if ((s = gemm64::make_map(ctx, &P->map_lb[q], P->d_ldig + q * lbuf, gemm64::TW,
+                                (uint64_t)(nJ - 1) * gemm64::NS * nb, gemm64::BN)) != EMU_OK)
+        return s;
   }
   if (P->any_e4m3) {
     size_t te = (size_t)nb * nb;
@@ -1085,12 +1156,41 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
     if (e != EMU_OK) return e;
     return gemm64::launch_slice(ctx, A->t64, A->t32, A->d_cls, P->d_zjobs + z0, nz, nb, P->d_exp64, P->d_digits);
   };
+  const int nJ = nb / gemm64::TW;
+  const size_t lbuf = (size_t)(nJ - 1) * gemm64::NS * nb * gemm64::TW;
+  // blocked FP64-class TRSM of n64 listed tiles: per column block J, the
+  // block solve on the FP64 pipe, then X_J L_{>J,J}^T off the later blocks
+  // as digit products (items J-major from b_off)
+  auto trsm64_blocked = [&](int k, int r64, int n64, int slot0, int b_off) -> emu_status {
+    ProfScope ps(ctx, PROF_TRSM64, n64 * nb3, 16.0 * n64 * te, 36.0 * n64 * nb3 * (nJ - 1) / nJ);
+    const double *Lkk = A->t64 + tile_index(k, k, NT) * te;
+    const double *Ls = P->d_ls64 + (size_t)(k & 1) * nb * 32, *ri = P->d_rinv64 + (size_t)(k & 1) * nb;
+    const int per_pair = n64 * (nb / gemm64::BM);
+    int off = b_off;
+    for (int J = 0; J < nJ; J++) {
+      const bool last = J + 1 == nJ;
+      emu_status e = gemm64::launch_trsm_block(ctx, A->t64, nb, P->d_tiles64 + r64, n64, Lkk, J, Ls, ri, slot0,
+                                               P->d_xexp, last ? nullptr : P->d_xdig);
+      if (e != EMU_OK || last) return e;
+      const int cnt = per_pair * (nJ - 1 - J);
+      if ((e = gemm64::launch(ctx, P->map_xa, P->map_lb[k & 1], P->d_items_tr + off, cnt, P->d_segs_tr,
+                              gemm64::TW, nb, nb, P->d_xexp, P->d_lexp + (size_t)(k & 1) * (nJ - 1) * nb,
+                              gemm64::TC64_SUB, A->t64, nb, ctx->sm_count)) != EMU_OK)
+        return e;
+      off += cnt;
+    }
+    return EMU_OK;
+  };
   auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
     emu_status e = EMU_OK;
     if (n64 > 0) {
-      if ((e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64, P->d_ls64 + (size_t)(k & 1) * nb * 32,
-                                   P->d_rinv64 + (size_t)(k & 1) * nb)) != EMU_OK)
-        return e;
+      const StepPlan &sp = P->steps[k];
+      if (P->blk64)
+        e = trsm64_blocked(k, r64, n64, critical ? 0 : 1, critical ? sp.b_off1 : sp.b_offr);
+      else
+        e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64, P->d_ls64 + (size_t)(k & 1) * nb * 32,
+                                P->d_rinv64 + (size_t)(k & 1) * nb);
+      if (e != EMU_OK) return e;
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
       k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
                                                                                     P->d_tiles64 + r64, nb, 0, st);
@@ -1158,6 +1258,10 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
     if (sp.n64_1 + sp.n64_r > 0 &&
         (s = launch_trsm64_prep(ctx, A->t64 + tkk * te, nb, P->d_ls64 + (size_t)(k & 1) * nb * 32,
                                 P->d_rinv64 + (size_t)(k & 1) * nb)) != EMU_OK)
+      break;
+    if (sp.n64_1 + sp.n64_r > 0 && P->blk64 &&
+        (s = gemm64::launch_lkk_digits(ctx, A->t64 + tkk * te, nb, P->d_lexp + (size_t)(k & 1) * (nJ - 1) * nb,
+                                       P->d_ldig + (k & 1) * lbuf)) != EMU_OK)
       break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
