@@ -186,14 +186,18 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
  * second word packs the SM id (bits 0-7) with three saturated durations in SM
  * clock cycles: the leaf (bits 8-25), the wait for the next sub-diagonal
  * block after it (bits 26-44) and the whole step (bits 45-63).  (When the
- * chain runs on one CTA because clusters of two cannot be resident, the
+ * chain runs on one CTA because clusters of three cannot be resident, the
  * second word holds the solve of block (s, s-1) and the compute warps' second
- * phase instead, and the middle timestamp ends the solve.)  In the pair form
- * the helper's records follow (kind 5, one per step s < nb/16 - 1): r = s+1,
- * c = s, the start of its step, the arrival of its inputs (X_{s+1,s-1} and
- * blocks (s+1, s), (s+1, s+1)) and the time X_{s+1,s} was sent and
- * published; the second word packs the SM id with the nanoseconds from the
- * inputs to the end of the solve (bits 8-25).
+ * phase instead, and the middle timestamp ends the solve.)  In the cluster
+ * form the first helper's records follow (kind 5, one per step s < nb/16 - 1):
+ * r = s+1, c = s, the start of its step, the arrival of its inputs
+ * (X_{s+1,s-1} and blocks (s+1, s), (s+1, s+1)) and the time C_{s+1} was
+ * sent and X_{s+1,s} published; the second word packs the SM id with the
+ * nanoseconds from the inputs to the end of the solve (bits 8-25).  Then the
+ * second helper's (kind 6, one per step s < nb/16 - 2): r = s+2, c = s, the
+ * start of its step, the arrival of its inputs, the publication of X_{s+2,s},
+ * and in the second word the nanoseconds from the inputs to the end of the
+ * solve.
  * emu_trace_read copies up to max_records records to host memory and reports
  * how many the last factor wrote. */
 emu_status emu_trace_enable(emu_ctx *ctx, int on);
@@ -209,9 +213,9 @@ emu_status emu_trace_read(emu_ctx *ctx, uint64_t *h_records, size_t max_records,
  * (16x16 blocks).  No task applies panel s to blocks (s+1, s+1) and
  * (s+2, s+1): the chain does.  single_tile = 1 gives the list of the
  * single-matrix factor whose chain runs on one CTA (one master task at the
- * head), 2 the list when the chain runs on a cluster of two CTAs (the head
- * task is not fetched, and the chain also applies panel s to block
- * (s+2, s+2)), 0 the batch form (one kind-0 task per step).  Writes min(n, max_tasks) tasks to h_tasks (may be
+ * head), 2 the list when the chain runs on a cluster of three CTAs (the head
+ * task is not fetched, and the chain also solves blocks (c+2, c) and applies
+ * panel s to block (s+2, s+2)), 0 the batch form (one kind-0 task per step).  Writes min(n, max_tasks) tasks to h_tasks (may be
  * NULL with max_tasks 0) and n to *n_tasks.  EMU_EINVAL unless nb is a
  * positive multiple of 16 no larger than 2048. */
 emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_tasks, size_t max_tasks, size_t *n_tasks);

@@ -465,7 +465,7 @@ def emu_mat_export(ctx: Context, A: Mat, out=None):
 def emu_potrf_task_list(nb: int, single_tile: int = 1) -> np.ndarray:
     """Task list of the dataflow POTRF of one nb x nb diagonal tile, rows
     (kind, r, c, s) in fetch order (host only; see emucov.h): single_tile 1
-    (chain on one CTA), 2 (chain on a cluster of two CTAs) or 0 (batch)."""
+    (chain on one CTA), 2 (chain on a cluster of three CTAs) or 0 (batch)."""
     L = load()
     n = ctypes.c_size_t(0)
     st = L.emu_potrf_task_list(int(nb), int(single_tile), None, 0, ctypes.byref(n))

@@ -89,9 +89,9 @@ struct emu_ctx {
   int *dag_ws = nullptr;
   size_t dag_ws_bytes = 0;
   int dag_ntasks = 0, dag_nbb = 0;
-  // 1: the single-tile POTRF runs its chain on a cluster of two CTAs; 0: on
+  // 1: the single-tile POTRF runs its chain on a cluster of three CTAs; 0: on
   // one CTA (clusters of this kernel cannot be resident); -1: not yet probed
-  int dag_pair = -1;
+  int dag_clus = -1;
   // batched factor (batch.cu): arenas, plan and captured graph of the last batch
   void *batch = nullptr;
   // single-matrix mixed factor (mixed.cu): captured graph, tuning table

@@ -46,7 +46,7 @@ __device__ inline bool failed(const int *st) {
 // X_{s,s-1} before its leaf, so that LT(s+1) applies panel s-1 to block
 // (s+1, s) while the leaf runs.
 constexpr int PB = 16;
-enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3, T_HELP = 5 };
+enum { T_LT = 0, T_TRSM = 1, T_UPD = 2, T_MASTER = 3, T_HELP = 5, T_HELP2 = 6 };
 // wait bound in SM clock cycles (about 2 s at 2 GHz)
 constexpr long long kDagWaitCycles = 4000000000ll;
 
@@ -134,7 +134,7 @@ __device__ inline void bar_sync_128(int id) { asm volatile("bar.sync %0, 128;" :
 __device__ inline void bar_sync_256(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
 __device__ inline void bar_arrive_256(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
 
-// ---- thread-block cluster of two (the single-tile chain on two SMs)
+// ---- thread-block cluster (the single-tile chain on three SMs)
 __device__ inline uint32_t cluster_nctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
@@ -477,38 +477,39 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
   }
 }
 
-// The chain of one tile on a cluster of two CTAs (CTA ranks 0 and 1 of
+// The chain of one tile on a cluster of three CTAs (ranks 0, 1 and 2 of
 // cluster 0; the other clusters run the TRSM / UPD tasks).  The master (rank
-// 0) keeps the four FP64 pipes of its SM for the leaf and the product that
-// forms the next diagonal block; the helper (rank 1) does the rest of the
-// step on its own SM and the two exchange data through distributed shared
-// memory:
+// 0) keeps the four FP64 pipes of its SM for the leaf; the helpers do the
+// rest of each step on their own SMs, and the three exchange data through
+// distributed shared memory:
 //   master, warps 0..3: factor C_s (block (s, s) after every panel < s, in
 //     registers v0, v1) with the leaf, which leaves each scaled column
 //     c_j / c_jj in xr[j] (local mbar[j]) and 1/L_kk in rinv (mbar[16]); then
 //     wait for C_{s+1} (written into this CTA's xc, mbar[17]);
-//   master, warps 4..7: 16 threads forward each column and then 1/L_kk into
-//     the helper's ms and rinv (arriving on its mbar[j], mbar[16]); then all
-//     publish L_{s,s} and its pivot reciprocals as soon as the leaf ends;
-//   helper, warps 0..3: load block (s+1, s) after the panels < s-1, wait
-//     for X_{s+1,s-1} (TRSM(s+1, s-1)), apply panel s-1 (B), solve
-//     X_{s+1,s} = B L_{s,s}^{-T} one column behind the leaf, scale it by
-//     1/L_jj and publish it;
-//   helper, warps 4..7: C' = block (s+1, s+1) after the panels < s-1, minus
-//     X_{s+1,s-1} X_{s+1,s-1}^T;
-//   helper, all: C_{s+1} = C' - X_{s+1,s} X_{s+1,s}^T, one entry per thread,
-//     into the master's xc.
-// mbar phases advance once per step (parity s & 1).  flags[2] of each CTA
-// is set by the other when it stops (a failed pivot or wait), and every wait
-// on the peer also gives up at that flag or the wait bound; both CTAs end at
-// one cluster barrier, so neither leaves while the other may still write into
-// its shared memory.
+//   master, warps 4 and 5: 16 threads each forward every column and then
+//     1/L_kk to one helper; then warps 4..7 publish L_{s,s} and its pivot
+//     reciprocals as soon as the leaf ends;
+//   first helper (rank 1), warps 0..3: block (s+1, s) after the panels < s-1
+//     minus X_{s+1,s-1} X_{s,s-1}^T (X_{s+1,s-1} from the second helper's
+//     step s-1), solved one column behind the leaf into X_{s+1,s}, scaled by
+//     1/L_jj and published;
+//   first helper, warps 4..7: C' = block (s+1, s+1) after the panels < s-1,
+//     minus X_{s+1,s-1} X_{s+1,s-1}^T, then C_{s+1} = C' - X_{s+1,s}
+//     X_{s+1,s}^T accumulated column by column as the solve finishes each,
+//     into the master's xc;
+//   second helper (rank 2): block (s+2, s) solved the same way into
+//     X_{s+2,s} (potrf_tri_helper).
+// The master's mbar phases advance once per step (parity s & 1).  flags[2]
+// of each CTA is set by another when it stops (a failed pivot or wait), and
+// every wait on a peer also gives up at that flag or the wait bound; the
+// three CTAs end at one cluster barrier, so none leaves while another may
+// still write into its shared memory.
 __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb, int gcol0, int *__restrict__ state,
                                                   double *__restrict__ rinv_g, int *st,
                                                   unsigned long long *__restrict__ trace, double (*lout)[PB + 1],
                                                   double (*mcol)[PB + 1], double (*xr)[PB + 1],
-                                                  double (*xc)[PB + 1], double *rinv, volatile int *flags,
-                                                  uint64_t *mbar) {
+                                                  double (*xc)[PB + 1], double *rinv, double (*rinv2)[PB],
+                                                  volatile int *flags, uint64_t *mbar) {
   const int nbb = nb / PB;
   const size_t ld = nb;
   const int tid = threadIdx.x, u = tid & 127;
@@ -516,10 +517,10 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
   const int ir = u & (PB - 1), ic = u >> 4;                                 // warps 4..7
   const int i = u & (PB - 1), k0 = (u >> 5) + 4 * ((u >> 4) & 1), k1 = k0 + 8;  // warps 0..3
   auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
-  // the helper's objects (same layout: its ms is the array this CTA calls mcol)
-  const uint32_t ms_h = peer_addr(mcol, 1), rinv_h = peer_addr(rinv, 1);
-  const uint32_t mbcol_h = peer_addr(&mbar[0], 1), mbr_h = peer_addr(&mbar[16], 1);
-  const uint32_t stop_h = peer_addr((const void *)&flags[2], 1);
+  // the helpers' objects (same layout: a helper's ms is the array this CTA
+  // calls mcol; the second helper takes odd steps' columns in its a, which
+  // this CTA calls lout)
+  const uint32_t stop_h = peer_addr((const void *)&flags[2], 1), stop_h2 = peer_addr((const void *)&flags[2], 2);
   if (io) {
     xc[ir][ic] = __ldcg(gp(0, 0, ir, ic));
     xc[ir][ic + 8] = __ldcg(gp(0, 0, ir, ic + 8));
@@ -549,7 +550,7 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
       }
       bar_arrive_256(6);  // L_{s,s} and 1/L_kk are in lout and rinv
       if (more && !fail) {
-        // C_{s+1}, formed by the helper
+        // C_{s+1}, formed by the first helper
         if (!wait_from_peer(&mbar[17], (uint32_t)s & 1u, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 4;
           flags[0] = 1;
@@ -559,11 +560,21 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
         v1 = xc[i][k1];
       }
     } else {
-      if (u < PB) {
+      const int fw = (tid >> 5) - 4;  // warp 4 feeds the first helper, warp 5 the second
+      if (fw < 2 && (tid & 31) < PB && (fw == 0 || s + 2 < nbb)) {
         // forward the leaf's scaled columns, then 1/L_kk, to the helper as
         // each is formed (the remote store and its cluster-scope release stay
-        // off the leaf's pivot chain)
-        const uint32_t par = (uint32_t)s & 1u;
+        // off the leaf's pivot chain).  First helper: columns into its ms,
+        // barriers mbar[0..15], 1/L_kk into rinv2[s & 1] (barrier mbar[16]
+        // for even steps, mbar[35] for odd ones).  Second helper: even steps
+        // into its mcol and mbar[0..16], odd ones into its lout and
+        // mbar[17..33], 1/L_kk into rinv2[s & 1].
+        const uint32_t par = (uint32_t)s & 1u, odd = (uint32_t)s & 1u;
+        const uint32_t rank = (uint32_t)fw + 1u;
+        const uint32_t ms_h = peer_addr(fw == 1 && odd ? lout : mcol, rank);
+        const uint32_t rinv_h = peer_addr(&rinv2[odd][0], rank);
+        const uint32_t mbcol_h = peer_addr(&mbar[fw == 1 && odd ? PB + 1 : 0], rank);
+        const uint32_t mbr_h = peer_addr(&mbar[fw == 0 ? (odd ? 35 : 16) : (odd ? 2 * PB + 1 : PB)], rank);
 #pragma unroll 1
         for (int j = 0; j <= PB; j++) {
           // the leaf releases columns 0-3, 4-7, 8-11, 12-13, 14, 15 (mbar[3],
@@ -573,16 +584,17 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
             if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 7;
             flags[0] = 1;
           }
+          const int l = tid & 31;  // < PB
           if (j < PB) {
-            st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + u) * 8u, xr[j][u]);
-            if (u == j) st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + PB) * 8u, xr[j][PB]);
+            st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + l) * 8u, xr[j][l]);
+            if (l == j) st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + PB) * 8u, xr[j][PB]);
           } else {
-            st_peer_f64(rinv_h + 8u * u, rinv[u]);
+            st_peer_f64(rinv_h + 8u * l, rinv[l]);
           }
-          // one arrival per column: thread 0's cluster-scope release covers
+          // one arrival per column: lane 0's cluster-scope release covers
           // the stores its partners ordered before it
           __syncwarp(0x0000ffffu);
-          if (u == 0) arrive_peer(j < PB ? mbcol_h + 8u * j : mbr_h);
+          if ((tid & 31) == 0) arrive_peer(j < PB ? mbcol_h + 8u * j : mbr_h);
         }
       }
       bar_sync_256(6);
@@ -597,7 +609,8 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
         }
       }
     }
-    __syncthreads();
+    // one decision for all threads: a peer may set flags[2] at any time
+    const bool stop = __syncthreads_or(flags[1] | flags[0] | flags[2]) != 0;
     if (trace && tid == 0) {
       unsigned smid;
       asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
@@ -613,11 +626,12 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
       rec[3] = t1;
       rec[4] = gtimer();
     }
-    if (flags[1] || flags[0] || flags[2]) {
+    if (stop) {
       if (tid == 0) {
         // the first failure of the factor keeps its pivot
         if (flags[1] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_NOTPD) == DEV_OK) st[ST_PIVOT] = gcol0 + s * PB + flags[1];
         st_peer_s32(stop_h, 1);
+        st_peer_s32(stop_h2, 1);
       }
       break;
     }
@@ -628,7 +642,7 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
 __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
                                                   unsigned long long *__restrict__ trace, double (*ms)[PB + 1],
                                                   double (*xprev)[PB + 1], double (*xo)[PB + 1],
-                                                  double (*uu)[PB + 1], double *rinv, volatile int *flags,
+                                                  double (*uu)[PB + 1], double (*rinv2)[PB], volatile int *flags,
                                                   uint64_t *mbar) {
   const int nbb = nb / PB;
   const size_t ld = nb;
@@ -641,6 +655,7 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
   // address); its mbar[17] counts one arrival per warp of this CTA
   const uint32_t xc_m = peer_addr(xo, 0);
   const uint32_t mbx_m = peer_addr(&mbar[17], 0), stop_m = peer_addr((const void *)&flags[2], 0);
+  const uint32_t stop_h2 = peer_addr((const void *)&flags[2], 2);
   for (int s = 0; s + 1 < nbb; s++) {
     const int n1 = s + 1;
     const uint32_t par = (uint32_t)s & 1u;
@@ -652,8 +667,7 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       if (!dag_wait2(state, n1 * nbb + s, s - 1, n1 * nbb + n1, s - 1, st)) flags[0] = 1;
       fence_acq_rel_gpu();
     }
-    __syncthreads();
-    if (flags[0] || flags[2]) break;
+    if (__syncthreads_or(flags[0] | flags[2])) break;
     double va, vb;
     if (cw) {
       va = __ldcg(gp(n1, s, cr, ct));
@@ -663,14 +677,13 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       vb = __ldcg(gp(n1, n1, ir, ic + 8));
     }
     if (s >= 1) {
-      // X_{n1,s-1} from TRSM(n1, s-1)
+      // X_{n1,s-1}, published by the second helper in its step s-1
       if (tid == 0) {
         if (!dag_wait(state, n1 * nbb + (s - 1), s, st)) flags[0] = 1;
         fence_acq_rel_gpu();
         if (trace) t1 = gtimer();
       }
-      __syncthreads();
-      if (flags[0] || flags[2]) break;
+      if (__syncthreads_or(flags[0] | flags[2])) break;
       if (!cw) {
         xo[ir][ic] = __ldcg(gp(n1, s - 1, ir, ic));
         xo[ir][ic + 8] = __ldcg(gp(n1, s - 1, ir, ic + 8));
@@ -733,15 +746,17 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       __syncwarp();
       if ((tid & 31) == 0) arrive_peer(mbx_m);  // one per warp (warps 4..7)
     }
-    // X_{n1,s} = u / L_jj, for TRSM tasks and the next step's B
-    if (cw && !wait_from_peer(&mbar[16], par, &flags[2])) {
+    // X_{n1,s} = u / L_jj, for TRSM tasks and the next step's B.  1/L_jj
+    // comes in rinv2[s & 1] (barrier mbar[16] for even steps, mbar[35] for
+    // odd ones, a phase every other step): the master may reach the end of
+    // its next leaf before this wait
+    if (cw && !wait_from_peer(&mbar[(s & 1) ? 35 : 16], (uint32_t)(s >> 1) & 1u, &flags[2])) {
       if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 6;
       flags[0] = 1;
     }
-    __syncthreads();  // every read of xo and xprev above is done
-    if (flags[0] || flags[2]) break;
+    if (__syncthreads_or(flags[0] | flags[2])) break;  // every read of xo and xprev above is done
     if (cw) {
-      const double xa = va * rinv[ct], xb = vb * rinv[ct];
+      const double xa = va * rinv2[s & 1][ct], xb = vb * rinv2[s & 1][ct];
       xprev[cr][ct] = xa;
       xprev[cr + 8][ct] = xb;
       __stcg(gp(n1, s, cr, ct), xa);
@@ -769,8 +784,116 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
     }
     __syncthreads();
   }
-  // a stop of this CTA (failed wait) stops the master's wait for X as well
-  if (tid == 0 && flags[0]) st_peer_s32(stop_m, 1);
+  // a stop of this CTA (failed wait) stops the other two CTAs' waits as well
+  if (tid == 0 && flags[0]) {
+    st_peer_s32(stop_m, 1);
+    st_peer_s32(stop_h2, 1);
+  }
+  cluster_barrier();
+}
+
+// The chain's second helper (CTA rank 2): in step s it solves block (s+2, s)
+// one column behind the master's leaf, as the first helper solves block
+// (s+1, s): block (s+2, s) after the panels < s-1 (UPD tasks), minus
+// X_{s+2,s-1} X_{s,s-1}^T (X_{s+2,s-1} from a TRSM task, X_{s,s-1} from the
+// first helper), is solved against L_{s,s} as its columns arrive and
+// published as X_{s+2,s}, which the first helper's step s+1 and the UPD tasks
+// of panel s read.  The columns come in two buffers (this CTA's ms0 and
+// barriers mbar[0..16] in even steps, ms1 and mbar[17..33] in odd ones, 1/L_kk
+// in rinv2[s & 1]), so that the master may run a step ahead of this CTA: its
+// step s+2 waits for the first helper's step s+1, which waits for this CTA's
+// X_{s+2,s}.
+__device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
+                                                 unsigned long long *__restrict__ trace, double (*ms0)[PB + 1],
+                                                 double (*ms1)[PB + 1], double (*xn)[PB + 1], double (*xs)[PB + 1],
+                                                 double (*rinv2)[PB], volatile int *flags, uint64_t *mbar) {
+  const int nbb = nb / PB;
+  const size_t ld = nb;
+  const int tid = threadIdx.x, u = tid & 127;
+  const bool cw = tid < 128;                 // warps 0..3: rows cr, cr + 8 of column ct
+  const int cr = u >> 4, ct = u & (PB - 1);
+  const int er = tid & (PB - 1), ec = tid >> 4;  // all threads: entry (er, ec) of a block
+  auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
+  const uint32_t stop_m = peer_addr((const void *)&flags[2], 0), stop_h = peer_addr((const void *)&flags[2], 1);
+  for (int s = 0; s + 2 < nbb; s++) {
+    const int n2 = s + 2, b = s & 1;
+    const uint32_t par = (uint32_t)(s >> 1) & 1u;
+    double(*ms)[PB + 1] = b ? ms1 : ms0;
+    uint64_t *mb = mbar + (b ? PB + 1 : 0);
+    unsigned long long t0 = 0, t1 = 0, t2 = 0;  // trace only
+    if (tid == 0) {
+      if (trace) t0 = gtimer();
+      // block (s+2, s) after the panels < s-1, X_{s+2,s-1} and X_{s,s-1}
+      if (!dag_wait3(state, n2 * nbb + s, s - 1, s >= 1 ? n2 * nbb + (s - 1) : -1, s,
+                     s >= 1 ? s * nbb + (s - 1) : -1, s, st))
+        flags[0] = 1;
+      fence_acq_rel_gpu();
+      if (trace) t1 = gtimer();
+    }
+    if (__syncthreads_or(flags[0] | flags[2])) break;
+    double va = 0.0, vb = 0.0;
+    if (cw) {
+      va = __ldcg(gp(n2, s, cr, ct));
+      vb = __ldcg(gp(n2, s, cr + 8, ct));
+    }
+    if (s >= 1) {
+      xn[er][ec] = __ldcg(gp(n2, s - 1, er, ec));
+      xs[er][ec] = __ldcg(gp(s, s - 1, er, ec));
+      __syncthreads();
+      if (cw) {
+        // panel s-1 applied to block (s+2, s)
+        va -= panel_dot(xn, xs, cr, ct);
+        vb -= panel_dot(xn, xs, cr + 8, ct);
+      }
+    }
+    if (cw) {
+      // X_{s+2,s} L_{s,s}^T = B2, column j once the leaf has formed column j
+#pragma unroll
+      for (int j = 0; j < PB; j++) {
+        if (!wait_from_peer(&mb[j], par, &flags[2])) {
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 9;
+          flags[0] = 1;
+        }
+        const double aj = __shfl_sync(0xffffffffu, va, j, PB), bj = __shfl_sync(0xffffffffu, vb, j, PB);
+        if (ct > j) {
+          const double mj = ms[j][ct];
+          va = fma(-aj, mj, va);
+          vb = fma(-bj, mj, vb);
+        }
+      }
+      if (!wait_from_peer(&mb[PB], par, &flags[2])) {
+        if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 10;
+        flags[0] = 1;
+      }
+      if (trace && tid == 0) t2 = gtimer();
+      if (!flags[0] && !flags[2]) {
+        const double r = rinv2[b][ct];
+        __stcg(gp(n2, s, cr, ct), va * r);
+        __stcg(gp(n2, s, cr + 8, ct), vb * r);
+      }
+      bar_sync_128(2);
+      if (tid == 0 && !flags[0] && !flags[2]) {
+        fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
+        atomicExch(&state[n2 * nbb + s], s + 1);
+        if (trace) {
+          unsigned smid;
+          asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+          unsigned long long *rec = trace + (size_t)s * 5;
+          rec[0] = (unsigned long long)T_HELP2 | ((unsigned long long)n2 << 8) | ((unsigned long long)s << 24) |
+                   ((unsigned long long)s << 40);
+          rec[1] = (smid & 0xFFull) | (min(t2 - t1, 0x3ffffull) << 8);  // ns from the inputs to the solve's end
+          rec[2] = t0;
+          rec[3] = t1;
+          rec[4] = gtimer();
+        }
+      }
+    }
+    if (__syncthreads_or(flags[0] | flags[2])) break;  // xn / xs are read; flags agree
+  }
+  if (tid == 0 && flags[0]) {
+    st_peer_s32(stop_m, 1);
+    st_peer_s32(stop_h, 1);
+  }
   cluster_barrier();
 }
 
@@ -789,9 +912,10 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   __shared__ double xr[PB][PB + 1];  // panel rows of block r
   __shared__ double xc[PB][PB + 1];  // panel rows of block c (or s)
   __shared__ double rinv[PB];
+  __shared__ double rinv2[2][PB];         // the cluster form's helpers: 1/L_kk of even / odd steps
   __shared__ int s_task, s_ok, bad, s_leave;
   __shared__ int mflags[3];
-  __shared__ uint64_t mbar[2 * PB + 2];  // the pair form's hand-over barriers
+  __shared__ uint64_t mbar[2 * PB + 4];  // the cluster form's hand-over barriers
   // ws = {task counter, then state[nbb*nbb] per tile, then (single tile) the
   // master's SM id + 1 and the number of CTAs that left it}; rinv_all = nb
   // pivot reciprocals per tile.  A batch of nbat tiles (dtiles = their
@@ -805,54 +929,63 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   // it starts there after the master, else after its current task), so that
   // the chain has that SM's FP64 pipes to itself.  At most half the launch
   // leaves, so the chain always keeps workers.
-  // ws extras: master SM id + 1, CTAs that left, helper SM id + 1
+  // ws extras: master SM id + 1, CTAs that left, the helpers' SM ids + 1
   int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
   unsigned my_sm = 0;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
-  // Pair form (one tile launched as clusters of two): cluster 0 runs the
-  // chain (rank 0 the master, rank 1 the helper) and never fetches a task;
-  // the other CTAs fetch tasks 1, 2, ...  Cluster 0 always reaches its final
-  // cluster barrier: its loops stop on the status word inside their bounded
-  // waits rather than returning here.
-  const bool pair = !BATCH && cluster_nctarank() == 2;
-  if (pair && cluster_id_x() == 0) {
+  // Cluster form (one tile launched as clusters of three): cluster 0 runs
+  // the chain (rank 0 the master, ranks 1 and 2 the helpers) and never
+  // fetches a task; the other CTAs fetch tasks 1, 2, ...  Cluster 0 always
+  // reaches its final cluster barrier: its loops stop on the status word
+  // inside their bounded waits rather than returning here.
+  const bool clus = !BATCH && cluster_nctarank() == 3;
+  if (clus && cluster_id_x() == 0) {
     const uint32_t rank = cluster_ctarank();
     if (threadIdx.x == 0) {
       mflags[0] = mflags[1] = mflags[2] = 0;
-      // per column / rinv: the 16 leaf threads (master) or one arrival of
-      // the master's forwarding warp (helper); mbar[17]: one per warp of the
-      // helper
-      for (int j = 0; j < PB + 1; j++) tc::mbar_init(&mbar[j], rank == 0 ? PB : 1);
-      if (rank == 0) tc::mbar_init(&mbar[17], 4);  // warps 4..7 of the helper
-      else
-        for (int j = 0; j < PB; j++) tc::mbar_init(&mbar[18 + j], 8);  // column j of u: one thread per half-warp
+      if (rank == 0) {
+        // per column / rinv: the 16 leaf threads; mbar[17]: C from the first
+        // helper's warps 4..7
+        for (int j = 0; j <= PB; j++) tc::mbar_init(&mbar[j], PB);
+        tc::mbar_init(&mbar[17], 4);
+      } else if (rank == 1) {
+        // columns (one arrival of the master's forwarding warp), rinv of even
+        // / odd steps, column j of u (one thread per half-warp of warps 0..3)
+        for (int j = 0; j <= PB; j++) tc::mbar_init(&mbar[j], 1);
+        tc::mbar_init(&mbar[35], 1);
+        for (int j = 0; j < PB; j++) tc::mbar_init(&mbar[18 + j], 8);
+      } else {
+        // columns and rinv of even / odd steps
+        for (int j = 0; j < 2 * (PB + 1); j++) tc::mbar_init(&mbar[j], 1);
+      }
       tc::fence_barrier_init();
-      atomicExch(master_sm + (rank == 0 ? 0 : 2), (int)my_sm + 1);
+      atomicExch(master_sm + (rank == 0 ? 0 : rank + 1), (int)my_sm + 1);
     }
-    cluster_barrier();  // both CTAs' barriers exist before any remote access
+    cluster_barrier();  // the three CTAs' barriers exist before any remote access
     double *rinv_g = rinv_all;
-    unsigned long long *tr = trace ? trace + (size_t)ntasks * 5 : nullptr;
+    unsigned long long *tr = trace ? trace + (size_t)(ntasks + (size_t)rank * nbb) * 5 : nullptr;
     if (rank == 0)
-      potrf_pair_master(D0, nb, gcol0, ws + 1, rinv_g, st, tr, a, m, xr, xc, rinv, mflags, mbar);
+      potrf_pair_master(D0, nb, gcol0, ws + 1, rinv_g, st, tr, a, m, xr, xc, rinv, rinv2, mflags, mbar);
+    else if (rank == 1)
+      potrf_pair_helper(D0, nb, ws + 1, st, tr, m, xr, xc, a, rinv2, mflags, mbar);
     else
-      potrf_pair_helper(D0, nb, ws + 1, st, trace ? trace + (size_t)(ntasks + nbb) * 5 : nullptr, m, xr, xc, a,
-                        rinv, mflags, mbar);
+      potrf_tri_helper(D0, nb, ws + 1, st, tr, m, a, xr, xc, rinv2, mflags, mbar);
     return;
   }
   // a factor that has already failed (status set by an earlier launch) stops
   if (*((volatile const int *)st) != DEV_OK) return;
-  if (threadIdx.x == 0) {
-    const int m0 = BATCH ? 0 : *((volatile int *)master_sm), h0 = BATCH ? 0 : *((volatile int *)(master_sm + 2));
-    s_leave = !BATCH && (m0 == (int)my_sm + 1 || h0 == (int)my_sm + 1) &&
-              atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2;
-  }
+  // a CTA on one of the chain's SMs
+  auto on_chain_sm = [&]() {
+    if (BATCH) return false;
+    const int me = (int)my_sm + 1;
+    return *((volatile int *)master_sm) == me || *((volatile int *)(master_sm + 2)) == me ||
+           *((volatile int *)(master_sm + 3)) == me;
+  };
+  if (threadIdx.x == 0) s_leave = on_chain_sm() && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2;
   while (true) {
     if (threadIdx.x == 0) {
-      const int m = BATCH ? 0 : *((volatile int *)master_sm), h = BATCH ? 0 : *((volatile int *)(master_sm + 2));
-      s_task = s_leave ? INT_MAX : atomicAdd(counter, 1) + (pair ? 1 : 0);  // pair: task 0 is cluster 0's
-      if (!BATCH && !s_leave && (m == (int)my_sm + 1 || h == (int)my_sm + 1) &&
-          atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2)
-        s_leave = 1;
+      s_task = s_leave ? INT_MAX : atomicAdd(counter, 1) + (clus ? 1 : 0);  // cluster form: task 0 is cluster 0's
+      if (!s_leave && on_chain_sm() && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2) s_leave = 1;
     }
     __syncthreads();
     int t = s_task;
@@ -1043,8 +1176,9 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
 
 // Task list of the dataflow POTRF for nbb blocks per side (see k_potrf_dag),
 // in topological, lookahead-first order.  With master = true the LT tasks
-// are replaced by one T_MASTER task at the head of the list (single tile).
-static void dag_tasks(int nbb, std::vector<short4> &out, bool master, bool pair = false) {
+// are replaced by one T_MASTER task at the head of the list (single tile);
+// clus = true: the chain runs on a cluster of three CTAs.
+static void dag_tasks(int nbb, std::vector<short4> &out, bool master, bool clus = false) {
   out.clear();
   auto push = [&](int kind, int r, int c, int s) {
     out.push_back(make_short4((short)kind, (short)r, (short)c, (short)s));
@@ -1053,26 +1187,21 @@ static void dag_tasks(int nbb, std::vector<short4> &out, bool master, bool pair 
     push(T_MASTER, 0, 0, 0);
   else
     push(T_LT, 0, 0, 0);
-  // Pair form: the helper's step c+1 waits for TRSM(c+2, c), which is
-  // therefore listed right after its last input, UPD(c+2, c, c-2), ahead of
-  // the other updates by panel c-2 (TRSM(3, 1) right after TRSM(3, 0)).
-  for (int r = 2; r < nbb; r++) {
-    push(T_TRSM, r, 0, 0);
-    if (pair && r == 3) push(T_TRSM, 3, 1, 1);
-  }
+  // Cluster form: the helpers solve blocks (c+1, c) and (c+2, c) of each
+  // column c, so TRSM(c+2, c) is not listed either.
+  for (int r = 2; r < nbb; r++)
+    if (!clus || r != 2) push(T_TRSM, r, 0, 0);
   for (int s = 0; s + 1 < nbb; s++) {
     if (!master) push(T_LT, s + 1, s, s + 1);
     // the master's step s+1 waits for UPD(s+2, s+2, s) before the step that
     // releases L_{s+1,s+1}, which the TRSMs of column s+1 wait for: listing
     // it first keeps the list topological whatever number of CTAs is resident
-    if (master && !pair && s + 2 < nbb) push(T_UPD, s + 2, s + 2, s);
+    if (master && !clus && s + 2 < nbb) push(T_UPD, s + 2, s + 2, s);
     for (int r = s + 3; r < nbb; r++)
-      if (!pair || r != s + 3) push(T_TRSM, r, s + 1, s + 1);
+      if (!clus || r != s + 3) push(T_TRSM, r, s + 1, s + 1);
     for (int c = s + 2; c < nbb; c++)
-      for (int r = c; r < nbb; r++) {
-        if (!master || r != s + 2 || c != s + 2) push(T_UPD, r, c, s);  // pair: the helper applies it
-        if (pair && c == s + 2 && r == s + 4) push(T_TRSM, s + 4, s + 2, s + 2);
-      }
+      for (int r = c; r < nbb; r++)
+        if (!master || r != s + 2 || c != s + 2) push(T_UPD, r, c, s);  // cluster form: the first helper applies it
   }
 }
 
@@ -1437,7 +1566,7 @@ extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_ta
 // helper SM id + 1; even, so that the pivot reciprocals after it are 8-byte
 // aligned
 static size_t dag_ws_ints(int nbb, int nbat) {
-  size_t n = 4 + (size_t)nbat * nbb * nbb;
+  size_t n = 5 + (size_t)nbat * nbb * nbb;
   return (n + 1) & ~(size_t)1;
 }
 
@@ -1456,26 +1585,26 @@ emu_status launch_potrf64_tile(emu_ctx *ctx, emu_mat *A, int k) {
 
 emu_status potrf_dag_prepare(emu_ctx *ctx, int nb) {
   int nbb = nb / PB;
-  if (ctx->dag_pair < 0) {
-    // can a cluster of two CTAs of this kernel be resident?
+  if (ctx->dag_clus < 0) {
+    // can a cluster of three CTAs of this kernel be resident?
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2);
+    cfg.gridDim = dim3(3);
     cfg.blockDim = dim3(PB * PB);
     cudaLaunchAttribute at;
     at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = 2;
+    at.val.clusterDim.x = 3;
     at.val.clusterDim.y = 1;
     at.val.clusterDim.z = 1;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int nclusters = 0;
     const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_dag<false>, &cfg);
-    ctx->dag_pair = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
+    ctx->dag_clus = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
     if (e != cudaSuccess) cudaGetLastError();
   }
   if (ctx->dag_nbb != nbb) {
     std::vector<short4> tasks;
-    dag_tasks(nbb, tasks, true, ctx->dag_pair == 1);
+    dag_tasks(nbb, tasks, true, ctx->dag_clus == 1);
     cudaFree(ctx->dag_tasks);
     cudaFree(ctx->dag_ws);
     ctx->dag_tasks = nullptr;
@@ -1503,8 +1632,8 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
   unsigned long long *trace = nullptr;
   if (ctx->trace_on) {
     // per tile: one record per task, then one per step of the chain's
-    // master, then one per step of its helper (pair form)
-    const size_t per_tile = (size_t)(ctx->dag_ntasks + 2 * nbb) * 5;
+    // master and of each of its helpers (cluster form)
+    const size_t per_tile = (size_t)(ctx->dag_ntasks + 3 * nbb) * 5;
     size_t need = (size_t)(k + 1) * per_tile;
     if (need > ctx->trace_cap) {
       // grow: keep earlier tiles' records of this factor
@@ -1521,15 +1650,15 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
       ctx->trace_cap = cap;
     }
     trace = ctx->trace_buf + (size_t)k * per_tile;
-    ctx->trace_records = (size_t)(k + 1) * (ctx->dag_ntasks + 2 * nbb);
+    ctx->trace_records = (size_t)(k + 1) * (ctx->dag_ntasks + 3 * nbb);
   }
   double *rinv = reinterpret_cast<double *>(ctx->dag_ws + dag_ws_ints(nbb, 1));
-  if (ctx->dag_pair == 1) {
-    // the chain on cluster 0 (two CTAs), the tasks on the other clusters
+  if (ctx->dag_clus == 1) {
+    // the chain on cluster 0 (three CTAs), the tasks on the other clusters;
     // two workers per SM: the task throughput paces the chain
-    int g = ctx->dag_ntasks + 1 < 2 * ctx->sm_count ? ctx->dag_ntasks + 1 : 2 * ctx->sm_count;
-    g = (g + 1) & ~1;
-    if (g < 4) g = 4;
+    int g = ctx->dag_ntasks + 2 < 2 * ctx->sm_count ? ctx->dag_ntasks + 2 : 2 * ctx->sm_count;
+    g = (g + 2) / 3 * 3;
+    if (g < 6) g = 6;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g);
     cfg.blockDim = dim3(PB * PB);
@@ -1537,7 +1666,7 @@ emu_status launch_potrf64_ptr(emu_ctx *ctx, double *D, int nb, int k) {
     cfg.stream = ctx->stream;
     cudaLaunchAttribute at;
     at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = 2;
+    at.val.clusterDim.x = 3;
     at.val.clusterDim.y = 1;
     at.val.clusterDim.z = 1;
     cfg.attrs = &at;

@@ -9,8 +9,10 @@ Prints a short text summary; ``--save PREFIX`` also writes the raw arrays as
 
 Records: one per worker task (TRSM, UPD), one per step of the chain (``LT``:
 the 16-column step run by the master CTA, from its start to its end; "work" is
-the part after its leaf) and, when the chain runs on a cluster of two CTAs,
-one per step of its helper (``HELP``: from its inputs' arrival to X sent).
+the part after its leaf) and, when the chain runs on a cluster of three
+CTAs, one per step of each helper (``HELP``: block (s+1, s) and the next
+diagonal block; ``HELP2``: block (s+2, s); from the inputs' arrival to the
+end).
 Tracing adds global stores inside the kernel, which the publishing fences then
 wait for, so traced times run longer than untraced ones.
 """
@@ -22,7 +24,7 @@ import numpy as np
 
 from . import PROF_GROUPS, Context, emu_cov_build, emu_potrf_mp
 
-KINDS = ("LT", "TRSM", "UPD", "", "", "HELP")
+KINDS = ("LT", "TRSM", "UPD", "", "", "HELP", "HELP2")
 STREAMS = ("ctx", "crit", "panel", "bulk")
 
 
@@ -47,7 +49,7 @@ def summarize_tasks(tr: np.ndarray, ntiles: int) -> list[str]:
         leaf = np.sort(done[kind == 0])
         if len(leaf) > 1:
             line += f"; LT step {np.median(np.diff(leaf)) / 1e3:.1f} us (median)"
-            # the chain's packed sub-phase durations in SM cycles (pair form:
+            # the chain's packed sub-phase durations in SM cycles (cluster form:
             # the leaf, the wait for X_{s+1,s} after it, the whole step)
             w = t[kind == 0, 1]
             f1, f2, step = (w >> 8) & 0x3FFFF, (w >> 26) & 0x7FFFF, (w >> 45) & 0x7FFFF

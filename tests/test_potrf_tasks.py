@@ -125,26 +125,39 @@ class Master:
         return False
 
 
-class PairMaster(Master):
-    """The chain on a cluster of two CTAs: step s factors block (s, s) (C_s
-    from step s-1) and releases L_{s,s} at once; then the helper waits for
-    X_{s+1,s-1} and blocks (s+1, s) and (s+1, s+1) after the panels < s-1,
-    applies panel s-1 to both, solves and publishes X_{s+1,s} and forms
-    C_{s+1} = block (s+1, s+1) after panel s-1, minus X_{s+1,s} X_{s+1,s}^T."""
+class ClusterMaster:
+    """The chain on a cluster of three CTAs.  Master: step s factors block
+    (s, s) from C_s (formed by the first helper's step s-1) and releases
+    L_{s,s}.  First helper, step s: once L_{s,s} is released, blocks (s+1, s)
+    and (s+1, s+1) carry the panels < s-1 and X_{s+1,s-1} is published (by
+    the second helper), it applies panel s-1 to both, solves and publishes
+    X_{s+1,s} and forms C_{s+1} = block (s+1, s+1) after panel s-1, minus
+    X_{s+1,s} X_{s+1,s}^T.  Second helper, step s: once L_{s,s} is released,
+    block (s+2, s) carries the panels < s-1 and X_{s+2,s-1} (a TRSM task) and
+    X_{s,s-1} are published, it applies panel s-1, solves and publishes
+    X_{s+2,s}.  The three advance independently, each on its own data."""
+
+    def __init__(self, T):
+        self.T = T
+        self.s = self.sa = self.sb = 0
+        self.C = {0: T.blk(0, 0).copy()}
+
+    def done(self):
+        nbb = self.T.nbb
+        return self.s >= nbb and self.sa >= nbb - 1 and self.sb >= max(nbb - 2, 0)
 
     def step(self):
-        T, s = self.T, self.s
-        if self.phase == 0:
-            C = T.blk(0, 0).copy() if s == 0 else self.C
-            T.put(s, s, np.linalg.cholesky(C))
-            T.st[s, s] = s + 1
-            self.phase = 1
-            return True
-        n1, st = s + 1, T.st
-        if n1 >= T.nbb:
+        T, st, nbb = self.T, self.T.st, self.T.nbb
+        moved = False
+        s = self.s
+        if s < nbb and s in self.C:
+            T.put(s, s, np.linalg.cholesky(self.C.pop(s)))
+            st[s, s] = s + 1
             self.s += 1
-            return True
-        if (s < 1 or st[n1, s - 1] >= s) and st[n1, s] >= s - 1 and st[n1, n1] >= s - 1:
+            moved = True
+        s, n1 = self.sa, self.sa + 1
+        if n1 < nbb and st[s, s] >= s + 1 and st[n1, s] >= s - 1 and st[n1, n1] >= s - 1 and \
+                (s < 1 or st[n1, s - 1] >= s):
             B, Cp = T.blk(n1, s).copy(), T.blk(n1, n1).copy()
             if s >= 1:
                 B -= T.blk(n1, s - 1) @ T.blk(s, s - 1).T
@@ -152,11 +165,20 @@ class PairMaster(Master):
             X = _solve_lt(T.blk(s, s), B)
             T.put(n1, s, X)
             st[n1, s] = s + 1
-            self.C = Cp - X @ X.T
-            self.s += 1
-            self.phase = 0
-            return True
-        return False
+            self.C[n1] = Cp - X @ X.T
+            self.sa += 1
+            moved = True
+        s, n2 = self.sb, self.sb + 2
+        if n2 < nbb and st[s, s] >= s + 1 and st[n2, s] >= s - 1 and \
+                (s < 1 or (st[n2, s - 1] >= s and st[s, s - 1] >= s)):
+            B = T.blk(n2, s).copy()
+            if s >= 1:
+                B -= T.blk(n2, s - 1) @ T.blk(s, s - 1).T
+            T.put(n2, s, _solve_lt(T.blk(s, s), B))
+            st[n2, s] = s + 1
+            self.sb += 1
+            moved = True
+        return moved
 
 
 def replay(nb, single_tile, window, seed):
@@ -167,7 +189,7 @@ def replay(nb, single_tile, window, seed):
     if single_tile:
         assert tuple(tasks[0]) == (T_MASTER, 0, 0, 0)
         assert not np.any(tasks[1:, 0] == T_MASTER)
-        master = Master(T) if single_tile == 1 else PairMaster(T)
+        master = Master(T) if single_tile == 1 else ClusterMaster(T)
         tasks = tasks[1:]
     nxt, fetched = 0, []
     while nxt < len(tasks) or fetched or (master is not None and not master.done()):
@@ -205,12 +227,13 @@ def test_task_list_covers_every_update_once():
         # every panel s updates every block (r, c), c >= s+1, except those
         # the chain (or the fused TRSM / LT update) applies: (s+1, s+1),
         # (r, s+1) for r >= s+2 (fused into TRSM(r, s+1) / LT(s+2)), and in
-        # the pair form also (s+2, s+2)
+        # the cluster form also (s+2, s+2)
         want = {(r, c, s) for s in range(nbb) for c in range(s + 2, nbb) for r in range(c, nbb)
                 if single_tile != 2 or (r, c) != (s + 2, s + 2)}
         assert upd == want
+        # blocks (c+1, c) are the chain's; in the cluster form (c+2, c) too
         trsm = {(int(r), int(c)) for k, r, c, s in t if k == T_TRSM}
-        assert trsm == {(r, c) for c in range(nbb) for r in range(c + 2, nbb)}
+        assert trsm == {(r, c) for c in range(nbb) for r in range(c + (3 if single_tile == 2 else 2), nbb)}
 
 
 def test_task_list_rejects_bad_sizes():
