@@ -195,9 +195,9 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
  * sent and X_{s+1,s} published; the second word packs the SM id with the
  * nanoseconds from the inputs to the end of the solve (bits 8-25).  Then the
  * second helper's (kind 6, one per step s < nb/16 - 2): r = s+2, c = s, the
- * start of its step, the arrival of its inputs, the publication of X_{s+2,s},
- * and in the second word the nanoseconds from the inputs to the end of the
- * solve.
+ * start of its step, the arrival of X_{s+2,s-1} and X_{s,s-1} (its update by
+ * panel s-1), the publication of X_{s+2,s}, and in the second word the
+ * nanoseconds from that arrival to the end of its solves.
  * emu_trace_read copies up to max_records records to host memory and reports
  * how many the last factor wrote. */
 emu_status emu_trace_enable(emu_ctx *ctx, int on);

@@ -110,6 +110,12 @@ __device__ inline bool dag_wait2(const int *state, int i0, int v0, int i1, int v
   return dag_wait3(state, i0, v0, i1, v1, -1, 0, st);
 }
 
+// The leaf releases its columns in groups 0-3, 4-7, 8-11, 12-13, 14, 15
+// (one barrier each, that of the group's last column): whether column j
+// opens its group, and the barrier of j's group.
+__host__ __device__ constexpr bool col_group_first(int j) { return j < 12 ? (j & 3) == 0 : j != 13; }
+__host__ __device__ constexpr int col_group_bar(int j) { return j < 12 ? (j | 3) : (j == 12 ? 13 : j); }
+
 // Pivot reciprocal: the hardware approximation y (relative error about
 // 2^-20, measured) refined by one third-order Newton-Raphson step for 1/d,
 // r = y (1 + e + e^2) with e = 1 - d y, whose truncation error e^3 is below
@@ -167,26 +173,43 @@ __device__ inline void st_peer_s32(uint32_t addr, int v) {
 __device__ inline void arrive_peer(uint32_t bar) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// wait, with cluster-scope acquire, for phase `parity` of a local mbarrier
-// that the peer CTA arrives on; false after the wait bound or when *abort
-// becomes nonzero
-__device__ inline bool wait_from_peer(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// Waits for the phase of the given parity of an mbarrier of this CTA; false
+// after the wait bound or when *abort is set.  SCOPE_CLUSTER: the arrivals
+// come from another CTA of the cluster (their remote stores become visible);
+// else from this CTA.
+template <bool SCOPE_CLUSTER>
+__device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort) {
   const uint32_t a = tc::smem_u32(bar);
   long long t0 = 0;
   for (int it = 0;; it++) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if (SCOPE_CLUSTER)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
     if (ok) return true;
     if (*abort) return false;
     if (it == 0) t0 = clock64();
     else if (clock64() - t0 > c_dag_wait_cycles) return false;
   }
+}
+__device__ inline bool wait_from_peer(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  return wait_phase<true>(bar, parity, abort);
+}
+__device__ inline bool wait_local(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  return wait_phase<false>(bar, parity, abort);
 }
 // every thread of both CTAs; orders each CTA's remote stores before the
 // other's exit
@@ -269,7 +292,7 @@ __device__ __forceinline__ int leaf16(int u, double v0, double v1, double (*mcol
     if (ms) tc::mbar_arrive(&mb[16]);
   }
   bar_sync_128(1);
-  if (!fail) {
+  if (!fail && out) {
     out[i][k0] = v0 * rinv[k0];  // the diagonal: c_kk / sqrt(c_kk)
     out[i][k1] = v1 * rinv[k1];
   }
@@ -484,21 +507,22 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
 // distributed shared memory:
 //   master, warps 0..3: factor C_s (block (s, s) after every panel < s, in
 //     registers v0, v1) with the leaf, which leaves each scaled column
-//     c_j / c_jj in xr[j] (local mbar[j]) and 1/L_kk in rinv (mbar[16]); then
-//     wait for C_{s+1} (written into this CTA's xc, mbar[17]);
-//   master, warps 4 and 5: 16 threads each forward every column and then
-//     1/L_kk to one helper; then warps 4..7 publish L_{s,s} and its pivot
-//     reciprocals as soon as the leaf ends;
+//     c_j / c_jj in xr[j] and 1/L_kk in rinv, released in groups (local
+//     mbar[3], [7], [11], [13], [14], [15], [16]); then wait for C_{s+1}
+//     (written into this CTA's xc, mbar[17]);
+//   master, warps 4..7: two per helper forward alternate groups of columns,
+//     then 1/L_kk; then they publish L_{s,s} and its pivot reciprocals;
 //   first helper (rank 1), warps 0..3: block (s+1, s) after the panels < s-1
 //     minus X_{s+1,s-1} X_{s,s-1}^T (X_{s+1,s-1} from the second helper's
 //     step s-1), solved one column behind the leaf into X_{s+1,s}, scaled by
 //     1/L_jj and published;
-//   first helper, warps 4..7: C' = block (s+1, s+1) after the panels < s-1,
-//     minus X_{s+1,s-1} X_{s+1,s-1}^T, then C_{s+1} = C' - X_{s+1,s}
-//     X_{s+1,s}^T accumulated column by column as the solve finishes each,
-//     into the master's xc;
+//   first helper, warps 4..7: C_{s+1} = C' - X_{s+1,s} X_{s+1,s}^T
+//     accumulated column by column as the solve finishes each, with C'
+//     (block (s+1, s+1) after every panel < s) from the second helper, into
+//     the master's xc;
 //   second helper (rank 2): block (s+2, s) solved the same way into
-//     X_{s+2,s} (potrf_tri_helper).
+//     X_{s+2,s}, then panel s applied to block (s+2, s+2), the first
+//     helper's next C' (potrf_tri_helper).
 // The master's mbar phases advance once per step (parity s & 1).  flags[2]
 // of each CTA is set by another when it stops (a failed pivot or wait), and
 // every wait on a peer also gives up at that flag or the wait bound; the
@@ -521,6 +545,7 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
   // calls mcol; the second helper takes odd steps' columns in its a, which
   // this CTA calls lout)
   const uint32_t stop_h = peer_addr((const void *)&flags[2], 1), stop_h2 = peer_addr((const void *)&flags[2], 2);
+  const uint32_t cfree_h2 = peer_addr(&mbar[34], 2);
   if (io) {
     xc[ir][ic] = __ldcg(gp(0, 0, ir, ic));
     xc[ir][ic + 8] = __ldcg(gp(0, 0, ir, ic + 8));
@@ -542,15 +567,19 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
     if (!io) {
       // the scaled columns go to xr and mbar[0..16], from where warps 4..7
       // forward them
-      const int fail = leaf16(u, v0, v1, mcol, lout, rinv, xr, mbar);
+      // L_{s,s} is mcol[k][i] / sqrt(c_kk): lout stays free for C'
+      const int fail = leaf16(u, v0, v1, mcol, nullptr, rinv, xr, mbar);
       if (fail && u == 0) flags[1] = fail;
       if (trace && tid == 0) {
         t1 = gtimer();
         c1 = clock64();
       }
-      bar_arrive_256(6);  // L_{s,s} and 1/L_kk are in lout and rinv
+      bar_arrive_256(6);  // the columns of L_{s,s} and 1/L_kk are in mcol and rinv
       if (more && !fail) {
-        // C_{s+1}, formed by the first helper
+        // C_{s+1} = C' - S: S = X_{s+1,s} X_{s+1,s}^T from the first helper
+        // (-S in xc; in step 0 it sends C_1 itself), C' = block (s+1, s+1)
+        // after every panel < s from the second helper (in lout, from step
+        // 1 on), which this CTA's compute warps then release to it again
         if (!wait_from_peer(&mbar[17], (uint32_t)s & 1u, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 4;
           flags[0] = 1;
@@ -558,49 +587,66 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
         if (trace && tid == 0) c7 = clock64();
         v0 = xc[i][k0];
         v1 = xc[i][k1];
+        if (s >= 1) {
+          if (!wait_from_peer(&mbar[18], (uint32_t)(s - 1) & 1u, &flags[2])) {
+            if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 13;
+            flags[0] = 1;
+          }
+          v0 += lout[i][k0];
+          v1 += lout[i][k1];
+          __syncwarp();
+          if ((tid & 31) == 0 && s + 2 < nbb) arrive_peer(cfree_h2);  // the second helper's next C' may come
+        }
       }
     } else {
-      const int fw = (tid >> 5) - 4;  // warp 4 feeds the first helper, warp 5 the second
-      if (fw < 2 && (tid & 31) < PB && (fw == 0 || s + 2 < nbb)) {
-        // forward the leaf's scaled columns, then 1/L_kk, to the helper as
-        // each is formed (the remote store and its cluster-scope release stay
-        // off the leaf's pivot chain).  First helper: columns into its ms,
-        // barriers mbar[0..15], 1/L_kk into rinv2[s & 1] (barrier mbar[16]
-        // for even steps, mbar[35] for odd ones).  Second helper: even steps
-        // into its mcol and mbar[0..16], odd ones into its lout and
-        // mbar[17..33], 1/L_kk into rinv2[s & 1].
+      // forward the leaf's scaled columns, then 1/L_kk, to the helpers in
+      // the groups the leaf releases them in (columns 0-3, 4-7, 8-11, 12-13,
+      // 14, 15, then 1/L_kk: local mbar[3], [7], [11], [13], [14], [15],
+      // [16]); each group's remote stores are released by one cluster-scope
+      // arrival on the helper's barrier of the group's last column, and two
+      // warps per helper take alternate groups, so that two releases are in
+      // flight (the remote store and its release stay off the leaf's pivot
+      // chain).  First helper (warps 4, 6): columns into its ms, 1/L_kk into
+      // rinv2[s & 1] (barrier mbar[16] for even steps, mbar[35] for odd ones).
+      // Second helper (warps 5, 7): even steps into its mcol and
+      // mbar[0..16], odd ones into its lout and mbar[17..33], 1/L_kk into
+      // rinv2[s & 1].
+      const int fw = (tid >> 5) - 4, h = fw & 1, half = fw >> 1;
+      if ((tid & 31) < PB && (h == 0 ? s + 1 < nbb : s + 2 < nbb)) {
         const uint32_t par = (uint32_t)s & 1u, odd = (uint32_t)s & 1u;
-        const uint32_t rank = (uint32_t)fw + 1u;
-        const uint32_t ms_h = peer_addr(fw == 1 && odd ? lout : mcol, rank);
+        const uint32_t rank = (uint32_t)h + 1u;
+        const uint32_t ms_h = peer_addr(h == 1 && odd ? lout : mcol, rank);
         const uint32_t rinv_h = peer_addr(&rinv2[odd][0], rank);
-        const uint32_t mbcol_h = peer_addr(&mbar[fw == 1 && odd ? PB + 1 : 0], rank);
-        const uint32_t mbr_h = peer_addr(&mbar[fw == 0 ? (odd ? 35 : 16) : (odd ? 2 * PB + 1 : PB)], rank);
+        const uint32_t mbcol_h = peer_addr(&mbar[h == 1 && odd ? PB + 1 : 0], rank);
+        const uint32_t mbr_h = peer_addr(&mbar[h == 0 ? (odd ? 35 : 16) : (odd ? 2 * PB + 1 : PB)], rank);
+        const int l = tid & 31;  // < PB
 #pragma unroll 1
-        for (int j = 0; j <= PB; j++) {
-          // the leaf releases columns 0-3, 4-7, 8-11, 12-13, 14, 15 (mbar[3],
-          // [7], [11], [13], [14], [15]), then rinv (mbar[16])
-          const int wb = j < 12 ? ((j & 3) == 0 ? j + 3 : -1) : (j == 12 ? 13 : (j == 13 ? -1 : j));
-          if (wb >= 0 && !tc::mbar_wait(&mbar[wb], par, &flags[2])) {
+        for (int g = half; g < 7; g += 2) {
+          const int j0 = g < 3 ? 4 * g : (g == 3 ? 12 : g + 10);
+          const int j1 = g < 3 ? 4 * g + 3 : (g == 3 ? 13 : g + 10);
+          if (!wait_local(&mbar[j1], par, &flags[2])) {
             if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 7;
             flags[0] = 1;
           }
-          const int l = tid & 31;  // < PB
-          if (j < PB) {
-            st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + l) * 8u, xr[j][l]);
-            if (l == j) st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + PB) * 8u, xr[j][PB]);
-          } else {
-            st_peer_f64(rinv_h + 8u * l, rinv[l]);
+          for (int j = j0; j <= j1; j++) {
+            if (j < PB) {
+              st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + l) * 8u, xr[j][l]);
+              if (l == j) st_peer_f64(ms_h + (uint32_t)(j * (PB + 1) + PB) * 8u, xr[j][PB]);
+            } else {
+              st_peer_f64(rinv_h + 8u * l, rinv[l]);
+            }
           }
-          // one arrival per column: lane 0's cluster-scope release covers
-          // the stores its partners ordered before it
+          // lane 0's cluster-scope release covers the stores its partners
+          // ordered before it
           __syncwarp(0x0000ffffu);
-          if ((tid & 31) == 0) arrive_peer(j < PB ? mbcol_h + 8u * j : mbr_h);
+          if (l == 0) arrive_peer(j1 < PB ? mbcol_h + 8u * j1 : mbr_h);
         }
       }
       bar_sync_256(6);
       if (!flags[1]) {
-        if (ir >= ic) __stcg(gp(s, s, ir, ic), lout[ir][ic]);
-        if (ir >= ic + 8) __stcg(gp(s, s, ir, ic + 8), lout[ir][ic + 8]);
+        // L_ik = c_ik / sqrt(c_kk), the diagonal c_kk / sqrt(c_kk)
+        if (ir >= ic) __stcg(gp(s, s, ir, ic), mcol[ic][ir] * rinv[ic]);
+        if (ir >= ic + 8) __stcg(gp(s, s, ir, ic + 8), mcol[ic + 8][ir] * rinv[ic + 8]);
         if (u < PB) __stcg(rinv_g + s * PB + u, rinv[u]);
         bar_sync_128(2);
         if (u == 0) {
@@ -660,53 +706,37 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
     const int n1 = s + 1;
     const uint32_t par = (uint32_t)s & 1u;
     unsigned long long t0 = 0, t1 = 0, t2 = 0;  // trace only
-    // blocks (n1, s) and (n1, n1) after the panels < s-1 (UPD tasks, usually
-    // complete long before); they load while X_{n1,s-1} is awaited
+    // block (n1, s) after the panels < s-1 (UPD tasks, usually complete long
+    // before) and X_{n1,s-1} (the second helper's step s-1)
     if (tid == 0) {
       if (trace) t0 = gtimer();
-      if (!dag_wait2(state, n1 * nbb + s, s - 1, n1 * nbb + n1, s - 1, st)) flags[0] = 1;
+      if (!dag_wait2(state, n1 * nbb + s, s - 1, s >= 1 ? n1 * nbb + (s - 1) : -1, s, st)) flags[0] = 1;
       fence_acq_rel_gpu();
+      if (trace) t1 = gtimer();
     }
     if (__syncthreads_or(flags[0] | flags[2])) break;
-    double va, vb;
+    double va = 0.0, vb = 0.0;
     if (cw) {
       va = __ldcg(gp(n1, s, cr, ct));
       vb = __ldcg(gp(n1, s, cr + 8, ct));
-    } else {
-      va = __ldcg(gp(n1, n1, ir, ic));  // C' entries (ir, ic), (ir, ic + 8)
-      vb = __ldcg(gp(n1, n1, ir, ic + 8));
+    } else if (s >= 1) {
+      xo[ir][ic] = __ldcg(gp(n1, s - 1, ir, ic));
+      xo[ir][ic + 8] = __ldcg(gp(n1, s - 1, ir, ic + 8));
     }
     if (s >= 1) {
-      // X_{n1,s-1}, published by the second helper in its step s-1
-      if (tid == 0) {
-        if (!dag_wait(state, n1 * nbb + (s - 1), s, st)) flags[0] = 1;
-        fence_acq_rel_gpu();
-        if (trace) t1 = gtimer();
-      }
-      if (__syncthreads_or(flags[0] | flags[2])) break;
-      if (!cw) {
-        xo[ir][ic] = __ldcg(gp(n1, s - 1, ir, ic));
-        xo[ir][ic + 8] = __ldcg(gp(n1, s - 1, ir, ic + 8));
-      }
       __syncthreads();  // X_{n1,s-1} is in xo
+      // panel s-1 applied to block (n1, s): B -= X_{n1,s-1} X_{s,s-1}^T
       if (cw) {
-        // panel s-1 applied to block (n1, s): B -= X_{n1,s-1} X_{s,s-1}^T
         va -= panel_dot(xo, xprev, cr, ct);
         vb -= panel_dot(xo, xprev, cr + 8, ct);
-      } else {
-        // panel s-1 applied to block (n1, n1): C' -= X_{n1,s-1} X_{n1,s-1}^T
-        va -= panel_dot(xo, xo, ir, ic);
-        vb -= panel_dot(xo, xo, ir, ic + 8);
       }
-    } else if (trace && tid == 0) {
-      t1 = gtimer();
     }
     if (cw) {
       // X_{n1,s} L_{s,s}^T = B, column j as soon as the master's leaf has
       // formed column j of L_{s,s} (in the unscaled form x_j L_jj)
 #pragma unroll
       for (int j = 0; j < PB; j++) {
-        if (!wait_from_peer(&mbar[j], par, &flags[2])) {
+        if (col_group_first(j) && !wait_from_peer(&mbar[col_group_bar(j)], par, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 5;
           flags[0] = 1;
         }
@@ -725,22 +755,43 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       }
       if (trace && tid == 0) t2 = gtimer();
     } else {
-      // C_{n1} = C' - X X^T needs no square root: with u_j = x_j L_jj (the
-      // solve's unscaled columns) and r_j = 1/c_jj = 1/L_jj^2,
-      // X X^T = sum_j u_j r_j u_j^T, accumulated column by column as the
-      // solve finishes each one
-#pragma unroll 1
-      for (int j = 0; j < PB; j++) {
-        if (!wait_from_peer(&mbar[18 + j], par, &flags[2])) {  // CTA-local arrivals; cluster acquire is stronger
-          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
-          flags[0] = 1;
-        }
-        const double p = uu[j][ir] * ms[j][PB];
-        va = fma(-p, uu[j][ic], va);
-        vb = fma(-p, uu[j][ic + 8], vb);
+      // S = X X^T needs no square root: with u_j = x_j L_jj (the solve's
+      // unscaled columns) and r_j = 1/c_jj = 1/L_jj^2, S = sum_j u_j r_j
+      // u_j^T, accumulated column by column as the solve finishes each one.
+      // The master adds C' (block (n1, n1) after every panel < s, from the
+      // second helper) to -S; in step 0, C' is block (1, 1) itself, and it
+      // goes in here.
+      if (s == 0) {
+        va = __ldcg(gp(n1, n1, ir, ic));
+        vb = __ldcg(gp(n1, n1, ir, ic + 8));
       }
-      // C_{n1} (entries (ir, ic), (ir, ic + 8)) into the master's xc: its
-      // next leaf starts from it
+      // p = r_j u_{ir,j} is formed as column j arrives and used one step of
+      // the loop later, and even and odd columns go to two sums, so that no
+      // FMA waits for the multiply or the FMA just before it
+      double va1 = 0.0, vb1 = 0.0, p = 0.0, q0 = 0.0, q1 = 0.0;
+#pragma unroll 2
+      for (int j = 0; j <= PB; j++) {
+        if (j & 1) {
+          va = fma(-p, q0, va);  // column j - 1, even
+          vb = fma(-p, q1, vb);
+        } else if (j >= 2) {
+          va1 = fma(-p, q0, va1);
+          vb1 = fma(-p, q1, vb1);
+        }
+        if (j < PB) {
+          if (!wait_local(&mbar[18 + j], par, &flags[2])) {  // arrivals of warps 0..3 of this CTA
+            if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
+            flags[0] = 1;
+          }
+          p = uu[j][ir] * ms[j][PB];
+          q0 = uu[j][ic];
+          q1 = uu[j][ic + 8];
+        }
+      }
+      va += va1;
+      vb += vb1;
+      // -S (step 0: C_1) entries (ir, ic), (ir, ic + 8) into the master's xc:
+      // its next leaf starts from C' - S
       st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic) * 8u, va);
       st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic + 8) * 8u, vb);
       __syncwarp();
@@ -794,15 +845,19 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
 
 // The chain's second helper (CTA rank 2): in step s it solves block (s+2, s)
 // one column behind the master's leaf, as the first helper solves block
-// (s+1, s): block (s+2, s) after the panels < s-1 (UPD tasks), minus
-// X_{s+2,s-1} X_{s,s-1}^T (X_{s+2,s-1} from a TRSM task, X_{s,s-1} from the
-// first helper), is solved against L_{s,s} as its columns arrive and
-// published as X_{s+2,s}, which the first helper's step s+1 and the UPD tasks
-// of panel s read.  The columns come in two buffers (this CTA's ms0 and
-// barriers mbar[0..16] in even steps, ms1 and mbar[17..33] in odd ones, 1/L_kk
-// in rinv2[s & 1]), so that the master may run a step ahead of this CTA: its
-// step s+2 waits for the first helper's step s+1, which waits for this CTA's
-// X_{s+2,s}.
+// (s+1, s), and publishes X_{s+2,s}, which the first helper's step s+1 and
+// the UPD tasks of panel s read.  The block's update by panel s-1,
+// D = X_{s+2,s-1} X_{s,s-1}^T, waits for X_{s+2,s-1} from a TRSM task, which
+// comes late in the step; the solve is linear, so warps 0..3 solve block
+// (s+2, s) after the panels < s-1 (UPD tasks, ready early) column by column
+// with the leaf, warps 4..7 form D once its inputs are published and solve
+// it against the columns received so far, and X_{s+2,s} is the difference.
+// It then applies panel s to block (s+2, s+2) (UPD(s+2, s+2, s)): C' of the
+// master's step s+1, which adds it to the first helper's -S.
+// The columns come in two buffers (ms0 and barriers mbar[0..16] in even
+// steps, ms1 and mbar[17..33] in odd ones, 1/L_kk in rinv2[s & 1]), so that
+// the master may run a step ahead of this CTA: its step s+2 waits for the
+// first helper's step s+1, which waits for this CTA's X_{s+2,s}.
 __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
                                                  unsigned long long *__restrict__ trace, double (*ms0)[PB + 1],
                                                  double (*ms1)[PB + 1], double (*xn)[PB + 1], double (*xs)[PB + 1],
@@ -810,11 +865,11 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
   const int nbb = nb / PB;
   const size_t ld = nb;
   const int tid = threadIdx.x, u = tid & 127;
-  const bool cw = tid < 128;                 // warps 0..3: rows cr, cr + 8 of column ct
-  const int cr = u >> 4, ct = u & (PB - 1);
-  const int er = tid & (PB - 1), ec = tid >> 4;  // all threads: entry (er, ec) of a block
+  const bool cw = tid < 128;                 // warps 0..3: the block; 4..7: D
+  const int cr = u >> 4, ct = u & (PB - 1);  // rows cr, cr + 8 of column ct
   auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
   const uint32_t stop_m = peer_addr((const void *)&flags[2], 0), stop_h = peer_addr((const void *)&flags[2], 1);
+  const uint32_t cp_m = peer_addr(ms1, 0), cready_m = peer_addr(&mbar[18], 0);  // the master's lout is its a
   for (int s = 0; s + 2 < nbb; s++) {
     const int n2 = s + 2, b = s & 1;
     const uint32_t par = (uint32_t)(s >> 1) & 1u;
@@ -823,34 +878,39 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
     unsigned long long t0 = 0, t1 = 0, t2 = 0;  // trace only
     if (tid == 0) {
       if (trace) t0 = gtimer();
-      // block (s+2, s) after the panels < s-1, X_{s+2,s-1} and X_{s,s-1}
-      if (!dag_wait3(state, n2 * nbb + s, s - 1, s >= 1 ? n2 * nbb + (s - 1) : -1, s,
-                     s >= 1 ? s * nbb + (s - 1) : -1, s, st))
-        flags[0] = 1;
+      // block (s+2, s) after the panels < s-1
+      if (!dag_wait(state, n2 * nbb + s, s - 1, st)) flags[0] = 1;
       fence_acq_rel_gpu();
-      if (trace) t1 = gtimer();
     }
     if (__syncthreads_or(flags[0] | flags[2])) break;
     double va = 0.0, vb = 0.0;
     if (cw) {
       va = __ldcg(gp(n2, s, cr, ct));
       vb = __ldcg(gp(n2, s, cr + 8, ct));
-    }
-    if (s >= 1) {
-      xn[er][ec] = __ldcg(gp(n2, s - 1, er, ec));
-      xs[er][ec] = __ldcg(gp(s, s - 1, er, ec));
-      __syncthreads();
-      if (cw) {
-        // panel s-1 applied to block (s+2, s)
-        va -= panel_dot(xn, xs, cr, ct);
-        vb -= panel_dot(xn, xs, cr + 8, ct);
+    } else if (s >= 1) {
+      // X_{s+2,s-1} (TRSM task) and X_{s,s-1} (the first helper), then D
+      if (tid == 128) {
+        if (!dag_wait2(state, n2 * nbb + (s - 1), s, s * nbb + (s - 1), s, st)) flags[0] = 1;
+        fence_acq_rel_gpu();
+        // trace: the arrival time, for thread 0, in xs's padding column
+        if (trace) xs[0][PB] = __longlong_as_double((long long)gtimer());
       }
+      bar_sync_128(3);
+      xn[cr][ct] = __ldcg(gp(n2, s - 1, cr, ct));
+      xn[cr + 8][ct] = __ldcg(gp(n2, s - 1, cr + 8, ct));
+      xs[cr][ct] = __ldcg(gp(s, s - 1, cr, ct));
+      xs[cr + 8][ct] = __ldcg(gp(s, s - 1, cr + 8, ct));
+      bar_sync_128(3);
+      va = panel_dot(xn, xs, cr, ct);
+      vb = panel_dot(xn, xs, cr + 8, ct);
     }
-    if (cw) {
-      // X_{s+2,s} L_{s,s}^T = B2, column j once the leaf has formed column j
+    // both halves: the unscaled solve of their 16 x 16 block against L_{s,s}
+    // (warps 4..7 only when there is a D), column j once the leaf has formed
+    // column j (in the unscaled form x_j L_jj)
+    if (cw || s >= 1) {
 #pragma unroll
       for (int j = 0; j < PB; j++) {
-        if (!wait_from_peer(&mb[j], par, &flags[2])) {
+        if (col_group_first(j) && !wait_from_peer(&mb[col_group_bar(j)], par, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 9;
           flags[0] = 1;
         }
@@ -861,18 +921,35 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
           vb = fma(-bj, mj, vb);
         }
       }
-      if (!wait_from_peer(&mb[PB], par, &flags[2])) {
-        if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 10;
-        flags[0] = 1;
+    }
+    if (!cw && s >= 1) {
+      bar_sync_128(3);  // every read of xn / xs is done
+      xn[cr][ct] = va;
+      xn[cr + 8][ct] = vb;
+    }
+    if (cw && !wait_from_peer(&mb[PB], par, &flags[2])) {
+      if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 10;
+      flags[0] = 1;
+    }
+    if (__syncthreads_or(flags[0] | flags[2])) break;  // D's solve is in xn
+    if (cw) {
+      if (trace && tid == 0) {
+        t2 = gtimer();
+        t1 = s >= 1 ? (unsigned long long)__double_as_longlong(xs[0][PB]) : t0;
       }
-      if (trace && tid == 0) t2 = gtimer();
-      if (!flags[0] && !flags[2]) {
-        const double r = rinv2[b][ct];
-        __stcg(gp(n2, s, cr, ct), va * r);
-        __stcg(gp(n2, s, cr + 8, ct), vb * r);
+      if (s >= 1) {
+        va -= xn[cr][ct];
+        vb -= xn[cr + 8][ct];
       }
+      const double r = rinv2[b][ct];
+      va *= r;
+      vb *= r;
+      __stcg(gp(n2, s, cr, ct), va);
+      __stcg(gp(n2, s, cr + 8, ct), vb);
+      xn[cr][ct] = va;  // each thread overwrites the entries of D's solve it read
+      xn[cr + 8][ct] = vb;
       bar_sync_128(2);
-      if (tid == 0 && !flags[0] && !flags[2]) {
+      if (tid == 0) {
         fence_acq_rel_gpu();  // releases the stores ordered before it by the barrier
         atomicExch(&state[n2 * nbb + s], s + 1);
         if (trace) {
@@ -881,14 +958,35 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
           unsigned long long *rec = trace + (size_t)s * 5;
           rec[0] = (unsigned long long)T_HELP2 | ((unsigned long long)n2 << 8) | ((unsigned long long)s << 24) |
                    ((unsigned long long)s << 40);
-          rec[1] = (smid & 0xFFull) | (min(t2 - t1, 0x3ffffull) << 8);  // ns from the inputs to the solve's end
+          // SM id | ns from the arrival of D's inputs to the end of both solves
+          rec[1] = (smid & 0xFFull) | (min(t2 - t1, 0x3ffffull) << 8);
           rec[2] = t0;
           rec[3] = t1;
           rec[4] = gtimer();
         }
       }
     }
-    if (__syncthreads_or(flags[0] | flags[2])) break;  // xn / xs are read; flags agree
+    // panel s applied to block (s+2, s+2) (after the panels < s, UPD tasks):
+    // C' of the master's step s+1, one entry per thread, written into its
+    // lout once it has read the last one there (this CTA's mbar[34], from
+    // step 1 on) and released by one arrival per warp on its mbar[18]
+    if (tid == 0) {
+      if (!dag_wait(state, n2 * nbb + n2, s, st)) flags[0] = 1;
+      fence_acq_rel_gpu();
+    }
+    if (__syncthreads_or(flags[0] | flags[2])) break;  // X_{s+2,s} is in xn
+    {
+      const int er = tid & (PB - 1), ec = tid >> 4;
+      const double c = __ldcg(gp(n2, n2, er, ec)) - panel_dot(xn, xn, er, ec);
+      if (s >= 1 && !wait_from_peer(&mbar[34], (uint32_t)(s - 1) & 1u, &flags[2])) {
+        if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 12;
+        flags[0] = 1;
+      }
+      st_peer_f64(cp_m + (uint32_t)(er * (PB + 1) + ec) * 8u, c);
+      __syncwarp();
+      if ((tid & 31) == 0) arrive_peer(cready_m);
+    }
+    __syncthreads();  // xn is read before the next step's loads
   }
   if (tid == 0 && flags[0]) {
     st_peer_s32(stop_m, 1);
@@ -948,6 +1046,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         // helper's warps 4..7
         for (int j = 0; j <= PB; j++) tc::mbar_init(&mbar[j], PB);
         tc::mbar_init(&mbar[17], 4);
+        tc::mbar_init(&mbar[18], 8);  // C' from the second helper: one arrival per warp
       } else if (rank == 1) {
         // columns (one arrival of the master's forwarding warp), rinv of even
         // / odd steps, column j of u (one thread per half-warp of warps 0..3)
@@ -955,8 +1054,10 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         tc::mbar_init(&mbar[35], 1);
         for (int j = 0; j < PB; j++) tc::mbar_init(&mbar[18 + j], 8);
       } else {
-        // columns and rinv of even / odd steps
+        // columns and rinv of even / odd steps; mbar[34]: the master has read
+        // the last C' (one arrival per compute warp of it)
         for (int j = 0; j < 2 * (PB + 1); j++) tc::mbar_init(&mbar[j], 1);
+        tc::mbar_init(&mbar[34], 4);
       }
       tc::fence_barrier_init();
       atomicExch(master_sm + (rank == 0 ? 0 : rank + 1), (int)my_sm + 1);

@@ -128,18 +128,21 @@ class Master:
 class ClusterMaster:
     """The chain on a cluster of three CTAs.  Master: step s factors block
     (s, s) from C_s (formed by the first helper's step s-1) and releases
-    L_{s,s}.  First helper, step s: once L_{s,s} is released, blocks (s+1, s)
-    and (s+1, s+1) carry the panels < s-1 and X_{s+1,s-1} is published (by
-    the second helper), it applies panel s-1 to both, solves and publishes
-    X_{s+1,s} and forms C_{s+1} = block (s+1, s+1) after panel s-1, minus
-    X_{s+1,s} X_{s+1,s}^T.  Second helper, step s: once L_{s,s} is released,
-    block (s+2, s) carries the panels < s-1 and X_{s+2,s-1} (a TRSM task) and
-    X_{s,s-1} are published, it applies panel s-1, solves and publishes
-    X_{s+2,s}.  The three advance independently, each on its own data."""
+    L_{s,s}.  First helper, step s: once L_{s,s} is released, block (s+1, s)
+    carries the panels < s-1, X_{s+1,s-1} is published and block (s+1, s+1)
+    carries the panels < s (the last one applied by the second helper), it
+    applies panel s-1 to block (s+1, s), solves and publishes X_{s+1,s} and
+    forms C_{s+1} = block (s+1, s+1) minus X_{s+1,s} X_{s+1,s}^T.  Second
+    helper, step s: once L_{s,s} is released, block (s+2, s) carries the
+    panels < s-1 and X_{s+2,s-1} (a TRSM task) and X_{s,s-1} are published,
+    it applies panel s-1, solves and publishes X_{s+2,s}; then, once block
+    (s+2, s+2) carries the panels < s, it applies panel s to it.  The three
+    advance independently, each on its own data."""
 
     def __init__(self, T):
         self.T = T
         self.s = self.sa = self.sb = 0
+        self.xb = None  # the second helper's X of its current step, once solved
         self.C = {0: T.blk(0, 0).copy()}
 
     def done(self):
@@ -156,26 +159,31 @@ class ClusterMaster:
             self.s += 1
             moved = True
         s, n1 = self.sa, self.sa + 1
-        if n1 < nbb and st[s, s] >= s + 1 and st[n1, s] >= s - 1 and st[n1, n1] >= s - 1 and \
+        if n1 < nbb and st[s, s] >= s + 1 and st[n1, s] >= s - 1 and st[n1, n1] >= s and \
                 (s < 1 or st[n1, s - 1] >= s):
-            B, Cp = T.blk(n1, s).copy(), T.blk(n1, n1).copy()
+            B = T.blk(n1, s).copy()
             if s >= 1:
                 B -= T.blk(n1, s - 1) @ T.blk(s, s - 1).T
-                Cp -= T.blk(n1, s - 1) @ T.blk(n1, s - 1).T
             X = _solve_lt(T.blk(s, s), B)
             T.put(n1, s, X)
             st[n1, s] = s + 1
-            self.C[n1] = Cp - X @ X.T
+            self.C[n1] = T.blk(n1, n1) - X @ X.T
             self.sa += 1
             moved = True
         s, n2 = self.sb, self.sb + 2
-        if n2 < nbb and st[s, s] >= s + 1 and st[n2, s] >= s - 1 and \
+        if n2 < nbb and self.xb is None and st[s, s] >= s + 1 and st[n2, s] >= s - 1 and \
                 (s < 1 or (st[n2, s - 1] >= s and st[s, s - 1] >= s)):
             B = T.blk(n2, s).copy()
             if s >= 1:
                 B -= T.blk(n2, s - 1) @ T.blk(s, s - 1).T
-            T.put(n2, s, _solve_lt(T.blk(s, s), B))
+            self.xb = _solve_lt(T.blk(s, s), B)
+            T.put(n2, s, self.xb)
             st[n2, s] = s + 1
+            moved = True
+        if self.xb is not None and st[n2, n2] >= s:
+            T.put(n2, n2, T.blk(n2, n2) - self.xb @ self.xb.T)
+            st[n2, n2] = s + 1
+            self.xb = None
             self.sb += 1
             moved = True
         return moved
