@@ -852,8 +852,9 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
 // (s+2, s) after the panels < s-1 (UPD tasks, ready early) column by column
 // with the leaf, warps 4..7 form D once its inputs are published and solve
 // it against the columns received so far, and X_{s+2,s} is the difference.
-// It then applies panel s to block (s+2, s+2) (UPD(s+2, s+2, s)): C' of the
-// master's step s+1, which adds it to the first helper's -S.
+// It applies panel s to block (s+2, s+2) (UPD(s+2, s+2, s)) early in its
+// next step: C' of the master's step s+1, which adds it to the first
+// helper's -S.
 // The columns come in two buffers (ms0 and barriers mbar[0..16] in even
 // steps, ms1 and mbar[17..33] in odd ones, 1/L_kk in rinv2[s & 1]), so that
 // the master may run a step ahead of this CTA: its step s+2 waits for the
@@ -870,6 +871,29 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
   auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
   const uint32_t stop_m = peer_addr((const void *)&flags[2], 0), stop_h = peer_addr((const void *)&flags[2], 1);
   const uint32_t cp_m = peer_addr(ms1, 0), cready_m = peer_addr(&mbar[18], 0);  // the master's lout is its a
+  // Hand-over k, by warps 4..7: panel k applied to block (k+2, k+2) (after
+  // the panels < k, UPD tasks), with X_{k+2,k} in xn: C' of the master's step
+  // k+1, written into its lout once it has read hand-over k-1 there (this
+  // CTA's mbar[34]) and released by one arrival per warp on its mbar[18].
+  auto hand_over = [&](int k) {
+    const int nk = k + 2;
+    if (tid == 128) {
+      if (!dag_wait(state, nk * nbb + nk, k, st)) flags[0] = 1;
+      fence_acq_rel_gpu();
+    }
+    bar_sync_128(3);
+    const double c0 = __ldcg(gp(nk, nk, cr, ct)) - panel_dot(xn, xn, cr, ct);
+    const double c1 = __ldcg(gp(nk, nk, cr + 8, ct)) - panel_dot(xn, xn, cr + 8, ct);
+    if (k >= 1 && !wait_from_peer(&mbar[34], (uint32_t)(k - 1) & 1u, &flags[2])) {
+      if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 12;
+      flags[0] = 1;
+    }
+    st_peer_f64(cp_m + (uint32_t)(cr * (PB + 1) + ct) * 8u, c0);
+    st_peer_f64(cp_m + (uint32_t)((cr + 8) * (PB + 1) + ct) * 8u, c1);
+    __syncwarp();
+    if ((tid & 31) == 0) arrive_peer(cready_m);
+    bar_sync_128(3);  // every read of xn is done
+  };
   for (int s = 0; s + 2 < nbb; s++) {
     const int n2 = s + 2, b = s & 1;
     const uint32_t par = (uint32_t)(s >> 1) & 1u;
@@ -888,6 +912,9 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
       va = __ldcg(gp(n2, s, cr, ct));
       vb = __ldcg(gp(n2, s, cr + 8, ct));
     } else if (s >= 1) {
+      // first the previous step's hand-over (its X is in xn), while the
+      // TRSM task that this step's update needs runs
+      hand_over(s - 1);
       // X_{s+2,s-1} (TRSM task) and X_{s,s-1} (the first helper), then D
       if (tid == 128) {
         if (!dag_wait2(state, n2 * nbb + (s - 1), s, s * nbb + (s - 1), s, st)) flags[0] = 1;
@@ -946,7 +973,7 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
       vb *= r;
       __stcg(gp(n2, s, cr, ct), va);
       __stcg(gp(n2, s, cr + 8, ct), vb);
-      xn[cr][ct] = va;  // each thread overwrites the entries of D's solve it read
+      xn[cr][ct] = va;  // for hand-over s; each thread overwrites the entries of D's solve it read
       xn[cr + 8][ct] = vb;
       bar_sync_128(2);
       if (tid == 0) {
@@ -966,28 +993,10 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
         }
       }
     }
-    // panel s applied to block (s+2, s+2) (after the panels < s, UPD tasks):
-    // C' of the master's step s+1, one entry per thread, written into its
-    // lout once it has read the last one there (this CTA's mbar[34], from
-    // step 1 on) and released by one arrival per warp on its mbar[18]
-    if (tid == 0) {
-      if (!dag_wait(state, n2 * nbb + n2, s, st)) flags[0] = 1;
-      fence_acq_rel_gpu();
-    }
-    if (__syncthreads_or(flags[0] | flags[2])) break;  // X_{s+2,s} is in xn
-    {
-      const int er = tid & (PB - 1), ec = tid >> 4;
-      const double c = __ldcg(gp(n2, n2, er, ec)) - panel_dot(xn, xn, er, ec);
-      if (s >= 1 && !wait_from_peer(&mbar[34], (uint32_t)(s - 1) & 1u, &flags[2])) {
-        if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 12;
-        flags[0] = 1;
-      }
-      st_peer_f64(cp_m + (uint32_t)(er * (PB + 1) + ec) * 8u, c);
-      __syncwarp();
-      if ((tid & 31) == 0) arrive_peer(cready_m);
-    }
-    __syncthreads();  // xn is read before the next step's loads
+    __syncthreads();  // xn holds X_{s+2,s}
   }
+  // the last hand-over, unless the chain has stopped (one decision for all)
+  if (!__syncthreads_or(flags[0] | flags[2]) && !cw && nbb >= 3) hand_over(nbb - 3);
   if (tid == 0 && flags[0]) {
     st_peer_s32(stop_m, 1);
     st_peer_s32(stop_h, 1);
@@ -1046,7 +1055,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         // helper's warps 4..7
         for (int j = 0; j <= PB; j++) tc::mbar_init(&mbar[j], PB);
         tc::mbar_init(&mbar[17], 4);
-        tc::mbar_init(&mbar[18], 8);  // C' from the second helper: one arrival per warp
+        tc::mbar_init(&mbar[18], 4);  // C' from the second helper: one arrival per warp 4..7 of it
       } else if (rank == 1) {
         // columns (one arrival of the master's forwarding warp), rinv of even
         // / odd steps, column j of u (one thread per half-warp of warps 0..3)
