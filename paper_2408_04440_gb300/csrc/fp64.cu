@@ -853,8 +853,8 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
 // with the leaf, warps 4..7 form D once its inputs are published and solve
 // it against the columns received so far, and X_{s+2,s} is the difference.
 // It applies panel s to block (s+2, s+2) (UPD(s+2, s+2, s)) early in its
-// next step: C' of the master's step s+1, which adds it to the first
-// helper's -S.
+// next step, on warps 0..3 before their solve: C' of the master's step s+1,
+// which adds it to the first helper's -S.
 // The columns come in two buffers (ms0 and barriers mbar[0..16] in even
 // steps, ms1 and mbar[17..33] in odd ones, 1/L_kk in rinv2[s & 1]), so that
 // the master may run a step ahead of this CTA: its step s+2 waits for the
@@ -871,17 +871,17 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
   auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
   const uint32_t stop_m = peer_addr((const void *)&flags[2], 0), stop_h = peer_addr((const void *)&flags[2], 1);
   const uint32_t cp_m = peer_addr(ms1, 0), cready_m = peer_addr(&mbar[18], 0);  // the master's lout is its a
-  // Hand-over k, by warps 4..7: panel k applied to block (k+2, k+2) (after
+  // Hand-over k, by warps 0..3: panel k applied to block (k+2, k+2) (after
   // the panels < k, UPD tasks), with X_{k+2,k} in xn: C' of the master's step
   // k+1, written into its lout once it has read hand-over k-1 there (this
   // CTA's mbar[34]) and released by one arrival per warp on its mbar[18].
   auto hand_over = [&](int k) {
     const int nk = k + 2;
-    if (tid == 128) {
+    if (tid == 0) {
       if (!dag_wait(state, nk * nbb + nk, k, st)) flags[0] = 1;
       fence_acq_rel_gpu();
     }
-    bar_sync_128(3);
+    bar_sync_128(2);
     const double c0 = __ldcg(gp(nk, nk, cr, ct)) - panel_dot(xn, xn, cr, ct);
     const double c1 = __ldcg(gp(nk, nk, cr + 8, ct)) - panel_dot(xn, xn, cr + 8, ct);
     if (k >= 1 && !wait_from_peer(&mbar[34], (uint32_t)(k - 1) & 1u, &flags[2])) {
@@ -892,7 +892,6 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
     st_peer_f64(cp_m + (uint32_t)((cr + 8) * (PB + 1) + ct) * 8u, c1);
     __syncwarp();
     if ((tid & 31) == 0) arrive_peer(cready_m);
-    bar_sync_128(3);  // every read of xn is done
   };
   for (int s = 0; s + 2 < nbb; s++) {
     const int n2 = s + 2, b = s & 1;
@@ -909,13 +908,19 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
     if (__syncthreads_or(flags[0] | flags[2])) break;
     double va = 0.0, vb = 0.0;
     if (cw) {
+      // first the previous step's hand-over (its X is in xn; the leaf's first
+      // columns arrive meanwhile and the solve below catches up), then the
+      // block after the panels < s-1
+      if (s >= 1) {
+        hand_over(s - 1);
+        bar_arrive_256(4);  // xn may take D's solve
+      }
       va = __ldcg(gp(n2, s, cr, ct));
       vb = __ldcg(gp(n2, s, cr + 8, ct));
     } else if (s >= 1) {
-      // first the previous step's hand-over (its X is in xn), while the
-      // TRSM task that this step's update needs runs
-      hand_over(s - 1);
-      // X_{s+2,s-1} (TRSM task) and X_{s,s-1} (the first helper), then D
+      // X_{s+2,s-1} (TRSM task) and X_{s,s-1} (the first helper), then D; the
+      // rows of X_{s+2,s-1} come from global memory (xn holds X_{s+1,s-1} for
+      // the hand-over)
       if (tid == 128) {
         if (!dag_wait2(state, n2 * nbb + (s - 1), s, s * nbb + (s - 1), s, st)) flags[0] = 1;
         fence_acq_rel_gpu();
@@ -923,13 +928,19 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
         if (trace) xs[0][PB] = __longlong_as_double((long long)gtimer());
       }
       bar_sync_128(3);
-      xn[cr][ct] = __ldcg(gp(n2, s - 1, cr, ct));
-      xn[cr + 8][ct] = __ldcg(gp(n2, s - 1, cr + 8, ct));
       xs[cr][ct] = __ldcg(gp(s, s - 1, cr, ct));
       xs[cr + 8][ct] = __ldcg(gp(s, s - 1, cr + 8, ct));
       bar_sync_128(3);
-      va = panel_dot(xn, xs, cr, ct);
-      vb = panel_dot(xn, xs, cr + 8, ct);
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll 4
+      for (int k = 0; k < PB; k += 2) {
+        a0 = fma(__ldcg(gp(n2, s - 1, cr, k)), xs[ct][k], a0);
+        b0 = fma(__ldcg(gp(n2, s - 1, cr + 8, k)), xs[ct][k], b0);
+        a1 = fma(__ldcg(gp(n2, s - 1, cr, k + 1)), xs[ct][k + 1], a1);
+        b1 = fma(__ldcg(gp(n2, s - 1, cr + 8, k + 1)), xs[ct][k + 1], b1);
+      }
+      va = a0 + a1;
+      vb = b0 + b1;
     }
     // both halves: the unscaled solve of their 16 x 16 block against L_{s,s}
     // (warps 4..7 only when there is a D), column j once the leaf has formed
@@ -950,7 +961,7 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
       }
     }
     if (!cw && s >= 1) {
-      bar_sync_128(3);  // every read of xn / xs is done
+      bar_sync_256(4);  // warps 0..3 have read xn (the hand-over)
       xn[cr][ct] = va;
       xn[cr + 8][ct] = vb;
     }
@@ -996,7 +1007,7 @@ __device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb,
     __syncthreads();  // xn holds X_{s+2,s}
   }
   // the last hand-over, unless the chain has stopped (one decision for all)
-  if (!__syncthreads_or(flags[0] | flags[2]) && !cw && nbb >= 3) hand_over(nbb - 3);
+  if (!__syncthreads_or(flags[0] | flags[2]) && cw && nbb >= 3) hand_over(nbb - 3);
   if (tid == 0 && flags[0]) {
     st_peer_s32(stop_m, 1);
     st_peer_s32(stop_h, 1);
