@@ -175,8 +175,10 @@ __device__ inline void arrive_peer(uint32_t bar) {
 }
 // Waits for the phase of the given parity of an mbarrier of this CTA; false
 // after the wait bound or when *abort is set.  SCOPE_CLUSTER: the arrivals
-// come from another CTA of the cluster (their remote stores become visible);
-// else from this CTA.
+// come from another CTA of the cluster (their remote stores become visible),
+// polled with try_wait; else from this CTA, polled with test_wait, which
+// never parks the thread (the column hand-overs inside a helper come every
+// few hundred cycles).
 template <bool SCOPE_CLUSTER>
 __device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort) {
   const uint32_t a = tc::smem_u32(bar);
@@ -194,7 +196,7 @@ __device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *
     else
       asm volatile(
           "{\n\t.reg .pred p;\n\t"
-          "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+          "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
           "selp.u32 %0, 1, 0, p;\n\t}\n"
           : "=r"(ok)
           : "r"(a), "r"(parity)
@@ -594,8 +596,6 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
           }
           v0 += lout[i][k0];
           v1 += lout[i][k1];
-          __syncwarp();
-          if ((tid & 31) == 0 && s + 2 < nbb) arrive_peer(cfree_h2);  // the second helper's next C' may come
         }
       }
     } else {
@@ -657,6 +657,9 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
     }
     // one decision for all threads: a peer may set flags[2] at any time
     const bool stop = __syncthreads_or(flags[1] | flags[0] | flags[2]) != 0;
+    // C' in lout is read: the second helper's next one may come (released by
+    // an I/O thread, off the compute warps' way to the next leaf)
+    if (tid == 128 && !stop && s >= 1 && s + 2 < nbb) arrive_peer(cfree_h2);
     if (trace && tid == 0) {
       unsigned smid;
       asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
@@ -768,9 +771,11 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       // p = r_j u_{ir,j} is formed as column j arrives and used one step of
       // the loop later, and even and odd columns go to two sums, so that no
       // FMA waits for the multiply or the FMA just before it
+      // (the odd sum joins the even one before the last column's FMA, so
+      // that only the multiply and one FMA follow the last column)
       double va1 = 0.0, vb1 = 0.0, p = 0.0, q0 = 0.0, q1 = 0.0;
 #pragma unroll 2
-      for (int j = 0; j <= PB; j++) {
+      for (int j = 0; j < PB; j++) {
         if (j & 1) {
           va = fma(-p, q0, va);  // column j - 1, even
           vb = fma(-p, q1, vb);
@@ -778,18 +783,20 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
           va1 = fma(-p, q0, va1);
           vb1 = fma(-p, q1, vb1);
         }
-        if (j < PB) {
-          if (!wait_local(&mbar[18 + j], par, &flags[2])) {  // arrivals of warps 0..3 of this CTA
-            if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
-            flags[0] = 1;
-          }
-          p = uu[j][ir] * ms[j][PB];
-          q0 = uu[j][ic];
-          q1 = uu[j][ic + 8];
+        if (j == PB - 1) {
+          va += va1;
+          vb += vb1;
         }
+        if (!wait_local(&mbar[18 + j], par, &flags[2])) {  // arrivals of warps 0..3 of this CTA
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
+          flags[0] = 1;
+        }
+        p = uu[j][ir] * ms[j][PB];
+        q0 = uu[j][ic];
+        q1 = uu[j][ic + 8];
       }
-      va += va1;
-      vb += vb1;
+      va = fma(-p, q0, va);  // column PB - 1
+      vb = fma(-p, q1, vb);
       // -S (step 0: C_1) entries (ir, ic), (ir, ic + 8) into the master's xc:
       // its next leaf starts from C' - S
       st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic) * 8u, va);
@@ -1075,9 +1082,9 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         for (int j = 0; j < PB; j++) tc::mbar_init(&mbar[18 + j], 8);
       } else {
         // columns and rinv of even / odd steps; mbar[34]: the master has read
-        // the last C' (one arrival per compute warp of it)
+        // the last C' (one arrival)
         for (int j = 0; j < 2 * (PB + 1); j++) tc::mbar_init(&mbar[j], 1);
-        tc::mbar_init(&mbar[34], 4);
+        tc::mbar_init(&mbar[34], 1);
       }
       tc::fence_barrier_init();
       atomicExch(master_sm + (rank == 0 ? 0 : rank + 1), (int)my_sm + 1);
