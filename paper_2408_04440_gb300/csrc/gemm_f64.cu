@@ -256,88 +256,94 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------- blocked TRSM
-// Row exponent (as the readers clamp it) and digits of one row held two
-// values per lane (columns lane and lane + 32 of a TW-column block): the
-// exponent is written to *e_out by lane 0 (0 for a row of zeros), plane p of
-// column c at d[c + p plane].
-__device__ inline void row_digits_tw(double x0, double x1, int *e_out, uint16_t *d, size_t plane) {
+constexpr int NQ = TW / 32;  // 32-column quarters of a block
+static_assert(TW % 32 == 0 && TW % BN == 0, "block width");
+
+// Row exponent (as the readers clamp it) and digits of one row of a
+// TW-column block held NQ values per lane (columns lane + 32 q): the exponent
+// is written to *e_out by lane 0 (0 for a row of zeros), plane p of column c
+// at d[c + p plane].
+__device__ inline void row_digits_tw(const double (&x)[NQ], int *e_out, uint16_t *d, size_t plane) {
   const int lane = threadIdx.x & 31;
-  double m = fmax(fabs(x0), fabs(x1));
+  double m = 0.0;
+#pragma unroll
+  for (int q = 0; q < NQ; q++) m = fmax(m, fabs(x[q]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   int e = 0;
   if (m > 0.0) frexp(m, &e);  // every |x| < 2^e
   if (lane == 0) *e_out = (m > 0.0) ? e + kExpBias : 0;
   const double sc = exp2i(-((m > 0.0) ? max(e, kExpMin) : kExpMin));  // exact: |x sc| < 1
-  write_digits(x0 * sc, d + lane, plane);
-  write_digits(x1 * sc, d + 32 + lane, plane);
+#pragma unroll
+  for (int q = 0; q < NQ; q++) write_digits(x[q] * sc, d + 32 * q + lane, plane);
 }
 
 // Digits of L_kk's column blocks: one CTA per (32 rows, block J), warp w
-// rows 4w..4w+3 of the 32, lane = columns lane and lane + 32 of the block.
+// rows 4w..4w+3 of the 32, lane = columns lane + 32 q of the block.
 __global__ void __launch_bounds__(256)
     k_lkk_digits(const double *__restrict__ L, int nb, int *__restrict__ exps, uint16_t *__restrict__ digits,
                  const int *st) {
   if (failed(st)) return;
   const int J = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c0 = J * TW;
-  for (int q = 0; q < 4; q++) {
-    const int r = blockIdx.x * 32 + w * 4 + q;
+  for (int i = 0; i < 4; i++) {
+    const int r = blockIdx.x * 32 + w * 4 + i;
     if (r < (J + 1) * TW) continue;  // warp-uniform: rows no product reads
-    const double x0 = L[(size_t)r + (size_t)(c0 + lane) * nb], x1 = L[(size_t)r + (size_t)(c0 + 32 + lane) * nb];
-    row_digits_tw(x0, x1, exps + (size_t)J * nb + r, digits + ((size_t)J * NS * nb + r) * TW, (size_t)nb * TW);
+    double x[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) x[q] = L[(size_t)r + (size_t)(c0 + 32 * q + lane) * nb];
+    row_digits_tw(x, exps + (size_t)J * nb + r, digits + ((size_t)J * NS * nb + r) * TW, (size_t)nb * TW);
   }
 }
 
 // Column block J of X = A L_kk^{-T} for every listed tile, in place: the
 // earlier blocks' contributions have been subtracted (digit products), so
 // only L_kk's TW x TW diagonal block enters.  One CTA per (4 rows, tile),
-// warp = row, lane = column of each 32-column half: the first half by
-// forward substitution against the pre-scaled diagonal block 2J, the second
-// after subtracting the first half's contribution (L_kk's 32 x 32 block below
-// block 2J, staged in shared memory), against block 2J + 1.
+// warp = row, lane = column of each 32-column quarter q: the earlier
+// quarters' contribution is subtracted (L_kk's entries read from L2, a
+// warp's 32 rows of one column at a time), then forward substitution against
+// the pre-scaled diagonal 32 x 32 block.
 __global__ void __launch_bounds__(128)
     k_trsm64_block(double *__restrict__ t64, int nb, const int *__restrict__ tiles, const double *__restrict__ Lkk,
                    int J, const double *__restrict__ Ls, const double *__restrict__ rinvs, int slot0,
                    int *__restrict__ exps, uint16_t *__restrict__ digits, const int *st) {
   if (failed(st)) return;
-  __shared__ double S[32][33];  // S[l][p] = L_kk(c0 + 32 + l, c0 + p)
-  const int z = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int z = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c0 = J * TW, r = blockIdx.x * 4 + w;
-  for (int e = tid; e < 32 * 32; e += 128) {
-    const int l = e & 31, p = e >> 5;
-    S[l][p] = Lkk[(size_t)(c0 + 32 + l) + (size_t)(c0 + p) * nb];
-  }
   double *X = t64 + (size_t)tiles[z] * nb * nb + r;
-  double a0 = X[(size_t)(c0 + lane) * nb], a1 = X[(size_t)(c0 + 32 + lane) * nb];
-  // Ls(p, l) = L(l, p) / L(p, p): a_l -= a_p Ls(p, l) on the unscaled a_p
-  auto solve32 = [&](double a, int cb) {
+  double a[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) a[q] = X[(size_t)(c0 + 32 * q + lane) * nb];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int qq = 0; qq < q; qq++) {
+      const double *lq = Lkk + (size_t)(c0 + 32 * q + lane) + (size_t)(c0 + 32 * qq) * nb;
+#pragma unroll 8
+      for (int p = 0; p < 32; p += 2) {
+        s0 = fma(__shfl_sync(0xffffffffu, a[qq], p), __ldg(lq + (size_t)p * nb), s0);
+        s1 = fma(__shfl_sync(0xffffffffu, a[qq], p + 1), __ldg(lq + (size_t)(p + 1) * nb), s1);
+      }
+    }
+    // Ls(p, l) = L(l, p) / L(p, p): a_l -= a_p Ls(p, l) on the unscaled a_p
+    const int cb = J * NQ + q;
+    double v = a[q] - (s0 + s1);
     double ld[32];
 #pragma unroll
     for (int p = 0; p < 32; p++) ld[p] = (p < lane) ? Ls[(size_t)(cb * 32 + p) * 32 + lane] : 0.0;
 #pragma unroll
     for (int j = 0; j < 32; j++) {
-      const double aj = __shfl_sync(0xffffffffu, a, j);
-      if (lane > j) a = fma(-aj, ld[j], a);
+      const double vj = __shfl_sync(0xffffffffu, v, j);
+      if (lane > j) v = fma(-vj, ld[j], v);
     }
-    return a * rinvs[cb * 32 + lane];
-  };
-  a0 = solve32(a0, 2 * J);
-  __syncthreads();  // S staged
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll
-  for (int p = 0; p < 32; p += 4) {
-    s0 = fma(__shfl_sync(0xffffffffu, a0, p), S[lane][p], s0);
-    s1 = fma(__shfl_sync(0xffffffffu, a0, p + 1), S[lane][p + 1], s1);
-    s2 = fma(__shfl_sync(0xffffffffu, a0, p + 2), S[lane][p + 2], s2);
-    s3 = fma(__shfl_sync(0xffffffffu, a0, p + 3), S[lane][p + 3], s3);
+    a[q] = v * rinvs[cb * 32 + lane];
   }
-  a1 = solve32(a1 - ((s0 + s1) + (s2 + s3)), 2 * J + 1);
-  X[(size_t)(c0 + lane) * nb] = a0;
-  X[(size_t)(c0 + 32 + lane) * nb] = a1;
+#pragma unroll
+  for (int q = 0; q < NQ; q++) X[(size_t)(c0 + 32 * q + lane) * nb] = a[q];
   if (digits) {
     const size_t slot = (size_t)slot0 + z;
-    row_digits_tw(a0, a1, exps + slot * nb + r, digits + (slot * NS * nb + r) * TW, (size_t)nb * TW);
+    row_digits_tw(a, exps + slot * nb + r, digits + (slot * NS * nb + r) * TW, (size_t)nb * TW);
   }
 }
 

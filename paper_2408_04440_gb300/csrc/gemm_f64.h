@@ -84,9 +84,9 @@ emu_status launch_dense_digits(emu_ctx *ctx, const double *X, long ld, int nrows
 // (TW columns) of every listed tile is solved on the FP64 pipe against the
 // TW x TW diagonal block of L_kk (launch_trsm_block), then its contribution to
 // the later blocks, X_J L_{>J,J}^T, is subtracted as digit products on the
-// tensor cores (launch, K = TW), so the FP64 pipe runs TW/nb of the nb^3 flops
-// of a tile.
-constexpr int TW = 64;
+// tensor cores (launch, K = TW, output blocks of BN columns), so the FP64 pipe
+// runs TW/nb of the nb^3 flops of a tile in nb/TW solve launches.
+constexpr int TW = 128;
 // Digits of L_kk's column blocks J < nb/TW - 1, rows r >= (J+1) TW (the rows
 // the products read): exps[J nb + r] (biased), plane p of row r at arena row
 // (J NS + p) nb + r of an arena with TW columns.  nb a multiple of BM.

@@ -707,11 +707,12 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
   }
   // blocked FP64-class TRSM: per step and list (row k+1 in slot 0, rows >= k+2
   // in slots 1..), for each column block J < nJ - 1 the products of every
-  // listed tile's (BM-row block, later TW-column block) pairs, J-major
+  // listed tile's (BM-row block, BN-column block right of block J) pairs,
+  // J-major
   std::vector<gemm64::Item> items_tr;
   std::vector<gemm64::Seg> segs_tr;
   const int nJ = nb / gemm64::TW;
-  P->blk64 = nb % gemm64::BM == 0 && nJ >= 2;
+  P->blk64 = nb % gemm64::TW == 0 && nb % gemm64::BM == 0 && nJ >= 2;
   if (P->blk64) {
     int max_r = 0;
     for (StepPlan &sp : P->steps) {
@@ -722,20 +723,20 @@ static emu_status build_plan(emu_ctx *ctx, emu_mat *A, MixedPlan *P) {
         for (int J = 0; J + 1 < nJ; J++)
           for (int z = 0; z < n; z++)
             for (int rb = 0; rb < nb / gemm64::BM; rb++)
-              for (int cb = J + 1; cb < nJ; cb++) {
+              for (int cb = (J + 1) * (gemm64::TW / gemm64::BN); cb < nb / gemm64::BN; cb++) {
                 gemm64::Seg sg;
                 sg.a_row = (slot0 + z) * gemm64::NS * nb + rb * gemm64::BM;
-                sg.b_row = J * gemm64::NS * nb + cb * gemm64::TW;
+                sg.b_row = J * gemm64::NS * nb + cb * gemm64::BN;
                 sg.a_x = sg.b_x = 0;
                 gemm64::Item it;
-                it.out_off = (long)tiles64[r0 + z] * nb * nb + rb * gemm64::BM + (long)cb * gemm64::TW * nb;
+                it.out_off = (long)tiles64[r0 + z] * nb * nb + rb * gemm64::BM + (long)cb * gemm64::BN * nb;
                 it.a_sc = (slot0 + z) * nb + rb * gemm64::BM;
-                it.b_sc = J * nb + cb * gemm64::TW;
+                it.b_sc = J * nb + cb * gemm64::BN;
                 it.seg_begin = (int)segs_tr.size();
                 segs_tr.push_back(sg);
                 it.seg_end = (int)segs_tr.size();
                 it.rows_valid = gemm64::BM;
-                it.cols_valid = gemm64::TW;
+                it.cols_valid = gemm64::BN;
                 items_tr.push_back(it);
               }
       }
@@ -1172,7 +1173,7 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
       emu_status e = gemm64::launch_trsm_block(ctx, A->t64, nb, P->d_tiles64 + r64, n64, Lkk, J, Ls, ri, slot0,
                                                P->d_xexp, last ? nullptr : P->d_xdig);
       if (e != EMU_OK || last) return e;
-      const int cnt = per_pair * (nJ - 1 - J);
+      const int cnt = per_pair * (nJ - 1 - J) * (gemm64::TW / gemm64::BN);
       if ((e = gemm64::launch(ctx, P->map_xa, P->map_lb[k & 1], P->d_items_tr + off, cnt, P->d_segs_tr,
                               gemm64::TW, nb, nb, P->d_xexp, P->d_lexp + (size_t)(k & 1) * (nJ - 1) * nb,
                               gemm64::TC64_SUB, A->t64, nb, ctx->sm_count)) != EMU_OK)
