@@ -113,8 +113,10 @@ __device__ inline void write_digits(double v, uint16_t *d, size_t plane) {
   }
 }
 
-// Row exponents: one CTA per (32 rows, listed tile): lane = row, warps stride
-// columns; exp[base + r] = max(exp[base + r], e_r) with every |x_rc| < 2^e_r.
+// Row exponents: one CTA per (32 rows, listed tile, stripe of the columns):
+// lane = row, warps stride the stripe's columns; exp[base + r] =
+// max(exp[base + r], e_r) with every |x_rc| < 2^e_r (the stripes combine
+// through the atomic maximum).
 __global__ void __launch_bounds__(256)
     k_rowexp64(const double *__restrict__ t64, const float *__restrict__ t32, const unsigned char *__restrict__ cls,
                const int4 *__restrict__ jobs, int nb, int *__restrict__ exps, const int *st) {
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(256)
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int r = blockIdx.x * 32 + lane;
   double m = 0.0;
-  for (int c = w; c < nb; c += 8) {
+  for (int c = blockIdx.z * 8 + w; c < nb; c += 8 * gridDim.z) {
     size_t o = base + r + (size_t)c * nb;
     double x = f64 ? t64[o] : (double)t32[o];
     m = fmax(m, fabs(x));
@@ -571,7 +573,7 @@ emu_status launch_row_exponents(emu_ctx *ctx, const double *t64, const float *t3
                                 const int4 *d_jobs, int njobs, int nb, int *exps) {
   if (njobs <= 0) return EMU_OK;
   ProfScope ps(ctx, PROF_SPLIT, 0.0, 8.0 * njobs * (double)nb * nb);
-  k_rowexp64<<<dim3(nb / 32, njobs), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, exps, ctx->d_status);
+  k_rowexp64<<<dim3(nb / 32, njobs, 8), 256, 0, ctx->stream>>>(t64, t32, cls, d_jobs, nb, exps, ctx->d_status);
   EMU_LAUNCHED(ctx);
   return EMU_OK;
 }

@@ -1240,7 +1240,9 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
     ctx->stream = ctx->crit;
     if (sp.diag_low) {
       ProfScope ps(ctx, PROF_SPLIT, 0.0, 12.0 * te);
-      k_tile_to_f64<<<64, 256, 0, ctx->stream>>>(A->t32 + tkk * te, A->t64 + tkk * te, te, st);
+      // one element per thread: the widening sits on the critical stream
+      k_tile_to_f64<<<(unsigned)((te + 255) / 256), 256, 0, ctx->stream>>>(A->t32 + tkk * te, A->t64 + tkk * te,
+                                                                          te, st);
       EMU_LAUNCHED(ctx);
     }
     if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) break;
