@@ -768,35 +768,41 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
         va = __ldcg(gp(n1, n1, ir, ic));
         vb = __ldcg(gp(n1, n1, ir, ic + 8));
       }
-      // p = r_j u_{ir,j} is formed as column j arrives and used one step of
+      // p = r_j u_{ir,j} is formed as column j arrives and used two steps of
       // the loop later, and even and odd columns go to two sums, so that no
-      // FMA waits for the multiply or the FMA just before it
-      // (the odd sum joins the even one before the last column's FMA, so
-      // that only the multiply and one FMA follow the last column)
-      double va1 = 0.0, vb1 = 0.0, p = 0.0, q0 = 0.0, q1 = 0.0;
+      // FMA waits for the multiply or the FMA before it; the odd sum joins the
+      // even one before the last two columns' FMAs
+      double va1 = 0.0, vb1 = 0.0;
+      double p1 = 0.0, q10 = 0.0, q11 = 0.0;  // column j - 1
+      double p2 = 0.0, q20 = 0.0, q21 = 0.0;  // column j - 2
 #pragma unroll 2
       for (int j = 0; j < PB; j++) {
-        if (j & 1) {
-          va = fma(-p, q0, va);  // column j - 1, even
-          vb = fma(-p, q1, vb);
-        } else if (j >= 2) {
-          va1 = fma(-p, q0, va1);
-          vb1 = fma(-p, q1, vb1);
+        if (j >= 2) {
+          if (j & 1) {
+            va1 = fma(-p2, q20, va1);  // column j - 2, odd
+            vb1 = fma(-p2, q21, vb1);
+          } else {
+            va = fma(-p2, q20, va);
+            vb = fma(-p2, q21, vb);
+          }
         }
-        if (j == PB - 1) {
-          va += va1;
-          vb += vb1;
-        }
+        p2 = p1;
+        q20 = q10;
+        q21 = q11;
         if (!wait_local(&mbar[18 + j], par, &flags[2])) {  // arrivals of warps 0..3 of this CTA
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 8;
           flags[0] = 1;
         }
-        p = uu[j][ir] * ms[j][PB];
-        q0 = uu[j][ic];
-        q1 = uu[j][ic + 8];
+        p1 = uu[j][ir] * ms[j][PB];
+        q10 = uu[j][ic];
+        q11 = uu[j][ic + 8];
       }
-      va = fma(-p, q0, va);  // column PB - 1
-      vb = fma(-p, q1, vb);
+      va += va1;
+      vb += vb1;
+      va = fma(-p2, q20, va);  // column PB - 2
+      vb = fma(-p2, q21, vb);
+      va = fma(-p1, q10, va);  // column PB - 1
+      vb = fma(-p1, q11, vb);
       // -S (step 0: C_1) entries (ir, ic), (ir, ic + 8) into the master's xc:
       // its next leaf starts from C' - S
       st_peer_f64(xc_m + (uint32_t)(ir * (PB + 1) + ic) * 8u, va);
