@@ -597,6 +597,17 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
           v0 += lout[i][k0];
           v1 += lout[i][k1];
         }
+        // the terms of columns 14 and 15, u_j r_j u_j^T: the first helper's
+        // u_j in xr rows 0, 1, the pivot reciprocals r_j in xr[j][PB]
+        if (!wait_from_peer(&mbar[19], (uint32_t)s & 1u, &flags[2])) {
+          if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 14;
+          flags[0] = 1;
+        }
+        const double pa = xr[0][i] * xr[PB - 2][PB], pb = xr[1][i] * xr[PB - 1][PB];
+        v0 = fma(-pa, xr[0][k0], v0);
+        v1 = fma(-pa, xr[0][k1], v1);
+        v0 = fma(-pb, xr[1][k0], v0);
+        v1 = fma(-pb, xr[1][k1], v1);
       }
     } else {
       // forward the leaf's scaled columns, then 1/L_kk, to the helpers in
@@ -702,8 +713,9 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
   auto gp = [&](int br, int bc, int r, int c) { return D + (size_t)(br * PB + r) + (size_t)(bc * PB + c) * ld; };
   // the master's objects: C_{s+1} goes to its xc (this CTA's xo at the same
   // address); its mbar[17] counts one arrival per warp of this CTA
-  const uint32_t xc_m = peer_addr(xo, 0);
+  const uint32_t xc_m = peer_addr(xo, 0), xr_m = peer_addr(xprev, 0);  // the master's xc and xr
   const uint32_t mbx_m = peer_addr(&mbar[17], 0), stop_m = peer_addr((const void *)&flags[2], 0);
+  const uint32_t mbu_m = peer_addr(&mbar[19], 0);
   const uint32_t stop_h2 = peer_addr((const void *)&flags[2], 2);
   for (int s = 0; s + 1 < nbb; s++) {
     const int n1 = s + 1;
@@ -739,12 +751,23 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       // formed column j of L_{s,s} (in the unscaled form x_j L_jj)
 #pragma unroll
       for (int j = 0; j < PB; j++) {
+        if (j >= PB - 2) {
+          // u_{.,j} is final once column j-1 is applied: the last two go to
+          // the master (rows 0, 1 of its xr, forwarded long before), which
+          // subtracts their terms of X X^T itself
+          if (ct == j) {
+            st_peer_f64(xr_m + (uint32_t)((j - (PB - 2)) * (PB + 1) + cr) * 8u, va);
+            st_peer_f64(xr_m + (uint32_t)((j - (PB - 2)) * (PB + 1) + cr + 8) * 8u, vb);
+          }
+          __syncwarp();
+          if ((tid & 31) == 0) arrive_peer(mbu_m);
+        }
         if (col_group_first(j) && !wait_from_peer(&mbar[col_group_bar(j)], par, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 5;
           flags[0] = 1;
         }
-        if (ct == j) {
-          // u_{cr,j}, u_{cr+8,j} are final: to the C accumulation (warps 4..7)
+        if (j < PB - 2 && ct == j) {
+          // u_{cr,j}, u_{cr+8,j} are final: to the accumulation (warps 4..7)
           uu[j][cr] = va;
           uu[j][cr + 8] = vb;
           tc::mbar_arrive(&mbar[18 + j]);
@@ -772,11 +795,12 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       // the loop later, and even and odd columns go to two sums, so that no
       // FMA waits for the multiply or the FMA before it; the odd sum joins the
       // even one before the last two columns' FMAs
+      // (columns 0..PB-3; the master takes the last two)
       double va1 = 0.0, vb1 = 0.0;
       double p1 = 0.0, q10 = 0.0, q11 = 0.0;  // column j - 1
       double p2 = 0.0, q20 = 0.0, q21 = 0.0;  // column j - 2
 #pragma unroll 2
-      for (int j = 0; j < PB; j++) {
+      for (int j = 0; j < PB - 2; j++) {
         if (j >= 2) {
           if (j & 1) {
             va1 = fma(-p2, q20, va1);  // column j - 2, odd
@@ -799,9 +823,9 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
       }
       va += va1;
       vb += vb1;
-      va = fma(-p2, q20, va);  // column PB - 2
+      va = fma(-p2, q20, va);  // column PB - 4
       vb = fma(-p2, q21, vb);
-      va = fma(-p1, q10, va);  // column PB - 1
+      va = fma(-p1, q10, va);  // column PB - 3
       vb = fma(-p1, q11, vb);
       // -S (step 0: C_1) entries (ir, ic), (ir, ic + 8) into the master's xc:
       // its next leaf starts from C' - S
@@ -1080,6 +1104,7 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
         for (int j = 0; j <= PB; j++) tc::mbar_init(&mbar[j], PB);
         tc::mbar_init(&mbar[17], 4);
         tc::mbar_init(&mbar[18], 4);  // C' from the second helper: one arrival per warp 4..7 of it
+        tc::mbar_init(&mbar[19], 8);  // u_14, u_15 from the first helper: one arrival per warp 0..3 and column
       } else if (rank == 1) {
         // columns (one arrival of the master's forwarding warp), rinv of even
         // / odd steps, column j of u (one thread per half-warp of warps 0..3)
