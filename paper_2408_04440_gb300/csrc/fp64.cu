@@ -237,8 +237,8 @@ __device__ inline double panel_dot(const double (*A)[PB + 1], const double (*Bm)
 // updates its trailing entries, x_ik -= c_j[i] c_j[k] / c_jj.  At the end
 // L_ik = c_k[i] / sqrt(c_kk) goes to out[i][k] and 1/L_kk to rinv[k].
 // Returns 0, or the 1-based column of the first non-positive pivot (the
-// same in every thread; out is then not written).  With ms given (the pair
-// form of the chain): at step j the 16 threads of rows i = u < 16 store the
+// same in every thread; out is then not written; out may be null).  With ms
+// given (the cluster form of the chain): at step j the 16 threads of rows i = u < 16 store the
 // scaled column c_j[i] / c_jj (= L_ij / L_jj) into ms[j][i] and thread j the
 // pivot reciprocal 1/c_jj into ms[j][16]; after columns 3, 7, 11, 13, 14 and
 // 15 each arrives on the local mbarrier mb[j] (16 arrivals); at the end they
@@ -524,13 +524,13 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
 //     the master's xc;
 //   second helper (rank 2): block (s+2, s) solved the same way into
 //     X_{s+2,s}, then panel s applied to block (s+2, s+2), the first
-//     helper's next C' (potrf_tri_helper).
+//     helper's next C' (potrf_chain_helper2).
 // The master's mbar phases advance once per step (parity s & 1).  flags[2]
 // of each CTA is set by another when it stops (a failed pivot or wait), and
 // every wait on a peer also gives up at that flag or the wait bound; the
 // three CTAs end at one cluster barrier, so none leaves while another may
 // still write into its shared memory.
-__device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb, int gcol0, int *__restrict__ state,
+__device__ __forceinline__ void potrf_chain_master(double *__restrict__ D, int nb, int gcol0, int *__restrict__ state,
                                                   double *__restrict__ rinv_g, int *st,
                                                   unsigned long long *__restrict__ trace, double (*lout)[PB + 1],
                                                   double (*mcol)[PB + 1], double (*xr)[PB + 1],
@@ -614,7 +614,7 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
       // the groups the leaf releases them in (columns 0-3, 4-7, 8-11, 12-13,
       // 14, 15, then 1/L_kk: local mbar[3], [7], [11], [13], [14], [15],
       // [16]); each group's remote stores are released by one cluster-scope
-      // arrival on the helper's barrier of the group's last column, and two
+      // arrival on that helper's barrier of the group's last column, and two
       // warps per helper take alternate groups, so that two releases are in
       // flight (the remote store and its release stay off the leaf's pivot
       // chain).  First helper (warps 4, 6): columns into its ms, 1/L_kk into
@@ -699,7 +699,7 @@ __device__ __forceinline__ void potrf_pair_master(double *__restrict__ D, int nb
   cluster_barrier();
 }
 
-__device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
+__device__ __forceinline__ void potrf_chain_helper1(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
                                                   unsigned long long *__restrict__ trace, double (*ms)[PB + 1],
                                                   double (*xprev)[PB + 1], double (*xo)[PB + 1],
                                                   double (*uu)[PB + 1], double (*rinv2)[PB], volatile int *flags,
@@ -896,7 +896,7 @@ __device__ __forceinline__ void potrf_pair_helper(double *__restrict__ D, int nb
 // steps, ms1 and mbar[17..33] in odd ones, 1/L_kk in rinv2[s & 1]), so that
 // the master may run a step ahead of this CTA: its step s+2 waits for the
 // first helper's step s+1, which waits for this CTA's X_{s+2,s}.
-__device__ __forceinline__ void potrf_tri_helper(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
+__device__ __forceinline__ void potrf_chain_helper2(double *__restrict__ D, int nb, int *__restrict__ state, int *st,
                                                  unsigned long long *__restrict__ trace, double (*ms0)[PB + 1],
                                                  double (*ms1)[PB + 1], double (*xn)[PB + 1], double (*xs)[PB + 1],
                                                  double (*rinv2)[PB], volatile int *flags, uint64_t *mbar) {
@@ -1124,11 +1124,11 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     double *rinv_g = rinv_all;
     unsigned long long *tr = trace ? trace + (size_t)(ntasks + (size_t)rank * nbb) * 5 : nullptr;
     if (rank == 0)
-      potrf_pair_master(D0, nb, gcol0, ws + 1, rinv_g, st, tr, a, m, xr, xc, rinv, rinv2, mflags, mbar);
+      potrf_chain_master(D0, nb, gcol0, ws + 1, rinv_g, st, tr, a, m, xr, xc, rinv, rinv2, mflags, mbar);
     else if (rank == 1)
-      potrf_pair_helper(D0, nb, ws + 1, st, tr, m, xr, xc, a, rinv2, mflags, mbar);
+      potrf_chain_helper1(D0, nb, ws + 1, st, tr, m, xr, xc, a, rinv2, mflags, mbar);
     else
-      potrf_tri_helper(D0, nb, ws + 1, st, tr, m, a, xr, xc, rinv2, mflags, mbar);
+      potrf_chain_helper2(D0, nb, ws + 1, st, tr, m, a, xr, xc, rinv2, mflags, mbar);
     return;
   }
   // a factor that has already failed (status set by an earlier launch) stops
