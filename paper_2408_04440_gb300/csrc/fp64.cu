@@ -578,10 +578,12 @@ __device__ __forceinline__ void potrf_chain_master(double *__restrict__ D, int n
       }
       bar_arrive_256(6);  // the columns of L_{s,s} and 1/L_kk are in mcol and rinv
       if (more && !fail) {
-        // C_{s+1} = C' - S: S = X_{s+1,s} X_{s+1,s}^T from the first helper
-        // (-S in xc; in step 0 it sends C_1 itself), C' = block (s+1, s+1)
-        // after every panel < s from the second helper (in lout, from step
-        // 1 on), which this CTA's compute warps then release to it again
+        // C_{s+1} = C' - X_{s+1,s} X_{s+1,s}^T: the first helper sends -S,
+        // S the sum over the solve's columns 0..13 (in xc; in step 0 block
+        // (1, 1) minus S), the second helper C' = block (s+1, s+1) after
+        // every panel < s (in lout, from step 1 on; released to it again
+        // after the step's barrier), and the terms of columns 14 and 15
+        // follow below
         if (!wait_from_peer(&mbar[17], (uint32_t)s & 1u, &flags[2])) {
           if (!flags[2] && atomicCAS(&st[ST_CODE], DEV_OK, DEV_TIMEOUT) == DEV_OK) st[ST_AUX] = 4;
           flags[0] = 1;
