@@ -518,13 +518,13 @@ __device__ __forceinline__ void potrf_master(double *__restrict__ D, int nb, int
 //     minus X_{s+1,s-1} X_{s,s-1}^T (X_{s+1,s-1} from the second helper's
 //     step s-1), solved one column behind the leaf into X_{s+1,s}, scaled by
 //     1/L_jj and published;
-//   first helper, warps 4..7: C_{s+1} = C' - X_{s+1,s} X_{s+1,s}^T
-//     accumulated column by column as the solve finishes each, with C'
-//     (block (s+1, s+1) after every panel < s) from the second helper, into
-//     the master's xc;
+//   first helper, warps 4..7: X_{s+1,s} X_{s+1,s}^T accumulated over the
+//     solve's columns 0..13 as the solve finishes each, sent negated into the
+//     master's xc; columns 14 and 15 of the solve go to the master's xr as
+//     soon as they are final, and the master adds their terms itself;
 //   second helper (rank 2): block (s+2, s) solved the same way into
-//     X_{s+2,s}, then panel s applied to block (s+2, s+2), the first
-//     helper's next C' (potrf_chain_helper2).
+//     X_{s+2,s}, then panel s applied to block (s+2, s+2), the master's C'
+//     of its step s+1 (into its lout; potrf_chain_helper2).
 // The master's mbar phases advance once per step (parity s & 1).  flags[2]
 // of each CTA is set by another when it stops (a failed pivot or wait), and
 // every wait on a peer also gives up at that flag or the wait bound; the
