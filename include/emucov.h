@@ -191,9 +191,10 @@ emu_status emu_prof_timeline(emu_ctx *ctx, double *h_out, size_t max_records,
  * phase instead, and the middle timestamp ends the solve.)  In the cluster
  * form the first helper's records follow (kind 5, one per step s < nb/16 - 1):
  * r = s+1, c = s, the start of its step, the arrival of its inputs
- * (X_{s+1,s-1} and blocks (s+1, s), (s+1, s+1)) and the time C_{s+1} was
- * sent and X_{s+1,s} published; the second word packs the SM id with the
- * nanoseconds from the inputs to the end of the solve (bits 8-25).  Then the
+ * (X_{s+1,s-1} and block (s+1, s)) and the time its part of
+ * X_{s+1,s} X_{s+1,s}^T was sent and X_{s+1,s} published; the second word
+ * packs the SM id with the nanoseconds from the inputs to the end of the
+ * solve (bits 8-25).  Then the
  * second helper's (kind 6, one per step s < nb/16 - 2): r = s+2, c = s, the
  * start of its step, the arrival of X_{s+2,s-1} and X_{s,s-1} (its update by
  * panel s-1), the publication of X_{s+2,s}, and in the second word the
