@@ -106,6 +106,15 @@ __device__ inline bool dag_wait3(const int *state, int i0, int v0, int i1, int v
     __nanosleep(32);
   }
 }
+// Thread 0 of an idle CTA: waits until *flag >= v, the factor has failed,
+// or the flag waits' bound has passed, whichever comes first; it sets no
+// status (the waits that need the flag report a timeout themselves).
+__device__ inline void idle_until(const int *flag, int v, const int *st) {
+  const long long t0 = clock64();
+  while (*((volatile const int *)flag) < v && *((volatile const int *)st) == DEV_OK &&
+         clock64() - t0 <= c_dag_wait_cycles)
+    __nanosleep(256);
+}
 __device__ inline bool dag_wait2(const int *state, int i0, int v0, int i1, int v1, int *st) {
   return dag_wait3(state, i0, v0, i1, v1, -1, 0, st);
 }
@@ -1082,11 +1091,16 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   const int nbb = nb / PB;
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
-  // Single tile: a CTA on the master's SM leaves (before its first task if
-  // it starts there after the master, else after its current task), so that
-  // the chain has that SM's FP64 pipes to itself.  At most half the launch
-  // leaves, so the chain always keeps workers.
-  // ws extras: master SM id + 1, CTAs that left, the helpers' SM ids + 1
+  // Single tile: a CTA on one of the chain's SMs fetches no task (from its
+  // start if it starts there after the chain, else from its next fetch).  It
+  // stays resident and idle until the chain has published its last diagonal
+  // block, so that neither it nor a CTA of another kernel takes that SM's
+  // FP64 pipes from the chain.  (A CTA that left instead was replaced on the
+  // same SM by the launch's next pending CTA, and once the number that could
+  // leave was used up, the rest worked there.)  At most kMaxIdle CTAs idle,
+  // so the chain always keeps workers.
+  // ws extras: master SM id + 1, idle CTAs, the helpers' SM ids + 1
+  constexpr int kMaxIdle = 12;  // 3 SMs x 3 further CTAs of 256 threads
   int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
   unsigned my_sm = 0;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
@@ -1142,11 +1156,12 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
     return *((volatile int *)master_sm) == me || *((volatile int *)(master_sm + 2)) == me ||
            *((volatile int *)(master_sm + 3)) == me;
   };
-  if (threadIdx.x == 0) s_leave = on_chain_sm() && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2;
+  if (threadIdx.x == 0) s_leave = 0;
   while (true) {
     if (threadIdx.x == 0) {
+      if (!s_leave && on_chain_sm() && atomicAdd(master_sm + 1, 1) < kMaxIdle) s_leave = 1;
       s_task = s_leave ? INT_MAX : atomicAdd(counter, 1) + (clus ? 1 : 0);  // cluster form: task 0 is cluster 0's
-      if (!s_leave && on_chain_sm() && atomicAdd(master_sm + 1, 1) < (int)gridDim.x / 2) s_leave = 1;
+      if (s_leave) idle_until(ws + 1 + (size_t)(nbb - 1) * (nbb + 1), nbb, st);  // L of the last diagonal block
     }
     __syncthreads();
     int t = s_task;
