@@ -1182,7 +1182,27 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
     }
     return EMU_OK;
   };
-  auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical) -> emu_status {
+  // BF16 pieces of n64 listed FP64-class tiles (the low-class updates' operands)
+  auto split64 = [&](int r64, int n64) -> emu_status {
+    if (n64 <= 0) return EMU_OK;
+    ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
+    k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
+                                                                                  P->d_tiles64 + r64, nb, 0, st);
+    EMU_LAUNCHED(ctx);
+    return EMU_OK;
+  };
+  // FP32 copy and BF16 pieces of L_kk for the low-class TRSMs of panel k
+  auto prep32 = [&](int k) -> emu_status {
+    const long tkk = tile_index(k, k, NT);
+    if (P->tc_trsm)
+      return trsm_tc::launch_prep(ctx, A->t64, tkk, nullptr, 1, P->d_lkk32 + (size_t)(k & 1) * te,
+                                  P->d_lkkp + (size_t)(k & 1) * 3 * te, nb);
+    k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te, P->d_lkk32 + (size_t)(k & 1) * te,
+                                                             te, st);
+    EMU_LAUNCHED(ctx);
+    return EMU_OK;
+  };
+  auto trsm_rows = [&](int k, int r64, int n64, int r32, int n32, bool critical, bool split = true) -> emu_status {
     emu_status e = EMU_OK;
     if (n64 > 0) {
       const StepPlan &sp = P->steps[k];
@@ -1192,10 +1212,7 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
         e = launch_trsm64_panel(ctx, A, k, P->d_rows64 + r64, n64, P->d_ls64 + (size_t)(k & 1) * nb * 32,
                                 P->d_rinv64 + (size_t)(k & 1) * nb);
       if (e != EMU_OK) return e;
-      ProfScope ps(ctx, PROF_SPLIT, 0.0, 14.0 * n64 * te);
-      k_split_tiles<double><<<dim3((nb / B) * (nb / B), n64), 256, 0, ctx->stream>>>(A->t64, A->op_bf16,
-                                                                                    P->d_tiles64 + r64, nb, 0, st);
-      EMU_LAUNCHED(ctx);
+      if (split && (e = split64(r64, n64)) != EMU_OK) return e;
     }
     if (n32 > 0 && P->tc_trsm)
       return trsm_tc::launch(ctx, P->lmap, P->opmap, P->d_lkk32, A->t32, nb, NT, k, P->d_rows32 + r32, nullptr, n32);
@@ -1246,18 +1263,9 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
       EMU_LAUNCHED(ctx);
     }
     if ((s = launch_potrf64_tile(ctx, A, k)) != EMU_OK) break;
-    if (sp.n32_1 + sp.n32_r > 0) {
-      if (P->tc_trsm) {
-        // FP32 copy and BF16 pieces of L_kk for the tensor-core TRSMs
-        if ((s = trsm_tc::launch_prep(ctx, A->t64, tkk, nullptr, 1, P->d_lkk32 + (size_t)(k & 1) * te,
-                                      P->d_lkkp + (size_t)(k & 1) * 3 * te, nb)) != EMU_OK)
-          break;
-      } else {
-        k_diag_to_f32<<<2 * ctx->sm_count, 256, 0, ctx->stream>>>(A->t64 + tkk * te,
-                                                                 P->d_lkk32 + (size_t)(k & 1) * te, te, st);
-        EMU_LAUNCHED(ctx);
-      }
-    }
+    // L_kk's FP32 copy and pieces are made on the critical stream only if its
+    // own TRSM needs them, else on the panel stream before its TRSMs
+    if (sp.n32_1 > 0 && (s = prep32(k)) != EMU_OK) break;
     if (sp.n64_1 + sp.n64_r > 0 &&
         (s = launch_trsm64_prep(ctx, A->t64 + tkk * te, nb, P->d_ls64 + (size_t)(k & 1) * nb * 32,
                                 P->d_rinv64 + (size_t)(k & 1) * nb)) != EMU_OK)
@@ -1268,7 +1276,11 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
       break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_P), ctx->crit));
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->crit, ev(k - 1, E_G1), 0));
-    if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true)) != EMU_OK) break;
+    // the BF16 pieces of an FP64-class row k+1 feed only the panel stream's
+    // G1(k), unless the critical SYRK or this row's E4M3 / TF32 copies read
+    // them: then they are made here, else on the panel stream before G1(k)
+    const bool split1_here = sp.i_n[GR_S] > 0 || sp.nq_1 > 0 || sp.nt_1 > 0;
+    if ((s = trsm_rows(k, sp.r64_1, sp.n64_1, sp.r32_1, sp.n32_1, true, split1_here)) != EMU_OK) break;
     if ((s = quantize(sp.q_1, sp.nq_1)) != EMU_OK) break;
     if ((s = tf32copy(sp.t_1, sp.nt_1)) != EMU_OK) break;
     if ((s = slice64(sp.z1_off, sp.z1_n)) != EMU_OK) break;
@@ -1278,12 +1290,14 @@ static emu_status factor_mixed_record(emu_ctx *ctx, emu_mat *A, MixedPlan *P, in
     // ---- mid stream
     ctx->stream = ctx->mid;
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_P), 0));
+    if (sp.n32_1 == 0 && sp.n32_r > 0 && (s = prep32(k)) != EMU_OK) break;
     if ((s = trsm_rows(k, sp.r64_r, sp.n64_r, sp.r32_r, sp.n32_r, false)) != EMU_OK) break;
     if ((s = quantize(sp.q_r, sp.nq_r)) != EMU_OK) break;
     if ((s = tf32copy(sp.t_r, sp.nt_r)) != EMU_OK) break;
     if ((s = slice64(sp.zr_off, sp.zr_n)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_T), ctx->mid));
     EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k, E_T1), 0));
+    if (!split1_here && (s = split64(sp.r64_1, sp.n64_1)) != EMU_OK) break;
     if (k > 0) EMU_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->mid, ev(k - 1, E_G2), 0));
     if ((s = update_group(k, GR_G1, ctx->sm_count)) != EMU_OK) break;
     EMU_CUDA_TRY(ctx, cudaEventRecord(ev(k, E_G1), ctx->mid));
