@@ -1092,15 +1092,18 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   const int tx = threadIdx.x % PB, ty = threadIdx.x / PB;
   const size_t ld = nb;
   // Single tile: a CTA on one of the chain's SMs fetches no task (from its
-  // start if it starts there after the chain, else from its next fetch).  It
-  // stays resident and idle until the chain has published its last diagonal
-  // block, so that neither it nor a CTA of another kernel takes that SM's
-  // FP64 pipes from the chain.  (A CTA that left instead was replaced on the
-  // same SM by the launch's next pending CTA, and once the number that could
-  // leave was used up, the rest worked there.)  At most kMaxIdle CTAs idle,
-  // so the chain always keeps workers.
-  // ws extras: master SM id + 1, idle CTAs, the helpers' SM ids + 1
-  constexpr int kMaxIdle = 12;  // 3 SMs x 3 further CTAs of 256 threads
+  // start if it starts there after the chain, else from its next fetch).  On
+  // the master's SM it stays resident and idle until the chain has published
+  // its last diagonal block, so that neither it nor a CTA of another kernel
+  // takes that SM's FP64 pipes from the leaf; a CTA that left instead was
+  // replaced there by the launch's next pending CTA, and once the number that
+  // could leave was used up, the rest worked there.  At most kMaxIdle CTAs
+  // idle.  On a helper's SM it leaves (at most half the launch leaves, so the
+  // chain always keeps workers): idle CTAs there measurably slowed the
+  // helpers' steps.
+  // ws extras: master SM id + 1, idle CTAs, the helpers' SM ids + 1, CTAs
+  // that left
+  constexpr int kMaxIdle = 12;
   int *master_sm = ws + 1 + (size_t)nbat * nbb * nbb;
   unsigned my_sm = 0;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
@@ -1149,19 +1152,20 @@ __global__ void __launch_bounds__(PB * PB, BATCH ? 1 : 4)
   }
   // a factor that has already failed (status set by an earlier launch) stops
   if (*((volatile const int *)st) != DEV_OK) return;
-  // a CTA on one of the chain's SMs
-  auto on_chain_sm = [&]() {
-    if (BATCH) return false;
-    const int me = (int)my_sm + 1;
-    return *((volatile int *)master_sm) == me || *((volatile int *)(master_sm + 2)) == me ||
-           *((volatile int *)(master_sm + 3)) == me;
-  };
   if (threadIdx.x == 0) s_leave = 0;
   while (true) {
     if (threadIdx.x == 0) {
-      if (!s_leave && on_chain_sm() && atomicAdd(master_sm + 1, 1) < kMaxIdle) s_leave = 1;
+      if (!s_leave && !BATCH) {
+        const int me = (int)my_sm + 1;
+        if (*((volatile int *)master_sm) == me) {
+          if (atomicAdd(master_sm + 1, 1) < kMaxIdle) s_leave = 2;
+        } else if ((*((volatile int *)(master_sm + 2)) == me || *((volatile int *)(master_sm + 3)) == me) &&
+                   atomicAdd(master_sm + 4, 1) < (int)gridDim.x / 2) {
+          s_leave = 1;
+        }
+      }
       s_task = s_leave ? INT_MAX : atomicAdd(counter, 1) + (clus ? 1 : 0);  // cluster form: task 0 is cluster 0's
-      if (s_leave) idle_until(ws + 1 + (size_t)(nbb - 1) * (nbb + 1), nbb, st);  // L of the last diagonal block
+      if (s_leave == 2) idle_until(ws + 1 + (size_t)(nbb - 1) * (nbb + 1), nbb, st);  // L of the last diagonal block
     }
     __syncthreads();
     int t = s_task;
@@ -1738,11 +1742,11 @@ extern "C" emu_status emu_potrf_task_list(int nb, int single_tile, int16_t *h_ta
 
 // Ints of the dataflow POTRF workspace for nbat tiles: the task counter and
 // each tile's block states, rounded up to a whole number of doubles.
-// counter, state[nbb*nbb] per tile, master SM id + 1, CTAs that left it,
-// helper SM id + 1; even, so that the pivot reciprocals after it are 8-byte
-// aligned
+// counter, state[nbb*nbb] per tile, master SM id + 1, CTAs idle on it, the
+// helpers' SM ids + 1, CTAs that left theirs; even, so that the pivot
+// reciprocals after it are 8-byte aligned
 static size_t dag_ws_ints(int nbb, int nbat) {
-  size_t n = 5 + (size_t)nbat * nbb * nbb;
+  size_t n = 6 + (size_t)nbat * nbb * nbb;
   return (n + 1) & ~(size_t)1;
 }
 
