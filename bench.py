@@ -188,6 +188,14 @@ def run_ours(a):
         return info
 
     with torch.cuda.stream(stream):
+        # untimed setup: the library's tuner times its four reserved-SM choices
+        # on the first four factors of a matrix signature (each choice's first
+        # factor also records its CUDA graph); they run here, before the W
+        # warm-up steps, so that every timed step uses the tuned schedule
+        tuning_steps = 0
+        while tuning_steps < 8 and ctx.schedule_info()[0] < 4:
+            step()
+            tuning_steps += 1
         for _ in range(max(a.warmup, 0)):
             info = step()
         factor_ms.clear()
@@ -222,7 +230,10 @@ def run_ours(a):
             return
 
         mixed_factor_ms = statistics.median(factor_ms)
+        _, r_free, r_free64 = ctx.schedule_info()
         extra = {"factor_ms": round(mixed_factor_ms, 4),
+                 "schedule": {"tuning_steps_before_warmup": tuning_steps, "reserved_sms": r_free,
+                              "reserved_sms_fp64": r_free64},
                  "factor_tflops": round(flops / (mixed_factor_ms * 1e-3) / 1e12, 3),
                  "tiles_per_class": dict(zip(E.CLASS_NAMES, info.tiles)),
                  "update_flop_share": {c: round(f / max(sum(info.update_flops), 1.0), 4)
