@@ -95,15 +95,28 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
-    def start(self):
+    INTERVAL_MS = 50
+
+    def start(self, ready_timeout_s: float = 3.0):
+        """Starts the sampler and returns once it has written its first sample (or after ready_timeout_s), so that
+        sampling runs through the whole timed region that follows."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.INTERVAL_MS), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+            return
+        t_end = time.monotonic() + ready_timeout_s
+        while time.monotonic() < t_end and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
